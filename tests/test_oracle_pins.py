@@ -1,0 +1,472 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test checks the oracle against mathematics the paper fixes or that has a
+plain independent definition: closed-form two-body orbits, Stumpff closed
+forms, brute-force long-double pair sums, the numerical gradient of the
+interaction potential (Eq. Hb), textbook RK4 integration of the H_A flow
+(Eq. Ha), invariants of the split (Eqs. H, Ha, Hb, Hc), time symmetry, and
+second-order convergence to the full Newtonian (N+1)-body solution.
+"""
+import math
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+from oracle import nbref
+from paper_2604_09184_b300 import ics
+from refmath import (newton_barycentric_deriv, propagate_two_body, rk4_longdouble,
+                     stumpff_mp)
+
+G = ics.G_GAUSS
+MU = G * 1.0
+
+
+# ---------------------------------------------------------------- changeover
+def test_changeover_limits_and_symmetry():
+    rc = 0.01
+    for r in [0.0, 1e-5, 0.05 * rc, 0.1 * rc]:
+        K, dK = nbref.changeover(r, rc)
+        assert K == 0.0 and dK == 0.0
+    for r in [rc, 1.5 * rc, 10 * rc]:
+        K, dK = nbref.changeover(r, rc)
+        assert K == 1.0 and dK == 0.0
+    # K(y) + K(1 - y) = 1 and K(1/2) = 1/2 (the form is antisymmetric about y = 1/2)
+    for y in np.linspace(0.01, 0.99, 41):
+        r1 = 0.1 * rc + y * 0.9 * rc
+        r2 = 0.1 * rc + (1 - y) * 0.9 * rc
+        assert abs(nbref.changeover(r1, rc)[0] + nbref.changeover(r2, rc)[0] - 1) < 1e-14
+    assert abs(nbref.changeover(0.1 * rc + 0.45 * rc, rc)[0] - 0.5) < 1e-15
+
+
+def test_changeover_monotone_smooth_and_derivative():
+    rc = 0.003
+    rs = np.linspace(0.0, 1.2 * rc, 4001)
+    K = np.array([nbref.changeover(r, rc)[0] for r in rs])
+    assert np.all(np.diff(K) >= 0)
+    # derivative against central differences of K itself
+    for y in np.linspace(0.02, 0.98, 25):
+        r = 0.1 * rc + y * 0.9 * rc
+        d = 1e-7 * rc
+        fd = (nbref.changeover(r + d, rc)[0] - nbref.changeover(r - d, rc)[0]) / (2 * d)
+        assert abs(nbref.changeover(r, rc)[1] - fd) < 1e-6 * (1 / rc)
+    # C^1 at both ends: K' -> 0
+    for y in [1e-6, 1 - 1e-6]:
+        r = 0.1 * rc + y * 0.9 * rc
+        assert abs(nbref.changeover(r, rc)[1]) * rc < 1e-4
+
+
+# ---------------------------------------------------------------- Stumpff
+@pytest.mark.parametrize("z", [0.0, 1e-12, -1e-8, 0.3, -0.7, 0.999, 1.0, -1.0, 1.001, 5.0,
+                               -5.0, 30.0, -40.0, 150.0])
+def test_stumpff_closed_forms(z):
+    c = nbref.stumpff(z)
+    for k in range(4):
+        ref = stumpff_mp(z, k)
+        assert abs(c[k] - ref) <= 2e-15 * max(1.0, abs(ref)), (z, k, c[k], ref)
+    # recurrence c_k = 1/k! - z c_{k+2}
+    assert abs(c[0] - (1 - z * c[2])) < 1e-14 * max(1, abs(z))
+    assert abs(c[1] - (1 - z * c[3])) < 1e-14 * max(1, abs(z))
+
+
+# ---------------------------------------------------------------- Kepler drift
+def _orbit(a, e, inc, Om, om, M, mu=MU):
+    x, v = ics.elements_to_state(mu, np.array([a]), np.array([e]), np.array([inc]),
+                                 np.array([Om]), np.array([om]), np.array([M]))
+    return x[0], v[0]
+
+
+@pytest.mark.parametrize("a,e,h", [(1.0, 0.01, 6.0), (1.0, 0.3, -6.0), (0.5, 0.05, 40.0),
+                                   (5.2, 0.048, 6.0), (1.0, 0.9, 3.0), (2.0, 0.2, 2000.0),
+                                   (1.0, 0.0005, 365.25)])
+def test_kepler_drift_elliptic_closed_form(a, e, h):
+    x0, v0 = _orbit(a, e, 0.1, 0.4, 1.3, 2.0)
+    st, x1, v1, it = nbref.kepler_drift(MU, x0, v0, h)
+    assert st == 0
+    xr, vr = propagate_two_body(MU, x0, v0, h)
+    assert np.max(np.abs(x1 - xr)) <= 1e-13 * np.linalg.norm(xr)
+    assert np.max(np.abs(v1 - vr)) <= 1e-13 * np.linalg.norm(vr)
+
+
+@pytest.mark.parametrize("speed,h", [(1.5, 6.0), (3.0, -20.0), (10.0, 100.0)])
+def test_kepler_drift_hyperbolic_closed_form(speed, h):
+    x0 = np.array([0.8, 0.3, 0.05])
+    vesc = math.sqrt(2 * MU / np.linalg.norm(x0))
+    v0 = speed * vesc * np.array([-0.2, 0.97, 0.1]) / np.linalg.norm([-0.2, 0.97, 0.1])
+    st, x1, v1, _ = nbref.kepler_drift(MU, x0, v0, h)
+    assert st == 0
+    xr, vr = propagate_two_body(MU, x0, v0, h)
+    assert np.max(np.abs(x1 - xr)) <= 1e-13 * np.linalg.norm(xr)
+    assert np.max(np.abs(v1 - vr)) <= 1e-13 * np.linalg.norm(vr)
+
+
+def test_kepler_circular_orbit_is_rotation():
+    r = 1.3
+    w = math.sqrt(MU / r ** 3)
+    x0 = np.array([r, 0.0, 0.0])
+    v0 = np.array([0.0, r * w, 0.0])
+    for h in [1.0, 6.0, 100.0, -37.0]:
+        st, x1, v1, _ = nbref.kepler_drift(MU, x0, v0, h)
+        ph = w * h
+        assert np.allclose(x1, [r * math.cos(ph), r * math.sin(ph), 0.0], rtol=0, atol=1e-14 * r)
+        assert np.allclose(v1, [-r * w * math.sin(ph), r * w * math.cos(ph), 0.0], rtol=0,
+                           atol=1e-14 * r * w)
+
+
+def test_kepler_fg_wronskian_and_invariants():
+    rng = np.random.default_rng(1)
+    for _ in range(40):
+        a = rng.uniform(0.3, 6.0)
+        e = rng.uniform(0.0, 0.95)
+        x0, v0 = _orbit(a, e, rng.uniform(0, 1), rng.uniform(0, 6), rng.uniform(0, 6),
+                        rng.uniform(0, 6))
+        h = rng.uniform(-50, 50)
+        st, fg = nbref.kepler_fg(MU, x0, v0, h)
+        assert st == 0
+        f, g, fd, gd = fg
+        assert abs(f * gd - fd * g - 1.0) < 1e-13
+        st, x1, v1, _ = nbref.kepler_drift(MU, x0, v0, h)
+        E0 = 0.5 * v0 @ v0 - MU / np.linalg.norm(x0)
+        E1 = 0.5 * v1 @ v1 - MU / np.linalg.norm(x1)
+        assert abs(E1 - E0) <= 1e-13 * abs(E0)
+        L0, L1 = np.cross(x0, v0), np.cross(x1, v1)
+        assert np.linalg.norm(L1 - L0) <= 1e-13 * np.linalg.norm(L0)
+
+
+def test_kepler_many_drifts_track_closed_form():
+    x0, v0 = _orbit(1.0, 0.05, 0.02, 0.3, 0.7, 0.1)
+    x, v = x0.copy(), v0.copy()
+    h = 6.0
+    for _ in range(10_000):
+        st, x, v, _ = nbref.kepler_drift(MU, x, v, h)
+        assert st == 0
+    xr, vr = propagate_two_body(MU, x0, v0, h * 10_000)
+    assert np.max(np.abs(x - xr)) <= 1e-11 * np.linalg.norm(xr)
+
+
+def test_kepler_iteration_cap_reports_noconv():
+    x0, v0 = _orbit(1.0, 0.6, 0.1, 0.2, 0.3, 0.4)
+    st, *_ = nbref.kepler_drift(MU, x0, v0, 300.0, max_iter=1)
+    assert st == nbref.lib().nbref_kepler_drift.restype(-4).value if False else st == -4
+
+
+def test_kepler_time_reversal():
+    x0, v0 = _orbit(0.7, 0.2, 0.05, 1.0, 2.0, 3.0)
+    _, x1, v1, _ = nbref.kepler_drift(MU, x0, v0, 17.0)
+    _, x2, v2, _ = nbref.kepler_drift(MU, x1, v1, -17.0)
+    assert np.max(np.abs(x2 - x0)) < 1e-14 * 4
+
+
+# ---------------------------------------------------------------- forces and flags
+def _brute_newton(x, m):
+    xl = np.asarray(x, dtype=np.longdouble)
+    ml = np.asarray(m, dtype=np.longdouble)
+    n = len(m)
+    a = np.zeros((n, 3), dtype=np.longdouble)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                d = xl[j] - xl[i]
+                r = np.sqrt((d * d).sum())
+                a[i] += np.longdouble(G) * ml[j] * d / r ** 3
+    return a
+
+
+def test_forces_far_pairs_match_brute_force_newton():
+    rng = np.random.default_rng(7)
+    for n in [2, 3, 5, 8]:
+        x = rng.uniform(-2, 2, (n, 3))
+        m = rng.uniform(1e-9, 1e-3, n)
+        rc = np.full(n, 1e-6)
+        a, pairs = nbref.forces(x, m, rc, G)
+        ref = _brute_newton(x, m)
+        scale = np.abs(ref).max()
+        assert len(pairs) == 0
+        assert float(np.max(np.abs(a - ref))) <= 2e-15 * scale * n
+
+
+def test_forces_third_law():
+    d = ics.workload("toy_disk_256")
+    p = nbref.params()
+    rc = np.array([nbref.rcrit(p, d.x[i], d.v[i], d.m[i]) for i in range(d.n)])
+    a, pairs = nbref.forces(d.x, d.m, rc * 5, G)
+    ma = d.m[:, None] * a
+    assert np.abs(ma.sum(0)).max() <= 1e-13 * np.abs(ma).sum(0).max()
+
+
+def test_forces_are_minus_gradient_of_Hb_potential():
+    """Kick acceleration = -(1/m_i) dU/dx_i with U = -sum G m_i m_j K(r_ij)/r_ij (Eq. Hb),
+    so the kick weight K - r K' is checked against numerical differentiation."""
+    rng = np.random.default_rng(3)
+    n = 5
+    x = rng.uniform(-0.01, 0.01, (n, 3)) + np.array([1.0, 0.0, 0.0])
+    m = rng.uniform(1e-8, 1e-6, n)
+    rc = rng.uniform(0.004, 0.012, n)
+    a, pairs = nbref.forces(x, m, rc, G)
+    assert len(pairs) > 0
+
+    def U(xx):
+        u = mp.mpf(0)
+        for i in range(n):
+            for j in range(i + 1, n):
+                r = float(np.linalg.norm(xx[j] - xx[i]))
+                K, _ = nbref.changeover(r, max(rc[i], rc[j]))
+                u -= mp.mpf(G) * m[i] * m[j] * K / mp.mpf(r)
+        return u
+
+    for i in range(n):
+        for k in range(3):
+            dlt = 1e-7
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += dlt
+            xm[i, k] -= dlt
+            grad = float((U(xp) - U(xm)) / (2 * dlt))
+            ai = -grad / m[i]
+            assert abs(a[i, k] - ai) <= 1e-6 * np.abs(a[i]).max() + 1e-20, (i, k, a[i, k], ai)
+
+
+def test_flags_match_pair_scan():
+    rng = np.random.default_rng(11)
+    n = 60
+    x = rng.uniform(-0.05, 0.05, (n, 3)) + np.array([1.0, 0.0, 0.0])
+    rc = rng.uniform(0.005, 0.02, n)
+    m = np.full(n, 1e-9)
+    a, pairs = nbref.forces(x, m, rc, G)
+    ref = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            r = np.linalg.norm(x[j] - x[i])
+            rcij = max(rc[i], rc[j])
+            if abs(r / rcij - 1) < 1e-9:
+                pytest.skip("pair on the threshold")
+            if r < rcij:
+                ref.append((i, j))
+    assert [tuple(p) for p in pairs] == ref
+
+
+# ---------------------------------------------------------------- Bulirsch-Stoer
+def test_bs_without_close_force_reproduces_kepler():
+    """Members farther apart than rc feel no close force (1 - w = 0): BS must
+    give the closed-form two-body orbits."""
+    p = nbref.params(merge=0)
+    x = np.array([[1.0, 0.0, 0.0], [0.0, 1.2, 0.01]])
+    v = np.array([[0.0, 0.0172, 0.0001], [-0.0155, 0.0, 0.0]])
+    res = nbref.bs_group(p, x, v, [1e-7, 1e-7], [1e-6, 1e-6], [1e-4, 1e-4], 6.0)
+    assert res["status"] == 0
+    for b in range(2):
+        xr, vr = propagate_two_body(MU, x[b], v[b], 6.0)
+        assert np.max(np.abs(res["x"][b] - xr)) <= 1e-13 * np.linalg.norm(xr)
+        assert np.max(np.abs(res["v"][b] - vr)) <= 1e-13 * np.linalg.norm(vr)
+
+
+def _ha_group_deriv(m, rc):
+    """H_A restricted to a group (Eq. Ha) in long double, for the RK4 pin."""
+    ml = np.asarray(m, dtype=np.longdouble)
+    Gl = np.longdouble(G)
+    n = len(m)
+
+    def K_and_w(r, rcij):
+        y = (r - np.longdouble(0.1) * rcij) / (np.longdouble(0.9) * rcij)
+        if y <= 0:
+            return np.longdouble(0)
+        if y >= 1:
+            return np.longdouble(1)
+        d = 2 * y * y - 2 * y + 1
+        K = y * y / d
+        dK = 2 * y * (1 - y) / (d * d) / (np.longdouble(0.9) * rcij)
+        return K - r * dK
+
+    def f(y):
+        out = np.zeros_like(y)
+        for i in range(n):
+            xi = y[6 * i:6 * i + 3]
+            out[6 * i:6 * i + 3] = y[6 * i + 3:6 * i + 6]
+            r = np.sqrt((xi * xi).sum())
+            acc = -Gl * xi / r ** 3
+            for j in range(n):
+                if j == i:
+                    continue
+                d = y[6 * j:6 * j + 3] - xi
+                q = np.sqrt((d * d).sum())
+                w = K_and_w(q, np.longdouble(max(rc[i], rc[j])))
+                acc = acc + Gl * ml[j] * (1 - w) * d / q ** 3
+            out[6 * i + 3:6 * i + 6] = acc
+        return out
+
+    return f
+
+
+@pytest.mark.parametrize("rc", [(4e-3, 3e-3), (1e-2, 8e-3)])
+def test_bs_close_pair_matches_longdouble_rk4(rc):
+    """A star + 2-body hyperbolic flyby through the changeover zone (first
+    case) or inside 0.1 rc (second case): BS vs classical RK4 in long double."""
+    p = nbref.params(merge=0)
+    m = [3e-7, 2e-7]
+    x = np.array([[1.0, 0.0, 0.0], [1.006, 5e-4, 1e-5]])
+    v = np.array([[0.0, 0.0172, 0.0], [-2e-3, 0.0172, 1e-6]])
+    res = nbref.bs_group(p, x, v, m, [1e-9, 1e-9], list(rc), 6.0)
+    assert res["status"] == 0
+    y0 = np.concatenate([np.concatenate([x[b], v[b]]) for b in range(2)])
+    yr = rk4_longdouble(_ha_group_deriv(m, rc), y0, 6.0, 40000).astype(np.float64)
+    for b in range(2):
+        assert np.max(np.abs(res["x"][b] - yr[6 * b:6 * b + 3])) <= 1e-12
+        # K is only C^1 at the edges of the changeover zone, so the extrapolation
+        # error estimate is optimistic there; the velocity bound allows for it
+        # (a dropped or sign-flipped close term would be off by ~1e-6).
+        assert np.max(np.abs(res["v"][b] - yr[6 * b + 3:6 * b + 6])) <= 5e-13
+
+
+def test_bs_deterministic():
+    p = nbref.params(merge=1)
+    x = np.array([[1.0, 0.0, 0.0], [1.0005, 0.0001, 0.0]])
+    v = np.array([[0.0, 0.0172, 0.0], [0.0, 0.0171, 0.0]])
+    r1 = nbref.bs_group(p, x, v, [1e-7, 1e-7], [1e-6, 1e-6], [3e-3, 3e-3], 6.0)
+    r2 = nbref.bs_group(p, x, v, [1e-7, 1e-7], [1e-6, 1e-6], [3e-3, 3e-3], 6.0)
+    assert np.array_equal(r1["x"], r2["x"]) and np.array_equal(r1["v"], r2["v"])
+    assert r1["stats"] == r2["stats"]
+
+
+def test_bs_halving_cap_reports_noconv():
+    p = nbref.params(merge=0, bs_kmax=3, bs_max_halvings=0, bs_tol=1e-30)
+    x = np.array([[1.0, 0.0, 0.0], [1.0003, 0.0, 0.0]])
+    v = np.array([[0.0, 0.0172, 0.0], [0.0, 0.0169, 0.0]])
+    res = nbref.bs_group(p, x, v, [1e-7, 1e-7], [1e-9, 1e-9], [3e-3, 3e-3], 6.0)
+    assert res["status"] == -4
+
+
+def test_merge_conserves_mass_and_momentum():
+    """Two overlapping bodies merge after the first substep: the survivor
+    carries the summed mass, the pair momentum and (R1^3 + R2^3)^(1/3)."""
+    p = nbref.params(merge=1)
+    m = np.array([2e-7, 1e-7])
+    R = np.array([5e-5, 4e-5])
+    x = np.array([[1.0, 0.0, 0.0], [1.0 + 6e-5, 1e-5, 0.0]])
+    v = np.array([[0.0, 0.0172, 0.0], [-5e-4, 0.0172, 1e-5]])
+    h = 1e-9
+    res = nbref.bs_group(p, x, v, m, R, [3e-3, 3e-3], h)
+    assert res["status"] == 0
+    assert list(res["alive"]) == [1, 0]
+    assert res["m"][0] == m.sum()
+    assert abs(res["R"][0] - np.cbrt((R ** 3).sum())) < 1e-18
+    assert res["stats"]["merges"] == 1
+    p_pair = (m[:, None] * v).sum(0)
+    # the star changes v by ~|a| h = 3e-13 during the 1e-9-day substep
+    assert np.max(np.abs(res["m"][0] * res["v"][0] - p_pair)) <= 1e-10 * np.abs(p_pair).max()
+    # energy removed = two-body energy before - merged body energy after
+    mu = G
+    e_before = (0.5 * m * (v ** 2).sum(1)).sum() - (mu * m / np.linalg.norm(x, axis=1)).sum() \
+        - G * m[0] * m[1] / np.linalg.norm(x[1] - x[0])
+    vm = p_pair / m.sum()
+    xm = (m[:, None] * x).sum(0) / m.sum()
+    e_after = 0.5 * m.sum() * vm @ vm - mu * m.sum() / np.linalg.norm(xm)
+    assert abs(res["E_lost"] - (e_before - e_after)) <= 1e-6 * abs(e_before - e_after)
+
+
+# ---------------------------------------------------------------- the step
+def _sparse_system(n, seed=5, mass=1e-7, spacing_au=0.15):
+    rng = np.random.default_rng(seed)
+    a = 0.6 + spacing_au * np.arange(n)
+    els = dict(a=a, e=rng.uniform(0, 0.03, n), inc=rng.uniform(0, 0.02, n),
+               Om=rng.uniform(0, 6.28, n), om=rng.uniform(0, 6.28, n), M=rng.uniform(0, 6.28, n))
+    x, vh = ics.elements_to_state(G * (1 + mass), els["a"], els["e"], els["inc"], els["Om"],
+                                  els["om"], els["M"])
+    m = np.full(n, mass)
+    v = vh - (m[:, None] * vh).sum(0) / (1 + m.sum())
+    return x, v, m, np.full(n, 1e-6)
+
+
+def test_step_single_test_particle_is_kepler():
+    x0, v0 = _orbit(1.1, 0.1, 0.05, 0.3, 0.2, 0.1)
+    p = nbref.params(dt_rcrit=6.0)
+    s = nbref.RefSystem(p, x0[None], v0[None], [1e-30], [1e-9])
+    s.step(200, 6.0)
+    st = s.state()
+    xr, vr = propagate_two_body(MU, x0, v0, 1200.0)
+    assert np.max(np.abs(st["x"][0] - xr)) <= 1e-12
+
+
+def test_step_energy_and_angular_momentum_conserved():
+    x, v, m, R = _sparse_system(8, mass=3e-6)
+    p = nbref.params(merge=0, dt_rcrit=6.0)
+    s = nbref.RefSystem(p, x, v, m, R)
+    e0 = s.energy_momentum()
+    errs = []
+    for _ in range(100):
+        s.step(100, 6.0)
+        em = s.energy_momentum()
+        errs.append(abs(em["E"] / e0["E"] - 1))
+        assert np.linalg.norm(em["L"] - e0["L"]) <= 1e-12 * np.linalg.norm(e0["L"])
+    assert s.stats()["encounter_pairs"] == 0
+    errs = np.array(errs)
+    assert errs.max() < 1e-7
+    # no secular drift: the second half is not systematically worse than the first
+    assert errs[50:].max() < 3 * errs[:50].max() + 1e-15
+
+
+def test_step_time_reversible():
+    x, v, m, R = _sparse_system(6, mass=1e-6)
+    p = nbref.params(merge=0, dt_rcrit=6.0)
+    s = nbref.RefSystem(p, x, v, m, R)
+    s.step(500, 6.0)
+    s.step(500, -6.0)
+    st = s.state()
+    assert np.max(np.abs(st["x"] - x)) <= 1e-13 * math.sqrt(1000)
+    assert np.max(np.abs(st["v"] - v)) <= 1e-13 * math.sqrt(1000) * 0.02
+
+
+def test_step_converges_at_second_order_to_newtonian_solution():
+    """The split B C A C B is a second-order approximation of the full
+    Newtonian (N+1)-body flow: halving h divides the error by ~4."""
+    x, v, m, R = _sparse_system(3, mass=2e-4, spacing_au=0.5)
+    T = 240.0
+    # reference: star + bodies in an inertial frame, long-double RK4
+    M = np.concatenate([[1.0], m])
+    # democratic heliocentric -> barycentric: X_star = -sum m x / M_tot
+    Mt = M.sum()
+    xs = -(m[:, None] * x).sum(0) / Mt
+    Xb = np.vstack([xs, x + xs])
+    vstar = -(m[:, None] * v).sum(0) / 1.0
+    Vb = np.vstack([vstar, v])
+    y0 = np.concatenate([Xb.reshape(-1), Vb.reshape(-1)])
+    yT = rk4_longdouble(newton_barycentric_deriv(G, M), y0, T, 24000).astype(np.float64)
+    XT = yT[:12].reshape(4, 3)
+    xref = XT[1:] - XT[0]
+    errs = []
+    for h in [8.0, 4.0, 2.0]:
+        p = nbref.params(merge=0, dt_rcrit=h)
+        s = nbref.RefSystem(p, x, v, m, R)
+        s.step(int(round(T / h)), h)
+        errs.append(np.max(np.abs(s.state()["x"] - xref)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.2 < r1 < 4.8 and 3.2 < r2 < 4.8, errs
+
+
+def test_step_encounter_and_merger_bookkeeping():
+    p = nbref.params(merge=1, dt_rcrit=6.0)
+    x = np.array([[1.0, 0.0, 0.0], [1.0 + 8e-4, 0.0, 0.0], [0.0, 1.5, 0.0]])
+    vk = math.sqrt(MU)
+    v = np.array([[0.0, vk, 0.0], [0.0, vk * (1 / math.sqrt(1.0008)), 0.0],
+                  [-math.sqrt(MU / 1.5), 0.0, 0.0]])
+    v[1, 0] = -2e-4
+    m = np.array([1e-7, 1e-7, 1e-7])
+    R = np.array([1e-4, 1e-4, 1e-6])
+    s = nbref.RefSystem(p, x, v, m, R)
+    em0 = s.energy_momentum()
+    s.step(3, 6.0)
+    enc = s.encounter_list()
+    assert len(enc) >= 1 and tuple(enc[0]) == (0, 0, 1)
+    assert s.n_active == 2
+    st = s.state()
+    assert list(st["ids"]) == [0, 2]
+    assert st["m"][0] == 2e-7
+    em1 = s.energy_momentum()
+    assert abs((em1["E"] + em1["E_lost"]) - em0["E"]) <= 1e-6 * abs(em0["E"])
+
+
+def test_invalid_inputs_rejected():
+    p = nbref.params()
+    x = np.array([[1.0, 0.0, np.nan]])
+    with pytest.raises(ValueError):
+        nbref.RefSystem(p, x, np.zeros((1, 3)), [1e-9], [1e-9])
+    with pytest.raises(ValueError):
+        nbref.RefSystem(p, np.ones((1, 3)), np.zeros((1, 3)), [0.0], [1e-9])
