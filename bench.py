@@ -1,0 +1,379 @@
+"""Benchmark of the hybrid symplectic step on the 64k MMSN disk.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: 65536 equal-mass planetesimals (5 Earth masses on 0.5-4 AU,
+Sigma ~ a^-1.5, e/i Rayleigh 0.01/0.005) plus Jupiter and Saturn analogues,
+N = 65538 bodies, dt = 6 days, synthetic seeded initial conditions. One step
+is the whole hot path: B(h/2) C(h/2) A(h) C(h/2) B(h/2) with the O(N^2) kick
+and flags, encounter groups, Bulirsch-Stoer and the incremental force update.
+
+Metric: pair interactions per second, N (N - 1) per step (one force
+evaluation per step), FP64. The line also carries steps/s, the mixed-precision
+kick's throughput, the roofline of the dominant kernel (the kick), the end-to-
+end number through the C ABI with host buffers, the oracle on the host cores,
+and the SM clocks sampled during the timed region.
+
+Under torchrun (N > 1) every rank integrates its own replica of the workload
+on its own GPU (the single-system step does not shard across ranks); the
+reported value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s & steps/s at N=65536 (FP64, % peak); mixed vs FP64"
+UNIT = "pair interactions/s"
+WORKLOAD = "mmsn_64k_js"
+FLOP_PER_PAIR = 20        # direct-summation convention (Nyland, Harris & Prins 2007)
+FP64_INSTR_PER_PAIR = 16  # FP64 instructions in the kick's pair loop (FP64 mode)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="planetesimal count override (small runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu),
+                                       "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def pairs_per_step(n):
+    return float(n) * float(n - 1)
+
+
+def flush_l2(buf):
+    buf.add_(1)  # 256 MiB read+write, larger than the 126 MB L2
+
+
+# ------------------------------------------------------------------ oracle arms
+def oracle_step_time(disk, steps: int, threads: int):
+    """Wall time per step of the CPU oracle on `threads` host cores."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    from oracle import nbref
+    p = nbref.params(dt_rcrit=disk.dt)
+    s = nbref.RefSystem(p, disk.x, disk.v, disk.m, disk.R)
+    t0 = time.perf_counter()
+    st = s.step(steps, disk.dt)
+    t1 = time.perf_counter()
+    if st != 0:
+        raise RuntimeError("oracle step failed: %d" % st)
+    return (t1 - t0) / steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2604_09184_b300 import ics
+    disk = ics.workload(args.workload, n=args.n)
+    threads = os.cpu_count() or 1
+    # each timed step is one full oracle step of the same workload
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    from oracle import nbref
+    p = nbref.params(dt_rcrit=disk.dt)
+    s = nbref.RefSystem(p, disk.x, disk.v, disk.m, disk.R)
+    for _ in range(args.warmup):
+        s.step(1, disk.dt)
+    t0 = time.perf_counter()
+    s.step(args.steps, disk.dt)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = pairs_per_step(disk.n) / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "n_bodies": disk.n,
+                                        "dt_days": disk.dt, "l2": "host run"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d full oracle steps of %s (N=%d)" % (args.steps,
+                                                                           args.workload, disk.n)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2604_09184_b300 import build, ics
+    build.build()
+    from paper_2604_09184_b300 import nb
+
+    disk = ics.workload(args.workload, n=args.n)
+    n = disk.n
+    pps = pairs_per_step(n)
+
+    # CPU baseline first (before any GPU work), rank 0 only, bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        t_step = oracle_step_time(disk, 1, threads)
+        cpu = {"value": pps / t_step, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "1 full oracle step of %s (N=%d), %d OpenMP threads, %.1f s" % (
+                   args.workload, n, threads, t_step)}
+
+    stream = torch.cuda.current_stream()
+    f64_peak, f32_peak = nb.measure_peaks()
+
+    p = nb.params(dt_rcrit=disk.dt, precision=nb.NB_PREC_FP64)
+    sysm = nb.NBodySystem(p, disk.x, disk.v, disk.m, disk.R)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        sysm.step(1, disk.dt)
+    sysm.set_timing(True)
+    launches0 = sysm.timing()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        sysm.step(1, disk.dt)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    tm = sysm.timing()
+    gpu_launches = tm["launches"] - launches0
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / max(args.steps, 1)
+    value = world * pps * args.steps / (total_ms * 1e-3)
+    kick_ms = tm["kick_ms"] / max(tm["kick_launches"], 1)
+    st = sysm.stats()
+
+    achieved = FLOP_PER_PAIR * pps / (kick_ms * 1e-3)
+    roofline = {
+        "bound": "alu", "achieved": achieved / 1e12, "peak": f64_peak / 1e12, "unit": "TFLOP/s",
+        "frac": achieved / f64_peak, "traffic": None,
+        "kernel": "k_kick<FP64>", "kick_ms": kick_ms,
+        "flop_per_pair": FLOP_PER_PAIR,
+        "peak_source": "FP64 DFMA loop measured in this run (nb_measure_peaks)",
+        "fp64_pipe_frac": FP64_INSTR_PER_PAIR * pps / (kick_ms * 1e-3) / (f64_peak / 2),
+        "fp32_peak_tflops": f32_peak / 1e12,
+    }
+    traffic_file = os.path.join(ROOT, "profiles", "kick_fp64_traffic.json")
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            tr = json.load(f)
+        if tr.get("n") == n:
+            roofline["traffic"] = tr.get("bytes_per_launch")
+
+    # mixed-precision kick on the same workload
+    mixed = None
+    if not args.no_mixed:
+        pm = nb.params(dt_rcrit=disk.dt, precision=nb.NB_PREC_MIXED)
+        sm = nb.NBodySystem(pm, disk.x, disk.v, disk.m, disk.R)
+        for _ in range(max(args.warmup, 0)):
+            sm.step(1, disk.dt)
+        sm.set_timing(True)
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush_l2(flush)
+            evm[k][0].record(stream)
+            sm.step(1, disk.dt)
+            evm[k][1].record(stream)
+        torch.cuda.synchronize()
+        mms = sum(a.elapsed_time(b) for a, b in evm) / max(args.steps, 1)
+        mk = sm.timing()
+        mkick = mk["kick_ms"] / max(mk["kick_launches"], 1)
+        # accuracy of the mixed kick against the FP64 kick on the initial state
+        xg = torch.as_tensor(disk.x, device="cuda")
+        mg = torch.as_tensor(disk.m, device="cuda")
+        rc = torch.as_tensor(nb_rc_initial(nb, disk), device="cuda")
+        a64, _, _ = nb.kick(xg, mg, rc, precision=nb.NB_PREC_FP64)
+        amx, _, _ = nb.kick(xg, mg, rc, precision=nb.NB_PREC_MIXED)
+        rel = (torch.linalg.norm(amx - a64, dim=1) / torch.linalg.norm(a64, dim=1)).max().item()
+        mixed = {"value": pps / (mms * 1e-3), "unit": UNIT, "ms_per_step": mms,
+                 "kick_ms": mkick, "speedup_step": ms_per_step / mms,
+                 "speedup_kick": kick_ms / mkick, "max_rel_err_accel_vs_fp64": rel}
+        del sm
+
+    # end to end through the C ABI with host buffers: per step, load the state
+    # from pinned host memory, step, read the state back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(nb, torch, sysm, disk, args.steps, pps)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "steps_per_s": 1e3 / ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_bodies": n, "dt_days": disk.dt,
+                   "precision": "fp64", "parallelism": "replica per GPU" if world > 1 else "1 GPU",
+                   "l2": "flushed before each timed step (256 MiB write, outside the step events)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+        "clocks": clk, "gpu_launches": gpu_launches,
+        "encounters": {"pairs": st["encounter_pairs"], "groups": st["groups"],
+                       "bs_substeps": st["bs_substeps"], "merges": st["merges"],
+                       "steps_total": st["steps"]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def nb_rc_initial(nb, disk):
+    s = nb.NBodySystem(nb.params(dt_rcrit=disk.dt), disk.x, disk.v, disk.m, disk.R)
+    rc = s.state()["rc"]
+    del s
+    return rc
+
+
+def run_e2e(nb, torch, sysm, disk, steps, pps):
+    n = disk.n
+    st = sysm.state()
+    a, pairs = sysm.fsal()
+    pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()  # noqa: E731
+    hx, hv, hm, hR, hrc = pin(st["x"]), pin(st["v"]), pin(st["m"]), pin(st["R"]), pin(st["rc"])
+    hid = pin(st["ids"].astype(np.int32))
+    ha = pin(a[:n])
+    hp = pin(pairs.astype(np.int32).reshape(-1, 2))
+    ox, ov, om, oR, orc = (torch.empty_like(t).pin_memory() for t in (hx, hv, hm, hR, hrc))
+    oid = torch.empty_like(hid).pin_memory()
+    import ctypes as C
+    L = nb.lib()
+    k = C.c_int()
+    h2d = sum(t.numel() * t.element_size() for t in (hx, hv, hm, hR, hrc, hid, ha, hp))
+    d2h = sum(t.numel() * t.element_size() for t in (ox, ov, om, oR, orc, oid))
+    if sysm.n != n:
+        return None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rcode = L.nb_set_state(sysm._h, C.c_void_p(hx.data_ptr()), C.c_void_p(hv.data_ptr()),
+                               C.c_void_p(hm.data_ptr()), C.c_void_p(hR.data_ptr()),
+                               C.c_void_p(hrc.data_ptr()), C.c_void_p(hid.data_ptr()),
+                               C.c_void_p(ha.data_ptr()), C.c_void_p(hp.data_ptr()),
+                               int(hp.shape[0]), 0)
+        if rcode:
+            return {"error": nb.status_string(rcode)}
+        rcode = L.nb_step(sysm._h, 1, disk.dt)
+        if rcode:
+            return {"error": nb.status_string(rcode)}
+        rcode = L.nb_get_state(sysm._h, C.c_void_p(ox.data_ptr()), C.c_void_p(ov.data_ptr()),
+                               C.c_void_p(om.data_ptr()), C.c_void_p(oR.data_ptr()),
+                               C.c_void_p(orc.data_ptr()), C.c_void_p(oid.data_ptr()),
+                               C.byref(k), 0)
+        if rcode:
+            return {"error": nb.status_string(rcode)}
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / max(steps, 1)
+    return {"value": pps / t, "unit": UNIT, "ms_per_step": t * 1e3,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "nb_set_state (pinned host) + nb_step(1) + nb_get_state (pinned host)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * nb.h — C ABI of the B300 hybrid symplectic N-body library (libnb.so).
+ *
+ * The library integrates a planetary system with the hybrid symplectic
+ * method of Grimm & Stadel ("Terrestrial planet formation in the era of GPU
+ * computing", section "The hybrid symplectic integrator"):
+ *   H = H_A + H_B + H_C                                            (Eq. H)
+ *   H_A  Kepler motion about the star + the (1 - K) close part     (Eq. Ha)
+ *   H_B  mutual interaction weighted by the changeover K(r_ij)     (Eq. Hb)
+ *   H_C  |sum p|^2 / (2 m0), the momentum term of mixed variables  (Eq. Hc)
+ *   r_crit,i = max(3 R_Hill,i, 0.4 dt v_i)                         (Eq. rcrit)
+ * One step is B(h/2) C(h/2) A(h) C(h/2) B(h/2); A is the Kepler drift of
+ * every body, replaced by a Bulirsch-Stoer integration of H_A for bodies in
+ * a close-encounter group (the "direct solver" of the same section), with
+ * perfect merging on contact (section "Detailing the outcomes of collisions").
+ *
+ * Conventions
+ *  - Units: AU, day, solar mass. The star is implicit (mass m0). Bodies carry
+ *    heliocentric positions x and barycentric velocities v (democratic
+ *    heliocentric coordinates), interleaved [n][3] in every argument.
+ *  - All device memory is provided by the caller: the library never calls
+ *    cudaMalloc or cudaFree. nb_workspace_bytes() sizes the workspace.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy stream.
+ *  - Functions return NB_OK (0) or a negative NB_E_* code; they never throw.
+ *    nb_last_error() gives a message for the last failure on a handle.
+ *  - Body order is the caller's order; ids must be strictly increasing, so
+ *    index order and id order agree. A merger keeps the lower id.
+ *  - nb_step() is atomic: on any error the state is restored to what it was
+ *    when the call started.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_OK 0
+#define NB_E_INVALID (-1)   /* bad argument, NaN/Inf input, n < 1, ids not increasing */
+#define NB_E_CUDA (-2)      /* a CUDA runtime call failed */
+#define NB_E_OVERFLOW (-3)  /* flagged-pair or group buffer full; grow pair_capacity */
+#define NB_E_NOCONV (-4)    /* Kepler or Bulirsch-Stoer iteration cap reached */
+#define NB_E_TIMEOUT (-5)   /* a bounded device loop gave up */
+#define NB_E_WORKSPACE (-6) /* workspace too small or not 256-byte aligned */
+
+#define NB_PREC_FP64 0  /* kick pair terms in FP64 */
+#define NB_PREC_MIXED 1 /* FP32 r^-3 seed, one FP64 Newton step, compensated sums */
+
+typedef struct {
+  double G;            /* gravitational constant; default k^2 = 2.959122082855911e-4 */
+  double m0;           /* central mass; default 1 */
+  double dt_rcrit;     /* time step in the velocity term of Eq. rcrit; default 6 days */
+  double hill_factor;  /* Eq. rcrit, default 3 */
+  double vel_factor;   /* Eq. rcrit, default 0.4 */
+  int vel_mode;        /* 0: |v - v_circ(x)| (default); 1: |v| */
+  int merge;           /* 1: perfect merging on contact (default) */
+  int precision;       /* NB_PREC_FP64 (default) or NB_PREC_MIXED */
+  int kepler_max_iter; /* Kepler iteration cap, default 30 */
+  double bs_tol;       /* Bulirsch-Stoer relative tolerance, default 1e-14 */
+  int bs_kmax;         /* extrapolation columns (substeps 2k), default 8, at most 12 */
+  int bs_max_halvings; /* default 20 */
+  int pair_capacity;   /* flagged-pair buffer, pairs; 0 = max(4096, 4n) */
+  int log_capacity;    /* encounter-log entries per nb_step call; 0 = 1<<20 */
+  int kick_split;      /* j-chunks per i-tile in the kick; 0 = automatic */
+} nb_params;
+
+typedef struct {
+  long long steps;           /* integrator steps completed */
+  long long force_evals;     /* full O(N^2) kick evaluations */
+  long long encounter_pairs; /* sum over steps of |E| */
+  long long groups;          /* close-encounter groups integrated */
+  long long bs_substeps;     /* accepted BS substeps */
+  long long bs_halvings;     /* BS substep halvings */
+  long long bs_derivs;       /* BS right-hand-side evaluations */
+  long long merges;          /* perfect mergers */
+  long long kepler_iters;    /* Kepler iterations summed over bodies and steps */
+  long long moved_bodies;    /* bodies re-integrated by BS (incremental force update) */
+  long long log_dropped;     /* encounter-log entries that did not fit */
+  int n_active;              /* bodies not absorbed by a merger */
+  int last_pairs;            /* |F| of the last force evaluation */
+} nb_stats_t;
+
+typedef struct nb_system nb_system; /* opaque host handle (small, malloc'd by the library) */
+
+/* Fill p with the defaults listed above. */
+void nb_default_params(nb_params* p);
+
+/* Bytes of device workspace that nb_init_system() needs for n bodies. */
+size_t nb_workspace_bytes(const nb_params* p, int n);
+
+/* Create a system in the caller's device workspace (>= nb_workspace_bytes,
+ * 256-byte aligned) and evaluate the first kick and flags (the cached
+ * "first same as last" force). x, v: [n][3]; m, R: [n]; rc_override: [n] or
+ * NULL (then r_crit follows Eq. rcrit); ids: [n] strictly increasing or NULL
+ * (then 0..n-1). The inputs are host pointers when inputs_on_device == 0,
+ * device pointers otherwise; they are copied in and not retained. The
+ * workspace must stay allocated until nb_destroy(). Returns NB_E_INVALID for
+ * NaN/Inf, m <= 0, R < 0, rc <= 0 or ids not increasing. */
+int nb_init_system(nb_system** out, const nb_params* p, int n, const double* x, const double* v,
+                   const double* m, const double* R, const double* rc_override, const int* ids,
+                   void* workspace, size_t ws_bytes, void* stream, int inputs_on_device);
+
+/* Replace the cached force and flag set (resume a run bit-exactly): a is
+ * [n][3] over all n slots, pairs_ij holds npairs (i, j) index pairs, i < j. */
+int nb_set_fsal(nb_system* s, const double* a, const int* pairs_ij, int npairs, int on_device);
+
+/* Load a complete state into an existing system of the same n (checkpoint
+ * restore, or feeding a new batch into a resident workspace): x, v [n][3],
+ * m, R, rc [n] (rc required), ids [n] or NULL, the cached force a [n][3] and
+ * npairs flagged index pairs. No force is evaluated. Host pointers when
+ * on_device == 0. Validation as in nb_init_system (NB_E_INVALID; the previous
+ * state is then undefined and must be reloaded). */
+int nb_set_state(nb_system* s, const double* x, const double* v, const double* m,
+                 const double* R, const double* rc, const int* ids, const double* a,
+                 const int* pairs_ij, int npairs, int on_device);
+
+/* Event timing of the kick launches inside nb_step (off by default).
+ * nb_timing() returns the summed kick time in ms and the number of timed kick
+ * launches since timing was enabled, and the total number of kernels the
+ * handle has launched. */
+int nb_set_timing(nb_system* s, int enable);
+int nb_timing(nb_system* s, double* kick_ms, long long* kick_launches, long long* launches);
+
+/* Advance nsteps steps of size dt (dt may be negative). Synchronises the
+ * stream before returning. The encounter log is cleared at entry. */
+int nb_step(nb_system* s, int nsteps, double dt);
+
+/* Total energy E = H_A + H_B + H_C (K cancels, Eqs. Ha-Hc), angular
+ * momentum L = sum m x cross v, P = sum m v and the energy removed by
+ * mergers. Host outputs; any pointer may be NULL. */
+int nb_energy_momentum(nb_system* s, double* E, double L[3], double P[3], double* E_lost);
+
+/* Active bodies in ascending id: x, v [k][3], m, R, rc [k], ids [k]. Any
+ * pointer may be NULL. Outputs are device pointers when out_on_device != 0.
+ * *n_active (host) receives k. */
+int nb_get_state(nb_system* s, double* x, double* v, double* m, double* R, double* rc, int* ids,
+                 int* n_active, int out_on_device);
+
+/* Cached force of all n slots [n][3] and the cached flag set (index pairs).
+ * *npairs (host) receives the pair count; at most cap pairs are written. */
+int nb_get_fsal(nb_system* s, double* a, int* pairs_ij, int cap, int* npairs, int out_on_device);
+
+/* Encounter pairs of the last nb_step() call as (step, id_i, id_j) triples,
+ * id_i < id_j, sorted by step then ids (host output). *count receives the
+ * total; if it exceeds cap, cap triples are written and NB_E_OVERFLOW is
+ * returned. */
+int nb_encounter_list(nb_system* s, int* step_ij, int cap, int* count);
+
+int nb_stats(nb_system* s, nb_stats_t* out);
+void nb_destroy(nb_system* s);
+const char* nb_last_error(const nb_system* s);
+const char* nb_status_string(int status);
+
+/* ---------------------------------------------------------------------
+ * Single-kernel entry points (one launch each, on caller device buffers).
+ * --------------------------------------------------------------------- */
+
+/* Kick accelerations (gradient of Eq. Hb) and close-pair flags of n bodies.
+ * x [n][3], m [n], rc [n] device inputs; a [n][3] device output; pairs_ij
+ * device output of up to cap (i, j) pairs, i < j, unordered; *npairs (host)
+ * receives the total count. scratch: device buffer of
+ * nb_kick_scratch_bytes(n, split) bytes. precision: NB_PREC_*. Returns
+ * NB_E_OVERFLOW when more than cap pairs were found (all others written). */
+size_t nb_kick_scratch_bytes(int n, int split);
+int nb_kick(int n, const double* x, const double* m, const double* rc, double G, int precision,
+            int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,
+            size_t scratch_bytes, void* stream);
+
+/* Universal-variable Kepler drift (first sum of Eq. Ha) of n bodies about
+ * mu = G m0 by dt, in place on device x, v [n][3]. Returns NB_E_NOCONV if a
+ * body hit max_iter. scratch: 16 bytes of device memory. */
+int nb_kepler_drift(int n, double mu, double* x, double* v, double dt, int max_iter,
+                    void* scratch, void* stream);
+
+/* Measured throughput of the chip's FP64 (DFMA) and FP32 (FFMA) pipes in
+ * FLOP/s, from the library's own dependent-free FMA loops. scratch: at least
+ * nb_peak_scratch_bytes() of device memory. */
+size_t nb_peak_scratch_bytes(void);
+int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

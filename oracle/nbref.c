@@ -355,6 +355,57 @@ int nbref_forces(int n, const double* x, const double* m, const double* rc, doub
   return NBREF_OK;
 }
 
+/* Kick acceleration of selected targets only (all sources), and the flagged
+ * pairs that involve a selected target, as (min, max) index pairs sorted and
+ * unique. Same pair expression as forces_flags. */
+int nbref_forces_targets(int n, const double* x, const double* m, const double* rc, double G,
+                         const int* targets, int nt, double* a, int* pairs, int cap,
+                         int* npairs) {
+  pairlist l = {0, 0, 0};
+  for (int q = 0; q < nt; ++q) {
+    int i = targets[q];
+    if (i < 0 || i >= n) return NBREF_E_INVALID;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double dx = x[3 * j] - x[3 * i];
+      double dy = x[3 * j + 1] - x[3 * i + 1];
+      double dz = x[3 * j + 2] - x[3 * i + 2];
+      double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      double rc_ij = rc[i] > rc[j] ? rc[i] : rc[j];
+      double rc2 = rc_ij * rc_ij;
+      if (r2 < rc2) pl_push(&l, i < j ? i : j, i < j ? j : i);
+      if (r2 == 0.0) continue;
+      double r = sqrt(r2);
+      double w = 1.0;
+      if (r2 < rc2) w = kick_weight(r, rc_ij);
+      double f = G * m[j] * w / (r2 * r);
+      ax += f * dx;
+      ay += f * dy;
+      az += f * dz;
+    }
+    a[3 * q] = ax;
+    a[3 * q + 1] = ay;
+    a[3 * q + 2] = az;
+  }
+  if (l.n) qsort(l.ij, (size_t)l.n, 2 * sizeof(int), pair_cmp);
+  int ne = 0;
+  for (int k = 0; k < l.n; ++k) {
+    if (ne > 0 && l.ij[2 * k] == l.ij[2 * (ne - 1)] && l.ij[2 * k + 1] == l.ij[2 * (ne - 1) + 1])
+      continue;
+    l.ij[2 * ne] = l.ij[2 * k];
+    l.ij[2 * ne + 1] = l.ij[2 * k + 1];
+    ne++;
+  }
+  *npairs = ne;
+  for (int k = 0; k < ne && k < cap; ++k) {
+    pairs[2 * k] = l.ij[2 * k];
+    pairs[2 * k + 1] = l.ij[2 * k + 1];
+  }
+  free(l.ij);
+  return NBREF_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Bulirsch-Stoer integration of H_A restricted to a group: the paper's */
 /* "direct solver" for close encounters (the paragraph after Eq. rcrit).*/

@@ -78,6 +78,12 @@ double nbref_rcrit(const nbref_params* p, const double x[3], const double v[3], 
 int nbref_forces(int n, const double* x, const double* m, const double* rc, double G,
                  double* a, int* pairs, int cap, int* npairs);
 
+/* Kick acceleration of the listed targets (a: [nt][3]) and the flagged pairs
+ * that involve a listed target, sorted unique (min, max) index pairs. */
+int nbref_forces_targets(int n, const double* x, const double* m, const double* rc, double G,
+                         const int* targets, int nt, double* a, int* pairs, int cap,
+                         int* npairs);
+
 /* Integrate the H_A flow restricted to a group of n bodies over h with the
  * Gragg-Bulirsch-Stoer method and perfect merging. Arrays are updated in
  * place; alive[k] = 0 marks a body absorbed by a merger. */

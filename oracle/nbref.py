@@ -57,6 +57,8 @@ def lib():
         L.nbref_rcrit.argtypes = [C.POINTER(RefParams), _D, _D, C.c_double]
         L.nbref_rcrit.restype = C.c_double
         L.nbref_forces.argtypes = [C.c_int, _D, _D, _D, C.c_double, _D, _I, C.c_int, _I]
+        L.nbref_forces_targets.argtypes = [C.c_int, _D, _D, _D, C.c_double, _I, C.c_int, _D,
+                                           _I, C.c_int, _I]
         L.nbref_bs_group.argtypes = [C.POINTER(RefParams), C.c_int, _D, _D, _D, _D, _D, _I,
                                      C.c_double, _D, C.POINTER(RefStats)]
         L.nbref_bs_group.restype = C.c_int
@@ -142,6 +144,24 @@ def forces(x, m, rc, G=2.959122082855911e-4, cap=None):
     k = npairs.value
     if k > cap:
         return forces(x, m, rc, G, cap=k)
+    return a, pairs[:k].copy()
+
+
+def forces_targets(x, m, rc, targets, G=2.959122082855911e-4, cap=None):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    rc = np.ascontiguousarray(rc, dtype=np.float64)
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    a = np.zeros((t.shape[0], 3))
+    cap = 64 * t.shape[0] + 64 if cap is None else cap
+    pairs = np.zeros((cap, 2), dtype=np.int32)
+    npairs = C.c_int()
+    lib().nbref_forces_targets(n, _dp(x), _dp(m), _dp(rc), G, _ip(t), t.shape[0], _dp(a),
+                               _ip(pairs), cap, C.byref(npairs))
+    k = npairs.value
+    if k > cap:
+        return forces_targets(x, m, rc, targets, G, cap=k)
     return a, pairs[:k].copy()
 
 

@@ -1,0 +1,472 @@
+// O(N) parts of the step: the kick flow of H_B with the cached force (Eq. Hb),
+// the momentum drift of H_C (Eq. Hc) and the Kepler drift of H_A's first sum
+// (Eq. Ha), plus system initialisation.
+//
+// One step is B(h/2) C(h/2) A(h) C(h/2) B(h/2). k_open applies the first
+// B(h/2); k_drift applies C(h/2), saves the state for the close-encounter
+// solver and Kepler-drifts every body; k_close applies C(h/2) and B(h/2) and,
+// between two steps of one call, the next step's opening B(h/2) as a second,
+// separate addition. Partial momenta are summed per block in a fixed order
+// and re-reduced in a fixed order by the consumer, so results are
+// deterministic.
+#include "nb_internal.cuh"
+
+namespace nb {
+
+constexpr int DNT = 256;  // threads per block of the O(N) kernels
+
+// ---------------------------------------------------------------------------
+// Stumpff functions c0..c3 (Danby's method): quarter z until |z| <= 0.1,
+// sum the c2, c3 series there, rebuild c0 = 1 - z c2 and c1 = 1 - z c3, then
+// undo each quartering with the argument-quadrupling identities
+//   c0(4z) = 2 c0^2 - 1,  c1(4z) = c0 c1,  c2(4z) = c1^2 / 2,
+//   c3(4z) = (c2 + c0 c3) / 4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double& c2,
+                                        double& c3) {
+  int nq = 0;
+  while (fabs(z) > 0.1 && nq < 64) {
+    z *= 0.25;
+    ++nq;
+  }
+  // c2 = sum_k (-z)^k / (2k+2)!,  c3 = sum_k (-z)^k / (2k+3)!,  k = 0..7
+  c2 = 1.0 / 2.0 -
+       z * (1.0 / 24.0 -
+            z * (1.0 / 720.0 -
+                 z * (1.0 / 40320.0 -
+                      z * (1.0 / 3628800.0 -
+                           z * (1.0 / 479001600.0 -
+                                z * (1.0 / 87178291200.0 - z * (1.0 / 20922789888000.0)))))));
+  c3 = 1.0 / 6.0 -
+       z * (1.0 / 120.0 -
+            z * (1.0 / 5040.0 -
+                 z * (1.0 / 362880.0 -
+                      z * (1.0 / 39916800.0 -
+                           z * (1.0 / 6227020800.0 -
+                                z * (1.0 / 1307674368000.0 - z * (1.0 / 355687428096000.0)))))));
+  c1 = 1.0 - z * c3;
+  c0 = 1.0 - z * c2;
+  for (; nq > 0; --nq) {
+    c3 = (c2 + c0 * c3) * 0.25;
+    c2 = c1 * c1 * 0.5;
+    c1 = c0 * c1;
+    c0 = 2.0 * c0 * c0 - 1.0;
+  }
+}
+
+// Universal Kepler equation t(s) = r0 G1(s) + eta G2(s) + mu G3(s) = h with
+// G_k = s^k c_k(beta s^2). Newton's method from the second-order start (or,
+// for an unbound orbit deep in the exponential regime, the asymptotic
+// inverse), Laguerre-Conway (n = 5) if Newton has not converged after 10
+// updates. An update below 1e-10 |s| is followed by one last update.
+// Returns 0 or NB_E_NOCONV; on return G[0..3] hold the G_k at the final s.
+__device__ int kepler_solve(double mu, double r0, double eta, double beta, double h,
+                            int max_iter, double G[4], int* iters) {
+  double s0 = h / r0 - eta * h * h / (2.0 * r0 * r0 * r0);
+  if (beta < 0.0) {
+    const double g = sqrt(-beta);
+    if (g * fabs(s0) > 2.0) {
+      const double sg = h > 0.0 ? 1.0 : -1.0;
+      const double c = r0 + sg * eta / g + mu / (g * g);
+      const double arg = 2.0 * g * fabs(h) / c;
+      if (c > 0.0 && arg > 1.0) {
+        const double sa = sg * log(arg) / g;
+        if (fabs(sa) < fabs(s0)) s0 = sa;
+      }
+    }
+  }
+  int it = 0;
+  for (int method = 0; method < 2; ++method) {
+    double s = s0;
+    bool last = false;
+    const int cap = method == 0 ? 10 : max_iter;
+    for (int k = 0; k < cap && it < max_iter; ++k, ++it) {
+      double c0, c1, c2, c3;
+      stumpff(beta * s * s, c0, c1, c2, c3);
+      const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+      const double F = r0 * G1 + eta * G2 + mu * G3 - h;
+      const double Fp = r0 * c0 + eta * G1 + mu * G2;
+      double ds;
+      if (method == 0) {
+        ds = F / Fp;
+      } else {
+        const double Fpp = eta * c0 + (mu - beta * r0) * G1;
+        const double disc = fabs(16.0 * Fp * Fp - 20.0 * F * Fpp);
+        ds = 5.0 * F / (Fp + copysign(sqrt(disc), Fp));
+      }
+      s -= ds;
+      if (!isfinite(s)) break;
+      if (last) {
+        double d0, d1, d2, d3;
+        stumpff(beta * s * s, d0, d1, d2, d3);
+        G[0] = d0;
+        G[1] = s * d1;
+        G[2] = s * s * d2;
+        G[3] = s * s * s * d3;
+        *iters = it + 1;
+        return 0;
+      }
+      if (fabs(ds) <= 1e-10 * fabs(s)) last = true;
+    }
+    if (it >= max_iter) break;
+  }
+  *iters = it;
+  return NB_E_NOCONV;
+}
+
+// Gauss f and g drift of one body by h; returns 0 or NB_E_NOCONV.
+__device__ __forceinline__ int kepler_drift(double mu, double& x, double& y, double& z,
+                                            double& vx, double& vy, double& vz, double h,
+                                            int max_iter, int* iters) {
+  *iters = 0;
+  if (h == 0.0) return 0;
+  const double r0 = sqrt(x * x + y * y + z * z);
+  const double v2 = vx * vx + vy * vy + vz * vz;
+  const double eta = x * vx + y * vy + z * vz;
+  const double beta = 2.0 * mu / r0 - v2;
+  double G[4];
+  const int st = kepler_solve(mu, r0, eta, beta, h, max_iter, G, iters);
+  if (st) return st;
+  const double r = r0 * G[0] + eta * G[1] + mu * G[2];
+  const double fm1 = -mu * G[2] / r0;           // f - 1
+  const double g = r0 * G[1] + eta * G[2];      // g
+  const double fd = -mu * G[1] / (r * r0);      // fdot
+  const double gdm1 = -mu * G[2] / r;           // gdot - 1
+  const double nx = x + (fm1 * x + g * vx), ny = y + (fm1 * y + g * vy), nz = z + (fm1 * z + g * vz);
+  const double nvx = vx + (fd * x + gdm1 * vx), nvy = vy + (fd * y + gdm1 * vy),
+               nvz = vz + (fd * z + gdm1 * vz);
+  x = nx; y = ny; z = nz;
+  vx = nvx; vy = nvy; vz = nvz;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DNT) k_open(Dev d, double hh) {
+  __shared__ int s_stop;
+  __shared__ double red[3 * 32 + 3];
+  if (threadIdx.x == 0) s_stop = d.ctrl->status;
+  __syncthreads();
+  if (s_stop) return;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  if (i < d.n && d.alive[i]) {
+    const double vx = d.vx[i] + hh * d.ax[i];
+    const double vy = d.vy[i] + hh * d.ay[i];
+    const double vz = d.vz[i] + hh * d.az[i];
+    d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
+    const double m = d.m[i];
+    px = m * vx; py = m * vy; pz = m * vz;
+  }
+  block_sum3(px, py, pz, red);
+  if (threadIdx.x == 0) {
+    d.ppartA[3 * blockIdx.x] = px;
+    d.ppartA[3 * blockIdx.x + 1] = py;
+    d.ppartA[3 * blockIdx.x + 2] = pz;
+  }
+}
+
+__global__ void __launch_bounds__(DNT) k_drift(Dev d, Phys P, double h) {
+  __shared__ int s_stop;
+  __shared__ double red[3 * 32 + 3];
+  __shared__ unsigned long long s_it;
+  if (threadIdx.x == 0) {
+    s_stop = d.ctrl->status;
+    s_it = 0ull;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->n_ftrial = 0;  // consumed by the next kick
+  double Pt[3];
+  reduce_parts3(d.ppartA, d.ppart_n, red, Pt);
+  const double hh = 0.5 * h;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  if (i < d.n && d.alive[i]) {
+    double x = d.x[i] + hh * Pt[0] / P.m0;
+    double y = d.y[i] + hh * Pt[1] / P.m0;
+    double z = d.z[i] + hh * Pt[2] / P.m0;
+    double vx = d.vx[i], vy = d.vy[i], vz = d.vz[i];
+    d.xs[i] = x; d.ys[i] = y; d.zs[i] = z;
+    d.vxs[i] = vx; d.vys[i] = vy; d.vzs[i] = vz;
+    int it = 0;
+    const int st = kepler_drift(P.mu, x, y, z, vx, vy, vz, h, P.kepler_max_iter, &it);
+    if (st) set_status(d.ctrl, st, 10);
+    atomicAdd(&s_it, (unsigned long long)it);
+    d.x[i] = x; d.y[i] = y; d.z[i] = z;
+    d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
+    const double m = d.m[i];
+    px = m * vx; py = m * vy; pz = m * vz;
+  }
+  block_sum3(px, py, pz, red);
+  if (threadIdx.x == 0) {
+    d.ppartB[3 * blockIdx.x] = px;
+    d.ppartB[3 * blockIdx.x + 1] = py;
+    d.ppartB[3 * blockIdx.x + 2] = pz;
+    atomicAdd(&d.ctrl->stats[ST_KEPLER_ITERS], s_it);
+  }
+}
+
+__global__ void __launch_bounds__(DNT) k_close(Dev d, Phys P, double h, int last) {
+  __shared__ int s_stop;
+  __shared__ double red[3 * 32 + 3];
+  if (threadIdx.x == 0) s_stop = d.ctrl->status;
+  __syncthreads();
+  if (s_stop) return;
+  double Pt[3];
+  reduce_parts3(d.ppartB, d.ppart_n, red, Pt);
+  if (d.ctrl->n_groups > 0) {
+    Pt[0] += d.ctrl->dP[0];
+    Pt[1] += d.ctrl->dP[1];
+    Pt[2] += d.ctrl->dP[2];
+  }
+  const double hh = 0.5 * h;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  if (i < d.n && d.alive[i]) {
+    d.x[i] += hh * Pt[0] / P.m0;
+    d.y[i] += hh * Pt[1] / P.m0;
+    d.z[i] += hh * Pt[2] / P.m0;
+    const double ax = d.ax[i], ay = d.ay[i], az = d.az[i];
+    double vx = d.vx[i] + hh * ax, vy = d.vy[i] + hh * ay, vz = d.vz[i] + hh * az;
+    if (!last) {  // the next step's opening B(h/2)
+      vx += hh * ax;
+      vy += hh * ay;
+      vz += hh * az;
+      const double m = d.m[i];
+      px = m * vx; py = m * vy; pz = m * vz;
+    }
+    d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
+  }
+  if (!last) {
+    block_sum3(px, py, pz, red);
+    if (threadIdx.x == 0) {
+      d.ppartA[3 * blockIdx.x] = px;
+      d.ppartA[3 * blockIdx.x + 1] = py;
+      d.ppartA[3 * blockIdx.x + 2] = pz;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.ctrl->step_index += 1;
+    d.ctrl->stats[ST_STEPS] += 1ull;
+  }
+}
+
+int ppart_blocks(int n) { return (n + DNT - 1) / DNT; }
+
+void launch_open_h(const Dev& d, double h, cudaStream_t st) {
+  k_open<<<d.ppart_n, DNT, 0, st>>>(d, 0.5 * h);
+}
+
+void launch_drift_h(const Dev& d, const Phys& P, double h, cudaStream_t st) {
+  k_drift<<<d.ppart_n, DNT, 0, st>>>(d, P, h);
+}
+
+void launch_close_h(const Dev& d, const Phys& P, double h, int last, cudaStream_t st) {
+  k_close<<<d.ppart_n, DNT, 0, st>>>(d, P, h, last);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation from staged inputs: interleaved x, v [n][3], m, R, optional
+// rc and ids. Validates and writes the SoA state.
+// ---------------------------------------------------------------------------
+struct InitIn {
+  const double *x3, *v3, *m, *R, *rc;
+  const int* ids;
+};
+
+__global__ void __launch_bounds__(DNT) k_init(Dev d, Phys P, InitIn in) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= d.n) return;
+  const double x = in.x3[3 * i], y = in.x3[3 * i + 1], z = in.x3[3 * i + 2];
+  const double vx = in.v3[3 * i], vy = in.v3[3 * i + 1], vz = in.v3[3 * i + 2];
+  const double m = in.m[i], R = in.R[i];
+  bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
+            isfinite(vz) && isfinite(m) && m > 0.0 && isfinite(R) && R >= 0.0;
+  ok = ok && (x != 0.0 || y != 0.0 || z != 0.0);
+  double rc = 0.0;
+  if (in.rc) {
+    rc = in.rc[i];
+    ok = ok && isfinite(rc) && rc > 0.0;
+  } else if (ok) {
+    rc = rcrit(P, x, y, z, vx, vy, vz, m);
+    ok = ok && isfinite(rc) && rc > 0.0;
+  }
+  int id = i;
+  if (in.ids) {
+    id = in.ids[i];
+    if (i > 0 && in.ids[i - 1] >= id) ok = false;
+  }
+  if (!ok) set_status(d.ctrl, NB_E_INVALID, 20);
+  d.x[i] = x; d.y[i] = y; d.z[i] = z;
+  d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
+  d.m[i] = m; d.R[i] = R; d.rc[i] = rc; d.rc2[i] = rc * rc;
+  d.ax[i] = d.ay[i] = d.az[i] = 0.0;
+  d.id[i] = id;
+  d.alive[i] = 1;
+  d.member_slot[i] = -1;
+}
+
+void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double* v3,
+                    const double* m, const double* R, const double* rc, const int* ids,
+                    cudaStream_t st) {
+  InitIn in{x3, v3, m, R, rc, ids};
+  k_init<<<d.ppart_n, DNT, 0, st>>>(d, P, in);
+}
+
+__global__ void k_fsal_init(Dev d) {
+  __shared__ int s_n;
+  if (threadIdx.x == 0) {
+    int nt = d.ctrl->n_ftrial;
+    if (nt > d.pair_cap) {
+      set_status(d.ctrl, NB_E_OVERFLOW, 21);
+      nt = d.pair_cap;
+    }
+    s_n = nt;
+    d.ctrl->n_fprev = nt;
+    d.ctrl->stats[ST_FORCE_EVALS] += 1ull;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < s_n; k += blockDim.x) d.fprev[k] = d.ftrial[k];
+}
+
+void launch_fsal_init(const Dev& d, cudaStream_t st) { k_fsal_init<<<1, 1024, 0, st>>>(d); }
+
+// ---------------------------------------------------------------------------
+// Standalone Kepler drift of interleaved device arrays.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DNT) k_kepler_raw(int n, double mu, double* x3, double* v3,
+                                                    double h, int max_iter, int* status) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= n) return;
+  double x = x3[3 * i], y = x3[3 * i + 1], z = x3[3 * i + 2];
+  double vx = v3[3 * i], vy = v3[3 * i + 1], vz = v3[3 * i + 2];
+  int it;
+  const int st = kepler_drift(mu, x, y, z, vx, vy, vz, h, max_iter, &it);
+  if (st) atomicCAS(status, 0, st);
+  x3[3 * i] = x; x3[3 * i + 1] = y; x3[3 * i + 2] = z;
+  v3[3 * i] = vx; v3[3 * i + 1] = vy; v3[3 * i + 2] = vz;
+}
+
+void launch_kepler_raw(int n, double mu, double* x3, double* v3, double dt, int max_iter,
+                       int* status, cudaStream_t st) {
+  if (n <= 0) return;
+  k_kepler_raw<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, mu, x3, v3, dt, max_iter, status);
+}
+
+}  // namespace nb
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// Gather the active bodies (ascending slot = ascending id) into interleaved
+// outputs. One CTA scans the alive flags chunk by chunk.
+// ---------------------------------------------------------------------------
+struct GatherOut {
+  double *x3, *v3, *m, *R, *rc;
+  int* ids;
+  int* count;
+};
+
+__global__ void __launch_bounds__(1024) k_gather(Dev d, GatherOut o) {
+  __shared__ int warp_tot[32];
+  __shared__ int s_base;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < d.n; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    const int f = (i < d.n && d.alive[i]) ? 1 : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int wpre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < wid; ++w) off += warp_tot[w];
+    const int pos = s_base + off + wpre;
+    if (f) {
+      if (o.x3) { o.x3[3 * pos] = d.x[i]; o.x3[3 * pos + 1] = d.y[i]; o.x3[3 * pos + 2] = d.z[i]; }
+      if (o.v3) { o.v3[3 * pos] = d.vx[i]; o.v3[3 * pos + 1] = d.vy[i]; o.v3[3 * pos + 2] = d.vz[i]; }
+      if (o.m) o.m[pos] = d.m[i];
+      if (o.R) o.R[pos] = d.R[i];
+      if (o.rc) o.rc[pos] = d.rc[i];
+      if (o.ids) o.ids[pos] = d.id[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < 32; ++w) tot += warp_tot[w];
+      s_base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && o.count) *o.count = s_base;
+}
+
+void launch_gather(const Dev& d, double* x3, double* v3, double* m, double* R, double* rc,
+                   int* ids, int* count, cudaStream_t st) {
+  GatherOut o{x3, v3, m, R, rc, ids, count};
+  k_gather<<<1, 1024, 0, st>>>(d, o);
+}
+
+// Interleaved <-> SoA helpers for the cached force.
+__global__ void __launch_bounds__(DNT) k_a_to_soa(Dev d, const double* a3) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= d.n) return;
+  d.ax[i] = a3[3 * i];
+  d.ay[i] = a3[3 * i + 1];
+  d.az[i] = a3[3 * i + 2];
+}
+
+__global__ void __launch_bounds__(DNT) k_a_to_aos(Dev d, double* a3) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= d.n) return;
+  a3[3 * i] = d.ax[i];
+  a3[3 * i + 1] = d.ay[i];
+  a3[3 * i + 2] = d.az[i];
+}
+
+void launch_a_convert(const Dev& d, double* a3, int to_soa, cudaStream_t st) {
+  if (to_soa)
+    k_a_to_soa<<<d.ppart_n, DNT, 0, st>>>(d, a3);
+  else
+    k_a_to_aos<<<d.ppart_n, DNT, 0, st>>>(d, a3);
+}
+
+// Standalone kick helpers: interleaved positions to SoA (+ rc^2), and the
+// fixed-order sum of the j-chunk partials times G into interleaved a.
+__global__ void __launch_bounds__(DNT) k_raw_prep(int n, const double* x3, const double* rc,
+                                                  double* x, double* y, double* z, double* rc2) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= n) return;
+  x[i] = x3[3 * i];
+  y[i] = x3[3 * i + 1];
+  z[i] = x3[3 * i + 2];
+  rc2[i] = rc[i] * rc[i];
+}
+
+__global__ void __launch_bounds__(DNT) k_raw_finish(int n, int S, const double* kpart, double G,
+                                                    double* a3) {
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= n) return;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const double* p = kpart + (size_t)(3 * s) * n;
+    ax += p[i];
+    ay += p[n + i];
+    az += p[2 * n + i];
+  }
+  a3[3 * i] = G * ax;
+  a3[3 * i + 1] = G * ay;
+  a3[3 * i + 2] = G * az;
+}
+
+void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
+                     double* rc2, cudaStream_t st) {
+  k_raw_prep<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, x3, rc, x, y, z, rc2);
+}
+
+void launch_raw_finish(int n, int S, const double* kpart, double G, double* a3, cudaStream_t st) {
+  k_raw_finish<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, S, kpart, G, a3);
+}
+
+}  // namespace nb

@@ -1,0 +1,124 @@
+// Energy and momentum diagnostics: E = H_A + H_B + H_C (Eqs. Ha, Hb, Hc; the
+// changeover K cancels between the close part of H_A and H_B, leaving the
+// Newtonian pair sum), L = sum m x cross v, P = sum m v.
+//
+// The O(N^2) pair potential uses 1/r from the same float seed as the kick,
+// refined to FP64 (second order in the residual). Per-thread and per-block
+// sums are Neumaier-compensated; the final reduction runs in a fixed order.
+#include "nb_internal.cuh"
+
+namespace nb {
+
+constexpr int ENT2 = 256;
+constexpr int ECOMP = 8;  // KE + star potential, pair potential, L(3), P(3)
+
+struct Neu {
+  double s, c;
+  __device__ void add(double x) {
+    const double t = s + x;
+    const double b = t - s;
+    c += (s - (t - b)) + (x - b);
+    s = t;
+  }
+};
+
+__device__ __forceinline__ double inv_r(double r2) {
+  const unsigned hr = (unsigned)__double2hiint(r2);
+  const float r2f = __uint_as_float((hr << 3) + 0x40000000u);
+  const unsigned yb = __float_as_uint(rsqrtf(r2f));
+  const double y0 = __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
+  const double e = __fma_rn(-r2, y0 * y0, 1.0);  // y0 (1 - e)^(-1/2)
+  return __fma_rn(y0, e * __fma_rn(0.375, e, 0.5), y0);
+}
+
+__global__ void __launch_bounds__(ENT2) k_energy_parts(Dev d, Phys P) {
+  __shared__ double sx[ENT2], sy[ENT2], sz[ENT2], sm[ENT2];
+  __shared__ double red[2 * ECOMP * ENT2];
+  const int n = d.n;
+  const int i = blockIdx.x * ENT2 + threadIdx.x;
+  const bool live = i < n && d.alive[i];
+  const double xi = live ? d.x[i] : 0.0, yi = live ? d.y[i] : 0.0, zi = live ? d.z[i] : 0.0;
+  const double mi = live ? d.m[i] : 0.0;
+  Neu pot{0.0, 0.0};
+  for (int jt = 0; jt < n; jt += ENT2) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < n) {
+      sx[threadIdx.x] = d.x[j];
+      sy[threadIdx.x] = d.y[j];
+      sz[threadIdx.x] = d.z[j];
+      sm[threadIdx.x] = d.m[j];
+    }
+    __syncthreads();
+    const int cnt = min(ENT2, n - jt);
+    if (live) {
+      double t = 0.0;
+      for (int q = 0; q < cnt; ++q) {
+        const double dx = sx[q] - xi, dy = sy[q] - yi, dz = sz[q] - zi;
+        const double r2 = sep2(dx, dy, dz);
+        if (r2 == 0.0) continue;
+        t += sm[q] * inv_r(r2);
+      }
+      pot.add(t);
+    }
+  }
+  double v[ECOMP] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (live) {
+    const double vx = d.vx[i], vy = d.vy[i], vz = d.vz[i];
+    const double r = sqrt(xi * xi + yi * yi + zi * zi);
+    v[0] = 0.5 * mi * (vx * vx + vy * vy + vz * vz) - P.G * P.m0 * mi / r;
+    v[1] = -0.5 * P.G * mi * (pot.s + pot.c);  // each pair is counted twice
+    v[2] = mi * (yi * vz - zi * vy);
+    v[3] = mi * (zi * vx - xi * vz);
+    v[4] = mi * (xi * vy - yi * vx);
+    v[5] = mi * vx;
+    v[6] = mi * vy;
+    v[7] = mi * vz;
+  }
+  for (int k = 0; k < ECOMP; ++k) red[k * ENT2 + threadIdx.x] = v[k];
+  __syncthreads();
+  if (threadIdx.x < ECOMP) {
+    Neu a{0.0, 0.0};
+    for (int t = 0; t < ENT2; ++t) a.add(red[threadIdx.x * ENT2 + t]);
+    d.eparts[2 * (ECOMP * blockIdx.x + threadIdx.x)] = a.s;
+    d.eparts[2 * (ECOMP * blockIdx.x + threadIdx.x) + 1] = a.c;
+  }
+}
+
+__global__ void k_energy_final(Dev d, Phys P, int nblocks, double* out8) {
+  __shared__ double acc[ECOMP];
+  if (threadIdx.x < ECOMP) {
+    Neu a{0.0, 0.0};
+    for (int b = 0; b < nblocks; ++b) {
+      a.add(d.eparts[2 * (ECOMP * b + threadIdx.x)]);
+      a.add(d.eparts[2 * (ECOMP * b + threadIdx.x) + 1]);
+    }
+    acc[threadIdx.x] = a.s + a.c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double Px = acc[5], Py = acc[6], Pz = acc[7];
+    Neu e{0.0, 0.0};
+    e.add(acc[0]);
+    e.add(acc[1]);
+    e.add((Px * Px + Py * Py + Pz * Pz) / (2.0 * P.m0));
+    out8[0] = e.s + e.c;
+    out8[1] = acc[2];
+    out8[2] = acc[3];
+    out8[3] = acc[4];
+    out8[4] = Px;
+    out8[5] = Py;
+    out8[6] = Pz;
+    out8[7] = d.ctrl->E_lost;
+  }
+}
+
+int energy_blocks(int n) { return (n + ENT2 - 1) / ENT2; }
+
+void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st) {
+  const int nb = energy_blocks(d.n);
+  k_energy_parts<<<nb, ENT2, 0, st>>>(d, P);
+  k_energy_final<<<1, 32, 0, st>>>(d, P, nb, out8);
+}
+
+}  // namespace nb

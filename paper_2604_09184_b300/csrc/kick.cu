@@ -1,0 +1,391 @@
+// Interaction kick of Eq. Hb with the encounter flags of the changeover.
+//
+// a_i = G sum_j m_j w_ij (x_j - x_i) / r_ij^3, w = K - r dK/dr (exact gradient
+// of H_B), and the pair (i < j) is flagged when r_ij^2 < max(rc_i, rc_j)^2.
+//
+// B300 design: the FP64 pipe issues ~1/60 of the FP32 rate, so the pair loop
+// spends as few FP64 instructions as it can and moves everything else to the
+// INT/FP32/MUFU pipes:
+//   - dx, dy, dz, r^2, the r^-3 refinement and the three accumulations are
+//     FP64 (16 FP64 instructions per pair in the FP64 mode);
+//   - the r^-3 seed is rsqrtf of a float built from r^2's high word with one
+//     integer shift-add, and the float seed goes back to a double by integer
+//     ops (no F2F conversions);
+//   - the encounter test first compares the high words of r^2 and
+//     max(rc_i^2, rc_j^2) as integers (IEEE order of non-negative doubles);
+//     only a tie or a close pair takes the exact FP64 branch, which computes
+//     the changeover weight and appends the flagged pair with one atomic per
+//     warp (ballot + popc).
+// j-tiles of 128 bodies are staged through shared memory; each thread owns two
+// targets; a CTA covers 256 targets x one j-chunk, and the j-chunks' partial
+// sums are added in a fixed order by k_finish (deterministic results).
+#include "nb_internal.cuh"
+
+namespace nb {
+
+constexpr int KNT = 128;  // threads per kick CTA (= j-tile size)
+constexpr int KIPT = 2;   // targets per thread
+
+struct KickArgs {
+  int n, S, jchunk;
+  const double *x, *y, *z, *m, *rc, *rc2;
+  double* kpart;  // S x 3 x n
+  int2* pairs;
+  int cap;
+  int* counter;
+  Ctrl* ctrl;
+};
+
+// Append (i, j) for the lanes with f set: one atomicAdd per warp.
+__device__ __forceinline__ void emit_pair(bool f, int i, int j, int2* pairs, int cap, int* counter,
+                                          Ctrl* ctrl) {
+  const unsigned mask = __activemask();
+  const unsigned fm = __ballot_sync(mask, f);
+  if (fm == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(fm) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(fm));
+  base = __shfl_sync(mask, base, leader);
+  if (f) {
+    const int pos = base + __popc(fm & ((1u << lane) - 1u));
+    if (pos < cap)
+      pairs[pos] = make_int2(i, j);
+    else
+      set_status(ctrl, NB_E_OVERFLOW, 1);
+  }
+}
+
+// r^-3 seed: rsqrtf of r^2 rounded toward zero to a float through its high
+// word, returned as a double. Valid for 2^-126 <= r^2 < 2^128.
+__device__ __forceinline__ double rsqrt_seed(double r2) {
+  const unsigned hr = (unsigned)__double2hiint(r2);
+  const float r2f = __uint_as_float((hr << 3) + 0x40000000u);
+  const unsigned yb = __float_as_uint(rsqrtf(r2f));
+  return __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
+}
+
+// m_j / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual),
+// r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...). |e| < 2e-6, so
+// the second-order form (FP64 mode) is exact to ~1e-17 and the first-order
+// form (mixed mode, "one Newton step") to ~1e-11 relative at worst.
+template <int PREC>
+__device__ __forceinline__ double scale_fast(double r2, double mj) {
+  const double y0 = rsqrt_seed(r2);
+  const double t = y0 * y0;
+  const double e = __fma_rn(-r2, t, 1.0);
+  const double my3 = mj * (t * y0);
+  if (PREC == NB_PREC_FP64) return __fma_rn(my3, e * __fma_rn(1.875, e, 1.5), my3);
+  return __fma_rn(my3, 1.5 * e, my3);
+}
+
+// The exact branch: coincident bodies, changeover pairs and flag emission.
+template <bool FLAGS>
+__device__ __forceinline__ double rare_pair(double r2, double sc, double mj, int i, int j,
+                                            double rc2i, double rci, const KickArgs& A) {
+  double s = sc;
+  const double rc2 = fmax(rc2i, __ldg(A.rc2 + j));
+  const bool flag = (r2 < rc2) && (i < j);  // coincident distinct bodies are flagged too
+  if (r2 == 0.0) {
+    s = 0.0;  // no force between coincident bodies (and none on itself)
+  } else if (r2 < rc2) {
+    const double rcij = fmax(rci, __ldg(A.rc + j));
+    const double r = sqrt(r2);
+    s = mj * kick_weight(r, rcij) / (r2 * r);
+  }
+  if (FLAGS) emit_pair(flag, i, j, A.pairs, A.cap, A.counter, A.ctrl);
+  return s;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
+  __shared__ double sx[KNT], sy[KNT], sz[KNT], sm[KNT];
+  __shared__ int sh[KNT];
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = A.ctrl->status;
+  __syncthreads();
+  if (s_stop) return;
+  const int n = A.n;
+  const int it = blockIdx.x / A.S;
+  const int sidx = blockIdx.x - it * A.S;
+  const int i0 = it * (KNT * KIPT) + threadIdx.x;
+
+  double xi[KIPT], yi[KIPT], zi[KIPT], rc2i[KIPT], rci[KIPT];
+  double ax[KIPT], ay[KIPT], az[KIPT];
+  double cx[KIPT], cy[KIPT], cz[KIPT];  // compensation (mixed mode)
+  int hi[KIPT], ii[KIPT];
+#pragma unroll
+  for (int k = 0; k < KIPT; ++k) {
+    const int i = i0 + k * KNT;
+    ii[k] = i;
+    if (i < n) {
+      xi[k] = A.x[i];
+      yi[k] = A.y[i];
+      zi[k] = A.z[i];
+      rc2i[k] = A.rc2[i];
+      rci[k] = A.rc[i];
+    } else {  // padding target far from everything, never flagged
+      xi[k] = yi[k] = zi[k] = 1e10;
+      rc2i[k] = 0.0;
+      rci[k] = 0.0;
+    }
+    hi[k] = __double2hiint(rc2i[k]);
+    ax[k] = ay[k] = az[k] = 0.0;
+    cx[k] = cy[k] = cz[k] = 0.0;
+  }
+  const int j0 = sidx * A.jchunk;
+  const int j1 = min(n, j0 + A.jchunk);
+  for (int jt = j0; jt < j1; jt += KNT) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < j1) {
+      sx[threadIdx.x] = A.x[j];
+      sy[threadIdx.x] = A.y[j];
+      sz[threadIdx.x] = A.z[j];
+      sm[threadIdx.x] = A.m[j];
+      sh[threadIdx.x] = __double2hiint(A.rc2[j]);
+    }
+    __syncthreads();
+    const int cnt = min(KNT, j1 - jt);
+    double tx[KIPT], ty[KIPT], tz[KIPT];  // tile sums (mixed mode)
+#pragma unroll
+    for (int k = 0; k < KIPT; ++k) tx[k] = ty[k] = tz[k] = 0.0;
+#pragma unroll 4
+    for (int q = 0; q < cnt; ++q) {
+      const double xj = sx[q], yj = sy[q], zj = sz[q], mj = sm[q];
+      const int hj = sh[q];
+#pragma unroll
+      for (int k = 0; k < KIPT; ++k) {
+        const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
+        const double r2 = sep2(dx, dy, dz);
+        double sc = scale_fast<PREC>(r2, mj);
+        if (__double2hiint(r2) <= max(hi[k], hj))
+          sc = rare_pair<true>(r2, sc, mj, ii[k], jt + q, rc2i[k], rci[k], A);
+        if (PREC == NB_PREC_FP64) {
+          ax[k] = __fma_rn(sc, dx, ax[k]);
+          ay[k] = __fma_rn(sc, dy, ay[k]);
+          az[k] = __fma_rn(sc, dz, az[k]);
+        } else {
+          tx[k] = __fma_rn(sc, dx, tx[k]);
+          ty[k] = __fma_rn(sc, dy, ty[k]);
+          tz[k] = __fma_rn(sc, dz, tz[k]);
+        }
+      }
+    }
+    if (PREC != NB_PREC_FP64) {
+      // Neumaier-compensated accumulation of the tile sums (TwoSum form).
+#pragma unroll
+      for (int k = 0; k < KIPT; ++k) {
+        double t, b;
+        t = ax[k] + tx[k]; b = t - ax[k]; cx[k] += (ax[k] - (t - b)) + (tx[k] - b); ax[k] = t;
+        t = ay[k] + ty[k]; b = t - ay[k]; cy[k] += (ay[k] - (t - b)) + (ty[k] - b); ay[k] = t;
+        t = az[k] + tz[k]; b = t - az[k]; cz[k] += (az[k] - (t - b)) + (tz[k] - b); az[k] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KIPT; ++k) {
+    const int i = ii[k];
+    if (i < n) {
+      double* p = A.kpart + (size_t)(3 * sidx) * n;
+      p[i] = ax[k] + cx[k];
+      p[n + i] = ay[k] + cy[k];
+      p[2 * n + i] = az[k] + cz[k];
+    }
+  }
+}
+
+int kick_blocks(int n, int S) { return ((n + KNT * KIPT - 1) / (KNT * KIPT)) * S; }
+
+static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) {
+  const int grid = kick_blocks(A.n, A.S);
+  if (grid <= 0) return;
+  if (precision == NB_PREC_MIXED)
+    k_kick<NB_PREC_MIXED><<<grid, KNT, 0, st>>>(A);
+  else
+    k_kick<NB_PREC_FP64><<<grid, KNT, 0, st>>>(A);
+}
+
+static int jchunk_for(int n, int S) {
+  int c = (n + S - 1) / S;
+  c = ((c + KNT - 1) / KNT) * KNT;  // whole tiles
+  return c > 0 ? c : KNT;
+}
+
+void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t st) {
+  KickArgs A;
+  A.n = d.n;
+  A.S = d.S;
+  A.jchunk = jchunk_for(d.n, d.S);
+  A.x = d.x; A.y = d.y; A.z = d.z; A.m = d.m; A.rc = d.rc; A.rc2 = d.rc2;
+  A.kpart = d.kpart;
+  A.pairs = d.ftrial;
+  A.cap = d.pair_cap;
+  A.counter = &d.ctrl->n_ftrial;
+  A.ctrl = d.ctrl;
+  launch_kick_args(A, P.precision, st);
+}
+
+void launch_kick_raw(int n, const double* x, const double* y, const double* z, const double* m,
+                     const double* rc, const double* rc2, int S, int precision, double* kpart,
+                     int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st) {
+  KickArgs A;
+  A.n = n; A.S = S; A.jchunk = jchunk_for(n, S);
+  A.x = x; A.y = y; A.z = z; A.m = m; A.rc = rc; A.rc2 = rc2;
+  A.kpart = kpart; A.pairs = pairs; A.cap = cap; A.counter = &ctrl->n_ftrial; A.ctrl = ctrl;
+  launch_kick_args(A, precision, st);
+}
+
+// ---------------------------------------------------------------------------
+// k_finish: a_i = G sum_s kpart[s] (fixed order). On a step with
+// close-encounter groups, bodies outside the groups also get the change of
+// the group bodies' pull: minus their contribution at the trial state, plus
+// their contribution at the state the BS integration produced. This equals a
+// full re-evaluation of the force at the final positions up to rounding (the
+// only pairs whose terms change are those with a group member).
+// ---------------------------------------------------------------------------
+constexpr int FNT = 256;
+
+__global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta) {
+  __shared__ int s_stop, s_M;
+  __shared__ double so[5][FNT], snw[5][FNT];
+  if (threadIdx.x == 0) {
+    s_stop = d.ctrl->status;
+    s_M = (with_delta && d.ctrl->n_groups > 0) ? d.ctrl->n_members : 0;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int n = d.n;
+  const int i = blockIdx.x * FNT + threadIdx.x;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  if (i < n) {
+    for (int s = 0; s < d.S; ++s) {
+      const double* p = d.kpart + (size_t)(3 * s) * n;
+      ax += p[i];
+      ay += p[n + i];
+      az += p[2 * n + i];
+    }
+  }
+  const int M = s_M;
+  const bool delta = (i < n) && M > 0 && d.member_slot[i] < 0 && d.alive[i];
+  double xi = 0.0, yi = 0.0, zi = 0.0, rci = 0.0;
+  if (delta) {
+    xi = d.x[i]; yi = d.y[i]; zi = d.z[i]; rci = d.rc[i];
+  }
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  for (int q0 = 0; q0 < M; q0 += FNT) {
+    __syncthreads();
+    const int q = q0 + threadIdx.x;
+    if (q < M) {
+      const int b = d.grp_mem[q];
+      so[0][threadIdx.x] = d.x[b];
+      so[1][threadIdx.x] = d.y[b];
+      so[2][threadIdx.x] = d.z[b];
+      so[3][threadIdx.x] = d.m[b];
+      so[4][threadIdx.x] = d.rc[b];
+      const double* g = d.gnew + (size_t)q * 10;
+      snw[0][threadIdx.x] = g[0];
+      snw[1][threadIdx.x] = g[1];
+      snw[2][threadIdx.x] = g[2];
+      snw[3][threadIdx.x] = g[9] != 0.0 ? g[6] : 0.0;  // absorbed: no pull
+      snw[4][threadIdx.x] = g[8];
+    }
+    __syncthreads();
+    if (delta) {
+      const int cnt = min(FNT, M - q0);
+      for (int k = 0; k < cnt; ++k) {
+        double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
+        double s = pair_scale(sep2(dx, dy, dz), so[3][k], rci, so[4][k]);
+        cx -= s * dx; cy -= s * dy; cz -= s * dz;
+        dx = snw[0][k] - xi; dy = snw[1][k] - yi; dz = snw[2][k] - zi;
+        s = pair_scale(sep2(dx, dy, dz), snw[3][k], rci, snw[4][k]);
+        cx += s * dx; cy += s * dy; cz += s * dz;
+      }
+    }
+  }
+  if (i < n) {
+    const bool live = d.alive[i] != 0;
+    d.ax[i] = live ? G * (ax + cx) : 0.0;
+    d.ay[i] = live ? G * (ay + cy) : 0.0;
+    d.az[i] = live ? G * (az + cz) : 0.0;
+  }
+}
+
+void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st) {
+  const int grid = (d.n + FNT - 1) / FNT;
+  k_finish<<<grid, FNT, 0, st>>>(d, P.G, with_delta);
+}
+
+// ---------------------------------------------------------------------------
+// k_member_kick: full force on every group member at the final positions and
+// the new flag set F (pairs with at least one member; all other pairs keep
+// their unflagged trial state). One CTA per member, grid-stride.
+// ---------------------------------------------------------------------------
+constexpr int MNT = 256;
+
+__global__ void __launch_bounds__(MNT) k_member_kick(Dev d, double G) {
+  __shared__ int s_stop, s_M;
+  __shared__ double red[3 * 32 + 3];
+  if (threadIdx.x == 0) {
+    s_stop = d.ctrl->status;
+    s_M = d.ctrl->n_groups > 0 ? d.ctrl->n_members : 0;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int M = s_M;
+  const int n = d.n;
+  KickArgs A;
+  A.rc = d.rc;
+  A.rc2 = d.rc2;
+  A.pairs = d.fprev;
+  A.cap = d.pair_cap;
+  A.counter = &d.ctrl->n_fprev;
+  A.ctrl = d.ctrl;
+  for (int q = blockIdx.x; q < M; q += gridDim.x) {
+    const int b = d.grp_mem[q];
+    const bool live = d.alive[b] != 0;
+    const double xb = d.x[b], yb = d.y[b], zb = d.z[b], rc2b = d.rc2[b], rcb = d.rc[b];
+    const int hb = __double2hiint(rc2b);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    if (live) {
+      for (int j = threadIdx.x; j < n; j += MNT) {
+        const double dx = d.x[j] - xb, dy = d.y[j] - yb, dz = d.z[j] - zb;
+        const double mj = d.m[j];
+        const double r2 = sep2(dx, dy, dz);
+        double sc = scale_fast<NB_PREC_FP64>(r2, mj);
+        if (__double2hiint(r2) <= max(hb, __double2hiint(d.rc2[j]))) {
+          // flag from the member side: (b, j) when j is not a member or b < j
+          double s = sc;
+          const double rc2 = fmax(rc2b, d.rc2[j]);
+          const bool close = (r2 < rc2) && d.alive[j] && (j != b);
+          const bool flag = close && ((d.member_slot[j] < 0) || (b < j));
+          if (r2 == 0.0) {
+            s = 0.0;
+          } else if (close) {
+            const double r = sqrt(r2);
+            s = mj * kick_weight(r, fmax(rcb, d.rc[j])) / (r2 * r);
+          }
+          emit_pair(flag, min(b, j), max(b, j), A.pairs, A.cap, A.counter, A.ctrl);
+          sc = s;
+        }
+        ax = __fma_rn(sc, dx, ax);
+        ay = __fma_rn(sc, dy, ay);
+        az = __fma_rn(sc, dz, az);
+      }
+    }
+    block_sum3(ax, ay, az, red);
+    if (threadIdx.x == 0) {
+      d.ax[b] = live ? G * ax : 0.0;
+      d.ay[b] = live ? G * ay : 0.0;
+      d.az[b] = live ? G * az : 0.0;
+    }
+  }
+}
+
+void launch_member_kick(const Dev& d, const Phys& P, cudaStream_t st) {
+  int grid = d.n < 4 * 148 ? d.n : 4 * 148;
+  if (grid < 1) grid = 1;
+  k_member_kick<<<grid, MNT, 0, st>>>(d, P.G);
+}
+
+}  // namespace nb

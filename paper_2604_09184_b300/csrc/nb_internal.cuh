@@ -1,0 +1,234 @@
+// Internal declarations of libnb: device state layout, control block and the
+// device-side physics shared by the kernels of this library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nb.h"
+
+namespace nb {
+
+constexpr int kMaxBsK = 12;          // upper bound on bs_kmax
+constexpr int kStatN = 12;           // device statistics counters
+constexpr double kDeadOffset = 1e6;  // absorbed bodies sit at (1e6 (id + 1), 0, 0) AU
+
+enum StatIdx {
+  ST_STEPS = 0,
+  ST_FORCE_EVALS,
+  ST_ENC_PAIRS,
+  ST_GROUPS,
+  ST_BS_SUBSTEPS,
+  ST_BS_HALVINGS,
+  ST_BS_DERIVS,
+  ST_MERGES,
+  ST_KEPLER_ITERS,
+  ST_MOVED,
+  ST_LOG_DROPPED,
+  ST_SPARE
+};
+
+// Control block in device memory: counters, status and per-step scalars.
+struct Ctrl {
+  int status;      // first error wins (NB_E_*), 0 while healthy
+  int err_where;   // which kernel set it
+  int n_ftrial;    // flagged pairs found by the trial kick
+  int n_fprev;     // flagged pairs of the cached force (F_prev)
+  int n_enc;       // |E| of the current step
+  int n_log;       // encounter-log entries written in this nb_step call
+  int n_groups;    // close-encounter groups of the current step
+  int n_members;   // bodies in those groups
+  int n_active;    // bodies not absorbed
+  int n_prev_members;
+  int pad[2];
+  long long step_index;  // global step counter
+  double h;              // step size of the current nb_step call
+  double E_lost;         // energy removed by mergers
+  double dP[3];          // momentum change of group bodies in the current step
+  unsigned long long stats[kStatN];
+};
+
+// Device arrays carved from the caller's workspace (SoA, FP64).
+struct Dev {
+  int n;          // body slots (fixed; absorbed bodies stay as massless slots)
+  int S;          // j-chunks of the kick
+  int pair_cap;   // F_trial / F_prev capacity (pairs)
+  int log_cap;    // encounter log capacity (entries)
+  int member_cap; // group-member capacity (= n)
+  int bs_kmax;
+  int ppart_n;    // blocks of the O(N) kernels (P partial sums)
+  double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *rc2, *ax, *ay, *az;
+  double *xs, *ys, *zs, *vxs, *vys, *vzs;  // saved state after C(h/2)
+  int *id, *alive, *member_slot, *uf;
+  double* kpart;      // S x 3 x n partial kick sums
+  double* ppartA;     // 3 x ppart_n partial momenta (after the opening kick)
+  double* ppartB;     // 3 x ppart_n partial momenta (after the drift)
+  int2* ftrial;       // pairs of the trial kick
+  int2* fprev;        // pairs of the cached force
+  unsigned long long* keys;  // sort buffer, 8 x pair_cap
+  int* log;           // 3 x log_cap
+  int* grp_off;       // member_cap + 1
+  int* grp_mem;       // member_cap (body index per member slot)
+  double* gscr;       // BS scratch, member_cap x bs_stride doubles
+  int bs_stride;
+  double* gnew;       // member_cap x 10: x y z vx vy vz m R rc alive(as double)
+  double* gEl;        // per-group energy removed by mergers (member_cap)
+  double* snap;       // rollback snapshot: 16 x n doubles
+  int* snap_i;        // rollback snapshot ints: alive (n) + fprev (2 x pair_cap)
+  Ctrl* ctrl;
+  Ctrl* snap_ctrl;
+  double* eparts;     // energy partial sums
+  int eparts_n;
+};
+
+// Parameters as the kernels see them.
+struct Phys {
+  double G, m0, mu, dt_rcrit, hill_factor, vel_factor, bs_tol;
+  int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings;
+};
+
+__device__ __forceinline__ void set_status(Ctrl* c, int code, int where) {
+  if (atomicCAS(&c->status, 0, code) == 0) c->err_where = where;
+}
+
+// ---------------------------------------------------------------------------
+// Changeover (the paragraph after Eq. Hc): smooth K from 0 to 1 between 0.1 rc
+// and rc, K(y) = y^2 / (2y^2 - 2y + 1) with y = (r - 0.1 rc) / (0.9 rc).
+// Returns the kick weight w = K - r dK/dr: the pair force of Eq. Hb is
+// G m_i m_j w (x_j - x_i) / r^3 and the close part of Eq. Ha carries 1 - w.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double kick_weight(double r, double rc) {
+  const double y = (r - 0.1 * rc) / (0.9 * rc);
+  if (y <= 0.0) return 0.0;
+  if (y >= 1.0) return 1.0;
+  const double q = 2.0 * y * y - 2.0 * y + 1.0;
+  const double K = y * y / q;
+  const double dKdy = 2.0 * y * (1.0 - y) / (q * q);
+  return K - r * dKdy / (0.9 * rc);
+}
+
+// Squared separation in the fixed rounding that decides encounter flags:
+// fma(dz, dz, fma(dy, dy, dx*dx)), every operation correctly rounded.
+__device__ __forceinline__ double sep2(double dx, double dy, double dz) {
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+
+// m_j w / r^3 for one pair with full-precision r (used off the hot loop).
+// w = 1 when r^2 >= rc^2 with rc = max(rc_i, rc_j); 0 for coincident bodies.
+__device__ __forceinline__ double pair_scale(double r2, double mj, double rci, double rcj) {
+  if (r2 == 0.0 || mj == 0.0) return 0.0;
+  const double rc = fmax(rci, rcj);
+  const double r = sqrt(r2);
+  const double w = (r2 < rc * rc) ? kick_weight(r, rc) : 1.0;
+  return mj * w / (r2 * r);
+}
+
+// Critical radius of Eq. rcrit. R_Hill = |x| (m / 3 m0)^(1/3); the velocity
+// term uses |v - v_circ(x)| (vel_mode 0: speed relative to the local circular
+// prograde orbit) or |v| (vel_mode 1).
+__device__ __forceinline__ double rcrit(const Phys& P, double x, double y, double z, double vx,
+                                        double vy, double vz, double m) {
+  const double r = sqrt(x * x + y * y + z * z);
+  const double rh = r * cbrt(m / (3.0 * P.m0));
+  double vr;
+  if (P.vel_mode == 0) {
+    const double rxy = sqrt(x * x + y * y);
+    double cx = 0.0, cy = 0.0;
+    if (rxy > 0.0 && r > 0.0) {
+      const double vk = sqrt(P.G * P.m0 / r);
+      cx = -vk * y / rxy;
+      cy = vk * x / rxy;
+    }
+    const double dx = vx - cx, dy = vy - cy;
+    vr = sqrt(dx * dx + dy * dy + vz * vz);
+  } else {
+    vr = sqrt(vx * vx + vy * vy + vz * vz);
+  }
+  return fmax(P.hill_factor * rh, P.vel_factor * fabs(P.dt_rcrit) * vr);
+}
+
+// Deterministic block reduction of three doubles (fixed shuffle tree, fixed
+// warp order). Valid in thread 0 on return. smem: >= 3 * 32 doubles.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* smem) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) {
+    smem[3 * w] = a;
+    smem[3 * w + 1] = b;
+    smem[3 * w + 2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = c = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      a += smem[3 * k];
+      b += smem[3 * k + 1];
+      c += smem[3 * k + 2];
+    }
+  }
+  __syncthreads();
+}
+
+// Sum of the 3 x nparts partial momenta in a fixed order; every block that
+// calls it obtains the same bits. Result valid in all threads.
+__device__ __forceinline__ void reduce_parts3(const double* parts, int nparts, double* smem,
+                                              double out[3]) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+    a += parts[3 * k];
+    b += parts[3 * k + 1];
+    c += parts[3 * k + 2];
+  }
+  block_sum3(a, b, c, smem);
+  if (threadIdx.x == 0) {
+    smem[96] = a;
+    smem[97] = b;
+    smem[98] = c;
+  }
+  __syncthreads();
+  out[0] = smem[96];
+  out[1] = smem[97];
+  out[2] = smem[98];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per kernel family), defined in the .cu files.
+// ---------------------------------------------------------------------------
+int kick_blocks(int n, int S);
+int ppart_blocks(int n);
+void launch_kick(const Dev& d, const Phys& P, int target_sel, cudaStream_t st);
+void launch_kick_raw(int n, const double* x, const double* y, const double* z, const double* m,
+                     const double* rc, const double* rc2, int S, int precision, double* kpart,
+                     int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st);
+void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st);
+void launch_member_kick(const Dev& d, const Phys& P, cudaStream_t st);
+void launch_open_h(const Dev& d, double h, cudaStream_t st);
+void launch_drift_h(const Dev& d, const Phys& P, double h, cudaStream_t st);
+void launch_close_h(const Dev& d, const Phys& P, double h, int last, cudaStream_t st);
+void launch_encounter(const Dev& d, const Phys& P, cudaStream_t st);
+void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st);
+void launch_scatter(const Dev& d, const Phys& P, cudaStream_t st);
+void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double* v3,
+                    const double* m, const double* R, const double* rc, const int* ids,
+                    cudaStream_t st);
+void launch_fsal_init(const Dev& d, cudaStream_t st);
+void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st);
+void launch_kepler_raw(int n, double mu, double* x3, double* v3, double dt, int max_iter,
+                       int* status, cudaStream_t st);
+int energy_blocks(int n);
+void launch_gather(const Dev& d, double* x3, double* v3, double* m, double* R, double* rc,
+                   int* ids, int* count, cudaStream_t st);
+void launch_a_convert(const Dev& d, double* a3, int to_soa, cudaStream_t st);
+void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
+                     double* rc2, cudaStream_t st);
+void launch_raw_finish(int n, int S, const double* kpart, double G, double* a3, cudaStream_t st);
+int peak_blocks();
+int measure_peaks(double* fp64, double* fp32, void* scratch, cudaStream_t st);
+
+}  // namespace nb

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libnb.so (include/nb.h).
+
+Argument marshalling only: every step of the integrator runs in the library's
+CUDA kernels. PyTorch provides the device memory (the workspace is a uint8
+CUDA tensor) and the stream. A missing library or a missing GPU raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnb.so")
+
+NB_OK = 0
+NB_E_INVALID = -1
+NB_E_CUDA = -2
+NB_E_OVERFLOW = -3
+NB_E_NOCONV = -4
+NB_E_TIMEOUT = -5
+NB_E_WORKSPACE = -6
+NB_PREC_FP64 = 0
+NB_PREC_MIXED = 1
+
+
+class NbParams(C.Structure):
+    _fields_ = [
+        ("G", C.c_double), ("m0", C.c_double), ("dt_rcrit", C.c_double),
+        ("hill_factor", C.c_double), ("vel_factor", C.c_double),
+        ("vel_mode", C.c_int), ("merge", C.c_int), ("precision", C.c_int),
+        ("kepler_max_iter", C.c_int), ("bs_tol", C.c_double), ("bs_kmax", C.c_int),
+        ("bs_max_halvings", C.c_int), ("pair_capacity", C.c_int), ("log_capacity", C.c_int),
+        ("kick_split", C.c_int),
+    ]
+
+
+class NbStats(C.Structure):
+    _fields_ = [(k, C.c_longlong) for k in (
+        "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
+        "bs_derivs", "merges", "kepler_iters", "moved_bodies", "log_dropped")] + [
+        ("n_active", C.c_int), ("last_pairs", C.c_int)]
+
+
+class NbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (status_string(code), code, msg))
+        self.code = code
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_lib = None
+
+
+def lib():
+    """Load libnb.so (built in-tree by paper_2604_09184_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libnb.so is missing: run `python -m paper_2604_09184_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        L.nb_default_params.argtypes = [C.POINTER(NbParams)]
+        L.nb_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int]
+        L.nb_workspace_bytes.restype = C.c_size_t
+        L.nb_init_system.argtypes = [C.POINTER(C.c_void_p), C.POINTER(NbParams), C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int]
+        L.nb_set_fsal.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]
+        L.nb_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.nb_set_state.argtypes = [C.c_void_p] + [C.c_void_p] * 8 + [C.c_int, C.c_int]
+        L.nb_set_timing.argtypes = [C.c_void_p, C.c_int]
+        L.nb_timing.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong),
+                                C.POINTER(C.c_longlong)]
+        L.nb_energy_momentum.argtypes = [C.c_void_p, _D, _D, _D, _D]
+        L.nb_get_state.argtypes = [C.c_void_p] + [C.c_void_p] * 6 + [_I, C.c_int]
+        L.nb_get_fsal.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_int]
+        L.nb_encounter_list.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _I]
+        L.nb_stats.argtypes = [C.c_void_p, C.POINTER(NbStats)]
+        L.nb_destroy.argtypes = [C.c_void_p]
+        L.nb_last_error.argtypes = [C.c_void_p]
+        L.nb_last_error.restype = C.c_char_p
+        L.nb_status_string.argtypes = [C.c_int]
+        L.nb_status_string.restype = C.c_char_p
+        L.nb_kick_scratch_bytes.argtypes = [C.c_int, C.c_int]
+        L.nb_kick_scratch_bytes.restype = C.c_size_t
+        L.nb_kick.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                              C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p,
+                              C.c_size_t, C.c_void_p]
+        L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
+                                      C.c_int, C.c_void_p, C.c_void_p]
+        L.nb_peak_scratch_bytes.argtypes = []
+        L.nb_peak_scratch_bytes.restype = C.c_size_t
+        L.nb_measure_peaks.argtypes = [_D, _D, C.c_void_p, C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().nb_status_string(code).decode()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libnb needs a CUDA device; there is no CPU fallback")
+    return torch
+
+
+def _stream(torch):
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def params(**kw) -> NbParams:
+    p = NbParams()
+    lib().nb_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class NBodySystem:
+    """A planetary system integrated on the GPU by libnb.
+
+    x, v: (n, 3) heliocentric positions / barycentric velocities (AU, AU/day);
+    m, R: (n,) masses (Msun) and radii (AU). numpy arrays are copied from the
+    host by the library; CUDA float64 tensors are read on the device.
+    """
+
+    def __init__(self, p: NbParams, x, v, m, R, rc=None, ids=None):
+        torch = _torch()
+        L = lib()
+        self.p = p
+        on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        if on_dev:
+            args = [t.contiguous().to(torch.float64) for t in (x, v, m, R)]
+            rcv = None if rc is None else rc.contiguous().to(torch.float64)
+            idv = None if ids is None else ids.contiguous().to(torch.int32)
+            self._keep = (args, rcv, idv)
+            ptrs = [_ptr(t) for t in args]
+            rcp = None if rcv is None else _ptr(rcv)
+            idp = None if idv is None else _ptr(idv)
+            n = args[0].shape[0]
+        else:
+            args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, m, R)]
+            n = args[2].shape[0]
+            rcv = None if rc is None else np.ascontiguousarray(rc, dtype=np.float64)
+            idv = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+            self._keep = (args, rcv, idv)
+            ptrs = [C.c_void_p(a.ctypes.data) for a in args]
+            rcp = None if rcv is None else C.c_void_p(rcv.ctypes.data)
+            idp = None if idv is None else C.c_void_p(idv.ctypes.data)
+        self.n = int(n)
+        nbytes = L.nb_workspace_bytes(C.byref(p), self.n)
+        if nbytes == 0:
+            raise NbError(NB_E_INVALID, "bad parameters or n")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self._ws_ptr = C.c_void_p(base + off)
+        self._ws_bytes = nbytes
+        h = C.c_void_p()
+        self._stream = _stream(torch)
+        rcode = L.nb_init_system(C.byref(h), C.byref(p), self.n, ptrs[0], ptrs[1], ptrs[2],
+                                 ptrs[3], rcp, idp, self._ws_ptr, self._ws_bytes, self._stream,
+                                 1 if on_dev else 0)
+        if rcode != NB_OK:
+            raise NbError(rcode, "nb_init_system failed")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().nb_destroy(h)
+            self._h = None
+
+    def _check(self, code):
+        if code != NB_OK:
+            raise NbError(code, lib().nb_last_error(self._h).decode())
+
+    def step(self, nsteps: int, dt: float):
+        self._check(lib().nb_step(self._h, int(nsteps), float(dt)))
+
+    def step_status(self, nsteps: int, dt: float) -> int:
+        return lib().nb_step(self._h, int(nsteps), float(dt))
+
+    def energy_momentum(self) -> dict:
+        E, El = C.c_double(), C.c_double()
+        Lv, P = np.zeros(3), np.zeros(3)
+        self._check(lib().nb_energy_momentum(self._h, C.byref(E), Lv.ctypes.data_as(_D),
+                                             P.ctypes.data_as(_D), C.byref(El)))
+        return dict(E=E.value, L=Lv, P=P, E_lost=El.value)
+
+    def state(self) -> dict:
+        n = self.n
+        x = np.zeros((n, 3)); v = np.zeros((n, 3)); m = np.zeros(n); R = np.zeros(n)
+        rc = np.zeros(n); ids = np.zeros(n, dtype=np.int32); k = C.c_int()
+        self._check(lib().nb_get_state(self._h, C.c_void_p(x.ctypes.data),
+                                       C.c_void_p(v.ctypes.data), C.c_void_p(m.ctypes.data),
+                                       C.c_void_p(R.ctypes.data), C.c_void_p(rc.ctypes.data),
+                                       C.c_void_p(ids.ctypes.data), C.byref(k), 0))
+        k = k.value
+        return dict(x=x[:k], v=v[:k], m=m[:k], R=R[:k], rc=rc[:k], ids=ids[:k])
+
+    def state_device(self, out: dict) -> int:
+        """Gather the active bodies into caller CUDA tensors; returns their count."""
+        k = C.c_int()
+        self._check(lib().nb_get_state(self._h, _ptr(out["x"]), _ptr(out["v"]), _ptr(out["m"]),
+                                       _ptr(out["R"]), _ptr(out["rc"]), _ptr(out["ids"]),
+                                       C.byref(k), 1))
+        return k.value
+
+    def fsal(self):
+        a = np.zeros((self.n, 3))
+        cnt = C.c_int()
+        self._check(lib().nb_get_fsal(self._h, C.c_void_p(a.ctypes.data), None, 0,
+                                      C.byref(cnt), 0))
+        pairs = np.zeros((max(cnt.value, 1), 2), dtype=np.int32)
+        code = lib().nb_get_fsal(self._h, None, C.c_void_p(pairs.ctypes.data), cnt.value,
+                                 C.byref(cnt), 0)
+        self._check(code)
+        return a, pairs[:cnt.value]
+
+    def set_fsal(self, a, pairs):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        self._check(lib().nb_set_fsal(self._h, C.c_void_p(a.ctypes.data),
+                                      C.c_void_p(pairs.ctypes.data), pairs.shape[0], 0))
+
+    def set_state(self, x, v, m, R, rc, ids, a, pairs):
+        """Load a full state (host numpy arrays or CUDA tensors) without a force
+        evaluation; a is the cached force [n][3], pairs the cached flags."""
+        import torch
+        on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        if on_dev:
+            ptr = _ptr
+            npairs = int(pairs.shape[0])
+        else:
+            def ptr(t):
+                return C.c_void_p(t.ctypes.data)
+            npairs = int(np.asarray(pairs).reshape(-1, 2).shape[0])
+        idp = None if ids is None else ptr(ids)
+        self._check(lib().nb_set_state(self._h, ptr(x), ptr(v), ptr(m), ptr(R), ptr(rc), idp,
+                                       ptr(a), ptr(pairs) if npairs else None, npairs,
+                                       1 if on_dev else 0))
+
+    def set_timing(self, enable: bool = True):
+        self._check(lib().nb_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self) -> dict:
+        ms, kl, la = C.c_double(), C.c_longlong(), C.c_longlong()
+        self._check(lib().nb_timing(self._h, C.byref(ms), C.byref(kl), C.byref(la)))
+        return dict(kick_ms=ms.value, kick_launches=kl.value, launches=la.value)
+
+    def encounter_list(self) -> np.ndarray:
+        cnt = C.c_int()
+        lib().nb_encounter_list(self._h, None, 0, C.byref(cnt))
+        out = np.zeros((max(cnt.value, 1), 3), dtype=np.int32)
+        code = lib().nb_encounter_list(self._h, C.c_void_p(out.ctypes.data), cnt.value,
+                                       C.byref(cnt))
+        self._check(code)
+        return out[:cnt.value]
+
+    def stats(self) -> dict:
+        st = NbStats()
+        self._check(lib().nb_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in NbStats._fields_}
+
+
+def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=None):
+    """One launch of the kick+flag kernel on CUDA tensors. Returns (a, pairs, status)."""
+    torch = _torch()
+    L = lib()
+    n = x.shape[0]
+    x = x.contiguous()
+    a = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    cap = 16 * n + 64 if cap is None else cap
+    pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+    nb = L.nb_kick_scratch_bytes(n, split)
+    scratch = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    sp = scratch.data_ptr() + ((-scratch.data_ptr()) % 256)
+    cnt = C.c_int()
+    code = L.nb_kick(n, _ptr(x), _ptr(m.contiguous()), _ptr(rc.contiguous()), G, precision,
+                     split, _ptr(a), _ptr(pairs), cap, C.byref(cnt), C.c_void_p(sp), nb,
+                     _stream(torch))
+    return a, pairs[:min(cnt.value, cap)], code
+
+
+def kepler_drift(x, v, mu, dt, max_iter=30):
+    """Kepler-drift CUDA tensors x, v (n, 3) in place; returns the status code."""
+    torch = _torch()
+    scratch = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    return lib().nb_kepler_drift(x.shape[0], mu, _ptr(x), _ptr(v), dt, max_iter,
+                                 _ptr(scratch), _stream(torch))
+
+
+def measure_peaks():
+    """(FP64 FLOP/s, FP32 FLOP/s) from the library's own FMA loops."""
+    torch = _torch()
+    L = lib()
+    scratch = torch.empty(L.nb_peak_scratch_bytes(), dtype=torch.uint8, device="cuda")
+    f64, f32 = C.c_double(), C.c_double()
+    code = L.nb_measure_peaks(C.byref(f64), C.byref(f32), _ptr(scratch), _stream(torch))
+    if code != NB_OK:
+        raise NbError(code, "nb_measure_peaks")
+    return f64.value, f32.value
