@@ -121,6 +121,18 @@ def load_peaks():
         return {}
 
 
+def read_traffic(path):
+    """key: value lines of a profiles/ summary (comments start with #)."""
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            line = line.split("#", 1)[0].strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                out[k.strip()] = v.strip()
+    return out
+
+
 def pairs_per_step(n):
     return float(n) * float(n - 1)
 
@@ -251,12 +263,10 @@ def run_ours(args):
         "fp64_pipe_frac": FP64_INSTR_PER_PAIR * pps / (kick_ms * 1e-3) / (f64_peak / 2),
         "fp32_peak_tflops": f32_peak / 1e12,
     }
-    traffic_file = os.path.join(ROOT, "profiles", "kick_fp64_traffic.json")
-    if os.path.exists(traffic_file):
-        with open(traffic_file) as f:
-            tr = json.load(f)
-        if tr.get("n") == n:
-            roofline["traffic"] = tr.get("bytes_per_launch")
+    tr = read_traffic(os.path.join(ROOT, "profiles", "kick_fp64_mmsn_64k_dram.txt"))
+    if tr.get("n") == str(n):
+        roofline["traffic"] = float(tr["bytes_per_launch"])
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 1 launch"
 
     # mixed-precision kick on the same workload
     mixed = None
