@@ -168,6 +168,20 @@ int nb_kick(int n, const double* x, const double* m, const double* rc, double G,
             int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,
             size_t scratch_bytes, void* stream);
 
+/* The kick of nb_kick() for callers that cannot allocate device memory (a
+ * framework allocator owns the device, allocation is forbidden after
+ * start-up, or the caller must never touch the CUDA allocator). The paper
+ * has no counterpart; this is a deployment convenience. Arguments as in
+ * nb_kick() minus the scratch: the library keeps a static device array of
+ * about 8.4 MB on every GPU that loads it, so n must not exceed
+ * NB_NOALLOC_MAX_N (NB_E_INVALID otherwise). The first call on a device looks
+ * up that array's device address (make it before any stream capture). Calls
+ * share the array: calls that overlap on the GPU race, so serialise them.
+ * Allocates nothing; synchronises the stream before returning. */
+#define NB_NOALLOC_MAX_N 65600
+int nb_kick_noalloc(int n, const double* x, const double* m, const double* rc, double G,
+                    int precision, double* a, int* pairs_ij, int cap, int* npairs, void* stream);
+
 /* Universal-variable Kepler drift (first sum of Eq. Ha) of n bodies about
  * mu = G m0 by dt, in place on device x, v [n][3]. Returns NB_E_NOCONV if a
  * body hit max_iter. scratch: 16 bytes of device memory. */

@@ -89,6 +89,8 @@ def lib():
         L.nb_kick.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                               C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p,
                               C.c_size_t, C.c_void_p]
+        L.nb_kick_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p]
         L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int, C.c_void_p, C.c_void_p]
         L.nb_peak_scratch_bytes.argtypes = []
@@ -292,6 +294,19 @@ def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=
                      split, _ptr(a), _ptr(pairs), cap, C.byref(cnt), C.c_void_p(sp), nb,
                      _stream(torch))
     return a, pairs[:min(cnt.value, cap)], code
+
+
+NB_NOALLOC_MAX_N = 65600
+
+
+def kick_noalloc(x, m, rc, a, pairs, G=2.959122082855911e-4, precision=NB_PREC_FP64):
+    """nb_kick_noalloc on caller-provided CUDA tensors a (n, 3) and pairs
+    (cap, 2): nothing is allocated by this call. Returns (npairs, status)."""
+    torch = _torch()
+    cnt = C.c_int()
+    code = lib().nb_kick_noalloc(x.shape[0], _ptr(x), _ptr(m), _ptr(rc), G, precision, _ptr(a),
+                                 _ptr(pairs), pairs.shape[0], C.byref(cnt), _stream(torch))
+    return cnt.value, code
 
 
 def kepler_drift(x, v, mu, dt, max_iter=30):
