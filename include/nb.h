@@ -47,6 +47,8 @@ extern "C" {
 
 #define NB_PREC_FP64 0  /* kick pair terms in FP64 */
 #define NB_PREC_MIXED 1 /* FP32 r^-3 seed, one FP64 Newton step, compensated sums */
+#define NB_PREC_DS 2    /* FP64 relative coordinates; r^2, r^-3, products and sums in   \
+                           double-single (float pairs) on the FP32 pipe; tile sums in FP64 */
 
 typedef struct {
   double G;            /* gravitational constant; default k^2 = 2.959122082855911e-4 */

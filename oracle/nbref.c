@@ -17,7 +17,7 @@
  * Where the paper is silent the following readings are taken (each is
  * repeated at the function that implements it):
  *   - operator order B(h/2) C(h/2) A(h) C(h/2) B(h/2);
- *   - K(y) = y^2 / (2y^2 - 2y + 1), y = (r - 0.1 rc) / (0.9 rc);
+ *   - K(y) = f(y) / (f(y) + f(1 - y)), f(y) = exp(-1/y), y = (r - 0.1 rc) / (0.9 rc);
  *   - kick weight w = K - r dK/dr (exact gradient of Eq. Hb), close weight 1 - w;
  *   - rc_ij = max(rc_i, rc_j); a pair is in encounter when r^2 < rc_ij^2 at the
  *     start of the step (flags of the previous force evaluation) or after the
@@ -37,8 +37,11 @@
 
 /* ------------------------------------------------------------------ */
 /* Changeover function (Eq. Hb and the paragraph after Eq. Hc).        */
-/* The paper states only that K is smooth and goes from 0 to 1. Reading:*/
-/* the rational form in y = (r - 0.1 rc) / (0.9 rc).                   */
+/* The paper states that K is smooth, goes from 0 to 1, and that the    */
+/* transition must be smooth enough. Reading: the infinitely            */
+/* differentiable switch K(y) = f(y) / (f(y) + f(1 - y)),               */
+/* f(y) = exp(-1/y) for y > 0, with y = (r - 0.1 rc) / (0.9 rc).        */
+/* dK/dy = f(y) f(1-y) (1/y^2 + 1/(1-y)^2) / (f(y) + f(1-y))^2.          */
 /* ------------------------------------------------------------------ */
 void nbref_changeover(double r, double rc, double* K, double* dKdr) {
   double y = (r - 0.1 * rc) / (0.9 * rc);
@@ -49,9 +52,13 @@ void nbref_changeover(double r, double rc, double* K, double* dKdr) {
     *K = 1.0;
     *dKdr = 0.0;
   } else {
-    double d = 2.0 * y * y - 2.0 * y + 1.0;
-    *K = y * y / d;
-    double dKdy = 2.0 * y * (1.0 - y) / (d * d);
+    double f = exp(-1.0 / y);
+    double g = exp(-1.0 / (1.0 - y));
+    double s = f + g;
+    *K = f / s;
+    double fg = f * g;
+    double dKdy = 0.0;
+    if (fg > 0.0) dKdy = fg * (1.0 / (y * y) + 1.0 / ((1.0 - y) * (1.0 - y))) / (s * s);
     *dKdr = dKdy / (0.9 * rc);
   }
 }

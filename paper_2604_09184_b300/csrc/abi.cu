@@ -127,7 +127,7 @@ bool params_ok(const nb_params* p) {
   if (!p) return false;
   if (!(p->G > 0.0) || !(p->m0 > 0.0) || !std::isfinite(p->dt_rcrit)) return false;
   if (!(p->hill_factor >= 0.0) || !(p->vel_factor >= 0.0)) return false;
-  if (p->precision != NB_PREC_FP64 && p->precision != NB_PREC_MIXED) return false;
+  if (p->precision < NB_PREC_FP64 || p->precision > NB_PREC_DS) return false;
   if (p->kepler_max_iter < 1 || p->bs_max_halvings < 0 || !(p->bs_tol > 0.0)) return false;
   if (p->pair_capacity < 0 || p->log_capacity < 0 || p->kick_split < 0) return false;
   return true;
@@ -582,7 +582,7 @@ int nb_kick(int n, const double* x, const double* m, const double* rc, double G,
             size_t scratch_bytes, void* stream) {
   nb_system* s = nullptr;  // for NB_CU
   if (n < 1 || !x || !m || !rc || !a || cap < 0 || (cap > 0 && !pairs_ij)) return NB_E_INVALID;
-  if (precision != NB_PREC_FP64 && precision != NB_PREC_MIXED) return NB_E_INVALID;
+  if (precision < NB_PREC_FP64 || precision > NB_PREC_DS) return NB_E_INVALID;
   const int S = split > 0 ? split : auto_split(n);
   if (!scratch || scratch_bytes < nb_kick_scratch_bytes(n, S) || ((uintptr_t)scratch & 255))
     return NB_E_WORKSPACE;

@@ -195,13 +195,194 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-single kick (NB_PREC_DS). Only the relative coordinates are formed in
+// FP64 (3 DADD per pair, exact to half an ulp); they are split into float
+// pairs by integer ops, and r^2, r^-3, m r^-3 and the products run as
+// double-single arithmetic (unevaluated float pairs, error-free FMA
+// transforms, Dekker/Knuth style) on the FP32 pipe. Each term is accurate to
+// a few 2^-48; per-tile sums are float pairs folded into FP64 accumulators.
+// The encounter test compares the float r^2 with a float threshold that
+// over-estimates max(rc_i^2, rc_j^2) by 2^-20; any pair that passes it takes
+// the exact FP64 branch of the FP64 kernel, so flags are identical.
+// All float arithmetic uses the _rn intrinsics so that no operation is
+// contracted or reassociated.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float h, l;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ F2 ds_mul(F2 a, F2 b) {
+  const F2 p = two_prod(a.h, b.h);
+  return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
+}
+
+// d (FP64) -> h + l: h is d truncated to 24 significant bits, l the next 23
+// bits; |d| < 2^-74 (irrelevant here) maps to 0.
+__device__ __forceinline__ F2 split_d(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  const unsigned sg = hi & 0x80000000u;
+  const unsigned hb = ((__funnelshift_l(lo, hi, 3) + 0x40000000u) & 0x7fffffffu) | sg;
+  const float km = __fsub_rn(__uint_as_float(0x4b000000u | ((lo >> 6) & 0x7fffffu)), 8388608.0f);
+  const float sc = __uint_as_float(((ex - 942u) << 23) | sg);  // +-2^(e - 1069)
+  const bool ok = ex >= 949u && ex <= 1150u;
+  return {ok ? __uint_as_float(hb) : 0.0f, ok ? __fmul_rn(km, sc) : 0.0f};
+}
+
+// Float threshold >= rc^2 (1 + 2^-20) for the encounter pre-test.
+__device__ __forceinline__ float rc2_threshold(double rc2) {
+  const float f = __double2float_ru(rc2);
+  return __uint_as_float(__float_as_uint(f) + 16u);
+}
+
+constexpr int DNT2 = 128;  // threads per DS kick CTA (= j-tile size)
+constexpr int DIPT = 2;    // targets per thread
+
+__global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
+  __shared__ double sx[DNT2], sy[DNT2], sz[DNT2];
+  __shared__ float smh[DNT2], sml[DNT2], sthr[DNT2];
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = A.ctrl->status;
+  __syncthreads();
+  if (s_stop) return;
+  const int n = A.n;
+  const int it = blockIdx.x / A.S;
+  const int sidx = blockIdx.x - it * A.S;
+  const int i0 = it * (DNT2 * DIPT) + threadIdx.x;
+  double xi[DIPT], yi[DIPT], zi[DIPT], rc2i[DIPT], rci[DIPT];
+  double ax[DIPT], ay[DIPT], az[DIPT];
+  float thi[DIPT];
+  int ii[DIPT];
+#pragma unroll
+  for (int k = 0; k < DIPT; ++k) {
+    const int i = i0 + k * DNT2;
+    ii[k] = i;
+    if (i < n) {
+      xi[k] = A.x[i]; yi[k] = A.y[i]; zi[k] = A.z[i];
+      rc2i[k] = A.rc2[i]; rci[k] = A.rc[i];
+    } else {
+      xi[k] = yi[k] = zi[k] = 1e10;
+      rc2i[k] = 0.0; rci[k] = 0.0;
+    }
+    thi[k] = rc2_threshold(rc2i[k]);
+    ax[k] = ay[k] = az[k] = 0.0;
+  }
+  const int j0 = sidx * A.jchunk;
+  const int j1 = min(n, j0 + A.jchunk);
+  for (int jt = j0; jt < j1; jt += DNT2) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < j1) {
+      sx[threadIdx.x] = A.x[j];
+      sy[threadIdx.x] = A.y[j];
+      sz[threadIdx.x] = A.z[j];
+      const F2 mm = split_d(A.m[j]);
+      smh[threadIdx.x] = mm.h;
+      sml[threadIdx.x] = mm.l;
+      sthr[threadIdx.x] = rc2_threshold(A.rc2[j]);
+    }
+    __syncthreads();
+    const int cnt = min(DNT2, j1 - jt);
+    F2 tx[DIPT], ty[DIPT], tz[DIPT];
+#pragma unroll
+    for (int k = 0; k < DIPT; ++k) tx[k] = ty[k] = tz[k] = F2{0.0f, 0.0f};
+#pragma unroll 2
+    for (int q = 0; q < cnt; ++q) {
+      const double xj = sx[q], yj = sy[q], zj = sz[q];
+      const F2 mj{smh[q], sml[q]};
+      const float thj = sthr[q];
+#pragma unroll
+      for (int k = 0; k < DIPT; ++k) {
+        const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
+        const F2 fx = split_d(dx), fy = split_d(dy), fz = split_d(dz);
+        // r^2 as a float pair (the 2^-48-relative squares of the low parts dropped)
+        F2 px = two_prod(fx.h, fx.h), py = two_prod(fy.h, fy.h), pz = two_prod(fz.h, fz.h);
+        px.l = __fmaf_rn(__fmul_rn(2.0f, fx.h), fx.l, px.l);
+        py.l = __fmaf_rn(__fmul_rn(2.0f, fy.h), fy.l, py.l);
+        pz.l = __fmaf_rn(__fmul_rn(2.0f, fz.h), fz.l, pz.l);
+        F2 t = two_sum(px.h, py.h);
+        t.l = __fadd_rn(t.l, __fadd_rn(px.l, py.l));
+        F2 u = two_sum(t.h, pz.h);
+        u.l = __fadd_rn(u.l, __fadd_rn(t.l, pz.l));
+        const F2 r2 = fast_two_sum(u.h, u.l);
+        // r^-1: float seed y0, residual e = 1 - r^2 y0^2 kept as e_h + e_l,
+        // y1 = y0 (1 + e/2 + 3 e^2 / 8)
+        const float y0 = rsqrtf(r2.h);
+        const F2 q2 = two_prod(y0, y0);
+        const F2 s = ds_mul(r2, q2);
+        const float eh = __fsub_rn(1.0f, s.h);  // exact (Sterbenz)
+        // y0 e / 2 = (c.h + c.l - y0 s.l) / 2 with y0 eh = c.h + c.l exactly;
+        // the 3 y0 e^2 / 8 term enters the low part as 0.75 y0 eh^2 / 2
+        const F2 c = two_prod(y0, eh);
+        const float cl =
+            __fmaf_rn(__fmul_rn(0.75f, y0), __fmul_rn(eh, eh), __fmaf_rn(y0, -s.l, c.l));
+        const F2 yy = fast_two_sum(y0, __fmul_rn(0.5f, c.h));
+        const F2 y1{yy.h, __fmaf_rn(0.5f, cl, yy.l)};
+        // m_j r^-3 = m_j y1^3
+        const F2 y12 = ds_mul(y1, y1);
+        F2 sc = ds_mul(mj, ds_mul(y12, y1));
+        if (r2.h <= fmaxf(thi[k], thj)) {
+          // possible encounter (or coincident bodies): exact FP64 branch
+          const double r2d = sep2(dx, dy, dz);
+          const double s64 = rare_pair<true>(r2d, scale_fast<NB_PREC_FP64>(r2d, A.m[jt + q]),
+                                             A.m[jt + q], ii[k], jt + q, rc2i[k], rci[k], A);
+          sc = split_d(s64);
+        }
+        const F2 cx = ds_mul(sc, fx), cy = ds_mul(sc, fy), cz = ds_mul(sc, fz);
+        F2 w = two_sum(tx[k].h, cx.h);
+        tx[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tx[k].l, cx.l))};
+        w = two_sum(ty[k].h, cy.h);
+        ty[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(ty[k].l, cy.l))};
+        w = two_sum(tz[k].h, cz.h);
+        tz[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tz[k].l, cz.l))};
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DIPT; ++k) {
+      ax[k] += (double)tx[k].h + (double)tx[k].l;
+      ay[k] += (double)ty[k].h + (double)ty[k].l;
+      az[k] += (double)tz[k].h + (double)tz[k].l;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DIPT; ++k) {
+    const int i = ii[k];
+    if (i < n) {
+      double* p = A.kpart + (size_t)(3 * sidx) * n;
+      p[i] = ax[k];
+      p[n + i] = ay[k];
+      p[2 * n + i] = az[k];
+    }
+  }
+}
+
 int kick_blocks(int n, int S) { return ((n + KNT * KIPT - 1) / (KNT * KIPT)) * S; }
 
 static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) {
   const int grid = kick_blocks(A.n, A.S);
   if (grid <= 0) return;
+  static_assert(KNT * KIPT == DNT2 * DIPT, "kick variants share the i-tile size");
   if (precision == NB_PREC_MIXED)
     k_kick<NB_PREC_MIXED><<<grid, KNT, 0, st>>>(A);
+  else if (precision == NB_PREC_DS)
+    k_kick_ds<<<grid, DNT2, 0, st>>>(A);
   else
     k_kick<NB_PREC_FP64><<<grid, KNT, 0, st>>>(A);
 }

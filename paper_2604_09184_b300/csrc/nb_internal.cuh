@@ -92,19 +92,25 @@ __device__ __forceinline__ void set_status(Ctrl* c, int code, int where) {
 }
 
 // ---------------------------------------------------------------------------
-// Changeover (the paragraph after Eq. Hc): smooth K from 0 to 1 between 0.1 rc
-// and rc, K(y) = y^2 / (2y^2 - 2y + 1) with y = (r - 0.1 rc) / (0.9 rc).
-// Returns the kick weight w = K - r dK/dr: the pair force of Eq. Hb is
-// G m_i m_j w (x_j - x_i) / r^3 and the close part of Eq. Ha carries 1 - w.
+// Changeover (the paragraph after Eq. Hc): K goes smoothly from 0 at 0.1 rc to
+// 1 at rc. Infinitely differentiable switch in y = (r - 0.1 rc) / (0.9 rc):
+// K = f(y) / (f(y) + f(1 - y)) with f(y) = exp(-1/y), so every derivative
+// vanishes at both edges and the extrapolation of the close-encounter solver
+// stays valid across them. Returns the kick weight w = K - r dK/dr: the pair
+// force of Eq. Hb is G m_i m_j w (x_j - x_i) / r^3 and the close part of
+// Eq. Ha carries 1 - w.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double kick_weight(double r, double rc) {
   const double y = (r - 0.1 * rc) / (0.9 * rc);
   if (y <= 0.0) return 0.0;
   if (y >= 1.0) return 1.0;
-  const double q = 2.0 * y * y - 2.0 * y + 1.0;
-  const double K = y * y / q;
-  const double dKdy = 2.0 * y * (1.0 - y) / (q * q);
-  return K - r * dKdy / (0.9 * rc);
+  const double u = 1.0 - y;
+  const double f = exp(-1.0 / y), g = exp(-1.0 / u);
+  const double s = f + g;
+  const double fg = f * g;
+  // dK/dy = f g (1/y^2 + 1/(1-y)^2) / (f + g)^2, zero where f g underflows
+  const double dKdy = fg > 0.0 ? fg * (1.0 / (y * y) + 1.0 / (u * u)) / (s * s) : 0.0;
+  return f / s - r * dKdy / (0.9 * rc);
 }
 
 // Squared separation in the fixed rounding that decides encounter flags:

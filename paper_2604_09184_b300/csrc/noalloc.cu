@@ -58,7 +58,7 @@ extern "C" int nb_kick_noalloc(int n, const double* x, const double* m, const do
                                int* npairs, void* stream) {
   if (n < 1 || !x || !m || !rc || !a || cap < 0 || (cap > 0 && !pairs_ij)) return NB_E_INVALID;
   if (n > NB_NOALLOC_MAX_N) return NB_E_INVALID;  // larger systems need nb_kick()
-  if (precision != NB_PREC_FP64 && precision != NB_PREC_MIXED) return NB_E_INVALID;
+  if (precision < NB_PREC_FP64 || precision > NB_PREC_DS) return NB_E_INVALID;
   void* base = nullptr;
   const int st0 = scratch_address(&base);
   if (st0 != NB_OK) return st0;

@@ -24,6 +24,7 @@ NB_E_TIMEOUT = -5
 NB_E_WORKSPACE = -6
 NB_PREC_FP64 = 0
 NB_PREC_MIXED = 1
+NB_PREC_DS = 2
 
 
 class NbParams(C.Structure):

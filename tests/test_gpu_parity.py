@@ -87,20 +87,39 @@ def test_kick_giants_and_disk():
     check_kick(d.x, d.m, oracle_rc(d), split=0)
 
 
-def test_kick_mixed_error_bound():
+@pytest.mark.parametrize("prec_name", ["NB_PREC_MIXED", "NB_PREC_DS"])
+def test_kick_reduced_precision_error_bound(prec_name):
+    """Mixed (float seed, one FP64 Newton step) and double-single kicks against
+    the FP64 kick and the oracle: flags identical, accelerations to 1e-10."""
     d = ics.workload("mmsn_16k_js", n=3000)
     nb = nbmod()
-    rc = oracle_rc(d)
+    rc = oracle_rc(d, scale=3.0)
+    prec = getattr(nb, prec_name)
     a64, p64, c1 = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, nb.NB_PREC_FP64)
-    amx, pmx, c2 = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, nb.NB_PREC_MIXED)
+    amx, pmx, c2 = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, prec)
     assert c1 == 0 and c2 == 0
     a64, amx = a64.cpu().numpy(), amx.cpu().numpy()
     rel = np.linalg.norm(amx - a64, axis=1) / np.linalg.norm(a64, axis=1)
     assert rel.max() < 1e-10
+    assert np.median(rel) < 1e-12
     assert pairset(pmx.cpu().numpy()) == pairset(p64.cpu().numpy())
     ar, _ = nbref.forces(d.x, d.m, rc, G)
     rel_o = np.linalg.norm(amx - ar, axis=1) / np.linalg.norm(ar, axis=1)
     assert rel_o.max() < 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 257, 1000])
+def test_kick_ds_small_and_ragged(n):
+    d = ics.workload("toy_disk_256", n=n, seed_offset=7 * n)
+    nb = nbmod()
+    rc = oracle_rc(d, scale=8.0)
+    a, pairs, code = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, nb.NB_PREC_DS, 3)
+    assert code == 0
+    ar, pr = nbref.forces(d.x, d.m, rc, G)
+    a = a.cpu().numpy()
+    err = np.linalg.norm(a - ar, axis=1)
+    assert np.all(err <= 1e-10 * np.linalg.norm(ar, axis=1) + 1e-13 * np.abs(ar).max())
+    assert pairset(pairs.cpu().numpy()) == pairset(pr)
 
 
 def test_kick_full_size_sampled():
@@ -156,12 +175,12 @@ def test_kepler_iteration_cap():
 
 
 # ------------------------------------------------------------------ full steps
-def run_both(d, steps, rc_scale=1.0, **kw):
+def run_both(d, steps, rc_scale=1.0, precision=0, **kw):
     nb = nbmod()
     rp = nbref.params(dt_rcrit=d.dt, **kw)
     rc = oracle_rc(d, rp, rc_scale)
     ref = nbref.RefSystem(rp, d.x, d.v, d.m, d.R, rc=rc)
-    gp = nb.params(dt_rcrit=d.dt, **kw)
+    gp = nb.params(dt_rcrit=d.dt, precision=precision, **kw)
     gpu = nb.NBodySystem(gp, d.x, d.v, d.m, d.R, rc=rc)
     assert ref.step(steps, d.dt) == 0
     gpu.step(steps, d.dt)
@@ -238,6 +257,17 @@ def test_step_parity_with_mergers():
     compare_states(ref, gpu)
     er, eg = ref.energy_momentum(), gpu.energy_momentum()
     assert abs(eg["E_lost"] - er["E_lost"]) <= 1e-10 * abs(er["E_lost"]) + 1e-22
+    assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+
+
+@pytest.mark.parametrize("prec_name", ["NB_PREC_MIXED", "NB_PREC_DS"])
+def test_step_parity_reduced_precision_100_steps(prec_name):
+    """The reduced-precision kicks perturb a planet-planet force that is ~1e-4
+    of the star's pull, so the 100-step state still meets the FP64 bar."""
+    d = ics.workload("toy_disk_256")
+    nb = nbmod()
+    ref, gpu = run_both(d, 100, precision=getattr(nb, prec_name))
+    compare_states(ref, gpu)
     assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
 
 

@@ -271,10 +271,10 @@ def _ha_group_deriv(m, rc):
             return np.longdouble(0)
         if y >= 1:
             return np.longdouble(1)
-        d = 2 * y * y - 2 * y + 1
-        K = y * y / d
-        dK = 2 * y * (1 - y) / (d * d) / (np.longdouble(0.9) * rcij)
-        return K - r * dK
+        f, g = np.exp(-1 / y), np.exp(-1 / (1 - y))
+        K = f / (f + g)
+        dK = f * g * (1 / (y * y) + 1 / ((1 - y) * (1 - y))) / ((f + g) ** 2)
+        return K - r * dK / (np.longdouble(0.9) * rcij)
 
     def f(y):
         out = np.zeros_like(y)
