@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed", "ds"], default="fp64",
                     help="kick precision of the timed run (profiling); the line's value is fp64")
     return ap.parse_args()
@@ -280,6 +281,10 @@ def run_ours(args):
                  "double_single": run_variant(nb, torch, disk, args, nb.NB_PREC_DS, ms_per_step,
                                               kick_ms, pps, flush, stream)}
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(nb, torch, args, flush, stream)
+
     # end to end through the C ABI with host buffers: per step, load the state
     # from pinned host memory, step, read the state back to pinned host memory
     e2e = None
@@ -295,6 +300,7 @@ def run_ours(args):
                    "precision": args.precision, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
                    "l2": "flushed before each timed step (256 MiB write, outside the step events)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+        "batched": batched,
         "clocks": clk, "gpu_launches": gpu_launches,
         "encounters": {"pairs": st["encounter_pairs"], "groups": st["groups"],
                        "bs_substeps": st["bs_substeps"], "merges": st["merges"],
@@ -339,6 +345,68 @@ def run_variant(nb, torch, disk, args, precision, ms64, kick64, pps, flush, stre
             "speedup_step": ms64 / ms, "speedup_kick": kick64 / kms,
             "max_rel_err_accel_vs_fp64": rel.max().item(),
             "median_rel_err_accel_vs_fp64": rel.median().item(), "flags_identical": same_flags}
+
+
+def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=32):
+    """The 4096-system ensemble (N log-uniform in [16, 512]) in one persistent
+    launch per step; speedup against integrating the same systems one at a time
+    through the single-system path, estimated on a random sample of systems."""
+    from paper_2604_09184_b300 import ics
+    disks = ics.ensemble(n_systems=n_systems)
+    pairs = float(sum(d.n * (d.n - 1) for d in disks))
+    b = nb.NBodyBatch(nb.params(dt_rcrit=dt), disks)
+    threads, _ = b.autotune(dt)
+    b.set_shape(threads, 25)
+    for _ in range(max(args.warmup, 0)):
+        b.step(1, dt)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        b.step(1, dt)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms_call = sum(a.elapsed_time(c) for a, c in ev) / max(args.steps, 1)
+    # production use: many steps per call, replayed from the captured graph
+    flush_l2(flush)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(2 * 25, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 50
+    st = b.stats()
+    del b
+    # single-system path on a random sample of the same systems
+    rng = np.random.default_rng(7)
+    pick = rng.choice(n_systems, size=min(sample, n_systems), replace=False)
+    t_single = []
+    for k in pick:
+        d = disks[int(k)]
+        s1 = nb.NBodySystem(nb.params(dt_rcrit=dt), d.x, d.v, d.m, d.R)
+        s1.step(1, dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            s1.step(1, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_single.append(e0.elapsed_time(e1) / 3)
+        del s1
+    single_ms = float(np.mean(t_single)) * n_systems
+    return {"workload": "ensemble_4096 (N log-uniform 16..512, dt 3 d)", "systems": n_systems,
+            "pairs_per_step": pairs, "value": pairs / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "steps_per_s": 1e3 / ms, "threads_per_cta": threads,
+            "timing": "one call of 50 steps (2 graph replays of 25-step chunks), L2 flushed before",
+            "ms_per_step_one_call_per_step": ms_call,
+            "single_system_path_ms_per_step_est": single_ms, "speedup_vs_single": single_ms / ms,
+            "speedup_vs_single_one_call_per_step": single_ms / ms_call,
+            "single_sample": int(len(pick)), "bs_substeps": st["bs_substeps"],
+            "groups": st["groups"], "merges": st["merges"]}
 
 
 def nb_rc_initial(nb, disk):

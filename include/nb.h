@@ -156,6 +156,50 @@ const char* nb_last_error(const nb_system* s);
 const char* nb_status_string(int status);
 
 /* ---------------------------------------------------------------------
+ * Batched ensembles: many independent systems (each its own star and
+ * bodies, the same method and parameters) integrated by one persistent
+ * launch in which a CTA takes whole systems, largest first, and runs all
+ * steps of a chunk with the system in shared memory. Chunks are replayed
+ * from a captured CUDA graph. System s owns body slots offsets[s] ..
+ * offsets[s+1]-1 of the concatenated arrays; 1 <= N_s <= NB_BATCH_MAX_N.
+ * --------------------------------------------------------------------- */
+#define NB_BATCH_MAX_N 512
+typedef struct nb_batch nb_batch;
+
+/* Workspace bytes for nsys systems with the given offsets (host, nsys + 1). */
+size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets);
+
+/* x, v [total][3], m, R [total], rc_override [total] or NULL; host pointers
+ * unless inputs_on_device. offsets are host. Evaluates the first force and
+ * flags of every system. Errors as nb_init_system. */
+int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offsets,
+                  const double* x, const double* v, const double* m, const double* R,
+                  const double* rc_override, void* workspace, size_t ws_bytes, void* stream,
+                  int inputs_on_device);
+
+/* Advance every system by nsteps steps of dt: full chunks replay a captured
+ * graph, the remainder is launched directly. Synchronises; atomic like
+ * nb_step (any error restores the state at entry). */
+int nb_batch_step(nb_batch* b, int nsteps, double dt);
+
+/* Launch shape: threads per CTA (64, 128 or 256) and steps per launch
+ * (1..1000). nb_batch_autotune() times each shape on a copy of the state
+ * (the state is restored afterwards) and keeps the fastest. */
+int nb_batch_set_shape(nb_batch* b, int threads, int chunk);
+int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step);
+
+/* All slots (offsets layout): x, v [total][3], m, R [total], alive [total]
+ * (0 for bodies absorbed by mergers). Any pointer may be NULL. */
+int nb_batch_get_state(nb_batch* b, double* x, double* v, double* m, double* R, int* alive,
+                       int out_on_device);
+
+/* Per-system energy (Eqs. Ha + Hb + Hc) and energy removed by mergers, host
+ * arrays of nsys. */
+int nb_batch_energy(nb_batch* b, double* E, double* E_lost);
+int nb_batch_stats(nb_batch* b, nb_stats_t* out);
+void nb_batch_destroy(nb_batch* b);
+
+/* ---------------------------------------------------------------------
  * Single-kernel entry points (one launch each, on caller device buffers).
  * --------------------------------------------------------------------- */
 

@@ -16,8 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnb.so")
 SOURCES = ["abi.cu", "kick.cu", "drift.cu", "encounter.cu", "energy.cu", "peaks.cu",
-           "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "nb_internal.cuh"), os.path.join(ROOT, "include", "nb.h")]
+           "noalloc.cu", "batch.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("nb_internal.cuh", "bs.cuh", "kepler.cuh")] + [
+    os.path.join(ROOT, "include", "nb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I" + os.path.join(ROOT, "include")]

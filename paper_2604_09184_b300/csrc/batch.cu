@@ -1,0 +1,928 @@
+// Batched ensembles: thousands of independent systems of uneven N integrated
+// by one persistent launch. A CTA takes a whole system (largest first, from a
+// work counter), loads it into shared memory and runs every step of the chunk
+// there: B(h/2) C(h/2) A(h) C(h/2) B(h/2) with the same kick, flags, Kepler
+// drift, encounter set, groups, Bulirsch-Stoer and mergers as the
+// single-system path (the force after an encounter is re-evaluated in full:
+// N <= 512 makes that cheaper than bookkeeping). Systems never interact, so
+// no CTA waits on another. Chunks of steps are replayed from a captured CUDA
+// graph; the launch shape (threads per CTA) comes from the autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "bs.cuh"
+#include "kepler.cuh"
+#include "nb_internal.cuh"
+
+namespace nb {
+
+constexpr int BPAIR = 1024;  // flagged pairs per system per force evaluation
+
+struct BatchDev {
+  int nsys, total, nmax;
+  const int* off;    // nsys + 1 body offsets
+  const int* order;  // systems, largest first
+  double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *ax, *ay, *az;
+  int* alive;
+  unsigned* fprev;  // nsys * BPAIR keys (i << 16 | j), local indices, i < j
+  int* nfprev;      // nsys
+  double* El;       // nsys: energy removed by mergers
+  double* gscr;     // total * bs_stride: BS scratch per body slot
+  double* gnew;     // total * 10
+  int bs_stride;
+  int* queue;       // work counter, reset before each launch
+  int* status;      // [0] first error, [1] system index
+  unsigned long long* stats;
+};
+
+// Shared-memory layout for nmax bodies and NT threads.
+struct BSmem {
+  double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *rc2, *ax, *ay, *az, *xs, *ys, *zs, *vxs, *vys,
+      *vzs;
+  double* red;   // 99 doubles (block reductions)
+  double* bred;  // NT doubles (BS error reduction)
+  int* alive;
+  unsigned *fp, *ft, *e;  // F_prev, F_trial (BPAIR each), E keys (2 BPAIR)
+  int *uf, *goff, *gmem, *gidx;
+  int* ints;  // [0] nFp [1] nFt [2] nE [3] ngroups [4] overflow [5] bs flags(2) ...
+};
+
+__host__ __device__ inline size_t batch_smem_bytes(int nmax, int NT) {
+  return (size_t)19 * nmax * 8 + (size_t)(99 + NT) * 8 + (size_t)nmax * 4 +
+         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + 16 * 4;
+}
+
+__device__ inline BSmem carve_smem(char* base, int nmax, int NT) {
+  BSmem s;
+  double* d = (double*)base;
+  double** arr[] = {&s.x,  &s.y,  &s.z,  &s.vx, &s.vy, &s.vz, &s.m,   &s.R,   &s.rc,  &s.rc2,
+                    &s.ax, &s.ay, &s.az, &s.xs, &s.ys, &s.zs, &s.vxs, &s.vys, &s.vzs};
+  for (double** a : arr) {
+    *a = d;
+    d += nmax;
+  }
+  s.red = d;
+  d += 99;
+  s.bred = d;
+  d += NT;
+  int* ip = (int*)d;
+  s.alive = ip;
+  ip += nmax;
+  unsigned* up = (unsigned*)ip;
+  s.fp = up;
+  up += BPAIR;
+  s.ft = up;
+  up += BPAIR;
+  s.e = up;
+  up += 2 * BPAIR;
+  ip = (int*)up;
+  s.uf = ip;
+  ip += nmax;
+  s.goff = ip;
+  ip += nmax + 1;
+  s.gmem = ip;
+  ip += nmax;
+  s.gidx = ip;
+  ip += nmax;
+  s.ints = ip;
+  return s;
+}
+
+// Sum of m v over live bodies (fixed order); result in all threads.
+__device__ void sys_momentum(const BSmem& s, int n, double P[3]) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (!s.alive[i]) continue;
+    a += s.m[i] * s.vx[i];
+    b += s.m[i] * s.vy[i];
+    c += s.m[i] * s.vz[i];
+  }
+  block_sum3(a, b, c, s.red);
+  if (threadIdx.x == 0) {
+    s.red[96] = a;
+    s.red[97] = b;
+    s.red[98] = c;
+  }
+  __syncthreads();
+  P[0] = s.red[96];
+  P[1] = s.red[97];
+  P[2] = s.red[98];
+  __syncthreads();
+}
+
+// Kick of Eq. Hb and flags for all live targets of the system (ascending j
+// sums; same pair expression and exact branch as the single-system kernel).
+__device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* fcount,
+                         int* overflow) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (!s.alive[i]) {
+      s.ax[i] = s.ay[i] = s.az[i] = 0.0;
+      continue;
+    }
+    const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
+    const int hi = __double2hiint(rc2i);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double dx = s.x[j] - xi, dy = s.y[j] - yi, dz = s.z[j] - zi;
+      const double r2 = sep2(dx, dy, dz);
+      const double mj = s.m[j];
+      double sc = scale_fast<NB_PREC_FP64>(r2, mj);
+      if (__double2hiint(r2) <= max(hi, __double2hiint(s.rc2[j]))) {
+        const double rc2 = fmax(rc2i, s.rc2[j]);
+        const bool close = (r2 < rc2) && s.alive[j] && (j != i);
+        if (close && i < j) {
+          const int pos = atomicAdd(fcount, 1);
+          if (pos < BPAIR)
+            flist[pos] = ((unsigned)i << 16) | (unsigned)j;
+          else
+            *overflow = 1;
+        }
+        if (r2 == 0.0) {
+          sc = 0.0;
+        } else if (close) {
+          const double r = sqrt(r2);
+          sc = mj * kick_weight(r, fmax(rci, s.rc[j])) / (r2 * r);
+        }
+      }
+      ax = __fma_rn(sc, dx, ax);
+      ay = __fma_rn(sc, dy, ay);
+      az = __fma_rn(sc, dz, az);
+    }
+    s.ax[i] = G * ax;
+    s.ay[i] = G * ay;
+    s.az[i] = G * az;
+  }
+}
+
+__device__ void sort_u32(unsigned* a, int P2) {
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const unsigned ai = a[i], aj = a[ixj];
+          if ((ai > aj) == up) {
+            a[i] = aj;
+            a[ixj] = ai;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int uf_root(int* uf, int k) {
+  while (uf[k] != k) {
+    uf[k] = uf[uf[k]];
+    k = uf[k];
+  }
+  return k;
+}
+
+struct SysTally {
+  unsigned long long force_evals, enc_pairs, groups, kepler_iters;
+};
+
+// One system for nsteps steps (nsteps == 0: initial force and flags only).
+__device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, int sys, int nsteps,
+                             double h, BsTally& bt, SysTally& st) {
+  const int base = B.off[sys];
+  const int n = B.off[sys + 1] - base;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    s.x[i] = B.x[g]; s.y[i] = B.y[g]; s.z[i] = B.z[g];
+    s.vx[i] = B.vx[g]; s.vy[i] = B.vy[g]; s.vz[i] = B.vz[g];
+    s.m[i] = B.m[g]; s.R[i] = B.R[g]; s.rc[i] = B.rc[g]; s.rc2[i] = B.rc[g] * B.rc[g];
+    s.ax[i] = B.ax[g]; s.ay[i] = B.ay[g]; s.az[i] = B.az[g];
+    s.alive[i] = B.alive[g];
+  }
+  const int nfp0 = min(B.nfprev[sys], BPAIR);
+  for (int k = threadIdx.x; k < nfp0; k += blockDim.x) s.fp[k] = B.fprev[(size_t)sys * BPAIR + k];
+  if (threadIdx.x == 0) {
+    s.ints[0] = nfp0;
+    s.ints[4] = 0;
+  }
+  double El_sys = 0.0;
+  int err = 0;
+  __syncthreads();
+  if (nsteps == 0) {
+    if (threadIdx.x == 0) s.ints[1] = 0;
+    __syncthreads();
+    sys_kick(s, n, P.G, s.fp, &s.ints[1], &s.ints[4]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s.ints[0] = min(s.ints[1], BPAIR);
+      st.force_evals += 1;
+      if (s.ints[4]) err = NB_E_OVERFLOW;
+    }
+    __syncthreads();
+  }
+  const double hh = 0.5 * h;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (!s.alive[i]) continue;
+      s.vx[i] += hh * s.ax[i];
+      s.vy[i] += hh * s.ay[i];
+      s.vz[i] += hh * s.az[i];
+    }
+    __syncthreads();
+    double Pt[3];
+    sys_momentum(s, n, Pt);
+    unsigned long long kit = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (!s.alive[i]) continue;
+      double x = s.x[i] + hh * Pt[0] / P.m0, y = s.y[i] + hh * Pt[1] / P.m0,
+             z = s.z[i] + hh * Pt[2] / P.m0;
+      double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
+      s.xs[i] = x; s.ys[i] = y; s.zs[i] = z;
+      s.vxs[i] = vx; s.vys[i] = vy; s.vzs[i] = vz;
+      int it = 0;
+      if (kepler_drift(P.mu, x, y, z, vx, vy, vz, h, P.kepler_max_iter, &it)) s.ints[4] = 2;
+      kit += it;
+      s.x[i] = x; s.y[i] = y; s.z[i] = z;
+      s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
+    }
+    if (threadIdx.x == 0) s.ints[1] = 0;
+    __syncthreads();
+    st.kepler_iters += kit;
+    sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
+    __syncthreads();
+    if (s.ints[4]) {  // overflow or Kepler failure: stop this system
+      err = s.ints[4] == 2 ? NB_E_NOCONV : NB_E_OVERFLOW;
+      break;
+    }
+    // E = F_prev U F_trial
+    const int nfp = s.ints[0], nft = min(s.ints[1], BPAIR), nk = nfp + nft;
+    int P2 = 1;
+    while (P2 < nk) P2 <<= 1;
+    for (int k = threadIdx.x; k < P2; k += blockDim.x)
+      s.e[k] = k < nfp ? s.fp[k] : (k < nk ? s.ft[k - nfp] : 0xffffffffu);
+    __syncthreads();
+    sort_u32(s.e, P2);
+    if (threadIdx.x == 0) {
+      int ne = 0;
+      for (int k = 0; k < nk; ++k)
+        if (ne == 0 || s.e[k] != s.e[ne - 1]) s.e[ne++] = s.e[k];
+      s.ints[2] = ne;
+      st.force_evals += 1;
+      st.enc_pairs += ne;
+      // groups: union by the smaller index; groups in ascending order of their
+      // smallest member, members ascending
+      int ng = 0;
+      if (ne > 0) {
+        for (int b = 0; b < n; ++b) {
+          s.uf[b] = b;
+          s.gidx[b] = -1;
+        }
+        for (int k = 0; k < ne; ++k) {
+          const int a = uf_root(s.uf, (int)(s.e[k] >> 16)), c = uf_root(s.uf, (int)(s.e[k] & 0xffffu));
+          if (a < c)
+            s.uf[c] = a;
+          else if (c < a)
+            s.uf[a] = c;
+        }
+        for (int k = 0; k < ne; ++k) {  // bodies in E
+          s.gidx[s.e[k] >> 16] = -2;
+          s.gidx[s.e[k] & 0xffffu] = -2;
+        }
+        // group index of each root (its smallest member), in ascending order
+        for (int b = 0; b < n; ++b)
+          if (s.gidx[b] == -2 && uf_root(s.uf, b) == b) s.gidx[b] = ng++;
+        // every member takes its root's group index (roots keep theirs)
+        for (int b = 0; b < n; ++b)
+          if (s.gidx[b] == -2) s.gidx[b] = s.gidx[uf_root(s.uf, b)];
+        for (int g = 0; g <= ng; ++g) s.goff[g] = 0;
+        for (int b = 0; b < n; ++b)
+          if (s.gidx[b] >= 0) ++s.goff[s.gidx[b] + 1];
+        for (int g = 0; g < ng; ++g) s.goff[g + 1] += s.goff[g];
+        for (int g = 0; g < ng; ++g) s.uf[g] = s.goff[g];  // cursors (roots no longer needed)
+        for (int b = 0; b < n; ++b)
+          if (s.gidx[b] >= 0) s.gmem[s.uf[s.gidx[b]]++] = b;
+        st.groups += ng;
+      }
+      s.ints[3] = ng;
+    }
+    __syncthreads();
+    const int ne = s.ints[2], ng = s.ints[3];
+    if (ne > 0) {
+      for (int g = 0; g < ng; ++g) {
+        const int g0 = s.goff[g];
+        BsCtx c;
+        c.M = s.goff[g + 1] - g0;
+        c.stride = B.bs_stride;
+        c.base = B.gscr + (size_t)(base + g0) * B.bs_stride;
+        c.g = B.gnew + (size_t)(base + g0) * 10;
+        c.kmax = P.bs_kmax;
+        c.G = P.G;
+        c.mu = P.mu;
+        for (int k = threadIdx.x; k < c.M; k += blockDim.x) {
+          const int b = s.gmem[g0 + k];
+          double* yk = c.base + (size_t)k * c.stride + OY;
+          yk[0] = s.xs[b]; yk[1] = s.ys[b]; yk[2] = s.zs[b];
+          yk[3] = s.vxs[b]; yk[4] = s.vys[b]; yk[5] = s.vzs[b];
+          double* gk = c.g + 10 * k;
+          gk[6] = s.m[b]; gk[7] = s.R[b]; gk[8] = s.rc[b]; gk[9] = 1.0;
+          bs_set_aux(c, k, P.G, gk[6], gk[8]);
+        }
+        __syncthreads();
+        double El = 0.0;
+        const int stb = bs_integrate_group(c, P, h, s.bred, &s.ints[6], bt, &El);
+        if (threadIdx.x == 0) El_sys += El;
+        for (int k = threadIdx.x; k < c.M; k += blockDim.x) {
+          const int b = s.gmem[g0 + k];
+          const double* yk = c.base + (size_t)k * c.stride + OY;
+          const double* gk = c.g + 10 * k;
+          if (gk[9] != 0.0) {
+            s.x[b] = yk[0]; s.y[b] = yk[1]; s.z[b] = yk[2];
+            s.vx[b] = yk[3]; s.vy[b] = yk[4]; s.vz[b] = yk[5];
+            s.m[b] = gk[6]; s.R[b] = gk[7]; s.rc[b] = gk[8]; s.rc2[b] = gk[8] * gk[8];
+          } else {  // absorbed: massless slot far from everything, never flagged
+            s.alive[b] = 0;
+            s.x[b] = kDeadOffset * (double)(base + b + 1); s.y[b] = 0.0; s.z[b] = 0.0;
+            s.vx[b] = s.vy[b] = s.vz[b] = 0.0;
+            s.m[b] = 0.0; s.R[b] = 0.0; s.rc[b] = 0.0; s.rc2[b] = 0.0;
+          }
+        }
+        __syncthreads();
+        if (stb) {
+          err = stb;
+          break;
+        }
+      }
+      if (err) break;
+      // force and flags at the final positions
+      if (threadIdx.x == 0) s.ints[1] = 0;
+      __syncthreads();
+      sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
+      __syncthreads();
+      if (s.ints[4]) {
+        err = NB_E_OVERFLOW;
+        break;
+      }
+      if (threadIdx.x == 0) st.force_evals += 1;
+    }
+    const int nf = min(s.ints[1], BPAIR);
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) s.fp[k] = s.ft[k];
+    if (threadIdx.x == 0) s.ints[0] = nf;
+    __syncthreads();
+    sys_momentum(s, n, Pt);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (!s.alive[i]) continue;
+      s.x[i] += hh * Pt[0] / P.m0;
+      s.y[i] += hh * Pt[1] / P.m0;
+      s.z[i] += hh * Pt[2] / P.m0;
+      s.vx[i] += hh * s.ax[i];
+      s.vy[i] += hh * s.ay[i];
+      s.vz[i] += hh * s.az[i];
+    }
+    __syncthreads();
+  }
+  if (err && threadIdx.x == 0) {
+    if (atomicCAS(&B.status[0], 0, err) == 0) B.status[1] = sys;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    B.x[g] = s.x[i]; B.y[g] = s.y[i]; B.z[g] = s.z[i];
+    B.vx[g] = s.vx[i]; B.vy[g] = s.vy[i]; B.vz[g] = s.vz[i];
+    B.m[g] = s.m[i]; B.R[g] = s.R[i]; B.rc[g] = s.rc[i];
+    B.ax[g] = s.ax[i]; B.ay[g] = s.ay[i]; B.az[g] = s.az[i];
+    B.alive[g] = s.alive[i];
+  }
+  const int nfp = s.ints[0];
+  for (int k = threadIdx.x; k < nfp; k += blockDim.x) B.fprev[(size_t)sys * BPAIR + k] = s.fp[k];
+  if (threadIdx.x == 0) {
+    B.nfprev[sys] = nfp;
+    B.El[sys] += El_sys;
+  }
+  __syncthreads();
+}
+
+__global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const BSmem s = carve_smem(smem_raw, B.nmax, blockDim.x);
+  __shared__ int s_next, s_stop;
+  BsTally bt{0, 0, 0, 0};
+  SysTally st{0, 0, 0, 0};
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_stop = B.status[0];
+      s_next = s_stop ? B.nsys : atomicAdd(B.queue, 1);
+    }
+    __syncthreads();
+    const int k = s_next;
+    if (k >= B.nsys) break;
+    batch_system(B, P, s, B.order[k], nsteps, h, bt, st);
+  }
+  // counters: kepler iterations are per thread; the rest are kept by thread 0
+  unsigned long long kit = st.kepler_iters;
+  for (int o = 16; o > 0; o >>= 1) kit += __shfl_down_sync(0xffffffffu, kit, o);
+  if ((threadIdx.x & 31) == 0 && kit) atomicAdd(&B.stats[ST_KEPLER_ITERS], kit);
+  if (threadIdx.x == 0) {
+    atomicAdd(&B.stats[ST_FORCE_EVALS], st.force_evals);
+    atomicAdd(&B.stats[ST_ENC_PAIRS], st.enc_pairs);
+    atomicAdd(&B.stats[ST_GROUPS], st.groups);
+    atomicAdd(&B.stats[ST_BS_SUBSTEPS], (unsigned long long)bt.substeps);
+    atomicAdd(&B.stats[ST_BS_HALVINGS], (unsigned long long)bt.halvings);
+    atomicAdd(&B.stats[ST_BS_DERIVS], (unsigned long long)bt.derivs);
+    atomicAdd(&B.stats[ST_MERGES], (unsigned long long)bt.merges);
+  }
+}
+
+// Per-body initialisation: validation and r_crit (Eq. rcrit).
+__global__ void k_batch_init(BatchDev B, Phys P, const double* x3, const double* v3,
+                             const double* m, const double* R, const double* rco) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.total) return;
+  const double x = x3[3 * i], y = x3[3 * i + 1], z = x3[3 * i + 2];
+  const double vx = v3[3 * i], vy = v3[3 * i + 1], vz = v3[3 * i + 2];
+  bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
+            isfinite(vz) && isfinite(m[i]) && m[i] > 0.0 && isfinite(R[i]) && R[i] >= 0.0 &&
+            (x != 0.0 || y != 0.0 || z != 0.0);
+  double rc = 0.0;
+  if (ok) rc = rco ? rco[i] : rcrit(P, x, y, z, vx, vy, vz, m[i]);
+  ok = ok && isfinite(rc) && rc > 0.0;
+  if (!ok && atomicCAS(&B.status[0], 0, NB_E_INVALID) == 0) B.status[1] = -1;
+  B.x[i] = x; B.y[i] = y; B.z[i] = z;
+  B.vx[i] = vx; B.vy[i] = vy; B.vz[i] = vz;
+  B.m[i] = m[i]; B.R[i] = R[i]; B.rc[i] = rc;
+  B.ax[i] = B.ay[i] = B.az[i] = 0.0;
+  B.alive[i] = 1;
+}
+
+// Per-system energy (H_A + H_B + H_C; K cancels), one CTA per system.
+__global__ void k_batch_energy(BatchDev B, Phys P, double* E) {
+  __shared__ double red[8 * 256];
+  const int sys = blockIdx.x;
+  const int base = B.off[sys], n = B.off[sys + 1] - base;
+  double ke = 0.0, pe = 0.0, pc = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    if (!B.alive[g]) continue;
+    const double r = sqrt(B.x[g] * B.x[g] + B.y[g] * B.y[g] + B.z[g] * B.z[g]);
+    ke += 0.5 * B.m[g] * (B.vx[g] * B.vx[g] + B.vy[g] * B.vy[g] + B.vz[g] * B.vz[g]) -
+          P.G * P.m0 * B.m[g] / r;
+    for (int j = i + 1; j < n; ++j) {
+      const int q = base + j;
+      if (!B.alive[q]) continue;
+      const double dx = B.x[q] - B.x[g], dy = B.y[q] - B.y[g], dz = B.z[q] - B.z[g];
+      const double t = -P.G * B.m[g] * B.m[q] / sqrt(dx * dx + dy * dy + dz * dz);
+      const double s2 = pe + t;  // Neumaier
+      const double bb = s2 - pe;
+      pc += (pe - (s2 - bb)) + (t - bb);
+      pe = s2;
+    }
+    px += B.m[g] * B.vx[g];
+    py += B.m[g] * B.vy[g];
+    pz += B.m[g] * B.vz[g];
+  }
+  red[threadIdx.x] = ke;
+  red[256 + threadIdx.x] = pe + pc;
+  red[512 + threadIdx.x] = px;
+  red[768 + threadIdx.x] = py;
+  red[1024 + threadIdx.x] = pz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, cx = 0, cy = 0, cz = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      a += red[t];
+      b += red[256 + t];
+      cx += red[512 + t];
+      cy += red[768 + t];
+      cz += red[1024 + t];
+    }
+    E[sys] = a + b + (cx * cx + cy * cy + cz * cz) / (2.0 * P.m0);
+  }
+}
+
+__global__ void k_batch_gather(BatchDev B, double* x3, double* v3, double* m, double* R,
+                               int* alive) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.total) return;
+  if (x3) { x3[3 * i] = B.x[i]; x3[3 * i + 1] = B.y[i]; x3[3 * i + 2] = B.z[i]; }
+  if (v3) { v3[3 * i] = B.vx[i]; v3[3 * i + 1] = B.vy[i]; v3[3 * i + 2] = B.vz[i]; }
+  if (m) m[i] = B.m[i];
+  if (R) R[i] = B.R[i];
+  if (alive) alive[i] = B.alive[i];
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+namespace {
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct BCarver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    off = a256(off);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int bs_stride_for(const nb_params& p) {
+  const int kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
+  return 6 * (4 + 2 * kmax) + 4;
+}
+
+struct Snap {
+  double* arrays;  // 12 * total
+  int* alive;
+  unsigned* fprev;
+  int* nfprev;
+  double* El;
+  unsigned long long* stats;
+};
+
+size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDev* out,
+                    Snap* snap, double** eout, double** stage) {
+  BatchDev d;
+  memset(&d, 0, sizeof(d));
+  d.nsys = nsys;
+  d.total = total;
+  d.bs_stride = bs_stride_for(p);
+  BCarver c{base, 0};
+  d.off = c.take<int>((size_t)nsys + 1);
+  d.order = c.take<int>(nsys);
+  double** arr[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.m, &d.R, &d.rc, &d.ax, &d.ay, &d.az};
+  for (double** a : arr) *a = c.take<double>(total);
+  d.alive = c.take<int>(total);
+  d.fprev = c.take<unsigned>((size_t)nsys * BPAIR);
+  d.nfprev = c.take<int>(nsys);
+  d.El = c.take<double>(nsys);
+  d.gscr = c.take<double>((size_t)total * d.bs_stride);
+  d.gnew = c.take<double>((size_t)total * 10);
+  d.queue = c.take<int>(4);
+  d.status = c.take<int>(4);
+  d.stats = c.take<unsigned long long>(kStatN);
+  Snap s;
+  s.arrays = c.take<double>((size_t)12 * total);
+  s.alive = c.take<int>(total);
+  s.fprev = c.take<unsigned>((size_t)nsys * BPAIR);
+  s.nfprev = c.take<int>(nsys);
+  s.El = c.take<double>(nsys);
+  s.stats = c.take<unsigned long long>(kStatN);
+  double* e = c.take<double>((size_t)nsys);
+  if (out) *out = d;
+  if (snap) *snap = s;
+  if (eout) *eout = e;
+  if (stage) *stage = s.arrays;  // host inputs are staged in the snapshot area
+  return a256(c.off);
+}
+
+}  // namespace
+
+struct nb_batch {
+  BatchDev d;
+  Phys P;
+  nb_params prm;
+  cudaStream_t st;
+  Snap snap;
+  double* E;
+  int threads, chunk;
+  size_t smem;
+  cudaGraphExec_t gexec;
+  cudaStream_t cap;  // private stream for graph capture (the caller's may be the legacy stream)
+  int g_threads, g_chunk;
+  double g_dt;
+  long long steps_done;
+  char err[256];
+};
+
+namespace {
+
+#define NB_BCU(call)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      if (b) snprintf(b->err, sizeof(b->err), "%s: %s", #call, cudaGetErrorString(e_)); \
+      return NB_E_CUDA;                                                                \
+    }                                                                                  \
+  } while (0)
+
+Phys phys_of(const nb_params& p) {
+  Phys P;
+  P.G = p.G; P.m0 = p.m0; P.mu = p.G * p.m0; P.dt_rcrit = p.dt_rcrit;
+  P.hill_factor = p.hill_factor; P.vel_factor = p.vel_factor; P.bs_tol = p.bs_tol;
+  P.vel_mode = p.vel_mode; P.merge = p.merge; P.precision = NB_PREC_FP64;
+  P.kepler_max_iter = p.kepler_max_iter;
+  P.bs_kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
+  P.bs_max_halvings = p.bs_max_halvings > 40 ? 40 : p.bs_max_halvings;
+  return P;
+}
+
+int batch_grid(const nb_batch* b) {
+  int dev = 0, sms = 148, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = maxsm > 0 ? (int)(maxsm / (b->smem + 1024)) : 1;
+  const int by_threads = 2048 / b->threads;
+  if (per_sm > by_threads) per_sm = by_threads;
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > b->d.nsys) grid = b->d.nsys;
+  return grid;
+}
+
+int launch_batch(nb_batch* b, int nsteps, double dt) {
+  b->smem = batch_smem_bytes(b->d.nmax, b->threads);
+  NB_BCU(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)b->smem));
+  NB_BCU(cudaMemsetAsync(b->d.queue, 0, sizeof(int), b->st));
+  k_batch<<<batch_grid(b), b->threads, b->smem, b->st>>>(b->d, b->P, nsteps, dt);
+  NB_BCU(cudaGetLastError());
+  return NB_OK;
+}
+
+int batch_snapshot(nb_batch* b, int dir) {
+  const BatchDev& d = b->d;
+  const Snap& s = b->snap;
+  const size_t nb = sizeof(double) * d.total;
+  double* arr[] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.R, d.rc, d.ax, d.ay, d.az};
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  for (int q = 0; q < 12; ++q) {
+    double* sp = s.arrays + (size_t)q * d.total;
+    NB_BCU(cudaMemcpyAsync(dir ? arr[q] : sp, dir ? sp : arr[q], nb, k, b->st));
+  }
+  const size_t fb = sizeof(unsigned) * (size_t)d.nsys * BPAIR;
+  NB_BCU(cudaMemcpyAsync(dir ? d.alive : s.alive, dir ? s.alive : d.alive, sizeof(int) * d.total, k, b->st));
+  NB_BCU(cudaMemcpyAsync(dir ? d.fprev : s.fprev, dir ? s.fprev : d.fprev, fb, k, b->st));
+  NB_BCU(cudaMemcpyAsync(dir ? d.nfprev : s.nfprev, dir ? s.nfprev : d.nfprev, sizeof(int) * d.nsys, k, b->st));
+  NB_BCU(cudaMemcpyAsync(dir ? d.El : s.El, dir ? s.El : d.El, sizeof(double) * d.nsys, k, b->st));
+  NB_BCU(cudaMemcpyAsync(dir ? d.stats : s.stats, dir ? s.stats : d.stats,
+                         sizeof(unsigned long long) * kStatN, k, b->st));
+  if (dir) NB_BCU(cudaMemsetAsync(d.status, 0, 2 * sizeof(int), b->st));
+  return NB_OK;
+}
+
+int read_status(nb_batch* b, int* st2) {
+  NB_BCU(cudaMemcpyAsync(st2, b->d.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  return NB_OK;
+}
+
+int run_steps(nb_batch* b, int nsteps, double dt) {
+  const int chunk = b->chunk;
+  const int full = nsteps / chunk, rem = nsteps - full * chunk;
+  if (full > 0) {
+    if (!b->gexec || b->g_threads != b->threads || b->g_chunk != chunk || b->g_dt != dt) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      // capture one chunk: reset the work counter, run `chunk` steps
+      b->smem = batch_smem_bytes(b->d.nmax, b->threads);
+      NB_BCU(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)b->smem));
+      const int grid = batch_grid(b);
+      if (!b->cap) NB_BCU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      NB_BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      cudaMemsetAsync(b->d.queue, 0, sizeof(int), b->cap);
+      k_batch<<<grid, b->threads, b->smem, b->cap>>>(b->d, b->P, chunk, dt);
+      NB_BCU(cudaStreamEndCapture(b->cap, &g));
+      NB_BCU(cudaGraphInstantiate(&b->gexec, g, 0));
+      cudaGraphDestroy(g);
+      b->g_threads = b->threads;
+      b->g_chunk = chunk;
+      b->g_dt = dt;
+    }
+    for (int k = 0; k < full; ++k) NB_BCU(cudaGraphLaunch(b->gexec, b->st));
+  }
+  if (rem > 0) {
+    const int rc = launch_batch(b, rem, dt);
+    if (rc) return rc;
+  }
+  return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets) {
+  if (!p || nsys < 1 || !offsets || offsets[0] != 0) return 0;
+  for (int s = 0; s < nsys; ++s) {
+    const int n = offsets[s + 1] - offsets[s];
+    if (n < 1 || n > NB_BATCH_MAX_N) return 0;
+  }
+  return batch_layout(*p, nsys, offsets[nsys], nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offsets,
+                  const double* x, const double* v, const double* m, const double* R,
+                  const double* rc_override, void* workspace, size_t ws_bytes, void* stream,
+                  int inputs_on_device) {
+  if (!out) return NB_E_INVALID;
+  *out = nullptr;
+  const size_t need = nb_batch_workspace_bytes(p, nsys, offsets);
+  if (need == 0 || !x || !v || !m || !R) return NB_E_INVALID;
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return NB_E_WORKSPACE;
+  nb_batch* b = (nb_batch*)calloc(1, sizeof(nb_batch));
+  if (!b) return NB_E_INVALID;
+  b->prm = *p;
+  b->P = phys_of(*p);
+  b->st = (cudaStream_t)stream;
+  const int total = offsets[nsys];
+  double* stage = nullptr;
+  batch_layout(*p, nsys, total, (char*)workspace, &b->d, &b->snap, &b->E, &stage);
+  // host bookkeeping: max N and the largest-first order
+  std::vector<int> order(nsys);
+  int nmax = 1;
+  for (int s = 0; s < nsys; ++s) {
+    order[s] = s;
+    nmax = std::max(nmax, offsets[s + 1] - offsets[s]);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return offsets[a + 1] - offsets[a] > offsets[c + 1] - offsets[c];
+  });
+  b->d.nmax = nmax;
+  b->threads = 128;
+  b->chunk = 25;
+  int rc = NB_OK;
+  do {
+    if (cudaMemcpyAsync((void*)b->d.off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice,
+                        b->st) != cudaSuccess ||
+        cudaMemcpyAsync((void*)b->d.order, order.data(), sizeof(int) * nsys,
+                        cudaMemcpyHostToDevice, b->st) != cudaSuccess) {
+      rc = NB_E_CUDA;
+      break;
+    }
+    cudaMemsetAsync(b->d.nfprev, 0, sizeof(int) * nsys, b->st);
+    cudaMemsetAsync(b->d.El, 0, sizeof(double) * nsys, b->st);
+    cudaMemsetAsync(b->d.status, 0, 4 * sizeof(int), b->st);
+    cudaMemsetAsync(b->d.stats, 0, sizeof(unsigned long long) * kStatN, b->st);
+    const double *ix = x, *iv = v, *im = m, *iR = R, *irc = rc_override;
+    if (!inputs_on_device) {
+      const size_t b3 = sizeof(double) * 3 * total, b1 = sizeof(double) * total;
+      cudaMemcpyAsync(stage, x, b3, cudaMemcpyHostToDevice, b->st);
+      cudaMemcpyAsync(stage + 3 * total, v, b3, cudaMemcpyHostToDevice, b->st);
+      cudaMemcpyAsync(stage + 6 * total, m, b1, cudaMemcpyHostToDevice, b->st);
+      cudaMemcpyAsync(stage + 7 * total, R, b1, cudaMemcpyHostToDevice, b->st);
+      ix = stage; iv = stage + 3 * total; im = stage + 6 * total; iR = stage + 7 * total;
+      if (rc_override) {
+        cudaMemcpyAsync(stage + 8 * total, rc_override, b1, cudaMemcpyHostToDevice, b->st);
+        irc = stage + 8 * total;
+      }
+    }
+    k_batch_init<<<(total + 255) / 256, 256, 0, b->st>>>(b->d, b->P, ix, iv, im, iR, irc);
+    rc = launch_batch(b, 0, 0.0);
+    if (rc) break;
+    int st2[2];
+    if (read_status(b, st2) != NB_OK || cudaGetLastError() != cudaSuccess) {
+      rc = NB_E_CUDA;
+      break;
+    }
+    if (st2[0]) rc = st2[0];
+  } while (0);
+  if (rc != NB_OK) {
+    nb_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return NB_OK;
+}
+
+int nb_batch_set_shape(nb_batch* b, int threads, int chunk) {
+  if (!b || (threads != 64 && threads != 128 && threads != 256) || chunk < 1 || chunk > 1000)
+    return NB_E_INVALID;
+  b->threads = threads;
+  b->chunk = chunk;
+  return NB_OK;
+}
+
+int nb_batch_step(nb_batch* b, int nsteps, double dt) {
+  if (!b || nsteps < 0 || !std::isfinite(dt)) return NB_E_INVALID;
+  if (nsteps == 0) return NB_OK;
+  int rc = batch_snapshot(b, 0);
+  if (rc) return rc;
+  rc = run_steps(b, nsteps, dt);
+  if (rc) return rc;
+  int st2[2];
+  rc = read_status(b, st2);
+  if (rc) return rc;
+  if (st2[0]) {
+    snprintf(b->err, sizeof(b->err), "%s in system %d (state rolled back)",
+             nb_status_string(st2[0]), st2[1]);
+    const int code = st2[0];
+    rc = batch_snapshot(b, 1);
+    NB_BCU(cudaStreamSynchronize(b->st));
+    return rc ? rc : code;
+  }
+  b->steps_done += nsteps;
+  return NB_OK;
+}
+
+int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step) {
+  if (!b || !std::isfinite(dt)) return NB_E_INVALID;
+  const int shapes[3] = {64, 128, 256};
+  const int probe = 2;
+  const int keep_t = b->threads, keep_c = b->chunk;
+  double best = 1e30;
+  int best_t = keep_t;
+  int rc = batch_snapshot(b, 0);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  NB_BCU(cudaEventCreate(&e0));
+  NB_BCU(cudaEventCreate(&e1));
+  for (int t : shapes) {
+    b->threads = t;
+    b->chunk = probe;
+    rc = launch_batch(b, 1, dt);  // warm-up
+    if (rc) break;
+    NB_BCU(cudaEventRecord(e0, b->st));
+    rc = launch_batch(b, probe, dt);
+    if (rc) break;
+    NB_BCU(cudaEventRecord(e1, b->st));
+    NB_BCU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    NB_BCU(cudaEventElapsedTime(&ms, e0, e1));
+    const double per = ms / probe;
+    if (per < best) {
+      best = per;
+      best_t = t;
+    }
+    rc = batch_snapshot(b, 1);  // restore the state after every trial
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  NB_BCU(cudaStreamSynchronize(b->st));
+  b->threads = rc ? keep_t : best_t;
+  b->chunk = keep_c;
+  if (threads) *threads = b->threads;
+  if (ms_per_step) *ms_per_step = best;
+  return rc;
+}
+
+int nb_batch_get_state(nb_batch* b, double* x, double* v, double* m, double* R, int* alive,
+                       int out_on_device) {
+  if (!b) return NB_E_INVALID;
+  const int total = b->d.total;
+  if (out_on_device) {
+    k_batch_gather<<<(total + 255) / 256, 256, 0, b->st>>>(b->d, x, v, m, R, alive);
+    NB_BCU(cudaStreamSynchronize(b->st));
+    return NB_OK;
+  }
+  // gather into the snapshot area, then copy out
+  double* g = b->snap.arrays;
+  int* ga = b->snap.alive;
+  k_batch_gather<<<(total + 255) / 256, 256, 0, b->st>>>(b->d, g, g + 3 * (size_t)total,
+                                                         g + 6 * (size_t)total,
+                                                         g + 7 * (size_t)total, ga);
+  const size_t b3 = sizeof(double) * 3 * total, b1 = sizeof(double) * total;
+  if (x) NB_BCU(cudaMemcpyAsync(x, g, b3, cudaMemcpyDeviceToHost, b->st));
+  if (v) NB_BCU(cudaMemcpyAsync(v, g + 3 * (size_t)total, b3, cudaMemcpyDeviceToHost, b->st));
+  if (m) NB_BCU(cudaMemcpyAsync(m, g + 6 * (size_t)total, b1, cudaMemcpyDeviceToHost, b->st));
+  if (R) NB_BCU(cudaMemcpyAsync(R, g + 7 * (size_t)total, b1, cudaMemcpyDeviceToHost, b->st));
+  if (alive) NB_BCU(cudaMemcpyAsync(alive, ga, sizeof(int) * total, cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  return NB_OK;
+}
+
+int nb_batch_energy(nb_batch* b, double* E, double* E_lost) {
+  if (!b) return NB_E_INVALID;
+  k_batch_energy<<<b->d.nsys, 256, 0, b->st>>>(b->d, b->P, b->E);
+  if (E) NB_BCU(cudaMemcpyAsync(E, b->E, sizeof(double) * b->d.nsys, cudaMemcpyDeviceToHost, b->st));
+  if (E_lost)
+    NB_BCU(cudaMemcpyAsync(E_lost, b->d.El, sizeof(double) * b->d.nsys, cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  return NB_OK;
+}
+
+int nb_batch_stats(nb_batch* b, nb_stats_t* out) {
+  if (!b || !out) return NB_E_INVALID;
+  unsigned long long h[kStatN];
+  NB_BCU(cudaMemcpyAsync(h, b->d.stats, sizeof(h), cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  memset(out, 0, sizeof(*out));
+  out->steps = b->steps_done;
+  out->force_evals = (long long)h[ST_FORCE_EVALS];
+  out->encounter_pairs = (long long)h[ST_ENC_PAIRS];
+  out->groups = (long long)h[ST_GROUPS];
+  out->bs_substeps = (long long)h[ST_BS_SUBSTEPS];
+  out->bs_halvings = (long long)h[ST_BS_HALVINGS];
+  out->bs_derivs = (long long)h[ST_BS_DERIVS];
+  out->merges = (long long)h[ST_MERGES];
+  out->kepler_iters = (long long)h[ST_KEPLER_ITERS];
+  return NB_OK;
+}
+
+void nb_batch_destroy(nb_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  free(b);
+}
+
+}  // extern "C"

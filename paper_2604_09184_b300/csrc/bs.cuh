@@ -1,0 +1,281 @@
+// Direct solver for close-encounter groups (the paper's "direct solver" for
+// H_A when bodies are in a close encounter, section "The hybrid symplectic
+// integrator"; perfect mergers per "Detailing the outcomes of collisions").
+// Shared by the single-system kernel (one CTA per group) and the batched
+// kernel (each system's CTA integrates its own groups).
+#pragma once
+
+#include "nb_internal.cuh"
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// Bulirsch-Stoer for one group per CTA.
+// Scratch per member slot (stride doubles): y[6] | zm[6] | zc[6] | f[6] |
+// T[2][kmax][6] | aux[4] = (G m, 1 / (0.9 rc), rc^2, unused). Working copies
+// of m, R, rc, alive live in gnew[slot*10+6..9].
+//
+// A group of two bodies keeps only two lanes of its CTA busy, and every FP64
+// warp instruction holds the B300 FP64 pipe for the full warp, so the solver's
+// speed is its FP64 instruction count per derivative: the right-hand side uses
+// the seeded reciprocal roots and reciprocals of nb_internal.cuh instead of
+// sqrt and divisions, and per-member constants are precomputed.
+// ---------------------------------------------------------------------------
+constexpr int OY = 0, OZM = 6, OZC = 12, OF = 18, OT = 24;
+
+struct BsCtx {
+  double* base;  // scratch of the group's first slot
+  double* g;     // gnew of the group's first slot
+  int stride, M, kmax;
+  double G, mu;
+};
+
+__device__ __forceinline__ bool bs_alive(const BsCtx& c, int b) { return c.g[10 * b + 9] != 0.0; }
+
+__device__ __forceinline__ double* bs_aux(const BsCtx& c, int b) {
+  return c.base + (size_t)b * c.stride + OT + 12 * c.kmax;
+}
+
+__device__ __forceinline__ void bs_set_aux(const BsCtx& c, int b, double G, double m, double rc) {
+  double* a = bs_aux(c, b);
+  a[0] = G * m;
+  a[1] = 1.0 / (0.9 * rc);
+  a[2] = rc * rc;
+}
+
+// 1 - w for a pair inside rc (w = K - r dK/dr, K the infinitely smooth switch):
+// y < 1/746 gives exp(-1/y) = 0 exactly, so w = 0; 1 - y < 1/746 gives w = 1.
+__device__ __forceinline__ double close_weight(double qq, double rc, double inv09) {
+  const double y = (qq - 0.1 * rc) * inv09;
+  if (y < 1.0 / 746.0) return 1.0;
+  const double u = 1.0 - y;
+  if (u < 1.0 / 746.0) return 0.0;
+  const double iy = rcp_fast(y), iu = rcp_fast(u);
+  const double f = exp(-iy), g = exp(-iu);
+  const double rs = rcp_fast(f + g);
+  const double fg = f * g;
+  const double dKdy = fg > 0.0 ? fg * __fma_rn(iy, iy, iu * iu) * (rs * rs) : 0.0;
+  return 1.0 - (f * rs - qq * dKdy * inv09);
+}
+
+// f = d/dt of field fo for member b (Eq. Ha restricted to the group).
+static __device__ void bs_deriv(const BsCtx& c, int fo, int b) {
+  const double* yb = c.base + (size_t)b * c.stride + fo;
+  double* fb = c.base + (size_t)b * c.stride + OF;
+  if (!bs_alive(c, b)) {
+    for (int k = 0; k < 6; ++k) fb[k] = 0.0;
+    return;
+  }
+  fb[0] = yb[3];
+  fb[1] = yb[4];
+  fb[2] = yb[5];
+  const double r2 = __fma_rn(yb[2], yb[2], __fma_rn(yb[1], yb[1], yb[0] * yb[0]));
+  const double ks = -scale_fast<NB_PREC_FP64>(r2, c.mu);  // -mu / r^3
+  double ax = ks * yb[0], ay = ks * yb[1], az = ks * yb[2];
+  const double rcb = c.g[10 * b + 8];
+  const double* ab = bs_aux(c, b);
+  for (int q = 0; q < c.M; ++q) {
+    if (q == b || !bs_alive(c, q)) continue;
+    const double* yq = c.base + (size_t)q * c.stride + fo;
+    const double dx = yq[0] - yb[0], dy = yq[1] - yb[1], dz = yq[2] - yb[2];
+    const double q2 = sep2(dx, dy, dz);
+    if (q2 == 0.0) continue;
+    const double* aq = bs_aux(c, q);
+    if (!(q2 < fmax(ab[2], aq[2]))) continue;  // 1 - w = 0 beyond rc
+    const double ri = rinv_fast(q2);
+    const double omw = close_weight(q2 * ri, fmax(rcb, c.g[10 * q + 8]), fmin(ab[1], aq[1]));
+    const double f = aq[0] * omw * (ri * ri * ri);
+    ax = __fma_rn(f, dx, ax);
+    ay = __fma_rn(f, dy, ay);
+    az = __fma_rn(f, dz, az);
+  }
+  fb[3] = ax;
+  fb[4] = ay;
+  fb[5] = az;
+}
+
+static __device__ double pair_energy(const Phys& P, const double* a, double ma, const double* b,
+                              double mb) {
+  const double va2 = a[3] * a[3] + a[4] * a[4] + a[5] * a[5];
+  const double vb2 = b[3] * b[3] + b[4] * b[4] + b[5] * b[5];
+  const double ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const double rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+  const double rab = sqrt(dx * dx + dy * dy + dz * dz);
+  return 0.5 * ma * va2 + 0.5 * mb * vb2 - P.G * P.m0 * ma / ra - P.G * P.m0 * mb / rb -
+         P.G * ma * mb / rab;
+}
+
+// Perfect merging on contact, scanned in ascending slot (= body) order.
+static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, int* merges) {
+  for (int a = 0; a < c.M; ++a) {
+    for (int b = a + 1; b < c.M; ++b) {
+      if (!bs_alive(c, a) || !bs_alive(c, b)) continue;
+      double* ya = c.base + (size_t)a * c.stride + OY;
+      double* yb = c.base + (size_t)b * c.stride + OY;
+      const double dx = yb[0] - ya[0], dy = yb[1] - ya[1], dz = yb[2] - ya[2];
+      const double rab = sqrt(dx * dx + dy * dy + dz * dz);
+      double* ga = c.g + 10 * a;
+      double* gb = c.g + 10 * b;
+      if (!(rab < ga[7] + gb[7])) continue;
+      const double ma = ga[6], mb = gb[6];
+      const double e0 = pair_energy(P, ya, ma, yb, mb);
+      const double M = ma + mb;
+      for (int k = 0; k < 6; ++k) ya[k] = (ma * ya[k] + mb * yb[k]) / M;
+      const double Rn = cbrt(ga[7] * ga[7] * ga[7] + gb[7] * gb[7] * gb[7]);
+      ga[6] = M;
+      ga[7] = Rn;
+      gb[9] = 0.0;
+      const double v2 = ya[3] * ya[3] + ya[4] * ya[4] + ya[5] * ya[5];
+      const double r = sqrt(ya[0] * ya[0] + ya[1] * ya[1] + ya[2] * ya[2]);
+      const double e1 = 0.5 * M * v2 - P.G * P.m0 * M / r;
+      *El += e0 - e1;
+      ga[8] = rcrit(P, ya[0], ya[1], ya[2], ya[3], ya[4], ya[5], M);
+      bs_set_aux(c, a, P.G, M, ga[8]);
+      *merges += 1;
+    }
+  }
+}
+
+
+// Counters of the direct solver (summed over the groups a CTA integrates).
+struct BsTally {
+  long long derivs, substeps, halvings, merges;
+};
+
+// Integrate H_A restricted to one group over h with all threads of the
+// calling CTA (any blockDim): Gragg modified midpoint with n_k = 2k substeps,
+// Neville extrapolation in the substep squared, acceptance at k >= 3 when
+// every live body's position and velocity changes between the two highest
+// columns are within bs_tol of its own max-norm; halving on failure at k_max,
+// doubling back after an early success on an aligned boundary; perfect
+// merging scan after every accepted substep. The group state starts in the
+// y fields and ends there. s_red: shared scratch of blockDim.x doubles;
+// s_flags: two shared ints. Returns 0, NB_E_NOCONV or NB_E_TIMEOUT (same in
+// every thread); *El (thread 0) receives the energy removed by mergers.
+static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
+                                  int* s_flags, BsTally& tally, double* El) {
+  const int kmax = c.kmax;
+  const int NT = blockDim.x;
+  int level = 0;
+  long long done = 0;
+  int status = 0;
+  long long attempts = 0;
+  int merges = 0;
+  while (done < (1ll << level)) {
+    const double H = ldexp(h, -level);
+    if (threadIdx.x == 0) {
+      s_flags[0] = 0;
+      s_flags[1] = 0;
+    }
+    for (int j = 1; j <= kmax; ++j) {
+      const int nsub = 2 * j;
+      const double hs = H / nsub;
+      for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OY, b);
+      __syncthreads();
+      for (int b = threadIdx.x; b < c.M; b += NT) {
+        double* s = c.base + (size_t)b * c.stride;
+        for (int k = 0; k < 6; ++k) {
+          s[OZM + k] = s[OY + k];
+          s[OZC + k] = s[OY + k] + hs * s[OF + k];
+        }
+      }
+      __syncthreads();
+      for (int m = 1; m < nsub; ++m) {
+        for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OZC, b);
+        __syncthreads();
+        for (int b = threadIdx.x; b < c.M; b += NT) {
+          double* s = c.base + (size_t)b * c.stride;
+          for (int k = 0; k < 6; ++k) {
+            const double zn = s[OZM + k] + 2.0 * hs * s[OF + k];
+            s[OZM + k] = s[OZC + k];
+            s[OZC + k] = zn;
+          }
+        }
+        __syncthreads();
+      }
+      for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OZC, b);
+      __syncthreads();
+      tally.derivs += nsub + 1;
+      double emax = 0.0;
+      for (int b = threadIdx.x; b < c.M; b += NT) {
+        double* s = c.base + (size_t)b * c.stride;
+        double* Tc = s + OT + (j & 1) * kmax * 6;
+        double* Tp = s + OT + ((j - 1) & 1) * kmax * 6;
+        for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (s[OZC + k] + s[OZM + k] + hs * s[OF + k]);
+        for (int q = 1; q < j; ++q) {
+          // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
+          const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+          for (int k = 0; k < 6; ++k) {
+            const double t = Tc[6 * (q - 1) + k];
+            Tc[6 * q + k] = __fma_rn(t - Tp[6 * (q - 1) + k], inv, t);
+          }
+        }
+        if (j >= 3 && bs_alive(c, b)) {
+          const double* A = Tc + 6 * (j - 1);
+          const double* B = Tc + 6 * (j - 2);
+          for (int part = 0; part < 2; ++part) {
+            double dm = 0.0, ym = 0.0;
+            for (int k = 3 * part; k < 3 * part + 3; ++k) {
+              dm = fmax(dm, fabs(A[k] - B[k]));
+              ym = fmax(ym, fabs(A[k]));
+            }
+            emax = fmax(emax, dm / (ym + 1e-300));
+          }
+        }
+      }
+      s_red[threadIdx.x] = emax;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int t = 0; t < NT; ++t) e = fmax(e, s_red[t]);
+        if (j >= 3 && e <= P.bs_tol) {
+          s_flags[0] = 1;
+          s_flags[1] = j;
+        }
+      }
+      __syncthreads();
+      if (s_flags[0]) {
+        for (int b = threadIdx.x; b < c.M; b += NT) {
+          double* s = c.base + (size_t)b * c.stride;
+          const double* Tc = s + OT + (j & 1) * kmax * 6 + 6 * (j - 1);
+          for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
+        }
+        __syncthreads();
+        break;
+      }
+    }
+    ++attempts;
+    const int acc = s_flags[0], kacc = s_flags[1];
+    if (acc) {
+      ++done;
+      ++tally.substeps;
+      if (P.merge) {
+        if (threadIdx.x == 0) bs_merge_scan(c, P, El, &merges);
+        __syncthreads();
+      }
+      if (level > 0 && (done & 1) == 0 && kacc <= kmax - 2) {
+        --level;
+        done >>= 1;
+      }
+    } else {
+      ++tally.halvings;
+      if (level >= P.bs_max_halvings) {
+        status = NB_E_NOCONV;
+        break;
+      }
+      ++level;
+      done *= 2;
+    }
+    if (attempts > 200000) {
+      status = NB_E_TIMEOUT;
+      break;
+    }
+    __syncthreads();
+  }
+  tally.merges += merges;
+  __syncthreads();
+  return status;
+}
+
+}  // namespace nb

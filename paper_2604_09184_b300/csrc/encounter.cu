@@ -13,6 +13,7 @@
 //   merging scan after every accepted substep.
 // k_scatter (one CTA): momentum change of the group bodies, energy removed
 //   by mergers, and the write-back of the group results.
+#include "bs.cuh"
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -202,113 +203,17 @@ void launch_encounter(const Dev& d, const Phys& P, cudaStream_t st) {
   k_encounter<<<1, ENT, 0, st>>>(d);
 }
 
-// ---------------------------------------------------------------------------
-// Bulirsch-Stoer for one group per CTA.
-// Scratch per member slot (stride doubles): y[6] | zm[6] | zc[6] | f[6] |
-// T[2][kmax][6]. Working copies of m, R, rc, alive live in gnew[slot*10+6..9].
-// ---------------------------------------------------------------------------
-constexpr int OY = 0, OZM = 6, OZC = 12, OF = 18, OT = 24;
-
-struct BsCtx {
-  double* base;  // scratch of the group's first slot
-  double* g;     // gnew of the group's first slot
-  int stride, M, kmax;
-  double G, mu;
-};
-
-__device__ __forceinline__ bool bs_alive(const BsCtx& c, int b) { return c.g[10 * b + 9] != 0.0; }
-
-// f = d/dt of field fo for member b (Eq. Ha restricted to the group).
-__device__ void bs_deriv(const BsCtx& c, int fo, int b) {
-  const double* yb = c.base + (size_t)b * c.stride + fo;
-  double* fb = c.base + (size_t)b * c.stride + OF;
-  if (!bs_alive(c, b)) {
-    for (int k = 0; k < 6; ++k) fb[k] = 0.0;
-    return;
-  }
-  fb[0] = yb[3];
-  fb[1] = yb[4];
-  fb[2] = yb[5];
-  const double r2 = yb[0] * yb[0] + yb[1] * yb[1] + yb[2] * yb[2];
-  const double r = sqrt(r2);
-  const double ks = -c.mu / (r2 * r);
-  double ax = ks * yb[0], ay = ks * yb[1], az = ks * yb[2];
-  const double rcb = c.g[10 * b + 8];
-  for (int q = 0; q < c.M; ++q) {
-    if (q == b || !bs_alive(c, q)) continue;
-    const double* yq = c.base + (size_t)q * c.stride + fo;
-    const double dx = yq[0] - yb[0], dy = yq[1] - yb[1], dz = yq[2] - yb[2];
-    const double q2 = sep2(dx, dy, dz);
-    if (q2 == 0.0) continue;
-    const double rc = fmax(rcb, c.g[10 * q + 8]);
-    if (!(q2 < rc * rc)) continue;  // 1 - w = 0 beyond rc
-    const double qq = sqrt(q2);
-    const double w = kick_weight(qq, rc);
-    const double f = c.G * c.g[10 * q + 6] * (1.0 - w) / (q2 * qq);
-    ax += f * dx;
-    ay += f * dy;
-    az += f * dz;
-  }
-  fb[3] = ax;
-  fb[4] = ay;
-  fb[5] = az;
-}
-
-__device__ double pair_energy(const Phys& P, const double* a, double ma, const double* b,
-                              double mb) {
-  const double va2 = a[3] * a[3] + a[4] * a[4] + a[5] * a[5];
-  const double vb2 = b[3] * b[3] + b[4] * b[4] + b[5] * b[5];
-  const double ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-  const double rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
-  const double rab = sqrt(dx * dx + dy * dy + dz * dz);
-  return 0.5 * ma * va2 + 0.5 * mb * vb2 - P.G * P.m0 * ma / ra - P.G * P.m0 * mb / rb -
-         P.G * ma * mb / rab;
-}
-
-// Perfect merging on contact, scanned in ascending slot (= body) order.
-__device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, int* merges) {
-  for (int a = 0; a < c.M; ++a) {
-    for (int b = a + 1; b < c.M; ++b) {
-      if (!bs_alive(c, a) || !bs_alive(c, b)) continue;
-      double* ya = c.base + (size_t)a * c.stride + OY;
-      double* yb = c.base + (size_t)b * c.stride + OY;
-      const double dx = yb[0] - ya[0], dy = yb[1] - ya[1], dz = yb[2] - ya[2];
-      const double rab = sqrt(dx * dx + dy * dy + dz * dz);
-      double* ga = c.g + 10 * a;
-      double* gb = c.g + 10 * b;
-      if (!(rab < ga[7] + gb[7])) continue;
-      const double ma = ga[6], mb = gb[6];
-      const double e0 = pair_energy(P, ya, ma, yb, mb);
-      const double M = ma + mb;
-      for (int k = 0; k < 6; ++k) ya[k] = (ma * ya[k] + mb * yb[k]) / M;
-      const double Rn = cbrt(ga[7] * ga[7] * ga[7] + gb[7] * gb[7] * gb[7]);
-      ga[6] = M;
-      ga[7] = Rn;
-      gb[9] = 0.0;
-      const double v2 = ya[3] * ya[3] + ya[4] * ya[4] + ya[5] * ya[5];
-      const double r = sqrt(ya[0] * ya[0] + ya[1] * ya[1] + ya[2] * ya[2]);
-      const double e1 = 0.5 * M * v2 - P.G * P.m0 * M / r;
-      *El += e0 - e1;
-      ga[8] = rcrit(P, ya[0], ya[1], ya[2], ya[3], ya[4], ya[5], M);
-      *merges += 1;
-    }
-  }
-}
-
 __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
   __shared__ int s_stop, s_ng;
-  __shared__ double s_err[BNT];
-  __shared__ int s_acc, s_kacc;
+  __shared__ double s_red[BNT];
+  __shared__ int s_flags[2];
   if (threadIdx.x == 0) {
     s_stop = d.ctrl->status;
     s_ng = d.ctrl->n_groups;
   }
   __syncthreads();
   if (s_stop) return;
-  const int kmax = P.bs_kmax;
-  long long derivs = 0, substeps = 0, halvings = 0;
-  int merges = 0;
+  BsTally tally{0, 0, 0, 0};
   for (int grp = blockIdx.x; grp < s_ng; grp += gridDim.x) {
     const int off = d.grp_off[grp];
     BsCtx c;
@@ -316,10 +221,10 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
     c.stride = d.bs_stride;
     c.base = d.gscr + (size_t)off * d.bs_stride;
     c.g = d.gnew + (size_t)off * 10;
-    c.kmax = kmax;
+    c.kmax = P.bs_kmax;
     c.G = P.G;
     c.mu = P.mu;
-    for (int b = threadIdx.x; b < c.M; b += BNT) {
+    for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
       const int body = d.grp_mem[off + b];
       double* y = c.base + (size_t)b * c.stride + OY;
       y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
@@ -329,125 +234,13 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
       g[7] = d.R[body];
       g[8] = d.rc[body];
       g[9] = 1.0;
+      bs_set_aux(c, b, P.G, g[6], g[8]);
     }
     __syncthreads();
     double El = 0.0;
-    int level = 0;
-    long long done = 0;
-    int status = 0;
-    long long attempts = 0;
-    while (done < (1ll << level)) {
-      const double H = ldexp(h, -level);
-      if (threadIdx.x == 0) {
-        s_acc = 0;
-        s_kacc = 0;
-      }
-      for (int j = 1; j <= kmax; ++j) {
-        const int nsub = 2 * j;
-        const double hs = H / nsub;
-        for (int b = threadIdx.x; b < c.M; b += BNT) bs_deriv(c, OY, b);
-        __syncthreads();
-        for (int b = threadIdx.x; b < c.M; b += BNT) {
-          double* s = c.base + (size_t)b * c.stride;
-          for (int k = 0; k < 6; ++k) {
-            s[OZM + k] = s[OY + k];
-            s[OZC + k] = s[OY + k] + hs * s[OF + k];
-          }
-        }
-        __syncthreads();
-        for (int m = 1; m < nsub; ++m) {
-          for (int b = threadIdx.x; b < c.M; b += BNT) bs_deriv(c, OZC, b);
-          __syncthreads();
-          for (int b = threadIdx.x; b < c.M; b += BNT) {
-            double* s = c.base + (size_t)b * c.stride;
-            for (int k = 0; k < 6; ++k) {
-              const double zn = s[OZM + k] + 2.0 * hs * s[OF + k];
-              s[OZM + k] = s[OZC + k];
-              s[OZC + k] = zn;
-            }
-          }
-          __syncthreads();
-        }
-        for (int b = threadIdx.x; b < c.M; b += BNT) bs_deriv(c, OZC, b);
-        __syncthreads();
-        derivs += nsub + 1;
-        double emax = 0.0;
-        for (int b = threadIdx.x; b < c.M; b += BNT) {
-          double* s = c.base + (size_t)b * c.stride;
-          double* Tc = s + OT + (j & 1) * kmax * 6;
-          double* Tp = s + OT + ((j - 1) & 1) * kmax * 6;
-          for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (s[OZC + k] + s[OZM + k] + hs * s[OF + k]);
-          for (int q = 1; q < j; ++q) {
-            const double ratio = (double)(2 * j) / (double)(2 * (j - q));
-            const double den = ratio * ratio - 1.0;
-            for (int k = 0; k < 6; ++k) {
-              const double t = Tc[6 * (q - 1) + k];
-              Tc[6 * q + k] = t + (t - Tp[6 * (q - 1) + k]) / den;
-            }
-          }
-          if (j >= 3 && bs_alive(c, b)) {
-            const double* A = Tc + 6 * (j - 1);
-            const double* B = Tc + 6 * (j - 2);
-            for (int part = 0; part < 2; ++part) {
-              double dm = 0.0, ym = 0.0;
-              for (int k = 3 * part; k < 3 * part + 3; ++k) {
-                dm = fmax(dm, fabs(A[k] - B[k]));
-                ym = fmax(ym, fabs(A[k]));
-              }
-              emax = fmax(emax, dm / (ym + 1e-300));
-            }
-          }
-        }
-        s_err[threadIdx.x] = emax;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double e = 0.0;
-          for (int t = 0; t < BNT; ++t) e = fmax(e, s_err[t]);
-          if (j >= 3 && e <= P.bs_tol) {
-            s_acc = 1;
-            s_kacc = j;
-          }
-        }
-        __syncthreads();
-        if (s_acc) {
-          for (int b = threadIdx.x; b < c.M; b += BNT) {
-            double* s = c.base + (size_t)b * c.stride;
-            const double* Tc = s + OT + (j & 1) * kmax * 6 + 6 * (j - 1);
-            for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
-          }
-          __syncthreads();
-          break;
-        }
-      }
-      ++attempts;
-      if (s_acc) {
-        ++done;
-        ++substeps;
-        if (P.merge) {
-          if (threadIdx.x == 0) bs_merge_scan(c, P, &El, &merges);
-          __syncthreads();
-        }
-        if (level > 0 && (done & 1) == 0 && s_kacc <= kmax - 2) {
-          --level;
-          done >>= 1;
-        }
-      } else {
-        ++halvings;
-        if (level >= P.bs_max_halvings) {
-          status = NB_E_NOCONV;
-          break;
-        }
-        ++level;
-        done *= 2;
-      }
-      if (attempts > 200000) {
-        status = NB_E_TIMEOUT;
-        break;
-      }
-      __syncthreads();
-    }
+    const int status = bs_integrate_group(c, P, h, s_red, s_flags, tally, &El);
     if (status && threadIdx.x == 0) set_status(d.ctrl, status, 30);
-    for (int b = threadIdx.x; b < c.M; b += BNT) {
+    for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
       const double* y = c.base + (size_t)b * c.stride + OY;
       double* g = c.g + 10 * b;
       for (int k = 0; k < 6; ++k) g[k] = y[k];
@@ -456,10 +249,10 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&d.ctrl->stats[ST_BS_DERIVS], (unsigned long long)derivs);
-    atomicAdd(&d.ctrl->stats[ST_BS_SUBSTEPS], (unsigned long long)substeps);
-    atomicAdd(&d.ctrl->stats[ST_BS_HALVINGS], (unsigned long long)halvings);
-    atomicAdd(&d.ctrl->stats[ST_MERGES], (unsigned long long)merges);
+    atomicAdd(&d.ctrl->stats[ST_BS_DERIVS], (unsigned long long)tally.derivs);
+    atomicAdd(&d.ctrl->stats[ST_BS_SUBSTEPS], (unsigned long long)tally.substeps);
+    atomicAdd(&d.ctrl->stats[ST_BS_HALVINGS], (unsigned long long)tally.halvings);
+    atomicAdd(&d.ctrl->stats[ST_MERGES], (unsigned long long)tally.merges);
   }
 }
 

@@ -56,29 +56,6 @@ __device__ __forceinline__ void emit_pair(bool f, int i, int j, int2* pairs, int
   }
 }
 
-// r^-3 seed: rsqrtf of r^2 rounded toward zero to a float through its high
-// word, returned as a double. Valid for 2^-126 <= r^2 < 2^128.
-__device__ __forceinline__ double rsqrt_seed(double r2) {
-  const unsigned hr = (unsigned)__double2hiint(r2);
-  const float r2f = __uint_as_float((hr << 3) + 0x40000000u);
-  const unsigned yb = __float_as_uint(rsqrtf(r2f));
-  return __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
-}
-
-// m_j / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual),
-// r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...). |e| < 2e-6, so
-// the second-order form (FP64 mode) is exact to ~1e-17 and the first-order
-// form (mixed mode, "one Newton step") to ~1e-11 relative at worst.
-template <int PREC>
-__device__ __forceinline__ double scale_fast(double r2, double mj) {
-  const double y0 = rsqrt_seed(r2);
-  const double t = y0 * y0;
-  const double e = __fma_rn(-r2, t, 1.0);
-  const double my3 = mj * (t * y0);
-  if (PREC == NB_PREC_FP64) return __fma_rn(my3, e * __fma_rn(1.875, e, 1.5), my3);
-  return __fma_rn(my3, 1.5 * e, my3);
-}
-
 // The exact branch: coincident bodies, changeover pairs and flag emission.
 template <bool FLAGS>
 __device__ __forceinline__ double rare_pair(double r2, double sc, double mj, int i, int j,

@@ -113,6 +113,53 @@ __device__ __forceinline__ double kick_weight(double r, double rc) {
   return f / s - r * dKdy / (0.9 * rc);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 reciprocal roots and reciprocals with few FP64 instructions: a float
+// seed from the MUFU unit (float built from the double's high word by one
+// integer shift-add, returned to a double by integer ops), refined in FP64.
+// ---------------------------------------------------------------------------
+// rsqrtf seed of r^2 > 0 rounded toward zero to a float; 2^-126 <= r^2 < 2^128.
+__device__ __forceinline__ double rsqrt_seed(double r2) {
+  const unsigned hr = (unsigned)__double2hiint(r2);
+  const float r2f = __uint_as_float((hr << 3) + 0x40000000u);
+  const unsigned yb = __float_as_uint(rsqrtf(r2f));
+  return __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
+}
+
+// m / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual),
+// r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...). |e| < 2e-6, so
+// the second-order form (FP64 mode) is exact to ~1e-17 and the first-order
+// form (mixed mode, "one Newton step") to ~1e-11 relative at worst.
+template <int PREC>
+__device__ __forceinline__ double scale_fast(double r2, double m) {
+  const double y0 = rsqrt_seed(r2);
+  const double t = y0 * y0;
+  const double e = __fma_rn(-r2, t, 1.0);
+  const double my3 = m * (t * y0);
+  if (PREC == NB_PREC_FP64) return __fma_rn(my3, e * __fma_rn(1.875, e, 1.5), my3);
+  return __fma_rn(my3, 1.5 * e, my3);
+}
+
+// 1/r from r^2: y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8), error ~1e-17 + rounding.
+__device__ __forceinline__ double rinv_fast(double r2) {
+  const double y0 = rsqrt_seed(r2);
+  const double e = __fma_rn(-r2, y0 * y0, 1.0);
+  return __fma_rn(y0 * e, __fma_rn(0.375, e, 0.5), y0);
+}
+
+// 1/x for positive normal x with 2^-126 <= x < 2^128: rcp.approx seed and two
+// Newton steps r <- r + r (1 - x r) (the error squares each step).
+__device__ __forceinline__ double rcp_fast(double x) {
+  const unsigned hx = (unsigned)__double2hiint(x);
+  const float xf = __uint_as_float((hx << 3) + 0x40000000u);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  const unsigned rb = __float_as_uint(rf);
+  double r = __hiloint2double((int)((rb >> 3) + 0x38000000u), (int)(rb << 29));
+  r = __fma_rn(r, __fma_rn(-x, r, 1.0), r);
+  return __fma_rn(r, __fma_rn(-x, r, 1.0), r);
+}
+
 // Squared separation in the fixed rounding that decides encounter flags:
 // fma(dz, dz, fma(dy, dy, dx*dx)), every operation correctly rounded.
 __device__ __forceinline__ double sep2(double dx, double dy, double dz) {

@@ -94,6 +94,18 @@ def lib():
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p]
         L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int, C.c_void_p, C.c_void_p]
+        L.nb_batch_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int, C.c_void_p]
+        L.nb_batch_workspace_bytes.restype = C.c_size_t
+        L.nb_batch_init.argtypes = [C.POINTER(C.c_void_p), C.POINTER(NbParams), C.c_int,
+                                    C.c_void_p] + [C.c_void_p] * 5 + [C.c_void_p, C.c_size_t,
+                                                                      C.c_void_p, C.c_int]
+        L.nb_batch_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.nb_batch_set_shape.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.nb_batch_autotune.argtypes = [C.c_void_p, C.c_double, _I, _D]
+        L.nb_batch_get_state.argtypes = [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]
+        L.nb_batch_energy.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.nb_batch_stats.argtypes = [C.c_void_p, C.POINTER(NbStats)]
+        L.nb_batch_destroy.argtypes = [C.c_void_p]
         L.nb_peak_scratch_bytes.argtypes = []
         L.nb_peak_scratch_bytes.restype = C.c_size_t
         L.nb_measure_peaks.argtypes = [_D, _D, C.c_void_p, C.c_void_p]
@@ -298,6 +310,96 @@ def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=
 
 
 NB_NOALLOC_MAX_N = 65600
+NB_BATCH_MAX_N = 512
+
+
+class NBodyBatch:
+    """Independent systems integrated together by libnb's batched kernel.
+
+    systems: list of objects with x (n,3), v (n,3), m (n,), R (n,) (numpy).
+    """
+
+    def __init__(self, p: NbParams, systems, rc=None):
+        torch = _torch()
+        L = lib()
+        self.p = p
+        ns = [int(np.asarray(d.m).shape[0]) for d in systems]
+        self.offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int32)
+        self.nsys = len(systems)
+        cat = lambda k: np.ascontiguousarray(np.concatenate([np.asarray(getattr(d, k), dtype=np.float64)  # noqa: E731
+                                                             for d in systems]))
+        self._x, self._v, self._m, self._R = cat("x"), cat("v"), cat("m"), cat("R")
+        self._rc = None if rc is None else np.ascontiguousarray(rc, dtype=np.float64)
+        nbytes = L.nb_batch_workspace_bytes(C.byref(p), self.nsys,
+                                            C.c_void_p(self.offsets.ctypes.data))
+        if nbytes == 0:
+            raise NbError(NB_E_INVALID, "bad parameters, sizes or offsets")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        ws = C.c_void_p(base + ((-base) % 256))
+        h = C.c_void_p()
+        code = L.nb_batch_init(C.byref(h), C.byref(p), self.nsys,
+                               C.c_void_p(self.offsets.ctypes.data),
+                               C.c_void_p(self._x.ctypes.data), C.c_void_p(self._v.ctypes.data),
+                               C.c_void_p(self._m.ctypes.data), C.c_void_p(self._R.ctypes.data),
+                               None if self._rc is None else C.c_void_p(self._rc.ctypes.data),
+                               ws, nbytes, _stream(torch), 0)
+        if code != NB_OK:
+            raise NbError(code, "nb_batch_init failed")
+        self._h = h
+        self.total = int(self.offsets[-1])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().nb_batch_destroy(h)
+            self._h = None
+
+    def _check(self, code):
+        if code != NB_OK:
+            raise NbError(code, "batched call failed")
+
+    def step(self, nsteps: int, dt: float):
+        self._check(lib().nb_batch_step(self._h, int(nsteps), float(dt)))
+
+    def step_status(self, nsteps: int, dt: float) -> int:
+        return lib().nb_batch_step(self._h, int(nsteps), float(dt))
+
+    def set_shape(self, threads: int, chunk: int):
+        self._check(lib().nb_batch_set_shape(self._h, threads, chunk))
+
+    def autotune(self, dt: float):
+        t, ms = C.c_int(), C.c_double()
+        self._check(lib().nb_batch_autotune(self._h, dt, C.byref(t), C.byref(ms)))
+        return t.value, ms.value
+
+    def state(self) -> dict:
+        n = self.total
+        x = np.zeros((n, 3)); v = np.zeros((n, 3)); m = np.zeros(n); R = np.zeros(n)
+        alive = np.zeros(n, dtype=np.int32)
+        self._check(lib().nb_batch_get_state(self._h, C.c_void_p(x.ctypes.data),
+                                             C.c_void_p(v.ctypes.data), C.c_void_p(m.ctypes.data),
+                                             C.c_void_p(R.ctypes.data),
+                                             C.c_void_p(alive.ctypes.data), 0))
+        return dict(x=x, v=v, m=m, R=R, alive=alive)
+
+    def system_state(self, s: int, st=None) -> dict:
+        st = st or self.state()
+        a, b = self.offsets[s], self.offsets[s + 1]
+        keep = st["alive"][a:b] != 0
+        return {k: st[k][a:b][keep] for k in ("x", "v", "m", "R")} | {
+            "ids": np.nonzero(keep)[0].astype(np.int32)}
+
+    def energy(self):
+        E = np.zeros(self.nsys); El = np.zeros(self.nsys)
+        self._check(lib().nb_batch_energy(self._h, C.c_void_p(E.ctypes.data),
+                                          C.c_void_p(El.ctypes.data)))
+        return E, El
+
+    def stats(self) -> dict:
+        st = NbStats()
+        self._check(lib().nb_batch_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in NbStats._fields_}
 
 
 def kick_noalloc(x, m, rc, a, pairs, G=2.959122082855911e-4, precision=NB_PREC_FP64):
