@@ -240,6 +240,63 @@ int nb_kepler_drift(int n, double mu, double* x, double* v, double dt, int max_i
 size_t nb_peak_scratch_bytes(void);
 int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of nb_step: the gradient of a scalar loss L(x_T, v_T, m_T)
+ * of the state after nsteps steps with respect to the initial x_0, v_0, m_0.
+ * The paper integrates forward only (Eqs. H, Ha-Hc); this is the transposed
+ * linearisation of exactly the forward algorithm: the kick of Eq. Hb, the
+ * drift of Eq. Hc, the Kepler drift of Eq. Ha (6x6 Jacobian of the f/g map
+ * with the implicit derivative of the universal anomaly) and, for bodies in
+ * close-encounter groups, the recorded Bulirsch-Stoer substeps (modified
+ * midpoint and Neville extrapolation) and perfect mergers. Encounter flags,
+ * groups, BS substep sizes and columns, mergers and the critical radii rc are
+ * held at their forward values (rc gets no gradient). FP64 only.
+ *
+ * Memory: the caller provides nb_adjoint_workspace_bytes() of device memory,
+ * 256-byte aligned; it holds an nb_system for the forward state, a
+ * checkpoint of the full state every checkpoint_every steps, per-step
+ * records of one segment and the BS replay scratch. The backward pass
+ * replays each segment from its checkpoint (the forward is deterministic,
+ * so the replay takes every decision of the forward again).
+ * Layout of host/device arrays as nb_init_system: x, v [n][3], m, R, rc [n].
+ * ------------------------------------------------------------------------ */
+typedef struct nb_adjoint nb_adjoint;
+
+/* Bytes of workspace for n bodies and up to nsteps steps; 0 if invalid. */
+size_t nb_adjoint_workspace_bytes(const nb_params* p, int n, int nsteps, int checkpoint_every);
+
+/* Create the handle and load the initial state (as nb_init_system; rc must
+ * be given so that the forward and its finite-difference checks keep it).
+ * p->precision must be NB_PREC_FP64. NB_E_WORKSPACE if ws is too small or
+ * misaligned; NB_E_INVALID for bad inputs. */
+int nb_adjoint_init(nb_adjoint** out, const nb_params* p, int n, const double* x,
+                    const double* v, const double* m, const double* R, const double* rc,
+                    int nsteps, int checkpoint_every, void* workspace, size_t ws_bytes,
+                    void* stream, int inputs_on_device);
+
+/* Run nsteps steps of size dt from the initial state, keeping checkpoints.
+ * May be called again; each call restarts from the initial state. Returns
+ * NB_E_OVERFLOW if nsteps exceeds the count the workspace was sized for, or
+ * the forward's status. */
+int nb_adjoint_forward(nb_adjoint* a, int nsteps, double dt);
+
+/* Final state of the forward (all n slots; absorbed bodies have m = 0,
+ * alive = 0). Any pointer may be NULL. Synchronises the stream. */
+int nb_adjoint_state(nb_adjoint* a, double* x, double* v, double* m, int* alive,
+                     int out_on_device);
+
+/* Pull back dL/dx_T, dL/dv_T [n][3] and dL/dm_T [n] to dL/dx_0, dL/dv_0
+ * [n][3] and dL/dm_0 [n]. Entries of bodies absorbed by the end are ignored
+ * (their final state is a constant). Output pointers may be NULL. Leaves the
+ * handle at the forward's final state, so backward can be called again with
+ * other cotangents. NB_E_OVERFLOW if a group needed more than 256 BS
+ * substeps or 16 mergers in one step (the records' capacity). */
+int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const double* gm,
+                        double* dx0, double* dv0, double* dm0, int on_device);
+
+const char* nb_adjoint_last_error(const nb_adjoint* a);
+void nb_adjoint_destroy(nb_adjoint* a);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnb.so")
 SOURCES = ["abi.cu", "kick.cu", "drift.cu", "encounter.cu", "energy.cu", "peaks.cu",
-           "noalloc.cu", "batch.cu"]
+           "noalloc.cu", "batch.cu", "adjoint.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("nb_internal.cuh", "bs.cuh", "kepler.cuh")] + [
     os.path.join(ROOT, "include", "nb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -14,22 +14,6 @@
 
 using namespace nb;
 
-struct nb_system {
-  Dev d;
-  Phys P;
-  nb_params prm;
-  cudaStream_t st;
-  double* out8;  // device: energy results
-  int* cnt;      // device: gather count
-  char err[256];
-  // kick timing (CUDA events on the launching stream) and launch counting
-  int timing;
-  std::vector<cudaEvent_t>* events;
-  double kick_ms;
-  long long kick_launches;
-  long long launches;
-};
-
 namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

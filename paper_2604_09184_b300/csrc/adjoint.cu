@@ -1,0 +1,955 @@
+// Discrete adjoint of the hybrid symplectic step: gradients of a loss on the
+// final state with respect to the initial positions, velocities and masses.
+//
+// The step is B(h/2) C(h/2) A(h) C(h/2) B(h/2) (Eqs. H, Ha, Hb, Hc); its
+// adjoint runs the same maps in reverse with their transposed Jacobians:
+//   B (kick, Eq. Hb):   lambda_x += J_a^T mu with mu = (h/2) lambda_v, where
+//                        J_a is the tidal tensor of the changeover-weighted
+//                        pair force, and lambda_m += (da/dm)^T mu;
+//   C (Eq. Hc):          lambda_v_i += (h/2) (m_i/m0) sum_k lambda_x_k and
+//                        lambda_m_i += (h/2) v_i . sum_k lambda_x_k / m0;
+//   A (Kepler, Eq. Ha):  per body, the transposed 6x6 Jacobian of the f/g map
+//                        (forward-mode dual numbers through the universal-
+//                        variable solve); bodies of a close-encounter group
+//                        take the adjoint of the recorded Bulirsch-Stoer
+//                        substeps: Neville extrapolation is linear in the
+//                        modified-midpoint results, each midpoint sequence is
+//                        reversed with the Jacobian of the group's equations
+//                        of motion, mergers with the Jacobian of the merge map.
+// All discrete events (flags, groups, BS substep sizes and columns, mergers)
+// and the critical radii are held at their forward values. The forward pass
+// keeps a checkpoint every `every` steps; the backward pass replays each
+// segment from its checkpoint (the forward is deterministic, so the replay
+// reproduces every decision) while recording the per-step states it needs.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "bs.cuh"
+#include "kepler.cuh"
+#include "nb_internal.cuh"
+
+namespace nb {
+
+constexpr int ANT = 256;     // threads of the O(N) and O(N^2) adjoint kernels
+constexpr int ABNT = 64;     // threads of the BS adjoint CTA
+constexpr int kSubCap = 256; // recorded BS substeps per group and step
+constexpr int kMrgCap = 16;  // recorded mergers per group and step
+
+// K, dK/dy, d2K/dy2 of the infinitely smooth switch K = f / (f + g),
+// f = exp(-1/y), g = exp(-1/(1-y)).
+__device__ void changeover_y(double y, double& K, double& K1, double& K2) {
+  if (y <= 0.0) {
+    K = 0.0; K1 = 0.0; K2 = 0.0;
+    return;
+  }
+  if (y >= 1.0) {
+    K = 1.0; K1 = 0.0; K2 = 0.0;
+    return;
+  }
+  const double u = 1.0 - y;
+  const double f = exp(-1.0 / y), g = exp(-1.0 / u);
+  const double s = f + g;
+  K = f / s;
+  const double fg = f * g;
+  if (!(fg > 0.0)) {
+    K1 = 0.0; K2 = 0.0;
+    return;
+  }
+  const double iy = 1.0 / y, iu = 1.0 / u;
+  const double A = iy * iy + iu * iu;
+  K1 = fg * A / (s * s);
+  const double sp_s = (f * iy * iy - g * iu * iu) / s;  // s' / s
+  K2 = fg / (s * s) * ((iy * iy - iu * iu) * A + (-2.0 * iy * iy * iy + 2.0 * iu * iu * iu) -
+                       2.0 * A * sp_s);
+}
+
+// Radial profile of a pair term and its derivative divided by r:
+// kick (close = 0): phi = w / r^3, w = K - r K_r (w = 1 beyond rc);
+// close force (close = 1): psi = (1 - w) / r^3 (0 beyond rc).
+__device__ void pair_profile(double r2, double rc, int close, double& p, double& dp_r) {
+  const double r = sqrt(r2);
+  const double ir = 1.0 / r;
+  const double ir3 = ir * ir * ir;
+  double w = 1.0, wp = 0.0;
+  if (r2 < rc * rc) {
+    const double L = 0.9 * rc;
+    double K, K1, K2;
+    changeover_y((r - 0.1 * rc) / L, K, K1, K2);
+    const double Kr = K1 / L, Krr = K2 / (L * L);
+    w = K - r * Kr;
+    wp = -r * Krr;
+  }
+  if (close) {
+    p = (1.0 - w) * ir3;
+    dp_r = (-wp - 3.0 * (1.0 - w) * ir) * ir3 * ir;
+  } else {
+    p = w * ir3;
+    dp_r = (wp - 3.0 * w * ir) * ir3 * ir;
+  }
+}
+
+struct Vjp {
+  const double *x, *y, *z, *m, *rc;
+  const int* alive;
+  const double *mux, *muy, *muz;  // (h/2) lambda_v
+  double *lx, *ly, *lz, *lm;      // accumulated
+  int n;
+  double G;
+};
+
+// lambda_x_k += G sum_j T_kj (m_k mu_j - m_j mu_k), T = phi I + (phi'/r) d d^T;
+// lambda_m_k += G sum_j phi mu_j . (x_k - x_j).
+__global__ void __launch_bounds__(ANT) k_kick_vjp(Vjp V) {
+  __shared__ double sx[ANT], sy[ANT], sz[ANT], sm[ANT], src[ANT], su[ANT], sv[ANT], sw[ANT];
+  __shared__ int sa[ANT];
+  const int k = blockIdx.x * ANT + threadIdx.x;
+  const bool act = k < V.n && V.alive[k];
+  const double xk = act ? V.x[k] : 0.0, yk = act ? V.y[k] : 0.0, zk = act ? V.z[k] : 0.0;
+  const double mk = act ? V.m[k] : 0.0, rck = act ? V.rc[k] : 0.0;
+  const double mxk = act ? V.mux[k] : 0.0, myk = act ? V.muy[k] : 0.0, mzk = act ? V.muz[k] : 0.0;
+  double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
+  for (int jt = 0; jt < V.n; jt += ANT) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < V.n) {
+      sx[threadIdx.x] = V.x[j]; sy[threadIdx.x] = V.y[j]; sz[threadIdx.x] = V.z[j];
+      sm[threadIdx.x] = V.m[j]; src[threadIdx.x] = V.rc[j]; sa[threadIdx.x] = V.alive[j];
+      su[threadIdx.x] = V.mux[j]; sv[threadIdx.x] = V.muy[j]; sw[threadIdx.x] = V.muz[j];
+    }
+    __syncthreads();
+    if (!act) continue;
+    const int cnt = min(ANT, V.n - jt);
+    for (int q = 0; q < cnt; ++q) {
+      if (jt + q == k || !sa[q]) continue;
+      const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
+      const double r2 = sep2(dx, dy, dz);
+      if (r2 == 0.0) continue;
+      double p, dp_r;
+      pair_profile(r2, fmax(rck, src[q]), 0, p, dp_r);
+      const double ux = mk * su[q] - sm[q] * mxk, uy = mk * sv[q] - sm[q] * myk,
+                   uz = mk * sw[q] - sm[q] * mzk;
+      const double du = dx * ux + dy * uy + dz * uz;
+      ax += p * ux + dp_r * du * dx;
+      ay += p * uy + dp_r * du * dy;
+      az += p * uz + dp_r * du * dz;
+      am -= p * (su[q] * dx + sv[q] * dy + sw[q] * dz);
+    }
+  }
+  if (act) {
+    V.lx[k] += V.G * ax;
+    V.ly[k] += V.G * ay;
+    V.lz[k] += V.G * az;
+    V.lm[k] += V.G * am;
+  }
+}
+
+// Per-block sums of lambda_x over the bodies with alive != 0 (fixed order).
+__global__ void __launch_bounds__(ANT) k_sum3(int n, const int* alive, const double* a,
+                                             const double* b, const double* c, double* parts) {
+  __shared__ double red[3 * 32 + 3];
+  const int i = blockIdx.x * ANT + threadIdx.x;
+  double x = 0.0, y = 0.0, z = 0.0;
+  if (i < n && alive[i]) {
+    x = a[i]; y = b[i]; z = c[i];
+  }
+  block_sum3(x, y, z, red);
+  if (threadIdx.x == 0) {
+    parts[3 * blockIdx.x] = x;
+    parts[3 * blockIdx.x + 1] = y;
+    parts[3 * blockIdx.x + 2] = z;
+  }
+}
+
+// Adjoint of C(h/2): x' = x + (h/2) P / m0 with P = sum m v.
+__global__ void __launch_bounds__(ANT) k_cdrift_vjp(int n, int nparts, const double* parts,
+                                                   const int* alive, const double* m,
+                                                   const double* vx, const double* vy,
+                                                   const double* vz, double hh, double m0,
+                                                   double* lvx, double* lvy, double* lvz,
+                                                   double* lm) {
+  __shared__ double red[3 * 32 + 3];
+  double S[3];
+  reduce_parts3(parts, nparts, red, S);
+  const int i = blockIdx.x * ANT + threadIdx.x;
+  if (i >= n || !alive[i]) return;
+  const double c = hh * m[i] / m0;
+  lvx[i] += c * S[0];
+  lvy[i] += c * S[1];
+  lvz[i] += c * S[2];
+  lm[i] += hh * (vx[i] * S[0] + vy[i] * S[1] + vz[i] * S[2]) / m0;
+}
+
+// Transposed Jacobian of the Kepler drift for bodies outside the step's groups.
+__global__ void __launch_bounds__(ANT) k_kepler_vjp(int n, const double* xs6, const int* alive,
+                                                   const int* ingrp, double mu, double h,
+                                                   int max_iter, double* lx, double* ly,
+                                                   double* lz, double* lvx, double* lvy,
+                                                   double* lvz, int* status) {
+  const int i = blockIdx.x * ANT + threadIdx.x;
+  if (i >= n || !alive[i] || ingrp[i]) return;
+  Dual6 q[6];
+  for (int a = 0; a < 6; ++a) {
+    q[a] = mkd(xs6[(size_t)a * n + i]);
+    q[a].d[a] = 1.0;
+  }
+  int it;
+  if (kepler_drift(mu, q[0], q[1], q[2], q[3], q[4], q[5], h, max_iter, &it)) {
+    atomicCAS(status, 0, NB_E_NOCONV);
+    return;
+  }
+  const double lo[6] = {lx[i], ly[i], lz[i], lvx[i], lvy[i], lvz[i]};
+  double li[6];
+  for (int b = 0; b < 6; ++b) {
+    double s = 0.0;
+    for (int a = 0; a < 6; ++a) s += lo[a] * q[a].d[b];
+    li[b] = s;
+  }
+  lx[i] = li[0]; ly[i] = li[1]; lz[i] = li[2];
+  lvx[i] = li[3]; lvy[i] = li[4]; lvz[i] = li[5];
+}
+
+// ---------------------------------------------------------------------------
+// Bulirsch-Stoer adjoint: one CTA per group.
+// ---------------------------------------------------------------------------
+// Per-member-slot scratch (doubles): recorded substep starts (kSubCap x
+// (6 + 4)), midpoint states z[0..2 kmax] (6 each) and their adjoints, the
+// running adjoint (6 state + 1 mass), an accumulator (6) and a derivative
+// buffer (6).
+__host__ __device__ inline int adj_slot_stride(int kmax) {
+  return kSubCap * 10 + 2 * (2 * kmax + 1) * 6 + 6 + 1 + 6 + 6;
+}
+
+struct AdjGroupArgs {
+  int n, kmax, bs_stride, slot_stride;
+  const int* grp;  // [0] ngroups [1] nmembers [2..] off[ng+1] then members
+  const double* xs6;
+  const double *m0, *R0, *rc0;
+  double* lx[3];
+  double* lv[3];
+  double* lm;
+  double* gscr;
+  double* gnew;
+  double* slot;    // n * slot_stride
+  double* H;       // n * kSubCap
+  int* kk;         // n * kSubCap
+  int* counts;     // n * 4
+  int* mrg;        // n * kMrgCap * 3
+  double* mst;     // n * kMrgCap * 14
+  int* status;
+};
+
+// d/dt of z (all members) -> accumulate J^T w into out (6 per member),
+// J the Jacobian of (x, v) -> (v, a(x)) of the group (Eq. Ha restricted to
+// the group), w = (w_x, w_v); mass terms into lm_acc. Uses the members'
+// masses, critical radii and alive flags in the BsCtx working copies.
+__device__ void bs_vjp_f(const BsCtx& c, const double* z, const double* w, double* out,
+                         double* lm_acc, double scale) {
+  for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
+    if (!bs_alive(c, b)) continue;
+    const double* zb = z + 6 * b;
+    const double* wb = w + 6 * b;
+    double o[3] = {0.0, 0.0, 0.0};
+    // Kepler part: -mu (I / r^3 - 3 x x^T / r^5) w_v
+    const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
+    const double r = sqrt(r2);
+    const double ir3 = 1.0 / (r2 * r);
+    const double xw = zb[0] * wb[3] + zb[1] * wb[4] + zb[2] * wb[5];
+    for (int k = 0; k < 3; ++k) o[k] = -c.mu * (wb[3 + k] * ir3 - 3.0 * zb[k] * xw * ir3 / r2);
+    double am = 0.0;
+    const double mb = c.g[10 * b + 6], rcb = c.g[10 * b + 8];
+    for (int q = 0; q < c.M; ++q) {
+      if (q == b || !bs_alive(c, q)) continue;
+      const double* zq = z + 6 * q;
+      const double* wq = w + 6 * q;
+      const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
+      const double q2 = sep2(dx, dy, dz);
+      const double rc = fmax(rcb, c.g[10 * q + 8]);
+      if (q2 == 0.0 || !(q2 < rc * rc)) continue;
+      double p, dp_r;
+      pair_profile(q2, rc, 1, p, dp_r);
+      const double mq = c.g[10 * q + 6];
+      const double ux = mb * wq[3] - mq * wb[3], uy = mb * wq[4] - mq * wb[4],
+                   uz = mb * wq[5] - mq * wb[5];
+      const double du = dx * ux + dy * uy + dz * uz;
+      o[0] += c.G * (p * ux + dp_r * du * dx);
+      o[1] += c.G * (p * uy + dp_r * du * dy);
+      o[2] += c.G * (p * uz + dp_r * du * dz);
+      am -= c.G * p * (wq[3] * dx + wq[4] * dy + wq[5] * dz);
+    }
+    double* ob = out + 6 * b;
+    for (int k = 0; k < 3; ++k) {
+      ob[k] += scale * o[k];
+      ob[3 + k] += scale * wb[k];
+    }
+    lm_acc[b] += scale * am;
+  }
+}
+
+__device__ void bs_f(const BsCtx& c, const double* z, double* f) {
+  for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
+    double* fb = f + 6 * b;
+    if (!bs_alive(c, b)) {
+      for (int k = 0; k < 6; ++k) fb[k] = 0.0;
+      continue;
+    }
+    const double* zb = z + 6 * b;
+    fb[0] = zb[3]; fb[1] = zb[4]; fb[2] = zb[5];
+    const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
+    const double r = sqrt(r2);
+    const double ks = -c.mu / (r2 * r);
+    double ax = ks * zb[0], ay = ks * zb[1], az = ks * zb[2];
+    for (int q = 0; q < c.M; ++q) {
+      if (q == b || !bs_alive(c, q)) continue;
+      const double* zq = z + 6 * q;
+      const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
+      const double q2 = sep2(dx, dy, dz);
+      const double rc = fmax(c.g[10 * b + 8], c.g[10 * q + 8]);
+      if (q2 == 0.0 || !(q2 < rc * rc)) continue;
+      double p, dp_r;
+      pair_profile(q2, rc, 1, p, dp_r);
+      const double f = c.G * c.g[10 * q + 6] * p;
+      ax += f * dx; ay += f * dy; az += f * dz;
+    }
+    fb[3] = ax; fb[4] = ay; fb[5] = az;
+  }
+}
+
+__global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
+  __shared__ double s_red[ABNT];
+  __shared__ int s_flags[2];
+  __shared__ double cw[kMaxBsK + 2];
+  __shared__ double Tn[kMaxBsK + 2][kMaxBsK + 2];
+  const int ng = A.grp[0];
+  const int* goff = A.grp + 2;
+  const int* gmem = A.grp + 2 + ng + 1;
+  const int n = A.n;
+  for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+    const int off = goff[grp];
+    BsCtx c;
+    c.M = goff[grp + 1] - off;
+    c.stride = A.bs_stride;
+    c.base = A.gscr + (size_t)off * A.bs_stride;
+    c.g = A.gnew + (size_t)off * 10;
+    c.kmax = A.kmax;
+    c.G = P.G;
+    c.mu = P.mu;
+    const int M = c.M;
+    double* slot = A.slot + (size_t)off * A.slot_stride;  // the group's contiguous slot block
+    // slot block layout (M members together): rec ys | ms | Rs | rcs | alv | z | lz | ly | lm | lin
+    double* r_ys = slot;
+    double* r_ms = r_ys + (size_t)kSubCap * M * 6;
+    double* r_Rs = r_ms + (size_t)kSubCap * M;
+    double* r_rcs = r_Rs + (size_t)kSubCap * M;
+    double* r_alv = r_rcs + (size_t)kSubCap * M;
+    double* zb = r_alv + (size_t)kSubCap * M;           // (2kmax+1) * 6M
+    double* lzb = zb + (size_t)(2 * A.kmax + 1) * 6 * M;  // (2kmax+1) * 6M
+    double* ly = lzb + (size_t)(2 * A.kmax + 1) * 6 * M;  // 6M
+    double* lmv = ly + 6 * M;                             // M
+    double* lin = lmv + M;                                // 6M
+    double* ftmp = lin + 6 * M;                           // 6M (derivative scratch)
+    BsRec rec;
+    rec.cap = kSubCap;
+    rec.mcap = kMrgCap;
+    rec.counts = A.counts + 4 * (size_t)grp;
+    rec.H = A.H + (size_t)grp * kSubCap;
+    rec.k = A.kk + (size_t)grp * kSubCap;
+    rec.ys = r_ys; rec.ms = r_ms; rec.Rs = r_Rs; rec.rcs = r_rcs; rec.alv = r_alv;
+    rec.mrg = A.mrg + (size_t)grp * kMrgCap * 3;
+    rec.mst = A.mst + (size_t)grp * kMrgCap * 14;
+    // forward replay from the saved state, recording the accepted substeps
+    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+      const int body = gmem[off + b];
+      double* y = c.base + (size_t)b * c.stride + OY;
+      for (int k = 0; k < 6; ++k) y[k] = A.xs6[(size_t)k * n + body];
+      double* g = c.g + 10 * b;
+      g[6] = A.m0[body]; g[7] = A.R0[body]; g[8] = A.rc0[body]; g[9] = 1.0;
+      bs_set_aux(c, b, P.G, g[6], g[8]);
+    }
+    if (threadIdx.x == 0) {
+      rec.counts[0] = 0; rec.counts[1] = 0; rec.counts[2] = 0;
+    }
+    __syncthreads();
+    BsTally tally{0, 0, 0, 0};
+    double El = 0.0;
+    int st = bs_integrate_group(c, P, h, s_red, s_flags, tally, &El, &rec);
+    __syncthreads();
+    if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
+    if (st) {
+      if (threadIdx.x == 0) atomicCAS(A.status, 0, st);
+      continue;
+    }
+    const int nsub = rec.counts[0], nmrg = rec.counts[1];
+    // adjoint at the end of the BS: members alive at the end take the step's
+    // lambda; absorbed members start from zero
+    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+      const int body = gmem[off + b];
+      const bool live = c.g[10 * b + 9] != 0.0;
+      for (int k = 0; k < 3; ++k) {
+        ly[6 * b + k] = live ? A.lx[k][body] : 0.0;
+        ly[6 * b + 3 + k] = live ? A.lv[k][body] : 0.0;
+      }
+      lmv[b] = live ? A.lm[body] : 0.0;
+    }
+    __syncthreads();
+    int mq = nmrg - 1;
+    for (int s = nsub - 1; s >= 0; --s) {
+      // undo the mergers that followed substep s (last first)
+      for (; mq >= 0 && rec.mrg[3 * mq] == s; --mq) {
+        if (threadIdx.x == 0) {
+          const int a = rec.mrg[3 * mq + 1], b = rec.mrg[3 * mq + 2];
+          const double* ya = rec.mst + 14 * mq;
+          const double* yb = ya + 6;
+          const double ma = ya[12], mb = ya[13], Mt = ma + mb;
+          double lyn[6], dot_a = 0.0, dot_b = 0.0;
+          for (int k = 0; k < 6; ++k) {
+            lyn[k] = ly[6 * a + k];
+            const double yn = (ma * ya[k] + mb * yb[k]) / Mt;
+            dot_a += lyn[k] * (ya[k] - yn) / Mt;
+            dot_b += lyn[k] * (yb[k] - yn) / Mt;
+          }
+          const double lM = lmv[a];
+          for (int k = 0; k < 6; ++k) {
+            ly[6 * a + k] = (ma / Mt) * lyn[k];
+            ly[6 * b + k] = (mb / Mt) * lyn[k];
+          }
+          lmv[a] = lM + dot_a;
+          lmv[b] = lM + dot_b;
+        }
+        __syncthreads();
+      }
+      // working copies of masses, radii, critical radii and flags at the
+      // substep's start
+      for (int b = threadIdx.x; b < M; b += blockDim.x) {
+        const size_t o = (size_t)s * M + b;
+        double* g = c.g + 10 * b;
+        g[6] = r_ms[o]; g[7] = r_Rs[o]; g[8] = r_rcs[o]; g[9] = r_alv[o];
+        for (int k = 0; k < 6; ++k) lin[6 * b + k] = 0.0;
+      }
+      const int kacc = rec.k[s];
+      const double H = rec.H[s];
+      if (threadIdx.x == 0) {
+        // extrapolation weights: T_kk = sum_j cw[j] T_j1 (Neville is linear)
+        for (int j0 = 1; j0 <= kacc; ++j0) {
+          for (int j = 1; j <= kacc; ++j) {
+            Tn[j][1] = (j == j0) ? 1.0 : 0.0;
+            for (int q = 1; q < j; ++q) {
+              const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+              Tn[j][q + 1] = Tn[j][q] + (Tn[j][q] - Tn[j - 1][q]) * inv;
+            }
+          }
+          cw[j0] = Tn[kacc][kacc];
+        }
+      }
+      __syncthreads();
+      for (int j = 1; j <= kacc; ++j) {
+        const int nsb = 2 * j;
+        const double hs = H / nsb;
+        // replay the midpoint sequence from the substep's start
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int k = 0; k < 6; ++k) zb[6 * b + k] = r_ys[((size_t)s * M + b) * 6 + k];
+        __syncthreads();
+        bs_f(c, zb, ftmp);
+        __syncthreads();
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int k = 0; k < 6; ++k) zb[6 * M + 6 * b + k] = zb[6 * b + k] + hs * ftmp[6 * b + k];
+        __syncthreads();
+        for (int mm = 1; mm < nsb; ++mm) {
+          bs_f(c, zb + (size_t)mm * 6 * M, ftmp);
+          __syncthreads();
+          for (int b = threadIdx.x; b < M; b += blockDim.x)
+            for (int k = 0; k < 6; ++k)
+              zb[(size_t)(mm + 1) * 6 * M + 6 * b + k] =
+                  zb[(size_t)(mm - 1) * 6 * M + 6 * b + k] + 2.0 * hs * ftmp[6 * b + k];
+          __syncthreads();
+        }
+        // reverse: out = (z_n + z_{n-1} + hs f(z_n)) / 2, weighted by cw[j]
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int m2 = 0; m2 <= nsb; ++m2)
+            for (int k = 0; k < 6; ++k) lzb[(size_t)m2 * 6 * M + 6 * b + k] = 0.0;
+        __syncthreads();
+        const double wj = cw[j];
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int k = 0; k < 6; ++k) {
+            const double lo = wj * ly[6 * b + k];
+            lzb[(size_t)nsb * 6 * M + 6 * b + k] += 0.5 * lo;
+            lzb[(size_t)(nsb - 1) * 6 * M + 6 * b + k] += 0.5 * lo;
+            ftmp[6 * b + k] = lo;  // w for the f-term
+          }
+        __syncthreads();
+        bs_vjp_f(c, zb + (size_t)nsb * 6 * M, ftmp, lzb + (size_t)nsb * 6 * M, lmv, 0.5 * hs);
+        __syncthreads();
+        for (int mm = nsb - 1; mm >= 1; --mm) {
+          // z_{mm+1} = z_{mm-1} + 2 hs f(z_mm)
+          double* lnext = lzb + (size_t)(mm + 1) * 6 * M;
+          for (int b = threadIdx.x; b < M; b += blockDim.x)
+            for (int k = 0; k < 6; ++k) lzb[(size_t)(mm - 1) * 6 * M + 6 * b + k] += lnext[6 * b + k];
+          __syncthreads();
+          bs_vjp_f(c, zb + (size_t)mm * 6 * M, lnext, lzb + (size_t)mm * 6 * M, lmv, 2.0 * hs);
+          __syncthreads();
+        }
+        // z_1 = z_0 + hs f(z_0)
+        double* l1 = lzb + 6 * (size_t)M;
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int k = 0; k < 6; ++k) lzb[6 * b + k] += l1[6 * b + k];
+        __syncthreads();
+        bs_vjp_f(c, zb, l1, lzb, lmv, hs);
+        __syncthreads();
+        for (int b = threadIdx.x; b < M; b += blockDim.x)
+          for (int k = 0; k < 6; ++k) lin[6 * b + k] += lzb[6 * b + k];
+        __syncthreads();
+      }
+      for (int b = threadIdx.x; b < M; b += blockDim.x)
+        for (int k = 0; k < 6; ++k) ly[6 * b + k] = lin[6 * b + k];
+      __syncthreads();
+    }
+    // lambda at the saved state of the members
+    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+      const int body = gmem[off + b];
+      for (int k = 0; k < 3; ++k) {
+        A.lx[k][body] = ly[6 * b + k];
+        A.lv[k][body] = ly[6 * b + 3 + k];
+      }
+      A.lm[body] = lmv[b];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Recording of one step of the replay.
+// ---------------------------------------------------------------------------
+struct StepRec {
+  double* xs6;    // 6n saved state (after C(h/2)): x y z vx vy vz
+  double* st0;    // 4n at the saved point: m, R, rc, (alive as double)
+  double* x26;    // 6n after A (before the closing C(h/2))
+  double* st1;    // 3n after A: m, rc, (alive as double)
+  int* ingrp;     // n
+  int* grp;       // 2 + (n + 1) + n: ngroups, nmembers, offsets, members
+};
+
+__global__ void k_rec_saved(Dev d, StepRec r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = d.n;
+  if (i >= n) return;
+  r.xs6[i] = d.xs[i]; r.xs6[n + i] = d.ys[i]; r.xs6[2 * n + i] = d.zs[i];
+  r.xs6[3 * n + i] = d.vxs[i]; r.xs6[4 * n + i] = d.vys[i]; r.xs6[5 * n + i] = d.vzs[i];
+  r.st0[i] = d.m[i]; r.st0[n + i] = d.R[i]; r.st0[2 * n + i] = d.rc[i];
+  r.st0[3 * n + i] = d.alive[i] ? 1.0 : 0.0;
+}
+
+__global__ void k_rec_after(Dev d, StepRec r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = d.n;
+  const int ng = d.ctrl->n_groups, nm = ng > 0 ? d.ctrl->n_members : 0;
+  if (i == 0) {
+    r.grp[0] = ng;
+    r.grp[1] = nm;
+  }
+  if (i <= ng) r.grp[2 + i] = ng > 0 ? d.grp_off[i] : 0;
+  if (i < nm) r.grp[2 + ng + 1 + i] = d.grp_mem[i];
+  if (i >= n) return;
+  r.x26[i] = d.x[i]; r.x26[n + i] = d.y[i]; r.x26[2 * n + i] = d.z[i];
+  r.x26[3 * n + i] = d.vx[i]; r.x26[4 * n + i] = d.vy[i]; r.x26[5 * n + i] = d.vz[i];
+  r.st1[i] = d.m[i]; r.st1[n + i] = d.rc[i]; r.st1[2 * n + i] = d.alive[i] ? 1.0 : 0.0;
+  r.ingrp[i] = (ng > 0 && d.member_slot[i] >= 0) ? 1 : 0;
+}
+
+__global__ void k_alive_from(int n, const double* a, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] != 0.0 ? 1 : 0;
+}
+
+__global__ void k_scale3(int n, double s, const double* a, const double* b, const double* c,
+                         double* oa, double* ob, double* oc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  oa[i] = s * a[i];
+  ob[i] = s * b[i];
+  oc[i] = s * c[i];
+}
+
+__global__ void k_aos_to_soa(int n, const double* a3, double* x, double* y, double* z, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (add) {
+    x[i] += a3[3 * i]; y[i] += a3[3 * i + 1]; z[i] += a3[3 * i + 2];
+  } else {
+    x[i] = a3[3 * i]; y[i] = a3[3 * i + 1]; z[i] = a3[3 * i + 2];
+  }
+}
+
+__global__ void k_soa_to_aos(int n, const double* x, const double* y, const double* z, double* a3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  a3[3 * i] = x[i]; a3[3 * i + 1] = y[i]; a3[3 * i + 2] = z[i];
+}
+
+__global__ void k_mask(int n, const int* alive, double* a, double* b, double* c, double* d2,
+                       double* e, double* f, double* g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || alive[i]) return;
+  a[i] = b[i] = c[i] = d2[i] = e[i] = f[i] = g[i] = 0.0;
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+struct nb_adjoint {
+  nb_system* sys;
+  cudaStream_t st;
+  int n, every, max_ckpt, nsteps_done;
+  double dt;
+  // checkpoints: per checkpoint 13n doubles, n alive ints, fprev pairs, ctrl
+  double* ck_d;
+  int* ck_i;
+  Ctrl* ck_c;
+  int n_ckpt;
+  // step records of one segment
+  StepRec* recs;  // host array of device pointers
+  int rec_cap;
+  // adjoint vectors and scratch
+  double *lx, *ly, *lz, *lvx, *lvy, *lvz, *lm, *mux, *muy, *muz, *parts;
+  int* alive0;
+  int* alive1;
+  int* status;
+  double *gscr, *gnew, *slot, *H, *mst;
+  int *kk, *counts, *mrg;
+  int slot_stride;
+  char err[256];
+};
+
+namespace {
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct ACarver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    off = al256(off);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int kmax_of(const nb_params& p) {
+  return p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
+}
+
+size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, nb_adjoint* a) {
+  const size_t sys_bytes = nb_workspace_bytes(&p, n);
+  ACarver c{base, 0};
+  char* sysws = c.take<char>(sys_bytes);
+  const int nck = nsteps / every + 2;
+  int pair_cap = 1;
+  {
+    const int cap = p.pair_capacity > 0 ? p.pair_capacity : (4 * n > 4096 ? 4 * n : 4096);
+    while (pair_cap < cap) pair_cap <<= 1;
+  }
+  double* ck_d = c.take<double>((size_t)nck * 13 * n);
+  int* ck_i = c.take<int>((size_t)nck * (n + 2 * (size_t)pair_cap));
+  Ctrl* ck_c = c.take<Ctrl>(nck);
+  const int kmax = kmax_of(p);
+  const int stride = adj_slot_stride(kmax);
+  std::vector<StepRec> recs(every);
+  for (int t = 0; t < every; ++t) {
+    recs[t].xs6 = c.take<double>(6 * (size_t)n);
+    recs[t].st0 = c.take<double>(4 * (size_t)n);
+    recs[t].x26 = c.take<double>(6 * (size_t)n);
+    recs[t].st1 = c.take<double>(3 * (size_t)n);
+    recs[t].ingrp = c.take<int>(n);
+    recs[t].grp = c.take<int>(2 * (size_t)n + 3);
+  }
+  double* vec = c.take<double>(10 * (size_t)n);
+  const int nparts = (n + ANT - 1) / ANT;
+  double* parts = c.take<double>(3 * (size_t)nparts);
+  int* alive0 = c.take<int>(n);
+  int* alive1 = c.take<int>(n);
+  int* status = c.take<int>(4);
+  double* gscr = c.take<double>((size_t)n * (6 * (4 + 2 * kmax) + 4));
+  double* gnew = c.take<double>((size_t)n * 10);
+  double* slot = c.take<double>((size_t)n * stride);
+  double* H = c.take<double>((size_t)n * kSubCap);
+  int* kk = c.take<int>((size_t)n * kSubCap);
+  int* counts = c.take<int>((size_t)n * 4);
+  int* mrg = c.take<int>((size_t)n * kMrgCap * 3);
+  double* mst = c.take<double>((size_t)n * kMrgCap * 14);
+  if (a && base) {
+    a->sys = (nb_system*)sysws;  // placeholder; replaced by the real handle in init
+    a->ck_d = ck_d; a->ck_i = ck_i; a->ck_c = ck_c;
+    a->max_ckpt = nck;
+    a->rec_cap = every;
+    a->recs = (StepRec*)malloc(sizeof(StepRec) * every);
+    for (int t = 0; t < every; ++t) a->recs[t] = recs[t];
+    a->lx = vec; a->ly = vec + n; a->lz = vec + 2 * n;
+    a->lvx = vec + 3 * n; a->lvy = vec + 4 * n; a->lvz = vec + 5 * n;
+    a->lm = vec + 6 * n; a->mux = vec + 7 * n; a->muy = vec + 8 * n; a->muz = vec + 9 * n;
+    a->parts = parts; a->alive0 = alive0; a->alive1 = alive1; a->status = status;
+    a->gscr = gscr; a->gnew = gnew; a->slot = slot; a->H = H; a->kk = kk;
+    a->counts = counts; a->mrg = mrg; a->mst = mst; a->slot_stride = stride;
+  }
+  (void)sysws;
+  return al256(c.off);
+}
+
+#define NB_ACU(call)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      snprintf(a->err, sizeof(a->err), "%s: %s", #call, cudaGetErrorString(e_));        \
+      return NB_E_CUDA;                                                                 \
+    }                                                                                   \
+  } while (0)
+
+// Copy the system's full state to (dir 0) or from (dir 1) checkpoint k.
+int checkpoint(nb_adjoint* a, int k, int dir) {
+  const Dev& d = a->sys->d;
+  const int n = d.n;
+  double* arr[] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.R, d.rc, d.rc2, d.ax, d.ay, d.az};
+  double* cd = a->ck_d + (size_t)k * 13 * n;
+  int* ci = a->ck_i + (size_t)k * (n + 2 * (size_t)d.pair_cap);
+  const cudaMemcpyKind K = cudaMemcpyDeviceToDevice;
+  for (int q = 0; q < 13; ++q)
+    NB_ACU(cudaMemcpyAsync(dir ? arr[q] : cd + (size_t)q * n, dir ? cd + (size_t)q * n : arr[q],
+                           sizeof(double) * n, K, a->st));
+  NB_ACU(cudaMemcpyAsync(dir ? d.alive : ci, dir ? ci : d.alive, sizeof(int) * n, K, a->st));
+  NB_ACU(cudaMemcpyAsync(dir ? (void*)d.fprev : (void*)(ci + n), dir ? (void*)(ci + n) : (void*)d.fprev,
+                         sizeof(int2) * d.pair_cap, K, a->st));
+  NB_ACU(cudaMemcpyAsync(dir ? d.ctrl : a->ck_c + k, dir ? a->ck_c + k : d.ctrl, sizeof(Ctrl), K, a->st));
+  if (dir) {
+    NB_ACU(cudaMemsetAsync(d.member_slot, 0xff, sizeof(int) * n, a->st));
+    // forget the previous step's members (their slots were just cleared)
+    NB_ACU(cudaMemsetAsync(&d.ctrl->n_prev_members, 0, sizeof(int), a->st));
+  }
+  return NB_OK;
+}
+
+// One step of the replay with the recording kernels around the BS phase
+// (the same kernels as nb_step(1)).
+void replay_step(nb_adjoint* a, double dt, const StepRec& r) {
+  nb_system* s = a->sys;
+  const Dev& d = s->d;
+  const int g = (d.n + 255) / 256;
+  launch_open_h(d, dt, a->st);
+  launch_drift_h(d, s->P, dt, a->st);
+  k_rec_saved<<<g, 256, 0, a->st>>>(d, r);
+  launch_kick(d, s->P, 0, a->st);
+  launch_encounter(d, s->P, a->st);
+  launch_bs(d, s->P, dt, a->st);
+  launch_finish(d, s->P, 1, a->st);
+  launch_scatter(d, s->P, a->st);
+  launch_member_kick(d, s->P, a->st);
+  k_rec_after<<<g + 1, 256, 0, a->st>>>(d, r);
+  launch_close_h(d, s->P, dt, 1, a->st);
+}
+
+void kick_vjp(nb_adjoint* a, const double* x6, const double* m, const double* rc,
+              const int* alive, double hh) {
+  const int n = a->n;
+  const int g = (n + ANT - 1) / ANT;
+  k_scale3<<<g, ANT, 0, a->st>>>(n, hh, a->lvx, a->lvy, a->lvz, a->mux, a->muy, a->muz);
+  Vjp V;
+  V.x = x6; V.y = x6 + n; V.z = x6 + 2 * n; V.m = m; V.rc = rc; V.alive = alive;
+  V.mux = a->mux; V.muy = a->muy; V.muz = a->muz;
+  V.lx = a->lx; V.ly = a->ly; V.lz = a->lz; V.lm = a->lm;
+  V.n = n;
+  V.G = a->sys->P.G;
+  k_kick_vjp<<<g, ANT, 0, a->st>>>(V);
+}
+
+void cdrift_vjp(nb_adjoint* a, const int* alive, const double* m, const double* v6, double hh) {
+  const int n = a->n;
+  const int g = (n + ANT - 1) / ANT;
+  k_sum3<<<g, ANT, 0, a->st>>>(n, alive, a->lx, a->ly, a->lz, a->parts);
+  k_cdrift_vjp<<<g, ANT, 0, a->st>>>(n, g, a->parts, alive, m, v6 + 3 * n, v6 + 4 * n,
+                                     v6 + 5 * n, hh, a->sys->P.m0, a->lvx, a->lvy, a->lvz,
+                                     a->lm);
+}
+
+void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
+  const int n = a->n;
+  const int g = (n + ANT - 1) / ANT;
+  const double hh = 0.5 * dt;
+  k_alive_from<<<g, ANT, 0, a->st>>>(n, r.st1 + 2 * n, a->alive1);
+  k_alive_from<<<g, ANT, 0, a->st>>>(n, r.st0 + 3 * n, a->alive0);
+  // closing B(h/2) at the final positions, then the closing C(h/2)
+  kick_vjp(a, r.x26, r.st1, r.st1 + n, a->alive1, hh);
+  cdrift_vjp(a, a->alive1, r.st1, r.x26, hh);
+  // A(h): Kepler outside the groups, Bulirsch-Stoer inside
+  const Phys& P = a->sys->P;
+  k_kepler_vjp<<<g, ANT, 0, a->st>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
+                                     a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
+  AdjGroupArgs A;
+  A.n = n;
+  A.kmax = P.bs_kmax;
+  A.bs_stride = 6 * (4 + 2 * P.bs_kmax) + 4;
+  A.slot_stride = a->slot_stride;
+  A.grp = r.grp;
+  A.xs6 = r.xs6;
+  A.m0 = r.st0; A.R0 = r.st0 + n; A.rc0 = r.st0 + 2 * n;
+  A.lx[0] = a->lx; A.lx[1] = a->ly; A.lx[2] = a->lz;
+  A.lv[0] = a->lvx; A.lv[1] = a->lvy; A.lv[2] = a->lvz;
+  A.lm = a->lm;
+  A.gscr = a->gscr; A.gnew = a->gnew; A.slot = a->slot; A.H = a->H; A.kk = a->kk;
+  A.counts = a->counts; A.mrg = a->mrg; A.mst = a->mst; A.status = a->status;
+  int grid = n < 2 * 148 ? n : 2 * 148;
+  k_bs_adjoint<<<grid, ABNT, 0, a->st>>>(A, P, dt);
+  // opening C(h/2), then the opening B(h/2) at the step's start positions
+  cdrift_vjp(a, a->alive0, r.st0, r.xs6, hh);
+  kick_vjp(a, r.xs6, r.st0, r.st0 + 2 * n, a->alive0, hh);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nb_adjoint_workspace_bytes(const nb_params* p, int n, int nsteps, int checkpoint_every) {
+  if (!p || n < 1 || nsteps < 1 || checkpoint_every < 1 || nb_workspace_bytes(p, n) == 0)
+    return 0;
+  return adj_layout(*p, n, nsteps, checkpoint_every, nullptr, nullptr);
+}
+
+int nb_adjoint_init(nb_adjoint** out, const nb_params* p, int n, const double* x,
+                    const double* v, const double* m, const double* R, const double* rc,
+                    int nsteps, int checkpoint_every, void* workspace, size_t ws_bytes,
+                    void* stream, int inputs_on_device) {
+  if (!out || !rc) return NB_E_INVALID;
+  *out = nullptr;
+  if (p && p->precision != NB_PREC_FP64) return NB_E_INVALID;
+  const size_t need = nb_adjoint_workspace_bytes(p, n, nsteps, checkpoint_every);
+  if (need == 0) return NB_E_INVALID;
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return NB_E_WORKSPACE;
+  nb_adjoint* a = (nb_adjoint*)calloc(1, sizeof(nb_adjoint));
+  if (!a) return NB_E_INVALID;
+  adj_layout(*p, n, nsteps, checkpoint_every, (char*)workspace, a);
+  a->n = n;
+  a->every = checkpoint_every;
+  a->st = (cudaStream_t)stream;
+  nb_system* s = nullptr;
+  const int rc0 = nb_init_system(&s, p, n, x, v, m, R, rc, nullptr, workspace,
+                                 nb_workspace_bytes(p, n), stream, inputs_on_device);
+  if (rc0 != NB_OK) {
+    free(a->recs);
+    free(a);
+    return rc0;
+  }
+  a->sys = s;
+  *out = a;
+  return NB_OK;
+}
+
+int nb_adjoint_forward(nb_adjoint* a, int nsteps, double dt) {
+  if (!a || nsteps < 1 || !std::isfinite(dt)) return NB_E_INVALID;
+  // segments plus one slot for the final state
+  const int nseg = (nsteps + a->every - 1) / a->every;
+  if (nseg + 1 > a->max_ckpt) return NB_E_OVERFLOW;
+  if (a->n_ckpt > 0) {  // back to the initial state of an earlier call
+    const int rc = checkpoint(a, 0, 1);
+    if (rc) return rc;
+  }
+  a->dt = dt;
+  a->n_ckpt = 0;
+  a->nsteps_done = 0;
+  for (int done = 0; done < nsteps;) {
+    int rc = checkpoint(a, a->n_ckpt++, 0);
+    if (rc) return rc;
+    const int k = nsteps - done < a->every ? nsteps - done : a->every;
+    rc = nb_step(a->sys, k, dt);
+    if (rc) {
+      snprintf(a->err, sizeof(a->err), "forward: %s", nb_last_error(a->sys));
+      return rc;
+    }
+    done += k;
+  }
+  const int rc = checkpoint(a, a->n_ckpt, 0);  // final state
+  if (rc) return rc;
+  a->nsteps_done = nsteps;
+  return NB_OK;
+}
+
+int nb_adjoint_state(nb_adjoint* a, double* x, double* v, double* m, int* alive,
+                     int out_on_device) {
+  if (!a) return NB_E_INVALID;
+  const Dev& d = a->sys->d;
+  const int n = d.n;
+  double* tmp = d.snap;
+  const int g = (n + 255) / 256;
+  const cudaMemcpyKind K = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (x) {
+    k_soa_to_aos<<<g, 256, 0, a->st>>>(n, d.x, d.y, d.z, tmp);
+    NB_ACU(cudaMemcpyAsync(x, tmp, sizeof(double) * 3 * n, K, a->st));
+  }
+  if (v) {
+    k_soa_to_aos<<<g, 256, 0, a->st>>>(n, d.vx, d.vy, d.vz, tmp + 3 * n);
+    NB_ACU(cudaMemcpyAsync(v, tmp + 3 * n, sizeof(double) * 3 * n, K, a->st));
+  }
+  if (m) NB_ACU(cudaMemcpyAsync(m, d.m, sizeof(double) * n, K, a->st));
+  if (alive) NB_ACU(cudaMemcpyAsync(alive, d.alive, sizeof(int) * n, K, a->st));
+  NB_ACU(cudaStreamSynchronize(a->st));
+  return NB_OK;
+}
+
+int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const double* gm,
+                        double* dx0, double* dv0, double* dm0, int on_device) {
+  if (!a || !gx || !gv || !gm || a->nsteps_done < 1) return NB_E_INVALID;
+  const int n = a->n;
+  const int g = (n + 255) / 256;
+  const Dev& d = a->sys->d;
+  double* tmp = d.snap;  // staging (16 n doubles)
+  const cudaMemcpyKind Kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  NB_ACU(cudaMemcpyAsync(tmp, gx, sizeof(double) * 3 * n, Kin, a->st));
+  NB_ACU(cudaMemcpyAsync(tmp + 3 * n, gv, sizeof(double) * 3 * n, Kin, a->st));
+  NB_ACU(cudaMemcpyAsync(a->lm, gm, sizeof(double) * n, Kin, a->st));
+  k_aos_to_soa<<<g, 256, 0, a->st>>>(n, tmp, a->lx, a->ly, a->lz, 0);
+  k_aos_to_soa<<<g, 256, 0, a->st>>>(n, tmp + 3 * n, a->lvx, a->lvy, a->lvz, 0);
+  // absorbed bodies' final states are constants
+  k_mask<<<g, 256, 0, a->st>>>(n, d.alive, a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->lm);
+  NB_ACU(cudaMemsetAsync(a->status, 0, 4 * sizeof(int), a->st));
+  const int total = a->nsteps_done;
+  for (int seg = a->n_ckpt - 1; seg >= 0; --seg) {
+    const int start = seg * a->every;
+    const int len = total - start < a->every ? total - start : a->every;
+    int rc = checkpoint(a, seg, 1);
+    if (rc) return rc;
+    for (int t = 0; t < len; ++t) replay_step(a, a->dt, a->recs[t]);
+    for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[t]);
+    int st[2] = {0, 0};
+    NB_ACU(cudaMemcpyAsync(st, a->status, sizeof(st), cudaMemcpyDeviceToHost, a->st));
+    Ctrl c;
+    NB_ACU(cudaMemcpyAsync(&c, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a->st));
+    NB_ACU(cudaStreamSynchronize(a->st));
+    NB_ACU(cudaGetLastError());
+    if (c.status || st[0]) {
+      snprintf(a->err, sizeof(a->err), "backward: %s", nb_status_string(c.status ? c.status : st[0]));
+      return c.status ? c.status : st[0];
+    }
+  }
+  // leave the system at its final state again
+  int rc = checkpoint(a, a->n_ckpt, 1);
+  if (rc) return rc;
+  const cudaMemcpyKind Kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  k_soa_to_aos<<<g, 256, 0, a->st>>>(n, a->lx, a->ly, a->lz, tmp);
+  k_soa_to_aos<<<g, 256, 0, a->st>>>(n, a->lvx, a->lvy, a->lvz, tmp + 3 * n);
+  if (dx0) NB_ACU(cudaMemcpyAsync(dx0, tmp, sizeof(double) * 3 * n, Kout, a->st));
+  if (dv0) NB_ACU(cudaMemcpyAsync(dv0, tmp + 3 * n, sizeof(double) * 3 * n, Kout, a->st));
+  if (dm0) NB_ACU(cudaMemcpyAsync(dm0, a->lm, sizeof(double) * n, Kout, a->st));
+  NB_ACU(cudaStreamSynchronize(a->st));
+  return NB_OK;
+}
+
+const char* nb_adjoint_last_error(const nb_adjoint* a) { return a ? a->err : "no adjoint"; }
+
+void nb_adjoint_destroy(nb_adjoint* a) {
+  if (!a) return;
+  nb_destroy(a->sys);
+  free(a->recs);
+  free(a);
+}
+
+}  // extern "C"

@@ -106,8 +106,23 @@ static __device__ double pair_energy(const Phys& P, const double* a, double ma, 
          P.G * ma * mb / rab;
 }
 
+// Record of one group's integration for the adjoint's replay: the state,
+// masses, radii, critical radii and alive flags at the start of every
+// accepted substep, its size H and extrapolation column k, and every merger
+// with the pre-merger states. Slots are per member (stride 6 for states).
+struct BsRec {
+  int cap, mcap;                      // substep and merger capacities
+  int* counts;                        // [0] substeps, [1] mergers, [2] overflow
+  double* H;                          // cap
+  int* k;                             // cap
+  double *ys, *ms, *Rs, *rcs, *alv;   // cap * M * 6, cap * M (x4)
+  int* mrg;                           // mcap * 3: (substep, a, b)
+  double* mst;                        // mcap * 14: y_a, y_b, m_a, m_b before the merger
+};
+
 // Perfect merging on contact, scanned in ascending slot (= body) order.
-static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, int* merges) {
+static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, int* merges,
+                                     BsRec* rec = nullptr, int sub = 0) {
   for (int a = 0; a < c.M; ++a) {
     for (int b = a + 1; b < c.M; ++b) {
       if (!bs_alive(c, a) || !bs_alive(c, b)) continue;
@@ -119,6 +134,23 @@ static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, 
       double* gb = c.g + 10 * b;
       if (!(rab < ga[7] + gb[7])) continue;
       const double ma = ga[6], mb = gb[6];
+      if (rec) {
+        const int q = rec->counts[1];
+        if (q < rec->mcap) {
+          rec->mrg[3 * q] = sub;
+          rec->mrg[3 * q + 1] = a;
+          rec->mrg[3 * q + 2] = b;
+          for (int k = 0; k < 6; ++k) {
+            rec->mst[14 * q + k] = ya[k];
+            rec->mst[14 * q + 6 + k] = yb[k];
+          }
+          rec->mst[14 * q + 12] = ma;
+          rec->mst[14 * q + 13] = mb;
+        } else {
+          rec->counts[2] = 1;
+        }
+        rec->counts[1] = q + 1;
+      }
       const double e0 = pair_energy(P, ya, ma, yb, mb);
       const double M = ma + mb;
       for (int k = 0; k < 6; ++k) ya[k] = (ma * ya[k] + mb * yb[k]) / M;
@@ -154,7 +186,9 @@ struct BsTally {
 // s_flags: two shared ints. Returns 0, NB_E_NOCONV or NB_E_TIMEOUT (same in
 // every thread); *El (thread 0) receives the energy removed by mergers.
 static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
-                                  int* s_flags, BsTally& tally, double* El) {
+                                         int* s_flags, BsTally& tally, double* El,
+                                         BsRec* rec = nullptr) {
+  int rec_n = 0;  // accepted substeps recorded (the same in every thread)
   const int kmax = c.kmax;
   const int NT = blockDim.x;
   int level = 0;
@@ -164,6 +198,18 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
   int merges = 0;
   while (done < (1ll << level)) {
     const double H = ldexp(h, -level);
+    if (rec && rec_n < rec->cap) {  // stage the substep's start (kept if it is accepted)
+      for (int b = threadIdx.x; b < c.M; b += NT) {
+        const double* y = c.base + (size_t)b * c.stride + OY;
+        const double* g = c.g + 10 * b;
+        const size_t o = (size_t)rec_n * c.M + b;
+        for (int k = 0; k < 6; ++k) rec->ys[6 * o + k] = y[k];
+        rec->ms[o] = g[6];
+        rec->Rs[o] = g[7];
+        rec->rcs[o] = g[8];
+        rec->alv[o] = g[9];
+      }
+    }
     if (threadIdx.x == 0) {
       s_flags[0] = 0;
       s_flags[1] = 0;
@@ -250,8 +296,19 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
     if (acc) {
       ++done;
       ++tally.substeps;
+      if (rec) {
+        if (threadIdx.x == 0) {
+          if (rec_n < rec->cap) {
+            rec->H[rec_n] = H;
+            rec->k[rec_n] = kacc;
+          } else {
+            rec->counts[2] = 1;
+          }
+        }
+        ++rec_n;
+      }
       if (P.merge) {
-        if (threadIdx.x == 0) bs_merge_scan(c, P, El, &merges);
+        if (threadIdx.x == 0) bs_merge_scan(c, P, El, &merges, rec, rec_n - 1);
         __syncthreads();
       }
       if (level > 0 && (done & 1) == 0 && kacc <= kmax - 2) {
@@ -274,6 +331,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
     __syncthreads();
   }
   tally.merges += merges;
+  if (rec && threadIdx.x == 0) rec->counts[0] = rec_n;
   __syncthreads();
   return status;
 }

@@ -1,11 +1,109 @@
 // Universal-variable Kepler drift (the first sum of Eq. Ha: Kepler motion
 // about mu = G m0, "solved analytically"), shared by the single-system drift
-// kernel and the batched kernel.
+// kernel, the batched kernel and the adjoint. The solver is written once,
+// templated on its scalar type: double for the integrator, Dual6 (value and
+// six partial derivatives) for the adjoint's Jacobian of the drift map.
 #pragma once
 
 #include "nb_internal.cuh"
 
 namespace nb {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers with six partials (the Jacobian of (x, v) -> (x', v')).
+// They live in their own namespace so that their sqrt/log/fabs/copysign are
+// found only by argument-dependent lookup and never hide the double versions.
+// ---------------------------------------------------------------------------
+namespace ad {
+struct Dual6 {
+  double v;
+  double d[6];
+};
+
+__device__ __forceinline__ double val(const Dual6& a) { return a.v; }
+
+__device__ __forceinline__ Dual6 mkd(double v) {
+  Dual6 r;
+  r.v = v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = 0.0;
+  return r;
+}
+__device__ __forceinline__ Dual6 operator+(const Dual6& a, const Dual6& b) {
+  Dual6 r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+__device__ __forceinline__ Dual6 operator-(const Dual6& a, const Dual6& b) {
+  Dual6 r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+__device__ __forceinline__ Dual6 operator-(const Dual6& a) {
+  Dual6 r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+__device__ __forceinline__ Dual6 operator*(const Dual6& a, const Dual6& b) {
+  Dual6 r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+__device__ __forceinline__ Dual6 operator/(const Dual6& a, const Dual6& b) {
+  Dual6 r;
+  r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+__device__ __forceinline__ Dual6 operator+(const Dual6& a, double b) { Dual6 r = a; r.v += b; return r; }
+__device__ __forceinline__ Dual6 operator+(double b, const Dual6& a) { return a + b; }
+__device__ __forceinline__ Dual6 operator-(const Dual6& a, double b) { Dual6 r = a; r.v -= b; return r; }
+__device__ __forceinline__ Dual6 operator-(double b, const Dual6& a) { return -(a - b); }
+__device__ __forceinline__ Dual6 operator*(const Dual6& a, double b) {
+  Dual6 r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+__device__ __forceinline__ Dual6 operator*(double b, const Dual6& a) { return a * b; }
+__device__ __forceinline__ Dual6 operator/(const Dual6& a, double b) { return a * (1.0 / b); }
+__device__ __forceinline__ Dual6 operator/(double a, const Dual6& b) { return mkd(a) / b; }
+__device__ __forceinline__ Dual6 sqrt(const Dual6& a) {
+  Dual6 r;
+  r.v = ::sqrt(a.v);
+  const double h = 0.5 / r.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+__device__ __forceinline__ Dual6 log(const Dual6& a) {
+  Dual6 r;
+  r.v = ::log(a.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] / a.v;
+  return r;
+}
+__device__ __forceinline__ Dual6 fabs(const Dual6& a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ Dual6 copysign(const Dual6& a, const Dual6& s) {
+  return (a.v < 0.0) != (s.v < 0.0) ? -a : a;
+}
+}  // namespace ad
+
+using ad::Dual6;
+using ad::mkd;
+__device__ __forceinline__ double val(double a) { return a; }
+using ad::val;
 
 // ---------------------------------------------------------------------------
 // Stumpff functions c0..c3 (Danby's method): quarter z until |z| <= 0.1,
@@ -14,11 +112,11 @@ namespace nb {
 //   c0(4z) = 2 c0^2 - 1,  c1(4z) = c0 c1,  c2(4z) = c1^2 / 2,
 //   c3(4z) = (c2 + c0 c3) / 4.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double& c2,
-                                        double& c3) {
+template <typename T>
+__device__ __forceinline__ void stumpff(T z, T& c0, T& c1, T& c2, T& c3) {
   int nq = 0;
-  while (fabs(z) > 0.1 && nq < 64) {
-    z *= 0.25;
+  while (::fabs(val(z)) > 0.1 && nq < 64) {
+    z = z * 0.25;
     ++nq;
   }
   // c2 = sum_k (-z)^k / (2k+2)!,  c3 = sum_k (-z)^k / (2k+3)!,  k = 0..7
@@ -50,46 +148,48 @@ __device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double
 // G_k = s^k c_k(beta s^2). Newton's method from the second-order start (or,
 // for an unbound orbit deep in the exponential regime, the asymptotic
 // inverse), Laguerre-Conway (n = 5) if Newton has not converged after 10
-// updates. An update below 1e-10 |s| is followed by one last update.
+// updates. An update below 1e-10 |s| is followed by one last update (for the
+// dual type that last update also carries the implicit derivative of s).
 // Returns 0 or NB_E_NOCONV; on return G[0..3] hold the G_k at the final s.
-static __device__ int kepler_solve(double mu, double r0, double eta, double beta, double h,
-                            int max_iter, double G[4], int* iters) {
-  double s0 = h / r0 - eta * h * h / (2.0 * r0 * r0 * r0);
-  if (beta < 0.0) {
-    const double g = sqrt(-beta);
-    if (g * fabs(s0) > 2.0) {
+template <typename T>
+static __device__ int kepler_solve(double mu, const T& r0, const T& eta, const T& beta, double h,
+                                   int max_iter, T G[4], int* iters) {
+  T s0 = h / r0 - eta * (h * h) / (2.0 * r0 * r0 * r0);
+  if (val(beta) < 0.0) {
+    const T g = sqrt(-beta);
+    if (val(g) * ::fabs(val(s0)) > 2.0) {
       const double sg = h > 0.0 ? 1.0 : -1.0;
-      const double c = r0 + sg * eta / g + mu / (g * g);
-      const double arg = 2.0 * g * fabs(h) / c;
-      if (c > 0.0 && arg > 1.0) {
-        const double sa = sg * log(arg) / g;
-        if (fabs(sa) < fabs(s0)) s0 = sa;
+      const T c = r0 + sg * eta / g + mu / (g * g);
+      const T arg = 2.0 * ::fabs(h) * g / c;
+      if (val(c) > 0.0 && val(arg) > 1.0) {
+        const T sa = sg * log(arg) / g;
+        if (::fabs(val(sa)) < ::fabs(val(s0))) s0 = sa;
       }
     }
   }
   int it = 0;
   for (int method = 0; method < 2; ++method) {
-    double s = s0;
+    T s = s0;
     bool last = false;
     const int cap = method == 0 ? 10 : max_iter;
     for (int k = 0; k < cap && it < max_iter; ++k, ++it) {
-      double c0, c1, c2, c3;
+      T c0, c1, c2, c3;
       stumpff(beta * s * s, c0, c1, c2, c3);
-      const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
-      const double F = r0 * G1 + eta * G2 + mu * G3 - h;
-      const double Fp = r0 * c0 + eta * G1 + mu * G2;
-      double ds;
+      const T G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+      const T F = r0 * G1 + eta * G2 + mu * G3 - h;
+      const T Fp = r0 * c0 + eta * G1 + mu * G2;
+      T ds;
       if (method == 0) {
         ds = F / Fp;
       } else {
-        const double Fpp = eta * c0 + (mu - beta * r0) * G1;
-        const double disc = fabs(16.0 * Fp * Fp - 20.0 * F * Fpp);
+        const T Fpp = eta * c0 + (mu - beta * r0) * G1;
+        const T disc = fabs(16.0 * Fp * Fp - 20.0 * F * Fpp);
         ds = 5.0 * F / (Fp + copysign(sqrt(disc), Fp));
       }
-      s -= ds;
-      if (!isfinite(s)) break;
+      s = s - ds;
+      if (!isfinite(val(s))) break;
       if (last) {
-        double d0, d1, d2, d3;
+        T d0, d1, d2, d3;
         stumpff(beta * s * s, d0, d1, d2, d3);
         G[0] = d0;
         G[1] = s * d1;
@@ -98,7 +198,7 @@ static __device__ int kepler_solve(double mu, double r0, double eta, double beta
         *iters = it + 1;
         return 0;
       }
-      if (fabs(ds) <= 1e-10 * fabs(s)) last = true;
+      if (::fabs(val(ds)) <= 1e-10 * ::fabs(val(s))) last = true;
     }
     if (it >= max_iter) break;
   }
@@ -107,26 +207,26 @@ static __device__ int kepler_solve(double mu, double r0, double eta, double beta
 }
 
 // Gauss f and g drift of one body by h; returns 0 or NB_E_NOCONV.
-__device__ __forceinline__ int kepler_drift(double mu, double& x, double& y, double& z,
-                                            double& vx, double& vy, double& vz, double h,
-                                            int max_iter, int* iters) {
+template <typename T>
+__device__ __forceinline__ int kepler_drift(double mu, T& x, T& y, T& z, T& vx, T& vy, T& vz,
+                                            double h, int max_iter, int* iters) {
   *iters = 0;
   if (h == 0.0) return 0;
-  const double r0 = sqrt(x * x + y * y + z * z);
-  const double v2 = vx * vx + vy * vy + vz * vz;
-  const double eta = x * vx + y * vy + z * vz;
-  const double beta = 2.0 * mu / r0 - v2;
-  double G[4];
+  const T r0 = sqrt(x * x + y * y + z * z);
+  const T v2 = vx * vx + vy * vy + vz * vz;
+  const T eta = x * vx + y * vy + z * vz;
+  const T beta = 2.0 * mu / r0 - v2;
+  T G[4];
   const int st = kepler_solve(mu, r0, eta, beta, h, max_iter, G, iters);
   if (st) return st;
-  const double r = r0 * G[0] + eta * G[1] + mu * G[2];
-  const double fm1 = -mu * G[2] / r0;           // f - 1
-  const double g = r0 * G[1] + eta * G[2];      // g
-  const double fd = -mu * G[1] / (r * r0);      // fdot
-  const double gdm1 = -mu * G[2] / r;           // gdot - 1
-  const double nx = x + (fm1 * x + g * vx), ny = y + (fm1 * y + g * vy), nz = z + (fm1 * z + g * vz);
-  const double nvx = vx + (fd * x + gdm1 * vx), nvy = vy + (fd * y + gdm1 * vy),
-               nvz = vz + (fd * z + gdm1 * vz);
+  const T r = r0 * G[0] + eta * G[1] + mu * G[2];
+  const T fm1 = -mu * G[2] / r0;       // f - 1
+  const T g = r0 * G[1] + eta * G[2];  // g
+  const T fd = -mu * G[1] / (r * r0);  // fdot
+  const T gdm1 = -mu * G[2] / r;       // gdot - 1
+  const T nx = x + (fm1 * x + g * vx), ny = y + (fm1 * y + g * vy), nz = z + (fm1 * z + g * vz);
+  const T nvx = vx + (fd * x + gdm1 * vx), nvy = vy + (fd * y + gdm1 * vy),
+          nvz = vz + (fd * z + gdm1 * vz);
   x = nx; y = ny; z = nz;
   vx = nvx; vy = nvy; vz = nvz;
   return 0;

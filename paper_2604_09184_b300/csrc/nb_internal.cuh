@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nb.h"
 
 namespace nb {
@@ -285,3 +287,20 @@ int peak_blocks();
 int measure_peaks(double* fp64, double* fp32, void* scratch, cudaStream_t st);
 
 }  // namespace nb
+
+// Host handle of one system (C ABI type nb_system).
+struct nb_system {
+  nb::Dev d;
+  nb::Phys P;
+  nb_params prm;
+  cudaStream_t st;
+  double* out8;  // device: energy results
+  int* cnt;      // device: gather count
+  char err[256];
+  // kick timing (CUDA events on the launching stream) and launch counting
+  int timing;
+  std::vector<cudaEvent_t>* events;
+  double kick_ms;
+  long long kick_launches;
+  long long launches;
+};

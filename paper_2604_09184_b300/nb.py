@@ -109,6 +109,16 @@ def lib():
         L.nb_peak_scratch_bytes.argtypes = []
         L.nb_peak_scratch_bytes.restype = C.c_size_t
         L.nb_measure_peaks.argtypes = [_D, _D, C.c_void_p, C.c_void_p]
+        L.nb_adjoint_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int, C.c_int, C.c_int]
+        L.nb_adjoint_workspace_bytes.restype = C.c_size_t
+        L.nb_adjoint_init.argtypes = [C.POINTER(C.c_void_p), C.POINTER(NbParams), C.c_int] + [
+            C.c_void_p] * 5 + [C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int]
+        L.nb_adjoint_forward.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.nb_adjoint_state.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]
+        L.nb_adjoint_backward.argtypes = [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]
+        L.nb_adjoint_last_error.argtypes = [C.c_void_p]
+        L.nb_adjoint_last_error.restype = C.c_char_p
+        L.nb_adjoint_destroy.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -430,3 +440,135 @@ def measure_peaks():
     if code != NB_OK:
         raise NbError(code, "nb_measure_peaks")
     return f64.value, f32.value
+
+
+class NBodyAdjoint:
+    """Forward integration with checkpoints and its discrete adjoint
+    (nb_adjoint_*): gradients of a loss on the final state with respect to
+    the initial positions, velocities and masses. rc is required and held
+    fixed, as are the encounter events of the forward.
+
+    Inputs are host numpy arrays or CUDA float64 tensors; results come back
+    in the same kind.
+    """
+
+    def __init__(self, p: NbParams, x, v, m, R, rc, nsteps: int, every: int = 100):
+        torch = _torch()
+        L = lib()
+        self.p = p
+        self.on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        if self.on_dev:
+            args = [t.contiguous().to(torch.float64) for t in (x, v, m, R, rc)]
+            ptrs = [_ptr(t) for t in args]
+            n = args[0].shape[0]
+        else:
+            args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, m, R, rc)]
+            ptrs = [C.c_void_p(a.ctypes.data) for a in args]
+            n = args[2].shape[0]
+        self._keep = args
+        self.n = int(n)
+        self.nsteps = int(nsteps)
+        nbytes = L.nb_adjoint_workspace_bytes(C.byref(p), self.n, self.nsteps, int(every))
+        if nbytes == 0:
+            raise NbError(NB_E_INVALID, "bad parameters, n, nsteps or checkpoint interval")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        self._ws_ptr = C.c_void_p(base + (-base) % 256)
+        h = C.c_void_p()
+        self._stream = _stream(torch)
+        code = L.nb_adjoint_init(C.byref(h), C.byref(p), self.n, *ptrs, self.nsteps, int(every),
+                                 self._ws_ptr, nbytes, self._stream, 1 if self.on_dev else 0)
+        if code != NB_OK:
+            raise NbError(code, "nb_adjoint_init failed")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().nb_adjoint_destroy(h)
+            self._h = None
+
+    def _check(self, code):
+        if code != NB_OK:
+            raise NbError(code, lib().nb_adjoint_last_error(self._h).decode())
+
+    def forward(self, dt: float, nsteps: int | None = None):
+        self._check(lib().nb_adjoint_forward(self._h, int(nsteps or self.nsteps), float(dt)))
+
+    def state(self) -> dict:
+        """Final state of all n slots: x, v (n, 3), m (n,), alive (n,)."""
+        n = self.n
+        if self.on_dev:
+            import torch
+            out = dict(x=torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+                       v=torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+                       m=torch.empty(n, dtype=torch.float64, device="cuda"),
+                       alive=torch.empty(n, dtype=torch.int32, device="cuda"))
+            ptrs = [_ptr(out[k]) for k in ("x", "v", "m", "alive")]
+        else:
+            out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), m=np.zeros(n),
+                       alive=np.zeros(n, dtype=np.int32))
+            ptrs = [C.c_void_p(out[k].ctypes.data) for k in ("x", "v", "m", "alive")]
+        self._check(lib().nb_adjoint_state(self._h, *ptrs, 1 if self.on_dev else 0))
+        return out
+
+    def backward(self, gx, gv, gm):
+        """Pull back (dL/dx_T, dL/dv_T, dL/dm_T) to (dL/dx_0, dL/dv_0, dL/dm_0)."""
+        n = self.n
+        if self.on_dev:
+            import torch
+            g = [t.contiguous().to(torch.float64) for t in (gx, gv, gm)]
+            out = (torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+                   torch.empty((n, 3), dtype=torch.float64, device="cuda"),
+                   torch.empty(n, dtype=torch.float64, device="cuda"))
+            gp = [_ptr(t) for t in g]
+            op = [_ptr(t) for t in out]
+        else:
+            g = [np.ascontiguousarray(a, dtype=np.float64) for a in (gx, gv, gm)]
+            out = (np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n))
+            gp = [C.c_void_p(a.ctypes.data) for a in g]
+            op = [C.c_void_p(a.ctypes.data) for a in out]
+        self._check(lib().nb_adjoint_backward(self._h, *gp, *op, 1 if self.on_dev else 0))
+        return out
+
+
+def _autograd_fn():
+    import torch
+
+    class NBodyFn(torch.autograd.Function):
+        """(x0, v0, m0) -> (x_T, v_T, m_T) through libnb, differentiable by the
+        library's discrete adjoint. R and rc are constants."""
+
+        @staticmethod
+        def forward(ctx, x0, v0, m0, R, rc, p, nsteps, dt, every):
+            adj = NBodyAdjoint(p, x0.detach(), v0.detach(), m0.detach(), R.detach(),
+                               rc.detach(), nsteps, every)
+            adj.forward(dt)
+            st = adj.state()
+            ctx.adj = adj
+            ctx.mark_non_differentiable(st["alive"])
+            return st["x"], st["v"], st["m"], st["alive"]
+
+        @staticmethod
+        def backward(ctx, gx, gv, gm, _galive):
+            n = ctx.adj.n
+            z3 = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+            z1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+            dx, dv, dm = ctx.adj.backward(z3 if gx is None else gx, z3 if gv is None else gv,
+                                          z1 if gm is None else gm)
+            return dx, dv, dm, None, None, None, None, None, None
+
+    return NBodyFn
+
+
+_NBodyFn = None
+
+
+def integrate(x0, v0, m0, R, rc, p: NbParams, nsteps: int, dt: float, every: int = 100):
+    """Differentiable integration of CUDA float64 tensors: returns
+    (x_T, v_T, m_T, alive_T); gradients reach x0, v0 and m0 through the
+    library's adjoint kernels."""
+    global _NBodyFn
+    if _NBodyFn is None:
+        _NBodyFn = _autograd_fn()
+    return _NBodyFn.apply(x0, v0, m0, R, rc, p, int(nsteps), float(dt), int(every))

@@ -1,0 +1,241 @@
+"""The library's discrete adjoint on the GPU.
+
+* Encounter-free systems: every entry of the gradient against reverse-mode
+  automatic differentiation of the CPU reference step (oracle/grad.py).
+* The Jacobian assembled from the adjoint is symplectic in (x, p = m v).
+* Systems with close encounters (Bulirsch-Stoer groups) and with mergers:
+  sampled entries against central finite differences of the C oracle's
+  forward with rc held (rc passed in). Coordinates whose +-h runs change the
+  event set (groups, substeps, mergers) are reported apart, with a looser bound.
+* The autograd.Function gives the same gradient as the direct call; backward
+  is deterministic and leaves the final state in place.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import grad as og  # noqa: E402
+from oracle import nbref  # noqa: E402
+from paper_2604_09184_b300 import build, ics  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def nbm():
+    from paper_2604_09184_b300 import nb
+    return nb
+
+
+def with_rc(d, **kw):
+    p = nbref.params(dt_rcrit=d.dt, **kw)
+    rc = np.array([nbref.rcrit(p, d.x[i], d.v[i], d.m[i]) for i in range(d.n)])
+    return p, rc
+
+
+def adjoint_grad(d, rc, steps, every, gx, gv, gm, **kw):
+    nb = nbm()
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt, **kw), d.x, d.v, d.m, d.R, rc, steps, every)
+    a.forward(d.dt)
+    return a, a.backward(gx, gv, gm)
+
+
+def cotangents(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, 3)), 60.0 * rng.standard_normal((n, 3)), \
+        1e5 * rng.standard_normal(n)
+
+
+def test_adjoint_matches_autodiff_reference():
+    d = ics.make_disk(32, 2.0, 0.8, 2.5, 0.02, 0.01, 8.0, seed=5101)
+    p, rc = with_rc(d)
+    steps, every = 25, 7  # segments of 7, 7, 7 and 4 steps
+    gx, gv, gm = cotangents(d.n, 1)
+    _, (dx, dv, dm) = adjoint_grad(d, rc, steps, every, gx, gv, gm)
+    rx, rv, rm = og.gradient(d.x, d.v, d.m, rc, d.dt, steps, gx, gv, gm)
+    for got, ref in ((dx, rx), (dv, rv), (dm, rm)):
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= 1e-10, err
+
+
+def test_adjoint_with_giant_matches_autodiff_reference():
+    d = ics.make_disk(15, 2.0, 0.8, 2.5, 0.02, 0.01, 8.0, seed=5102, giants=("J",))
+    p, rc = with_rc(d)
+    gx, gv, gm = cotangents(d.n, 2)
+    _, (dx, dv, dm) = adjoint_grad(d, rc, 12, 5, gx, gv, gm)
+    rx, rv, rm = og.gradient(d.x, d.v, d.m, rc, d.dt, 12, gx, gv, gm)
+    for got, ref in ((dx, rx), (dv, rv), (dm, rm)):
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_adjoint_jacobian_is_symplectic():
+    n, steps = 4, 3
+    d = ics.make_disk(n, 2.0, 0.8, 2.5, 0.02, 0.01, 8.0, seed=5103)
+    p, rc = with_rc(d)
+    nb = nbm()
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc, steps, 2)
+    a.forward(d.dt)
+    Mxv = np.zeros((6 * n, 6 * n))
+    for row in range(6 * n):
+        gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
+        (gx if row < 3 * n else gv).reshape(-1)[row % (3 * n)] = 1.0
+        dx, dv, _ = a.backward(gx, gv, np.zeros(n))
+        Mxv[row] = np.r_[dx.reshape(-1), dv.reshape(-1)]
+    Dm = np.diag(np.r_[np.ones(3 * n), np.repeat(d.m, 3)])
+    M = Dm @ Mxv @ np.linalg.inv(Dm)  # (x, p) coordinates
+    Om = np.zeros((6 * n, 6 * n))
+    Om[:3 * n, 3 * n:] = np.eye(3 * n)
+    Om[3 * n:, :3 * n] = -np.eye(3 * n)
+    resid = M.T @ Om @ M - Om
+    scale = np.abs(M).T @ np.abs(Om) @ np.abs(M)
+    assert np.max(np.abs(resid) / scale) <= 1e-12
+
+
+def _events(s):
+    st = s.stats()
+    return (st["groups"], st["bs_substeps"], st["merges"], st["encounter_pairs"])
+
+
+def _fd_check(d, rc, steps, every, ncoord, seed, merge, tol, tol_changed):
+    p = nbref.params(dt_rcrit=d.dt, merge=merge)
+    gx, gv, gm = cotangents(d.n, seed)
+    _, (dx, dv, dm) = adjoint_grad(d, rc, steps, every, gx, gv, gm, merge=merge)
+    base = nbref.RefSystem(p, d.x, d.v, d.m, d.R, rc=rc)
+    assert base.step(steps, d.dt) == 0
+    ev0 = _events(base)
+    assert ev0[0] > 0, "no close encounters: the check would not reach the BS adjoint"
+    if merge:
+        assert ev0[2] > 0
+
+    def loss(x, v, m):
+        s = nbref.RefSystem(p, x, v, m, d.R, rc=rc)
+        assert s.step(steps, d.dt) == 0
+        st = s.state()
+        ids = st["ids"]
+        return float((gx[ids] * st["x"]).sum() + (gv[ids] * st["v"]).sum() +
+                     (gm[ids] * st["m"]).sum()), _events(s)
+
+    rng = np.random.default_rng(seed + 100)
+    grads = (dx, dv, dm)
+    arrays = (d.x, d.v, d.m)
+
+    def central(k, idx, rel):
+        h = rel * abs(arrays[k][idx]) or 1e-9
+        plus = [a.copy() for a in arrays]
+        minus = [a.copy() for a in arrays]
+        plus[k][idx] += h
+        minus[k][idx] -= h
+        Lp, ep = loss(*plus)
+        Lm, em = loss(*minus)
+        return (Lp - Lm) / (2 * h), ep == ev0 and em == ev0
+
+    # Close encounters make the map chaotic: rounding noise of the forward,
+    # amplified, limits a finite difference to ~1e-5 of the gradient's scale.
+    # Each coordinate takes two step sizes; their spread u bounds the error of
+    # the smaller one (its truncation error is 100x below the larger one's, its
+    # noise 10x above), and the adjoint must agree with it within 3 u plus a
+    # floor; the median error must stay at the finite differences' noise level.
+    worst, worst_changed, changed, ratios = 0.0, 0.0, 0, []
+    for _ in range(ncoord):
+        k = int(rng.integers(0, 3))
+        idx = tuple(int(rng.integers(0, s)) for s in arrays[k].shape)
+        big, small = (1e-2, 1e-3) if k == 2 else (1e-6, 1e-7)
+        f1, same1 = central(k, idx, big)
+        f2, same2 = central(k, idx, small)
+        scale = np.abs(grads[k]).max()
+        u = abs(f1 - f2) + tol * scale
+        err = abs(f2 - grads[k][idx])
+        if same1 and same2:
+            worst = max(worst, err / u)
+            ratios.append(err / scale)
+        else:
+            changed += 1
+            worst_changed = max(worst_changed, err / scale)
+    print("fd check: worst err/bound %.3g, median err %.3g of scale; %d coordinates changed "
+          "the event set (worst %.3g of scale)"
+          % (worst, float(np.median(ratios)), changed, worst_changed))
+    assert worst <= 3.0
+    assert float(np.median(ratios)) <= 1e-6
+    assert worst_changed <= tol_changed
+
+
+def test_adjoint_with_encounters_matches_finite_differences():
+    d = ics.make_disk(32, 2.0, 0.97, 1.03, 0.02, 0.01, 6.0, seed=6)
+    p, rc = with_rc(d, merge=0)
+    _fd_check(d, rc, steps=60, every=16, ncoord=48, seed=3, merge=0, tol=1e-7,
+              tol_changed=1e-2)
+
+
+def test_adjoint_with_mergers_matches_finite_differences():
+    d = ics.make_disk(24, 2.0, 0.97, 1.03, 0.01, 0.005, 6.0, seed=12, f_radius=300.0)
+    p, rc = with_rc(d, merge=1)
+    _fd_check(d, rc, steps=60, every=20, ncoord=48, seed=4, merge=1, tol=1e-7,
+              tol_changed=1e-1)
+
+
+def test_autograd_function_and_determinism():
+    nb = nbm()
+    d = ics.make_disk(48, 2.0, 0.8, 2.5, 0.02, 0.01, 8.0, seed=5104)
+    p, rc = with_rc(d)
+    cuda = dict(dtype=torch.float64, device="cuda")
+    x0 = torch.tensor(d.x, **cuda, requires_grad=True)
+    v0 = torch.tensor(d.v, **cuda, requires_grad=True)
+    m0 = torch.tensor(d.m, **cuda, requires_grad=True)
+    R, rct = torch.tensor(d.R, **cuda), torch.tensor(rc, **cuda)
+    xT, vT, mT, alive = nb.integrate(x0, v0, m0, R, rct, nb.params(dt_rcrit=d.dt), 20, d.dt,
+                                     every=6)
+    tagged = slice(0, 16)
+    loss = (xT[tagged] ** 2).sum() + 0.5 * (mT[:, None] * vT ** 2).sum()
+    loss.backward()
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc, 20, 6)
+    a.forward(d.dt)
+    st = a.state()
+    assert np.array_equal(st["x"], xT.detach().cpu().numpy())
+    gx = np.zeros((d.n, 3))
+    gx[tagged] = 2.0 * st["x"][tagged]
+    gv = st["m"][:, None] * st["v"]
+    gm = 0.5 * (st["v"] ** 2).sum(1)
+    dx, dv, dm = a.backward(gx, gv, gm)
+    assert np.array_equal(dx, x0.grad.cpu().numpy())
+    assert np.array_equal(dv, v0.grad.cpu().numpy())
+    assert np.array_equal(dm, m0.grad.cpu().numpy())
+    # a second backward gives the same bits and leaves the final state
+    dx2, dv2, dm2 = a.backward(gx, gv, gm)
+    assert np.array_equal(dx, dx2) and np.array_equal(dv, dv2) and np.array_equal(dm, dm2)
+    st2 = a.state()
+    assert np.array_equal(st["x"], st2["x"]) and np.array_equal(st["v"], st2["v"])
+
+
+def test_adjoint_forward_equals_nb_step():
+    """The checkpointed forward is nb_step: same final state bit for bit."""
+    nb = nbm()
+    d = ics.make_disk(32, 2.0, 0.97, 1.03, 0.02, 0.01, 6.0, seed=6)
+    p, rc = with_rc(d)
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc, 60, 16)
+    a.forward(d.dt)
+    s = nb.NBodySystem(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc=rc)
+    s.step(60, d.dt)
+    ref = s.state()
+    st = a.state()
+    assert np.array_equal(st["x"][ref["ids"]], ref["x"])
+    assert np.array_equal(st["v"][ref["ids"]], ref["v"])
+
+
+def test_adjoint_rejects_bad_requests():
+    nb = nbm()
+    d = ics.make_disk(16, 2.0, 0.8, 2.5, 0.02, 0.01, 8.0, seed=5105)
+    p, rc = with_rc(d)
+    with pytest.raises(nb.NbError):
+        nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt, precision=nb.NB_PREC_MIXED), d.x, d.v, d.m,
+                        d.R, rc, 10, 5)
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc, 10, 5)
+    with pytest.raises(nb.NbError):
+        a.forward(d.dt, nsteps=40)  # more steps than the checkpoints were sized for
+    with pytest.raises(nb.NbError):
+        a.backward(np.zeros((16, 3)), np.zeros((16, 3)), np.zeros(16))  # no forward yet
