@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed", "ds"], default="fp64",
                     help="kick precision of the timed run (profiling); the line's value is fp64")
     return ap.parse_args()
@@ -285,6 +286,10 @@ def run_ours(args):
     if not args.no_batch:
         batched = run_batched(nb, torch, args, flush, stream)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(nb, torch, stream)
+
     # end to end through the C ABI with host buffers: per step, load the state
     # from pinned host memory, step, read the state back to pinned host memory
     e2e = None
@@ -300,7 +305,7 @@ def run_ours(args):
                    "precision": args.precision, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
                    "l2": "flushed before each timed step (256 MiB write, outside the step events)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
-        "batched": batched,
+        "batched": batched, "adjoint": adjoint,
         "clocks": clk, "gpu_launches": gpu_launches,
         "encounters": {"pairs": st["encounter_pairs"], "groups": st["groups"],
                        "bs_substeps": st["bs_substeps"], "merges": st["merges"],
@@ -407,6 +412,50 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
             "speedup_vs_single_one_call_per_step": single_ms / ms_call,
             "single_sample": int(len(pick)), "bs_substeps": st["bs_substeps"],
             "groups": st["groups"], "merges": st["merges"]}
+
+
+def run_adjoint(nb, torch, stream, nsteps=2000, every=100):
+    """Gradient of a loss on the final state of the 2048-planetesimal disk
+    with Jupiter (2000 steps of 6 d) with respect to the initial x, v, m:
+    checkpointed forward, then the backward pass (segment replays plus the
+    adjoint kernels). Loss: |x|^2 of 16 tagged bodies plus the kinetic energy."""
+    from paper_2604_09184_b300 import ics
+    disk = ics.workload("adjoint_2k_j")
+    rc = nb_rc_initial(nb, disk)
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=disk.dt), disk.x, disk.v, disk.m, disk.R, rc,
+                        nsteps, every)
+    n = disk.n
+
+    def cotangent():
+        st = a.state()
+        gx = np.zeros((n, 3))
+        gx[:16] = 2.0 * st["x"][:16]
+        return gx, st["m"][:, None] * st["v"], 0.5 * (st["v"] ** 2).sum(1)
+
+    # warm-up on a short run
+    a.forward(disk.dt, nsteps=every)
+    a.backward(*cotangent())
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    a.forward(disk.dt)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    g = cotangent()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dx, dv, dm = a.backward(*g)
+    t_bwd = time.perf_counter() - t0
+    fwd_ms = e[0].elapsed_time(e[1])
+    ok = bool(np.isfinite(dx).all() and np.isfinite(dv).all() and np.isfinite(dm).all())
+    ckpt = (nsteps // every + 2) * (13 * n * 8 + n * 4)
+    del a
+    return {"workload": "adjoint_2k_j (2048 planetesimals + Jupiter, dt 6 d)", "n_bodies": n,
+            "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd_ms,
+            "backward_ms": t_bwd * 1e3, "backward_over_forward": t_bwd * 1e3 / fwd_ms,
+            "gradient_steps_per_s": nsteps / t_bwd, "checkpoint_bytes": ckpt,
+            "finite": ok, "timing": "forward: CUDA events; backward: host clock around the "
+            "synchronous nb_adjoint_backward call (includes its host copies of 7n doubles)"}
 
 
 def nb_rc_initial(nb, disk):

@@ -33,7 +33,8 @@
 
 namespace nb {
 
-constexpr int ANT = 256;     // threads of the O(N) and O(N^2) adjoint kernels
+constexpr int ANT = 256;     // threads of the O(N) adjoint kernels
+constexpr int VNT = 128;     // threads of the kick VJP (targets per CTA)
 constexpr int ABNT = 64;     // threads of the BS adjoint CTA
 constexpr int kSubCap = 256; // recorded BS substeps per group and step
 constexpr int kMrgCap = 16;  // recorded mergers per group and step
@@ -95,55 +96,94 @@ struct Vjp {
   const double *x, *y, *z, *m, *rc;
   const int* alive;
   const double *mux, *muy, *muz;  // (h/2) lambda_v
-  double *lx, *ly, *lz, *lm;      // accumulated
-  int n;
-  double G;
+  double* part;                   // S x 4 x n partial sums (x, y, z, m)
+  int n, chunk;
 };
 
-// lambda_x_k += G sum_j T_kj (m_k mu_j - m_j mu_k), T = phi I + (phi'/r) d d^T;
-// lambda_m_k += G sum_j phi mu_j . (x_k - x_j).
-__global__ void __launch_bounds__(ANT) k_kick_vjp(Vjp V) {
-  __shared__ double sx[ANT], sy[ANT], sz[ANT], sm[ANT], src[ANT], su[ANT], sv[ANT], sw[ANT];
-  __shared__ int sa[ANT];
-  const int k = blockIdx.x * ANT + threadIdx.x;
+// Partial sums over the j-chunk blockIdx.y of
+//   lambda_x_k += G sum_j T_kj (m_k mu_j - m_j mu_k), T = phi I + (phi'/r) d d^T,
+//   lambda_m_k += G sum_j phi mu_j . (x_k - x_j),
+// phi = w / r^3. Beyond rc (w = 1, the common case) phi = r^-3 and
+// phi'/r = -3 r^-5, with 1/r from the seeded reciprocal root.
+__global__ void __launch_bounds__(VNT) k_kick_vjp(Vjp V) {
+  __shared__ double sx[VNT], sy[VNT], sz[VNT], sm[VNT], src2[VNT], su[VNT], sv[VNT], sw[VNT];
+  __shared__ double srcv[VNT];
+  const int k = blockIdx.x * VNT + threadIdx.x;
   const bool act = k < V.n && V.alive[k];
   const double xk = act ? V.x[k] : 0.0, yk = act ? V.y[k] : 0.0, zk = act ? V.z[k] : 0.0;
   const double mk = act ? V.m[k] : 0.0, rck = act ? V.rc[k] : 0.0;
+  const double rck2 = rck * rck;
   const double mxk = act ? V.mux[k] : 0.0, myk = act ? V.muy[k] : 0.0, mzk = act ? V.muz[k] : 0.0;
   double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
-  for (int jt = 0; jt < V.n; jt += ANT) {
+  const int j0 = blockIdx.y * V.chunk;
+  const int j1 = min(V.n, j0 + V.chunk);
+  for (int jt = j0; jt < j1; jt += VNT) {
     __syncthreads();
     const int j = jt + threadIdx.x;
-    if (j < V.n) {
+    if (j < j1) {
+      const bool aj = V.alive[j] != 0;
       sx[threadIdx.x] = V.x[j]; sy[threadIdx.x] = V.y[j]; sz[threadIdx.x] = V.z[j];
-      sm[threadIdx.x] = V.m[j]; src[threadIdx.x] = V.rc[j]; sa[threadIdx.x] = V.alive[j];
-      su[threadIdx.x] = V.mux[j]; sv[threadIdx.x] = V.muy[j]; sw[threadIdx.x] = V.muz[j];
+      // absorbed bodies: zero mass and cotangent, so every term vanishes
+      sm[threadIdx.x] = aj ? V.m[j] : 0.0;
+      srcv[threadIdx.x] = V.rc[j];
+      src2[threadIdx.x] = V.rc[j] * V.rc[j];
+      su[threadIdx.x] = aj ? V.mux[j] : 0.0;
+      sv[threadIdx.x] = aj ? V.muy[j] : 0.0;
+      sw[threadIdx.x] = aj ? V.muz[j] : 0.0;
     }
     __syncthreads();
     if (!act) continue;
-    const int cnt = min(ANT, V.n - jt);
+    const int cnt = min(VNT, j1 - jt);
     for (int q = 0; q < cnt; ++q) {
-      if (jt + q == k || !sa[q]) continue;
       const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
       const double r2 = sep2(dx, dy, dz);
-      if (r2 == 0.0) continue;
+      if (r2 == 0.0) continue;  // the target itself (and coincident bodies)
       double p, dp_r;
-      pair_profile(r2, fmax(rck, src[q]), 0, p, dp_r);
-      const double ux = mk * su[q] - sm[q] * mxk, uy = mk * sv[q] - sm[q] * myk,
-                   uz = mk * sw[q] - sm[q] * mzk;
-      const double du = dx * ux + dy * uy + dz * uz;
-      ax += p * ux + dp_r * du * dx;
-      ay += p * uy + dp_r * du * dy;
-      az += p * uz + dp_r * du * dz;
-      am -= p * (su[q] * dx + sv[q] * dy + sw[q] * dz);
+      if (r2 >= fmax(rck2, src2[q])) {
+        const double ri = rinv_fast(r2);
+        const double ir2 = ri * ri;
+        p = ri * ir2;
+        dp_r = -3.0 * p * ir2;
+      } else {
+        pair_profile(r2, fmax(rck, srcv[q]), 0, p, dp_r);
+      }
+      const double ux = __fma_rn(mk, su[q], -sm[q] * mxk);
+      const double uy = __fma_rn(mk, sv[q], -sm[q] * myk);
+      const double uz = __fma_rn(mk, sw[q], -sm[q] * mzk);
+      const double t = dp_r * (dx * ux + dy * uy + dz * uz);
+      ax = __fma_rn(t, dx, __fma_rn(p, ux, ax));
+      ay = __fma_rn(t, dy, __fma_rn(p, uy, ay));
+      az = __fma_rn(t, dz, __fma_rn(p, uz, az));
+      am = __fma_rn(-p, su[q] * dx + sv[q] * dy + sw[q] * dz, am);
     }
   }
-  if (act) {
-    V.lx[k] += V.G * ax;
-    V.ly[k] += V.G * ay;
-    V.lz[k] += V.G * az;
-    V.lm[k] += V.G * am;
+  if (k < V.n) {
+    double* o = V.part + (size_t)blockIdx.y * 4 * V.n;
+    o[k] = ax;
+    o[V.n + k] = ay;
+    o[2 * V.n + k] = az;
+    o[3 * V.n + k] = am;
   }
+}
+
+// lambda += G sum_s part[s] in a fixed order (deterministic).
+__global__ void __launch_bounds__(ANT) k_kick_vjp_sum(int n, int S, const double* part, double G,
+                                                     const int* alive, double* lx, double* ly,
+                                                     double* lz, double* lm) {
+  const int k = blockIdx.x * ANT + threadIdx.x;
+  if (k >= n || !alive[k]) return;
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+  for (int q = 0; q < S; ++q) {
+    const double* o = part + (size_t)q * 4 * n;
+    a += o[k];
+    b += o[n + k];
+    c += o[2 * n + k];
+    d += o[3 * n + k];
+  }
+  lx[k] += G * a;
+  ly[k] += G * b;
+  lz[k] += G * c;
+  lm[k] += G * d;
 }
 
 // Per-block sums of lambda_x over the bodies with alive != 0 (fixed order).
@@ -619,6 +659,8 @@ struct nb_adjoint {
   double *gscr, *gnew, *slot, *H, *mst;
   int *kk, *counts, *mrg;
   int slot_stride;
+  double* vpart;  // kick VJP partial sums, vjp_S x 4 x n
+  int vjp_S;
   char err[256];
 };
 
@@ -640,6 +682,14 @@ struct ACarver {
 
 int kmax_of(const nb_params& p) {
   return p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
+}
+
+// j-chunks of the kick VJP: about four CTAs per SM on 148 SMs, whole tiles.
+int vjp_split(int n) {
+  const int tiles = (n + VNT - 1) / VNT;
+  int S = (148 * 4 + tiles - 1) / tiles;
+  if (S > tiles) S = tiles;
+  return S < 1 ? 1 : S;
 }
 
 size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, nb_adjoint* a) {
@@ -680,7 +730,11 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
   int* counts = c.take<int>((size_t)n * 4);
   int* mrg = c.take<int>((size_t)n * kMrgCap * 3);
   double* mst = c.take<double>((size_t)n * kMrgCap * 14);
+  const int vS = vjp_split(n);
+  double* vpart = c.take<double>((size_t)vS * 4 * n);
   if (a && base) {
+    a->vpart = vpart;
+    a->vjp_S = vS;
     a->sys = (nb_system*)sysws;  // placeholder; replaced by the real handle in init
     a->ck_d = ck_d; a->ck_i = ck_i; a->ck_c = ck_c;
     a->max_ckpt = nck;
@@ -754,13 +808,17 @@ void kick_vjp(nb_adjoint* a, const double* x6, const double* m, const double* rc
   const int n = a->n;
   const int g = (n + ANT - 1) / ANT;
   k_scale3<<<g, ANT, 0, a->st>>>(n, hh, a->lvx, a->lvy, a->lvz, a->mux, a->muy, a->muz);
+  const int S = a->vjp_S;
+  const int tiles = (n + VNT - 1) / VNT;
   Vjp V;
   V.x = x6; V.y = x6 + n; V.z = x6 + 2 * n; V.m = m; V.rc = rc; V.alive = alive;
   V.mux = a->mux; V.muy = a->muy; V.muz = a->muz;
-  V.lx = a->lx; V.ly = a->ly; V.lz = a->lz; V.lm = a->lm;
+  V.part = a->vpart;
   V.n = n;
-  V.G = a->sys->P.G;
-  k_kick_vjp<<<g, ANT, 0, a->st>>>(V);
+  V.chunk = ((tiles + S - 1) / S) * VNT;
+  k_kick_vjp<<<dim3(tiles, S), VNT, 0, a->st>>>(V);
+  k_kick_vjp_sum<<<g, ANT, 0, a->st>>>(n, S, a->vpart, a->sys->P.G, alive, a->lx, a->ly, a->lz,
+                                       a->lm);
 }
 
 void cdrift_vjp(nb_adjoint* a, const int* alive, const double* m, const double* v6, double hh) {
