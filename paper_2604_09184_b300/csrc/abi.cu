@@ -57,7 +57,7 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
   d.log_cap = p.log_capacity > 0 ? p.log_capacity : (1 << 20);
   d.member_cap = n;
   d.bs_kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
-  d.bs_stride = 6 * (4 + 2 * d.bs_kmax) + 4;  // + aux (G m, 1/(0.9 rc), rc^2)
+  d.bs_stride = bs_stride_for_kmax(d.bs_kmax);
   d.ppart_n = ppart_blocks(n);
   d.eparts_n = energy_blocks(n);
   Carver c{base, 0};

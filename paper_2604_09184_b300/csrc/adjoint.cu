@@ -254,12 +254,17 @@ __global__ void __launch_bounds__(ANT) k_kepler_vjp(int n, const double* xs6, co
 // ---------------------------------------------------------------------------
 // Bulirsch-Stoer adjoint: one CTA per group.
 // ---------------------------------------------------------------------------
+// Midpoint states of one substep: column j keeps z_0..z_2j at state index
+// j^2 - 1 + t, kmax^2 + 2 kmax states in all.
+__host__ __device__ constexpr int adj_nstates(int kmax) { return kmax * kmax + 2 * kmax; }
+__host__ __device__ constexpr int adj_sidx(int j, int t) { return j * j - 1 + t; }
+
 // Per-member-slot scratch (doubles): recorded substep starts (kSubCap x
-// (6 + 4)), midpoint states z[0..2 kmax] (6 each) and their adjoints, the
-// running adjoint (6 state + 1 mass), an accumulator (6) and a derivative
-// buffer (6).
+// (6 + 4)), the midpoint states of one substep and their adjoints, a
+// derivative buffer per column, f0 and its adjoint, the running adjoint
+// (6 state + 1 mass), an accumulator (6) and a mass accumulator per column.
 __host__ __device__ inline int adj_slot_stride(int kmax) {
-  return kSubCap * 10 + 2 * (2 * kmax + 1) * 6 + 6 + 1 + 6 + 6;
+  return kSubCap * 10 + 12 * adj_nstates(kmax) + 7 * kmax + 25;
 }
 
 struct AdjGroupArgs {
@@ -281,82 +286,88 @@ struct AdjGroupArgs {
   int* status;
 };
 
-// d/dt of z (all members) -> accumulate J^T w into out (6 per member),
-// J the Jacobian of (x, v) -> (v, a(x)) of the group (Eq. Ha restricted to
-// the group), w = (w_x, w_v); mass terms into lm_acc. Uses the members'
-// masses, critical radii and alive flags in the BsCtx working copies.
-__device__ void bs_vjp_f(const BsCtx& c, const double* z, const double* w, double* out,
-                         double* lm_acc, double scale) {
-  for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
-    if (!bs_alive(c, b)) continue;
-    const double* zb = z + 6 * b;
-    const double* wb = w + 6 * b;
-    double o[3] = {0.0, 0.0, 0.0};
-    // Kepler part: -mu (I / r^3 - 3 x x^T / r^5) w_v
-    const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
-    const double r = sqrt(r2);
-    const double ir3 = 1.0 / (r2 * r);
-    const double xw = zb[0] * wb[3] + zb[1] * wb[4] + zb[2] * wb[5];
-    for (int k = 0; k < 3; ++k) o[k] = -c.mu * (wb[3 + k] * ir3 - 3.0 * zb[k] * xw * ir3 / r2);
-    double am = 0.0;
-    const double mb = c.g[10 * b + 6], rcb = c.g[10 * b + 8];
-    for (int q = 0; q < c.M; ++q) {
-      if (q == b || !bs_alive(c, q)) continue;
-      const double* zq = z + 6 * q;
-      const double* wq = w + 6 * q;
-      const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
-      const double q2 = sep2(dx, dy, dz);
-      const double rc = fmax(rcb, c.g[10 * q + 8]);
-      if (q2 == 0.0 || !(q2 < rc * rc)) continue;
-      double p, dp_r;
-      pair_profile(q2, rc, 1, p, dp_r);
-      const double mq = c.g[10 * q + 6];
-      const double ux = mb * wq[3] - mq * wb[3], uy = mb * wq[4] - mq * wb[4],
-                   uz = mb * wq[5] - mq * wb[5];
-      const double du = dx * ux + dy * uy + dz * uz;
-      o[0] += c.G * (p * ux + dp_r * du * dx);
-      o[1] += c.G * (p * uy + dp_r * du * dy);
-      o[2] += c.G * (p * uz + dp_r * du * dz);
-      am -= c.G * p * (wq[3] * dx + wq[4] * dy + wq[5] * dz);
-    }
-    double* ob = out + 6 * b;
-    for (int k = 0; k < 3; ++k) {
-      ob[k] += scale * o[k];
-      ob[3 + k] += scale * wb[k];
-    }
-    lm_acc[b] += scale * am;
+// Right-hand side of the group's equations of motion (Eq. Ha restricted to
+// the group) for member b: f_b = (v_b, -mu x_b / r_b^3 + G sum_q m_q psi d_bq),
+// psi = (1 - w) / r^3 inside rc. z: states of all M members (6 each). Uses
+// the members' masses, critical radii and alive flags in the working copies.
+__device__ void grp_f(const BsCtx& c, const double* z, int b, double* fb) {
+  if (!bs_alive(c, b)) {
+    for (int k = 0; k < 6; ++k) fb[k] = 0.0;
+    return;
   }
+  const double* zb = z + 6 * b;
+  fb[0] = zb[3]; fb[1] = zb[4]; fb[2] = zb[5];
+  const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
+  const double r = sqrt(r2);
+  const double ks = -c.mu / (r2 * r);
+  double ax = ks * zb[0], ay = ks * zb[1], az = ks * zb[2];
+  for (int q = 0; q < c.M; ++q) {
+    if (q == b || !bs_alive(c, q)) continue;
+    const double* zq = z + 6 * q;
+    const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
+    const double q2 = sep2(dx, dy, dz);
+    const double rc = fmax(c.g[10 * b + 8], c.g[10 * q + 8]);
+    if (q2 == 0.0 || !(q2 < rc * rc)) continue;
+    double p, dp_r;
+    pair_profile(q2, rc, 1, p, dp_r);
+    const double f = c.G * c.g[10 * q + 6] * p;
+    ax += f * dx; ay += f * dy; az += f * dz;
+  }
+  fb[3] = ax; fb[4] = ay; fb[5] = az;
 }
 
-__device__ void bs_f(const BsCtx& c, const double* z, double* f) {
-  for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
-    double* fb = f + 6 * b;
-    if (!bs_alive(c, b)) {
-      for (int k = 0; k < 6; ++k) fb[k] = 0.0;
-      continue;
-    }
-    const double* zb = z + 6 * b;
-    fb[0] = zb[3]; fb[1] = zb[4]; fb[2] = zb[5];
-    const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
-    const double r = sqrt(r2);
-    const double ks = -c.mu / (r2 * r);
-    double ax = ks * zb[0], ay = ks * zb[1], az = ks * zb[2];
-    for (int q = 0; q < c.M; ++q) {
-      if (q == b || !bs_alive(c, q)) continue;
-      const double* zq = z + 6 * q;
-      const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
-      const double q2 = sep2(dx, dy, dz);
-      const double rc = fmax(c.g[10 * b + 8], c.g[10 * q + 8]);
-      if (q2 == 0.0 || !(q2 < rc * rc)) continue;
-      double p, dp_r;
-      pair_profile(q2, rc, 1, p, dp_r);
-      const double f = c.G * c.g[10 * q + 6] * p;
-      ax += f * dx; ay += f * dy; az += f * dz;
-    }
-    fb[3] = ax; fb[4] = ay; fb[5] = az;
+// out_b += scale (J^T w)_b and lm_b += scale (dF/dm_b)^T w for member b, J the
+// Jacobian of grp_f at the states z, w = (w_x, w_v) per member:
+//   (J^T w)_x,b = -mu (I / r^3 - 3 x x^T / r^5) w_v,b
+//                 + G sum_q T_bq (m_b w_v,q - m_q w_v,b),  T = psi I + (psi'/r) d d^T,
+//   (J^T w)_v,b = w_x,b,   dF/dm_b . w = G sum_q psi w_v,q . (x_b - x_q).
+__device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b, double* ob,
+                        double* lmb, double scale) {
+  if (!bs_alive(c, b)) return;
+  const double* zb = z + 6 * b;
+  const double* wb = w + 6 * b;
+  double o[3];
+  const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
+  const double r = sqrt(r2);
+  const double ir3 = 1.0 / (r2 * r);
+  const double xw = zb[0] * wb[3] + zb[1] * wb[4] + zb[2] * wb[5];
+  for (int k = 0; k < 3; ++k) o[k] = -c.mu * (wb[3 + k] * ir3 - 3.0 * zb[k] * xw * ir3 / r2);
+  double am = 0.0;
+  const double mb = c.g[10 * b + 6], rcb = c.g[10 * b + 8];
+  for (int q = 0; q < c.M; ++q) {
+    if (q == b || !bs_alive(c, q)) continue;
+    const double* zq = z + 6 * q;
+    const double* wq = w + 6 * q;
+    const double dx = zq[0] - zb[0], dy = zq[1] - zb[1], dz = zq[2] - zb[2];
+    const double q2 = sep2(dx, dy, dz);
+    const double rc = fmax(rcb, c.g[10 * q + 8]);
+    if (q2 == 0.0 || !(q2 < rc * rc)) continue;
+    double p, dp_r;
+    pair_profile(q2, rc, 1, p, dp_r);
+    const double mq = c.g[10 * q + 6];
+    const double ux = mb * wq[3] - mq * wb[3], uy = mb * wq[4] - mq * wb[4],
+                 uz = mb * wq[5] - mq * wb[5];
+    const double du = dx * ux + dy * uy + dz * uz;
+    o[0] += c.G * (p * ux + dp_r * du * dx);
+    o[1] += c.G * (p * uy + dp_r * du * dy);
+    o[2] += c.G * (p * uz + dp_r * du * dz);
+    am -= c.G * p * (wq[3] * dx + wq[4] * dy + wq[5] * dz);
   }
+  for (int k = 0; k < 3; ++k) {
+    ob[k] += scale * o[k];
+    ob[3 + k] += scale * wb[k];
+  }
+  *lmb += scale * am;
 }
 
+// One CTA per group: replay the group's integration from the saved state,
+// recording every accepted substep (bs_integrate_group with a BsRec), then
+// pull the adjoint back through the substeps, last first. Per substep: undo
+// the mergers that followed it (merge map x' = (m_a x_a + m_b x_b) / M,
+// M = m_a + m_b), replay the midpoint sequences of columns 1..k (k the
+// accepted column) keeping every state, and reverse them as a wave over the
+// columns; the Neville extrapolation is linear in the column results, with
+// weights c_j from the same recursion applied to unit vectors.
 __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
   __shared__ double s_red[ABNT];
   __shared__ int s_flags[2];
@@ -366,6 +377,8 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
   const int* goff = A.grp + 2;
   const int* gmem = A.grp + 2 + ng + 1;
   const int n = A.n;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int NS = adj_nstates(A.kmax);
   for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
     const int off = goff[grp];
     BsCtx c;
@@ -377,19 +390,21 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
     c.G = P.G;
     c.mu = P.mu;
     const int M = c.M;
-    double* slot = A.slot + (size_t)off * A.slot_stride;  // the group's contiguous slot block
-    // slot block layout (M members together): rec ys | ms | Rs | rcs | alv | z | lz | ly | lm | lin
-    double* r_ys = slot;
+    // the group's contiguous slot block, arrays of M members each
+    double* r_ys = A.slot + (size_t)off * A.slot_stride;
     double* r_ms = r_ys + (size_t)kSubCap * M * 6;
     double* r_Rs = r_ms + (size_t)kSubCap * M;
     double* r_rcs = r_Rs + (size_t)kSubCap * M;
     double* r_alv = r_rcs + (size_t)kSubCap * M;
-    double* zb = r_alv + (size_t)kSubCap * M;           // (2kmax+1) * 6M
-    double* lzb = zb + (size_t)(2 * A.kmax + 1) * 6 * M;  // (2kmax+1) * 6M
-    double* ly = lzb + (size_t)(2 * A.kmax + 1) * 6 * M;  // 6M
-    double* lmv = ly + 6 * M;                             // M
-    double* lin = lmv + M;                                // 6M
-    double* ftmp = lin + 6 * M;                           // 6M (derivative scratch)
+    double* zst = r_alv + (size_t)kSubCap * M;      // NS states x 6M
+    double* lzst = zst + (size_t)NS * 6 * M;        // NS states x 6M
+    double* fcol = lzst + (size_t)NS * 6 * M;       // kmax x 6M
+    double* f0 = fcol + (size_t)A.kmax * 6 * M;     // 6M
+    double* lf0 = f0 + 6 * M;                       // 6M
+    double* ly = lf0 + 6 * M;                       // 6M
+    double* lin = ly + 6 * M;                       // 6M
+    double* lmv = lin + 6 * M;                      // M
+    double* lmc = lmv + M;                          // kmax x M
     BsRec rec;
     rec.cap = kSubCap;
     rec.mcap = kMrgCap;
@@ -400,7 +415,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
     rec.mrg = A.mrg + (size_t)grp * kMrgCap * 3;
     rec.mst = A.mst + (size_t)grp * kMrgCap * 14;
     // forward replay from the saved state, recording the accepted substeps
-    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+    for (int b = tid; b < M; b += NT) {
       const int body = gmem[off + b];
       double* y = c.base + (size_t)b * c.stride + OY;
       for (int k = 0; k < 6; ++k) y[k] = A.xs6[(size_t)k * n + body];
@@ -408,7 +423,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
       g[6] = A.m0[body]; g[7] = A.R0[body]; g[8] = A.rc0[body]; g[9] = 1.0;
       bs_set_aux(c, b, P.G, g[6], g[8]);
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       rec.counts[0] = 0; rec.counts[1] = 0; rec.counts[2] = 0;
     }
     __syncthreads();
@@ -418,13 +433,13 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
     __syncthreads();
     if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
     if (st) {
-      if (threadIdx.x == 0) atomicCAS(A.status, 0, st);
+      if (tid == 0) atomicCAS(A.status, 0, st);
       continue;
     }
     const int nsub = rec.counts[0], nmrg = rec.counts[1];
     // adjoint at the end of the BS: members alive at the end take the step's
     // lambda; absorbed members start from zero
-    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+    for (int b = tid; b < M; b += NT) {
       const int body = gmem[off + b];
       const bool live = c.g[10 * b + 9] != 0.0;
       for (int k = 0; k < 3; ++k) {
@@ -438,7 +453,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
     for (int s = nsub - 1; s >= 0; --s) {
       // undo the mergers that followed substep s (last first)
       for (; mq >= 0 && rec.mrg[3 * mq] == s; --mq) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
           const int a = rec.mrg[3 * mq + 1], b = rec.mrg[3 * mq + 2];
           const double* ya = rec.mst + 14 * mq;
           const double* yb = ya + 6;
@@ -460,17 +475,21 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
         }
         __syncthreads();
       }
-      // working copies of masses, radii, critical radii and flags at the
-      // substep's start
-      for (int b = threadIdx.x; b < M; b += blockDim.x) {
+      const int kacc = rec.k[s];
+      const double H = rec.H[s];
+      // working copies at the substep's start; clear the adjoint buffers
+      for (int b = tid; b < M; b += NT) {
         const size_t o = (size_t)s * M + b;
         double* g = c.g + 10 * b;
         g[6] = r_ms[o]; g[7] = r_Rs[o]; g[8] = r_rcs[o]; g[9] = r_alv[o];
-        for (int k = 0; k < 6; ++k) lin[6 * b + k] = 0.0;
+        for (int k = 0; k < 6; ++k) {
+          zst[6 * b + k] = r_ys[6 * o + k];  // state (1, 0) doubles as y
+          lf0[6 * b + k] = 0.0;
+        }
+        for (int j = 1; j <= kacc; ++j) lmc[(j - 1) * M + b] = 0.0;
       }
-      const int kacc = rec.k[s];
-      const double H = rec.H[s];
-      if (threadIdx.x == 0) {
+      for (int e = tid; e < adj_nstates(kacc) * 6 * M; e += NT) lzst[e] = 0.0;
+      if (tid == 0) {
         // extrapolation weights: T_kk = sum_j cw[j] T_j1 (Neville is linear)
         for (int j0 = 1; j0 <= kacc; ++j0) {
           for (int j = 1; j <= kacc; ++j) {
@@ -484,69 +503,113 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
         }
       }
       __syncthreads();
-      for (int j = 1; j <= kacc; ++j) {
-        const int nsb = 2 * j;
-        const double hs = H / nsb;
-        // replay the midpoint sequence from the substep's start
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int k = 0; k < 6; ++k) zb[6 * b + k] = r_ys[((size_t)s * M + b) * 6 + k];
-        __syncthreads();
-        bs_f(c, zb, ftmp);
-        __syncthreads();
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int k = 0; k < 6; ++k) zb[6 * M + 6 * b + k] = zb[6 * b + k] + hs * ftmp[6 * b + k];
-        __syncthreads();
-        for (int mm = 1; mm < nsb; ++mm) {
-          bs_f(c, zb + (size_t)mm * 6 * M, ftmp);
-          __syncthreads();
-          for (int b = threadIdx.x; b < M; b += blockDim.x)
-            for (int k = 0; k < 6; ++k)
-              zb[(size_t)(mm + 1) * 6 * M + 6 * b + k] =
-                  zb[(size_t)(mm - 1) * 6 * M + 6 * b + k] + 2.0 * hs * ftmp[6 * b + k];
-          __syncthreads();
+      const double* y = zst;  // M states
+      for (int b = tid; b < M; b += NT) grp_f(c, y, b, f0 + 6 * b);
+      __syncthreads();
+      // replay: z_0 = y, z_1 = y + hs f0, z_{t+1} = z_{t-1} + 2 hs f(z_t)
+      for (int it = tid; it < kacc * M; it += NT) {
+        const int j = 1 + it / M, b = it % M;
+        const double hs = H / (2 * j);
+        double* z0 = zst + (size_t)adj_sidx(j, 0) * 6 * M + 6 * b;
+        double* z1 = zst + (size_t)adj_sidx(j, 1) * 6 * M + 6 * b;
+        for (int k = 0; k < 6; ++k) {
+          if (j > 1) z0[k] = y[6 * b + k];  // column 1's z_0 is y itself
+          z1[k] = y[6 * b + k] + hs * f0[6 * b + k];
         }
-        // reverse: out = (z_n + z_{n-1} + hs f(z_n)) / 2, weighted by cw[j]
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int m2 = 0; m2 <= nsb; ++m2)
-            for (int k = 0; k < 6; ++k) lzb[(size_t)m2 * 6 * M + 6 * b + k] = 0.0;
-        __syncthreads();
-        const double wj = cw[j];
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int k = 0; k < 6; ++k) {
-            const double lo = wj * ly[6 * b + k];
-            lzb[(size_t)nsb * 6 * M + 6 * b + k] += 0.5 * lo;
-            lzb[(size_t)(nsb - 1) * 6 * M + 6 * b + k] += 0.5 * lo;
-            ftmp[6 * b + k] = lo;  // w for the f-term
-          }
-        __syncthreads();
-        bs_vjp_f(c, zb + (size_t)nsb * 6 * M, ftmp, lzb + (size_t)nsb * 6 * M, lmv, 0.5 * hs);
-        __syncthreads();
-        for (int mm = nsb - 1; mm >= 1; --mm) {
-          // z_{mm+1} = z_{mm-1} + 2 hs f(z_mm)
-          double* lnext = lzb + (size_t)(mm + 1) * 6 * M;
-          for (int b = threadIdx.x; b < M; b += blockDim.x)
-            for (int k = 0; k < 6; ++k) lzb[(size_t)(mm - 1) * 6 * M + 6 * b + k] += lnext[6 * b + k];
-          __syncthreads();
-          bs_vjp_f(c, zb + (size_t)mm * 6 * M, lnext, lzb + (size_t)mm * 6 * M, lmv, 2.0 * hs);
-          __syncthreads();
+      }
+      __syncthreads();
+      for (int t = 1; t < 2 * kacc; ++t) {
+        const int j0 = t / 2 + 1;  // columns with t < 2j
+        const int ncol = kacc - j0 + 1;
+        for (int it = tid; it < ncol * M; it += NT) {
+          const int j = j0 + it / M, b = it % M;
+          grp_f(c, zst + (size_t)adj_sidx(j, t) * 6 * M, b, fcol + (size_t)(j - 1) * 6 * M + 6 * b);
         }
-        // z_1 = z_0 + hs f(z_0)
-        double* l1 = lzb + 6 * (size_t)M;
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int k = 0; k < 6; ++k) lzb[6 * b + k] += l1[6 * b + k];
         __syncthreads();
-        bs_vjp_f(c, zb, l1, lzb, lmv, hs);
-        __syncthreads();
-        for (int b = threadIdx.x; b < M; b += blockDim.x)
-          for (int k = 0; k < 6; ++k) lin[6 * b + k] += lzb[6 * b + k];
+        for (int it = tid; it < ncol * M; it += NT) {
+          const int j = j0 + it / M, b = it % M;
+          const double hs = H / (2 * j);
+          const double* zm = zst + (size_t)adj_sidx(j, t - 1) * 6 * M + 6 * b;
+          double* zn = zst + (size_t)adj_sidx(j, t + 1) * 6 * M + 6 * b;
+          const double* f = fcol + (size_t)(j - 1) * 6 * M + 6 * b;
+          for (int k = 0; k < 6; ++k) zn[k] = zm[k] + 2.0 * hs * f[k];
+        }
         __syncthreads();
       }
-      for (int b = threadIdx.x; b < M; b += blockDim.x)
+      // reverse, tau = 0: T_j = (z_2j + z_2j-1 + hs f(z_2j)) / 2 with
+      // lambda_T = cw_j lambda_Y
+      for (int it = tid; it < kacc * M; it += NT) {
+        const int j = 1 + it / M, b = it % M;
+        double* lzn = lzst + (size_t)adj_sidx(j, 2 * j) * 6 * M;
+        double* lzp = lzst + (size_t)adj_sidx(j, 2 * j - 1) * 6 * M;
+        for (int k = 0; k < 6; ++k) {
+          const double lT = cw[j] * ly[6 * b + k];
+          lzn[6 * b + k] += 0.5 * lT;
+          lzp[6 * b + k] += 0.5 * lT;
+        }
+      }
+      __syncthreads();
+      // the f-term of T: w = cw_j lambda_Y for every member; staged in fcol
+      for (int it = tid; it < kacc * M; it += NT) {
+        const int j = 1 + it / M, b = it % M;
+        for (int k = 0; k < 6; ++k) fcol[(size_t)(j - 1) * 6 * M + 6 * b + k] = cw[j] * ly[6 * b + k];
+      }
+      __syncthreads();
+      for (int it = tid; it < kacc * M; it += NT) {
+        const int j = 1 + it / M, b = it % M;
+        const double hs = H / (2 * j);
+        grp_vjp(c, zst + (size_t)adj_sidx(j, 2 * j) * 6 * M, fcol + (size_t)(j - 1) * 6 * M, b,
+                lzst + (size_t)adj_sidx(j, 2 * j) * 6 * M + 6 * b, lmc + (j - 1) * M + b,
+                0.5 * hs);
+      }
+      __syncthreads();
+      // tau = 1 .. 2k - 1: column j reverses z_{m+1} = z_{m-1} + 2 hs f(z_m) at m = 2j - tau
+      for (int tau = 1; tau < 2 * kacc; ++tau) {
+        const int j0 = (tau + 2) / 2;  // columns with m = 2j - tau >= 1
+        const int ncol = kacc - j0 + 1;
+        for (int it = tid; it < ncol * M; it += NT) {
+          const int j = j0 + it / M, b = it % M;
+          const int m = 2 * j - tau;
+          const double hs = H / (2 * j);
+          const double* lnext = lzst + (size_t)adj_sidx(j, m + 1) * 6 * M;
+          double* lprev = lzst + (size_t)adj_sidx(j, m - 1) * 6 * M + 6 * b;
+          for (int k = 0; k < 6; ++k) lprev[k] += lnext[6 * b + k];
+          grp_vjp(c, zst + (size_t)adj_sidx(j, m) * 6 * M, lnext, b,
+                  lzst + (size_t)adj_sidx(j, m) * 6 * M + 6 * b, lmc + (j - 1) * M + b,
+                  2.0 * hs);
+        }
+        __syncthreads();
+      }
+      // z_1 = z_0 + hs f0 and z_0 = y: lambda_y = sum_j (lambda_z0 + lambda_z1),
+      // lambda_f0 = sum_j hs_j lambda_z1 (columns in ascending order)
+      for (int b = tid; b < M; b += NT) {
+        double acc[6] = {0, 0, 0, 0, 0, 0}, af[6] = {0, 0, 0, 0, 0, 0};
+        double am = 0.0;
+        for (int j = 1; j <= kacc; ++j) {
+          const double hs = H / (2 * j);
+          const double* l0 = lzst + (size_t)adj_sidx(j, 0) * 6 * M + 6 * b;
+          const double* l1 = lzst + (size_t)adj_sidx(j, 1) * 6 * M + 6 * b;
+          for (int k = 0; k < 6; ++k) {
+            acc[k] += l0[k] + l1[k];
+            af[k] += hs * l1[k];
+          }
+          am += lmc[(j - 1) * M + b];
+        }
+        for (int k = 0; k < 6; ++k) {
+          lin[6 * b + k] = acc[k];
+          lf0[6 * b + k] = af[k];
+        }
+        lmv[b] += am;
+      }
+      __syncthreads();
+      for (int b = tid; b < M; b += NT) grp_vjp(c, y, lf0, b, lin + 6 * b, lmv + b, 1.0);
+      __syncthreads();
+      for (int b = tid; b < M; b += NT)
         for (int k = 0; k < 6; ++k) ly[6 * b + k] = lin[6 * b + k];
       __syncthreads();
     }
     // lambda at the saved state of the members
-    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+    for (int b = tid; b < M; b += NT) {
       const int body = gmem[off + b];
       for (int k = 0; k < 3; ++k) {
         A.lx[k][body] = ly[6 * b + k];
@@ -722,7 +785,7 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
   int* alive0 = c.take<int>(n);
   int* alive1 = c.take<int>(n);
   int* status = c.take<int>(4);
-  double* gscr = c.take<double>((size_t)n * (6 * (4 + 2 * kmax) + 4));
+  double* gscr = c.take<double>((size_t)n * bs_stride_for_kmax(kmax));
   double* gnew = c.take<double>((size_t)n * 10);
   double* slot = c.take<double>((size_t)n * stride);
   double* H = c.take<double>((size_t)n * kSubCap);
@@ -846,7 +909,7 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
   AdjGroupArgs A;
   A.n = n;
   A.kmax = P.bs_kmax;
-  A.bs_stride = 6 * (4 + 2 * P.bs_kmax) + 4;
+  A.bs_stride = bs_stride_for_kmax(P.bs_kmax);
   A.slot_stride = a->slot_stride;
   A.grp = r.grp;
   A.xs6 = r.xs6;

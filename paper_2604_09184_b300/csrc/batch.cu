@@ -533,7 +533,7 @@ struct BCarver {
 
 int bs_stride_for(const nb_params& p) {
   const int kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
-  return 6 * (4 + 2 * kmax) + 4;
+  return bs_stride_for_kmax(kmax);
 }
 
 struct Snap {

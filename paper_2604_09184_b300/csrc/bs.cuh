@@ -11,17 +11,26 @@ namespace nb {
 
 // ---------------------------------------------------------------------------
 // Bulirsch-Stoer for one group per CTA.
-// Scratch per member slot (stride doubles): y[6] | zm[6] | zc[6] | f[6] |
-// T[2][kmax][6] | aux[4] = (G m, 1 / (0.9 rc), rc^2, unused). Working copies
-// of m, R, rc, alive live in gnew[slot*10+6..9].
+// Scratch per member slot (bs_stride_for_kmax(kmax) doubles):
+//   y[6] | f0[6] | per extrapolation column j = 1..kmax: zm[6] zc[6] f[6] |
+//   T[2][kmax][6] | aux[4] = (G m, 1 / (0.9 rc), rc^2, unused).
+// Working copies of m, R, rc, alive live in gnew[slot*10+6..9].
 //
 // A group of two bodies keeps only two lanes of its CTA busy, and every FP64
 // warp instruction holds the B300 FP64 pipe for the full warp, so the solver's
-// speed is its FP64 instruction count per derivative: the right-hand side uses
-// the seeded reciprocal roots and reciprocals of nb_internal.cuh instead of
-// sqrt and divisions, and per-member constants are precomputed.
+// speed is its count of dependent FP64 warp instructions. Two consequences:
+// the right-hand side uses the seeded reciprocal roots and reciprocals of
+// nb_internal.cuh and precomputed per-member constants, and the modified-
+// midpoint sequences of the extrapolation columns, which are independent of
+// one another, advance together in separate lanes (a "wave" over columns):
+// an attempt that converges at column J takes 2J + 1 dependent derivative
+// evaluations instead of J^2 + 2J. Each column's arithmetic, the Neville
+// table and the acceptance test are the same as column-after-column, so the
+// result does not depend on how many columns run at once.
 // ---------------------------------------------------------------------------
-constexpr int OY = 0, OZM = 6, OZC = 12, OF = 18, OT = 24;
+constexpr int OY = 0, OF0 = 6;
+constexpr int CZM = 0, CZC = 6, CF = 12;  // fields of a column block
+
 
 struct BsCtx {
   double* base;  // scratch of the group's first slot
@@ -33,7 +42,7 @@ struct BsCtx {
 __device__ __forceinline__ bool bs_alive(const BsCtx& c, int b) { return c.g[10 * b + 9] != 0.0; }
 
 __device__ __forceinline__ double* bs_aux(const BsCtx& c, int b) {
-  return c.base + (size_t)b * c.stride + OT + 12 * c.kmax;
+  return c.base + (size_t)b * c.stride + bs_off_T(c.kmax) + 12 * c.kmax;
 }
 
 __device__ __forceinline__ void bs_set_aux(const BsCtx& c, int b, double G, double m, double rc) {
@@ -58,10 +67,10 @@ __device__ __forceinline__ double close_weight(double qq, double rc, double inv0
   return 1.0 - (f * rs - qq * dKdy * inv09);
 }
 
-// f = d/dt of field fo for member b (Eq. Ha restricted to the group).
-static __device__ void bs_deriv(const BsCtx& c, int fo, int b) {
+// Field fout of member b = d/dt of field fo (Eq. Ha restricted to the group).
+static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
   const double* yb = c.base + (size_t)b * c.stride + fo;
-  double* fb = c.base + (size_t)b * c.stride + OF;
+  double* fb = c.base + (size_t)b * c.stride + fout;
   if (!bs_alive(c, b)) {
     for (int k = 0; k < 6; ++k) fb[k] = 0.0;
     return;
@@ -176,13 +185,16 @@ struct BsTally {
 };
 
 // Integrate H_A restricted to one group over h with all threads of the
-// calling CTA (any blockDim): Gragg modified midpoint with n_k = 2k substeps,
-// Neville extrapolation in the substep squared, acceptance at k >= 3 when
+// calling CTA (any blockDim): Gragg modified midpoint with n_j = 2j substeps,
+// Neville extrapolation in the substep squared, acceptance at j >= 3 when
 // every live body's position and velocity changes between the two highest
 // columns are within bs_tol of its own max-norm; halving on failure at k_max,
 // doubling back after an early success on an aligned boundary; perfect
-// merging scan after every accepted substep. The group state starts in the
-// y fields and ends there. s_red: shared scratch of blockDim.x doubles;
+// merging scan after every accepted substep. Columns run in windows of W
+// (all of them for small groups): within a window every column advances one
+// midpoint substep per wave step, and column j completes at wave step 2j,
+// when its Neville row is built and tested. The group state starts in the y
+// fields and ends there. s_red: shared scratch of blockDim.x doubles;
 // s_flags: two shared ints. Returns 0, NB_E_NOCONV or NB_E_TIMEOUT (same in
 // every thread); *El (thread 0) receives the energy removed by mergers.
 static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
@@ -190,7 +202,14 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
                                          BsRec* rec = nullptr) {
   int rec_n = 0;  // accepted substeps recorded (the same in every thread)
   const int kmax = c.kmax;
+  const int M = c.M;
   const int NT = blockDim.x;
+  const int tid = threadIdx.x;
+  const int offT = bs_off_T(kmax);
+  // columns per window: enough (column, member) items to fill about two
+  // passes of the CTA, never fewer than one column
+  int W = (2 * NT) / (M > 0 ? M : 1);
+  W = W < 1 ? 1 : (W > kmax ? kmax : W);
   int level = 0;
   long long done = 0;
   int status = 0;
@@ -199,10 +218,10 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
   while (done < (1ll << level)) {
     const double H = ldexp(h, -level);
     if (rec && rec_n < rec->cap) {  // stage the substep's start (kept if it is accepted)
-      for (int b = threadIdx.x; b < c.M; b += NT) {
+      for (int b = tid; b < M; b += NT) {
         const double* y = c.base + (size_t)b * c.stride + OY;
         const double* g = c.g + 10 * b;
-        const size_t o = (size_t)rec_n * c.M + b;
+        const size_t o = (size_t)rec_n * M + b;
         for (int k = 0; k < 6; ++k) rec->ys[6 * o + k] = y[k];
         rec->ms[o] = g[6];
         rec->Rs[o] = g[7];
@@ -210,85 +229,104 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
         rec->alv[o] = g[9];
       }
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       s_flags[0] = 0;
       s_flags[1] = 0;
     }
-    for (int j = 1; j <= kmax; ++j) {
-      const int nsub = 2 * j;
-      const double hs = H / nsub;
-      for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OY, b);
-      __syncthreads();
-      for (int b = threadIdx.x; b < c.M; b += NT) {
+    // f0 = f(y), shared by every column
+    for (int b = tid; b < M; b += NT) bs_deriv(c, OY, OF0, b);
+    __syncthreads();
+    tally.derivs += 1;
+    for (int ja = 1; ja <= kmax && !s_flags[0]; ja += W) {
+      const int jb = ja + W - 1 < kmax ? ja + W - 1 : kmax;
+      const int nw = jb - ja + 1;
+      // start the window's columns: z0 = y, z1 = y + hs f0
+      for (int it = tid; it < nw * M; it += NT) {
+        const int j = ja + it / M, b = it % M;
         double* s = c.base + (size_t)b * c.stride;
+        double* col = s + bs_off_col(j);
+        const double hs = H / (2 * j);
         for (int k = 0; k < 6; ++k) {
-          s[OZM + k] = s[OY + k];
-          s[OZC + k] = s[OY + k] + hs * s[OF + k];
+          col[CZM + k] = s[OY + k];
+          col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
         }
       }
       __syncthreads();
-      for (int m = 1; m < nsub; ++m) {
-        for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OZC, b);
+      for (int t = 1; t <= 2 * jb; ++t) {
+        // columns still running at wave step t: 2j >= t
+        const int j0 = max(ja, (t + 1) / 2);
+        const int ncol = jb - j0 + 1;
+        for (int it = tid; it < ncol * M; it += NT) {
+          const int j = j0 + it / M, b = it % M;
+          bs_deriv(c, bs_off_col(j) + CZC, bs_off_col(j) + CF, b);
+        }
         __syncthreads();
-        for (int b = threadIdx.x; b < c.M; b += NT) {
+        tally.derivs += ncol;
+        for (int it = tid; it < ncol * M; it += NT) {
+          const int j = j0 + it / M, b = it % M;
           double* s = c.base + (size_t)b * c.stride;
-          for (int k = 0; k < 6; ++k) {
-            const double zn = s[OZM + k] + 2.0 * hs * s[OF + k];
-            s[OZM + k] = s[OZC + k];
-            s[OZC + k] = zn;
-          }
-        }
-        __syncthreads();
-      }
-      for (int b = threadIdx.x; b < c.M; b += NT) bs_deriv(c, OZC, b);
-      __syncthreads();
-      tally.derivs += nsub + 1;
-      double emax = 0.0;
-      for (int b = threadIdx.x; b < c.M; b += NT) {
-        double* s = c.base + (size_t)b * c.stride;
-        double* Tc = s + OT + (j & 1) * kmax * 6;
-        double* Tp = s + OT + ((j - 1) & 1) * kmax * 6;
-        for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (s[OZC + k] + s[OZM + k] + hs * s[OF + k]);
-        for (int q = 1; q < j; ++q) {
-          // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
-          const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
-          for (int k = 0; k < 6; ++k) {
-            const double t = Tc[6 * (q - 1) + k];
-            Tc[6 * q + k] = __fma_rn(t - Tp[6 * (q - 1) + k], inv, t);
-          }
-        }
-        if (j >= 3 && bs_alive(c, b)) {
-          const double* A = Tc + 6 * (j - 1);
-          const double* B = Tc + 6 * (j - 2);
-          for (int part = 0; part < 2; ++part) {
-            double dm = 0.0, ym = 0.0;
-            for (int k = 3 * part; k < 3 * part + 3; ++k) {
-              dm = fmax(dm, fabs(A[k] - B[k]));
-              ym = fmax(ym, fabs(A[k]));
+          double* col = s + bs_off_col(j);
+          const double hs = H / (2 * j);
+          if (t < 2 * j) {
+            for (int k = 0; k < 6; ++k) {
+              const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
+              col[CZM + k] = col[CZC + k];
+              col[CZC + k] = zn;
             }
-            emax = fmax(emax, dm / (ym + 1e-300));
+          } else {  // t == 2j: the column's result T_j1
+            double* Tc = s + offT + (j & 1) * kmax * 6;
+            for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (col[CZC + k] + col[CZM + k] + hs * col[CF + k]);
           }
         }
-      }
-      s_red[threadIdx.x] = emax;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double e = 0.0;
-        for (int t = 0; t < NT; ++t) e = fmax(e, s_red[t]);
-        if (j >= 3 && e <= P.bs_tol) {
-          s_flags[0] = 1;
-          s_flags[1] = j;
-        }
-      }
-      __syncthreads();
-      if (s_flags[0]) {
-        for (int b = threadIdx.x; b < c.M; b += NT) {
+        __syncthreads();
+        if ((t & 1) || t / 2 < ja) continue;
+        const int j = t / 2;  // column j is complete: Neville row j and the test
+        double emax = 0.0;
+        for (int b = tid; b < M; b += NT) {
           double* s = c.base + (size_t)b * c.stride;
-          const double* Tc = s + OT + (j & 1) * kmax * 6 + 6 * (j - 1);
-          for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
+          double* Tc = s + offT + (j & 1) * kmax * 6;
+          double* Tp = s + offT + ((j - 1) & 1) * kmax * 6;
+          for (int q = 1; q < j; ++q) {
+            // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
+            const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+            for (int k = 0; k < 6; ++k) {
+              const double tq = Tc[6 * (q - 1) + k];
+              Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
+            }
+          }
+          if (j >= 3 && bs_alive(c, b)) {
+            const double* A = Tc + 6 * (j - 1);
+            const double* B = Tc + 6 * (j - 2);
+            for (int part = 0; part < 2; ++part) {
+              double dm = 0.0, ym = 0.0;
+              for (int k = 3 * part; k < 3 * part + 3; ++k) {
+                dm = fmax(dm, fabs(A[k] - B[k]));
+                ym = fmax(ym, fabs(A[k]));
+              }
+              emax = fmax(emax, dm / (ym + 1e-300));
+            }
+          }
+        }
+        s_red[tid] = emax;
+        __syncthreads();
+        if (tid == 0) {
+          double e = 0.0;
+          for (int q = 0; q < NT; ++q) e = fmax(e, s_red[q]);
+          if (j >= 3 && e <= P.bs_tol) {
+            s_flags[0] = 1;
+            s_flags[1] = j;
+          }
         }
         __syncthreads();
-        break;
+        if (s_flags[0]) {
+          for (int b = tid; b < M; b += NT) {
+            double* s = c.base + (size_t)b * c.stride;
+            const double* Tc = s + offT + (j & 1) * kmax * 6 + 6 * (j - 1);
+            for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
+          }
+          __syncthreads();
+          break;
+        }
       }
     }
     ++attempts;
@@ -297,7 +335,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
       ++done;
       ++tally.substeps;
       if (rec) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
           if (rec_n < rec->cap) {
             rec->H[rec_n] = H;
             rec->k[rec_n] = kacc;
@@ -308,7 +346,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
         ++rec_n;
       }
       if (P.merge) {
-        if (threadIdx.x == 0) bs_merge_scan(c, P, El, &merges, rec, rec_n - 1);
+        if (tid == 0) bs_merge_scan(c, P, El, &merges, rec, rec_n - 1);
         __syncthreads();
       }
       if (level > 0 && (done & 1) == 0 && kacc <= kmax - 2) {
@@ -331,7 +369,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
     __syncthreads();
   }
   tally.merges += merges;
-  if (rec && threadIdx.x == 0) rec->counts[0] = rec_n;
+  if (rec && tid == 0) rec->counts[0] = rec_n;
   __syncthreads();
   return status;
 }

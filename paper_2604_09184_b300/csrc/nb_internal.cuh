@@ -15,6 +15,12 @@ constexpr int kMaxBsK = 12;          // upper bound on bs_kmax
 constexpr int kStatN = 12;           // device statistics counters
 constexpr double kDeadOffset = 1e6;  // absorbed bodies sit at (1e6 (id + 1), 0, 0) AU
 
+// Bulirsch-Stoer scratch per group member (doubles): y[6] | f0[6] | per
+// extrapolation column j = 1..kmax: zm[6] zc[6] f[6] | T[2][kmax][6] | aux[4].
+__host__ __device__ constexpr int bs_off_col(int j) { return 12 + 18 * (j - 1); }
+__host__ __device__ constexpr int bs_off_T(int kmax) { return 12 + 18 * kmax; }
+__host__ __device__ constexpr int bs_stride_for_kmax(int kmax) { return 16 + 30 * kmax; }
+
 enum StatIdx {
   ST_STEPS = 0,
   ST_FORCE_EVALS,
