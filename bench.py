@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="steps of the adjoint leg (2000 is the workload; fewer for profiling)")
+    ap.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval")
     ap.add_argument("--precision", choices=["fp64", "mixed", "ds"], default="fp64",
                     help="kick precision of the timed run (profiling); the line's value is fp64")
     return ap.parse_args()
@@ -64,6 +67,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of every rank's value (the slowest rank's time); the
+    value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Units processed by all ranks (replicas: each rank its own copy) per
+    second of the slowest rank."""
+    return world * units_per_rank_step * steps / (max_ms * 1e-3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -249,12 +270,9 @@ def run_ours(args):
     total_ms = sum(step_ms)
     tm = sysm.timing()
     gpu_launches = tm["launches"] - launches0
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_per_step = total_ms / max(args.steps, 1)
-    value = world * pps * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(pps, args.steps, world, total_ms)
     kick_ms = tm["kick_ms"] / max(tm["kick_launches"], 1)
     st = sysm.stats()
 
@@ -288,7 +306,7 @@ def run_ours(args):
 
     adjoint = None
     if not args.no_adjoint:
-        adjoint = run_adjoint(nb, torch, stream)
+        adjoint = run_adjoint(nb, torch, stream, args.adjoint_steps, args.adjoint_every)
 
     # end to end through the C ABI with host buffers: per step, load the state
     # from pinned host memory, step, read the state back to pinned host memory
@@ -383,6 +401,7 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 50
+    bal = b.balance()  # the last 25-step launch
     st = b.stats()
     del b
     # single-system path on a random sample of the same systems
@@ -411,6 +430,9 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
             "single_system_path_ms_per_step_est": single_ms, "speedup_vs_single": single_ms / ms,
             "speedup_vs_single_one_call_per_step": single_ms / ms_call,
             "single_sample": int(len(pick)), "bs_substeps": st["bs_substeps"],
+            "load_balance": {"efficiency": bal["efficiency"], "ctas": bal["ctas"],
+                             "max_cta_ms": bal["max_cta_ms"],
+                             "definition": "sum of CTA busy times / (CTAs x longest), last launch"},
             "groups": st["groups"], "merges": st["merges"]}
 
 

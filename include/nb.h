@@ -58,7 +58,7 @@ typedef struct {
   double vel_factor;   /* Eq. rcrit, default 0.4 */
   int vel_mode;        /* 0: |v - v_circ(x)| (default); 1: |v| */
   int merge;           /* 1: perfect merging on contact (default) */
-  int precision;       /* NB_PREC_FP64 (default) or NB_PREC_MIXED */
+  int precision;       /* NB_PREC_FP64 (default), NB_PREC_MIXED or NB_PREC_DS */
   int kepler_max_iter; /* Kepler iteration cap, default 30 */
   double bs_tol;       /* Bulirsch-Stoer relative tolerance, default 1e-14 */
   int bs_kmax;         /* extrapolation columns (substeps 2k), default 8, at most 12 */
@@ -66,6 +66,13 @@ typedef struct {
   int pair_capacity;   /* flagged-pair buffer, pairs; 0 = max(4096, 4n) */
   int log_capacity;    /* encounter-log entries per nb_step call; 0 = 1<<20 */
   int kick_split;      /* j-chunks per i-tile in the kick; 0 = automatic */
+  int rcrit_refresh;   /* cadence of Eq. rcrit. 0 (default): rc from the initial state, recomputed
+                          only for a merged survivor, so one force evaluation per step serves the
+                          step's end and the next step's start. 1: rc recomputed for every body
+                          from its state at the start of every step, and the force and flags
+                          re-evaluated with the new radii (two evaluations per step). Only
+                          nb_init_system / nb_step take 1; the batch and adjoint entry points
+                          reject it (NB_E_INVALID). */
 } nb_params;
 
 typedef struct {
@@ -197,6 +204,16 @@ int nb_batch_get_state(nb_batch* b, double* x, double* v, double* m, double* R, 
  * arrays of nsys. */
 int nb_batch_energy(nb_batch* b, double* E, double* E_lost);
 int nb_batch_stats(nb_batch* b, nb_stats_t* out);
+
+/* Time budget of one persistent launch: a CTA takes no further system once it
+ * has run longer than max_ms_per_launch, and the call then returns
+ * NB_E_TIMEOUT with the state rolled back to the call's start (0 = no budget,
+ * the default). Keeps any launch bounded on a shared GPU. */
+int nb_batch_set_budget(nb_batch* b, double max_ms_per_launch);
+
+/* Load balance of the last launch: efficiency = sum over CTAs of their busy
+ * time / (CTAs x the longest), the longest CTA time in ms, and the CTA count. */
+int nb_batch_balance(nb_batch* b, double* efficiency, double* max_cta_ms, int* ctas);
 void nb_batch_destroy(nb_batch* b);
 
 /* ---------------------------------------------------------------------
@@ -213,6 +230,18 @@ size_t nb_kick_scratch_bytes(int n, int split);
 int nb_kick(int n, const double* x, const double* m, const double* rc, double G, int precision,
             int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,
             size_t scratch_bytes, void* stream);
+
+/* The kick of nb_kick() for the target rows row0 <= i < row1 only, every one
+ * of the n bodies acting on them: the unit of a row-sharded kick (each
+ * device owning a block of rows after gathering all positions). a receives
+ * (row1 - row0) x 3 doubles, row i at a[3 (i - row0)]; pairs_ij the flagged
+ * pairs (i, j), i < j, with i in the block. With the same n and split the
+ * rows are bit-identical to those of nb_kick(), so blocks that partition
+ * 0..n-1 reproduce the full kick and its pair set. NB_E_INVALID unless
+ * 0 <= row0 < row1 <= n; scratch and errors as nb_kick(). */
+int nb_kick_rows(int n, int row0, int row1, const double* x, const double* m, const double* rc,
+                 double G, int precision, int split, double* a, int* pairs_ij, int cap,
+                 int* npairs, void* scratch, size_t scratch_bytes, void* stream);
 
 /* The kick of nb_kick() for callers that cannot allocate device memory (a
  * framework allocator owns the device, allocation is forbidden after

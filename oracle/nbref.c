@@ -269,6 +269,7 @@ void nbref_default_params(nbref_params* p) {
   p->bs_kmax = 8;
   p->bs_max_halvings = 20;
   p->kepler_max_iter = 30;
+  p->rcrit_refresh = 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -749,6 +750,15 @@ static int one_step(nbref_system* s, double h) {
   int n = s->n;
   const nbref_params* p = &s->p;
   double mu = p->G * p->m0;
+  if (p->rcrit_refresh) {
+    /* Eq. rcrit evaluated afresh for every body at the start of the step;
+     * the cached force and flags are then re-evaluated with the new radii. */
+    for (int i = 0; i < n; ++i)
+      if (s->alive[i]) s->rc[i] = nbref_rcrit(p, s->x + 3 * i, s->v + 3 * i, s->m[i]);
+    s->fprev.n = 0;
+    forces_flags(n, s->x, s->m, s->rc, s->alive, p->G, s->a, &s->fprev);
+    s->st.force_evals++;
+  }
   kick(s, 0.5 * h);
   momentum_drift(s, 0.5 * h);
   size_t b3 = sizeof(double) * 3 * (size_t)n;

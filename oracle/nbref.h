@@ -37,6 +37,7 @@ typedef struct {
   int bs_kmax;         /* extrapolation columns (substep sequence n_k = 2k) */
   int bs_max_halvings; /* cap on substep halvings inside one step */
   int kepler_max_iter; /* cap on Kepler-equation iterations */
+  int rcrit_refresh;   /* 0: r_crit at start and for merged survivors; 1: every step (see step) */
 } nbref_params;
 
 typedef struct {

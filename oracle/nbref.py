@@ -29,6 +29,7 @@ class RefParams(C.Structure):
         ("bs_kmax", C.c_int),
         ("bs_max_halvings", C.c_int),
         ("kepler_max_iter", C.c_int),
+        ("rcrit_refresh", C.c_int),
     ]
 
 

@@ -104,6 +104,7 @@ Phys make_phys(const nb_params& p) {
   P.kepler_max_iter = p.kepler_max_iter;
   P.bs_kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
   P.bs_max_halvings = p.bs_max_halvings > 40 ? 40 : p.bs_max_halvings;
+  P.rcrit_refresh = p.rcrit_refresh;
   return P;
 }
 
@@ -114,6 +115,7 @@ bool params_ok(const nb_params* p) {
   if (p->precision < NB_PREC_FP64 || p->precision > NB_PREC_DS) return false;
   if (p->kepler_max_iter < 1 || p->bs_max_halvings < 0 || !(p->bs_tol > 0.0)) return false;
   if (p->pair_capacity < 0 || p->log_capacity < 0 || p->kick_split < 0) return false;
+  if (p->rcrit_refresh != 0 && p->rcrit_refresh != 1) return false;
   return true;
 }
 
@@ -201,6 +203,7 @@ void nb_default_params(nb_params* p) {
   p->pair_capacity = 0;
   p->log_capacity = 0;
   p->kick_split = 0;
+  p->rcrit_refresh = 0;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {
@@ -332,8 +335,17 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       s->events->push_back(e);
     }
   }
-  launch_open_h(d, dt, s->st);
+  const int refresh = s->P.rcrit_refresh;
+  if (!refresh) launch_open_h(d, dt, s->st);
   for (int k = 0; k < nsteps; ++k) {
+    if (refresh) {
+      // Eq. rcrit at the step's start, then the cached force and flags anew
+      launch_refresh_rcrit(d, s->P, s->st);
+      launch_kick(d, s->P, 0, s->st);
+      launch_finish(d, s->P, 0, s->st);
+      launch_fsal_init(d, s->st);
+      launch_open_h(d, dt, s->st);
+    }
     launch_drift_h(d, s->P, dt, s->st);
     if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k], s->st));
     launch_kick(d, s->P, 0, s->st);
@@ -343,14 +355,14 @@ int nb_step(nb_system* s, int nsteps, double dt) {
     launch_finish(d, s->P, 1, s->st);
     launch_scatter(d, s->P, s->st);
     launch_member_kick(d, s->P, s->st);
-    launch_close_h(d, s->P, dt, k == nsteps - 1, s->st);
+    launch_close_h(d, s->P, dt, refresh || k == nsteps - 1, s->st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e, "nb_step launch");
   Ctrl c;
   rc = read_ctrl(s, &c);
   if (rc) return rc;
-  s->launches += 1 + 8LL * nsteps;
+  s->launches += refresh ? 14LL * nsteps : 1 + 8LL * nsteps;
   if (s->timing) {
     for (int k = 0; k < nsteps; ++k) {
       float ms = 0.f;
@@ -561,11 +573,12 @@ size_t nb_kick_scratch_bytes(int n, int split) {
   return b;
 }
 
-int nb_kick(int n, const double* x, const double* m, const double* rc, double G, int precision,
-            int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,
-            size_t scratch_bytes, void* stream) {
+int nb_kick_rows(int n, int row0, int row1, const double* x, const double* m, const double* rc,
+                 double G, int precision, int split, double* a, int* pairs_ij, int cap,
+                 int* npairs, void* scratch, size_t scratch_bytes, void* stream) {
   nb_system* s = nullptr;  // for NB_CU
   if (n < 1 || !x || !m || !rc || !a || cap < 0 || (cap > 0 && !pairs_ij)) return NB_E_INVALID;
+  if (row0 < 0 || row1 > n || row0 >= row1) return NB_E_INVALID;
   if (precision < NB_PREC_FP64 || precision > NB_PREC_DS) return NB_E_INVALID;
   const int S = split > 0 ? split : auto_split(n);
   if (!scratch || scratch_bytes < nb_kick_scratch_bytes(n, S) || ((uintptr_t)scratch & 255))
@@ -582,15 +595,22 @@ int nb_kick(int n, const double* x, const double* m, const double* rc, double G,
   Ctrl* ctrl = (Ctrl*)p;
   NB_CU(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
   launch_raw_prep(n, x, rc, sx, sy, sz, src2, st);
-  launch_kick_raw(n, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij, cap, ctrl,
-                  st);
-  launch_raw_finish(n, S, kpart, G, a, st);
+  launch_kick_raw(n, row0, row1, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij,
+                  cap, ctrl, st);
+  launch_raw_finish(n, row0, row1, S, kpart, G, a, st);
   int cnt = 0;
   NB_CU(cudaMemcpyAsync(&cnt, &ctrl->n_ftrial, sizeof(int), cudaMemcpyDeviceToHost, st));
   NB_CU(cudaStreamSynchronize(st));
   NB_CU(cudaGetLastError());
   if (npairs) *npairs = cnt;
   return cnt > cap ? NB_E_OVERFLOW : NB_OK;
+}
+
+int nb_kick(int n, const double* x, const double* m, const double* rc, double G, int precision,
+            int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,
+            size_t scratch_bytes, void* stream) {
+  return nb_kick_rows(n, 0, n, x, m, rc, G, precision, split, a, pairs_ij, cap, npairs, scratch,
+                      scratch_bytes, stream);
 }
 
 int nb_kepler_drift(int n, double mu, double* x, double* v, double dt, int max_iter,

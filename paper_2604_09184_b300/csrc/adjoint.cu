@@ -931,7 +931,8 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
 extern "C" {
 
 size_t nb_adjoint_workspace_bytes(const nb_params* p, int n, int nsteps, int checkpoint_every) {
-  if (!p || n < 1 || nsteps < 1 || checkpoint_every < 1 || nb_workspace_bytes(p, n) == 0)
+  if (!p || n < 1 || nsteps < 1 || checkpoint_every < 1 || nb_workspace_bytes(p, n) == 0 ||
+      p->rcrit_refresh != 0)
     return 0;
   return adj_layout(*p, n, nsteps, checkpoint_every, nullptr, nullptr);
 }

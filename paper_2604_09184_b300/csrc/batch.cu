@@ -37,7 +37,18 @@ struct BatchDev {
   int* queue;       // work counter, reset before each launch
   int* status;      // [0] first error, [1] system index
   unsigned long long* stats;
+  unsigned long long* cta_ns;  // per CTA of the last launch: ns from its start to its exit
+  int cta_cap;
+  const long long* budget_ns;  // per-launch time budget of a CTA in ns (0: none)
 };
+
+constexpr int kCtaCap = 4096;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Shared-memory layout for nmax bodies and NT threads.
 struct BSmem {
@@ -409,9 +420,16 @@ __global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
   __shared__ int s_next, s_stop;
   BsTally bt{0, 0, 0, 0};
   SysTally st{0, 0, 0, 0};
+  const unsigned long long t0 = global_ns();
+  const long long budget = *B.budget_ns;
   for (;;) {
     if (threadIdx.x == 0) {
       s_stop = B.status[0];
+      // time budget: no new system once this CTA has run longer than allowed
+      if (!s_stop && budget > 0 && (long long)(global_ns() - t0) > budget) {
+        if (atomicCAS(&B.status[0], 0, NB_E_TIMEOUT) == 0) B.status[1] = -1;
+        s_stop = 1;
+      }
       s_next = s_stop ? B.nsys : atomicAdd(B.queue, 1);
     }
     __syncthreads();
@@ -419,6 +437,7 @@ __global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
     if (k >= B.nsys) break;
     batch_system(B, P, s, B.order[k], nsteps, h, bt, st);
   }
+  if (threadIdx.x == 0 && blockIdx.x < B.cta_cap) B.cta_ns[blockIdx.x] = global_ns() - t0;
   // counters: kepler iterations are per thread; the rest are kept by thread 0
   unsigned long long kit = st.kepler_iters;
   for (int o = 16; o > 0; o >>= 1) kit += __shfl_down_sync(0xffffffffu, kit, o);
@@ -566,6 +585,9 @@ size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDe
   d.queue = c.take<int>(4);
   d.status = c.take<int>(4);
   d.stats = c.take<unsigned long long>(kStatN);
+  d.cta_ns = c.take<unsigned long long>(kCtaCap);
+  d.cta_cap = kCtaCap;
+  d.budget_ns = c.take<long long>(1);
   Snap s;
   s.arrays = c.take<double>((size_t)12 * total);
   s.alive = c.take<int>(total);
@@ -596,6 +618,7 @@ struct nb_batch {
   cudaStream_t cap;  // private stream for graph capture (the caller's may be the legacy stream)
   int g_threads, g_chunk;
   double g_dt;
+  int last_grid;  // CTAs of the last launch (for nb_batch_balance)
   long long steps_done;
   char err[256];
 };
@@ -641,7 +664,8 @@ int launch_batch(nb_batch* b, int nsteps, double dt) {
   NB_BCU(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)b->smem));
   NB_BCU(cudaMemsetAsync(b->d.queue, 0, sizeof(int), b->st));
-  k_batch<<<batch_grid(b), b->threads, b->smem, b->st>>>(b->d, b->P, nsteps, dt);
+  b->last_grid = batch_grid(b);
+  k_batch<<<b->last_grid, b->threads, b->smem, b->st>>>(b->d, b->P, nsteps, dt);
   NB_BCU(cudaGetLastError());
   return NB_OK;
 }
@@ -698,6 +722,7 @@ int run_steps(nb_batch* b, int nsteps, double dt) {
       b->g_dt = dt;
     }
     for (int k = 0; k < full; ++k) NB_BCU(cudaGraphLaunch(b->gexec, b->st));
+    b->last_grid = batch_grid(b);
   }
   if (rem > 0) {
     const int rc = launch_batch(b, rem, dt);
@@ -711,7 +736,7 @@ int run_steps(nb_batch* b, int nsteps, double dt) {
 extern "C" {
 
 size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets) {
-  if (!p || nsys < 1 || !offsets || offsets[0] != 0) return 0;
+  if (!p || nsys < 1 || !offsets || offsets[0] != 0 || p->rcrit_refresh != 0) return 0;
   for (int s = 0; s < nsys; ++s) {
     const int n = offsets[s + 1] - offsets[s];
     if (n < 1 || n > NB_BATCH_MAX_N) return 0;
@@ -762,6 +787,8 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
     cudaMemsetAsync(b->d.El, 0, sizeof(double) * nsys, b->st);
     cudaMemsetAsync(b->d.status, 0, 4 * sizeof(int), b->st);
     cudaMemsetAsync(b->d.stats, 0, sizeof(unsigned long long) * kStatN, b->st);
+    cudaMemsetAsync((void*)b->d.budget_ns, 0, sizeof(long long), b->st);
+    cudaMemsetAsync(b->d.cta_ns, 0, sizeof(unsigned long long) * kCtaCap, b->st);
     const double *ix = x, *iv = v, *im = m, *iR = R, *irc = rc_override;
     if (!inputs_on_device) {
       const size_t b3 = sizeof(double) * 3 * total, b1 = sizeof(double) * total;
@@ -820,6 +847,33 @@ int nb_batch_step(nb_batch* b, int nsteps, double dt) {
     return rc ? rc : code;
   }
   b->steps_done += nsteps;
+  return NB_OK;
+}
+
+int nb_batch_set_budget(nb_batch* b, double max_ms_per_launch) {
+  if (!b || !(max_ms_per_launch >= 0.0) || !std::isfinite(max_ms_per_launch)) return NB_E_INVALID;
+  const long long ns = (long long)(max_ms_per_launch * 1e6);
+  NB_BCU(cudaMemcpyAsync((void*)b->d.budget_ns, &ns, sizeof(ns), cudaMemcpyHostToDevice, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  return NB_OK;
+}
+
+int nb_batch_balance(nb_batch* b, double* efficiency, double* max_cta_ms, int* ctas) {
+  if (!b) return NB_E_INVALID;
+  const int g = b->last_grid < kCtaCap ? b->last_grid : kCtaCap;
+  if (g < 1) return NB_E_INVALID;
+  std::vector<unsigned long long> t(g);
+  NB_BCU(cudaMemcpyAsync(t.data(), b->d.cta_ns, sizeof(unsigned long long) * g,
+                         cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  double sum = 0.0, mx = 0.0;
+  for (int k = 0; k < g; ++k) {
+    sum += (double)t[k];
+    if ((double)t[k] > mx) mx = (double)t[k];
+  }
+  if (efficiency) *efficiency = mx > 0.0 ? sum / (g * mx) : 0.0;
+  if (max_cta_ms) *max_cta_ms = mx * 1e-6;
+  if (ctas) *ctas = g;
   return NB_OK;
 }
 

@@ -207,6 +207,23 @@ __global__ void k_fsal_init(Dev d) {
 
 void launch_fsal_init(const Dev& d, cudaStream_t st) { k_fsal_init<<<1, 1024, 0, st>>>(d); }
 
+// Eq. rcrit for every live body from its current state (rcrit_refresh = 1,
+// at the start of a step); clears the trial-flag count for the force
+// evaluation that follows.
+__global__ void __launch_bounds__(DNT) k_refresh_rcrit(Dev d, Phys P) {
+  if (d.ctrl->status) return;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i == 0) d.ctrl->n_ftrial = 0;
+  if (i >= d.n || !d.alive[i]) return;
+  const double rc = rcrit(P, d.x[i], d.y[i], d.z[i], d.vx[i], d.vy[i], d.vz[i], d.m[i]);
+  d.rc[i] = rc;
+  d.rc2[i] = rc * rc;
+}
+
+void launch_refresh_rcrit(const Dev& d, const Phys& P, cudaStream_t st) {
+  k_refresh_rcrit<<<d.ppart_n, DNT, 0, st>>>(d, P);
+}
+
 // ---------------------------------------------------------------------------
 // Standalone Kepler drift of interleaved device arrays.
 // ---------------------------------------------------------------------------
@@ -320,10 +337,11 @@ __global__ void __launch_bounds__(DNT) k_raw_prep(int n, const double* x3, const
   rc2[i] = rc[i] * rc[i];
 }
 
-__global__ void __launch_bounds__(DNT) k_raw_finish(int n, int S, const double* kpart, double G,
-                                                    double* a3) {
-  const int i = blockIdx.x * DNT + threadIdx.x;
-  if (i >= n) return;
+// a3 holds rows [ib, ie): row i goes to a3[3 (i - ib)].
+__global__ void __launch_bounds__(DNT) k_raw_finish(int n, int ib, int ie, int S,
+                                                    const double* kpart, double G, double* a3) {
+  const int i = ib + blockIdx.x * DNT + threadIdx.x;
+  if (i >= ie) return;
   double ax = 0.0, ay = 0.0, az = 0.0;
   for (int s = 0; s < S; ++s) {
     const double* p = kpart + (size_t)(3 * s) * n;
@@ -331,9 +349,10 @@ __global__ void __launch_bounds__(DNT) k_raw_finish(int n, int S, const double* 
     ay += p[n + i];
     az += p[2 * n + i];
   }
-  a3[3 * i] = G * ax;
-  a3[3 * i + 1] = G * ay;
-  a3[3 * i + 2] = G * az;
+  double* o = a3 + 3 * (size_t)(i - ib);
+  o[0] = G * ax;
+  o[1] = G * ay;
+  o[2] = G * az;
 }
 
 void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
@@ -341,8 +360,10 @@ void launch_raw_prep(int n, const double* x3, const double* rc, double* x, doubl
   k_raw_prep<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, x3, rc, x, y, z, rc2);
 }
 
-void launch_raw_finish(int n, int S, const double* kpart, double G, double* a3, cudaStream_t st) {
-  k_raw_finish<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, S, kpart, G, a3);
+void launch_raw_finish(int n, int ib, int ie, int S, const double* kpart, double G, double* a3,
+                       cudaStream_t st) {
+  if (ie <= ib) return;
+  k_raw_finish<<<(ie - ib + DNT - 1) / DNT, DNT, 0, st>>>(n, ib, ie, S, kpart, G, a3);
 }
 
 }  // namespace nb

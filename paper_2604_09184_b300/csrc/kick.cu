@@ -28,6 +28,7 @@ constexpr int KIPT = 2;   // targets per thread
 
 struct KickArgs {
   int n, S, jchunk;
+  int ib, ie;  // target rows [ib, ie) (all sources 0..n-1 act on them)
   const double *x, *y, *z, *m, *rc, *rc2;
   double* kpart;  // S x 3 x n
   int2* pairs;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
   const int n = A.n;
   const int it = blockIdx.x / A.S;
   const int sidx = blockIdx.x - it * A.S;
-  const int i0 = it * (KNT * KIPT) + threadIdx.x;
+  const int i0 = A.ib + it * (KNT * KIPT) + threadIdx.x;
 
   double xi[KIPT], yi[KIPT], zi[KIPT], rc2i[KIPT], rci[KIPT];
   double ax[KIPT], ay[KIPT], az[KIPT];
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
   for (int k = 0; k < KIPT; ++k) {
     const int i = i0 + k * KNT;
     ii[k] = i;
-    if (i < n) {
+    if (i < A.ie) {
       xi[k] = A.x[i];
       yi[k] = A.y[i];
       zi[k] = A.z[i];
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
 #pragma unroll
   for (int k = 0; k < KIPT; ++k) {
     const int i = ii[k];
-    if (i < n) {
+    if (i < A.ie) {
       double* p = A.kpart + (size_t)(3 * sidx) * n;
       p[i] = ax[k] + cx[k];
       p[n + i] = ay[k] + cy[k];
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
   const int n = A.n;
   const int it = blockIdx.x / A.S;
   const int sidx = blockIdx.x - it * A.S;
-  const int i0 = it * (DNT2 * DIPT) + threadIdx.x;
+  const int i0 = A.ib + it * (DNT2 * DIPT) + threadIdx.x;
   double xi[DIPT], yi[DIPT], zi[DIPT], rc2i[DIPT], rci[DIPT];
   double ax[DIPT], ay[DIPT], az[DIPT];
   float thi[DIPT];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
   for (int k = 0; k < DIPT; ++k) {
     const int i = i0 + k * DNT2;
     ii[k] = i;
-    if (i < n) {
+    if (i < A.ie) {
       xi[k] = A.x[i]; yi[k] = A.y[i]; zi[k] = A.z[i];
       rc2i[k] = A.rc2[i]; rci[k] = A.rc[i];
     } else {
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
 #pragma unroll
   for (int k = 0; k < DIPT; ++k) {
     const int i = ii[k];
-    if (i < n) {
+    if (i < A.ie) {
       double* p = A.kpart + (size_t)(3 * sidx) * n;
       p[i] = ax[k];
       p[n + i] = ay[k];
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
 int kick_blocks(int n, int S) { return ((n + KNT * KIPT - 1) / (KNT * KIPT)) * S; }
 
 static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) {
-  const int grid = kick_blocks(A.n, A.S);
+  const int grid = kick_blocks(A.ie - A.ib, A.S);
   if (grid <= 0) return;
   static_assert(KNT * KIPT == DNT2 * DIPT, "kick variants share the i-tile size");
   if (precision == NB_PREC_MIXED)
@@ -375,6 +376,8 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   A.n = d.n;
   A.S = d.S;
   A.jchunk = jchunk_for(d.n, d.S);
+  A.ib = 0;
+  A.ie = d.n;
   A.x = d.x; A.y = d.y; A.z = d.z; A.m = d.m; A.rc = d.rc; A.rc2 = d.rc2;
   A.kpart = d.kpart;
   A.pairs = d.ftrial;
@@ -384,11 +387,12 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   launch_kick_args(A, P.precision, st);
 }
 
-void launch_kick_raw(int n, const double* x, const double* y, const double* z, const double* m,
-                     const double* rc, const double* rc2, int S, int precision, double* kpart,
-                     int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st) {
+void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, const double* z,
+                     const double* m, const double* rc, const double* rc2, int S, int precision,
+                     double* kpart, int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st) {
   KickArgs A;
   A.n = n; A.S = S; A.jchunk = jchunk_for(n, S);
+  A.ib = ib; A.ie = ie;
   A.x = x; A.y = y; A.z = z; A.m = m; A.rc = rc; A.rc2 = rc2;
   A.kpart = kpart; A.pairs = pairs; A.cap = cap; A.counter = &ctrl->n_ftrial; A.ctrl = ctrl;
   launch_kick_args(A, precision, st);

@@ -92,7 +92,7 @@ struct Dev {
 // Parameters as the kernels see them.
 struct Phys {
   double G, m0, mu, dt_rcrit, hill_factor, vel_factor, bs_tol;
-  int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings;
+  int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings, rcrit_refresh;
 };
 
 __device__ __forceinline__ void set_status(Ctrl* c, int code, int where) {
@@ -264,9 +264,9 @@ __device__ __forceinline__ void reduce_parts3(const double* parts, int nparts, d
 int kick_blocks(int n, int S);
 int ppart_blocks(int n);
 void launch_kick(const Dev& d, const Phys& P, int target_sel, cudaStream_t st);
-void launch_kick_raw(int n, const double* x, const double* y, const double* z, const double* m,
-                     const double* rc, const double* rc2, int S, int precision, double* kpart,
-                     int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st);
+void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, const double* z,
+                     const double* m, const double* rc, const double* rc2, int S, int precision,
+                     double* kpart, int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st);
 void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st);
 void launch_member_kick(const Dev& d, const Phys& P, cudaStream_t st);
 void launch_open_h(const Dev& d, double h, cudaStream_t st);
@@ -279,6 +279,7 @@ void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double*
                     const double* m, const double* R, const double* rc, const int* ids,
                     cudaStream_t st);
 void launch_fsal_init(const Dev& d, cudaStream_t st);
+void launch_refresh_rcrit(const Dev& d, const Phys& P, cudaStream_t st);
 void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st);
 void launch_kepler_raw(int n, double mu, double* x3, double* v3, double dt, int max_iter,
                        int* status, cudaStream_t st);
@@ -288,7 +289,8 @@ void launch_gather(const Dev& d, double* x3, double* v3, double* m, double* R, d
 void launch_a_convert(const Dev& d, double* a3, int to_soa, cudaStream_t st);
 void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
                      double* rc2, cudaStream_t st);
-void launch_raw_finish(int n, int S, const double* kpart, double G, double* a3, cudaStream_t st);
+void launch_raw_finish(int n, int ib, int ie, int S, const double* kpart, double G, double* a3,
+                       cudaStream_t st);
 int peak_blocks();
 int measure_peaks(double* fp64, double* fp32, void* scratch, cudaStream_t st);
 

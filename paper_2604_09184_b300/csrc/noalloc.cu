@@ -77,9 +77,9 @@ extern "C" int nb_kick_noalloc(int n, const double* x, const double* m, const do
   Ctrl* ctrl = (Ctrl*)((char*)base + ctrl_off);
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return NB_E_CUDA;
   launch_raw_prep(n, x, rc, sx, sy, sz, src2, st);
-  launch_kick_raw(n, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij, cap, ctrl,
+  launch_kick_raw(n, 0, n, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij, cap, ctrl,
                   st);
-  launch_raw_finish(n, S, kpart, G, a, st);
+  launch_raw_finish(n, 0, n, S, kpart, G, a, st);
   int cnt = 0;
   if (cudaMemcpyAsync(&cnt, &ctrl->n_ftrial, sizeof(int), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)

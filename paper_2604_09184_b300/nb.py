@@ -34,7 +34,7 @@ class NbParams(C.Structure):
         ("vel_mode", C.c_int), ("merge", C.c_int), ("precision", C.c_int),
         ("kepler_max_iter", C.c_int), ("bs_tol", C.c_double), ("bs_kmax", C.c_int),
         ("bs_max_halvings", C.c_int), ("pair_capacity", C.c_int), ("log_capacity", C.c_int),
-        ("kick_split", C.c_int),
+        ("kick_split", C.c_int), ("rcrit_refresh", C.c_int),
     ]
 
 
@@ -90,6 +90,9 @@ def lib():
         L.nb_kick.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                               C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p,
                               C.c_size_t, C.c_void_p]
+        L.nb_kick_rows.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                   _I, C.c_void_p, C.c_size_t, C.c_void_p]
         L.nb_kick_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p]
         L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
@@ -106,6 +109,8 @@ def lib():
         L.nb_batch_energy.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.nb_batch_stats.argtypes = [C.c_void_p, C.POINTER(NbStats)]
         L.nb_batch_destroy.argtypes = [C.c_void_p]
+        L.nb_batch_set_budget.argtypes = [C.c_void_p, C.c_double]
+        L.nb_batch_balance.argtypes = [C.c_void_p, _D, _D, _I]
         L.nb_peak_scratch_bytes.argtypes = []
         L.nb_peak_scratch_bytes.restype = C.c_size_t
         L.nb_measure_peaks.argtypes = [_D, _D, C.c_void_p, C.c_void_p]
@@ -300,23 +305,26 @@ class NBodySystem:
         return {k: getattr(st, k) for k, _ in NbStats._fields_}
 
 
-def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=None):
-    """One launch of the kick+flag kernel on CUDA tensors. Returns (a, pairs, status)."""
+def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=None,
+         rows=None):
+    """One launch of the kick+flag kernel on CUDA tensors. Returns (a, pairs,
+    status); with rows = (row0, row1) only those target rows (nb_kick_rows)."""
     torch = _torch()
     L = lib()
     n = x.shape[0]
     x = x.contiguous()
-    a = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    r0, r1 = (0, n) if rows is None else rows
+    a = torch.empty((max(r1 - r0, 1), 3), dtype=torch.float64, device="cuda")
     cap = 16 * n + 64 if cap is None else cap
     pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
     nb = L.nb_kick_scratch_bytes(n, split)
     scratch = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
     sp = scratch.data_ptr() + ((-scratch.data_ptr()) % 256)
     cnt = C.c_int()
-    code = L.nb_kick(n, _ptr(x), _ptr(m.contiguous()), _ptr(rc.contiguous()), G, precision,
-                     split, _ptr(a), _ptr(pairs), cap, C.byref(cnt), C.c_void_p(sp), nb,
-                     _stream(torch))
-    return a, pairs[:min(cnt.value, cap)], code
+    code = L.nb_kick_rows(n, r0, r1, _ptr(x), _ptr(m.contiguous()), _ptr(rc.contiguous()), G,
+                          precision, split, _ptr(a), _ptr(pairs), cap, C.byref(cnt),
+                          C.c_void_p(sp), nb, _stream(torch))
+    return a[:max(r1 - r0, 0)], pairs[:min(cnt.value, cap)], code
 
 
 NB_NOALLOC_MAX_N = 65600
@@ -410,6 +418,15 @@ class NBodyBatch:
         st = NbStats()
         self._check(lib().nb_batch_stats(self._h, C.byref(st)))
         return {k: getattr(st, k) for k, _ in NbStats._fields_}
+
+    def set_budget(self, max_ms_per_launch: float):
+        self._check(lib().nb_batch_set_budget(self._h, float(max_ms_per_launch)))
+
+    def balance(self) -> dict:
+        """Load balance of the last launch (efficiency, longest CTA in ms, CTAs)."""
+        e, mx, g = C.c_double(), C.c_double(), C.c_int()
+        self._check(lib().nb_batch_balance(self._h, C.byref(e), C.byref(mx), C.byref(g)))
+        return {"efficiency": e.value, "max_cta_ms": mx.value, "ctas": g.value}
 
 
 def kick_noalloc(x, m, rc, a, pairs, G=2.959122082855911e-4, precision=NB_PREC_FP64):

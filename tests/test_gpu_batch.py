@@ -149,3 +149,35 @@ def test_batch_rejects_oversize_system():
     big = ics.make_disk(nb.NB_BATCH_MAX_N + 1, 1.0, 0.5, 2.0, 0.02, 0.01, 3.0, seed=1)
     with pytest.raises(nb.NbError):
         nb.NBodyBatch(nb.params(dt_rcrit=3.0), [big])
+
+
+def test_batch_time_budget_rolls_back():
+    """A per-launch time budget far below one system's step: the call fails
+    with NB_E_TIMEOUT and leaves the state as it was; without the budget the
+    same call succeeds."""
+    nb = nbm()
+    disks = ics.ensemble(n_systems=64, seed=ics.SEED_BASE + 37)
+    dt = 3.0
+    b = batch_of(disks, dt)
+    b.step(2, dt)
+    before = b.state()
+    b.set_budget(1e-6)
+    with pytest.raises(nb.NbError) as e:
+        b.step(5, dt)
+    assert e.value.code == nb.NB_E_TIMEOUT
+    after = b.state()
+    assert np.array_equal(before["x"], after["x"]) and np.array_equal(before["v"], after["v"])
+    b.set_budget(0.0)
+    b.step(5, dt)
+    ref = batch_of(disks, dt)
+    ref.step(7, dt)
+    assert np.array_equal(b.state()["x"], ref.state()["x"])
+
+
+def test_batch_load_balance_report():
+    disks = ics.ensemble(n_systems=256, seed=ics.SEED_BASE + 38)
+    b = batch_of(disks, 3.0)
+    b.step(3, 3.0)
+    bal = b.balance()
+    assert bal["ctas"] >= 1 and bal["max_cta_ms"] > 0
+    assert 0.0 < bal["efficiency"] <= 1.0

@@ -122,6 +122,33 @@ def test_kick_ds_small_and_ragged(n):
     assert pairset(pairs.cpu().numpy()) == pairset(pr)
 
 
+@pytest.mark.parametrize("prec_name", ["NB_PREC_FP64", "NB_PREC_DS"])
+def test_kick_row_blocks_reproduce_full_kick(prec_name):
+    """Row sharding emulated on one GPU: the kick of row blocks that partition
+    the bodies, each against all positions, equals the full kick bit for bit
+    and the blocks' flags add up to the full pair set."""
+    nb = nbmod()
+    d = ics.workload("mmsn_16k_js", n=5000)
+    rc = oracle_rc(d, scale=3.0)
+    prec = getattr(nb, prec_name)
+    a, p, code = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, prec)
+    assert code == 0 and len(p) > 0
+    parts, pairs, count = [], set(), 0
+    for r0, r1 in ((0, 1), (1, 1234), (1234, 2600), (2600, d.n)):
+        ab, pb, cb = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, prec, rows=(r0, r1))
+        assert cb == 0
+        pb = pb.cpu().numpy()
+        assert np.all((pb[:, 0] >= r0) & (pb[:, 0] < r1))
+        parts.append(ab.cpu().numpy())
+        pairs |= set(pairset(pb))
+        count += len(pb)
+    assert np.array_equal(np.concatenate(parts), a.cpu().numpy())
+    assert pairs == set(pairset(p.cpu().numpy())) and count == len(p)
+    for bad in ((5, 5), (-1, 3), (0, d.n + 1)):
+        _, _, cb = nb.kick(cuda(d.x), cuda(d.m), cuda(rc), G, prec, rows=bad)
+        assert cb == nb.NB_E_INVALID
+
+
 def test_kick_full_size_sampled():
     """N = 65538 (the benchmark workload) in the benchmark's launch shape;
     48 sampled bodies checked against the oracle row by row."""
@@ -269,6 +296,22 @@ def test_step_parity_reduced_precision_100_steps(prec_name):
     ref, gpu = run_both(d, 100, precision=getattr(nb, prec_name))
     compare_states(ref, gpu)
     assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+
+
+def test_step_parity_rcrit_refresh_every_step():
+    """rcrit_refresh = 1: r_crit from Eq. rcrit for every body at every step's
+    start, force and flags re-evaluated; same states, radii and encounter
+    lists as the oracle."""
+    d = ics.workload("toy_disk_256")
+    ref, gpu = run_both(d, 100, rcrit_refresh=1)
+    compare_states(ref, gpu)
+    assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+    assert len(ref.encounter_list()) > 0
+    sr, sg = ref.state(), gpu.state()
+    assert np.allclose(sg["rc"], sr["rc"], rtol=1e-12, atol=0)
+    # the GPU evaluates the force at init, at every step's start and at the
+    # trial positions; the end-of-step force after encounters is incremental
+    assert gpu.stats()["force_evals"] == 1 + 2 * 100
 
 
 def test_step_parity_velocity_mode_literal():

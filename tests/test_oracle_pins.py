@@ -470,3 +470,25 @@ def test_invalid_inputs_rejected():
         nbref.RefSystem(p, x, np.zeros((1, 3)), [1e-9], [1e-9])
     with pytest.raises(ValueError):
         nbref.RefSystem(p, np.ones((1, 3)), np.zeros((1, 3)), [0.0], [1e-9])
+
+
+def test_rcrit_refresh_cadence():
+    """rcrit_refresh = 1 (the every-step cadence of Eq. rcrit): after k steps
+    each body's r_crit is Eq. rcrit of its state at the start of step k, and
+    every step evaluates the force once more than with radii fixed."""
+    d = ics.workload("toy_disk_256", n=64)
+    p = nbref.params(dt_rcrit=d.dt, rcrit_refresh=1, merge=0)
+    a = nbref.RefSystem(p, d.x, d.v, d.m, d.R)
+    assert a.step(9, d.dt) == 0
+    st9 = a.state()
+    expect = np.array([nbref.rcrit(p, st9["x"][i], st9["v"][i], st9["m"][i])
+                       for i in range(len(st9["m"]))])
+    assert a.step(1, d.dt) == 0
+    st10 = a.state()
+    assert np.array_equal(st10["rc"], expect)
+    assert not np.array_equal(st10["rc"], st9["rc"])
+    p0 = nbref.params(dt_rcrit=d.dt, rcrit_refresh=0, merge=0)
+    b = nbref.RefSystem(p0, d.x, d.v, d.m, d.R)
+    assert b.step(10, d.dt) == 0
+    assert not np.array_equal(b.state()["rc"], a.state()["rc"])
+    assert a.stats()["force_evals"] - b.stats()["force_evals"] == 10
