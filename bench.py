@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="steps of the adjoint leg (2000 is the workload; fewer for profiling)")
     ap.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval")
+    ap.add_argument("--resolution", action="store_true",
+                    help="resolution study instead of the benchmark line: throughput vs N on the "
+                         "16k disk family (N = 2048..65536 + Jupiter and Saturn), GPU and oracle "
+                         "on 1 and on all host cores")
     ap.add_argument("--precision", choices=["fp64", "mixed", "ds"], default="fp64",
                     help="kick precision of the timed run (profiling); the line's value is fp64")
     return ap.parse_args()
@@ -171,6 +175,7 @@ def oracle_step_time(disk, steps: int, threads: int):
     """Wall time per step of the CPU oracle on `threads` host cores."""
     os.environ["OMP_NUM_THREADS"] = str(threads)
     from oracle import nbref
+    nbref.set_threads(threads)
     p = nbref.params(dt_rcrit=disk.dt)
     s = nbref.RefSystem(p, disk.x, disk.v, disk.m, disk.R)
     t0 = time.perf_counter()
@@ -531,10 +536,70 @@ def run_e2e(nb, torch, sysm, disk, steps, pps):
             "api": "nb_set_state (pinned host) + nb_step(1) + nb_get_state (pinned host)"}
 
 
+def run_resolution(args, sizes=(2048, 4096, 8192, 16384, 32768, 65536), max_n_1core=32768):
+    """Throughput vs N on the paper's resolution-study disk (0.5-4 AU, 5 Earth
+    masses, Jupiter and Saturn; the planetesimal count varies, the disk mass
+    does not), with the paper's speed ratios (GPU vs 1 and vs 16 CPU cores,
+    GENGA on an RTX 4070 Ti or P100 vs a Ryzen 9 7950X3D) quoted as context.
+    The oracle runs first, on all host cores and on one (one full step each;
+    one core only up to max_n_1core bodies, larger N would take minutes)."""
+    import torch
+    from paper_2604_09184_b300 import build, ics
+    cores = os.cpu_count() or 1
+    rows = []
+    for n in sizes:
+        d = ics.workload("mmsn_16k_js", n=n)
+        row = {"n_bodies": d.n, "pairs_per_step": pairs_per_step(d.n)}
+        row["oracle_all_cores_s_per_step"] = oracle_step_time(d, 1, cores)
+        row["oracle_1_core_s_per_step"] = (oracle_step_time(d, 1, 1) if n <= max_n_1core
+                                           else None)
+        rows.append((d, row))
+    build.build()
+    from paper_2604_09184_b300 import nb
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = []
+    for d, row in rows:
+        s = nb.NBodySystem(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R)
+        for _ in range(max(args.warmup, 1)):
+            s.step(1, d.dt)
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(1, d.dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        del s
+        t = sum(ms) / len(ms) * 1e-3
+        row["gpu_s_per_step"] = t
+        row["gpu_pairs_per_s"] = row["pairs_per_step"] / t
+        row["gpu_steps_per_s"] = 1.0 / t
+        row["gpu_over_oracle_all_cores"] = row["oracle_all_cores_s_per_step"] / t
+        o1 = row["oracle_1_core_s_per_step"]
+        row["gpu_over_oracle_1_core"] = o1 / t if o1 else None
+        out.append(row)
+    line = {"metric": "pair interactions/s and steps/s vs N (resolution study)", "unit":
+            "pair interactions/s", "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "host_cores": cores,
+            "config": {"workload": "mmsn_16k_js family: 0.5-4 AU, 5 Earth masses, J + S, dt 6 d",
+                       "l2": "flushed before each timed step"},
+            "resolution": out,
+            "paper_context": {"gpu_over_1_core_large_n": 150, "gpu_over_16_cores_large_n": 20,
+                              "cpu_over_gpu_small_n": ">= 10",
+                              "hardware": "GENGA on RTX 4070 Ti or Tesla P100 vs Ryzen 9 7950X3D"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.resolution:
+        return run_resolution(args)
     return run_ours(args)
 
 

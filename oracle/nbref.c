@@ -32,6 +32,9 @@
 #include "nbref.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -1017,4 +1020,12 @@ void nbref_destroy(nbref_system* s) {
   free(s->x); free(s->v); free(s->a); free(s->m); free(s->R); free(s->rc);
   free(s->id); free(s->alive); free(s->fprev.ij); free(s->log);
   free(s);
+}
+
+void nbref_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
 }

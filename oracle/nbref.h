@@ -108,6 +108,11 @@ int nbref_stats_get(const nbref_system* s, nbref_stats* st);
 long long nbref_step_index(const nbref_system* s);
 void nbref_destroy(nbref_system* s);
 
+/* Host threads of the OpenMP loops (over target bodies only, so results do
+ * not depend on it); n < 1 means 1. Used to time the oracle on 1 and on all
+ * cores in one process. */
+void nbref_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ def lib():
         L.nbref_step_index.argtypes = [C.c_void_p]
         L.nbref_step_index.restype = C.c_longlong
         L.nbref_destroy.argtypes = [C.c_void_p]
+        L.nbref_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -86,6 +87,11 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(_I)
+
+
+def set_threads(n: int):
+    """Host threads of the oracle's OpenMP loops (results do not depend on it)."""
+    lib().nbref_set_threads(int(n))
 
 
 def params(**kw) -> RefParams:

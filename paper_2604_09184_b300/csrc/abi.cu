@@ -25,10 +25,14 @@ int round_pow2(int v) {
 }
 
 int auto_split(int n) {
-  // aim at ~8 resident kick CTAs per SM on 148 SMs, whole 128-body tiles per chunk
+  // About 48 kick CTAs per SM over the launch (4 are resident at a time), so
+  // the last partial wave is a small fraction of the kernel; measured at
+  // N = 65538 this is 4 % faster (FP64) and 14 % faster (double-single) than
+  // ~8 per SM. Whole 128-body j-tiles per chunk, at most 64 chunks.
   const int itiles = (n + 255) / 256;
-  int S = (148 * 8 + itiles - 1) / itiles;
+  int S = (148 * 48 + itiles - 1) / itiles;
   const int maxS = (n + 127) / 128;
+  if (S > 64) S = 64;
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
   return S;
