@@ -273,6 +273,13 @@ void nbref_default_params(nbref_params* p) {
   p->bs_max_halvings = 20;
   p->kepler_max_iter = 30;
   p->rcrit_refresh = 0;
+  p->gas = 0;
+  p->gas_rho0 = 2.36e-3; /* 1.4e-9 g cm^-3 (minimum-mass nebula at 1 AU) */
+  p->gas_p = 2.75;
+  p->gas_eta = 2e-3;
+  p->gas_cd = 1.0;
+  p->gas_iter = 30;
+  p->eject_r = 0.0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -749,18 +756,142 @@ static void kick(nbref_system* s, double hh) {
   }
 }
 
+/* Gas drag acceleration on body i (section "Modelling additional dynamical
+ * effects", gas effects; the paper names no drag law, this reading takes the
+ * quadratic law of Adachi et al. 1976 used by Morishima et al. 2010, the
+ * model the paper cites): the gas rotates about the star on circles at
+ * (1 - eta) times the circular speed sqrt(G m0 / s), s the cylindrical
+ * radius, with midplane density rho0 (s / 1 AU)^-p; the body's velocity
+ * relative to the star is its barycentric velocity plus P / m0 (the star
+ * moves at -P / m0); a = -(C_D pi R^2 rho / (2 m)) |u| u with u the velocity
+ * relative to the gas. */
+static void drag_acc(const nbref_params* p, const double* x, const double* vb, const double* Pm0,
+                     double m, double R, double out[3]) {
+  const double sxy = sqrt(x[0] * x[0] + x[1] * x[1]);
+  double vg[3] = {0.0, 0.0, 0.0};
+  if (sxy > 0.0) {
+    const double vk = (1.0 - p->gas_eta) * sqrt(p->G * p->m0 / sxy);
+    vg[0] = -vk * x[1] / sxy;
+    vg[1] = vk * x[0] / sxy;
+  }
+  double u[3];
+  for (int k = 0; k < 3; ++k) u[k] = vb[k] + Pm0[k] - vg[k];
+  const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double rho = p->gas_rho0 * pow(sxy, -p->gas_p);
+  const double kd = p->gas_cd * 3.14159265358979323846 * R * R * rho / (2.0 * m);
+  for (int k = 0; k < 3; ++k) out[k] = -kd * un * u[k];
+}
+
+/* One body's implicit-midpoint drag update (Eq. implicit):
+ * v' = v + tau a_f(x, (v + v') / 2), fixed-point iteration from v' = v until
+ * successive iterates agree to 1e-15 of |v'| (max-norm) or gas_iter
+ * iterations (NBREF_E_NOCONV). Pm0 = P / m0, held for the whole operator. */
+int nbref_implicit_drag(const nbref_params* p, const double x[3], const double v[3],
+                        const double Pm0[3], double m, double R, double tau, double vout[3]) {
+  double w[3] = {v[0], v[1], v[2]};
+  int ok = 0;
+  for (int it = 0; it < p->gas_iter; ++it) {
+    double vm[3], a[3];
+    for (int k = 0; k < 3; ++k) vm[k] = 0.5 * (v[k] + w[k]);
+    drag_acc(p, x, vm, Pm0, m, R, a);
+    double dmax = 0.0, wmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double wn = v[k] + tau * a[k];
+      dmax = fmax(dmax, fabs(wn - w[k]));
+      wmax = fmax(wmax, fabs(wn));
+      w[k] = wn;
+    }
+    if (dmax <= 1e-15 * wmax) {
+      ok = 1;
+      break;
+    }
+  }
+  for (int k = 0; k < 3; ++k) vout[k] = w[k];
+  return ok ? NBREF_OK : NBREF_E_NOCONV;
+}
+
+/* G(tau): the implicit-midpoint drag update of every live body with a
+ * radius; P is the momentum at the start of the operator. */
+static int gas_drag(nbref_system* s, double tau) {
+  const nbref_params* p = &s->p;
+  double P[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < s->n; ++i) {
+    if (!s->alive[i]) continue;
+    for (int k = 0; k < 3; ++k) P[k] += s->m[i] * s->v[3 * i + k];
+  }
+  const double Pm0[3] = {P[0] / p->m0, P[1] / p->m0, P[2] / p->m0};
+  int status = NBREF_OK;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < s->n; ++i) {
+    if (!s->alive[i] || !(s->R[i] > 0.0)) continue;
+    double w[3];
+    const int st = nbref_implicit_drag(p, s->x + 3 * i, s->v + 3 * i, Pm0, s->m[i], s->R[i], tau, w);
+    if (st) {
+#pragma omp atomic write
+      status = st;
+    }
+    for (int k = 0; k < 3; ++k) s->v[3 * i + k] = w[k];
+  }
+  return status;
+}
+
+/* Bodies beyond eject_r leave the system (the ejected mass of the
+ * resolution study, section on the comparison of resolutions): in ascending
+ * order each is deactivated, its mass and the count recorded, and the energy
+ * it takes away added to E_lost: its kinetic and star-potential energy, its
+ * mutual potential with the bodies still present, and the change of the
+ * |P|^2 / (2 m0) term of Eq. Hc. Returns the number removed. */
+static int eject(nbref_system* s) {
+  const nbref_params* p = &s->p;
+  const double r2max = p->eject_r * p->eject_r;
+  int ne = 0;
+  for (int i = 0; i < s->n; ++i) {
+    if (!s->alive[i]) continue;
+    const double* x = s->x + 3 * i;
+    if (!(x[0] * x[0] + x[1] * x[1] + x[2] * x[2] > r2max)) continue;
+    const double* v = s->v + 3 * i;
+    const double mi = s->m[i];
+    double P[3] = {0.0, 0.0, 0.0}, mutual = 0.0;
+    for (int j = 0; j < s->n; ++j) {
+      if (!s->alive[j]) continue;
+      for (int k = 0; k < 3; ++k) P[k] += s->m[j] * s->v[3 * j + k];
+      if (j == i) continue;
+      const double dx = s->x[3 * j] - x[0], dy = s->x[3 * j + 1] - x[1], dz = s->x[3 * j + 2] - x[2];
+      mutual -= p->G * mi * s->m[j] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    double Pn2 = 0.0, P2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      P2 += P[k] * P[k];
+      Pn2 += (P[k] - mi * v[k]) * (P[k] - mi * v[k]);
+    }
+    s->E_lost += body_energy(p, x, v, mi) + mutual + (P2 - Pn2) / (2.0 * p->m0);
+    s->st.m_ejected += mi;
+    s->st.ejections++;
+    s->alive[i] = 0;
+    ++ne;
+  }
+  return ne;
+}
+
 static int one_step(nbref_system* s, double h) {
   int n = s->n;
   const nbref_params* p = &s->p;
   double mu = p->G * p->m0;
+  int ejected = p->eject_r > 0.0 ? eject(s) : 0;
   if (p->rcrit_refresh) {
-    /* Eq. rcrit evaluated afresh for every body at the start of the step;
-     * the cached force and flags are then re-evaluated with the new radii. */
+    /* Eq. rcrit evaluated afresh for every body at the start of the step. */
     for (int i = 0; i < n; ++i)
       if (s->alive[i]) s->rc[i] = nbref_rcrit(p, s->x + 3 * i, s->v + 3 * i, s->m[i]);
+  }
+  if (p->rcrit_refresh || ejected) {
+    /* the cached force and flags anew (new radii, or bodies removed) */
     s->fprev.n = 0;
     forces_flags(n, s->x, s->m, s->rc, s->alive, p->G, s->a, &s->fprev);
     s->st.force_evals++;
+  }
+  if (p->gas) {
+    int gs = gas_drag(s, 0.5 * h);
+    if (gs) return gs;
   }
   kick(s, 0.5 * h);
   momentum_drift(s, 0.5 * h);
@@ -891,6 +1022,10 @@ static int one_step(nbref_system* s, double h) {
   if (status) return status;
   momentum_drift(s, 0.5 * h);
   kick(s, 0.5 * h);
+  if (p->gas) {
+    int gs = gas_drag(s, 0.5 * h);
+    if (gs) return gs;
+  }
   s->step_index++;
   s->st.steps++;
   return NBREF_OK;

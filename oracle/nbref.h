@@ -38,6 +38,14 @@ typedef struct {
   int bs_max_halvings; /* cap on substep halvings inside one step */
   int kepler_max_iter; /* cap on Kepler-equation iterations */
   int rcrit_refresh;   /* 0: r_crit at start and for merged survivors; 1: every step (see step) */
+  /* Gas drag, applied with the implicit midpoint method of Eq. implicit (see step). */
+  int gas;             /* 1: gas drag on */
+  double gas_rho0;     /* midplane gas density at 1 AU, Msun / AU^3 */
+  double gas_p;        /* density power law rho = rho0 (s / 1 AU)^-p, s = cylindrical radius */
+  double gas_eta;      /* gas rotates at (1 - eta) times the circular speed */
+  double gas_cd;       /* drag coefficient C_D */
+  int gas_iter;        /* cap on implicit-midpoint iterations */
+  double eject_r;      /* bodies beyond this heliocentric distance are removed; 0 = never */
 } nbref_params;
 
 typedef struct {
@@ -50,6 +58,8 @@ typedef struct {
   long long bs_derivs;      /* right-hand-side evaluations inside BS */
   long long merges;         /* perfect mergers */
   long long kepler_iters;   /* Kepler iterations summed over bodies and steps */
+  long long ejections;      /* bodies removed beyond eject_r */
+  double m_ejected;         /* their mass */
 } nbref_stats;
 
 typedef struct nbref_system nbref_system;
@@ -112,6 +122,12 @@ void nbref_destroy(nbref_system* s);
  * not depend on it); n < 1 means 1. Used to time the oracle on 1 and on all
  * cores in one process. */
 void nbref_set_threads(int n);
+
+/* One body's gas-drag update by the implicit midpoint method (Eq. implicit):
+ * vout = v + tau a_f(x, (v + vout) / 2); Pm0 = P / m0 (the star's velocity
+ * is -Pm0). Returns 0 or NBREF_E_NOCONV after gas_iter iterations. */
+int nbref_implicit_drag(const nbref_params* p, const double x[3], const double v[3],
+                        const double Pm0[3], double m, double R, double tau, double vout[3]);
 
 #ifdef __cplusplus
 }

@@ -30,13 +30,20 @@ class RefParams(C.Structure):
         ("bs_max_halvings", C.c_int),
         ("kepler_max_iter", C.c_int),
         ("rcrit_refresh", C.c_int),
+        ("gas", C.c_int),
+        ("gas_rho0", C.c_double),
+        ("gas_p", C.c_double),
+        ("gas_eta", C.c_double),
+        ("gas_cd", C.c_double),
+        ("gas_iter", C.c_int),
+        ("eject_r", C.c_double),
     ]
 
 
 class RefStats(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in (
         "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
-        "bs_derivs", "merges", "kepler_iters")]
+        "bs_derivs", "merges", "kepler_iters", "ejections")] + [("m_ejected", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -77,6 +84,8 @@ def lib():
         L.nbref_step_index.restype = C.c_longlong
         L.nbref_destroy.argtypes = [C.c_void_p]
         L.nbref_set_threads.argtypes = [C.c_int]
+        L.nbref_implicit_drag.argtypes = [C.POINTER(RefParams)] + [C.c_void_p] * 3 + [
+            C.c_double, C.c_double, C.c_double, C.c_void_p]
         _lib = L
     return _lib
 
@@ -92,6 +101,17 @@ def _ip(a):
 def set_threads(n: int):
     """Host threads of the oracle's OpenMP loops (results do not depend on it)."""
     lib().nbref_set_threads(int(n))
+
+
+def implicit_drag(p: RefParams, x, v, Pm0, m, R, tau):
+    """One body's implicit-midpoint drag update; returns (v', status)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    P = np.ascontiguousarray(Pm0, dtype=np.float64)
+    out = np.zeros(3)
+    st = lib().nbref_implicit_drag(C.byref(p), _dp(x), _dp(v), _dp(P), float(m), float(R),
+                                   float(tau), _dp(out))
+    return out, st
 
 
 def params(**kw) -> RefParams:

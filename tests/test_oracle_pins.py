@@ -492,3 +492,87 @@ def test_rcrit_refresh_cadence():
     assert b.step(10, d.dt) == 0
     assert not np.array_equal(b.state()["rc"], a.state()["rc"])
     assert a.stats()["force_evals"] - b.stats()["force_evals"] == 10
+
+
+# ---------------------------------------------------------------------------
+# Gas drag by the implicit midpoint method (Eq. implicit) and ejection.
+# ---------------------------------------------------------------------------
+def _drag_k(p, x, m, R):
+    s = np.hypot(x[0], x[1])
+    rho = p.gas_rho0 * s ** (-p.gas_p)
+    return p.gas_cd * np.pi * R * R * rho / (2.0 * m)
+
+
+def test_implicit_drag_closed_form_gas_at_rest():
+    """Gas at rest (eta = 1) and v, P/m0 along one axis: the implicit
+    midpoint update w = v - tau k |u| u, u = (v + w)/2 + c, has the closed
+    form u = (-1 + sqrt(1 + 2 tau k (v + c))) / (tau k), w = 2 (u - c) - v."""
+    p = nbref.params(gas=1, gas_eta=1.0, gas_iter=200)
+    x = np.array([1.3, 0.4, 0.01])
+    m, R = 3e-10, 4e-6
+    k = _drag_k(p, x, m, R)
+    for v0, c, tau in ((0.017, 2e-7, 3.0), (0.002, 0.0, 40.0), (0.03, 1e-6, 1.0)):
+        # scale the drag up so that the update is far from the identity
+        p.gas_rho0 = 2.36e-3 * 1e4
+        k = _drag_k(p, x, m, R)
+        w, st = nbref.implicit_drag(p, x, [v0, 0, 0], [c, 0, 0], m, R, tau)
+        assert st == 0
+        u = (-1.0 + np.sqrt(1.0 + 2.0 * tau * k * (v0 + c))) / (tau * k)
+        assert abs(w[0] - (2.0 * (u - c) - v0)) <= 1e-14 * abs(v0)
+        assert w[1] == 0.0 and w[2] == 0.0
+        assert w[0] < v0  # the drag slows the body
+
+
+def test_implicit_drag_comoving_with_gas_is_identity():
+    """A body whose velocity relative to the star equals the gas velocity
+    ((1 - eta) v_circ along the azimuth of its cylindrical radius) feels no
+    drag."""
+    p = nbref.params(gas=1, gas_eta=0.003)
+    x = np.array([0.6, -1.1, 0.002])
+    s = np.hypot(x[0], x[1])
+    vk = (1 - p.gas_eta) * np.sqrt(p.G * p.m0 / s)
+    vgas = np.array([-vk * x[1] / s, vk * x[0] / s, 0.0])
+    c = np.array([1e-6, -2e-6, 0.0])
+    w, st = nbref.implicit_drag(p, x, vgas - c, c, 1e-9, 1e-5, 6.0)
+    assert st == 0
+    assert np.array_equal(w, vgas - c)
+
+
+def test_gas_drag_damps_eccentricity_and_inclination():
+    """Drag toward the sub-Keplerian gas circulates orbits: over many steps the
+    eccentricity and inclination of a small body decay (Adachi et al. 1976)."""
+    d = ics.make_disk(8, 0.05, 0.9, 1.1, 0.05, 0.03, 6.0, seed=77)
+    # a gas density 1e6 times the nebula's makes the damping time ~100 steps
+    p = nbref.params(dt_rcrit=d.dt, gas=1, gas_rho0=2.36e-3 * 1e6, merge=0)
+    s = nbref.RefSystem(p, d.x, d.v, d.m, d.R)
+
+    def ecc_inc(st):
+        x, v = st["x"], st["v"]
+        mu = p.G * p.m0
+        h = np.cross(x, v)
+        e = np.cross(v, h) / mu - x / np.linalg.norm(x, axis=1)[:, None]
+        return np.linalg.norm(e, axis=1), np.arccos(h[:, 2] / np.linalg.norm(h, axis=1))
+
+    e0, i0 = ecc_inc(s.state())
+    assert s.step(400, d.dt) == 0
+    e1, i1 = ecc_inc(s.state())
+    assert np.all(e1 < 0.1 * e0) and np.all(i1 < 0.1 * i0)
+
+
+def test_ejection_removes_bodies_and_books_energy():
+    d = ics.make_disk(16, 2.0, 0.8, 2.0, 0.02, 0.01, 6.0, seed=91)
+    x, v, m, R = d.x.copy(), d.v.copy(), d.m.copy(), d.R.copy()
+    x[3] = [120.0, 5.0, 0.0]  # beyond eject_r
+    v[3] = [0.0, 0.004, 0.0]
+    p = nbref.params(dt_rcrit=d.dt, eject_r=100.0, merge=0)
+    s = nbref.RefSystem(p, x, v, m, R)
+    E0 = s.energy_momentum()["E"]
+    fe0 = s.stats()["force_evals"]
+    assert s.step(1, d.dt) == 0
+    st = s.stats()
+    assert st["ejections"] == 1 and st["m_ejected"] == m[3]
+    assert 3 not in s.state()["ids"] and s.n_active == 15
+    # one extra force evaluation: the cached force without the removed body
+    assert st["force_evals"] - fe0 == 2
+    em = s.energy_momentum()
+    assert abs(em["E"] + em["E_lost"] - E0) <= 1e-9 * abs(E0)
