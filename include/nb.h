@@ -73,6 +73,27 @@ typedef struct {
                           re-evaluated with the new radii (two evaluations per step). Only
                           nb_init_system / nb_step take 1; the batch and adjoint entry points
                           reject it (NB_E_INVALID). */
+  /* Gas drag (section "Modelling additional dynamical effects"), applied as
+   * G(h/2) B(h/2) C(h/2) A(h) C(h/2) B(h/2) G(h/2), each G(tau) the implicit
+   * midpoint update of Eq. implicit, v' = v + tau a_f(x, (v + v') / 2),
+   * solved by fixed-point iteration to 1e-15 relative (NB_E_NOCONV after
+   * gas_iter). Drag law (a reading; the paper names none): the quadratic law
+   * a_f = -(C_D pi R^2 rho / (2 m)) |u| u, u the velocity relative to gas that
+   * circles the star at (1 - eta) times the circular speed sqrt(G m0 / s) of
+   * the cylindrical radius s, midplane density rho = rho0 (s / 1 AU)^-p.
+   * Bodies with R = 0 feel no drag. Single-system path only (the batch and
+   * adjoint entry points reject gas != 0). */
+  int gas;             /* 1: gas drag on; default 0 */
+  double gas_rho0;     /* Msun / AU^3; default 2.36e-3 (1.4e-9 g cm^-3) */
+  double gas_p;        /* default 2.75 */
+  double gas_eta;      /* default 2e-3 */
+  double gas_cd;       /* default 1 */
+  int gas_iter;        /* default 30 */
+  /* Ejection: at the start of every step, bodies farther than eject_r (AU)
+   * from the star are removed (their mass and the energy they carry away,
+   * mutual and Eq. Hc terms included, are booked; the cached force is then
+   * re-evaluated). 0 (default) = never. Single-system path only. */
+  double eject_r;
 } nb_params;
 
 typedef struct {
@@ -87,8 +108,10 @@ typedef struct {
   long long kepler_iters;    /* Kepler iterations summed over bodies and steps */
   long long moved_bodies;    /* bodies re-integrated by BS (incremental force update) */
   long long log_dropped;     /* encounter-log entries that did not fit */
-  int n_active;              /* bodies not absorbed by a merger */
+  int n_active;              /* bodies not absorbed by a merger or ejected */
   int last_pairs;            /* |F| of the last force evaluation */
+  long long ejections;       /* bodies removed beyond eject_r */
+  double m_ejected;          /* their mass */
 } nb_stats_t;
 
 typedef struct nb_system nb_system; /* opaque host handle (small, malloc'd by the library) */

@@ -109,6 +109,13 @@ Phys make_phys(const nb_params& p) {
   P.bs_kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
   P.bs_max_halvings = p.bs_max_halvings > 40 ? 40 : p.bs_max_halvings;
   P.rcrit_refresh = p.rcrit_refresh;
+  P.gas = p.gas;
+  P.gas_iter = p.gas_iter;
+  P.gas_rho0 = p.gas_rho0;
+  P.gas_p = p.gas_p;
+  P.gas_eta = p.gas_eta;
+  P.gas_cd = p.gas_cd;
+  P.eject_r = p.eject_r;
   return P;
 }
 
@@ -120,6 +127,12 @@ bool params_ok(const nb_params* p) {
   if (p->kepler_max_iter < 1 || p->bs_max_halvings < 0 || !(p->bs_tol > 0.0)) return false;
   if (p->pair_capacity < 0 || p->log_capacity < 0 || p->kick_split < 0) return false;
   if (p->rcrit_refresh != 0 && p->rcrit_refresh != 1) return false;
+  if (p->gas != 0 && p->gas != 1) return false;
+  if (p->gas && (!(p->gas_rho0 >= 0.0) || !std::isfinite(p->gas_p) || !(p->gas_eta <= 1.0) ||
+                 !(p->gas_cd >= 0.0) || p->gas_iter < 1))
+    return false;
+  if (!(p->eject_r >= 0.0) || !std::isfinite(p->eject_r) || p->eject_r >= 0.5 * kDeadOffset)
+    return false;
   return true;
 }
 
@@ -208,6 +221,13 @@ void nb_default_params(nb_params* p) {
   p->log_capacity = 0;
   p->kick_split = 0;
   p->rcrit_refresh = 0;
+  p->gas = 0;
+  p->gas_rho0 = 2.36e-3;
+  p->gas_p = 2.75;
+  p->gas_eta = 2e-3;
+  p->gas_cd = 1.0;
+  p->gas_iter = 30;
+  p->eject_r = 0.0;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {
@@ -340,14 +360,18 @@ int nb_step(nb_system* s, int nsteps, double dt) {
     }
   }
   const int refresh = s->P.rcrit_refresh;
-  if (!refresh) launch_open_h(d, dt, s->st);
+  const int eject = s->P.eject_r > 0.0;
+  const int gas = s->P.gas;
+  const int split = refresh || eject || gas;  // no fusion of closing and opening kicks
+  if (!split) launch_open_h(d, dt, s->st);
   for (int k = 0; k < nsteps; ++k) {
-    if (refresh) {
-      // Eq. rcrit at the step's start, then the cached force and flags anew
-      launch_refresh_rcrit(d, s->P, s->st);
-      launch_kick(d, s->P, 0, s->st);
-      launch_finish(d, s->P, 0, s->st);
-      launch_fsal_init(d, s->st);
+    if (split) {
+      // step start: ejection, Eq. rcrit anew, the cached force and flags
+      // anew where either changed, then G(h/2) and the opening B(h/2)
+      if (eject) launch_eject(d, s->P, s->st);
+      if (refresh) launch_refresh_rcrit(d, s->P, s->st);
+      if (refresh || eject) launch_force_anew(d, s->P, !refresh, s->st);
+      if (gas) launch_gas(d, s->P, 0.5 * dt, s->st);
       launch_open_h(d, dt, s->st);
     }
     launch_drift_h(d, s->P, dt, s->st);
@@ -359,14 +383,17 @@ int nb_step(nb_system* s, int nsteps, double dt) {
     launch_finish(d, s->P, 1, s->st);
     launch_scatter(d, s->P, s->st);
     launch_member_kick(d, s->P, s->st);
-    launch_close_h(d, s->P, dt, refresh || k == nsteps - 1, s->st);
+    launch_close_h(d, s->P, dt, split || k == nsteps - 1, s->st);
+    if (gas) launch_gas(d, s->P, 0.5 * dt, s->st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e, "nb_step launch");
   Ctrl c;
   rc = read_ctrl(s, &c);
   if (rc) return rc;
-  s->launches += refresh ? 14LL * nsteps : 1 + 8LL * nsteps;
+  s->launches += split ? (long long)nsteps * (9 + (eject ? 1 : 0) + (refresh ? 1 : 0) +
+                                               ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0))
+                      : 1 + 8LL * nsteps;
   if (s->timing) {
     for (int k = 0; k < nsteps; ++k) {
       float ms = 0.f;
@@ -484,6 +511,8 @@ int nb_stats(nb_system* s, nb_stats_t* out) {
   out->log_dropped = (long long)c.stats[ST_LOG_DROPPED];
   out->n_active = c.n_active;
   out->last_pairs = c.n_fprev;
+  out->ejections = (long long)c.stats[ST_EJECTIONS];
+  out->m_ejected = c.m_ejected;
   return NB_OK;
 }
 

@@ -189,8 +189,9 @@ void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double*
   k_init<<<d.ppart_n, DNT, 0, st>>>(d, P, in);
 }
 
-__global__ void k_fsal_init(Dev d) {
+__global__ void k_fsal_init(Dev d, const int* cond) {
   __shared__ int s_n;
+  if (cond && *cond == 0) return;
   if (threadIdx.x == 0) {
     int nt = d.ctrl->n_ftrial;
     if (nt > d.pair_cap) {
@@ -205,7 +206,9 @@ __global__ void k_fsal_init(Dev d) {
   for (int k = threadIdx.x; k < s_n; k += blockDim.x) d.fprev[k] = d.ftrial[k];
 }
 
-void launch_fsal_init(const Dev& d, cudaStream_t st) { k_fsal_init<<<1, 1024, 0, st>>>(d); }
+void launch_fsal_init(const Dev& d, cudaStream_t st, const int* cond) {
+  k_fsal_init<<<1, 1024, 0, st>>>(d, cond);
+}
 
 // Eq. rcrit for every live body from its current state (rcrit_refresh = 1,
 // at the start of a step); clears the trial-flag count for the force
@@ -223,6 +226,169 @@ __global__ void __launch_bounds__(DNT) k_refresh_rcrit(Dev d, Phys P) {
 void launch_refresh_rcrit(const Dev& d, const Phys& P, cudaStream_t st) {
   k_refresh_rcrit<<<d.ppart_n, DNT, 0, st>>>(d, P);
 }
+
+// ---------------------------------------------------------------------------
+// Gas drag G(tau) by the implicit midpoint method (Eq. implicit):
+// v' = v + tau a_f(x, (v + v') / 2), fixed-point iteration to 1e-15 of |v'|.
+// a_f = -(C_D pi R^2 rho / (2 m)) |u| u, u = v + P / m0 - v_gas, the gas
+// circling the star at (1 - eta) sqrt(G m0 / s), rho = rho0 s^-p (s the
+// cylindrical radius). P (the momentum at the operator's start) is summed
+// per block by k_gas_parts and re-reduced in a fixed order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DNT) k_gas_parts(Dev d) {
+  __shared__ double red[3 * 32 + 3];
+  if (d.ctrl->status) return;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  if (i < d.n && d.alive[i]) {
+    const double m = d.m[i];
+    px = m * d.vx[i]; py = m * d.vy[i]; pz = m * d.vz[i];
+  }
+  block_sum3(px, py, pz, red);
+  if (threadIdx.x == 0) {
+    d.ppartB[3 * blockIdx.x] = px;
+    d.ppartB[3 * blockIdx.x + 1] = py;
+    d.ppartB[3 * blockIdx.x + 2] = pz;
+  }
+}
+
+__device__ __forceinline__ void drag_acc(const Phys& P, double x, double y, const double u0[3],
+                                         double kcoef, double a[3]) {
+  const double s = sqrt(x * x + y * y);
+  double gx = 0.0, gy = 0.0;
+  if (s > 0.0) {
+    const double vk = (1.0 - P.gas_eta) * sqrt(P.G * P.m0 / s);
+    gx = -vk * y / s;
+    gy = vk * x / s;
+  }
+  const double ux = u0[0] - gx, uy = u0[1] - gy, uz = u0[2];
+  const double un = sqrt(ux * ux + uy * uy + uz * uz);
+  const double kd = kcoef * pow(s, -P.gas_p);
+  a[0] = -kd * un * ux;
+  a[1] = -kd * un * uy;
+  a[2] = -kd * un * uz;
+}
+
+__global__ void __launch_bounds__(DNT) k_gas(Dev d, Phys P, double tau) {
+  __shared__ int s_stop;
+  __shared__ double red[3 * 32 + 3];
+  if (threadIdx.x == 0) s_stop = d.ctrl->status;
+  __syncthreads();
+  if (s_stop) return;
+  double Pt[3];
+  reduce_parts3(d.ppartB, d.ppart_n, red, Pt);
+  const double cx = Pt[0] / P.m0, cy = Pt[1] / P.m0, cz = Pt[2] / P.m0;
+  const int i = blockIdx.x * DNT + threadIdx.x;
+  if (i >= d.n || !d.alive[i] || !(d.R[i] > 0.0)) return;
+  const double x = d.x[i], y = d.y[i];
+  const double R = d.R[i];
+  const double kcoef = P.gas_cd * 3.14159265358979323846 * R * R * P.gas_rho0 / (2.0 * d.m[i]);
+  const double v0[3] = {d.vx[i], d.vy[i], d.vz[i]};
+  double w[3] = {v0[0], v0[1], v0[2]};
+  bool ok = false;
+  for (int it = 0; it < P.gas_iter; ++it) {
+    const double u[3] = {0.5 * (v0[0] + w[0]) + cx, 0.5 * (v0[1] + w[1]) + cy,
+                         0.5 * (v0[2] + w[2]) + cz};
+    double a[3];
+    drag_acc(P, x, y, u, kcoef, a);
+    double dmax = 0.0, wmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double wn = v0[k] + tau * a[k];
+      dmax = fmax(dmax, fabs(wn - w[k]));
+      wmax = fmax(wmax, fabs(wn));
+      w[k] = wn;
+    }
+    if (dmax <= 1e-15 * wmax) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) set_status(d.ctrl, NB_E_NOCONV, 26);
+  d.vx[i] = w[0];
+  d.vy[i] = w[1];
+  d.vz[i] = w[2];
+}
+
+void launch_gas(const Dev& d, const Phys& P, double tau, cudaStream_t st) {
+  k_gas_parts<<<d.ppart_n, DNT, 0, st>>>(d);
+  k_gas<<<d.ppart_n, DNT, 0, st>>>(d, P, tau);
+}
+
+// ---------------------------------------------------------------------------
+// Ejection at the start of a step: bodies beyond eject_r leave, in ascending
+// index order; each takes away its kinetic and star-potential energy, its
+// mutual potential with the bodies still present and the change of the
+// |P|^2 / (2 m0) term of Eq. Hc (booked in E_lost). One CTA; the scan is
+// O(N) per step and each removal O(N) (removals are rare).
+// ---------------------------------------------------------------------------
+constexpr int ENT2 = 1024;
+
+__global__ void __launch_bounds__(ENT2) k_eject(Dev d, Phys P) {
+  __shared__ double red[3 * 32 + 3];
+  __shared__ int s_next, s_count;
+  if (d.ctrl->status) return;
+  if (threadIdx.x == 0) s_count = 0;
+  const double r2max = P.eject_r * P.eject_r;
+  int start = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = d.n;
+    __syncthreads();
+    // the lowest index at or after `start` beyond eject_r
+    for (int i = start + threadIdx.x; i < d.n; i += ENT2) {
+      if (!d.alive[i]) continue;
+      const double x = d.x[i], y = d.y[i], z = d.z[i];
+      if (x * x + y * y + z * z > r2max) {
+        atomicMin(&s_next, i);
+        break;
+      }
+    }
+    __syncthreads();
+    const int e = s_next;
+    if (e >= d.n) break;
+    const double xe = d.x[e], ye = d.y[e], ze = d.z[e], me = d.m[e];
+    const double vxe = d.vx[e], vye = d.vy[e], vze = d.vz[e];
+    double px = 0.0, py = 0.0, pot = 0.0;
+    double pz = 0.0;
+    for (int j = threadIdx.x; j < d.n; j += ENT2) {
+      if (!d.alive[j]) continue;
+      const double mj = d.m[j];
+      px += mj * d.vx[j]; py += mj * d.vy[j]; pz += mj * d.vz[j];
+      if (j == e) continue;
+      const double dx = d.x[j] - xe, dy = d.y[j] - ye, dz = d.z[j] - ze;
+      pot -= P.G * me * mj / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    block_sum3(px, py, pz, red);
+    double dum1 = 0.0, dum2 = 0.0;
+    block_sum3(pot, dum1, dum2, red);
+    if (threadIdx.x == 0) {
+      const double P2 = px * px + py * py + pz * pz;
+      const double qx = px - me * vxe, qy = py - me * vye, qz = pz - me * vze;
+      const double Pn2 = qx * qx + qy * qy + qz * qz;
+      const double v2 = vxe * vxe + vye * vye + vze * vze;
+      const double r = sqrt(xe * xe + ye * ye + ze * ze);
+      const double eb = 0.5 * me * v2 - P.G * P.m0 * me / r;
+      Ctrl* C = d.ctrl;
+      C->E_lost += eb + pot + (P2 - Pn2) / (2.0 * P.m0);
+      C->m_ejected += me;
+      C->stats[ST_EJECTIONS] += 1ull;
+      C->n_active -= 1;
+      s_count += 1;
+      d.alive[e] = 0;
+      d.x[e] = kDeadOffset * (double)(d.id[e] + 1);
+      d.y[e] = 0.0; d.z[e] = 0.0;
+      d.vx[e] = 0.0; d.vy[e] = 0.0; d.vz[e] = 0.0;
+      d.m[e] = 0.0; d.R[e] = 0.0; d.rc[e] = 0.0; d.rc2[e] = 0.0;
+    }
+    __syncthreads();
+    start = e + 1;
+  }
+  if (threadIdx.x == 0) {
+    d.ctrl->n_eject_step = s_count;
+    if (s_count) d.ctrl->n_ftrial = 0;  // for the force evaluation that follows
+  }
+}
+
+void launch_eject(const Dev& d, const Phys& P, cudaStream_t st) { k_eject<<<1, ENT2, 0, st>>>(d, P); }
 
 // ---------------------------------------------------------------------------
 // Standalone Kepler drift of interleaved device arrays.

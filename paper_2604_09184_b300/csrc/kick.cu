@@ -29,6 +29,7 @@ constexpr int KIPT = 2;   // targets per thread
 struct KickArgs {
   int n, S, jchunk;
   int ib, ie;  // target rows [ib, ie) (all sources 0..n-1 act on them)
+  const int* cond;  // if set, the launch does nothing while *cond == 0
   const double *x, *y, *z, *m, *rc, *rc2;
   double* kpart;  // S x 3 x n
   int2* pairs;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
   __shared__ double sx[KNT], sy[KNT], sz[KNT], sm[KNT];
   __shared__ int sh[KNT];
   __shared__ int s_stop;
-  if (threadIdx.x == 0) s_stop = A.ctrl->status;
+  if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
   __syncthreads();
   if (s_stop) return;
   const int n = A.n;
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
   __shared__ double sx[DNT2], sy[DNT2], sz[DNT2];
   __shared__ float smh[DNT2], sml[DNT2], sthr[DNT2];
   __shared__ int s_stop;
-  if (threadIdx.x == 0) s_stop = A.ctrl->status;
+  if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
   __syncthreads();
   if (s_stop) return;
   const int n = A.n;
@@ -378,6 +379,7 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   A.jchunk = jchunk_for(d.n, d.S);
   A.ib = 0;
   A.ie = d.n;
+  A.cond = nullptr;
   A.x = d.x; A.y = d.y; A.z = d.z; A.m = d.m; A.rc = d.rc; A.rc2 = d.rc2;
   A.kpart = d.kpart;
   A.pairs = d.ftrial;
@@ -393,6 +395,7 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
   KickArgs A;
   A.n = n; A.S = S; A.jchunk = jchunk_for(n, S);
   A.ib = ib; A.ie = ie;
+  A.cond = nullptr;
   A.x = x; A.y = y; A.z = z; A.m = m; A.rc = rc; A.rc2 = rc2;
   A.kpart = kpart; A.pairs = pairs; A.cap = cap; A.counter = &ctrl->n_ftrial; A.ctrl = ctrl;
   launch_kick_args(A, precision, st);
@@ -408,11 +411,12 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
 // ---------------------------------------------------------------------------
 constexpr int FNT = 256;
 
-__global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta) {
+__global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
+                                               const int* cond) {
   __shared__ int s_stop, s_M;
   __shared__ double so[5][FNT], snw[5][FNT];
   if (threadIdx.x == 0) {
-    s_stop = d.ctrl->status;
+    s_stop = d.ctrl->status || (cond && *cond == 0);
     s_M = (with_delta && d.ctrl->n_groups > 0) ? d.ctrl->n_members : 0;
   }
   __syncthreads();
@@ -475,7 +479,27 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta)
 
 void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st) {
   const int grid = (d.n + FNT - 1) / FNT;
-  k_finish<<<grid, FNT, 0, st>>>(d, P.G, with_delta);
+  k_finish<<<grid, FNT, 0, st>>>(d, P.G, with_delta, nullptr);
+}
+
+void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStream_t st) {
+  const int* cond = only_if_ejected ? &d.ctrl->n_eject_step : nullptr;
+  KickArgs A;
+  A.n = d.n;
+  A.S = d.S;
+  A.jchunk = jchunk_for(d.n, d.S);
+  A.ib = 0;
+  A.ie = d.n;
+  A.cond = cond;
+  A.x = d.x; A.y = d.y; A.z = d.z; A.m = d.m; A.rc = d.rc; A.rc2 = d.rc2;
+  A.kpart = d.kpart;
+  A.pairs = d.ftrial;
+  A.cap = d.pair_cap;
+  A.counter = &d.ctrl->n_ftrial;
+  A.ctrl = d.ctrl;
+  launch_kick_args(A, P.precision, st);
+  k_finish<<<(d.n + FNT - 1) / FNT, FNT, 0, st>>>(d, P.G, 0, cond);
+  launch_fsal_init(d, st, cond);
 }
 
 // ---------------------------------------------------------------------------

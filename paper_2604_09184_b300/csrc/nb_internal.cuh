@@ -33,7 +33,7 @@ enum StatIdx {
   ST_KEPLER_ITERS,
   ST_MOVED,
   ST_LOG_DROPPED,
-  ST_SPARE
+  ST_EJECTIONS
 };
 
 // Control block in device memory: counters, status and per-step scalars.
@@ -54,6 +54,9 @@ struct Ctrl {
   double E_lost;         // energy removed by mergers
   double dP[3];          // momentum change of group bodies in the current step
   unsigned long long stats[kStatN];
+  double m_ejected;  // mass removed beyond eject_r
+  int n_eject_step;  // bodies removed at the start of the current step
+  int pad3;
 };
 
 // Device arrays carved from the caller's workspace (SoA, FP64).
@@ -93,6 +96,8 @@ struct Dev {
 struct Phys {
   double G, m0, mu, dt_rcrit, hill_factor, vel_factor, bs_tol;
   int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings, rcrit_refresh;
+  int gas, gas_iter;
+  double gas_rho0, gas_p, gas_eta, gas_cd, eject_r;
 };
 
 __device__ __forceinline__ void set_status(Ctrl* c, int code, int where) {
@@ -278,8 +283,13 @@ void launch_scatter(const Dev& d, const Phys& P, cudaStream_t st);
 void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double* v3,
                     const double* m, const double* R, const double* rc, const int* ids,
                     cudaStream_t st);
-void launch_fsal_init(const Dev& d, cudaStream_t st);
+void launch_fsal_init(const Dev& d, cudaStream_t st, const int* cond = nullptr);
 void launch_refresh_rcrit(const Dev& d, const Phys& P, cudaStream_t st);
+void launch_gas(const Dev& d, const Phys& P, double tau, cudaStream_t st);
+void launch_eject(const Dev& d, const Phys& P, cudaStream_t st);
+// force and flags at the current positions (the start-of-step evaluation);
+// with only_if_ejected, nothing happens unless bodies were removed this step
+void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStream_t st);
 void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st);
 void launch_kepler_raw(int n, double mu, double* x3, double* v3, double dt, int max_iter,
                        int* status, cudaStream_t st);

@@ -35,6 +35,9 @@ class NbParams(C.Structure):
         ("kepler_max_iter", C.c_int), ("bs_tol", C.c_double), ("bs_kmax", C.c_int),
         ("bs_max_halvings", C.c_int), ("pair_capacity", C.c_int), ("log_capacity", C.c_int),
         ("kick_split", C.c_int), ("rcrit_refresh", C.c_int),
+        ("gas", C.c_int), ("gas_rho0", C.c_double), ("gas_p", C.c_double),
+        ("gas_eta", C.c_double), ("gas_cd", C.c_double), ("gas_iter", C.c_int),
+        ("eject_r", C.c_double),
     ]
 
 
@@ -42,7 +45,8 @@ class NbStats(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in (
         "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
         "bs_derivs", "merges", "kepler_iters", "moved_bodies", "log_dropped")] + [
-        ("n_active", C.c_int), ("last_pairs", C.c_int)]
+        ("n_active", C.c_int), ("last_pairs", C.c_int), ("ejections", C.c_longlong),
+        ("m_ejected", C.c_double)]
 
 
 class NbError(RuntimeError):
