@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-options", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="steps of the adjoint leg (2000 is the workload; fewer for profiling)")
     ap.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval")
@@ -309,6 +310,12 @@ def run_ours(args):
     if not args.no_batch:
         batched = run_batched(nb, torch, args, flush, stream)
 
+    # the step with the start-of-step options of the non-Newtonian row on:
+    # gas drag at both ends of the step and the ejection scan
+    options = None
+    if not args.no_options:
+        options = run_options(nb, torch, disk, args, ms_per_step, flush, stream)
+
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(nb, torch, stream, args.adjoint_steps, args.adjoint_every)
@@ -328,7 +335,7 @@ def run_ours(args):
                    "precision": args.precision, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
                    "l2": "flushed before each timed step (256 MiB write, outside the step events)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
-        "batched": batched, "adjoint": adjoint,
+        "batched": batched, "adjoint": adjoint, "options": options,
         "clocks": clk, "gpu_launches": gpu_launches,
         "encounters": {"pairs": st["encounter_pairs"], "groups": st["groups"],
                        "bs_substeps": st["bs_substeps"], "merges": st["merges"],
@@ -439,6 +446,31 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
                              "max_cta_ms": bal["max_cta_ms"],
                              "definition": "sum of CTA busy times / (CTAs x longest), last launch"},
             "groups": st["groups"], "merges": st["merges"]}
+
+
+def run_options(nb, torch, disk, args, ms_plain, flush, stream, steps=3):
+    """The same step with gas drag (nominal nebula density) and ejection beyond
+    100 AU switched on; reports the step time and its overhead."""
+    s = nb.NBodySystem(nb.params(dt_rcrit=disk.dt, gas=1, eject_r=100.0), disk.x, disk.v,
+                       disk.m, disk.R)
+    for _ in range(max(args.warmup, 1)):
+        s.step(1, disk.dt)
+    ms = []
+    for _ in range(steps):
+        flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1, disk.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = s.stats()
+    del s
+    t = sum(ms) / len(ms)
+    return {"gas_drag_and_ejection_ms_per_step": t, "plain_ms_per_step": ms_plain,
+            "overhead_ms": t - ms_plain, "ejections": st["ejections"],
+            "setting": "gas rho0 = 2.36e-3 Msun/AU^3 (1.4e-9 g/cm^3) s^-2.75, eta 2e-3, C_D 1; "
+                       "eject_r 100 AU; %d steps after %d warm-up" % (steps, max(args.warmup, 1))}
 
 
 def run_adjoint(nb, torch, stream, nsteps=2000, every=100):
