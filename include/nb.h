@@ -94,6 +94,11 @@ typedef struct {
    * mutual and Eq. Hc terms included, are booked; the cached force is then
    * re-evaluated). 0 (default) = never. Single-system path only. */
   double eject_r;
+  /* Groups of at least bs_cluster_min bodies are integrated by a cluster of
+   * 8 CTAs (one thread per extrapolation column and member, the cluster's
+   * hardware barrier between phases) instead of one CTA; same results bit
+   * for bit. Default 64; 0 = one CTA for every group. */
+  int bs_cluster_min;
 } nb_params;
 
 typedef struct {

@@ -116,6 +116,7 @@ Phys make_phys(const nb_params& p) {
   P.gas_eta = p.gas_eta;
   P.gas_cd = p.gas_cd;
   P.eject_r = p.eject_r;
+  P.bs_cluster_min = p.bs_cluster_min;
   return P;
 }
 
@@ -133,6 +134,7 @@ bool params_ok(const nb_params* p) {
     return false;
   if (!(p->eject_r >= 0.0) || !std::isfinite(p->eject_r) || p->eject_r >= 0.5 * kDeadOffset)
     return false;
+  if (p->bs_cluster_min < 0) return false;
   return true;
 }
 
@@ -228,6 +230,7 @@ void nb_default_params(nb_params* p) {
   p->gas_cd = 1.0;
   p->gas_iter = 30;
   p->eject_r = 0.0;
+  p->bs_cluster_min = 64;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {

@@ -194,17 +194,21 @@ struct BsTally {
 // (all of them for small groups): within a window every column advances one
 // midpoint substep per wave step, and column j completes at wave step 2j,
 // when its Neville row is built and tested. The group state starts in the y
-// fields and ends there. s_red: shared scratch of blockDim.x doubles;
-// s_flags: two shared ints. Returns 0, NB_E_NOCONV or NB_E_TIMEOUT (same in
-// every thread); *El (thread 0) receives the energy removed by mergers.
-static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
-                                         int* s_flags, BsTally& tally, double* El,
-                                         BsRec* rec = nullptr) {
+// fields and ends there. Sy is the team that runs it: one CTA (BlockTeam)
+// or a thread-block cluster (ClusterTeam, in encounter.cu); it provides the
+// thread index and count, the barrier, a max-reduction and two flag words.
+// Every team member takes the same branches. Returns 0, NB_E_NOCONV or
+// NB_E_TIMEOUT (the same in every thread); *El (tid 0) receives the energy
+// removed by mergers.
+template <class Sy>
+static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& sy,
+                                   BsTally& tally, double* El, BsRec* rec) {
   int rec_n = 0;  // accepted substeps recorded (the same in every thread)
   const int kmax = c.kmax;
   const int M = c.M;
-  const int NT = blockDim.x;
-  const int tid = threadIdx.x;
+  const int NT = sy.nthreads();
+  const int tid = sy.tid();
+  int* s_flags = sy.flags();
   const int offT = bs_off_T(kmax);
   // columns per window: enough (column, member) items to fill about two
   // passes of the CTA, never fewer than one column
@@ -235,7 +239,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
     }
     // f0 = f(y), shared by every column
     for (int b = tid; b < M; b += NT) bs_deriv(c, OY, OF0, b);
-    __syncthreads();
+    sy.sync();
     tally.derivs += 1;
     for (int ja = 1; ja <= kmax && !s_flags[0]; ja += W) {
       const int jb = ja + W - 1 < kmax ? ja + W - 1 : kmax;
@@ -251,7 +255,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
           col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
         }
       }
-      __syncthreads();
+      sy.sync();
       for (int t = 1; t <= 2 * jb; ++t) {
         // columns still running at wave step t: 2j >= t
         const int j0 = max(ja, (t + 1) / 2);
@@ -260,7 +264,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
           const int j = j0 + it / M, b = it % M;
           bs_deriv(c, bs_off_col(j) + CZC, bs_off_col(j) + CF, b);
         }
-        __syncthreads();
+        sy.sync();
         tally.derivs += ncol;
         for (int it = tid; it < ncol * M; it += NT) {
           const int j = j0 + it / M, b = it % M;
@@ -278,7 +282,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
             for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (col[CZC + k] + col[CZM + k] + hs * col[CF + k]);
           }
         }
-        __syncthreads();
+        sy.sync();
         if ((t & 1) || t / 2 < ja) continue;
         const int j = t / 2;  // column j is complete: Neville row j and the test
         double emax = 0.0;
@@ -307,24 +311,21 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
             }
           }
         }
-        s_red[tid] = emax;
-        __syncthreads();
+        const double e = sy.max_to_first(emax);  // valid in tid 0
         if (tid == 0) {
-          double e = 0.0;
-          for (int q = 0; q < NT; ++q) e = fmax(e, s_red[q]);
           if (j >= 3 && e <= P.bs_tol) {
             s_flags[0] = 1;
             s_flags[1] = j;
           }
         }
-        __syncthreads();
+        sy.sync();
         if (s_flags[0]) {
           for (int b = tid; b < M; b += NT) {
             double* s = c.base + (size_t)b * c.stride;
             const double* Tc = s + offT + (j & 1) * kmax * 6 + 6 * (j - 1);
             for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
           }
-          __syncthreads();
+          sy.sync();
           break;
         }
       }
@@ -347,7 +348,7 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
       }
       if (P.merge) {
         if (tid == 0) bs_merge_scan(c, P, El, &merges, rec, rec_n - 1);
-        __syncthreads();
+        sy.sync();
       }
       if (level > 0 && (done & 1) == 0 && kacc <= kmax - 2) {
         --level;
@@ -366,12 +367,38 @@ static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h
       status = NB_E_TIMEOUT;
       break;
     }
-    __syncthreads();
+    sy.sync();
   }
   tally.merges += merges;
   if (rec && tid == 0) rec->counts[0] = rec_n;
-  __syncthreads();
+  sy.sync();
   return status;
+}
+
+// One CTA as the team: shared scratch s_red (blockDim.x doubles) and two
+// shared flag words.
+struct BlockTeam {
+  double* s_red;
+  int* s_flags;
+  __device__ int tid() const { return threadIdx.x; }
+  __device__ int nthreads() const { return blockDim.x; }
+  __device__ int* flags() const { return s_flags; }
+  __device__ void sync() const { __syncthreads(); }
+  __device__ double max_to_first(double v) const {
+    s_red[threadIdx.x] = v;
+    __syncthreads();
+    double e = 0.0;
+    if (threadIdx.x == 0)
+      for (int q = 0; q < (int)blockDim.x; ++q) e = fmax(e, s_red[q]);
+    return e;
+  }
+};
+
+static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
+                                         int* s_flags, BsTally& tally, double* El,
+                                         BsRec* rec = nullptr) {
+  BlockTeam t{s_red, s_flags};
+  return bs_integrate(c, P, h, t, tally, El, rec);
 }
 
 }  // namespace nb

@@ -11,15 +11,26 @@
 //   restarting from the state saved after C(h/2). Substep halving on
 //   failure, doubling back after an early success on an aligned boundary,
 //   merging scan after every accepted substep.
+// k_bs_cluster (one thread-block cluster of 16 CTAs, else 8, per large group, groups
+//   of at least bs_cluster_min bodies): the same solver with the group's
+//   (column, member) work items spread over the cluster's threads and the
+//   hardware cluster barrier between phases; results are bit-identical to
+//   the single-CTA solver (same arithmetic per item, max-reductions only).
 // k_scatter (one CTA): momentum change of the group bodies, energy removed
 //   by mergers, and the write-back of the group results.
+#include <cooperative_groups.h>
+
 #include "bs.cuh"
 #include "nb_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nb {
 
 constexpr int ENT = 1024;  // threads of k_encounter
 constexpr int BNT = 64;    // threads of a BS CTA
+constexpr int CCL_MAX = 16;  // CTAs per cluster of the large-group solver (16: opt-in size)
+constexpr int CNT = 128;     // threads per CTA of the large-group solver
 
 __device__ void bitonic_sort(unsigned long long* a, int P2) {
   for (int k = 2; k <= P2; k <<= 1) {
@@ -216,6 +227,7 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
   BsTally tally{0, 0, 0, 0};
   for (int grp = blockIdx.x; grp < s_ng; grp += gridDim.x) {
     const int off = d.grp_off[grp];
+    if (P.bs_cluster_min > 0 && d.grp_off[grp + 1] - off >= P.bs_cluster_min) continue;
     BsCtx c;
     c.M = d.grp_off[grp + 1] - off;
     c.stride = d.bs_stride;
@@ -256,10 +268,161 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
   }
 }
 
+// A thread-block cluster as the Bulirsch-Stoer team: flags and the per-CTA
+// maxima live in the shared memory of the cluster's first CTA (read by the
+// others through distributed shared memory); the barrier is the cluster's.
+struct ClusterTeam {
+  int* s_flags;    // CTA 0's flags (mapped)
+  double* s_slot;  // CTA 0's per-CTA maxima (mapped), one per CTA of the cluster
+  double* s_red;   // this CTA's reduction scratch, CNT entries
+  int ncta;        // CTAs in the cluster
+  __device__ int tid() const { return (int)cg::this_cluster().block_rank() * CNT + threadIdx.x; }
+  __device__ int nthreads() const { return ncta * CNT; }
+  __device__ int* flags() const { return s_flags; }
+  __device__ void sync() const { cg::this_cluster().sync(); }
+  __device__ double max_to_first(double v) const {
+    s_red[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double e = 0.0;
+      for (int q = 0; q < CNT; ++q) e = fmax(e, s_red[q]);
+      s_slot[cg::this_cluster().block_rank()] = e;
+    }
+    cg::this_cluster().sync();
+    double e = 0.0;
+    if (tid() == 0)
+      for (int q = 0; q < ncta; ++q) e = fmax(e, s_slot[q]);
+    return e;
+  }
+};
+
+__global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int min_m) {
+  __shared__ double s_red[CNT];
+  __shared__ double s_slot_own[CCL_MAX];
+  __shared__ int s_flags_own[2];
+  __shared__ int s_ctl[2];
+  cg::cluster_group cl = cg::this_cluster();
+  // the cluster's first CTA reads the control block once; every CTA takes
+  // its values from there, so all CTAs of the cluster decide alike
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    s_ctl[0] = d.ctrl->status;
+    s_ctl[1] = d.ctrl->n_groups;
+  }
+  cl.sync();
+  const int* ctl0 = cl.map_shared_rank(s_ctl, 0);
+  const int stop = ctl0[0], ng = ctl0[1];
+  if (stop) {
+    cl.sync();  // CTA 0's shared memory stays until every CTA has read it
+    return;
+  }
+  const int ncta = (int)cl.num_blocks();
+  ClusterTeam team{cl.map_shared_rank(s_flags_own, 0), cl.map_shared_rank(s_slot_own, 0), s_red,
+                   ncta};
+  const int cid = blockIdx.x / ncta, ncl = gridDim.x / ncta;
+  const int tid = team.tid(), NT = team.nthreads();
+  BsTally tally{0, 0, 0, 0};
+  for (int grp = cid; grp < ng; grp += ncl) {
+    const int off = d.grp_off[grp];
+    const int M = d.grp_off[grp + 1] - off;
+    if (M < min_m) continue;
+    BsCtx c;
+    c.M = M;
+    c.stride = d.bs_stride;
+    c.base = d.gscr + (size_t)off * d.bs_stride;
+    c.g = d.gnew + (size_t)off * 10;
+    c.kmax = P.bs_kmax;
+    c.G = P.G;
+    c.mu = P.mu;
+    for (int b = tid; b < M; b += NT) {
+      const int body = d.grp_mem[off + b];
+      double* y = c.base + (size_t)b * c.stride + OY;
+      y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
+      y[3] = d.vxs[body]; y[4] = d.vys[body]; y[5] = d.vzs[body];
+      double* g = c.g + 10 * b;
+      g[6] = d.m[body];
+      g[7] = d.R[body];
+      g[8] = d.rc[body];
+      g[9] = 1.0;
+      bs_set_aux(c, b, P.G, g[6], g[8]);
+    }
+    cl.sync();
+    double El = 0.0;
+    const int status = bs_integrate(c, P, h, team, tally, &El, (BsRec*)nullptr);
+    if (status && tid == 0) set_status(d.ctrl, status, 31);
+    for (int b = tid; b < M; b += NT) {
+      const double* y = c.base + (size_t)b * c.stride + OY;
+      double* g = c.g + 10 * b;
+      for (int k = 0; k < 6; ++k) g[k] = y[k];
+    }
+    if (tid == 0) d.gEl[grp] = El;
+    cl.sync();
+  }
+  if (tid == 0) {
+    atomicAdd(&d.ctrl->stats[ST_BS_DERIVS], (unsigned long long)tally.derivs);
+    atomicAdd(&d.ctrl->stats[ST_BS_SUBSTEPS], (unsigned long long)tally.substeps);
+    atomicAdd(&d.ctrl->stats[ST_BS_HALVINGS], (unsigned long long)tally.halvings);
+    atomicAdd(&d.ctrl->stats[ST_MERGES], (unsigned long long)tally.merges);
+  }
+  // no CTA may exit while another still reads its shared memory
+  cl.sync();
+}
+
+// Cluster size for the large-group solver: 16 CTAs (opt-in size) where the
+// device can schedule such clusters, else the portable 8; as many clusters
+// as fit on the device at once.
+static int cluster_shape(int* ncl) {
+  static int size = 0, count = 0;
+  if (!size) {
+    cudaFuncSetAttribute(k_bs_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c = CCL_MAX; c >= 8 && !size; c /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(c, 1, 1);
+      cfg.blockDim = dim3(CNT, 1, 1);
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int active = 0;
+      if (cudaOccupancyMaxActiveClusters(&active, k_bs_cluster, &cfg) == cudaSuccess && active > 0) {
+        size = c;
+        count = active;
+      }
+    }
+    cudaGetLastError();  // a refused size leaves an error behind
+    if (!size) {
+      size = 8;
+      count = 1;
+    }
+  }
+  *ncl = count;
+  return size;
+}
+
+void launch_bs_cluster(const Dev& d, const Phys& P, double h, cudaStream_t st) {
+  int ncl = 1;
+  const int c = cluster_shape(&ncl);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = c;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(c * ncl, 1, 1);
+  cfg.blockDim = dim3(CNT, 1, 1);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_bs_cluster, d, P, h, P.bs_cluster_min);
+}
+
 void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
   int grid = d.n < 2 * 148 ? d.n : 2 * 148;
   if (grid < 1) grid = 1;
   k_bs<<<grid, BNT, 0, st>>>(d, P, h);
+  if (P.bs_cluster_min > 0 && d.n >= P.bs_cluster_min) launch_bs_cluster(d, P, h, st);
 }
 
 // ---------------------------------------------------------------------------

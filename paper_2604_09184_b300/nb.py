@@ -37,7 +37,7 @@ class NbParams(C.Structure):
         ("kick_split", C.c_int), ("rcrit_refresh", C.c_int),
         ("gas", C.c_int), ("gas_rho0", C.c_double), ("gas_p", C.c_double),
         ("gas_eta", C.c_double), ("gas_cd", C.c_double), ("gas_iter", C.c_int),
-        ("eject_r", C.c_double),
+        ("eject_r", C.c_double), ("bs_cluster_min", C.c_int),
     ]
 
 

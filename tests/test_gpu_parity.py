@@ -365,6 +365,34 @@ def test_step_parity_ejection_and_all_start_of_step_options():
         assert abs(eg["E"] - er["E"]) <= 1e-12 * abs(er["E"])
 
 
+def test_large_groups_on_clusters_bit_identical_and_match_oracle():
+    """Groups of at least bs_cluster_min bodies go to the cluster solver (8
+    CTAs, hardware cluster barrier). Literal velocity term (vel_mode 1) on a
+    2050-body disk makes groups of up to ~20 bodies; with the threshold at 8
+    several run on clusters. Same bits as the one-CTA solver, and the oracle's
+    states and encounter lists."""
+    nb = nbmod()
+    d = ics.workload("mmsn_16k_js", n=2048)
+    rp = nbref.params(dt_rcrit=d.dt, vel_mode=1)
+    rc = oracle_rc(d, rp)
+    runs = {}
+    for thr in (0, 8):
+        g = nb.NBodySystem(nb.params(dt_rcrit=d.dt, vel_mode=1, bs_cluster_min=thr), d.x, d.v,
+                           d.m, d.R, rc=rc)
+        g.step(10, d.dt)
+        runs[thr] = g
+    a, b = runs[0].state(), runs[8].state()
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+    sa, sb = runs[0].stats(), runs[8].stats()
+    for k in ("groups", "bs_substeps", "bs_halvings", "merges", "encounter_pairs"):
+        assert sa[k] == sb[k], k
+    assert sa["groups"] > 0
+    ref = nbref.RefSystem(rp, d.x, d.v, d.m, d.R, rc=rc)
+    assert ref.step(10, d.dt) == 0
+    compare_states(ref, runs[8])
+    assert np.array_equal(ref.encounter_list(), runs[8].encounter_list())
+
+
 def test_step_parity_velocity_mode_literal():
     d = ics.workload("toy_disk_256", n=128)
     ref, gpu = run_both(d, 30, vel_mode=1)
