@@ -280,6 +280,8 @@ void nbref_default_params(nbref_params* p) {
   p->gas_cd = 1.0;
   p->gas_iter = 30;
   p->eject_r = 0.0;
+  p->ml_levels = 0;
+  p->ml_factor = 3;
 }
 
 /* ------------------------------------------------------------------ */
@@ -441,6 +443,7 @@ typedef struct {
   const double* rc;
   const int* alive;
   long long derivs;
+  double rc_scale; /* the level's critical radii are rc * rc_scale */
 } bs_sys;
 
 /* y layout: per body [x, y, z, vx, vy, vz] */
@@ -469,7 +472,7 @@ static void bs_deriv(bs_sys* S, const double* y, double* dy) {
       double q2 = fma(dz, dz, fma(dyy, dyy, dx * dx));
       if (q2 == 0.0) continue;
       double q = sqrt(q2);
-      double rc = S->rc[i] > S->rc[j] ? S->rc[i] : S->rc[j];
+      double rc = (S->rc[i] > S->rc[j] ? S->rc[i] : S->rc[j]) * S->rc_scale;
       double w = (q2 < rc * rc) ? kick_weight(q, rc) : 1.0;
       double f = G * S->m[j] * (1.0 - w) / (q2 * q);
       ax += f * dx;
@@ -577,8 +580,21 @@ static void bs_merge_scan(const nbref_params* p, int n, double* y, double* m, do
   }
 }
 
+static int bs_group_scaled(const nbref_params* p, int n, double* x, double* v, double* m,
+                           double* R, double* rc, int* alive, double h, double rc_scale,
+                           double* E_lost, nbref_stats* st);
+
 int nbref_bs_group(const nbref_params* p, int n, double* x, double* v, double* m, double* R,
                    double* rc, int* alive, double h, double* E_lost, nbref_stats* st) {
+  return bs_group_scaled(p, n, x, v, m, R, rc, alive, h, 1.0, E_lost, st);
+}
+
+/* The direct solver with the critical radii of the changeover scaled by
+ * rc_scale (the last level of the multi-level changeover); r_crit itself,
+ * and a merged survivor's recomputed r_crit, stay unscaled. */
+static int bs_group_scaled(const nbref_params* p, int n, double* x, double* v, double* m,
+                           double* R, double* rc, int* alive, double h, double rc_scale,
+                           double* E_lost, nbref_stats* st) {
   int d = 6 * n;
   int kmax = p->bs_kmax;
   if (kmax < 3) kmax = 3;
@@ -592,7 +608,7 @@ int nbref_bs_group(const nbref_params* p, int n, double* x, double* v, double* m
       y[6 * i + k] = x[3 * i + k];
       y[6 * i + 3 + k] = v[3 * i + k];
     }
-  bs_sys S = {p, n, m, rc, alive, 0};
+  bs_sys S = {p, n, m, rc, alive, 0, rc_scale};
 #define TT(j, k) (T + ((size_t)(j) * (kmax + 1) + (k)) * d)
   int level = 0;          /* substep = h / 2^level */
   long long done = 0;     /* substeps completed at the current level */
@@ -653,6 +669,194 @@ int nbref_bs_group(const nbref_params* p, int n, double* x, double* v, double* m
   free(zm);
   free(zc);
   free(f);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Multi-level changeover (section "Increasing N": the step is reduced  */
+/* level by level for the bodies concerned, each level with its own     */
+/* smooth changeover, and only the last level uses the direct solver).  */
+/* Level l has critical radii r_crit * f^-l and substeps tau / f.       */
+/* ml_integrate(S, l, tau) moves the bodies S over tau under their       */
+/* Kepler motion and the close part of their mutual interaction with    */
+/* weight 1 - w_l; at l = L (ml_levels) that is the direct solver with  */
+/* radii scaled by f^-L, below it is f substeps of                      */
+/*   K_{l+1}(tau'/2) A_{l+1}(tau') K_{l+1}(tau'/2),  tau' = tau / f,     */
+/* K_{l+1} the kick with weight w_{l+1} - w_l (the split                  */
+/* 1 - w_l = (w_{l+1} - w_l) + (1 - w_{l+1}) of the close part), and    */
+/* A_{l+1} the Kepler drift of S except for the level-(l+1) groups:      */
+/* pairs within r_crit f^-(l+1) at the substep's start or after the     */
+/* trial drift, joined into connected components, each restarted from  */
+/* the substep's start and integrated by ml_integrate at level l + 1.   */
+/* ------------------------------------------------------------------ */
+static int uf_find(int* parent, int k);
+
+typedef struct {
+  const nbref_params* p;
+  double *x, *v, *m, *R, *rc; /* group-local arrays, x and v 3 per body */
+  int* alive;
+  double* E_lost;
+  nbref_stats* st;
+} ml_ctx;
+
+/* f^-level by repeated division (the same rounding on every side) */
+static double ml_scale(const nbref_params* p, int level) {
+  double s = 1.0;
+  for (int l = 0; l < level; ++l) s /= (double)p->ml_factor;
+  return s;
+}
+
+static double pair_w(double q2, double q, double rcl) {
+  return (q2 < rcl * rcl) ? kick_weight(q, rcl) : 1.0;
+}
+
+/* K_level(tau): v_i += tau sum_j G m_j (w_level - w_{level-1}) d_ij / r_ij^3 over
+ * the live pairs of S (accelerations from the positions first, then applied). */
+static void ml_kick(ml_ctx* c, const int* S, int ns, int level, double tau) {
+  const double G = c->p->G;
+  const double sl = ml_scale(c->p, level), sp = ml_scale(c->p, level - 1);
+  double* acc = (double*)calloc(3 * (size_t)ns, sizeof(double));
+  for (int a = 0; a < ns; ++a) {
+    const int i = S[a];
+    if (!c->alive[i]) continue;
+    for (int b = 0; b < ns; ++b) {
+      const int j = S[b];
+      if (j == i || !c->alive[j]) continue;
+      const double dx = c->x[3 * j] - c->x[3 * i], dy = c->x[3 * j + 1] - c->x[3 * i + 1],
+                   dz = c->x[3 * j + 2] - c->x[3 * i + 2];
+      const double q2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      if (q2 == 0.0) continue;
+      const double q = sqrt(q2);
+      const double rcp = c->rc[i] > c->rc[j] ? c->rc[i] : c->rc[j];
+      const double dw = pair_w(q2, q, rcp * sl) - pair_w(q2, q, rcp * sp);
+      if (dw == 0.0) continue;
+      const double f = G * c->m[j] * dw / (q2 * q);
+      acc[3 * a] += f * dx;
+      acc[3 * a + 1] += f * dy;
+      acc[3 * a + 2] += f * dz;
+    }
+  }
+  for (int a = 0; a < ns; ++a) {
+    const int i = S[a];
+    if (!c->alive[i]) continue;
+    for (int k = 0; k < 3; ++k) c->v[3 * i + k] += tau * acc[3 * a + k];
+  }
+  free(acc);
+}
+
+/* pairs (a < b) of S within the level's radii join in parent[] */
+static void ml_flag(ml_ctx* c, const int* S, int ns, int level, int* parent) {
+  const double sl = ml_scale(c->p, level);
+  for (int a = 0; a < ns; ++a) {
+    const int i = S[a];
+    if (!c->alive[i]) continue;
+    for (int b = a + 1; b < ns; ++b) {
+      const int j = S[b];
+      if (!c->alive[j]) continue;
+      const double dx = c->x[3 * j] - c->x[3 * i], dy = c->x[3 * j + 1] - c->x[3 * i + 1],
+                   dz = c->x[3 * j + 2] - c->x[3 * i + 2];
+      const double q2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      const double rcl = (c->rc[i] > c->rc[j] ? c->rc[i] : c->rc[j]) * sl;
+      if (!(q2 < rcl * rcl)) continue;
+      const int ra = uf_find(parent, a), rb = uf_find(parent, b);
+      if (ra < rb)
+        parent[rb] = ra;
+      else if (rb < ra)
+        parent[ra] = rb;
+    }
+  }
+}
+
+static int ml_integrate(ml_ctx* c, const int* S, int ns, int level, double tau) {
+  const nbref_params* p = c->p;
+  if (level >= p->ml_levels) {
+    /* the direct solver on S with the level's radii */
+    double* gx = (double*)malloc(sizeof(double) * 3 * (size_t)ns);
+    double* gv = (double*)malloc(sizeof(double) * 3 * (size_t)ns);
+    double* gm = (double*)malloc(sizeof(double) * (size_t)ns);
+    double* gR = (double*)malloc(sizeof(double) * (size_t)ns);
+    double* grc = (double*)malloc(sizeof(double) * (size_t)ns);
+    int* ga = (int*)malloc(sizeof(int) * (size_t)ns);
+    for (int a = 0; a < ns; ++a) {
+      const int i = S[a];
+      for (int k = 0; k < 3; ++k) {
+        gx[3 * a + k] = c->x[3 * i + k];
+        gv[3 * a + k] = c->v[3 * i + k];
+      }
+      gm[a] = c->m[i]; gR[a] = c->R[i]; grc[a] = c->rc[i]; ga[a] = c->alive[i];
+    }
+    const int st = bs_group_scaled(p, ns, gx, gv, gm, gR, grc, ga, tau, ml_scale(p, level),
+                                   c->E_lost, c->st);
+    for (int a = 0; a < ns; ++a) {
+      const int i = S[a];
+      for (int k = 0; k < 3; ++k) {
+        c->x[3 * i + k] = gx[3 * a + k];
+        c->v[3 * i + k] = gv[3 * a + k];
+      }
+      c->m[i] = gm[a]; c->R[i] = gR[a]; c->rc[i] = grc[a]; c->alive[i] = ga[a];
+    }
+    free(gx); free(gv); free(gm); free(gR); free(grc); free(ga);
+    return st;
+  }
+  const int f = p->ml_factor;
+  const double t1 = tau / (double)f;
+  const double mu = p->G * p->m0;
+  double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)ns);
+  double* vs = (double*)malloc(sizeof(double) * 3 * (size_t)ns);
+  int* parent = (int*)malloc(sizeof(int) * (size_t)ns);
+  int* sub = (int*)malloc(sizeof(int) * (size_t)ns);
+  int status = NBREF_OK;
+  for (int k = 0; k < f && status == NBREF_OK; ++k) {
+    ml_kick(c, S, ns, level + 1, 0.5 * t1);
+    for (int a = 0; a < ns; ++a) parent[a] = a;
+    ml_flag(c, S, ns, level + 1, parent);
+    for (int a = 0; a < ns; ++a)
+      for (int q = 0; q < 3; ++q) {
+        xs[3 * a + q] = c->x[3 * S[a] + q];
+        vs[3 * a + q] = c->v[3 * S[a] + q];
+      }
+    for (int a = 0; a < ns; ++a) {
+      const int i = S[a];
+      if (!c->alive[i]) continue;
+      int it;
+      const int kst = nbref_kepler_drift(mu, c->x + 3 * i, c->v + 3 * i, t1, p->kepler_max_iter, &it);
+      if (c->st) c->st->kepler_iters += it;
+      if (kst) status = kst;
+    }
+    if (status) break;
+    ml_flag(c, S, ns, level + 1, parent);
+    for (int a = 0; a < ns; ++a) parent[a] = uf_find(parent, a);
+    for (int a = 0; a < ns && status == NBREF_OK; ++a) {
+      if (parent[a] != a) continue;
+      int nsub = 0;
+      for (int b = a; b < ns; ++b)
+        if (parent[b] == a) sub[nsub++] = S[b];
+      if (nsub < 2) continue;
+      for (int b = a; b < ns; ++b) {
+        if (parent[b] != a) continue;
+        for (int q = 0; q < 3; ++q) {
+          c->x[3 * S[b] + q] = xs[3 * b + q];
+          c->v[3 * S[b] + q] = vs[3 * b + q];
+        }
+      }
+      if (c->st) c->st->ml_groups++;
+      status = ml_integrate(c, sub, nsub, level + 1, t1);
+    }
+    if (status) break;
+    ml_kick(c, S, ns, level + 1, 0.5 * t1);
+    if (c->st) c->st->ml_substeps++;
+  }
+  free(xs); free(vs); free(parent); free(sub);
+  return status;
+}
+
+int nbref_ml_group(const nbref_params* p, int n, double* x, double* v, double* m, double* R,
+                   double* rc, int* alive, double h, double* E_lost, nbref_stats* st) {
+  ml_ctx mc = {p, x, v, m, R, rc, alive, E_lost, st};
+  int* idx = (int*)malloc(sizeof(int) * (size_t)n);
+  for (int q = 0; q < n; ++q) idx[q] = q;
+  const int status = ml_integrate(&mc, idx, n, 0, h);
+  free(idx);
   return status;
 }
 
@@ -986,7 +1190,15 @@ static int one_step(nbref_system* s, double h) {
         grc[q] = s->rc[b];
         ga[q] = 1;
       }
-      status = nbref_bs_group(p, gn, gx, gv, gm, gR, grc, ga, h, &s->E_lost, &s->st);
+      if (p->ml_levels > 0) {
+        ml_ctx mc = {p, gx, gv, gm, gR, grc, ga, &s->E_lost, &s->st};
+        int* idx = (int*)malloc(sizeof(int) * (size_t)gn);
+        for (int q = 0; q < gn; ++q) idx[q] = q;
+        status = ml_integrate(&mc, idx, gn, 0, h);
+        free(idx);
+      } else {
+        status = nbref_bs_group(p, gn, gx, gv, gm, gR, grc, ga, h, &s->E_lost, &s->st);
+      }
       s->st.groups++;
       for (int q = 0; q < gn; ++q) {
         int b = members[q];

@@ -46,6 +46,12 @@ typedef struct {
   double gas_cd;       /* drag coefficient C_D */
   int gas_iter;        /* cap on implicit-midpoint iterations */
   double eject_r;      /* bodies beyond this heliocentric distance are removed; 0 = never */
+  /* Multi-level changeover (section "Increasing N"): ml_levels intermediate
+   * levels between the step and the direct solver; level l uses critical
+   * radii r_crit / ml_factor^l and steps dt / ml_factor^l. 0 = groups go to
+   * the direct solver at once. */
+  int ml_levels;
+  int ml_factor;
 } nbref_params;
 
 typedef struct {
@@ -60,6 +66,8 @@ typedef struct {
   long long kepler_iters;   /* Kepler iterations summed over bodies and steps */
   long long ejections;      /* bodies removed beyond eject_r */
   double m_ejected;         /* their mass */
+  long long ml_substeps;    /* substeps taken on the intermediate changeover levels */
+  long long ml_groups;      /* groups formed on the intermediate levels */
 } nbref_stats;
 
 typedef struct nbref_system nbref_system;
@@ -122,6 +130,12 @@ void nbref_destroy(nbref_system* s);
  * not depend on it); n < 1 means 1. Used to time the oracle on 1 and on all
  * cores in one process. */
 void nbref_set_threads(int n);
+
+/* One close-encounter group over h by the multi-level changeover
+ * (ml_levels levels; the direct solver of nbref_bs_group when 0). Arguments
+ * as nbref_bs_group. */
+int nbref_ml_group(const nbref_params* p, int n, double* x, double* v, double* m, double* R,
+                   double* rc, int* alive, double h, double* E_lost, nbref_stats* st);
 
 /* One body's gas-drag update by the implicit midpoint method (Eq. implicit):
  * vout = v + tau a_f(x, (v + vout) / 2); Pm0 = P / m0 (the star's velocity

@@ -37,13 +37,16 @@ class RefParams(C.Structure):
         ("gas_cd", C.c_double),
         ("gas_iter", C.c_int),
         ("eject_r", C.c_double),
+        ("ml_levels", C.c_int),
+        ("ml_factor", C.c_int),
     ]
 
 
 class RefStats(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in (
         "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
-        "bs_derivs", "merges", "kepler_iters", "ejections")] + [("m_ejected", C.c_double)]
+        "bs_derivs", "merges", "kepler_iters", "ejections")] + [("m_ejected", C.c_double)] + [
+        (k, C.c_longlong) for k in ("ml_substeps", "ml_groups")]
 
 
 _D = C.POINTER(C.c_double)
@@ -70,6 +73,8 @@ def lib():
         L.nbref_bs_group.argtypes = [C.POINTER(RefParams), C.c_int, _D, _D, _D, _D, _D, _I,
                                      C.c_double, _D, C.POINTER(RefStats)]
         L.nbref_bs_group.restype = C.c_int
+        L.nbref_ml_group.argtypes = L.nbref_bs_group.argtypes
+        L.nbref_ml_group.restype = C.c_int
         L.nbref_create.argtypes = [C.POINTER(RefParams), C.c_int, _D, _D, _D, _D, _D, _I, _I]
         L.nbref_create.restype = C.c_void_p
         L.nbref_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
@@ -192,7 +197,9 @@ def forces_targets(x, m, rc, targets, G=2.959122082855911e-4, cap=None):
     return a, pairs[:k].copy()
 
 
-def bs_group(p: RefParams, x, v, m, R, rc, h):
+def bs_group(p: RefParams, x, v, m, R, rc, h, multilevel=False):
+    """One group over h by the direct solver, or by the multi-level
+    changeover (p.ml_levels levels) when multilevel is set."""
     x = np.array(x, dtype=np.float64).reshape(-1, 3)
     v = np.array(v, dtype=np.float64).reshape(-1, 3)
     n = x.shape[0]
@@ -202,8 +209,9 @@ def bs_group(p: RefParams, x, v, m, R, rc, h):
     alive = np.ones(n, dtype=np.int32)
     El = C.c_double(0.0)
     st = RefStats()
-    status = lib().nbref_bs_group(C.byref(p), n, _dp(x), _dp(v), _dp(m), _dp(R), _dp(rc),
-                                  _ip(alive), h, C.byref(El), C.byref(st))
+    fn = lib().nbref_ml_group if multilevel else lib().nbref_bs_group
+    status = fn(C.byref(p), n, _dp(x), _dp(v), _dp(m), _dp(R), _dp(rc), _ip(alive), h,
+                C.byref(El), C.byref(st))
     return dict(status=status, x=x, v=v, m=m, R=R, rc=rc, alive=alive, E_lost=El.value,
                 stats={k: getattr(st, k) for k, _ in RefStats._fields_})
 
