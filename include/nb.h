@@ -99,6 +99,18 @@ typedef struct {
    * hardware barrier between phases) instead of one CTA; same results bit
    * for bit. Default 64; 0 = one CTA for every group. */
   int bs_cluster_min;
+  /* Multi-level changeover (section "Increasing N": the step is reduced level
+   * by level for the bodies of a close encounter, each level with its own
+   * changeover, the direct solver only at the last level). Level l has
+   * critical radii r_crit ml_factor^-l and substeps tau / ml_factor; a group
+   * of level l is integrated by ml_factor substeps of a kick with weight
+   * w_(l+1) - w_l, the Kepler drift of its bodies and, for the pairs within
+   * the level-(l+1) radii, groups of level l + 1; at l = ml_levels by the
+   * direct solver with the radii of that level. 0 (default) = the direct
+   * solver for every group; at most 3. With levels on, every group runs on
+   * one CTA (bs_cluster_min does not apply). Single-system path only. */
+  int ml_levels;
+  int ml_factor;       /* default 3; 2..64 */
 } nb_params;
 
 typedef struct {
@@ -117,6 +129,8 @@ typedef struct {
   int last_pairs;            /* |F| of the last force evaluation */
   long long ejections;       /* bodies removed beyond eject_r */
   double m_ejected;          /* their mass */
+  long long ml_substeps;     /* substeps on the intermediate changeover levels */
+  long long ml_groups;       /* groups formed on the intermediate levels */
 } nb_stats_t;
 
 typedef struct nb_system nb_system; /* opaque host handle (small, malloc'd by the library) */

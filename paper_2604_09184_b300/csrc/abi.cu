@@ -84,6 +84,12 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
   d.gscr = c.take<double>((size_t)n * d.bs_stride);
   d.gnew = c.take<double>((size_t)n * 10);
   d.gEl = c.take<double>(n);
+  if (p.ml_levels > 0) {
+    d.ml_gscr = c.take<double>((size_t)n * d.bs_stride);
+    d.ml_gnew = c.take<double>((size_t)n * 10);
+    d.ml_list = c.take<int>((size_t)(kMlMax + 1) * n);
+    d.ml_parent = c.take<int>((size_t)(kMlMax + 1) * n);
+  }
   d.snap = c.take<double>((size_t)16 * n);
   d.snap_i = c.take<int>((size_t)n + 2 * (size_t)d.pair_cap);
   d.ctrl = c.take<Ctrl>(1);
@@ -117,6 +123,8 @@ Phys make_phys(const nb_params& p) {
   P.gas_cd = p.gas_cd;
   P.eject_r = p.eject_r;
   P.bs_cluster_min = p.bs_cluster_min;
+  P.ml_levels = p.ml_levels;
+  P.ml_factor = p.ml_factor;
   return P;
 }
 
@@ -135,6 +143,8 @@ bool params_ok(const nb_params* p) {
   if (!(p->eject_r >= 0.0) || !std::isfinite(p->eject_r) || p->eject_r >= 0.5 * kDeadOffset)
     return false;
   if (p->bs_cluster_min < 0) return false;
+  if (p->ml_levels < 0 || p->ml_levels > kMlMax || p->ml_factor < 2 || p->ml_factor > 64)
+    return false;
   return true;
 }
 
@@ -231,6 +241,8 @@ void nb_default_params(nb_params* p) {
   p->gas_iter = 30;
   p->eject_r = 0.0;
   p->bs_cluster_min = 64;
+  p->ml_levels = 0;
+  p->ml_factor = 3;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {
@@ -516,6 +528,8 @@ int nb_stats(nb_system* s, nb_stats_t* out) {
   out->last_pairs = c.n_fprev;
   out->ejections = (long long)c.stats[ST_EJECTIONS];
   out->m_ejected = c.m_ejected;
+  out->ml_substeps = (long long)c.stats[ST_ML_SUBSTEPS];
+  out->ml_groups = (long long)c.stats[ST_ML_GROUPS];
   return NB_OK;
 }
 

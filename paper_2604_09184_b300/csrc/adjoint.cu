@@ -932,7 +932,7 @@ extern "C" {
 
 size_t nb_adjoint_workspace_bytes(const nb_params* p, int n, int nsteps, int checkpoint_every) {
   if (!p || n < 1 || nsteps < 1 || checkpoint_every < 1 || nb_workspace_bytes(p, n) == 0 ||
-      p->rcrit_refresh != 0 || p->gas != 0 || p->eject_r != 0.0)
+      p->rcrit_refresh != 0 || p->gas != 0 || p->eject_r != 0.0 || p->ml_levels != 0)
     return 0;
   return adj_layout(*p, n, nsteps, checkpoint_every, nullptr, nullptr);
 }

@@ -737,7 +737,7 @@ extern "C" {
 
 size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets) {
   if (!p || nsys < 1 || !offsets || offsets[0] != 0 || p->rcrit_refresh != 0 || p->gas != 0 ||
-      p->eject_r != 0.0)
+      p->eject_r != 0.0 || p->ml_levels != 0)
     return 0;
   for (int s = 0; s < nsys; ++s) {
     const int n = offsets[s + 1] - offsets[s];

@@ -37,6 +37,7 @@ struct BsCtx {
   double* g;     // gnew of the group's first slot
   int stride, M, kmax;
   double G, mu;
+  double rc_scale = 1.0;  // changeover radii r_crit * rc_scale (multi-level changeover)
 };
 
 __device__ __forceinline__ bool bs_alive(const BsCtx& c, int b) { return c.g[10 * b + 9] != 0.0; }
@@ -92,7 +93,8 @@ static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
     const double* aq = bs_aux(c, q);
     if (!(q2 < fmax(ab[2], aq[2]))) continue;  // 1 - w = 0 beyond rc
     const double ri = rinv_fast(q2);
-    const double omw = close_weight(q2 * ri, fmax(rcb, c.g[10 * q + 8]), fmin(ab[1], aq[1]));
+    const double omw =
+        close_weight(q2 * ri, fmax(rcb, c.g[10 * q + 8]) * c.rc_scale, fmin(ab[1], aq[1]));
     const double f = aq[0] * omw * (ri * ri * ri);
     ax = __fma_rn(f, dx, ax);
     ay = __fma_rn(f, dy, ay);
@@ -172,7 +174,7 @@ static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, 
       const double e1 = 0.5 * M * v2 - P.G * P.m0 * M / r;
       *El += e0 - e1;
       ga[8] = rcrit(P, ya[0], ya[1], ya[2], ya[3], ya[4], ya[5], M);
-      bs_set_aux(c, a, P.G, M, ga[8]);
+      bs_set_aux(c, a, P.G, M, ga[8] * c.rc_scale);
       *merges += 1;
     }
   }
@@ -182,6 +184,7 @@ static __device__ void bs_merge_scan(const BsCtx& c, const Phys& P, double* El, 
 // Counters of the direct solver (summed over the groups a CTA integrates).
 struct BsTally {
   long long derivs, substeps, halvings, merges;
+  long long ml_substeps = 0, ml_groups = 0;  // multi-level changeover
 };
 
 // Integrate H_A restricted to one group over h with all threads of the

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include "bs.cuh"
+#include "kepler.cuh"
 #include "nb_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -214,10 +215,238 @@ void launch_encounter(const Dev& d, const Phys& P, cudaStream_t st) {
   k_encounter<<<1, ENT, 0, st>>>(d);
 }
 
-__global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
+// ---------------------------------------------------------------------------
+// Multi-level changeover (section "Increasing N"), one CTA per level-0 group.
+// Level l has radii r_crit f^-l and substeps tau / f. ml_level<LV>(S, tau)
+// moves the members S over tau under their Kepler motion and the close part
+// of their interaction with weight 1 - w_LV: at LV = ml_levels by the direct
+// solver (the members gathered into the second scratch region, radii scaled
+// by f^-LV), below it by f substeps K A K with the kick weight
+// w_(LV+1) - w_LV and the level-(LV+1) groups (pairs within the next radii at
+// the substep's start or after the trial Kepler drift, restarted from the
+// substep's start) integrated by ml_level<LV+1>. The recursion is unrolled at
+// compile time (kMlMax levels), so no device stack is used. Members are the
+// group's slots 0..M-1; their state lives in the y fields of the group's
+// scratch; the column fields hold the per-level saved states and the kick
+// accelerations (the direct solver works in the second region).
+// ---------------------------------------------------------------------------
+struct MlCtx {
+  BsCtx a;       // the group's scratch (region A)
+  double* bbase; // the group's slots in the second region
+  double* bg;
+  int* list;     // (kMlMax + 1) x M
+  int* parent;   // (kMlMax + 1) x M
+  int L, f, Mg;
+  Phys P;
+  double* s_red;
+  int* s_flags;
+  int* s_int;    // 2 shared ints: a count and an error flag
+  BsTally* tally;
+  double El;     // energy removed by mergers (thread 0)
+};
+
+// f^-level by repeated division (the oracle computes it the same way)
+__device__ __forceinline__ double ml_scale(int f, int level) {
+  double s = 1.0;
+  for (int l = 0; l < level; ++l) s /= (double)f;
+  return s;
+}
+
+__device__ __forceinline__ double* ml_y(const MlCtx& m, int i) {
+  return m.a.base + (size_t)i * m.a.stride + OY;
+}
+
+__device__ __forceinline__ double ml_pw(double q2, double q, double rcl) {
+  return (q2 < rcl * rcl) ? kick_weight(q, rcl) : 1.0;
+}
+
+// K_level(tau) over the live members of S: v += tau sum G m_j (w_level -
+// w_(level-1)) d / r^3, accelerations first (all of them), then applied.
+__device__ void ml_kick(MlCtx& m, const int* S, int ns, int level, double tau) {
+  const double sl = ml_scale(m.f, level), sp = ml_scale(m.f, level - 1);
+  const double* g = m.a.g;
+  for (int a = threadIdx.x; a < ns; a += blockDim.x) {
+    const int i = S[a];
+    double* acc = m.a.base + (size_t)i * m.a.stride + bs_off_col(1) + CZC;
+    acc[0] = acc[1] = acc[2] = 0.0;
+    if (g[10 * i + 9] == 0.0) continue;
+    const double* yi = ml_y(m, i);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int b = 0; b < ns; ++b) {
+      const int j = S[b];
+      if (j == i || g[10 * j + 9] == 0.0) continue;
+      const double* yj = ml_y(m, j);
+      const double dx = yj[0] - yi[0], dy = yj[1] - yi[1], dz = yj[2] - yi[2];
+      const double q2 = sep2(dx, dy, dz);
+      if (q2 == 0.0) continue;
+      const double q = sqrt(q2);
+      const double rcp = fmax(g[10 * i + 8], g[10 * j + 8]);
+      const double dw = ml_pw(q2, q, rcp * sl) - ml_pw(q2, q, rcp * sp);
+      if (dw == 0.0) continue;
+      const double fr = m.P.G * g[10 * j + 6] * dw / (q2 * q);
+      ax += fr * dx;
+      ay += fr * dy;
+      az += fr * dz;
+    }
+    acc[0] = ax; acc[1] = ay; acc[2] = az;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < ns; a += blockDim.x) {
+    const int i = S[a];
+    if (g[10 * i + 9] == 0.0) continue;
+    double* y = ml_y(m, i);
+    const double* acc = m.a.base + (size_t)i * m.a.stride + bs_off_col(1) + CZC;
+    y[3] += tau * acc[0];
+    y[4] += tau * acc[1];
+    y[5] += tau * acc[2];
+  }
+  __syncthreads();
+}
+
+// pairs (a < b) of S within the radii r_crit * sl join in parent[] (thread 0)
+__device__ void ml_flag(const MlCtx& m, const int* S, int ns, double sl, int* parent) {
+  const double* g = m.a.g;
+  for (int a = 0; a < ns; ++a) {
+    const int i = S[a];
+    if (g[10 * i + 9] == 0.0) continue;
+    const double* yi = ml_y(m, i);
+    for (int b = a + 1; b < ns; ++b) {
+      const int j = S[b];
+      if (g[10 * j + 9] == 0.0) continue;
+      const double* yj = ml_y(m, j);
+      const double q2 = sep2(yj[0] - yi[0], yj[1] - yi[1], yj[2] - yi[2]);
+      const double rcl = fmax(g[10 * i + 8], g[10 * j + 8]) * sl;
+      if (!(q2 < rcl * rcl)) continue;
+      int ra = a, rb = b;
+      while (parent[ra] != ra) ra = parent[ra];
+      while (parent[rb] != rb) rb = parent[rb];
+      if (ra < rb)
+        parent[rb] = ra;
+      else if (rb < ra)
+        parent[ra] = rb;
+    }
+  }
+}
+
+// The direct solver on S with the radii of level LV, in the second region.
+__device__ int ml_direct(MlCtx& m, const int* S, int ns, double tau, int level) {
+  const double scale = ml_scale(m.f, level);
+  BsCtx c = m.a;
+  c.base = m.bbase;
+  c.g = m.bg;
+  c.M = ns;
+  c.rc_scale = scale;
+  for (int a = threadIdx.x; a < ns; a += blockDim.x) {
+    const int i = S[a];
+    const double* ya = ml_y(m, i);
+    double* yb = c.base + (size_t)a * c.stride + OY;
+    for (int k = 0; k < 6; ++k) yb[k] = ya[k];
+    const double* ga = m.a.g + 10 * i;
+    double* gb = c.g + 10 * a;
+    for (int k = 6; k < 10; ++k) gb[k] = ga[k];
+    bs_set_aux(c, a, m.P.G, gb[6], gb[8] * scale);
+  }
+  __syncthreads();
+  double El = 0.0;
+  const int st = bs_integrate_group(c, m.P, tau, m.s_red, m.s_flags, *m.tally, &El);
+  if (threadIdx.x == 0) m.El += El;
+  for (int a = threadIdx.x; a < ns; a += blockDim.x) {
+    const int i = S[a];
+    double* ya = ml_y(m, i);
+    const double* yb = c.base + (size_t)a * c.stride + OY;
+    for (int k = 0; k < 6; ++k) ya[k] = yb[k];
+    double* ga = m.a.g + 10 * i;
+    const double* gb = c.g + 10 * a;
+    for (int k = 6; k < 10; ++k) ga[k] = gb[k];
+  }
+  __syncthreads();
+  return st;
+}
+
+template <int LV>
+__device__ int ml_level(MlCtx& m, const int* S, int ns, double tau) {
+  if (LV >= m.L) return ml_direct(m, S, ns, tau, LV);
+  if constexpr (LV >= kMlMax) {
+    return NB_E_INVALID;  // unreachable: ml_levels <= kMlMax
+  } else {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const double t1 = tau / (double)m.f;
+    const double sn = ml_scale(m.f, LV + 1);
+    int* parent = m.parent + (size_t)(LV + 1) * m.Mg;
+    int* sub = m.list + (size_t)(LV + 1) * m.Mg;
+    const int save = bs_off_col(LV + 1) + CZM;  // this level's substep-start state
+    const double mu = m.P.mu;
+    int status = 0;
+    for (int k = 0; k < m.f && !status; ++k) {
+      ml_kick(m, S, ns, LV + 1, 0.5 * t1);
+      if (tid == 0) {
+        for (int a = 0; a < ns; ++a) parent[a] = a;
+        ml_flag(m, S, ns, sn, parent);
+        m.s_int[1] = 0;
+      }
+      for (int a = tid; a < ns; a += NT) {
+        double* y = ml_y(m, S[a]);
+        double* sv = m.a.base + (size_t)S[a] * m.a.stride + save;
+        for (int q = 0; q < 6; ++q) sv[q] = y[q];
+      }
+      __syncthreads();
+      for (int a = tid; a < ns; a += NT) {
+        const int i = S[a];
+        if (m.a.g[10 * i + 9] == 0.0) continue;
+        double* y = ml_y(m, i);
+        int it;
+        if (kepler_drift(mu, y[0], y[1], y[2], y[3], y[4], y[5], t1, m.P.kepler_max_iter, &it))
+          m.s_int[1] = 1;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        ml_flag(m, S, ns, sn, parent);
+        for (int a = 0; a < ns; ++a) {
+          int r = a;
+          while (parent[r] != r) r = parent[r];
+          parent[a] = r;
+        }
+      }
+      __syncthreads();
+      if (m.s_int[1]) status = NB_E_NOCONV;
+      for (int a = 0; a < ns && !status; ++a) {
+        if (parent[a] != a) continue;
+        if (tid == 0) {
+          int nsub = 0;
+          for (int b = a; b < ns; ++b)
+            if (parent[b] == a) sub[nsub++] = S[b];
+          m.s_int[0] = nsub;
+        }
+        __syncthreads();
+        const int nsub = m.s_int[0];
+        if (nsub < 2) continue;
+        for (int b = a + tid; b < ns; b += NT) {
+          if (parent[b] != a) continue;
+          double* y = ml_y(m, S[b]);
+          const double* sv = m.a.base + (size_t)S[b] * m.a.stride + save;
+          for (int q = 0; q < 6; ++q) y[q] = sv[q];
+        }
+        __syncthreads();
+        if (tid == 0) m.tally->ml_groups += 1;
+        status = ml_level<LV + 1>(m, sub, nsub, t1);
+      }
+      if (status) break;
+      ml_kick(m, S, ns, LV + 1, 0.5 * t1);
+      if (tid == 0) m.tally->ml_substeps += 1;
+    }
+    return status;
+  }
+}
+
+// One CTA per group: the direct solver (ML = false) or the multi-level
+// changeover (ML = true, its own kernel so that the direct solver's kernel
+// keeps its registers).
+template <bool ML>
+__global__ void __launch_bounds__(BNT) k_bs_t(Dev d, Phys P, double h) {
   __shared__ int s_stop, s_ng;
   __shared__ double s_red[BNT];
   __shared__ int s_flags[2];
+  __shared__ int s_int[2];
   if (threadIdx.x == 0) {
     s_stop = d.ctrl->status;
     s_ng = d.ctrl->n_groups;
@@ -227,7 +456,7 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
   BsTally tally{0, 0, 0, 0};
   for (int grp = blockIdx.x; grp < s_ng; grp += gridDim.x) {
     const int off = d.grp_off[grp];
-    if (P.bs_cluster_min > 0 && d.grp_off[grp + 1] - off >= P.bs_cluster_min) continue;
+    if (!ML && P.bs_cluster_min > 0 && d.grp_off[grp + 1] - off >= P.bs_cluster_min) continue;
     BsCtx c;
     c.M = d.grp_off[grp + 1] - off;
     c.stride = d.bs_stride;
@@ -250,7 +479,30 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
     }
     __syncthreads();
     double El = 0.0;
-    const int status = bs_integrate_group(c, P, h, s_red, s_flags, tally, &El);
+    int status;
+    if constexpr (ML) {
+      MlCtx m;
+      m.a = c;
+      m.bbase = d.ml_gscr + (size_t)off * d.bs_stride;
+      m.bg = d.ml_gnew + (size_t)off * 10;
+      m.list = d.ml_list + (size_t)(kMlMax + 1) * off;
+      m.parent = d.ml_parent + (size_t)(kMlMax + 1) * off;
+      m.L = P.ml_levels;
+      m.f = P.ml_factor;
+      m.Mg = c.M;
+      m.P = P;
+      m.s_red = s_red;
+      m.s_flags = s_flags;
+      m.s_int = s_int;
+      m.tally = &tally;
+      m.El = 0.0;
+      for (int b = threadIdx.x; b < c.M; b += blockDim.x) m.list[b] = b;
+      __syncthreads();
+      status = ml_level<0>(m, m.list, c.M, h);
+      El = m.El;
+    } else {
+      status = bs_integrate_group(c, P, h, s_red, s_flags, tally, &El);
+    }
     if (status && threadIdx.x == 0) set_status(d.ctrl, status, 30);
     for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
       const double* y = c.base + (size_t)b * c.stride + OY;
@@ -265,6 +517,8 @@ __global__ void __launch_bounds__(BNT) k_bs(Dev d, Phys P, double h) {
     atomicAdd(&d.ctrl->stats[ST_BS_SUBSTEPS], (unsigned long long)tally.substeps);
     atomicAdd(&d.ctrl->stats[ST_BS_HALVINGS], (unsigned long long)tally.halvings);
     atomicAdd(&d.ctrl->stats[ST_MERGES], (unsigned long long)tally.merges);
+    atomicAdd(&d.ctrl->stats[ST_ML_SUBSTEPS], (unsigned long long)tally.ml_substeps);
+    atomicAdd(&d.ctrl->stats[ST_ML_GROUPS], (unsigned long long)tally.ml_groups);
   }
 }
 
@@ -421,7 +675,11 @@ void launch_bs_cluster(const Dev& d, const Phys& P, double h, cudaStream_t st) {
 void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
   int grid = d.n < 2 * 148 ? d.n : 2 * 148;
   if (grid < 1) grid = 1;
-  k_bs<<<grid, BNT, 0, st>>>(d, P, h);
+  if (P.ml_levels > 0) {
+    k_bs_t<true><<<grid, BNT, 0, st>>>(d, P, h);
+    return;
+  }
+  k_bs_t<false><<<grid, BNT, 0, st>>>(d, P, h);
   if (P.bs_cluster_min > 0 && d.n >= P.bs_cluster_min) launch_bs_cluster(d, P, h, st);
 }
 

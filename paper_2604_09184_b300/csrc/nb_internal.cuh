@@ -12,7 +12,8 @@
 namespace nb {
 
 constexpr int kMaxBsK = 12;          // upper bound on bs_kmax
-constexpr int kStatN = 12;           // device statistics counters
+constexpr int kStatN = 14;           // device statistics counters
+constexpr int kMlMax = 3;            // deepest multi-level changeover supported
 constexpr double kDeadOffset = 1e6;  // absorbed bodies sit at (1e6 (id + 1), 0, 0) AU
 
 // Bulirsch-Stoer scratch per group member (doubles): y[6] | f0[6] | per
@@ -33,7 +34,9 @@ enum StatIdx {
   ST_KEPLER_ITERS,
   ST_MOVED,
   ST_LOG_DROPPED,
-  ST_EJECTIONS
+  ST_EJECTIONS,
+  ST_ML_SUBSTEPS,
+  ST_ML_GROUPS
 };
 
 // Control block in device memory: counters, status and per-step scalars.
@@ -90,13 +93,20 @@ struct Dev {
   Ctrl* snap_ctrl;
   double* eparts;     // energy partial sums
   int eparts_n;
+  // multi-level changeover (allocated when ml_levels > 0): a second BS
+  // scratch region where the last level's subgroups are gathered, and per
+  // level member lists and union-find parents
+  double* ml_gscr;    // member_cap x bs_stride
+  double* ml_gnew;    // member_cap x 10
+  int* ml_list;       // (kMlMax + 1) x member_cap
+  int* ml_parent;     // (kMlMax + 1) x member_cap
 };
 
 // Parameters as the kernels see them.
 struct Phys {
   double G, m0, mu, dt_rcrit, hill_factor, vel_factor, bs_tol;
   int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings, rcrit_refresh;
-  int gas, gas_iter, bs_cluster_min;
+  int gas, gas_iter, bs_cluster_min, ml_levels, ml_factor;
   double gas_rho0, gas_p, gas_eta, gas_cd, eject_r;
 };
 

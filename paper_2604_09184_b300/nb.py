@@ -37,7 +37,8 @@ class NbParams(C.Structure):
         ("kick_split", C.c_int), ("rcrit_refresh", C.c_int),
         ("gas", C.c_int), ("gas_rho0", C.c_double), ("gas_p", C.c_double),
         ("gas_eta", C.c_double), ("gas_cd", C.c_double), ("gas_iter", C.c_int),
-        ("eject_r", C.c_double), ("bs_cluster_min", C.c_int),
+        ("eject_r", C.c_double), ("bs_cluster_min", C.c_int), ("ml_levels", C.c_int),
+        ("ml_factor", C.c_int),
     ]
 
 
@@ -46,7 +47,7 @@ class NbStats(C.Structure):
         "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
         "bs_derivs", "merges", "kepler_iters", "moved_bodies", "log_dropped")] + [
         ("n_active", C.c_int), ("last_pairs", C.c_int), ("ejections", C.c_longlong),
-        ("m_ejected", C.c_double)]
+        ("m_ejected", C.c_double), ("ml_substeps", C.c_longlong), ("ml_groups", C.c_longlong)]
 
 
 class NbError(RuntimeError):

@@ -393,6 +393,23 @@ def test_large_groups_on_clusters_bit_identical_and_match_oracle():
     assert np.array_equal(ref.encounter_list(), runs[8].encounter_list())
 
 
+@pytest.mark.parametrize("levels,factor,merge", [(1, 3, 0), (2, 3, 1), (3, 2, 1)])
+def test_step_parity_multilevel_changeover(levels, factor, merge):
+    """Multi-level changeover: close-encounter groups are integrated by
+    substeps with intermediate changeovers and the direct solver only at the
+    last level. Same states, encounter lists and level statistics as the
+    oracle after 100 steps of the toy disk."""
+    d = ics.workload("toy_disk_256")
+    kw = dict(ml_levels=levels, ml_factor=factor, merge=merge)
+    ref, gpu = run_both(d, 100, **kw)
+    compare_states(ref, gpu)
+    assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+    sr, sg = ref.stats(), gpu.stats()
+    assert sr["groups"] > 0 and sr["ml_substeps"] > 0
+    for k in ("ml_substeps", "ml_groups", "bs_substeps", "merges"):
+        assert sr[k] == sg[k], (k, sr[k], sg[k])
+
+
 def test_step_parity_velocity_mode_literal():
     d = ics.workload("toy_disk_256", n=128)
     ref, gpu = run_both(d, 30, vel_mode=1)
