@@ -467,10 +467,33 @@ def run_options(nb, torch, disk, args, ms_plain, flush, stream, steps=3):
     st = s.stats()
     del s
     t = sum(ms) / len(ms)
-    return {"gas_drag_and_ejection_ms_per_step": t, "plain_ms_per_step": ms_plain,
-            "overhead_ms": t - ms_plain, "ejections": st["ejections"],
-            "setting": "gas rho0 = 2.36e-3 Msun/AU^3 (1.4e-9 g/cm^3) s^-2.75, eta 2e-3, C_D 1; "
-                       "eject_r 100 AU; %d steps after %d warm-up" % (steps, max(args.warmup, 1))}
+    out = {"gas_drag_and_ejection_ms_per_step": t, "plain_ms_per_step": ms_plain,
+           "overhead_ms": t - ms_plain, "ejections": st["ejections"],
+           "setting": "gas rho0 = 2.36e-3 Msun/AU^3 (1.4e-9 g/cm^3) s^-2.75, eta 2e-3, C_D 1; "
+                      "eject_r 100 AU; %d steps after %d warm-up" % (steps, max(args.warmup, 1))}
+    # multi-level changeover on the encounter-dominated 2049-body disk
+    from paper_2604_09184_b300 import ics
+    d2 = ics.workload("adjoint_2k_j")
+    ml = []
+    for L in (0, 1, 2):
+        s = nb.NBodySystem(nb.params(dt_rcrit=d2.dt, ml_levels=L, ml_factor=3, merge=0), d2.x,
+                           d2.v, d2.m, d2.R)
+        E0 = s.energy_momentum()["E"]
+        s.step(2, d2.dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(200, d2.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        ml.append({"ml_levels": L, "ml_factor": 3, "ms_per_step": e0.elapsed_time(e1) / 200,
+                   "energy_error": abs(s.energy_momentum()["E"] / E0 - 1),
+                   "bs_derivs": st["bs_derivs"], "ml_substeps": st["ml_substeps"]})
+        del s
+    out["multilevel"] = {"workload": "adjoint_2k_j (2049 bodies), 202 steps, mergers off",
+                         "runs": ml}
+    return out
 
 
 def run_adjoint(nb, torch, stream, nsteps=2000, every=100):
