@@ -53,19 +53,24 @@ __device__ __forceinline__ void bs_set_aux(const BsCtx& c, int b, double G, doub
   a[2] = rc * rc;
 }
 
-// 1 - w for a pair inside rc (w = K - r dK/dr, K the infinitely smooth switch):
-// y < 1/746 gives exp(-1/y) = 0 exactly, so w = 0; 1 - y < 1/746 gives w = 1.
+// 1 - w for a pair inside rc (w = K - r dK/dr, K the infinitely smooth switch
+// K = f(y) / (f(y) + f(1 - y)), f(y) = exp(-1/y)). One exponential: with
+// E = exp(1/y - 1/(1-y)), K = 1 / (1 + E) and dK/dy = K (1 - K) (1/y^2 +
+// 1/(1-y)^2) = E K^2 (1/y^2 + 1/(1-y)^2). Where |1/y - 1/(1-y)| > 80, K is
+// within 2e-35 of 0 or 1 and w is 0 or 1 to double precision.
 __device__ __forceinline__ double close_weight(double qq, double rc, double inv09) {
   const double y = (qq - 0.1 * rc) * inv09;
   if (y < 1.0 / 746.0) return 1.0;
   const double u = 1.0 - y;
   if (u < 1.0 / 746.0) return 0.0;
   const double iy = rcp_fast(y), iu = rcp_fast(u);
-  const double f = exp(-iy), g = exp(-iu);
-  const double rs = rcp_fast(f + g);
-  const double fg = f * g;
-  const double dKdy = fg > 0.0 ? fg * __fma_rn(iy, iy, iu * iu) * (rs * rs) : 0.0;
-  return 1.0 - (f * rs - qq * dKdy * inv09);
+  const double dd = iy - iu;
+  if (dd > 80.0) return 1.0;
+  if (dd < -80.0) return 0.0;
+  const double E = exp(dd);
+  const double K = rcp_fast(1.0 + E);
+  const double dKdy = (E * K) * K * __fma_rn(iy, iy, iu * iu);
+  return 1.0 - (K - qq * dKdy * inv09);
 }
 
 // Field fout of member b = d/dt of field fo (Eq. Ha restricted to the group).

@@ -410,6 +410,32 @@ def test_step_parity_multilevel_changeover(levels, factor, merge):
         assert sr[k] == sg[k], (k, sr[k], sg[k])
 
 
+def test_new_options_validate_and_fail_atomically():
+    """Out-of-range options are refused at creation; the batch and adjoint
+    entry points refuse the single-system options; an implicit-midpoint drag
+    that cannot converge in its iteration cap fails the step with
+    NB_E_NOCONV and leaves the state as it was."""
+    nb = nbmod()
+    d = ics.workload("toy_disk_256", n=32)
+    for bad in (dict(ml_levels=4), dict(ml_levels=1, ml_factor=1), dict(gas=2),
+                dict(gas=1, gas_eta=1.5), dict(eject_r=-1.0), dict(bs_cluster_min=-3),
+                dict(rcrit_refresh=2)):
+        with pytest.raises(nb.NbError):
+            nb.NBodySystem(nb.params(dt_rcrit=d.dt, **bad), d.x, d.v, d.m, d.R)
+    for opt in (dict(ml_levels=1), dict(gas=1), dict(eject_r=50.0), dict(rcrit_refresh=1)):
+        with pytest.raises(nb.NbError):
+            nb.NBodyBatch(nb.params(dt_rcrit=3.0, **opt), ics.ensemble(n_systems=4))
+        rc = np.ones(d.n) * 1e-3
+        with pytest.raises(nb.NbError):
+            nb.NBodyAdjoint(nb.params(dt_rcrit=d.dt, **opt), d.x, d.v, d.m, d.R, rc, 4, 2)
+    s = nb.NBodySystem(nb.params(dt_rcrit=d.dt, gas=1, gas_rho0=1e6, gas_iter=2), d.x, d.v,
+                       d.m, d.R)
+    before = s.state()
+    assert s.step_status(3, d.dt) == nb.NB_E_NOCONV
+    after = s.state()
+    assert np.array_equal(before["x"], after["x"]) and np.array_equal(before["v"], after["v"])
+
+
 def test_step_parity_velocity_mode_literal():
     d = ics.workload("toy_disk_256", n=128)
     ref, gpu = run_both(d, 30, vel_mode=1)
