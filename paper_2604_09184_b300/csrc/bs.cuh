@@ -402,6 +402,20 @@ struct BlockTeam {
   }
 };
 
+// One warp as the team (small groups: a CTA integrates one group per warp
+// and the barriers are warp barriers). s_flags: this warp's two shared ints.
+struct WarpTeam {
+  int* s_flags;
+  __device__ int tid() const { return threadIdx.x & 31; }
+  __device__ int nthreads() const { return 32; }
+  __device__ int* flags() const { return s_flags; }
+  __device__ void sync() const { __syncwarp(); }
+  __device__ double max_to_first(double v) const {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  }
+};
+
 static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,
                                          int* s_flags, BsTally& tally, double* El,
                                          BsRec* rec = nullptr) {

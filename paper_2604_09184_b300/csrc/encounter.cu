@@ -30,6 +30,16 @@ namespace nb {
 
 constexpr int ENT = 1024;  // threads of k_encounter
 constexpr int BNT = 64;    // threads of a BS CTA
+constexpr int kWarpGroupMax = 8;  // groups of up to 8 bodies run on one warp
+
+// Which solver takes a group of M bodies: 2 = a cluster (bs_cluster_min > 0
+// and M >= it), 1 = one warp (M <= kWarpGroupMax), 0 = one CTA. The
+// multi-level path runs every group on one CTA.
+__host__ __device__ inline int group_route(const Phys& P, int M) {
+  if (P.ml_levels > 0) return 0;
+  if (P.bs_cluster_min > 0 && M >= P.bs_cluster_min) return 2;
+  return M <= kWarpGroupMax ? 1 : 0;
+}
 constexpr int CCL_MAX = 16;  // CTAs per cluster of the large-group solver (16: opt-in size)
 constexpr int CNT = 128;     // threads per CTA of the large-group solver
 
@@ -442,7 +452,7 @@ __device__ int ml_level(MlCtx& m, const int* S, int ns, double tau) {
 // changeover (ML = true, its own kernel so that the direct solver's kernel
 // keeps its registers).
 template <bool ML>
-__global__ void __launch_bounds__(BNT) k_bs_t(Dev d, Phys P, double h) {
+__global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
   __shared__ int s_stop, s_ng;
   __shared__ double s_red[BNT];
   __shared__ int s_flags[2];
@@ -454,9 +464,70 @@ __global__ void __launch_bounds__(BNT) k_bs_t(Dev d, Phys P, double h) {
   __syncthreads();
   if (s_stop) return;
   BsTally tally{0, 0, 0, 0};
+  if constexpr (!ML) {
+    // small groups: one per warp, with warp barriers only
+    __shared__ int s_wflags[BNT / 32][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTeam wt{s_wflags[warp]};
+    for (int grp = blockIdx.x * (BNT / 32) + warp; grp < s_ng; grp += gridDim.x * (BNT / 32)) {
+      const int off = d.grp_off[grp];
+      const int M = d.grp_off[grp + 1] - off;
+      if (group_route(P, M) != 1) continue;
+      BsCtx c;
+      c.M = M;
+      c.stride = d.bs_stride;
+      c.base = d.gscr + (size_t)off * d.bs_stride;
+      c.g = d.gnew + (size_t)off * 10;
+      c.kmax = P.bs_kmax;
+      c.G = P.G;
+      c.mu = P.mu;
+      for (int b = lane; b < M; b += 32) {
+        const int body = d.grp_mem[off + b];
+        double* y = c.base + (size_t)b * c.stride + OY;
+        y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
+        y[3] = d.vxs[body]; y[4] = d.vys[body]; y[5] = d.vzs[body];
+        double* g = c.g + 10 * b;
+        g[6] = d.m[body];
+        g[7] = d.R[body];
+        g[8] = d.rc[body];
+        g[9] = 1.0;
+        bs_set_aux(c, b, P.G, g[6], g[8]);
+      }
+      __syncwarp();
+      double El = 0.0;
+      const int status = bs_integrate(c, P, h, wt, tally, &El, (BsRec*)nullptr);
+      if (status && lane == 0) set_status(d.ctrl, status, 30);
+      for (int b = lane; b < M; b += 32) {
+        const double* y = c.base + (size_t)b * c.stride + OY;
+        double* g = c.g + 10 * b;
+        for (int k = 0; k < 6; ++k) g[k] = y[k];
+      }
+      if (lane == 0) d.gEl[grp] = El;
+      __syncwarp();
+    }
+    // the warps' counters go through warp 0 of each CTA below; fold them
+    // into thread 0's tally (each warp's lane 0 holds its own)
+    __shared__ long long s_tal[BNT / 32][4];
+    if (lane == 0) {
+      s_tal[warp][0] = tally.derivs;
+      s_tal[warp][1] = tally.substeps;
+      s_tal[warp][2] = tally.halvings;
+      s_tal[warp][3] = tally.merges;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tally.derivs = tally.substeps = tally.halvings = tally.merges = 0;
+      for (int w = 0; w < BNT / 32; ++w) {
+        tally.derivs += s_tal[w][0];
+        tally.substeps += s_tal[w][1];
+        tally.halvings += s_tal[w][2];
+        tally.merges += s_tal[w][3];
+      }
+    }
+  }
   for (int grp = blockIdx.x; grp < s_ng; grp += gridDim.x) {
     const int off = d.grp_off[grp];
-    if (!ML && P.bs_cluster_min > 0 && d.grp_off[grp + 1] - off >= P.bs_cluster_min) continue;
+    if (!ML && group_route(P, d.grp_off[grp + 1] - off) != 0) continue;  // a warp or a cluster
     BsCtx c;
     c.M = d.grp_off[grp + 1] - off;
     c.stride = d.bs_stride;
@@ -578,7 +649,7 @@ __global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int
   for (int grp = cid; grp < ng; grp += ncl) {
     const int off = d.grp_off[grp];
     const int M = d.grp_off[grp + 1] - off;
-    if (M < min_m) continue;
+    if (group_route(P, M) != 2) continue;
     BsCtx c;
     c.M = M;
     c.stride = d.bs_stride;
