@@ -368,18 +368,18 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
 // accepted column) keeping every state, and reverse them as a wave over the
 // columns; the Neville extrapolation is linear in the column results, with
 // weights c_j from the same recursion applied to unit vectors.
-__global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
-  __shared__ double s_red[ABNT];
-  __shared__ int s_flags[2];
-  __shared__ double cw[kMaxBsK + 2];
-  __shared__ double Tn[kMaxBsK + 2][kMaxBsK + 2];
+// The adjoint of one group's integration by a team (one warp or one CTA):
+// cw and Tn are the team's shared scratch for the extrapolation weights.
+template <class Team>
+__device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
+                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2]) {
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int* gmem = A.grp + 2 + ng + 1;
   const int n = A.n;
-  const int tid = threadIdx.x, NT = blockDim.x;
+  const int tid = team.tid(), NT = team.nthreads();
   const int NS = adj_nstates(A.kmax);
-  for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+  {
     const int off = goff[grp];
     BsCtx c;
     c.M = goff[grp + 1] - off;
@@ -426,15 +426,15 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
     if (tid == 0) {
       rec.counts[0] = 0; rec.counts[1] = 0; rec.counts[2] = 0;
     }
-    __syncthreads();
+    team.sync();
     BsTally tally{0, 0, 0, 0};
     double El = 0.0;
-    int st = bs_integrate_group(c, P, h, s_red, s_flags, tally, &El, &rec);
-    __syncthreads();
+    int st = bs_integrate(c, P, h, team, tally, &El, &rec);
+    team.sync();
     if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
     if (st) {
       if (tid == 0) atomicCAS(A.status, 0, st);
-      continue;
+      return;
     }
     const int nsub = rec.counts[0], nmrg = rec.counts[1];
     // adjoint at the end of the BS: members alive at the end take the step's
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
       }
       lmv[b] = live ? A.lm[body] : 0.0;
     }
-    __syncthreads();
+    team.sync();
     int mq = nmrg - 1;
     for (int s = nsub - 1; s >= 0; --s) {
       // undo the mergers that followed substep s (last first)
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           lmv[a] = lM + dot_a;
           lmv[b] = lM + dot_b;
         }
-        __syncthreads();
+        team.sync();
       }
       const int kacc = rec.k[s];
       const double H = rec.H[s];
@@ -502,10 +502,10 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           cw[j0] = Tn[kacc][kacc];
         }
       }
-      __syncthreads();
+      team.sync();
       const double* y = zst;  // M states
       for (int b = tid; b < M; b += NT) grp_f(c, y, b, f0 + 6 * b);
-      __syncthreads();
+      team.sync();
       // replay: z_0 = y, z_1 = y + hs f0, z_{t+1} = z_{t-1} + 2 hs f(z_t)
       for (int it = tid; it < kacc * M; it += NT) {
         const int j = 1 + it / M, b = it % M;
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           z1[k] = y[6 * b + k] + hs * f0[6 * b + k];
         }
       }
-      __syncthreads();
+      team.sync();
       for (int t = 1; t < 2 * kacc; ++t) {
         const int j0 = t / 2 + 1;  // columns with t < 2j
         const int ncol = kacc - j0 + 1;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           const int j = j0 + it / M, b = it % M;
           grp_f(c, zst + (size_t)adj_sidx(j, t) * 6 * M, b, fcol + (size_t)(j - 1) * 6 * M + 6 * b);
         }
-        __syncthreads();
+        team.sync();
         for (int it = tid; it < ncol * M; it += NT) {
           const int j = j0 + it / M, b = it % M;
           const double hs = H / (2 * j);
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           const double* f = fcol + (size_t)(j - 1) * 6 * M + 6 * b;
           for (int k = 0; k < 6; ++k) zn[k] = zm[k] + 2.0 * hs * f[k];
         }
-        __syncthreads();
+        team.sync();
       }
       // reverse, tau = 0: T_j = (z_2j + z_2j-1 + hs f(z_2j)) / 2 with
       // lambda_T = cw_j lambda_Y
@@ -548,13 +548,13 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
           lzp[6 * b + k] += 0.5 * lT;
         }
       }
-      __syncthreads();
+      team.sync();
       // the f-term of T: w = cw_j lambda_Y for every member; staged in fcol
       for (int it = tid; it < kacc * M; it += NT) {
         const int j = 1 + it / M, b = it % M;
         for (int k = 0; k < 6; ++k) fcol[(size_t)(j - 1) * 6 * M + 6 * b + k] = cw[j] * ly[6 * b + k];
       }
-      __syncthreads();
+      team.sync();
       for (int it = tid; it < kacc * M; it += NT) {
         const int j = 1 + it / M, b = it % M;
         const double hs = H / (2 * j);
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
                 lzst + (size_t)adj_sidx(j, 2 * j) * 6 * M + 6 * b, lmc + (j - 1) * M + b,
                 0.5 * hs);
       }
-      __syncthreads();
+      team.sync();
       // tau = 1 .. 2k - 1: column j reverses z_{m+1} = z_{m-1} + 2 hs f(z_m) at m = 2j - tau
       for (int tau = 1; tau < 2 * kacc; ++tau) {
         const int j0 = (tau + 2) / 2;  // columns with m = 2j - tau >= 1
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
                   lzst + (size_t)adj_sidx(j, m) * 6 * M + 6 * b, lmc + (j - 1) * M + b,
                   2.0 * hs);
         }
-        __syncthreads();
+        team.sync();
       }
       // z_1 = z_0 + hs f0 and z_0 = y: lambda_y = sum_j (lambda_z0 + lambda_z1),
       // lambda_f0 = sum_j hs_j lambda_z1 (columns in ascending order)
@@ -601,12 +601,12 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
         }
         lmv[b] += am;
       }
-      __syncthreads();
+      team.sync();
       for (int b = tid; b < M; b += NT) grp_vjp(c, y, lf0, b, lin + 6 * b, lmv + b, 1.0);
-      __syncthreads();
+      team.sync();
       for (int b = tid; b < M; b += NT)
         for (int k = 0; k < 6; ++k) ly[6 * b + k] = lin[6 * b + k];
-      __syncthreads();
+      team.sync();
     }
     // lambda at the saved state of the members
     for (int b = tid; b < M; b += NT) {
@@ -617,7 +617,31 @@ __global__ void __launch_bounds__(ABNT) k_bs_adjoint(AdjGroupArgs A, Phys P, dou
       }
       A.lm[body] = lmv[b];
     }
-    __syncthreads();
+    team.sync();
+  }
+}
+
+
+__global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
+  __shared__ double s_red[ABNT];
+  __shared__ int s_flags[2];
+  __shared__ double cw[ABNT / 32][kMaxBsK + 2];
+  __shared__ double Tn[ABNT / 32][kMaxBsK + 2][kMaxBsK + 2];
+  __shared__ int s_wflags[ABNT / 32][2];
+  const int ng = A.grp[0];
+  const int* goff = A.grp + 2;
+  const int warp = threadIdx.x >> 5;
+  // groups of up to 8 bodies: one per warp, warp barriers only
+  WarpTeam wt{s_wflags[warp]};
+  for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
+    if (goff[grp + 1] - goff[grp] > 8) continue;
+    bs_adjoint_group(A, P, h, grp, wt, cw[warp], Tn[warp]);
+  }
+  __syncthreads();
+  BlockTeam bt{s_red, s_flags};
+  for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+    if (goff[grp + 1] - goff[grp] <= 8) continue;
+    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0]);
   }
 }
 
