@@ -374,6 +374,7 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       s->events->push_back(e);
     }
   }
+  NvtxRange whole("nb_step");
   const int refresh = s->P.rcrit_refresh;
   const int eject = s->P.eject_r > 0.0;
   const int gas = s->P.gas;
@@ -383,23 +384,39 @@ int nb_step(nb_system* s, int nsteps, double dt) {
     if (split) {
       // step start: ejection, Eq. rcrit anew, the cached force and flags
       // anew where either changed, then G(h/2) and the opening B(h/2)
+      NvtxRange r("step start: eject / rcrit / force / gas / B(h/2)");
       if (eject) launch_eject(d, s->P, s->st);
       if (refresh) launch_refresh_rcrit(d, s->P, s->st);
       if (refresh || eject) launch_force_anew(d, s->P, !refresh, s->st);
       if (gas) launch_gas(d, s->P, 0.5 * dt, s->st);
       launch_open_h(d, dt, s->st);
     }
-    launch_drift_h(d, s->P, dt, s->st);
-    if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k], s->st));
-    launch_kick(d, s->P, 0, s->st);
-    if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k + 1], s->st));
-    launch_encounter(d, s->P, s->st);
-    launch_bs(d, s->P, dt, s->st);
-    launch_finish(d, s->P, 1, s->st);
-    launch_scatter(d, s->P, s->st);
-    launch_member_kick(d, s->P, s->st);
-    launch_close_h(d, s->P, dt, split || k == nsteps - 1, s->st);
-    if (gas) launch_gas(d, s->P, 0.5 * dt, s->st);
+    {
+      NvtxRange r("C(h/2) + Kepler drift A(h)");
+      launch_drift_h(d, s->P, dt, s->st);
+    }
+    {
+      NvtxRange r("kick + flags at the trial positions");
+      if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k], s->st));
+      launch_kick(d, s->P, 0, s->st);
+      if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k + 1], s->st));
+    }
+    {
+      NvtxRange r("encounter set, groups, direct solver");
+      launch_encounter(d, s->P, s->st);
+      launch_bs(d, s->P, dt, s->st);
+    }
+    {
+      NvtxRange r("final force (incremental) and scatter");
+      launch_finish(d, s->P, 1, s->st);
+      launch_scatter(d, s->P, s->st);
+      launch_member_kick(d, s->P, s->st);
+    }
+    {
+      NvtxRange r("C(h/2) + B(h/2)");
+      launch_close_h(d, s->P, dt, split || k == nsteps - 1, s->st);
+      if (gas) launch_gas(d, s->P, 0.5 * dt, s->st);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e, "nb_step launch");

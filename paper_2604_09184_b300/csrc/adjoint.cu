@@ -999,6 +999,7 @@ int nb_adjoint_forward(nb_adjoint* a, int nsteps, double dt) {
     const int rc = checkpoint(a, 0, 1);
     if (rc) return rc;
   }
+  NvtxRange range("nb_adjoint_forward");
   a->dt = dt;
   a->n_ckpt = 0;
   a->nsteps_done = 0;
@@ -1063,8 +1064,14 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
     const int len = total - start < a->every ? total - start : a->every;
     int rc = checkpoint(a, seg, 1);
     if (rc) return rc;
-    for (int t = 0; t < len; ++t) replay_step(a, a->dt, a->recs[t]);
-    for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[t]);
+    {
+      NvtxRange r("adjoint: replay segment");
+      for (int t = 0; t < len; ++t) replay_step(a, a->dt, a->recs[t]);
+    }
+    {
+      NvtxRange r("adjoint: reverse segment");
+      for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[t]);
+    }
     int st[2] = {0, 0};
     NB_ACU(cudaMemcpyAsync(st, a->status, sizeof(st), cudaMemcpyDeviceToHost, a->st));
     Ctrl c;

@@ -833,6 +833,7 @@ int nb_batch_set_shape(nb_batch* b, int threads, int chunk) {
 int nb_batch_step(nb_batch* b, int nsteps, double dt) {
   if (!b || nsteps < 0 || !std::isfinite(dt)) return NB_E_INVALID;
   if (nsteps == 0) return NB_OK;
+  NvtxRange range("nb_batch_step");
   int rc = batch_snapshot(b, 0);
   if (rc) return rc;
   rc = run_steps(b, nsteps, dt);

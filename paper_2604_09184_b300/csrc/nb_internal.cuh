@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -313,6 +314,15 @@ void launch_raw_finish(int n, int ib, int ie, int S, const double* kpart, double
                        cudaStream_t st);
 int peak_blocks();
 int measure_peaks(double* fp64, double* fp32, void* scratch, cudaStream_t st);
+
+// NVTX range around a host-side phase (what a profiler shows as the phase
+// that enqueued the kernels); free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace nb
 
