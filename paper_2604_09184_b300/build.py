@@ -1,6 +1,7 @@
 """Build libnb.so (the CUDA library behind include/nb.h) for sm_103a.
 
-    python -m paper_2604_09184_b300.build      # writes paper_2604_09184_b300/libnb.so
+    python -m paper_2604_09184_b300.build          # writes paper_2604_09184_b300/libnb.so
+    python -m paper_2604_09184_b300.build --debug  # libnb_debug.so: -DNB_DEBUG index checks
 
 nvcc cross-compiles without a GPU. The library is built in-tree so that it
 travels with the repository to the machine that runs it.
@@ -15,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnb.so")
+LIB_DEBUG = os.path.join(HERE, "libnb_debug.so")
 SOURCES = ["abi.cu", "kick.cu", "drift.cu", "encounter.cu", "energy.cu", "peaks.cu",
            "noalloc.cu", "batch.cu", "adjoint.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("nb_internal.cuh", "bs.cuh", "kepler.cuh")] + [
@@ -31,18 +33,23 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES] + HEADERS
     return any(os.path.getmtime(f) > t for f in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not (force or needs_build()):
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          debug: bool = False) -> str:
+    """Compile and link the library; debug=True builds libnb_debug.so with the
+    NB_DEBUG index checks (the binding loads it when NB_DEBUG=1)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not (force or needs_build(lib)):
+        return lib
+    extra = list(extra or []) + (["-DNB_DEBUG"] if debug else [])
+    objdir = os.path.join(HERE, "_build_debug" if debug else "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
     procs = []
@@ -57,12 +64,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     for p, cmd in procs:
         if p.wait() != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                debug="--debug" in sys.argv))

@@ -102,7 +102,10 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
   if (s_stop) return;
   // previous members are no longer members
   const int nprev = C->n_prev_members;
-  for (int q = threadIdx.x; q < nprev; q += ENT) d.member_slot[d.grp_mem[q]] = -1;
+  for (int q = threadIdx.x; q < nprev; q += ENT) {
+    const int b = d.grp_mem[q];
+    if (NB_GUARD(C, q < d.member_cap && b >= 0 && b < d.n, 50)) d.member_slot[b] = -1;
+  }
   const int nT = s_nT, nP = s_nP, nK = nT + nP;
   // region A holds <= next_pow2(2 pair_cap) pair keys and later <= 4 pair_cap
   // group keys; region B holds <= 4 pair_cap body keys (pair_cap is a power of 2)
@@ -113,9 +116,11 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
     unsigned long long key = ~0ull;
     if (k < nP) {
       const int2 p = d.fprev[k];
+      if (!NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 51)) continue;
       key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
     } else if (k < nK) {
       const int2 p = d.ftrial[k - nP];
+      if (!NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 52)) continue;
       key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
     }
     kA[k] = key;
@@ -138,6 +143,7 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
     const int pos = base + k;
     if (pos < d.log_cap) {
       const int i = (int)(kA[k] >> 32), j = (int)(kA[k] & 0xffffffffu);
+      if (!NB_GUARD(C, i >= 0 && i < d.n && j >= 0 && j < d.n, 53)) continue;
       d.log[3 * pos] = s_step;
       d.log[3 * pos + 1] = d.id[i];
       d.log[3 * pos + 2] = d.id[j];
@@ -204,6 +210,7 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
   bitonic_sort(kA, P2g);
   for (int k = threadIdx.x; k < nb; k += ENT) {
     const int body = (int)(kA[k] & 0xffffffffu);
+    if (!NB_GUARD(C, k < d.member_cap && body >= 0 && body < d.n, 54)) continue;
     d.grp_mem[k] = body;
     d.member_slot[body] = k;
   }
@@ -483,6 +490,7 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
       c.mu = P.mu;
       for (int b = lane; b < M; b += 32) {
         const int body = d.grp_mem[off + b];
+        if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;
         double* y = c.base + (size_t)b * c.stride + OY;
         y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
         y[3] = d.vxs[body]; y[4] = d.vys[body]; y[5] = d.vzs[body];
@@ -538,6 +546,7 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
     c.mu = P.mu;
     for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
       const int body = d.grp_mem[off + b];
+      if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;
       double* y = c.base + (size_t)b * c.stride + OY;
       y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
       y[3] = d.vxs[body]; y[4] = d.vys[body]; y[5] = d.vzs[body];
@@ -660,6 +669,7 @@ __global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int
     c.mu = P.mu;
     for (int b = tid; b < M; b += NT) {
       const int body = d.grp_mem[off + b];
+      if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;
       double* y = c.base + (size_t)b * c.stride + OY;
       y[0] = d.xs[body]; y[1] = d.ys[body]; y[2] = d.zs[body];
       y[3] = d.vxs[body]; y[4] = d.vys[body]; y[5] = d.vzs[body];
@@ -773,6 +783,7 @@ __global__ void __launch_bounds__(SNT) k_scatter(Dev d) {
   int dead = 0;
   for (int q = threadIdx.x; q < M; q += SNT) {
     const int b = d.grp_mem[q];
+    if (!NB_GUARD(C, b >= 0 && b < d.n, 55)) continue;
     const double* g = d.gnew + (size_t)q * 10;
     const double mn = g[9] != 0.0 ? g[6] : 0.0;
     px += mn * g[3] - d.m[b] * d.vx[b];
@@ -799,6 +810,7 @@ __global__ void __launch_bounds__(SNT) k_scatter(Dev d) {
   __syncthreads();
   for (int q = threadIdx.x; q < M; q += SNT) {
     const int b = d.grp_mem[q];
+    if (!NB_GUARD(C, b >= 0 && b < d.n, 56)) continue;
     const double* g = d.gnew + (size_t)q * 10;
     if (g[9] != 0.0) {
       d.x[b] = g[0]; d.y[b] = g[1]; d.z[b] = g[2];

@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
     __syncthreads();
     const int q = q0 + threadIdx.x;
     if (q < M) {
-      const int b = d.grp_mem[q];
+      int b = d.grp_mem[q];
+      if (!NB_GUARD(d.ctrl, b >= 0 && b < d.n, 58)) b = 0;
       so[0][threadIdx.x] = d.x[b];
       so[1][threadIdx.x] = d.y[b];
       so[2][threadIdx.x] = d.z[b];
@@ -529,6 +530,7 @@ __global__ void __launch_bounds__(MNT) k_member_kick(Dev d, double G) {
   A.ctrl = d.ctrl;
   for (int q = blockIdx.x; q < M; q += gridDim.x) {
     const int b = d.grp_mem[q];
+    if (!NB_GUARD(d.ctrl, b >= 0 && b < d.n, 59)) continue;
     const bool live = d.alive[b] != 0;
     const double xb = d.x[b], yb = d.y[b], zb = d.z[b], rc2b = d.rc2[b], rcb = d.rc[b];
     const int hb = __double2hiint(rc2b);

@@ -115,6 +115,20 @@ __device__ __forceinline__ void set_status(Ctrl* c, int code, int where) {
   if (atomicCAS(&c->status, 0, code) == 0) c->err_where = where;
 }
 
+// Index checks of the debug build (NB_DEBUG, libnb_debug.so): an index taken
+// from device data (a pair list, a member list) that falls outside its array
+// sets NB_E_INVALID with the site's code and the access is skipped. In the
+// release build the check compiles to `true`.
+#ifdef NB_DEBUG
+__device__ __forceinline__ bool nb_guard(Ctrl* c, bool ok, int where) {
+  if (!ok) set_status(c, NB_E_INVALID, where);
+  return ok;
+}
+#define NB_GUARD(ctrl, cond, where) nb::nb_guard((ctrl), (cond), (where))
+#else
+#define NB_GUARD(ctrl, cond, where) true
+#endif
+
 // ---------------------------------------------------------------------------
 // Changeover (the paragraph after Eq. Hc): K goes smoothly from 0 at 0.1 rc to
 // 1 at rc. Infinitely differentiable switch in y = (r - 0.1 rc) / (0.9 rc):

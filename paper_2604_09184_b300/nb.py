@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libnb.so")
+# NB_DEBUG=1 selects the debug build (index checks that report NB_E_INVALID)
+LIB_PATH = os.path.join(_HERE, "libnb_debug.so" if os.environ.get("NB_DEBUG") == "1"
+                        else "libnb.so")
 
 NB_OK = 0
 NB_E_INVALID = -1
@@ -66,7 +68,9 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libnb.so is missing: run `python -m paper_2604_09184_b300.build`")
+            raise ImportError("%s is missing: run `python -m paper_2604_09184_b300.build%s`"
+                              % (os.path.basename(LIB_PATH),
+                                 " --debug" if LIB_PATH.endswith("_debug.so") else ""))
         L = C.CDLL(LIB_PATH)
         L.nb_default_params.argtypes = [C.POINTER(NbParams)]
         L.nb_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int]
