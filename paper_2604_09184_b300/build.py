@@ -48,6 +48,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     lib = LIB_DEBUG if debug else LIB
     if not (force or needs_build(lib)):
         return lib
+    # one build at a time (ranks of a multi-process launch share the tree)
+    import fcntl
+    with open(os.path.join(HERE, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not (force or needs_build(lib)):
+            return lib
+        return _build_locked(lib, verbose, extra, debug)
+
+
+def _build_locked(lib, verbose, extra, debug):
     extra = list(extra or []) + (["-DNB_DEBUG"] if debug else [])
     objdir = os.path.join(HERE, "_build_debug" if debug else "_build")
     os.makedirs(objdir, exist_ok=True)
