@@ -411,6 +411,15 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
 // ---------------------------------------------------------------------------
 constexpr int FNT = 256;
 
+// m_j w / r^3 as the kick computes it: the seeded reciprocal root beyond
+// rc_ij, the exact changeover weight inside, 0 for coincident bodies.
+__device__ __forceinline__ double finish_scale(double r2, double mj, double rci, double rcj) {
+  if (r2 == 0.0 || mj == 0.0) return 0.0;
+  const double rc = fmax(rci, rcj);
+  if (r2 < rc * rc) return pair_scale(r2, mj, rci, rcj);
+  return scale_fast<NB_PREC_FP64>(r2, mj);
+}
+
 __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
                                                const int* cond) {
   __shared__ int s_stop, s_M;
@@ -461,11 +470,14 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
     if (delta) {
       const int cnt = min(FNT, M - q0);
       for (int k = 0; k < cnt; ++k) {
+        // the trial kick's term of member k (same arithmetic as the kick:
+        // seeded reciprocal root beyond rc, the exact weight inside), then
+        // the term at the member's new state
         double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
-        double s = pair_scale(sep2(dx, dy, dz), so[3][k], rci, so[4][k]);
+        double s = finish_scale(sep2(dx, dy, dz), so[3][k], rci, so[4][k]);
         cx -= s * dx; cy -= s * dy; cz -= s * dz;
         dx = snw[0][k] - xi; dy = snw[1][k] - yi; dz = snw[2][k] - zi;
-        s = pair_scale(sep2(dx, dy, dz), snw[3][k], rci, snw[4][k]);
+        s = finish_scale(sep2(dx, dy, dz), snw[3][k], rci, snw[4][k]);
         cx += s * dx; cy += s * dy; cz += s * dz;
       }
     }
