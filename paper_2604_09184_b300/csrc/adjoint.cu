@@ -39,47 +39,56 @@ constexpr int ABNT = 64;     // threads of the BS adjoint CTA
 constexpr int kSubCap = 256; // recorded BS substeps per group and step
 constexpr int kMrgCap = 16;  // recorded mergers per group and step
 
-// K, dK/dy, d2K/dy2 of the infinitely smooth switch K = f / (f + g),
-// f = exp(-1/y), g = exp(-1/(1-y)).
+// K, dK/dy, d2K/dy2 of the infinitely smooth switch K = f(y) / (f(y) + f(1-y)),
+// f(y) = exp(-1/y), with one exponential: E = exp(1/y - 1/(1-y)), K = 1/(1+E),
+// A = 1/y^2 + 1/(1-y)^2, A' = -2/y^3 + 2/(1-y)^3,
+// K' = E K^2 A, K'' = E K^2 (2 K E A^2 + A' - A^2). Where |1/y - 1/(1-y)| > 80
+// K is within 2e-35 of 0 or 1 and its derivatives vanish to double precision.
 __device__ void changeover_y(double y, double& K, double& K1, double& K2) {
+  K1 = 0.0;
+  K2 = 0.0;
   if (y <= 0.0) {
-    K = 0.0; K1 = 0.0; K2 = 0.0;
+    K = 0.0;
     return;
   }
   if (y >= 1.0) {
-    K = 1.0; K1 = 0.0; K2 = 0.0;
+    K = 1.0;
     return;
   }
   const double u = 1.0 - y;
-  const double f = exp(-1.0 / y), g = exp(-1.0 / u);
-  const double s = f + g;
-  K = f / s;
-  const double fg = f * g;
-  if (!(fg > 0.0)) {
-    K1 = 0.0; K2 = 0.0;
+  const double iy = rcp_fast(y), iu = rcp_fast(u);
+  const double dd = iy - iu;
+  if (dd > 80.0) {
+    K = 0.0;
     return;
   }
-  const double iy = 1.0 / y, iu = 1.0 / u;
-  const double A = iy * iy + iu * iu;
-  K1 = fg * A / (s * s);
-  const double sp_s = (f * iy * iy - g * iu * iu) / s;  // s' / s
-  K2 = fg / (s * s) * ((iy * iy - iu * iu) * A + (-2.0 * iy * iy * iy + 2.0 * iu * iu * iu) -
-                       2.0 * A * sp_s);
+  if (dd < -80.0) {
+    K = 1.0;
+    return;
+  }
+  const double E = exp(dd);
+  K = rcp_fast(1.0 + E);
+  const double A = __fma_rn(iy, iy, iu * iu);
+  const double A1 = 2.0 * (iu * iu * iu - iy * iy * iy);
+  const double EK2 = E * K * K;
+  K1 = EK2 * A;
+  K2 = EK2 * (2.0 * K * E * A * A + A1 - A * A);
 }
 
 // Radial profile of a pair term and its derivative divided by r:
 // kick (close = 0): phi = w / r^3, w = K - r K_r (w = 1 beyond rc);
 // close force (close = 1): psi = (1 - w) / r^3 (0 beyond rc).
 __device__ void pair_profile(double r2, double rc, int close, double& p, double& dp_r) {
-  const double r = sqrt(r2);
-  const double ir = 1.0 / r;
+  const double ir = rinv_fast(r2);
+  const double r = r2 * ir;
   const double ir3 = ir * ir * ir;
   double w = 1.0, wp = 0.0;
   if (r2 < rc * rc) {
     const double L = 0.9 * rc;
+    const double iL = rcp_fast(L);
     double K, K1, K2;
-    changeover_y((r - 0.1 * rc) / L, K, K1, K2);
-    const double Kr = K1 / L, Krr = K2 / (L * L);
+    changeover_y((r - 0.1 * rc) * iL, K, K1, K2);
+    const double Kr = K1 * iL, Krr = K2 * iL * iL;
     w = K - r * Kr;
     wp = -r * Krr;
   }
@@ -298,8 +307,8 @@ __device__ void grp_f(const BsCtx& c, const double* z, int b, double* fb) {
   const double* zb = z + 6 * b;
   fb[0] = zb[3]; fb[1] = zb[4]; fb[2] = zb[5];
   const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
-  const double r = sqrt(r2);
-  const double ks = -c.mu / (r2 * r);
+  const double ir = rinv_fast(r2);
+  const double ks = -c.mu * (ir * ir * ir);
   double ax = ks * zb[0], ay = ks * zb[1], az = ks * zb[2];
   for (int q = 0; q < c.M; ++q) {
     if (q == b || !bs_alive(c, q)) continue;
@@ -328,10 +337,11 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
   const double* wb = w + 6 * b;
   double o[3];
   const double r2 = zb[0] * zb[0] + zb[1] * zb[1] + zb[2] * zb[2];
-  const double r = sqrt(r2);
-  const double ir3 = 1.0 / (r2 * r);
+  const double ir = rinv_fast(r2);
+  const double ir3 = ir * ir * ir;
+  const double ir5 = ir3 * ir * ir;
   const double xw = zb[0] * wb[3] + zb[1] * wb[4] + zb[2] * wb[5];
-  for (int k = 0; k < 3; ++k) o[k] = -c.mu * (wb[3 + k] * ir3 - 3.0 * zb[k] * xw * ir3 / r2);
+  for (int k = 0; k < 3; ++k) o[k] = -c.mu * (wb[3 + k] * ir3 - 3.0 * zb[k] * xw * ir5);
   double am = 0.0;
   const double mb = c.g[10 * b + 6], rcb = c.g[10 * b + 8];
   for (int q = 0; q < c.M; ++q) {

@@ -625,3 +625,35 @@ def test_time_reversal_on_gpu():
     s.step(500, 6.0)
     s.step(500, -6.0)
     assert np.max(np.abs(s.state()["x"] - x)) <= 1e-13 * np.sqrt(1000)
+
+
+def test_long_run_energy_bounded_like_oracle():
+    """10^4 steps of the 256-body toy disk with close encounters (mergers
+    off): the GPU run's energy error stays within the spread of the oracle's
+    own runs of the same system (the trajectory is chaotic: runs started 1e-14
+    apart meet different encounters, and the energy error, made mostly at
+    the encounters, ends anywhere between ~1e-7 and ~5e-7 after 10^4 steps);
+    angular momentum stays conserved. The no-drift property itself is pinned
+    on the oracle for an encounter-free system."""
+    nb = nbmod()
+    d = ics.workload("toy_disk_256")
+    rp = nbref.params(dt_rcrit=d.dt, merge=0)
+    rc = oracle_rc(d, rp)
+    worst_ref = 0.0
+    for k in range(3):
+        x = d.x if k == 0 else d.x * (1 + 1e-14 * np.random.default_rng(k).standard_normal(d.x.shape))
+        ref = nbref.RefSystem(rp, x, d.v, d.m, d.R, rc=rc)
+        e0r = ref.energy_momentum()["E"]
+        for _ in range(50):
+            assert ref.step(200, d.dt) == 0
+            worst_ref = max(worst_ref, abs(ref.energy_momentum()["E"] / e0r - 1))
+    gpu = nb.NBodySystem(nb.params(dt_rcrit=d.dt, merge=0), d.x, d.v, d.m, d.R, rc=rc)
+    e0g = gpu.energy_momentum()
+    eg = []
+    for _ in range(50):
+        gpu.step(200, d.dt)
+        emg = gpu.energy_momentum()
+        eg.append(abs(emg["E"] / e0g["E"] - 1))
+        assert np.linalg.norm(emg["L"] - e0g["L"]) <= 1e-10 * np.linalg.norm(e0g["L"])
+    assert gpu.stats()["groups"] > 0
+    assert max(eg) <= 2.0 * worst_ref, (max(eg), worst_ref)
