@@ -423,9 +423,12 @@ int nb_step(nb_system* s, int nsteps, double dt) {
   Ctrl c;
   rc = read_ctrl(s, &c);
   if (rc) return rc;
-  s->launches += split ? (long long)nsteps * (9 + (eject ? 1 : 0) + (refresh ? 1 : 0) +
-                                               ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0))
-                      : 1 + 8LL * nsteps;
+  // kernels per step: open (split) or once per call, drift, kick, encounter,
+  // the direct solver (1 or 2), finish, scatter, member re-kick, close; and
+  // eject 1, r_crit 1, the force anew 3, gas 2 + 2
+  const long long per_step = 7 + bs_launches(d, s->P) + (split ? 1 : 0) + (eject ? 1 : 0) +
+                             (refresh ? 1 : 0) + ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0);
+  s->launches += (split ? 0 : 1) + per_step * nsteps;
   if (s->timing) {
     for (int k = 0; k < nsteps; ++k) {
       float ms = 0.f;

@@ -753,6 +753,10 @@ void launch_bs_cluster(const Dev& d, const Phys& P, double h, cudaStream_t st) {
   cudaLaunchKernelEx(&cfg, k_bs_cluster, d, P, h, P.bs_cluster_min);
 }
 
+int bs_launches(const Dev& d, const Phys& P) {
+  return (P.ml_levels == 0 && P.bs_cluster_min > 0 && d.n >= P.bs_cluster_min) ? 2 : 1;
+}
+
 void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
   int grid = d.n < 2 * 148 ? d.n : 2 * 148;
   if (grid < 1) grid = 1;
@@ -761,7 +765,7 @@ void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
     return;
   }
   k_bs_t<false><<<grid, BNT, 0, st>>>(d, P, h);
-  if (P.bs_cluster_min > 0 && d.n >= P.bs_cluster_min) launch_bs_cluster(d, P, h, st);
+  if (bs_launches(d, P) == 2) launch_bs_cluster(d, P, h, st);
 }
 
 // ---------------------------------------------------------------------------
