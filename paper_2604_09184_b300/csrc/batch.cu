@@ -59,12 +59,13 @@ struct BSmem {
   int* alive;
   unsigned *fp, *ft, *e;  // F_prev, F_trial (BPAIR each), E keys (2 BPAIR)
   int *uf, *goff, *gmem, *gidx;
-  int* ints;  // [0] nFp [1] nFt [2] nE [3] ngroups [4] overflow [5] bs flags(2) ...
+  int* ints;  // [0] nFp [1] nFt [2] nE [3] ngroups [4] overflow [6..7] bs flags;
+              // [16 + 2w ..] flags of warp w (warp-team groups), [8] error of a warp team
 };
 
 __host__ __device__ inline size_t batch_smem_bytes(int nmax, int NT) {
   return (size_t)19 * nmax * 8 + (size_t)(99 + NT) * 8 + (size_t)nmax * 4 +
-         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + 16 * 4;
+         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + (16 + 2 * 32) * 4;
 }
 
 __device__ inline BSmem carve_smem(char* base, int nmax, int NT) {
@@ -202,7 +203,7 @@ struct SysTally {
 
 // One system for nsteps steps (nsteps == 0: initial force and flags only).
 __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, int sys, int nsteps,
-                             double h, BsTally& bt, SysTally& st) {
+                             double h, BsTally& bt, BsTally& wbt, SysTally& st) {
   const int base = B.off[sys];
   const int n = B.off[sys + 1] - base;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -322,8 +323,69 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
     __syncthreads();
     const int ne = s.ints[2], ng = s.ints[3];
     if (ne > 0) {
-      for (int g = 0; g < ng; ++g) {
+      // groups of up to 8 bodies: one per warp (warp barriers only); the
+      // others below, one after another on the whole CTA. The arithmetic per
+      // work item is the same on both teams.
+      {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        WarpTeam wt{&s.ints[16 + 2 * warp]};
+        if (threadIdx.x == 0) s.ints[8] = 0;
+        if (lane == 0) s.bred[warp] = 0.0;  // this warp's energy removed by mergers
+        __syncthreads();
+        for (int g = warp; g < ng; g += nw) {
+          const int g0 = s.goff[g];
+          const int M = s.goff[g + 1] - g0;
+          if (M > 8) continue;
+          BsCtx c;
+          c.M = M;
+          c.stride = B.bs_stride;
+          c.base = B.gscr + (size_t)(base + g0) * B.bs_stride;
+          c.g = B.gnew + (size_t)(base + g0) * 10;
+          c.kmax = P.bs_kmax;
+          c.G = P.G;
+          c.mu = P.mu;
+          for (int k = lane; k < M; k += 32) {
+            const int b = s.gmem[g0 + k];
+            double* yk = c.base + (size_t)k * c.stride + OY;
+            yk[0] = s.xs[b]; yk[1] = s.ys[b]; yk[2] = s.zs[b];
+            yk[3] = s.vxs[b]; yk[4] = s.vys[b]; yk[5] = s.vzs[b];
+            double* gk = c.g + 10 * k;
+            gk[6] = s.m[b]; gk[7] = s.R[b]; gk[8] = s.rc[b]; gk[9] = 1.0;
+            bs_set_aux(c, k, P.G, gk[6], gk[8]);
+          }
+          __syncwarp();
+          double El = 0.0;
+          const int stb = bs_integrate(c, P, h, wt, wbt, &El, (BsRec*)nullptr);
+          if (lane == 0) {
+            s.bred[warp] += El;
+            if (stb) atomicCAS(&s.ints[8], 0, stb);
+          }
+          for (int k = lane; k < M; k += 32) {
+            const int b = s.gmem[g0 + k];
+            const double* yk = c.base + (size_t)k * c.stride + OY;
+            const double* gk = c.g + 10 * k;
+            if (gk[9] != 0.0) {
+              s.x[b] = yk[0]; s.y[b] = yk[1]; s.z[b] = yk[2];
+              s.vx[b] = yk[3]; s.vy[b] = yk[4]; s.vz[b] = yk[5];
+              s.m[b] = gk[6]; s.R[b] = gk[7]; s.rc[b] = gk[8]; s.rc2[b] = gk[8] * gk[8];
+            } else {  // absorbed: massless slot far from everything, never flagged
+              s.alive[b] = 0;
+              s.x[b] = kDeadOffset * (double)(base + b + 1); s.y[b] = 0.0; s.z[b] = 0.0;
+              s.vx[b] = s.vy[b] = s.vz[b] = 0.0;
+              s.m[b] = 0.0; s.R[b] = 0.0; s.rc[b] = 0.0; s.rc2[b] = 0.0;
+            }
+          }
+          __syncwarp();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int w = 0; w < nw; ++w) El_sys += s.bred[w];  // fixed order
+        if (s.ints[8]) err = s.ints[8];
+        __syncthreads();
+      }
+      for (int g = 0; g < ng && !err; ++g) {
         const int g0 = s.goff[g];
+        if (s.goff[g + 1] - g0 <= 8) continue;  // done by a warp
         BsCtx c;
         c.M = s.goff[g + 1] - g0;
         c.stride = B.bs_stride;
@@ -419,6 +481,7 @@ __global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
   const BSmem s = carve_smem(smem_raw, B.nmax, blockDim.x);
   __shared__ int s_next, s_stop;
   BsTally bt{0, 0, 0, 0};
+  BsTally wbt{0, 0, 0, 0};  // warp-team groups (each warp's lane 0 counts its own)
   SysTally st{0, 0, 0, 0};
   const unsigned long long t0 = global_ns();
   const long long budget = *B.budget_ns;
@@ -435,13 +498,19 @@ __global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
     __syncthreads();
     const int k = s_next;
     if (k >= B.nsys) break;
-    batch_system(B, P, s, B.order[k], nsteps, h, bt, st);
+    batch_system(B, P, s, B.order[k], nsteps, h, bt, wbt, st);
   }
   if (threadIdx.x == 0 && blockIdx.x < B.cta_cap) B.cta_ns[blockIdx.x] = global_ns() - t0;
   // counters: kepler iterations are per thread; the rest are kept by thread 0
   unsigned long long kit = st.kepler_iters;
   for (int o = 16; o > 0; o >>= 1) kit += __shfl_down_sync(0xffffffffu, kit, o);
   if ((threadIdx.x & 31) == 0 && kit) atomicAdd(&B.stats[ST_KEPLER_ITERS], kit);
+  if ((threadIdx.x & 31) == 0 && (wbt.substeps || wbt.derivs || wbt.halvings || wbt.merges)) {
+    atomicAdd(&B.stats[ST_BS_SUBSTEPS], (unsigned long long)wbt.substeps);
+    atomicAdd(&B.stats[ST_BS_HALVINGS], (unsigned long long)wbt.halvings);
+    atomicAdd(&B.stats[ST_BS_DERIVS], (unsigned long long)wbt.derivs);
+    atomicAdd(&B.stats[ST_MERGES], (unsigned long long)wbt.merges);
+  }
   if (threadIdx.x == 0) {
     atomicAdd(&B.stats[ST_FORCE_EVALS], st.force_evals);
     atomicAdd(&B.stats[ST_ENC_PAIRS], st.enc_pairs);
