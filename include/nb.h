@@ -311,6 +311,31 @@ int nb_kepler_drift(int n, double mu, double* x, double* v, double dt, int max_i
 size_t nb_peak_scratch_bytes(void);
 int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void* stream);
 
+/* Element-wise evaluation, on device arrays in[n] -> out[n], of the device
+ * arithmetic helpers the kernels are built from, for checking them one by one
+ * (the integrator never calls this):
+ *   NB_MATH_EXP            exp(x), table-driven (|x| <= 700)
+ *   NB_MATH_RCP            1/x (x positive normal, 2^-126 <= x < 2^128)
+ *   NB_MATH_RSQRT          1/sqrt(x) (same range)
+ *   NB_MATH_RPOW32         x^(-3/2) as the FP64 kick forms m r^-3 from x = r^2
+ *   NB_MATH_RPOW32_MIXED   the same with the mixed kick's single Newton step
+ *   NB_MATH_RPOW32_M       the same as NB_MATH_RPOW32 from the mass alone (the
+ *                          form used by the finishing and batched kernels)
+ *   NB_MATH_CLOSE_WEIGHT   1 - w(r) of the changeover (w = K - r dK/dr, the
+ *                          paragraph after Eq. Hc) for rc = 1, x = r
+ * NB_E_INVALID for an unknown fn, n < 0 or null arrays (n > 0); asynchronous
+ * on the stream. */
+enum {
+  NB_MATH_EXP = 0,
+  NB_MATH_RCP = 1,
+  NB_MATH_RSQRT = 2,
+  NB_MATH_RPOW32 = 3,
+  NB_MATH_RPOW32_MIXED = 4,
+  NB_MATH_RPOW32_M = 5,
+  NB_MATH_CLOSE_WEIGHT = 6
+};
+int nb_math_eval(int fn, int n, const double* in, double* out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Discrete adjoint of nb_step: the gradient of a scalar loss L(x_T, v_T, m_T)
  * of the state after nsteps steps with respect to the initial x_0, v_0, m_0.

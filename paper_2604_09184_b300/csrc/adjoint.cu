@@ -399,6 +399,8 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
     c.kmax = A.kmax;
     c.G = P.G;
     c.mu = P.mu;
+    c.mu15 = 1.5 * P.mu;
+    c.mu1875 = 1.875 * P.mu;
     const int M = c.M;
     // the group's contiguous slot block, arrays of M members each
     double* r_ys = A.slot + (size_t)off * A.slot_stride;

@@ -344,6 +344,8 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
           c.kmax = P.bs_kmax;
           c.G = P.G;
           c.mu = P.mu;
+          c.mu15 = 1.5 * P.mu;
+          c.mu1875 = 1.875 * P.mu;
           for (int k = lane; k < M; k += 32) {
             const int b = s.gmem[g0 + k];
             double* yk = c.base + (size_t)k * c.stride + OY;
@@ -394,6 +396,8 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
         c.kmax = P.bs_kmax;
         c.G = P.G;
         c.mu = P.mu;
+        c.mu15 = 1.5 * P.mu;
+        c.mu1875 = 1.875 * P.mu;
         for (int k = threadIdx.x; k < c.M; k += blockDim.x) {
           const int b = s.gmem[g0 + k];
           double* yk = c.base + (size_t)k * c.stride + OY;

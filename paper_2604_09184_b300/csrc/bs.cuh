@@ -13,7 +13,7 @@ namespace nb {
 // Bulirsch-Stoer for one group per CTA.
 // Scratch per member slot (bs_stride_for_kmax(kmax) doubles):
 //   y[6] | f0[6] | per extrapolation column j = 1..kmax: zm[6] zc[6] f[6] |
-//   T[2][kmax][6] | aux[4] = (G m, 1 / (0.9 rc), rc^2, unused).
+//   T[2][kmax][6] | aux[4] = (G m, 1 / (0.9 rc), rc^2, 0.1 rc).
 // Working copies of m, R, rc, alive live in gnew[slot*10+6..9].
 //
 // A group of two bodies keeps only two lanes of its CTA busy, and every FP64
@@ -37,6 +37,7 @@ struct BsCtx {
   double* g;     // gnew of the group's first slot
   int stride, M, kmax;
   double G, mu;
+  double mu15, mu1875;  // 1.5 mu and 1.875 mu (the star term's refinement polynomial)
   double rc_scale = 1.0;  // changeover radii r_crit * rc_scale (multi-level changeover)
 };
 
@@ -51,25 +52,36 @@ __device__ __forceinline__ void bs_set_aux(const BsCtx& c, int b, double G, doub
   a[0] = G * m;
   a[1] = 1.0 / (0.9 * rc);
   a[2] = rc * rc;
+  a[3] = 0.1 * rc;
 }
 
+// Order of non-negative doubles by their bit patterns (integer compares and
+// selects, off the FP64 pipe).
+__device__ __forceinline__ bool nn_less(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ double nn_max(double a, double b) { return nn_less(a, b) ? b : a; }
+__device__ __forceinline__ double nn_min(double a, double b) { return nn_less(a, b) ? a : b; }
+
 // 1 - w for a pair inside rc (w = K - r dK/dr, K the infinitely smooth switch
-// K = f(y) / (f(y) + f(1 - y)), f(y) = exp(-1/y)). One exponential: with
-// E = exp(1/y - 1/(1-y)), K = 1 / (1 + E) and dK/dy = K (1 - K) (1/y^2 +
-// 1/(1-y)^2) = E K^2 (1/y^2 + 1/(1-y)^2). Where |1/y - 1/(1-y)| > 80, K is
-// within 2e-35 of 0 or 1 and w is 0 or 1 to double precision.
-__device__ __forceinline__ double close_weight(double qq, double rc, double inv09) {
-  const double y = (qq - 0.1 * rc) * inv09;
-  if (y < 1.0 / 746.0) return 1.0;
+// K = f(y) / (f(y) + f(1 - y)), f(y) = exp(-1/y)), from r = qq, rc01 =
+// 0.1 rc and inv09 = 1 / (0.9 rc). One exponential and two reciprocals: with
+// E = exp(1/y - 1/(1-y)) = exp((u - y) / (y u)), u = 1 - y, K = 1 / (1 + E)
+// and dK/dy = K (1 - K) (1/y^2 + 1/u^2) = E K^2 (y^2 + u^2) / (y u)^2. Where
+// |1/y - 1/u| > 80, K is within 2e-35 of 0 or 1 and w is 0 or 1 to double
+// precision. The range tests compare bit patterns.
+__device__ __forceinline__ double close_weight(double qq, double rc01, double inv09) {
+  const double y = (qq - rc01) * inv09;
+  if (__double_as_longlong(y) < __double_as_longlong(1.0 / 746.0)) return 1.0;  // also y < 0
   const double u = 1.0 - y;
-  if (u < 1.0 / 746.0) return 0.0;
-  const double iy = rcp_fast(y), iu = rcp_fast(u);
-  const double dd = iy - iu;
-  if (dd > 80.0) return 1.0;
-  if (dd < -80.0) return 0.0;
-  const double E = exp(dd);
+  if (__double_as_longlong(u) < __double_as_longlong(1.0 / 746.0)) return 0.0;
+  const double iw = rcp_fast(y * u);
+  const double dd = (u - y) * iw;
+  const long long bd = __double_as_longlong(dd);
+  if ((bd & 0x7fffffffffffffffll) > __double_as_longlong(80.0)) return bd > 0 ? 1.0 : 0.0;
+  const double E = exp_fast(dd);
   const double K = rcp_fast(1.0 + E);
-  const double dKdy = (E * K) * K * __fma_rn(iy, iy, iu * iu);
+  const double dKdy = (E * K) * K * (__fma_rn(y, y, u * u) * (iw * iw));
   return 1.0 - (K - qq * dKdy * inv09);
 }
 
@@ -85,21 +97,19 @@ static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
   fb[1] = yb[4];
   fb[2] = yb[5];
   const double r2 = __fma_rn(yb[2], yb[2], __fma_rn(yb[1], yb[1], yb[0] * yb[0]));
-  const double ks = -scale_fast<NB_PREC_FP64>(r2, c.mu);  // -mu / r^3
+  const double ks = -scale_fast<NB_PREC_FP64>(r2, c.mu, c.mu15, c.mu1875);  // -mu / r^3
   double ax = ks * yb[0], ay = ks * yb[1], az = ks * yb[2];
-  const double rcb = c.g[10 * b + 8];
   const double* ab = bs_aux(c, b);
   for (int q = 0; q < c.M; ++q) {
     if (q == b || !bs_alive(c, q)) continue;
     const double* yq = c.base + (size_t)q * c.stride + fo;
     const double dx = yq[0] - yb[0], dy = yq[1] - yb[1], dz = yq[2] - yb[2];
     const double q2 = sep2(dx, dy, dz);
-    if (q2 == 0.0) continue;
+    if (__double_as_longlong(q2) == 0ll) continue;
     const double* aq = bs_aux(c, q);
-    if (!(q2 < fmax(ab[2], aq[2]))) continue;  // 1 - w = 0 beyond rc
+    if (!(nn_less(q2, ab[2]) || nn_less(q2, aq[2]))) continue;  // 1 - w = 0 beyond rc
     const double ri = rinv_fast(q2);
-    const double omw =
-        close_weight(q2 * ri, fmax(rcb, c.g[10 * q + 8]) * c.rc_scale, fmin(ab[1], aq[1]));
+    const double omw = close_weight(q2 * ri, nn_max(ab[3], aq[3]), nn_min(ab[1], aq[1]));
     const double f = aq[0] * omw * (ri * ri * ri);
     ax = __fma_rn(f, dx, ax);
     ay = __fma_rn(f, dy, ay);

@@ -488,6 +488,8 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
       c.kmax = P.bs_kmax;
       c.G = P.G;
       c.mu = P.mu;
+      c.mu15 = 1.5 * P.mu;
+      c.mu1875 = 1.875 * P.mu;
       for (int b = lane; b < M; b += 32) {
         const int body = d.grp_mem[off + b];
         if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;
@@ -544,6 +546,8 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
     c.kmax = P.bs_kmax;
     c.G = P.G;
     c.mu = P.mu;
+    c.mu15 = 1.5 * P.mu;
+    c.mu1875 = 1.875 * P.mu;
     for (int b = threadIdx.x; b < c.M; b += blockDim.x) {
       const int body = d.grp_mem[off + b];
       if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;
@@ -667,6 +671,8 @@ __global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int
     c.kmax = P.bs_kmax;
     c.G = P.G;
     c.mu = P.mu;
+    c.mu15 = 1.5 * P.mu;
+    c.mu1875 = 1.875 * P.mu;
     for (int b = tid; b < M; b += NT) {
       const int body = d.grp_mem[off + b];
       if (!NB_GUARD(d.ctrl, body >= 0 && body < d.n && off + b < d.member_cap, 57)) continue;

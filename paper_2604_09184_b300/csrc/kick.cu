@@ -7,10 +7,13 @@
 // spends as few FP64 instructions as it can and moves everything else to the
 // INT/FP32/MUFU pipes:
 //   - dx, dy, dz, r^2, the r^-3 refinement and the three accumulations are
-//     FP64 (16 FP64 instructions per pair in the FP64 mode);
+//     FP64 (13 FP64 instructions per pair in the FP64 mode, 12 in the mixed
+//     mode);
 //   - the r^-3 seed is rsqrtf of a float built from r^2's high word with one
-//     integer shift-add, and the float seed goes back to a double by integer
-//     ops (no F2F conversions);
+//     integer shift-add; its square (exact) and cube (rounded) are built as
+//     doubles from integer products of its significand (no F2F conversions,
+//     no FP64 multiplies), and the source mass enters the refinement
+//     polynomial through m, 1.5 m and 1.875 m staged with the j-tile;
 //   - the encounter test first compares the high words of r^2 and
 //     max(rc_i^2, rc_j^2) as integers (IEEE order of non-negative doubles);
 //     only a tie or a close pair takes the exact FP64 branch, which computes
@@ -78,7 +81,7 @@ __device__ __forceinline__ double rare_pair(double r2, double sc, double mj, int
 
 template <int PREC>
 __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
-  __shared__ double sx[KNT], sy[KNT], sz[KNT], sm[KNT];
+  __shared__ double sx[KNT], sy[KNT], sz[KNT], sm[KNT], sm15[KNT], sm1875[KNT];
   __shared__ int sh[KNT];
   __shared__ int s_stop;
   if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
@@ -121,7 +124,10 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
       sx[threadIdx.x] = A.x[j];
       sy[threadIdx.x] = A.y[j];
       sz[threadIdx.x] = A.z[j];
-      sm[threadIdx.x] = A.m[j];
+      const double mj = A.m[j];
+      sm[threadIdx.x] = mj;
+      sm15[threadIdx.x] = 1.5 * mj;
+      sm1875[threadIdx.x] = 1.875 * mj;
       sh[threadIdx.x] = __double2hiint(A.rc2[j]);
     }
     __syncthreads();
@@ -132,12 +138,13 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
 #pragma unroll 4
     for (int q = 0; q < cnt; ++q) {
       const double xj = sx[q], yj = sy[q], zj = sz[q], mj = sm[q];
+      const double mj15 = sm15[q], mj1875 = PREC == NB_PREC_FP64 ? sm1875[q] : 0.0;
       const int hj = sh[q];
 #pragma unroll
       for (int k = 0; k < KIPT; ++k) {
         const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
         const double r2 = sep2(dx, dy, dz);
-        double sc = scale_fast<PREC>(r2, mj);
+        double sc = scale_fast<PREC>(r2, mj, mj15, mj1875);
         if (__double2hiint(r2) <= max(hi[k], hj))
           sc = rare_pair<true>(r2, sc, mj, ii[k], jt + q, rc2i[k], rci[k], A);
         if (PREC == NB_PREC_FP64) {

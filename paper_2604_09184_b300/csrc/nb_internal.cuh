@@ -157,46 +157,178 @@ __device__ __forceinline__ double kick_weight(double r, double rc) {
 // integer shift-add, returned to a double by integer ops), refined in FP64.
 // ---------------------------------------------------------------------------
 // rsqrtf seed of r^2 > 0 rounded toward zero to a float; 2^-126 <= r^2 < 2^128.
-__device__ __forceinline__ double rsqrt_seed(double r2) {
+// rsqrt_seed_bits returns the float's bit pattern, rsqrt_seed the same value
+// as a double.
+__device__ __forceinline__ unsigned rsqrt_seed_bits(double r2) {
   const unsigned hr = (unsigned)__double2hiint(r2);
   const float r2f = __uint_as_float((hr << 3) + 0x40000000u);
-  const unsigned yb = __float_as_uint(rsqrtf(r2f));
+  return __float_as_uint(rsqrtf(r2f));
+}
+__device__ __forceinline__ double rsqrt_seed(double r2) {
+  const unsigned yb = rsqrt_seed_bits(r2);
   return __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
 }
 
-// m / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual),
-// r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...). |e| < 2e-6, so
-// the second-order form (FP64 mode) is exact to ~1e-17 and the first-order
-// form (mixed mode, "one Newton step") to ~1e-11 relative at worst.
+// Powers of a positive normal float y0 (bit pattern yb) as doubles, by integer
+// arithmetic on its 24-bit significand s: t = y0^2 exactly (s^2 has 48 bits)
+// and y3 = y0^3 rounded to 53 bits (s^3 has 72 bits; the lowest 8 are dropped
+// before the rounding, so ties may round either way). For y0 in
+// [2^-64, 2^64] both are normal doubles. Host-callable so that the bit
+// arithmetic can be checked against exact integer products on the CPU.
+struct SeedPow {
+  double t, y3;
+};
+__host__ __device__ __forceinline__ int nb_clzll(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+__host__ __device__ __forceinline__ SeedPow seed_powers(unsigned yb) {
+  const unsigned s = (yb & 0x7fffffu) | 0x800000u;
+  const unsigned ey = yb >> 23;  // biased float exponent (y0 > 0)
+  // s^2 in [2^46, 2^48): shift its leading bit to position 52 and add the
+  // exponent field (the leading bit itself carries one unit into it)
+  const unsigned long long P = (unsigned long long)s * s;
+  const unsigned top = (unsigned)(P >> 47);
+  const unsigned long long Qt = P << (6u - top);
+  const unsigned long long bt = Qt + ((unsigned long long)(2u * ey + 768u + top) << 52);
+  // s^3 / 2^8 in [2^61, 2^64), rounded at bit L - 53 to 53 significant bits
+  const unsigned long long A = (unsigned long long)(unsigned)P * s;          // < 2^56
+  const unsigned long long B = (unsigned long long)(unsigned)(P >> 32) * s;  // < 2^40
+  const unsigned long long R8 = (B << 24) + (A >> 8);
+  const int L = 63 - nb_clzll(R8);
+  const unsigned long long Q3 = (R8 + (1ull << (L - 53))) >> (L - 52);
+  const unsigned long long b3 = Q3 + ((unsigned long long)(L + 3 * (int)ey + 580) << 52);
+  SeedPow r;
+#ifdef __CUDA_ARCH__
+  r.t = __longlong_as_double((long long)bt);
+  r.y3 = __longlong_as_double((long long)b3);
+#else
+  __builtin_memcpy(&r.t, &bt, 8);
+  __builtin_memcpy(&r.y3, &b3, 8);
+#endif
+  return r;
+}
+
+// m / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual,
+// |e| < 2e-6), r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...).
+// The FP64 mode keeps the e^2 term (truncation ~2^-56 relative), the mixed
+// mode ("one Newton step") the linear term only (~1e-11 relative at worst).
+// The mass is folded into the polynomial, m15 = 1.5 m and m1875 = 1.875 m
+// (per source body, computed once), and y0^2, y0^3 come from seed_powers, so
+// the FP64 pipe does 4 operations (3 in the mixed mode).
+template <int PREC>
+__device__ __forceinline__ double scale_fast(double r2, double m, double m15, double m1875) {
+  const SeedPow sp = seed_powers(rsqrt_seed_bits(r2));
+  const double e = __fma_rn(-r2, sp.t, 1.0);
+  if (PREC == NB_PREC_FP64) return sp.y3 * __fma_rn(__fma_rn(m1875, e, m15), e, m);
+  return sp.y3 * __fma_rn(m15, e, m);
+}
+// The same with the mass as the only per-source input (5 FP64 operations in
+// the FP64 mode, 4 in the mixed mode).
 template <int PREC>
 __device__ __forceinline__ double scale_fast(double r2, double m) {
-  const double y0 = rsqrt_seed(r2);
-  const double t = y0 * y0;
-  const double e = __fma_rn(-r2, t, 1.0);
-  const double my3 = m * (t * y0);
+  const SeedPow sp = seed_powers(rsqrt_seed_bits(r2));
+  const double e = __fma_rn(-r2, sp.t, 1.0);
+  const double my3 = sp.y3 * m;
   if (PREC == NB_PREC_FP64) return __fma_rn(my3, e * __fma_rn(1.875, e, 1.5), my3);
   return __fma_rn(my3, 1.5 * e, my3);
 }
 
 // 1/r from r^2: y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8), error ~1e-17 + rounding.
 __device__ __forceinline__ double rinv_fast(double r2) {
-  const double y0 = rsqrt_seed(r2);
-  const double e = __fma_rn(-r2, y0 * y0, 1.0);
+  const unsigned yb = rsqrt_seed_bits(r2);
+  const double y0 = __hiloint2double((int)((yb >> 3) + 0x38000000u), (int)(yb << 29));
+  const double e = __fma_rn(-r2, seed_powers(yb).t, 1.0);
   return __fma_rn(y0 * e, __fma_rn(0.375, e, 0.5), y0);
 }
 
-// 1/x for positive normal x with 2^-126 <= x < 2^128: rcp.approx seed and two
-// Newton steps r <- r + r (1 - x r) (the error squares each step).
+// 1/x for positive normal x with 2^-126 <= x < 2^128: rcp.approx seed r0 of
+// the float built from x's high word (relative error < 2^-19), then with the
+// exact residual e = 1 - x r0, 1/x = r0 / (1 - e) = r0 (1 + e + e^2) + O(e^3)
+// (truncation < 2^-57): 3 FP64 instructions.
 __device__ __forceinline__ double rcp_fast(double x) {
   const unsigned hx = (unsigned)__double2hiint(x);
   const float xf = __uint_as_float((hx << 3) + 0x40000000u);
   float rf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
   const unsigned rb = __float_as_uint(rf);
-  double r = __hiloint2double((int)((rb >> 3) + 0x38000000u), (int)(rb << 29));
-  r = __fma_rn(r, __fma_rn(-x, r, 1.0), r);
-  return __fma_rn(r, __fma_rn(-x, r, 1.0), r);
+  const double r = __hiloint2double((int)((rb >> 3) + 0x38000000u), (int)(rb << 29));
+  const double e = __fma_rn(-x, r, 1.0);
+  return __fma_rn(r, __fma_rn(e, e, e), r);
 }
+
+// ---------------------------------------------------------------------------
+// exp(x) for |x| <= 700 with few FP64 instructions, by the table-driven
+// method of P. T. P. Tang (ACM TOMS 15, 1989) with 128 table points:
+// x = (128 m + j) ln2/128 + r, |r| <= ln2/256 (+ the seed's slack), so
+// exp(x) = 2^m 2^(j/128) exp(r). k = 128 m + j is picked in FP32 from a
+// float built from x's high word (any nearby integer works: it only sets
+// the size of r); r = x - k ln2/128 in two FMAs with ln2/128 split into a
+// double and its remainder; exp(r) - 1 by its Taylor polynomial of degree 5
+// (truncation < 1e-18 relative); 2^m is added to the exponent field. 8 FP64
+// instructions, about 1 ulp. The table holds 2^(j/128) rounded to nearest.
+// ---------------------------------------------------------------------------
+static __device__ const double kExp2Tab[128] = {
+    0x1.0000000000000p+0, 0x1.0163da9fb3335p+0, 0x1.02c9a3e778061p+0, 0x1.04315e86e7f85p+0,
+    0x1.059b0d3158574p+0, 0x1.0706b29ddf6dep+0, 0x1.0874518759bc8p+0, 0x1.09e3ecac6f383p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0cc922b7247f7p+0, 0x1.0e3ec32d3d1a2p+0, 0x1.0fb66affed31bp+0,
+    0x1.11301d0125b51p+0, 0x1.12abdc06c31ccp+0, 0x1.1429aaea92de0p+0, 0x1.15a98c8a58e51p+0,
+    0x1.172b83c7d517bp+0, 0x1.18af9388c8deap+0, 0x1.1a35beb6fcb75p+0, 0x1.1bbe084045cd4p+0,
+    0x1.1d4873168b9aap+0, 0x1.1ed5022fcd91dp+0, 0x1.2063b88628cd6p+0, 0x1.21f49917ddc96p+0,
+    0x1.2387a6e756238p+0, 0x1.251ce4fb2a63fp+0, 0x1.26b4565e27cddp+0, 0x1.284dfe1f56381p+0,
+    0x1.29e9df51fdee1p+0, 0x1.2b87fd0dad990p+0, 0x1.2d285a6e4030bp+0, 0x1.2ecafa93e2f56p+0,
+    0x1.306fe0a31b715p+0, 0x1.32170fc4cd831p+0, 0x1.33c08b26416ffp+0, 0x1.356c55f929ff1p+0,
+    0x1.371a7373aa9cbp+0, 0x1.38cae6d05d866p+0, 0x1.3a7db34e59ff7p+0, 0x1.3c32dc313a8e5p+0,
+    0x1.3dea64c123422p+0, 0x1.3fa4504ac801cp+0, 0x1.4160a21f72e2ap+0, 0x1.431f5d950a897p+0,
+    0x1.44e086061892dp+0, 0x1.46a41ed1d0057p+0, 0x1.486a2b5c13cd0p+0, 0x1.4a32af0d7d3dep+0,
+    0x1.4bfdad5362a27p+0, 0x1.4dcb299fddd0dp+0, 0x1.4f9b2769d2ca7p+0, 0x1.516daa2cf6642p+0,
+    0x1.5342b569d4f82p+0, 0x1.551a4ca5d920fp+0, 0x1.56f4736b527dap+0, 0x1.58d12d497c7fdp+0,
+    0x1.5ab07dd485429p+0, 0x1.5c9268a5946b7p+0, 0x1.5e76f15ad2148p+0, 0x1.605e1b976dc09p+0,
+    0x1.6247eb03a5585p+0, 0x1.6434634ccc320p+0, 0x1.6623882552225p+0, 0x1.68155d44ca973p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6c012750bdabfp+0, 0x1.6dfb23c651a2fp+0, 0x1.6ff7df9519484p+0,
+    0x1.71f75e8ec5f74p+0, 0x1.73f9a48a58174p+0, 0x1.75feb564267c9p+0, 0x1.780694fde5d3fp+0,
+    0x1.7a11473eb0187p+0, 0x1.7c1ed0130c132p+0, 0x1.7e2f336cf4e62p+0, 0x1.80427543e1a12p+0,
+    0x1.82589994cce13p+0, 0x1.8471a4623c7adp+0, 0x1.868d99b4492edp+0, 0x1.88ac7d98a6699p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8cf3216b5448cp+0, 0x1.8f1ae99157736p+0, 0x1.9145b0b91ffc6p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.95a44cbc8520fp+0, 0x1.97d829fde4e50p+0, 0x1.9a0f170ca07bap+0,
+    0x1.9c49182a3f090p+0, 0x1.9e86319e32323p+0, 0x1.a0c667b5de565p+0, 0x1.a309bec4a2d33p+0,
+    0x1.a5503b23e255dp+0, 0x1.a799e1330b358p+0, 0x1.a9e6b5579fdbfp+0, 0x1.ac36bbfd3f37ap+0,
+    0x1.ae89f995ad3adp+0, 0x1.b0e07298db666p+0, 0x1.b33a2b84f15fbp+0, 0x1.b59728de5593ap+0,
+    0x1.b7f76f2fb5e47p+0, 0x1.ba5b030a1064ap+0, 0x1.bcc1e904bc1d2p+0, 0x1.bf2c25bd71e09p+0,
+    0x1.c199bdd85529cp+0, 0x1.c40ab5fffd07ap+0, 0x1.c67f12e57d14bp+0, 0x1.c8f6d9406e7b5p+0,
+    0x1.cb720dcef9069p+0, 0x1.cdf0b555dc3fap+0, 0x1.d072d4a07897cp+0, 0x1.d2f87080d89f2p+0,
+    0x1.d5818dcfba487p+0, 0x1.d80e316c98398p+0, 0x1.da9e603db3285p+0, 0x1.dd321f301b460p+0,
+    0x1.dfc97337b9b5fp+0, 0x1.e264614f5a129p+0, 0x1.e502ee78b3ff6p+0, 0x1.e7a51fbc74c83p+0,
+    0x1.ea4afa2a490dap+0, 0x1.ecf482d8e67f1p+0, 0x1.efa1bee615a27p+0, 0x1.f252b376bba97p+0,
+    0x1.f50765b6e4540p+0, 0x1.f7bfdad9cbe14p+0, 0x1.fa7c1819e90d8p+0, 0x1.fd3c22b8f71f1p+0,
+};
+
+__device__ __forceinline__ double exp_fast(double x) {
+  const unsigned hx = (unsigned)__double2hiint(x);
+  const unsigned ex = (hx >> 20) & 0x7ffu;
+  // float of x from its sign, exponent and top 20 fraction bits; |x| < 2^-9
+  // takes k = 0 (r = x is already small enough)
+  const float xf = __uint_as_float((hx & 0x80000000u) | ((ex - 896u) << 23) | ((hx & 0xfffffu) << 3));
+  const int k = ex < 1014u ? 0 : __float2int_rn(xf * 184.6649652337873f);  // 128 / ln2
+  // k as a double by integer ops (|k| < 2^24 is exact in a float)
+  const unsigned kb = __float_as_uint((float)k);
+  const double kd = k == 0 ? 0.0
+                           : __hiloint2double((int)((kb & 0x80000000u) | (((kb & 0x7fffffffu) >> 3) + 0x38000000u)),
+                                              (int)(kb << 29));
+  double r = __fma_rn(-kd, 0x1.62e42fefa39efp-8, x);  // ln2/128, rounded
+  r = __fma_rn(-kd, 0x1.abc9e3b39803fp-63, r);        // its remainder
+  double p = __fma_rn(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = __fma_rn(p, r, 1.0 / 6.0);
+  p = __fma_rn(p, r, 0.5);
+  p = __fma_rn(p, r, 1.0);
+  const double T = __ldg(&kExp2Tab[k & 127]);
+  const double e = __fma_rn(T, p * r, T);
+  return __hiloint2double(__double2hiint(e) + (k >> 7) * (1 << 20), __double2loint(e));
+}
+
 
 // Squared separation in the fixed rounding that decides encounter flags:
 // fma(dz, dz, fma(dy, dy, dx*dx)), every operation correctly rounded.

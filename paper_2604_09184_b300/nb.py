@@ -27,6 +27,8 @@ NB_E_WORKSPACE = -6
 NB_PREC_FP64 = 0
 NB_PREC_MIXED = 1
 NB_PREC_DS = 2
+NB_MATH_EXP, NB_MATH_RCP, NB_MATH_RSQRT, NB_MATH_RPOW32 = 0, 1, 2, 3
+NB_MATH_RPOW32_MIXED, NB_MATH_RPOW32_M, NB_MATH_CLOSE_WEIGHT = 4, 5, 6
 
 
 class NbParams(C.Structure):
@@ -123,6 +125,7 @@ def lib():
         L.nb_peak_scratch_bytes.argtypes = []
         L.nb_peak_scratch_bytes.restype = C.c_size_t
         L.nb_measure_peaks.argtypes = [_D, _D, C.c_void_p, C.c_void_p]
+        L.nb_math_eval.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.nb_adjoint_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int, C.c_int, C.c_int]
         L.nb_adjoint_workspace_bytes.restype = C.c_size_t
         L.nb_adjoint_init.argtypes = [C.POINTER(C.c_void_p), C.POINTER(NbParams), C.c_int] + [
@@ -454,6 +457,18 @@ def kepler_drift(x, v, mu, dt, max_iter=30):
     scratch = torch.zeros(64, dtype=torch.uint8, device="cuda")
     return lib().nb_kepler_drift(x.shape[0], mu, _ptr(x), _ptr(v), dt, max_iter,
                                  _ptr(scratch), _stream(torch))
+
+
+def math_eval(fn: int, x):
+    """Evaluate device arithmetic helper fn (NB_MATH_*) element-wise on a
+    float64 CUDA tensor (nb_math_eval); returns a new tensor."""
+    torch = _torch()
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    code = lib().nb_math_eval(fn, x.numel(), _ptr(x), _ptr(out), _stream(torch))
+    if code != NB_OK:
+        raise NbError(code, "nb_math_eval")
+    return out
 
 
 def measure_peaks():

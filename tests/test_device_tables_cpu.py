@@ -1,0 +1,89 @@
+"""Constants that the CUDA kernels carry as literals, checked on the CPU
+against their definitions computed independently to 60 digits: the
+table-driven exponential's 2^(j/128) table and its ln2/128 split, and the
+host-callable integer construction of a float seed's square and cube."""
+import os
+import re
+import subprocess
+from decimal import Decimal, getcontext
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "paper_2604_09184_b300", "csrc", "nb_internal.cuh")
+
+
+def _body(name):
+    src = open(HDR).read()
+    i = src.index(name)
+    return src[i:src.index("}", i)]
+
+
+def test_exp_table_is_two_to_the_j_over_128_rounded():
+    getcontext().prec = 60
+    tab = _body("kExp2Tab[128] = {")
+    vals = [float.fromhex(t) for t in re.findall(r"0x[0-9a-f.]+p[+-]\d+", tab)]
+    assert len(vals) == 128
+    for j, v in enumerate(vals):
+        assert v == float(Decimal(2) ** (Decimal(j) / Decimal(128))), j
+
+
+def test_ln2_over_128_split():
+    getcontext().prec = 60
+    src = open(HDR).read()
+    hi, lo = [float.fromhex(h) for h in re.findall(
+        r"__fma_rn\(-kd, (0x[0-9a-f.]+p[+-]\d+), [rx]\)", src)]
+    L = Decimal(2).ln() / 128
+    assert hi == float(L)
+    assert lo == float(L - Decimal(hi))
+    assert abs(Decimal(hi) + Decimal(lo) - L) < Decimal(2) ** -115  # 2^-107 relative
+    k = re.search(r"xf \* ([0-9.]+)f\)", src).group(1)  # 128 / ln2 in FP32 (only picks k)
+    assert abs(float(k) - float(128 / Decimal(2).ln())) < 1e-9
+
+
+def test_seed_powers_bit_construction(tmp_path):
+    """seed_powers (host-callable) against exact integer products for every
+    significand pattern class: y0^2 exact, y0^3 within half an ulp."""
+    nvcc = "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "sp.cu"
+    src.write_text(r'''
+#include "nb_internal.cuh"
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+int main() {
+  unsigned long long state = 88172645463325252ull;
+  long bad = 0;
+  for (long it = 0; it < 2000000; ++it) {
+    state ^= state << 13; state ^= state >> 7; state ^= state << 17;
+    unsigned e = 63 + (unsigned)(state % 128), mant = (unsigned)((state >> 8) & 0x7fffff);
+    if (it < 3) mant = it == 0 ? 0u : (it == 1 ? 0x7fffffu : 1u);
+    unsigned yb = (e << 23) | mant;
+    float yf; memcpy(&yf, &yb, 4);
+    nb::SeedPow sp = nb::seed_powers(yb);
+    long double y = yf;
+    if ((long double)sp.t != y * y) ++bad;
+    unsigned __int128 s = mant | 0x800000u, s3 = s * s * s;
+    // |y3 - y0^3| <= half an ulp of y3 (exact value from the 72-bit integer)
+    int L = 127 - __builtin_clzll((unsigned long long)(s3 >> 64));
+    unsigned __int128 q = s3 >> (L - 52), rem = s3 - (q << (L - 52));
+    unsigned __int128 half = (unsigned __int128)1 << (L - 53);
+    unsigned __int128 qr = q + (rem >= half ? 1 : 0);
+    double want_lo = ldexp((double)(unsigned long long)q, L - 52 + 3 * ((int)e - 127) - 69);
+    double want_hi = ldexp((double)(unsigned long long)qr, L - 52 + 3 * ((int)e - 127) - 69);
+    bool tie = rem == half;
+    if (!(sp.y3 == want_hi || (tie && sp.y3 == want_lo))) ++bad;
+  }
+  printf("%ld\n", bad);
+  return bad != 0;
+}
+''')
+    exe = tmp_path / "sp"
+    r = subprocess.run([nvcc, "-O2", "-std=c++17", "-I" + os.path.dirname(HDR),
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "0", out.stdout + out.stderr
