@@ -323,6 +323,8 @@ int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void
  *                          form used by the finishing and batched kernels)
  *   NB_MATH_CLOSE_WEIGHT   1 - w(r) of the changeover (w = K - r dK/dr, the
  *                          paragraph after Eq. Hc) for rc = 1, x = r
+ *   NB_MATH_MASS15         1.5 m as the kernels build it from a mass x
+ *   NB_MATH_MASS1875       1.875 m likewise (x = 0 or 2^-126 <= x <= 2^127)
  * NB_E_INVALID for an unknown fn, n < 0 or null arrays (n > 0); asynchronous
  * on the stream. */
 enum {
@@ -332,7 +334,9 @@ enum {
   NB_MATH_RPOW32 = 3,
   NB_MATH_RPOW32_MIXED = 4,
   NB_MATH_RPOW32_M = 5,
-  NB_MATH_CLOSE_WEIGHT = 6
+  NB_MATH_CLOSE_WEIGHT = 6,
+  NB_MATH_MASS15 = 7,
+  NB_MATH_MASS1875 = 8
 };
 int nb_math_eval(int fn, int n, const double* in, double* out, void* stream);
 

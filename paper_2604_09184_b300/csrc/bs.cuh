@@ -55,13 +55,6 @@ __device__ __forceinline__ void bs_set_aux(const BsCtx& c, int b, double G, doub
   a[3] = 0.1 * rc;
 }
 
-// Order of non-negative doubles by their bit patterns (integer compares and
-// selects, off the FP64 pipe).
-__device__ __forceinline__ bool nn_less(double a, double b) {
-  return __double_as_longlong(a) < __double_as_longlong(b);
-}
-__device__ __forceinline__ double nn_max(double a, double b) { return nn_less(a, b) ? b : a; }
-__device__ __forceinline__ double nn_min(double a, double b) { return nn_less(a, b) ? a : b; }
 
 // 1 - w for a pair inside rc (w = K - r dK/dr, K the infinitely smooth switch
 // K = f(y) / (f(y) + f(1 - y)), f(y) = exp(-1/y)), from r = qq, rc01 =

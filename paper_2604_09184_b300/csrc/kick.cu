@@ -28,6 +28,10 @@ namespace nb {
 
 constexpr int KNT = 128;  // threads per kick CTA (= j-tile size)
 constexpr int KIPT = 2;   // targets per thread
+#ifndef NB_KICK_UNROLL
+#define NB_KICK_UNROLL 4
+#endif
+constexpr int kKickUnroll = NB_KICK_UNROLL;  // j-loop unroll of the FP64/mixed kick (tuning)
 
 struct KickArgs {
   int n, S, jchunk;
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
     double tx[KIPT], ty[KIPT], tz[KIPT];  // tile sums (mixed mode)
 #pragma unroll
     for (int k = 0; k < KIPT; ++k) tx[k] = ty[k] = tz[k] = 0.0;
-#pragma unroll 4
+#pragma unroll kKickUnroll
     for (int q = 0; q < cnt; ++q) {
       const double xj = sx[q], yj = sy[q], zj = sz[q], mj = sm[q];
       const double mj15 = sm15[q], mj1875 = PREC == NB_PREC_FP64 ? sm1875[q] : 0.0;
@@ -419,18 +423,21 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
 constexpr int FNT = 256;
 
 // m_j w / r^3 as the kick computes it: the seeded reciprocal root beyond
-// rc_ij, the exact changeover weight inside, 0 for coincident bodies.
-__device__ __forceinline__ double finish_scale(double r2, double mj, double rci, double rcj) {
-  if (r2 == 0.0 || mj == 0.0) return 0.0;
-  const double rc = fmax(rci, rcj);
-  if (r2 < rc * rc) return pair_scale(r2, mj, rci, rcj);
-  return scale_fast<NB_PREC_FP64>(r2, mj);
+// rc_ij (m_j with 1.5 m_j and 1.875 m_j), the exact changeover weight inside,
+// 0 for coincident bodies; the range test compares bit patterns.
+__device__ __forceinline__ double finish_scale(double r2, const double* sj, int k, double rci,
+                                               double rc2i) {
+  const double mj = sj[3 * FNT + k];
+  if ((nn_less(r2, rc2i) || nn_less(r2, sj[5 * FNT + k])) || __double_as_longlong(r2) == 0ll)
+    return pair_scale(r2, mj, rci, sj[4 * FNT + k]);
+  return scale_fast<NB_PREC_FP64>(r2, mj, sj[6 * FNT + k], sj[7 * FNT + k]);
 }
 
 __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
                                                const int* cond) {
   __shared__ int s_stop, s_M;
-  __shared__ double so[5][FNT], snw[5][FNT];
+  // members' trial (so) and final (snw) states: x, y, z, m, rc, rc^2, 1.5 m, 1.875 m
+  __shared__ double so[8][FNT], snw[8][FNT];
   if (threadIdx.x == 0) {
     s_stop = d.ctrl->status || (cond && *cond == 0);
     s_M = (with_delta && d.ctrl->n_groups > 0) ? d.ctrl->n_members : 0;
@@ -450,9 +457,9 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
   }
   const int M = s_M;
   const bool delta = (i < n) && M > 0 && d.member_slot[i] < 0 && d.alive[i];
-  double xi = 0.0, yi = 0.0, zi = 0.0, rci = 0.0;
+  double xi = 0.0, yi = 0.0, zi = 0.0, rci = 0.0, rc2i = 0.0;
   if (delta) {
-    xi = d.x[i]; yi = d.y[i]; zi = d.z[i]; rci = d.rc[i];
+    xi = d.x[i]; yi = d.y[i]; zi = d.z[i]; rci = d.rc[i]; rc2i = d.rc2[i];
   }
   double cx = 0.0, cy = 0.0, cz = 0.0;
   for (int q0 = 0; q0 < M; q0 += FNT) {
@@ -464,14 +471,22 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
       so[0][threadIdx.x] = d.x[b];
       so[1][threadIdx.x] = d.y[b];
       so[2][threadIdx.x] = d.z[b];
-      so[3][threadIdx.x] = d.m[b];
+      const double mo = d.m[b];
+      so[3][threadIdx.x] = mo;
       so[4][threadIdx.x] = d.rc[b];
+      so[5][threadIdx.x] = d.rc2[b];
+      so[6][threadIdx.x] = 1.5 * mo;
+      so[7][threadIdx.x] = 1.875 * mo;
       const double* g = d.gnew + (size_t)q * 10;
       snw[0][threadIdx.x] = g[0];
       snw[1][threadIdx.x] = g[1];
       snw[2][threadIdx.x] = g[2];
-      snw[3][threadIdx.x] = g[9] != 0.0 ? g[6] : 0.0;  // absorbed: no pull
+      const double mn = g[9] != 0.0 ? g[6] : 0.0;  // absorbed: no pull
+      snw[3][threadIdx.x] = mn;
       snw[4][threadIdx.x] = g[8];
+      snw[5][threadIdx.x] = g[8] * g[8];
+      snw[6][threadIdx.x] = 1.5 * mn;
+      snw[7][threadIdx.x] = 1.875 * mn;
     }
     __syncthreads();
     if (delta) {
@@ -481,10 +496,10 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
         // seeded reciprocal root beyond rc, the exact weight inside), then
         // the term at the member's new state
         double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
-        double s = finish_scale(sep2(dx, dy, dz), so[3][k], rci, so[4][k]);
+        double s = finish_scale(sep2(dx, dy, dz), &so[0][0], k, rci, rc2i);
         cx -= s * dx; cy -= s * dy; cz -= s * dz;
         dx = snw[0][k] - xi; dy = snw[1][k] - yi; dz = snw[2][k] - zi;
-        s = finish_scale(sep2(dx, dy, dz), snw[3][k], rci, snw[4][k]);
+        s = finish_scale(sep2(dx, dy, dz), &snw[0][0], k, rci, rc2i);
         cx += s * dx; cy += s * dy; cz += s * dz;
       }
     }

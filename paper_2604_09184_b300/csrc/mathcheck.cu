@@ -19,6 +19,18 @@ __global__ void k_math_eval(int fn, int n, const double* in, double* out) {
     case NB_MATH_RPOW32_MIXED: r = scale_fast<NB_PREC_MIXED>(x, 1.0, 1.5, 0.0); break;
     case NB_MATH_RPOW32_M: r = scale_fast<NB_PREC_FP64>(x, 1.0); break;
     case NB_MATH_CLOSE_WEIGHT: r = close_weight(x, 0.1, 1.0 / 0.9); break;
+    case NB_MATH_MASS15: {
+      double a, b;
+      mass_coeffs(x, a, b);
+      r = a;
+      break;
+    }
+    case NB_MATH_MASS1875: {
+      double a, b;
+      mass_coeffs(x, a, b);
+      r = b;
+      break;
+    }
     default: r = 0.0;
   }
   out[i] = r;
@@ -27,7 +39,7 @@ __global__ void k_math_eval(int fn, int n, const double* in, double* out) {
 }  // namespace nb
 
 extern "C" int nb_math_eval(int fn, int n, const double* in, double* out, void* stream) {
-  if (n < 0 || fn < 0 || fn > NB_MATH_CLOSE_WEIGHT) return NB_E_INVALID;
+  if (n < 0 || fn < 0 || fn > NB_MATH_MASS1875) return NB_E_INVALID;
   if (n == 0) return NB_OK;
   if (!in || !out) return NB_E_INVALID;
   nb::k_math_eval<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fn, n, in, out);

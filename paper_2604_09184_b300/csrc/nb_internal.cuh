@@ -212,6 +212,14 @@ __host__ __device__ __forceinline__ SeedPow seed_powers(unsigned yb) {
   return r;
 }
 
+// Order of non-negative doubles by their bit patterns (integer compares and
+// selects, off the FP64 pipe).
+__device__ __forceinline__ bool nn_less(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ double nn_max(double a, double b) { return nn_less(a, b) ? b : a; }
+__device__ __forceinline__ double nn_min(double a, double b) { return nn_less(a, b) ? a : b; }
+
 // m / r^3 from the seed y0 ~ r^-1: with e = 1 - r^2 y0^2 (exact residual,
 // |e| < 2e-6), r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3e/2 + 15e^2/8 + ...).
 // The FP64 mode keeps the e^2 term (truncation ~2^-56 relative), the mixed
@@ -226,15 +234,31 @@ __device__ __forceinline__ double scale_fast(double r2, double m, double m15, do
   if (PREC == NB_PREC_FP64) return sp.y3 * __fma_rn(__fma_rn(m1875, e, m15), e, m);
   return sp.y3 * __fma_rn(m15, e, m);
 }
-// The same with the mass as the only per-source input (5 FP64 operations in
-// the FP64 mode, 4 in the mixed mode).
+// 1.5 m and 1.875 m for m >= 0 (zero or normal) by integer ops on m's bits:
+// 1.5 m = m + m/2 as a significand sum (truncated, relative error < 2^-52)
+// and 1.875 m through the float built from m's high word (relative error
+// < 2^-19). Both only multiply e (|e| < 2^-19) and e^2 in the refinement
+// polynomial, so their errors enter m r^-3 below 2^-56 relative.
+__device__ __forceinline__ void mass_coeffs(double m, double& m15, double& m1875) {
+  const unsigned long long B = (unsigned long long)__double_as_longlong(m);
+  const unsigned long long M = (B & 0xfffffffffffffull) | 0x10000000000000ull;
+  const unsigned long long S = M + (M >> 1);  // [1.5 2^52, 3 2^52)
+  const unsigned c = (unsigned)(S >> 53);
+  const unsigned long long R = (((B >> 52) + c - 1ull) << 52) + (S >> c);
+  const unsigned hm = (unsigned)(B >> 32);
+  const unsigned fb = __float_as_uint(__uint_as_float((hm << 3) + 0x40000000u) * 1.875f);
+  m15 = B == 0ull ? 0.0 : __longlong_as_double((long long)R);
+  m1875 = B == 0ull ? 0.0 : __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
+}
+
+// The same with the mass as the only per-source input: the coefficients come
+// from mass_coeffs, so the FP64 pipe still does 4 operations (3 mixed).
+// m in [2^-126, 2^127] or 0.
 template <int PREC>
 __device__ __forceinline__ double scale_fast(double r2, double m) {
-  const SeedPow sp = seed_powers(rsqrt_seed_bits(r2));
-  const double e = __fma_rn(-r2, sp.t, 1.0);
-  const double my3 = sp.y3 * m;
-  if (PREC == NB_PREC_FP64) return __fma_rn(my3, e * __fma_rn(1.875, e, 1.5), my3);
-  return __fma_rn(my3, 1.5 * e, my3);
+  double m15, m1875;
+  mass_coeffs(m, m15, m1875);
+  return scale_fast<PREC>(r2, m, m15, m1875);
 }
 
 // 1/r from r^2: y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8), error ~1e-17 + rounding.

@@ -29,6 +29,7 @@ NB_PREC_MIXED = 1
 NB_PREC_DS = 2
 NB_MATH_EXP, NB_MATH_RCP, NB_MATH_RSQRT, NB_MATH_RPOW32 = 0, 1, 2, 3
 NB_MATH_RPOW32_MIXED, NB_MATH_RPOW32_M, NB_MATH_CLOSE_WEIGHT = 4, 5, 6
+NB_MATH_MASS15, NB_MATH_MASS1875 = 7, 8
 
 
 class NbParams(C.Structure):

@@ -102,6 +102,23 @@ def test_close_weight_matches_oracle_changeover(nb):
     assert np.all(got[r <= 0.1] == 1.0)
 
 
+def test_mass_coefficients(nb):
+    """1.5 m (significand sum, truncated) and 1.875 m (through a float) as the
+    two-argument r^-3 builds them: relative errors below 2^-52 and 2^-18, zero
+    for zero (the polynomial multiplies them by e < 2^-19 and e^2)."""
+    rng = np.random.default_rng(5)
+    m = np.concatenate([10.0 ** rng.uniform(-30, 30, 20000), [0.0, 1.0, 2.0 - 2.0 ** -52, 1e-10,
+                                                              2.29e-10, 9.5e-4, 2.0 ** -126]])
+    m15 = evaluate(nb, nb.NB_MATH_MASS15, m)
+    m1875 = evaluate(nb, nb.NB_MATH_MASS1875, m)
+    nz = m > 0
+    getcontext().prec = 40
+    ref15 = np.array([float(Decimal(float(v)) * Decimal("1.5")) for v in m])
+    assert np.all(np.abs(m15[nz] - ref15[nz]) <= 2.0 ** -52 * ref15[nz])
+    assert np.all(np.abs(m1875[nz] - 1.875 * m[nz]) <= 2.0 ** -18 * 1.875 * m[nz])
+    assert m15[~nz].tolist() == [0.0] and m1875[~nz].tolist() == [0.0]
+
+
 def test_invalid_function_rejected(nb):
     L = nb.lib()
     assert L.nb_math_eval(99, 0, None, None, None) == nb.NB_E_INVALID
