@@ -40,36 +40,39 @@ constexpr int kSubCap = 256; // recorded BS substeps per group and step
 constexpr int kMrgCap = 16;  // recorded mergers per group and step
 
 // K, dK/dy, d2K/dy2 of the infinitely smooth switch K = f(y) / (f(y) + f(1-y)),
-// f(y) = exp(-1/y), with one exponential: E = exp(1/y - 1/(1-y)), K = 1/(1+E),
-// A = 1/y^2 + 1/(1-y)^2, A' = -2/y^3 + 2/(1-y)^3,
-// K' = E K^2 A, K'' = E K^2 (2 K E A^2 + A' - A^2). Where |1/y - 1/(1-y)| > 80
+// f(y) = exp(-1/y), with one exponential and one reciprocal: u = 1 - y,
+// w = 1 / (y u), E = exp(1/y - 1/u) = exp((u - y) w), K = 1/(1+E),
+// A = 1/y^2 + 1/u^2 = (y^2 + u^2) w^2, A' = 2/u^3 - 2/y^3 = 2 (y^3 - u^3) w^3,
+// K' = E K^2 A, K'' = E K^2 (2 K E A^2 + A' - A^2). Where |1/y - 1/u| > 80
 // K is within 2e-35 of 0 or 1 and its derivatives vanish to double precision.
+// The range tests compare bit patterns.
 __device__ void changeover_y(double y, double& K, double& K1, double& K2) {
   K1 = 0.0;
   K2 = 0.0;
-  if (y <= 0.0) {
+  const long long by = __double_as_longlong(y);
+  if (by <= 0ll) {  // y <= 0 (either zero)
     K = 0.0;
     return;
   }
-  if (y >= 1.0) {
+  if (by >= __double_as_longlong(1.0)) {
     K = 1.0;
     return;
   }
   const double u = 1.0 - y;
-  const double iy = rcp_fast(y), iu = rcp_fast(u);
-  const double dd = iy - iu;
-  if (dd > 80.0) {
-    K = 0.0;
+  const double yu = y * u;
+  const double iw = rcp_fast(yu);
+  const double dd = (u - y) * iw;
+  const long long bd = __double_as_longlong(dd);
+  if ((bd & 0x7fffffffffffffffll) > __double_as_longlong(80.0)) {
+    K = bd > 0 ? 0.0 : 1.0;
     return;
   }
-  if (dd < -80.0) {
-    K = 1.0;
-    return;
-  }
-  const double E = exp(dd);
+  const double E = exp_fast(dd);
   K = rcp_fast(1.0 + E);
-  const double A = __fma_rn(iy, iy, iu * iu);
-  const double A1 = 2.0 * (iu * iu * iu - iy * iy * iy);
+  const double s2 = __fma_rn(y, y, u * u);
+  const double iw2 = iw * iw;
+  const double A = s2 * iw2;
+  const double A1 = 2.0 * ((y - u) * (s2 + yu)) * (iw2 * iw);
   const double EK2 = E * K * K;
   K1 = EK2 * A;
   K2 = EK2 * (2.0 * K * E * A * A + A1 - A * A);
@@ -146,9 +149,9 @@ __global__ void __launch_bounds__(VNT) k_kick_vjp(Vjp V) {
     for (int q = 0; q < cnt; ++q) {
       const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
       const double r2 = sep2(dx, dy, dz);
-      if (r2 == 0.0) continue;  // the target itself (and coincident bodies)
+      if (__double_as_longlong(r2) == 0ll) continue;  // the target itself (and coincident bodies)
       double p, dp_r;
-      if (r2 >= fmax(rck2, src2[q])) {
+      if (!(nn_less(r2, rck2) || nn_less(r2, src2[q]))) {
         const double ri = rinv_fast(r2);
         const double ir2 = ri * ri;
         p = ri * ir2;
@@ -380,9 +383,10 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
 // weights c_j from the same recursion applied to unit vectors.
 // The adjoint of one group's integration by a team (one warp or one CTA):
 // cw and Tn are the team's shared scratch for the extrapolation weights.
+// scr: the team's direct-solver scratch (M slots of bs_stride doubles).
 template <class Team>
 __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
-                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2]) {
+                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2], double* scr) {
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int* gmem = A.grp + 2 + ng + 1;
@@ -394,7 +398,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
     BsCtx c;
     c.M = goff[grp + 1] - off;
     c.stride = A.bs_stride;
-    c.base = A.gscr + (size_t)off * A.bs_stride;
+    c.base = scr;
     c.g = A.gnew + (size_t)off * 10;
     c.kmax = A.kmax;
     c.G = P.G;
@@ -640,6 +644,7 @@ __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) 
   __shared__ double cw[ABNT / 32][kMaxBsK + 2];
   __shared__ double Tn[ABNT / 32][kMaxBsK + 2][kMaxBsK + 2];
   __shared__ int s_wflags[ABNT / 32][2];
+  extern __shared__ double s_bscr[];  // the warp teams' scratch, 8 slots each
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int warp = threadIdx.x >> 5;
@@ -647,13 +652,14 @@ __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) 
   WarpTeam wt{s_wflags[warp]};
   for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
     if (goff[grp + 1] - goff[grp] > 8) continue;
-    bs_adjoint_group(A, P, h, grp, wt, cw[warp], Tn[warp]);
+    bs_adjoint_group(A, P, h, grp, wt, cw[warp], Tn[warp],
+                     s_bscr + (size_t)warp * 8 * A.bs_stride);
   }
   __syncthreads();
   BlockTeam bt{s_red, s_flags};
   for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
     if (goff[grp + 1] - goff[grp] <= 8) continue;
-    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0]);
+    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0], A.gscr + (size_t)goff[grp] * A.bs_stride);
   }
 }
 
@@ -956,7 +962,10 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
   A.gscr = a->gscr; A.gnew = a->gnew; A.slot = a->slot; A.H = a->H; A.kk = a->kk;
   A.counts = a->counts; A.mrg = a->mrg; A.mst = a->mst; A.status = a->status;
   int grid = n < 2 * 148 ? n : 2 * 148;
-  k_bs_adjoint<<<grid, ABNT, 0, a->st>>>(A, P, dt);
+  const size_t wsm = (size_t)(ABNT / 32) * 8 * A.bs_stride * sizeof(double);  // <= 48.1 KB
+  if (wsm > 40 * 1024)  // with the static shared memory beyond the 48 KB default
+    cudaFuncSetAttribute(k_bs_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+  k_bs_adjoint<<<grid, ABNT, wsm, a->st>>>(A, P, dt);
   // opening C(h/2), then the opening B(h/2) at the step's start positions
   cdrift_vjp(a, a->alive0, r.st0, r.xs6, hh);
   kick_vjp(a, r.xs6, r.st0, r.st0 + 2 * n, a->alive0, hh);

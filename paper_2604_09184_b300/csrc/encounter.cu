@@ -31,6 +31,10 @@ namespace nb {
 constexpr int ENT = 1024;  // threads of k_encounter
 constexpr int BNT = 64;    // threads of a BS CTA
 constexpr int kWarpGroupMax = 8;  // groups of up to 8 bodies run on one warp
+// the warp teams' scratch of a CTA fits the 48 KB of dynamic shared memory
+// that needs no opt-in, with room for the kernel's static shared memory
+static_assert((size_t)(BNT / 32) * kWarpGroupMax * bs_stride_for_kmax(kMaxBsK) * sizeof(double) <=
+                  48 * 1024 - 1024, "warp-team scratch exceeds 47 KB");
 
 // Which solver takes a group of M bodies: 2 = a cluster (bs_cluster_min > 0
 // and M >= it), 1 = one warp (M <= kWarpGroupMax), 0 = one CTA. The
@@ -472,8 +476,11 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
   if (s_stop) return;
   BsTally tally{0, 0, 0, 0};
   if constexpr (!ML) {
-    // small groups: one per warp, with warp barriers only
+    // small groups: one per warp, with warp barriers only; the group's scratch
+    // (kWarpGroupMax slots of bs_stride doubles per warp) in dynamic shared
+    // memory (the CTA's other groups keep theirs in gscr)
     __shared__ int s_wflags[BNT / 32][2];
+    extern __shared__ double s_bscr[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTeam wt{s_wflags[warp]};
     for (int grp = blockIdx.x * (BNT / 32) + warp; grp < s_ng; grp += gridDim.x * (BNT / 32)) {
@@ -483,7 +490,7 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
       BsCtx c;
       c.M = M;
       c.stride = d.bs_stride;
-      c.base = d.gscr + (size_t)off * d.bs_stride;
+      c.base = s_bscr + (size_t)warp * kWarpGroupMax * d.bs_stride;  // the warp's scratch
       c.g = d.gnew + (size_t)off * 10;
       c.kmax = P.bs_kmax;
       c.G = P.G;
@@ -770,7 +777,9 @@ void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
     k_bs_t<true><<<grid, BNT, 0, st>>>(d, P, h);
     return;
   }
-  k_bs_t<false><<<grid, BNT, 0, st>>>(d, P, h);
+  // <= 48 KB for bs_kmax <= 12 (2 warps x 8 slots x 376 doubles)
+  const size_t wsm = (size_t)(BNT / 32) * kWarpGroupMax * d.bs_stride * sizeof(double);
+  k_bs_t<false><<<grid, BNT, wsm, st>>>(d, P, h);
   if (bs_launches(d, P) == 2) launch_bs_cluster(d, P, h, st);
 }
 
