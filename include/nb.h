@@ -111,6 +111,12 @@ typedef struct {
    * one CTA (bs_cluster_min does not apply). Single-system path only. */
   int ml_levels;
   int ml_factor;       /* default 3; 2..64 */
+  /* Speculative half-size attempts in the direct solver: 1 (default) = a group
+   * of up to 4 bodies run by one warp also integrates, in its spare lanes,
+   * the half-size attempt that a failure of the current attempt would lead
+   * to, and takes it on a failure; 0 = attempts one after the other. The
+   * results, counters and adjoint records are the same bit for bit. */
+  int bs_speculate;
 } nb_params;
 
 typedef struct {

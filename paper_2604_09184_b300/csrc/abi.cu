@@ -100,7 +100,7 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
 }
 
 Phys make_phys(const nb_params& p) {
-  Phys P;
+  Phys P{};
   P.G = p.G;
   P.m0 = p.m0;
   P.mu = p.G * p.m0;
@@ -125,6 +125,7 @@ Phys make_phys(const nb_params& p) {
   P.bs_cluster_min = p.bs_cluster_min;
   P.ml_levels = p.ml_levels;
   P.ml_factor = p.ml_factor;
+  P.bs_speculate = p.bs_speculate;
   return P;
 }
 
@@ -145,6 +146,7 @@ bool params_ok(const nb_params* p) {
   if (p->bs_cluster_min < 0) return false;
   if (p->ml_levels < 0 || p->ml_levels > kMlMax || p->ml_factor < 2 || p->ml_factor > 64)
     return false;
+  if (p->bs_speculate != 0 && p->bs_speculate != 1) return false;
   return true;
 }
 
@@ -243,6 +245,7 @@ void nb_default_params(nb_params* p) {
   p->bs_cluster_min = 64;
   p->ml_levels = 0;
   p->ml_factor = 3;
+  p->bs_speculate = 1;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {

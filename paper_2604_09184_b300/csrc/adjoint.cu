@@ -383,10 +383,12 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
 // weights c_j from the same recursion applied to unit vectors.
 // The adjoint of one group's integration by a team (one warp or one CTA):
 // cw and Tn are the team's shared scratch for the extrapolation weights.
-// scr: the team's direct-solver scratch (M slots of bs_stride doubles).
+// scr: the team's direct-solver scratch (M slots of bs_stride doubles;
+// nslots >= 2 M lets the replay speculate on half-size attempts).
 template <class Team>
 __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
-                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2], double* scr) {
+                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2], double* scr,
+                                 int nslots) {
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int* gmem = A.grp + 2 + ng + 1;
@@ -445,7 +447,9 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
     team.sync();
     BsTally tally{0, 0, 0, 0};
     double El = 0.0;
-    int st = bs_integrate(c, P, h, team, tally, &El, &rec);
+    int st = bs_integrate(c, P, h, team, tally, &El, &rec,
+                          P.bs_speculate && 2 * M <= nslots ? scr + (size_t)M * c.stride
+                                                            : nullptr);
     team.sync();
     if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
     if (st) {
@@ -640,10 +644,10 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
 
 __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
   __shared__ double s_red[ABNT];
-  __shared__ int s_flags[2];
+  __shared__ int s_flags[4];
   __shared__ double cw[ABNT / 32][kMaxBsK + 2];
   __shared__ double Tn[ABNT / 32][kMaxBsK + 2][kMaxBsK + 2];
-  __shared__ int s_wflags[ABNT / 32][2];
+  __shared__ int s_wflags[ABNT / 32][4];
   extern __shared__ double s_bscr[];  // the warp teams' scratch, 8 slots each
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
@@ -653,13 +657,14 @@ __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) 
   for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
     if (goff[grp + 1] - goff[grp] > 8) continue;
     bs_adjoint_group(A, P, h, grp, wt, cw[warp], Tn[warp],
-                     s_bscr + (size_t)warp * 8 * A.bs_stride);
+                     s_bscr + (size_t)warp * 8 * A.bs_stride, 8);
   }
   __syncthreads();
   BlockTeam bt{s_red, s_flags};
   for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
     if (goff[grp + 1] - goff[grp] <= 8) continue;
-    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0], A.gscr + (size_t)goff[grp] * A.bs_stride);
+    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0], A.gscr + (size_t)goff[grp] * A.bs_stride,
+                     0);
   }
 }
 

@@ -680,7 +680,7 @@ size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDe
 
 struct nb_batch {
   BatchDev d;
-  Phys P;
+  Phys P{};
   nb_params prm;
   cudaStream_t st;
   Snap snap;
@@ -708,7 +708,7 @@ namespace {
   } while (0)
 
 Phys phys_of(const nb_params& p) {
-  Phys P;
+  Phys P{};
   P.G = p.G; P.m0 = p.m0; P.mu = p.G * p.m0; P.dt_rcrit = p.dt_rcrit;
   P.hill_factor = p.hill_factor; P.vel_factor = p.vel_factor; P.bs_tol = p.bs_tol;
   P.vel_mode = p.vel_mode; P.merge = p.merge; P.precision = NB_PREC_FP64;

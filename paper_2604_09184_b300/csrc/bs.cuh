@@ -195,6 +195,127 @@ struct BsTally {
   long long ml_substeps = 0, ml_groups = 0;  // multi-level changeover
 };
 
+// One speculative attempt pair (see bs_integrate): the attempt of size H
+// from y (slots of c) and, in the other lanes, the attempt of size H/2 from
+// the same y (column and Neville scratch in the slots of cs; it reads y, f0
+// and the masses and radii from c's slots and its own copy of the members'
+// aux words). Both columns sets advance in one wave over the kmax columns;
+// f0 = f(y) is shared (the half-size attempt would compute the same values).
+// Flags: [0], [1] = the H attempt accepted at column [1]; [2], [3] = the H/2
+// attempt accepted at column [3]. After its acceptance the H/2 attempt's
+// Neville rows stop, so its accepted row stays in place. Returns the number
+// of derivative evaluations the H/2 attempt would have taken on its own
+// (its f0 included), up to its acceptance or its last column.
+template <class Sy>
+static __device__ long long bs_attempt_pair(const BsCtx& c, const BsCtx& cs, const Phys& P,
+                                            double H, Sy& sy, BsTally& tally) {
+  const int kmax = c.kmax, M = c.M;
+  const int NT = sy.nthreads(), tid = sy.tid();
+  int* s_flags = sy.flags();
+  const int offT = bs_off_T(kmax);
+  const int KM = kmax * M;
+  // start both column sets: z0 = y, z1 = y + hs f0
+  for (int it = tid; it < 2 * KM; it += NT) {
+    const int half = it >= KM, r = it - half * KM;
+    const int j = 1 + r / M, b = r % M;
+    const double* s = c.base + (size_t)b * c.stride;
+    double* col = (half ? cs.base : c.base) + (size_t)b * c.stride + bs_off_col(j);
+    const double hs = (half ? 0.5 * H : H) / (2 * j);
+    for (int k = 0; k < 6; ++k) {
+      col[CZM + k] = s[OY + k];
+      col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
+    }
+  }
+  sy.sync();
+  long long sd = 1;  // the H/2 attempt's own f0
+  for (int t = 1; t <= 2 * kmax; ++t) {
+    const int j0 = max(1, (t + 1) / 2);
+    const int ncol = kmax - j0 + 1, NI = ncol * M;
+    const bool sdone = s_flags[2] != 0;
+    for (int it = tid; it < 2 * NI; it += NT) {
+      const int half = it >= NI, r = it - half * NI;
+      const int j = j0 + r / M, b = r % M;
+      bs_deriv(half ? cs : c, bs_off_col(j) + CZC, bs_off_col(j) + CF, b);
+    }
+    sy.sync();
+    tally.derivs += ncol;
+    if (!sdone) sd += ncol;
+    for (int it = tid; it < 2 * NI; it += NT) {
+      const int half = it >= NI, r = it - half * NI;
+      const int j = j0 + r / M, b = r % M;
+      double* sl = (half ? cs.base : c.base) + (size_t)b * c.stride;
+      double* col = sl + bs_off_col(j);
+      const double hs = (half ? 0.5 * H : H) / (2 * j);
+      if (t < 2 * j) {
+        for (int k = 0; k < 6; ++k) {
+          const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
+          col[CZM + k] = col[CZC + k];
+          col[CZC + k] = zn;
+        }
+      } else if (!(half && sdone)) {  // t == 2j: the column's result T_j1
+        double* Tc = sl + offT + (j & 1) * kmax * 6;
+        for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (col[CZC + k] + col[CZM + k] + hs * col[CF + k]);
+      }
+    }
+    sy.sync();
+    if (t & 1) continue;
+    const int j = t / 2;  // column j of both attempts is complete: Neville rows and tests
+    double em = 0.0, es = 0.0;
+    for (int it = tid; it < 2 * M; it += NT) {
+      const int half = it >= M, b = it - half * M;
+      if (half && sdone) continue;
+      double* sl = (half ? cs.base : c.base) + (size_t)b * c.stride;
+      double* Tc = sl + offT + (j & 1) * kmax * 6;
+      double* Tp = sl + offT + ((j - 1) & 1) * kmax * 6;
+      for (int q = 1; q < j; ++q) {
+        const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+        for (int k = 0; k < 6; ++k) {
+          const double tq = Tc[6 * (q - 1) + k];
+          Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
+        }
+      }
+      if (j >= 3 && bs_alive(c, b)) {
+        const double* A = Tc + 6 * (j - 1);
+        const double* B = Tc + 6 * (j - 2);
+        double e = 0.0;
+        for (int part = 0; part < 2; ++part) {
+          double dm = 0.0, ym = 0.0;
+          for (int k = 3 * part; k < 3 * part + 3; ++k) {
+            dm = fmax(dm, fabs(A[k] - B[k]));
+            ym = fmax(ym, fabs(A[k]));
+          }
+          e = fmax(e, dm / (ym + 1e-300));
+        }
+        if (half) es = fmax(es, e); else em = fmax(em, e);
+      }
+    }
+    const double Em = sy.max_to_first(em);
+    sy.sync();  // the team's reduction scratch is reused
+    const double Es = sy.max_to_first(es);
+    if (tid == 0 && j >= 3) {
+      if (Em <= P.bs_tol) {
+        s_flags[0] = 1;
+        s_flags[1] = j;
+      }
+      if (!sdone && Es <= P.bs_tol) {
+        s_flags[2] = 1;
+        s_flags[3] = j;
+      }
+    }
+    sy.sync();
+    if (s_flags[0]) {
+      for (int b = tid; b < M; b += NT) {
+        double* sl = c.base + (size_t)b * c.stride;
+        const double* Tc = sl + offT + (j & 1) * kmax * 6 + 6 * (j - 1);
+        for (int k = 0; k < 6; ++k) sl[OY + k] = Tc[k];
+      }
+      sy.sync();
+      break;
+    }
+  }
+  return sd;
+}
+
 // Integrate H_A restricted to one group over h with all threads of the
 // calling CTA (any blockDim): Gragg modified midpoint with n_j = 2j substeps,
 // Neville extrapolation in the substep squared, acceptance at j >= 3 when
@@ -207,13 +328,23 @@ struct BsTally {
 // when its Neville row is built and tested. The group state starts in the y
 // fields and ends there. Sy is the team that runs it: one CTA (BlockTeam)
 // or a thread-block cluster (ClusterTeam, in encounter.cu); it provides the
-// thread index and count, the barrier, a max-reduction and two flag words.
+// thread index and count, the barrier, a max-reduction and four flag words.
 // Every team member takes the same branches. Returns 0, NB_E_NOCONV or
 // NB_E_TIMEOUT (the same in every thread); *El (tid 0) receives the energy
 // removed by mergers.
+//
+// Speculation (spec: M more slots of scratch after the group's, or null):
+// when the team has lanes for both (2 kmax M <= its threads), every attempt
+// of size H also runs, in the spare lanes, the attempt of size H/2 that a
+// failure would lead to (bs_attempt_pair). If the H attempt fails and the
+// H/2 one was accepted, the H/2 result is taken, with the same state updates,
+// counters and records as running the two attempts one after the other; the
+// arithmetic of each attempt is unchanged, so the result is the same bit for
+// bit, and a failure costs no wave steps of its own.
 template <class Sy>
 static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& sy,
-                                   BsTally& tally, double* El, BsRec* rec) {
+                                   BsTally& tally, double* El, BsRec* rec,
+                                   double* spec = nullptr) {
   int rec_n = 0;  // accepted substeps recorded (the same in every thread)
   const int kmax = c.kmax;
   const int M = c.M;
@@ -225,6 +356,9 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
   // passes of the CTA, never fewer than one column
   int W = (2 * NT) / (M > 0 ? M : 1);
   W = W < 1 ? 1 : (W > kmax ? kmax : W);
+  const bool can_spec = spec != nullptr && 2 * kmax * M <= NT;
+  BsCtx cs = c;
+  if (can_spec) cs.base = spec;
   int level = 0;
   long long done = 0;
   int status = 0;
@@ -232,6 +366,7 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
   int merges = 0;
   while (done < (1ll << level)) {
     const double H = ldexp(h, -level);
+    const bool sp = can_spec && level + 1 <= P.bs_max_halvings;
     if (rec && rec_n < rec->cap) {  // stage the substep's start (kept if it is accepted)
       for (int b = tid; b < M; b += NT) {
         const double* y = c.base + (size_t)b * c.stride + OY;
@@ -247,109 +382,163 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
     if (tid == 0) {
       s_flags[0] = 0;
       s_flags[1] = 0;
+      if (sp) {
+        s_flags[2] = 0;
+        s_flags[3] = 0;
+      }
     }
-    // f0 = f(y), shared by every column
-    for (int b = tid; b < M; b += NT) bs_deriv(c, OY, OF0, b);
+    // f0 = f(y), shared by every column (and by the speculative attempt)
+    for (int b = tid; b < M; b += NT) {
+      bs_deriv(c, OY, OF0, b);
+      if (sp) {  // the speculative slots' copy of the aux words
+        const double* a = bs_aux(c, b);
+        double* as = bs_aux(cs, b);
+        for (int k = 0; k < 4; ++k) as[k] = a[k];
+      }
+    }
     sy.sync();
     tally.derivs += 1;
-    for (int ja = 1; ja <= kmax && !s_flags[0]; ja += W) {
-      const int jb = ja + W - 1 < kmax ? ja + W - 1 : kmax;
-      const int nw = jb - ja + 1;
-      // start the window's columns: z0 = y, z1 = y + hs f0
-      for (int it = tid; it < nw * M; it += NT) {
-        const int j = ja + it / M, b = it % M;
-        double* s = c.base + (size_t)b * c.stride;
-        double* col = s + bs_off_col(j);
-        const double hs = H / (2 * j);
-        for (int k = 0; k < 6; ++k) {
-          col[CZM + k] = s[OY + k];
-          col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
-        }
-      }
-      sy.sync();
-      for (int t = 1; t <= 2 * jb; ++t) {
-        // columns still running at wave step t: 2j >= t
-        const int j0 = max(ja, (t + 1) / 2);
-        const int ncol = jb - j0 + 1;
-        for (int it = tid; it < ncol * M; it += NT) {
-          const int j = j0 + it / M, b = it % M;
-          bs_deriv(c, bs_off_col(j) + CZC, bs_off_col(j) + CF, b);
-        }
-        sy.sync();
-        tally.derivs += ncol;
-        for (int it = tid; it < ncol * M; it += NT) {
-          const int j = j0 + it / M, b = it % M;
+    long long sderivs = 0;
+    if (sp) {
+      sderivs = bs_attempt_pair(c, cs, P, H, sy, tally);
+    } else {
+      for (int ja = 1; ja <= kmax && !s_flags[0]; ja += W) {
+        const int jb = ja + W - 1 < kmax ? ja + W - 1 : kmax;
+        const int nw = jb - ja + 1;
+        // start the window's columns: z0 = y, z1 = y + hs f0
+        for (int it = tid; it < nw * M; it += NT) {
+          const int j = ja + it / M, b = it % M;
           double* s = c.base + (size_t)b * c.stride;
           double* col = s + bs_off_col(j);
           const double hs = H / (2 * j);
-          if (t < 2 * j) {
-            for (int k = 0; k < 6; ++k) {
-              const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
-              col[CZM + k] = col[CZC + k];
-              col[CZC + k] = zn;
-            }
-          } else {  // t == 2j: the column's result T_j1
-            double* Tc = s + offT + (j & 1) * kmax * 6;
-            for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (col[CZC + k] + col[CZM + k] + hs * col[CF + k]);
+          for (int k = 0; k < 6; ++k) {
+            col[CZM + k] = s[OY + k];
+            col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
           }
         }
         sy.sync();
-        if ((t & 1) || t / 2 < ja) continue;
-        const int j = t / 2;  // column j is complete: Neville row j and the test
-        double emax = 0.0;
-        for (int b = tid; b < M; b += NT) {
-          double* s = c.base + (size_t)b * c.stride;
-          double* Tc = s + offT + (j & 1) * kmax * 6;
-          double* Tp = s + offT + ((j - 1) & 1) * kmax * 6;
-          for (int q = 1; q < j; ++q) {
-            // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
-            const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
-            for (int k = 0; k < 6; ++k) {
-              const double tq = Tc[6 * (q - 1) + k];
-              Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
-            }
-          }
-          if (j >= 3 && bs_alive(c, b)) {
-            const double* A = Tc + 6 * (j - 1);
-            const double* B = Tc + 6 * (j - 2);
-            for (int part = 0; part < 2; ++part) {
-              double dm = 0.0, ym = 0.0;
-              for (int k = 3 * part; k < 3 * part + 3; ++k) {
-                dm = fmax(dm, fabs(A[k] - B[k]));
-                ym = fmax(ym, fabs(A[k]));
-              }
-              emax = fmax(emax, dm / (ym + 1e-300));
-            }
-          }
-        }
-        const double e = sy.max_to_first(emax);  // valid in tid 0
-        if (tid == 0) {
-          if (j >= 3 && e <= P.bs_tol) {
-            s_flags[0] = 1;
-            s_flags[1] = j;
-          }
-        }
-        sy.sync();
-        if (s_flags[0]) {
-          for (int b = tid; b < M; b += NT) {
-            double* s = c.base + (size_t)b * c.stride;
-            const double* Tc = s + offT + (j & 1) * kmax * 6 + 6 * (j - 1);
-            for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
+        for (int t = 1; t <= 2 * jb; ++t) {
+          // columns still running at wave step t: 2j >= t
+          const int j0 = max(ja, (t + 1) / 2);
+          const int ncol = jb - j0 + 1;
+          for (int it = tid; it < ncol * M; it += NT) {
+            const int j = j0 + it / M, b = it % M;
+            bs_deriv(c, bs_off_col(j) + CZC, bs_off_col(j) + CF, b);
           }
           sy.sync();
-          break;
+          tally.derivs += ncol;
+          for (int it = tid; it < ncol * M; it += NT) {
+            const int j = j0 + it / M, b = it % M;
+            double* s = c.base + (size_t)b * c.stride;
+            double* col = s + bs_off_col(j);
+            const double hs = H / (2 * j);
+            if (t < 2 * j) {
+              for (int k = 0; k < 6; ++k) {
+                const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
+                col[CZM + k] = col[CZC + k];
+                col[CZC + k] = zn;
+              }
+            } else {  // t == 2j: the column's result T_j1
+              double* Tc = s + offT + (j & 1) * kmax * 6;
+              for (int k = 0; k < 6; ++k) Tc[k] = 0.5 * (col[CZC + k] + col[CZM + k] + hs * col[CF + k]);
+            }
+          }
+          sy.sync();
+          if ((t & 1) || t / 2 < ja) continue;
+          const int j = t / 2;  // column j is complete: Neville row j and the test
+          double emax = 0.0;
+          for (int b = tid; b < M; b += NT) {
+            double* s = c.base + (size_t)b * c.stride;
+            double* Tc = s + offT + (j & 1) * kmax * 6;
+            double* Tp = s + offT + ((j - 1) & 1) * kmax * 6;
+            for (int q = 1; q < j; ++q) {
+              // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
+              const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+              for (int k = 0; k < 6; ++k) {
+                const double tq = Tc[6 * (q - 1) + k];
+                Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
+              }
+            }
+            if (j >= 3 && bs_alive(c, b)) {
+              const double* A = Tc + 6 * (j - 1);
+              const double* B = Tc + 6 * (j - 2);
+              for (int part = 0; part < 2; ++part) {
+                double dm = 0.0, ym = 0.0;
+                for (int k = 3 * part; k < 3 * part + 3; ++k) {
+                  dm = fmax(dm, fabs(A[k] - B[k]));
+                  ym = fmax(ym, fabs(A[k]));
+                }
+                emax = fmax(emax, dm / (ym + 1e-300));
+              }
+            }
+          }
+          const double e = sy.max_to_first(emax);  // valid in tid 0
+          if (tid == 0) {
+            if (j >= 3 && e <= P.bs_tol) {
+              s_flags[0] = 1;
+              s_flags[1] = j;
+            }
+          }
+          sy.sync();
+          if (s_flags[0]) {
+            for (int b = tid; b < M; b += NT) {
+              double* s = c.base + (size_t)b * c.stride;
+              const double* Tc = s + offT + (j & 1) * kmax * 6 + 6 * (j - 1);
+              for (int k = 0; k < 6; ++k) s[OY + k] = Tc[k];
+            }
+            sy.sync();
+            break;
+          }
         }
       }
     }
     ++attempts;
-    const int acc = s_flags[0], kacc = s_flags[1];
+    int acc = s_flags[0], kacc = s_flags[1];
+    double Hacc = H;
+    if (!acc) {
+      ++tally.halvings;
+      if (level >= P.bs_max_halvings) {
+        status = NB_E_NOCONV;
+        break;
+      }
+      ++level;
+      done *= 2;
+      if (sp && attempts > 200000) {
+        status = NB_E_TIMEOUT;
+        break;
+      }
+      if (sp) {  // the H/2 attempt ran already: take its outcome
+        ++attempts;
+        tally.derivs += sderivs;
+        if (s_flags[2]) {
+          acc = 1;
+          kacc = s_flags[3];
+          Hacc = 0.5 * H;
+          for (int b = tid; b < M; b += NT) {
+            const double* Tc = cs.base + (size_t)b * c.stride + offT + (kacc & 1) * kmax * 6 +
+                               6 * (kacc - 1);
+            double* y = c.base + (size_t)b * c.stride + OY;
+            for (int k = 0; k < 6; ++k) y[k] = Tc[k];
+          }
+          sy.sync();
+        } else {
+          ++tally.halvings;
+          if (level >= P.bs_max_halvings) {
+            status = NB_E_NOCONV;
+            break;
+          }
+          ++level;
+          done *= 2;
+        }
+      }
+    }
     if (acc) {
       ++done;
       ++tally.substeps;
       if (rec) {
         if (tid == 0) {
           if (rec_n < rec->cap) {
-            rec->H[rec_n] = H;
+            rec->H[rec_n] = Hacc;
             rec->k[rec_n] = kacc;
           } else {
             rec->counts[2] = 1;
@@ -365,14 +554,6 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
         --level;
         done >>= 1;
       }
-    } else {
-      ++tally.halvings;
-      if (level >= P.bs_max_halvings) {
-        status = NB_E_NOCONV;
-        break;
-      }
-      ++level;
-      done *= 2;
     }
     if (attempts > 200000) {
       status = NB_E_TIMEOUT;

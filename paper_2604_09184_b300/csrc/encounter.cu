@@ -466,7 +466,7 @@ template <bool ML>
 __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
   __shared__ int s_stop, s_ng;
   __shared__ double s_red[BNT];
-  __shared__ int s_flags[2];
+  __shared__ int s_flags[4];
   __shared__ int s_int[2];
   if (threadIdx.x == 0) {
     s_stop = d.ctrl->status;
@@ -479,7 +479,7 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
     // small groups: one per warp, with warp barriers only; the group's scratch
     // (kWarpGroupMax slots of bs_stride doubles per warp) in dynamic shared
     // memory (the CTA's other groups keep theirs in gscr)
-    __shared__ int s_wflags[BNT / 32][2];
+    __shared__ int s_wflags[BNT / 32][4];
     extern __shared__ double s_bscr[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTeam wt{s_wflags[warp]};
@@ -512,7 +512,11 @@ __global__ void __maxnreg__(128) k_bs_t(Dev d, Phys P, double h) {
       }
       __syncwarp();
       double El = 0.0;
-      const int status = bs_integrate(c, P, h, wt, tally, &El, (BsRec*)nullptr);
+      // groups of up to 4 bodies speculate on the half-size attempt in the
+      // warp's spare slots and lanes
+      double* spec =
+          P.bs_speculate && 2 * M <= kWarpGroupMax ? c.base + (size_t)M * c.stride : nullptr;
+      const int status = bs_integrate(c, P, h, wt, tally, &El, (BsRec*)nullptr, spec);
       if (status && lane == 0) set_status(d.ctrl, status, 30);
       for (int b = lane; b < M; b += 32) {
         const double* y = c.base + (size_t)b * c.stride + OY;
@@ -644,7 +648,7 @@ struct ClusterTeam {
 __global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int min_m) {
   __shared__ double s_red[CNT];
   __shared__ double s_slot_own[CCL_MAX];
-  __shared__ int s_flags_own[2];
+  __shared__ int s_flags_own[4];
   __shared__ int s_ctl[2];
   cg::cluster_group cl = cg::this_cluster();
   // the cluster's first CTA reads the control block once; every CTA takes

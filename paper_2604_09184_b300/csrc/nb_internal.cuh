@@ -107,7 +107,7 @@ struct Dev {
 struct Phys {
   double G, m0, mu, dt_rcrit, hill_factor, vel_factor, bs_tol;
   int vel_mode, merge, precision, kepler_max_iter, bs_kmax, bs_max_halvings, rcrit_refresh;
-  int gas, gas_iter, bs_cluster_min, ml_levels, ml_factor;
+  int gas, gas_iter, bs_cluster_min, ml_levels, ml_factor, bs_speculate;
   double gas_rho0, gas_p, gas_eta, gas_cd, eject_r;
 };
 

@@ -43,7 +43,7 @@ class NbParams(C.Structure):
         ("gas", C.c_int), ("gas_rho0", C.c_double), ("gas_p", C.c_double),
         ("gas_eta", C.c_double), ("gas_cd", C.c_double), ("gas_iter", C.c_int),
         ("eject_r", C.c_double), ("bs_cluster_min", C.c_int), ("ml_levels", C.c_int),
-        ("ml_factor", C.c_int),
+        ("ml_factor", C.c_int), ("bs_speculate", C.c_int),
     ]
 
 

@@ -249,3 +249,21 @@ def test_adjoint_rejects_bad_requests():
         a.forward(d.dt, nsteps=40)  # more steps than the checkpoints were sized for
     with pytest.raises(nb.NbError):
         a.backward(np.zeros((16, 3)), np.zeros((16, 3)), np.zeros(16))  # no forward yet
+
+
+def test_speculative_half_steps_do_not_change_the_gradient():
+    """The direct solver's speculative half-size attempts (bs_speculate) change
+    no bit of the forward state or of the gradient: mergers, encounters and
+    halvings on the 24-body merging disk, 60 steps."""
+    d = ics.make_disk(24, 2.0, 0.97, 1.03, 0.01, 0.005, 6.0, seed=12, f_radius=300.0)
+    p, rc = with_rc(d, merge=1)
+    gx, gv, gm = cotangents(d.n, 4)
+    out = {}
+    for sp in (0, 1):
+        a, g = adjoint_grad(d, rc, 60, 20, gx, gv, gm, merge=1, bs_speculate=sp)
+        out[sp] = (a.state(), g)
+    (s0, g0), (s1, g1) = out[0], out[1]
+    for k in ("x", "v", "m"):
+        assert np.array_equal(s0[k], s1[k]), k
+    for a0, a1 in zip(g0, g1):
+        assert np.array_equal(a0, a1)

@@ -684,4 +684,34 @@ def test_random_configurations_match_oracle(case):
     compare_states(ref, gpu)
     assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
     sr, sg = ref.stats(), gpu.stats()
-    assert sr["merges"] == sg["merges"] and sr["groups"] == sg["groups"]
+    for k in ("merges", "groups", "bs_substeps", "bs_halvings"):
+        assert sr[k] == sg[k], (k, sr[k], sg[k])
+
+
+@pytest.mark.parametrize("workload", ["merging_toy", "adjoint_2k_j"])
+def test_speculative_half_steps_are_bit_identical(workload):
+    """bs_speculate = 1 (the default: groups of up to 4 bodies on one warp also
+    integrate the half-size attempt a failure leads to) against attempts one
+    after the other: identical states, encounter lists and every counter of
+    the direct solver (derivatives, substeps, halvings, mergers)."""
+    nb = nbmod()
+    if workload == "merging_toy":
+        d = ics.workload("toy_disk_256", f_radius=400.0)
+        steps = 60
+    else:
+        d = ics.workload(workload)
+        steps = 40
+    rc = oracle_rc(d)
+    runs = []
+    for sp in (0, 1):
+        g = nb.NBodySystem(nb.params(dt_rcrit=d.dt, bs_speculate=sp), d.x, d.v, d.m, d.R, rc=rc)
+        g.step(steps, d.dt)
+        runs.append(g)
+    a, b = runs[0].state(), runs[1].state()
+    for k in ("ids", "x", "v", "m"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(runs[0].encounter_list(), runs[1].encounter_list())
+    sa, sb = runs[0].stats(), runs[1].stats()
+    for k in ("groups", "bs_derivs", "bs_substeps", "bs_halvings", "merges"):
+        assert sa[k] == sb[k], (k, sa[k], sb[k])
+    assert sa["bs_halvings"] > 0
