@@ -39,10 +39,13 @@ struct BatchDev {
   unsigned long long* stats;
   unsigned long long* cta_ns;  // per CTA of the last launch: ns from its start to its exit
   int cta_cap;
+  double* spec;  // kSpecWarps x 4 slots x bs_stride: speculative-attempt scratch per warp
+  int spec_cap;  // warps with a spec block (blockIdx.x * warps per CTA + warp < spec_cap)
   const long long* budget_ns;  // per-launch time budget of a CTA in ns (0: none)
 };
 
 constexpr int kCtaCap = 4096;
+constexpr int kSpecWarps = 148 * 64;  // resident warps of a full B300 (64 per SM)
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -60,12 +63,12 @@ struct BSmem {
   unsigned *fp, *ft, *e;  // F_prev, F_trial (BPAIR each), E keys (2 BPAIR)
   int *uf, *goff, *gmem, *gidx;
   int* ints;  // [0] nFp [1] nFt [2] nE [3] ngroups [4] overflow [6..7] bs flags;
-              // [16 + 2w ..] flags of warp w (warp-team groups), [8] error of a warp team
+              // [16 + 4w ..] flags of warp w (warp-team groups), [8] error of a warp team
 };
 
 __host__ __device__ inline size_t batch_smem_bytes(int nmax, int NT) {
   return (size_t)19 * nmax * 8 + (size_t)(99 + NT) * 8 + (size_t)nmax * 4 +
-         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + (16 + 2 * 32) * 4;
+         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + (16 + 4 * 32) * 4;
 }
 
 __device__ inline BSmem carve_smem(char* base, int nmax, int NT) {
@@ -328,7 +331,7 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
       // work item is the same on both teams.
       {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        WarpTeam wt{&s.ints[16 + 2 * warp]};
+        WarpTeam wt{&s.ints[16 + 4 * warp]};
         if (threadIdx.x == 0) s.ints[8] = 0;
         if (lane == 0) s.bred[warp] = 0.0;  // this warp's energy removed by mergers
         __syncthreads();
@@ -357,7 +360,13 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
           }
           __syncwarp();
           double El = 0.0;
-          const int stb = bs_integrate(c, P, h, wt, wbt, &El, (BsRec*)nullptr);
+          // groups of up to 4 bodies speculate on the half-size attempt (their
+          // warp's block of 4 scratch slots, the warp's spare lanes)
+          const int gw = blockIdx.x * nw + warp;
+          double* spec = (P.bs_speculate && 2 * M <= 8 && gw < B.spec_cap)
+                             ? B.spec + (size_t)gw * 4 * B.bs_stride
+                             : nullptr;
+          const int stb = bs_integrate(c, P, h, wt, wbt, &El, (BsRec*)nullptr, spec);
           if (lane == 0) {
             s.bred[warp] += El;
             if (stb) atomicCAS(&s.ints[8], 0, stb);
@@ -661,6 +670,8 @@ size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDe
   d.cta_ns = c.take<unsigned long long>(kCtaCap);
   d.cta_cap = kCtaCap;
   d.budget_ns = c.take<long long>(1);
+  d.spec = c.take<double>((size_t)kSpecWarps * 4 * d.bs_stride);
+  d.spec_cap = kSpecWarps;
   Snap s;
   s.arrays = c.take<double>((size_t)12 * total);
   s.alive = c.take<int>(total);
@@ -715,6 +726,7 @@ Phys phys_of(const nb_params& p) {
   P.kepler_max_iter = p.kepler_max_iter;
   P.bs_kmax = p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
   P.bs_max_halvings = p.bs_max_halvings > 40 ? 40 : p.bs_max_halvings;
+  P.bs_speculate = p.bs_speculate;
   return P;
 }
 

@@ -181,3 +181,22 @@ def test_batch_load_balance_report():
     bal = b.balance()
     assert bal["ctas"] >= 1 and bal["max_cta_ms"] > 0
     assert 0.0 < bal["efficiency"] <= 1.0
+
+
+def test_batch_speculative_half_steps_are_bit_identical():
+    """bs_speculate on (default) and off: identical states and direct-solver
+    counters on systems with encounters, halvings and mergers."""
+    disks = [ics.make_disk(n, 2.0, 0.7, 1.3, 0.01, 0.005, 6.0, seed=900 + n, f_radius=400.0)
+             for n in (64, 128, 200)] + ics.ensemble(n_systems=16, seed=ics.SEED_BASE + 35)
+    dt, steps = 6.0, 40
+    out = []
+    for sp in (0, 1):
+        b = batch_of(disks, dt, bs_speculate=sp)
+        b.step(steps, dt)
+        out.append((b.state(), b.stats()))
+    (s0, t0), (s1, t1) = out
+    for k in s0:
+        assert np.array_equal(np.asarray(s0[k]), np.asarray(s1[k])), k
+    for k in ("groups", "bs_derivs", "bs_substeps", "bs_halvings", "merges"):
+        assert t0[k] == t1[k], (k, t0[k], t1[k])
+    assert t0["bs_halvings"] > 0 and t0["merges"] > 0
