@@ -38,7 +38,7 @@ METRIC = "pair interactions/s & steps/s at N=65536 (FP64, % peak); mixed vs FP64
 UNIT = "pair interactions/s"
 WORKLOAD = "mmsn_64k_js"
 FLOP_PER_PAIR = 20        # direct-summation convention (Nyland, Harris & Prins 2007)
-FP64_INSTR_PER_PAIR = 13  # FP64 instructions in the kick's pair loop (FP64 mode)
+FP64_INSTR_PER_PAIR = 10  # FP64 instructions in the kick's pair loop (FP64 mode)
 
 
 def parse():

@@ -148,10 +148,18 @@ __global__ void __launch_bounds__(VNT) k_kick_vjp(Vjp V) {
     const int cnt = min(VNT, j1 - jt);
     for (int q = 0; q < cnt; ++q) {
       const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
-      const double r2 = sep2(dx, dy, dz);
-      if (__double_as_longlong(r2) == 0ll) continue;  // the target itself (and coincident bodies)
+      // r^2 on the integer pipe; a pair within one high-word unit of its
+      // threshold, or coincident, is decided on the FP64 expression (as the
+      // forward kick decides it)
+      double r2 = sep2_int(dx, dy, dz);
+      bool inside = false;
+      if (__double2hiint(r2) <= max(__double2hiint(rck2), __double2hiint(src2[q])) + 1) {
+        r2 = sep2(dx, dy, dz);
+        if (__double_as_longlong(r2) == 0ll) continue;  // the target itself (and coincident bodies)
+        inside = nn_less(r2, rck2) || nn_less(r2, src2[q]);
+      }
       double p, dp_r;
-      if (!(nn_less(r2, rck2) || nn_less(r2, src2[q]))) {
+      if (!inside) {
         const double ri = rinv_fast(r2);
         const double ir2 = ri * ri;
         p = ri * ir2;

@@ -143,10 +143,11 @@ __device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* 
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int j = 0; j < n; ++j) {
       const double dx = s.x[j] - xi, dy = s.y[j] - yi, dz = s.z[j] - zi;
-      const double r2 = sep2(dx, dy, dz);
+      double r2 = sep2_int(dx, dy, dz);
       const double mj = s.m[j];
       double sc = scale_fast<NB_PREC_FP64>(r2, mj);
-      if (__double2hiint(r2) <= max(hi, __double2hiint(s.rc2[j]))) {
+      if (__double2hiint(r2) <= max(hi, __double2hiint(s.rc2[j])) + 1) {
+        r2 = sep2(dx, dy, dz);  // flags and weights from the FP64 expression
         const double rc2 = fmax(rc2i, s.rc2[j]);
         const bool close = (r2 < rc2) && s.alive[j] && (j != i);
         if (close && i < j) {

@@ -89,7 +89,7 @@ static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
   fb[0] = yb[3];
   fb[1] = yb[4];
   fb[2] = yb[5];
-  const double r2 = __fma_rn(yb[2], yb[2], __fma_rn(yb[1], yb[1], yb[0] * yb[0]));
+  const double r2 = sep2_int(yb[0], yb[1], yb[2]);  // r^2 on the integer pipe
   const double ks = -scale_fast<NB_PREC_FP64>(r2, c.mu, c.mu15, c.mu1875);  // -mu / r^3
   double ax = ks * yb[0], ay = ks * yb[1], az = ks * yb[2];
   const double* ab = bs_aux(c, b);
@@ -97,7 +97,7 @@ static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
     if (q == b || !bs_alive(c, q)) continue;
     const double* yq = c.base + (size_t)q * c.stride + fo;
     const double dx = yq[0] - yb[0], dy = yq[1] - yb[1], dz = yq[2] - yb[2];
-    const double q2 = sep2(dx, dy, dz);
+    const double q2 = sep2_int(dx, dy, dz);
     if (__double_as_longlong(q2) == 0ll) continue;
     const double* aq = bs_aux(c, q);
     if (!(nn_less(q2, ab[2]) || nn_less(q2, aq[2]))) continue;  // 1 - w = 0 beyond rc

@@ -6,19 +6,22 @@
 // B300 design: the FP64 pipe issues ~1/60 of the FP32 rate, so the pair loop
 // spends as few FP64 instructions as it can and moves everything else to the
 // INT/FP32/MUFU pipes:
-//   - dx, dy, dz, r^2, the r^-3 refinement and the three accumulations are
-//     FP64 (13 FP64 instructions per pair in the FP64 mode, 12 in the mixed
-//     mode);
+//   - dx, dy, dz, the r^-3 refinement and the three accumulations are FP64
+//     (10 FP64 instructions per pair in the FP64 mode, 9 in the mixed mode);
+//     r^2 is formed on the integer pipe from the significands of dx, dy, dz
+//     (sep2_int: 64 x 64-bit high products, aligned sum, rounding), within an
+//     ulp of the exact value;
 //   - the r^-3 seed is rsqrtf of a float built from r^2's high word with one
 //     integer shift-add; its square (exact) and cube (rounded) are built as
 //     doubles from integer products of its significand (no F2F conversions,
 //     no FP64 multiplies), and the source mass enters the refinement
 //     polynomial through m, 1.5 m and 1.875 m staged with the j-tile;
 //   - the encounter test first compares the high words of r^2 and
-//     max(rc_i^2, rc_j^2) as integers (IEEE order of non-negative doubles);
-//     only a tie or a close pair takes the exact FP64 branch, which computes
-//     the changeover weight and appends the flagged pair with one atomic per
-//     warp (ballot + popc).
+//     max(rc_i^2, rc_j^2) as integers (IEEE order of non-negative doubles),
+//     with one unit of slack for the integer r^2; only a near-tie or a close
+//     pair takes the exact FP64 branch, which recomputes r^2 in the fixed FP64
+//     rounding of the flags, computes the changeover weight and appends the
+//     flagged pair with one atomic per warp (ballot + popc).
 // j-tiles of 128 bodies are staged through shared memory; each thread owns two
 // targets; a CTA covers 256 targets x one j-chunk, and the j-chunks' partial
 // sums are added in a fixed order by k_finish (deterministic results).
@@ -147,10 +150,13 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
 #pragma unroll
       for (int k = 0; k < KIPT; ++k) {
         const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
-        const double r2 = sep2(dx, dy, dz);
+        // r^2 on the integer pipe (within an ulp); a pair whose high word is
+        // within one unit of the threshold's takes the exact branch, which
+        // decides the flag and the weight from the FP64 expression sep2
+        const double r2 = sep2_int(dx, dy, dz);
         double sc = scale_fast<PREC>(r2, mj, mj15, mj1875);
-        if (__double2hiint(r2) <= max(hi[k], hj))
-          sc = rare_pair<true>(r2, sc, mj, ii[k], jt + q, rc2i[k], rci[k], A);
+        if (__double2hiint(r2) <= max(hi[k], hj) + 1)
+          sc = rare_pair<true>(sep2(dx, dy, dz), sc, mj, ii[k], jt + q, rc2i[k], rci[k], A);
         if (PREC == NB_PREC_FP64) {
           ax[k] = __fma_rn(sc, dx, ax[k]);
           ay[k] = __fma_rn(sc, dy, ay[k]);
@@ -425,11 +431,17 @@ constexpr int FNT = 256;
 // m_j w / r^3 as the kick computes it: the seeded reciprocal root beyond
 // rc_ij (m_j with 1.5 m_j and 1.875 m_j), the exact changeover weight inside,
 // 0 for coincident bodies; the range test compares bit patterns.
-__device__ __forceinline__ double finish_scale(double r2, const double* sj, int k, double rci,
-                                               double rc2i) {
+__device__ __forceinline__ double finish_scale(double dx, double dy, double dz, const double* sj,
+                                               int k, double rci, double rc2i) {
   const double mj = sj[3 * FNT + k];
-  if ((nn_less(r2, rc2i) || nn_less(r2, sj[5 * FNT + k])) || __double_as_longlong(r2) == 0ll)
-    return pair_scale(r2, mj, rci, sj[4 * FNT + k]);
+  const double r2 = sep2_int(dx, dy, dz);
+  // near or inside rc (one high-word unit of slack for the integer r^2), or
+  // coincident: the kick's exact branch, decided on the FP64 expression
+  if (__double2hiint(r2) <= max(__double2hiint(rc2i), __double2hiint(sj[5 * FNT + k])) + 1) {
+    const double r2x = sep2(dx, dy, dz);
+    if (nn_less(r2x, rc2i) || nn_less(r2x, sj[5 * FNT + k]) || __double_as_longlong(r2x) == 0ll)
+      return pair_scale(r2x, mj, rci, sj[4 * FNT + k]);
+  }
   return scale_fast<NB_PREC_FP64>(r2, mj, sj[6 * FNT + k], sj[7 * FNT + k]);
 }
 
@@ -496,10 +508,10 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
         // seeded reciprocal root beyond rc, the exact weight inside), then
         // the term at the member's new state
         double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
-        double s = finish_scale(sep2(dx, dy, dz), &so[0][0], k, rci, rc2i);
+        double s = finish_scale(dx, dy, dz, &so[0][0], k, rci, rc2i);
         cx -= s * dx; cy -= s * dy; cz -= s * dz;
         dx = snw[0][k] - xi; dy = snw[1][k] - yi; dz = snw[2][k] - zi;
-        s = finish_scale(sep2(dx, dy, dz), &snw[0][0], k, rci, rc2i);
+        s = finish_scale(dx, dy, dz, &snw[0][0], k, rci, rc2i);
         cx += s * dx; cy += s * dy; cz += s * dz;
       }
     }
@@ -573,10 +585,12 @@ __global__ void __launch_bounds__(MNT) k_member_kick(Dev d, double G) {
       for (int j = threadIdx.x; j < n; j += MNT) {
         const double dx = d.x[j] - xb, dy = d.y[j] - yb, dz = d.z[j] - zb;
         const double mj = d.m[j];
-        const double r2 = sep2(dx, dy, dz);
+        double r2 = sep2_int(dx, dy, dz);
         double sc = scale_fast<NB_PREC_FP64>(r2, mj);
-        if (__double2hiint(r2) <= max(hb, __double2hiint(d.rc2[j]))) {
-          // flag from the member side: (b, j) when j is not a member or b < j
+        if (__double2hiint(r2) <= max(hb, __double2hiint(d.rc2[j])) + 1) {
+          // flag from the member side: (b, j) when j is not a member or b < j;
+          // decided on the FP64 expression of r^2, as in the kick
+          r2 = sep2(dx, dy, dz);
           double s = sc;
           const double rc2 = fmax(rc2b, d.rc2[j]);
           const bool close = (r2 < rc2) && d.alive[j] && (j != b);

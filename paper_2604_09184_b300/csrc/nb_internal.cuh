@@ -360,6 +360,60 @@ __device__ __forceinline__ double sep2(double dx, double dy, double dz) {
   return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
 }
 
+// r^2 = dx^2 + dy^2 + dz^2 by integer arithmetic, rounded to nearest from a
+// sum exact to ~2^-60 relative (at most one ulp from the exact value; sep2
+// may differ from it by an ulp): each significand, normalised to 64 bits, is
+// squared to its top 64 bits (a 64 x 64 -> 128-bit high product), the three
+// are aligned to the largest and added, and the sum is rounded to 53 bits.
+// No FP64 instruction; zero and subnormal components count as zero; 0 for
+// coincident bodies; components below 2^500 in size. Host-callable so that it
+// can be checked on the CPU.
+__host__ __device__ __forceinline__ unsigned long long nb_umulhi64(unsigned long long a,
+                                                                  unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long nb_dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &v, 8);
+  return b;
+#endif
+}
+// top 64 bits of the square of |v|'s significand and 2 x v's exponent field
+__host__ __device__ __forceinline__ unsigned long long sq_top(double v, int& key) {
+  const unsigned long long b = nb_dbits(v);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long mn = ((b << 11) | 0x8000000000000000ull);
+  key = ex == 0 ? -4096 : 2 * ex;
+  return ex == 0 ? 0ull : nb_umulhi64(mn, mn);  // [2^62, 2^64)
+}
+__host__ __device__ __forceinline__ double sep2_int(double dx, double dy, double dz) {
+  int kx, ky, kz;
+  const unsigned long long qx = sq_top(dx, kx), qy = sq_top(dy, ky), qz = sq_top(dz, kz);
+  const int K = kx > ky ? (kx > kz ? kx : kz) : (ky > kz ? ky : kz);
+  // value of q with key k: q 2^(k - 2108); aligned to K with 2 bits of headroom
+  const int sx = K - kx + 2, sy = K - ky + 2, sz = K - kz + 2;
+  const unsigned long long S = (sx < 64 ? qx >> sx : 0ull) + (sy < 64 ? qy >> sy : 0ull) +
+                               (sz < 64 ? qz >> sz : 0ull);  // r^2 = S 2^(K - 2106)
+  if (S == 0ull) return 0.0;
+  const int L = 63 - nb_clzll(S);  // >= 60 (the largest term is >= 2^60)
+  const unsigned long long Q = (S + (1ull << (L - 53))) >> (L - 52);
+  const unsigned long long bits = Q + ((unsigned long long)(L + K - 1084) << 52);
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double r;
+  __builtin_memcpy(&r, &bits, 8);
+  return r;
+#endif
+}
+
 // m_j w / r^3 for one pair with full-precision r (used off the hot loop).
 // w = 1 when r^2 >= rc^2 with rc = max(rc_i, rc_j); 0 for coincident bodies.
 __device__ __forceinline__ double pair_scale(double r2, double mj, double rci, double rcj) {

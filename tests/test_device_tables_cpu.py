@@ -87,3 +87,53 @@ int main() {
     assert r.returncode == 0, r.stderr[-2000:]
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "0", out.stdout + out.stderr
+
+
+def test_sep2_int_against_long_double(tmp_path):
+    """The integer-arithmetic r^2 of the kick's pair loop (host-callable, the
+    same code): within half an ulp plus 2^-58 relative of the sum computed in
+    long double (64-bit significands) for components spread over 2^-60..2^20,
+    with zeros, signs and near-cancelling magnitudes."""
+    nvcc = "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "r2.cu"
+    src.write_text(r"""
+#include "nb_internal.cuh"
+#include <cstdio>
+#include <cmath>
+int main() {
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return st; };
+  long bad = 0;
+  for (long it = 0; it < 3000000; ++it) {
+    double c[3];
+    const int e0 = (int)(rnd() % 81) - 60;
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long r = rnd();
+      const int mode = (int)(r % 8);
+      double v = ldexp(1.0 + (double)(rnd() >> 12) * 0x1p-52, e0 - (int)(rnd() % (mode < 4 ? 4 : 70)));
+      if (mode == 7) v = 0.0;
+      c[k] = (r & 256) ? -v : v;
+    }
+    const double got = nb::sep2_int(c[0], c[1], c[2]);
+    long double ex = (long double)c[0] * c[0] + (long double)c[1] * c[1] + (long double)c[2] * c[2];
+    if (ex == 0.0L) { if (got != 0.0) ++bad; continue; }
+    const long double ulp = (long double)(nextafter((double)ex, INFINITY) - (double)ex);
+    const long double err = fabsl((long double)got - ex);
+    if (err > 0.5L * ulp + ldexpl(ex, -58)) {
+      if (bad < 5) printf("bad %.20Lg %.20g\n", ex, got);
+      ++bad;
+    }
+  }
+  printf("%ld\n", bad);
+  return bad != 0;
+}
+""")
+    exe = tmp_path / "r2"
+    r = subprocess.run([nvcc, "-O2", "-std=c++17", "-I" + os.path.dirname(HDR),
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip().endswith("0"), out.stdout + out.stderr
