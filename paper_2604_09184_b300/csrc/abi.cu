@@ -25,10 +25,11 @@ int round_pow2(int v) {
 }
 
 int auto_split(int n) {
-  // About 48 kick CTAs per SM over the launch (4 are resident at a time), so
-  // the last partial wave is a small fraction of the kernel; measured at
-  // N = 65538 this is 4 % faster (FP64) and 14 % faster (double-single) than
-  // ~8 per SM. Whole 128-body j-tiles per chunk, at most 64 chunks.
+  // About 48 kick CTAs per SM over the launch for 256-target tiles (96 for
+  // the FP64 kernel's 128-target tiles), so the last partial wave is a small
+  // fraction of the kernel; measured at N = 65538 this was 4 % faster (FP64)
+  // and 14 % faster (double-single) than ~8 per SM. Whole 128-body j-tiles per
+  // chunk, at most 64 chunks.
   const int itiles = (n + 255) / 256;
   int S = (148 * 48 + itiles - 1) / itiles;
   const int maxS = (n + 127) / 128;

@@ -6,11 +6,13 @@
 // B300 design: the FP64 pipe issues ~1/60 of the FP32 rate, so the pair loop
 // spends as few FP64 instructions as it can and moves everything else to the
 // INT/FP32/MUFU pipes:
-//   - dx, dy, dz, the r^-3 refinement and the three accumulations are FP64
-//     (10 FP64 instructions per pair in the FP64 mode, 9 in the mixed mode);
-//     r^2 is formed on the integer pipe from the significands of dx, dy, dz
-//     (sep2_int: 64 x 64-bit high products, aligned sum, rounding), within an
-//     ulp of the exact value;
+//   - the r^-3 refinement and the three accumulations are FP64 (7 FP64
+//     instructions per pair in the FP64 mode, 6 in the mixed mode);
+//   - dx, dy, dz come from positions held as 128-bit fixed-point integers
+//     (fix_of: exact for 2^-36 <= |x| < 2^38 AU): their difference is exact
+//     and is rounded to a double by integer ops (fix_diff), which also give
+//     the top 64 bits of its square, so r^2 is an aligned integer sum rounded
+//     once (sep2_fix, within an ulp of the exact value);
 //   - the r^-3 seed is rsqrtf of a float built from r^2's high word with one
 //     integer shift-add; its square (exact) and cube (rounded) are built as
 //     doubles from integer products of its significand (no F2F conversions,
@@ -19,18 +21,23 @@
 //   - the encounter test first compares the high words of r^2 and
 //     max(rc_i^2, rc_j^2) as integers (IEEE order of non-negative doubles),
 //     with one unit of slack for the integer r^2; only a near-tie or a close
-//     pair takes the exact FP64 branch, which recomputes r^2 in the fixed FP64
-//     rounding of the flags, computes the changeover weight and appends the
-//     flagged pair with one atomic per warp (ballot + popc).
-// j-tiles of 128 bodies are staged through shared memory; each thread owns two
-// targets; a CTA covers 256 targets x one j-chunk, and the j-chunks' partial
-// sums are added in a fixed order by k_finish (deterministic results).
+//     pair takes the exact FP64 branch, which forms dx, dy, dz and r^2 in the
+//     FP64 subtractions and fixed rounding that decide the flags, computes the
+//     changeover weight and appends the flagged pair with one atomic per warp
+//     (ballot + popc).
+// j-tiles of 128 bodies (fixed-point positions, m, 1.5 m, 1.875 m) are staged
+// through shared memory; each thread owns one target (the integer arithmetic
+// takes registers: 80 per thread, 6 CTAs per SM); a CTA covers 128 targets x
+// one j-chunk, and the j-chunks' partial sums are added in a fixed order by
+// k_finish (deterministic results). The double-single kernel keeps two
+// targets per thread (256 per CTA).
 #include "nb_internal.cuh"
 
 namespace nb {
 
 constexpr int KNT = 128;  // threads per kick CTA (= j-tile size)
-constexpr int KIPT = 2;   // targets per thread
+constexpr int KIPT = 1;   // targets per thread (the integer pair arithmetic needs registers:
+                          // one target, 80 registers, 6 CTAs per SM)
 #ifndef NB_KICK_UNROLL
 #define NB_KICK_UNROLL 4
 #endif
@@ -87,8 +94,9 @@ __device__ __forceinline__ double rare_pair(double r2, double sc, double mj, int
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
-  __shared__ double sx[KNT], sy[KNT], sz[KNT], sm[KNT], sm15[KNT], sm1875[KNT];
+__global__ void __launch_bounds__(KNT, 6) k_kick(KickArgs A) {
+  __shared__ nb_u128 sX[KNT], sY[KNT], sZ[KNT];  // fixed-point positions of the j-tile
+  __shared__ double sm[KNT], sm15[KNT], sm1875[KNT];
   __shared__ int sh[KNT];
   __shared__ int s_stop;
   if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
@@ -99,7 +107,8 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
   const int sidx = blockIdx.x - it * A.S;
   const int i0 = A.ib + it * (KNT * KIPT) + threadIdx.x;
 
-  double xi[KIPT], yi[KIPT], zi[KIPT], rc2i[KIPT], rci[KIPT];
+  nb_u128 Xi[KIPT], Yi[KIPT], Zi[KIPT];
+  double rc2i[KIPT], rci[KIPT];
   double ax[KIPT], ay[KIPT], az[KIPT];
   double cx[KIPT], cy[KIPT], cz[KIPT];  // compensation (mixed mode)
   int hi[KIPT], ii[KIPT];
@@ -108,13 +117,13 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
     const int i = i0 + k * KNT;
     ii[k] = i;
     if (i < A.ie) {
-      xi[k] = A.x[i];
-      yi[k] = A.y[i];
-      zi[k] = A.z[i];
+      Xi[k] = fix_of(A.x[i]);
+      Yi[k] = fix_of(A.y[i]);
+      Zi[k] = fix_of(A.z[i]);
       rc2i[k] = A.rc2[i];
       rci[k] = A.rc[i];
     } else {  // padding target far from everything, never flagged
-      xi[k] = yi[k] = zi[k] = 1e10;
+      Xi[k] = Yi[k] = Zi[k] = fix_of(1e10);
       rc2i[k] = 0.0;
       rci[k] = 0.0;
     }
@@ -128,9 +137,9 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
     __syncthreads();
     const int j = jt + threadIdx.x;
     if (j < j1) {
-      sx[threadIdx.x] = A.x[j];
-      sy[threadIdx.x] = A.y[j];
-      sz[threadIdx.x] = A.z[j];
+      sX[threadIdx.x] = fix_of(A.x[j]);
+      sY[threadIdx.x] = fix_of(A.y[j]);
+      sZ[threadIdx.x] = fix_of(A.z[j]);
       const double mj = A.m[j];
       sm[threadIdx.x] = mj;
       sm15[threadIdx.x] = 1.5 * mj;
@@ -144,19 +153,27 @@ __global__ void __launch_bounds__(KNT) k_kick(KickArgs A) {
     for (int k = 0; k < KIPT; ++k) tx[k] = ty[k] = tz[k] = 0.0;
 #pragma unroll kKickUnroll
     for (int q = 0; q < cnt; ++q) {
-      const double xj = sx[q], yj = sy[q], zj = sz[q], mj = sm[q];
+      const nb_u128 Xj = sX[q], Yj = sY[q], Zj = sZ[q];
+      const double mj = sm[q];
       const double mj15 = sm15[q], mj1875 = PREC == NB_PREC_FP64 ? sm1875[q] : 0.0;
       const int hj = sh[q];
 #pragma unroll
       for (int k = 0; k < KIPT; ++k) {
-        const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
-        // r^2 on the integer pipe (within an ulp); a pair whose high word is
+        // dx, dy, dz and r^2 on the integer pipe (exact differences of the
+        // fixed-point positions, rounded); a pair whose r^2 high word is
         // within one unit of the threshold's takes the exact branch, which
-        // decides the flag and the weight from the FP64 expression sep2
-        const double r2 = sep2_int(dx, dy, dz);
+        // decides the flag and the weight from the FP64 subtractions and sep2
+        const FixDiff fx = fix_diff(Xj, Xi[k]), fy = fix_diff(Yj, Yi[k]), fz = fix_diff(Zj, Zi[k]);
+        const double dx = fx.d, dy = fy.d, dz = fz.d;
+        const double r2 = sep2_fix(fx, fy, fz);
         double sc = scale_fast<PREC>(r2, mj, mj15, mj1875);
-        if (__double2hiint(r2) <= max(hi[k], hj) + 1)
-          sc = rare_pair<true>(sep2(dx, dy, dz), sc, mj, ii[k], jt + q, rc2i[k], rci[k], A);
+        if (__double2hiint(r2) <= max(hi[k], hj) + 1) {
+          const int i = ii[k] < A.ie ? ii[k] : A.ie - 1, j = jt + q;
+          const double ex = __ldg(A.x + j) - __ldg(A.x + i), ey = __ldg(A.y + j) - __ldg(A.y + i),
+                       ez = __ldg(A.z + j) - __ldg(A.z + i);
+          sc = rare_pair<true>(ii[k] < A.ie ? sep2(ex, ey, ez) : 1e20, sc, mj, ii[k], j, rc2i[k],
+                               rci[k], A);
+        }
         if (PREC == NB_PREC_FP64) {
           ax[k] = __fma_rn(sc, dx, ax[k]);
           ay[k] = __fma_rn(sc, dy, ay[k]);
@@ -369,12 +386,16 @@ __global__ void __launch_bounds__(DNT2) k_kick_ds(KickArgs A) {
   }
 }
 
-int kick_blocks(int n, int S) { return ((n + KNT * KIPT - 1) / (KNT * KIPT)) * S; }
+// CTAs of a kick launch: target tiles (KNT KIPT targets, DNT2 DIPT for the
+// double-single kernel) x S j-chunks
+int kick_blocks(int n, int S, int precision) {
+  const int t = precision == NB_PREC_DS ? DNT2 * DIPT : KNT * KIPT;
+  return ((n + t - 1) / t) * S;
+}
 
 static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) {
-  const int grid = kick_blocks(A.ie - A.ib, A.S);
+  const int grid = kick_blocks(A.ie - A.ib, A.S, precision);
   if (grid <= 0) return;
-  static_assert(KNT * KIPT == DNT2 * DIPT, "kick variants share the i-tile size");
   if (precision == NB_PREC_MIXED)
     k_kick<NB_PREC_MIXED><<<grid, KNT, 0, st>>>(A);
   else if (precision == NB_PREC_DS)

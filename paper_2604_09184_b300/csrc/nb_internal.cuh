@@ -414,6 +414,77 @@ __host__ __device__ __forceinline__ double sep2_int(double dx, double dy, double
 #endif
 }
 
+// Positions as signed 128-bit fixed-point numbers X = x 2^88 (two's
+// complement in an unsigned __int128): exact for 2^-36 <= |x| < 2^38 AU,
+// truncated below (error < 2^-88 AU), saturated at 2^38 AU beyond (only
+// absorbed bodies, which have no mass and no changeover radius, can sit
+// there: at 1e6 (id + 1) AU, beyond 2^38 AU from id ~ 275 000).
+// The difference of two of them is exact, so the kick forms dx, dy, dz on the
+// integer pipe: fix_diff rounds X_j - X_i to a double (to nearest, ties
+// upward) and returns the top 64 bits of its square for sep2_fix.
+typedef unsigned __int128 nb_u128;
+__host__ __device__ __forceinline__ nb_u128 fix_of(double x) {
+  const unsigned long long b = nb_dbits(x);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  const nb_u128 m = (nb_u128)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = ex - 987;  // x = m 2^(ex - 1075) = m 2^(sh - 88)
+  nb_u128 mag = ex == 0 ? (nb_u128)0
+                        : (sh >= 0 ? (sh <= 73 ? m << sh : ((nb_u128)1 << 126))
+                                   : (sh > -53 ? m >> (-sh) : (nb_u128)0));
+  return (b >> 63) ? (nb_u128)0 - mag : mag;
+}
+struct FixDiff {
+  double d;               // X_j - X_i as a double
+  unsigned long long sq;  // top 64 bits of the square of the normalised magnitude
+  int key;                // 2 L, L the leading bit of the magnitude (-4096 for zero)
+};
+__host__ __device__ __forceinline__ FixDiff fix_diff(nb_u128 xj, nb_u128 xi) {
+  const nb_u128 dv = xj - xi;
+  const bool neg = (dv >> 127) != 0;
+  const nb_u128 mag = neg ? (nb_u128)0 - dv : dv;
+  const unsigned long long h = (unsigned long long)(mag >> 64), l = (unsigned long long)mag;
+  FixDiff r;
+  if ((h | l) == 0ull) {
+    r.d = 0.0;
+    r.sq = 0ull;
+    r.key = -4096;
+    return r;
+  }
+  const int L = h ? 127 - nb_clzll(h) : 63 - nb_clzll(l);
+  const unsigned long long N = (unsigned long long)((mag << (127 - L)) >> 64);  // bit 63 set
+  const unsigned long long Q = (N + (1ull << 10)) >> 11;  // 53 bits (2^53 on a carry)
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) + Q + ((unsigned long long)(L + 934) << 52);
+#ifdef __CUDA_ARCH__
+  r.d = __longlong_as_double((long long)bits);
+#else
+  __builtin_memcpy(&r.d, &bits, 8);
+#endif
+  r.sq = nb_umulhi64(N, N);  // [2^62, 2^64): d^2 = sq 2^(2L - 238)
+  r.key = 2 * L;
+  return r;
+}
+// r^2 from the three fix_diff squares (aligned sum rounded to 53 bits, as
+// in sep2_int): within half an ulp plus ~2^-58 of the exact value.
+__host__ __device__ __forceinline__ double sep2_fix(const FixDiff& a, const FixDiff& b,
+                                                   const FixDiff& c) {
+  const int K = a.key > b.key ? (a.key > c.key ? a.key : c.key) : (b.key > c.key ? b.key : c.key);
+  const int sa = K - a.key + 2, sb = K - b.key + 2, sc = K - c.key + 2;
+  const unsigned long long S = (sa < 64 ? a.sq >> sa : 0ull) + (sb < 64 ? b.sq >> sb : 0ull) +
+                               (sc < 64 ? c.sq >> sc : 0ull);  // r^2 = S 2^(K - 236)
+  if (S == 0ull) return 0.0;
+  const int L = 63 - nb_clzll(S);
+  const unsigned long long Q = (S + (1ull << (L - 53))) >> (L - 52);
+  const unsigned long long bits = Q + ((unsigned long long)(L + K + 786) << 52);
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double r;
+  __builtin_memcpy(&r, &bits, 8);
+  return r;
+#endif
+}
+
 // m_j w / r^3 for one pair with full-precision r (used off the hot loop).
 // w = 1 when r^2 >= rc^2 with rc = max(rc_i, rc_j); 0 for coincident bodies.
 __device__ __forceinline__ double pair_scale(double r2, double mj, double rci, double rcj) {
@@ -501,7 +572,7 @@ __device__ __forceinline__ void reduce_parts3(const double* parts, int nparts, d
 // ---------------------------------------------------------------------------
 // Host-side launchers (one per kernel family), defined in the .cu files.
 // ---------------------------------------------------------------------------
-int kick_blocks(int n, int S);
+int kick_blocks(int n, int S, int precision);
 int ppart_blocks(int n);
 void launch_kick(const Dev& d, const Phys& P, int target_sel, cudaStream_t st);
 void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, const double* z,

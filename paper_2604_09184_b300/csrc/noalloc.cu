@@ -63,7 +63,7 @@ extern "C" int nb_kick_noalloc(int n, const double* x, const double* m, const do
   const int st0 = scratch_address(&base);
   if (st0 != NB_OK) return st0;
   cudaStream_t st = (cudaStream_t)stream;
-  int S = kick_blocks(n, 1);  // i-tiles
+  int S = kick_blocks(n, 1, precision);  // target tiles
   S = (148 * 8 + S - 1) / S;
   if (S > kNoallocSplit) S = kNoallocSplit;
   if (S > (n + 127) / 128) S = (n + 127) / 128;

@@ -137,3 +137,79 @@ int main() {
     assert r.returncode == 0, r.stderr[-2000:]
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip().endswith("0"), out.stdout + out.stderr
+
+
+def test_fixed_point_differences(tmp_path):
+    """The kick's integer dx (128-bit fixed-point positions, exact difference,
+    rounded to a double): for coordinates in the exact range (2^-36..1e8 AU,
+    both signs, coincident and nearly coincident pairs) it equals the FP64
+    subtraction except on exact ties (rounded upward, so within half an ulp);
+    for smaller coordinates its error stays below 2^-87 AU plus half an ulp;
+    r^2 is within half an ulp plus 2^-57 of the long-double sum of the exact
+    differences."""
+    nvcc = "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "fx.cu"
+    src.write_text(r"""
+#include "nb_internal.cuh"
+#include <cstdio>
+#include <cmath>
+int main() {
+  unsigned long long st = 0x2545F4914F6CDD1Dull;
+  auto rnd = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return st; };
+  auto uni = [&]() { return (double)((rnd() >> 11) | 1ull) * 0x1p-53; };
+  long bad = 0, ties = 0, n = 0;
+  for (long it = 0; it < 2000000; ++it) {
+    const bool tiny = (it % 10) == 0;
+    double a[3], b[3];
+    for (int k = 0; k < 3; ++k) {
+      const int mode = (int)(rnd() % 6);
+      const double lo = tiny ? -16.0 : -10.8, span = tiny ? 8.0 : 18.8;  // log10 range
+      const double sa = pow(10.0, lo + span * uni()), sb = pow(10.0, lo + span * uni());
+      a[k] = (rnd() & 1 ? -1.0 : 1.0) * sa;
+      if (mode == 0) b[k] = a[k];                                        // coincident
+      else if (mode == 1) b[k] = a[k] * (1.0 + 1e-12 * (uni() - 0.5));   // nearly
+      else if (mode == 2) b[k] = -a[k];
+      else b[k] = (rnd() & 1 ? -1.0 : 1.0) * sb;
+    }
+    nb::FixDiff f[3];
+    long double ex = 0.0L;
+    for (int k = 0; k < 3; ++k) {
+      f[k] = nb::fix_diff(nb::fix_of(a[k]), nb::fix_of(b[k]));
+      const double want = a[k] - b[k];
+      const long double dl = (long double)a[k] - (long double)b[k];
+      ex += dl * dl;
+      if (tiny) {  // truncation of each coordinate (< 2^-88) plus the rounding of dx
+        const long double u = (long double)fabs(nextafter(want, INFINITY) - want);
+        if (fabsl((long double)f[k].d - dl) > ldexpl(1.0L, -87) + 0.5L * u) ++bad;
+        continue;
+      }
+      ++n;
+      if (f[k].d != want) {
+        const double u = fabs(nextafter(want, INFINITY) - want);
+        const long double err = fabsl((long double)f[k].d - dl);
+        if (err > 0.5L * u) { if (bad < 5) printf("dx %.17g %.17g: %.17g vs %.17g\n", a[k], b[k], f[k].d, want); ++bad; }
+        else ++ties;
+      }
+    }
+    const double r2 = nb::sep2_fix(f[0], f[1], f[2]);
+    if (ex == 0.0L) { if (r2 != 0.0) ++bad; continue; }
+    const long double ulp = (long double)(nextafter((double)ex, INFINITY) - (double)ex);
+    // tiny: each difference is off by e < 2^-87 (plus its rounding), so r^2 by
+    // at most 3 (2 |d| e + e^2)
+    const long double tol = tiny ? ldexpl(ex, -50) + 3.0L * (ldexpl(sqrtl(ex), -86) + ldexpl(1.0L, -174))
+                                 : 0.5L * ulp + ldexpl(ex, -57);
+    if (fabsl((long double)r2 - ex) > tol) { if (bad < 10) printf("r2 %.20Lg %.20g\n", ex, r2); ++bad; }
+  }
+  printf("ties %ld of %ld\n%ld\n", ties, n, bad);
+  return bad != 0;
+}
+""")
+    exe = tmp_path / "fx"
+    r = subprocess.run([nvcc, "-O2", "-std=c++17", "-I" + os.path.dirname(HDR),
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
