@@ -273,7 +273,10 @@ void nb_batch_destroy(nb_batch* b);
  * device output of up to cap (i, j) pairs, i < j, unordered; *npairs (host)
  * receives the total count. scratch: device buffer of
  * nb_kick_scratch_bytes(n, split) bytes. precision: NB_PREC_*. Returns
- * NB_E_OVERFLOW when more than cap pairs were found (all others written). */
+ * NB_E_OVERFLOW when more than cap pairs were found (all others written) and
+ * NB_E_INVALID when a coordinate is not finite or |x| >= 2^37 AU (the FP64
+ * kick forms its differences from 128-bit fixed-point positions, exact below
+ * 2^38 AU; nb_init_system and nb_set_state apply the same bound). */
 size_t nb_kick_scratch_bytes(int n, int split);
 int nb_kick(int n, const double* x, const double* m, const double* rc, double G, int precision,
             int split, double* a, int* pairs_ij, int cap, int* npairs, void* scratch,

@@ -208,6 +208,7 @@ const char* where_name(int w) {
     case 10: return "Kepler drift";
     case 20: return "input validation";
     case 21: return "initial flag set";
+    case 22: return "coordinate range of the standalone kick";
     case 30: return "Bulirsch-Stoer";
     default: return "device";
   }
@@ -668,15 +669,17 @@ int nb_kick_rows(int n, int row0, int row1, const double* x, const double* m, co
   p += align256(sizeof(double) * 3 * (size_t)S * n);
   Ctrl* ctrl = (Ctrl*)p;
   NB_CU(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-  launch_raw_prep(n, x, rc, sx, sy, sz, src2, st);
+  launch_raw_prep(n, x, rc, sx, sy, sz, src2, ctrl, st);
   launch_kick_raw(n, row0, row1, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij,
                   cap, ctrl, st);
   launch_raw_finish(n, row0, row1, S, kpart, G, a, st);
-  int cnt = 0;
+  int cnt = 0, stat = 0;
   NB_CU(cudaMemcpyAsync(&cnt, &ctrl->n_ftrial, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NB_CU(cudaMemcpyAsync(&stat, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   NB_CU(cudaStreamSynchronize(st));
   NB_CU(cudaGetLastError());
   if (npairs) *npairs = cnt;
+  if (stat == NB_E_INVALID) return NB_E_INVALID;  // a coordinate beyond 2^37 AU (or NaN)
   return cnt > cap ? NB_E_OVERFLOW : NB_OK;
 }
 

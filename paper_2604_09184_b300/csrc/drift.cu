@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(DNT) k_init(Dev d, Phys P, InitIn in) {
   const double m = in.m[i], R = in.R[i];
   bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
             isfinite(vz) && isfinite(m) && m > 0.0 && isfinite(R) && R >= 0.0;
+  // the kick's fixed-point positions cover |x| < 2^38 AU
+  ok = ok && fabs(x) < kPosMax && fabs(y) < kPosMax && fabs(z) < kPosMax;
   ok = ok && (x != 0.0 || y != 0.0 || z != 0.0);
   double rc = 0.0;
   if (in.rc) {
@@ -494,13 +496,17 @@ void launch_a_convert(const Dev& d, double* a3, int to_soa, cudaStream_t st) {
 // Standalone kick helpers: interleaved positions to SoA (+ rc^2), and the
 // fixed-order sum of the j-chunk partials times G into interleaved a.
 __global__ void __launch_bounds__(DNT) k_raw_prep(int n, const double* x3, const double* rc,
-                                                  double* x, double* y, double* z, double* rc2) {
+                                                  double* x, double* y, double* z, double* rc2,
+                                                  Ctrl* ctrl) {
   const int i = blockIdx.x * DNT + threadIdx.x;
   if (i >= n) return;
   x[i] = x3[3 * i];
   y[i] = x3[3 * i + 1];
   z[i] = x3[3 * i + 2];
   rc2[i] = rc[i] * rc[i];
+  // the kick's fixed-point positions cover |x| < 2^38 AU (NaN fails too)
+  if (!(fabs(x[i]) < kPosMax && fabs(y[i]) < kPosMax && fabs(z[i]) < kPosMax))
+    set_status(ctrl, NB_E_INVALID, 22);
 }
 
 // a3 holds rows [ib, ie): row i goes to a3[3 (i - ib)].
@@ -522,8 +528,8 @@ __global__ void __launch_bounds__(DNT) k_raw_finish(int n, int ib, int ie, int S
 }
 
 void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
-                     double* rc2, cudaStream_t st) {
-  k_raw_prep<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, x3, rc, x, y, z, rc2);
+                     double* rc2, Ctrl* ctrl, cudaStream_t st) {
+  k_raw_prep<<<(n + DNT - 1) / DNT, DNT, 0, st>>>(n, x3, rc, x, y, z, rc2, ctrl);
 }
 
 void launch_raw_finish(int n, int ib, int ie, int S, const double* kpart, double G, double* a3,

@@ -16,6 +16,9 @@ constexpr int kMaxBsK = 12;          // upper bound on bs_kmax
 constexpr int kStatN = 14;           // device statistics counters
 constexpr int kMlMax = 3;            // deepest multi-level changeover supported
 constexpr double kDeadOffset = 1e6;  // absorbed bodies sit at (1e6 (id + 1), 0, 0) AU
+// Largest accepted |coordinate| of a live body (the kick's fixed-point
+// positions are exact below 2^38 AU).
+constexpr double kPosMax = 0x1p37;
 
 // Bulirsch-Stoer scratch per group member (doubles): y[6] | f0[6] | per
 // extrapolation column j = 1..kmax: zm[6] zc[6] f[6] | T[2][kmax][6] | aux[4].
@@ -605,7 +608,7 @@ void launch_gather(const Dev& d, double* x3, double* v3, double* m, double* R, d
                    int* ids, int* count, cudaStream_t st);
 void launch_a_convert(const Dev& d, double* a3, int to_soa, cudaStream_t st);
 void launch_raw_prep(int n, const double* x3, const double* rc, double* x, double* y, double* z,
-                     double* rc2, cudaStream_t st);
+                     double* rc2, Ctrl* ctrl, cudaStream_t st);
 void launch_raw_finish(int n, int ib, int ie, int S, const double* kpart, double G, double* a3,
                        cudaStream_t st);
 int peak_blocks();

@@ -76,16 +76,19 @@ extern "C" int nb_kick_noalloc(int n, const double* x, const double* m, const do
   const size_t ctrl_off = (kNoallocDoubles * sizeof(double) + 255) & ~(size_t)255;
   Ctrl* ctrl = (Ctrl*)((char*)base + ctrl_off);
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return NB_E_CUDA;
-  launch_raw_prep(n, x, rc, sx, sy, sz, src2, st);
+  launch_raw_prep(n, x, rc, sx, sy, sz, src2, ctrl, st);
   launch_kick_raw(n, 0, n, sx, sy, sz, m, rc, src2, S, precision, kpart, (int2*)pairs_ij, cap, ctrl,
                   st);
   launch_raw_finish(n, 0, n, S, kpart, G, a, st);
-  int cnt = 0;
+  int cnt = 0, stat = 0;
   if (cudaMemcpyAsync(&cnt, &ctrl->n_ftrial, sizeof(int), cudaMemcpyDeviceToHost, st) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaMemcpyAsync(&stat, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
     return NB_E_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return NB_E_CUDA;
   if (cudaGetLastError() != cudaSuccess) return NB_E_CUDA;
   if (npairs) *npairs = cnt;
+  if (stat == NB_E_INVALID) return NB_E_INVALID;  // a coordinate beyond 2^37 AU (or NaN)
   return cnt > cap ? NB_E_OVERFLOW : NB_OK;
 }

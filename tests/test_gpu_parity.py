@@ -487,6 +487,22 @@ def test_invalid_inputs_rejected():
     ids = np.arange(16)[::-1].copy()
     with pytest.raises(nb.NbError):
         nb.NBodySystem(p, d.x, d.v, d.m, d.R, ids=ids)
+    # coordinates beyond the kick's fixed-point range (2^37 AU accepted, 2^38 exact)
+    far = d.x.copy()
+    far[5, 0] = 2.0 ** 37
+    with pytest.raises(nb.NbError) as e:
+        nb.NBodySystem(p, far, d.v, d.m, d.R)
+    assert e.value.code == nb.NB_E_INVALID
+    rc = oracle_rc(d)
+    a, pairs, code = nb.kick(cuda(far), cuda(d.m), cuda(rc), G, 0, 0)
+    assert code == nb.NB_E_INVALID
+    near = d.x.copy()
+    near[5, 0] = 2.0 ** 36  # inside the range: a valid (distant) body
+    a, pairs, code = nb.kick(cuda(near), cuda(d.m), cuda(rc), G, 0, 0)
+    assert code == 0
+    ar, _ = nbref.forces(near, d.m, rc, G)
+    a = a.cpu().numpy()
+    assert np.abs(a - ar).max() <= 1e-13 * np.abs(ar).max()
 
 
 def _approaching_pairs():
