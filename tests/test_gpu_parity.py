@@ -82,6 +82,27 @@ def test_kick_edge_cases_coincident_and_far():
     check_kick(x, d.m, rc, split=2)
 
 
+@pytest.mark.parametrize("prec_name", ["NB_PREC_FP64", "NB_PREC_MIXED"])
+def test_kick_tiny_and_mixed_magnitude_coordinates(prec_name):
+    """Coordinates the kick's fixed-point positions do not hold exactly
+    (|x| < 2^-36 AU, truncated to 2^-88 AU), exact zeros, a flat disk, bodies
+    near the 2^37 AU limit and close pairs straddling an axis: accelerations
+    against the oracle at the FP64 bar (mixed mode at its own) and identical
+    flags."""
+    nb = nbmod()
+    d = ics.workload("toy_disk_256", n=60)
+    x = d.x.copy()
+    x[:20, 2] = 0.0                                   # flat part of the disk
+    x[20:30, 2] = np.linspace(-3e-13, 3e-13, 10)      # below 2^-36 AU
+    x[30, :] = [1e-12, 0.9, 0.0]                      # near the y axis
+    x[31, :] = [-2e-12, 0.9 + 1e-4, 1e-14]            # its close neighbour across the axis
+    x[32, :] = [2.0 ** 36, 0.0, 0.0]                  # far out, inside the range
+    x[33, :] = x[34, :] * (1 + 1e-9)                  # nearly coincident
+    rc = oracle_rc(d, scale=3.0)
+    tol = 1e-13 if prec_name == "NB_PREC_FP64" else 1e-10
+    check_kick(x, d.m, rc, split=3, precision=getattr(nb, prec_name), tol=tol)
+
+
 def test_kick_giants_and_disk():
     d = ics.workload("mmsn_16k_js", n=3000)
     check_kick(d.x, d.m, oracle_rc(d), split=0)
