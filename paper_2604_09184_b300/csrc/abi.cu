@@ -25,14 +25,15 @@ int round_pow2(int v) {
 }
 
 int auto_split(int n) {
-  // About 96 kick CTAs per SM over the launch for 256-target tiles (192 for
-  // the FP64 kernel's 128-target tiles), so the last partial wave is a small
-  // fraction of the kernel: at N = 65538 the FP64 kick took 61.0, 60.0, 59.6,
-  // 58.9 and 58.6 ms with S = 8, 14, 20, 28 and 64 (the 16-instruction kick and
-  // the double-single kick gained 4 % and 14 % from ~8 to ~48 per SM). Whole
-  // 128-body j-tiles per chunk, at most 64 chunks.
+  // About 48 kick CTAs per SM over the launch per 256 targets (~97 for the
+  // kernels' 128-target tiles), so the last partial wave is a small fraction
+  // of the kernel: at N = 65538 the FP64 kick took 61.0, 60.0, 59.6, 58.9 and
+  // 58.6 ms with S = 8, 14, 20, 28 and 64. Beyond S ~ 28 the partial sums
+  // (S x 3 x N doubles) outgrow L2: at S = 56 the kick wrote 36.5 MB to DRAM
+  // per launch (1.1 MB at S = 28) for a 0.4 ms gain, so S stays near 28.
+  // Whole 128-body j-tiles per chunk, at most 64 chunks.
   const int itiles = (n + 255) / 256;
-  int S = (148 * 96 + itiles - 1) / itiles;
+  int S = (148 * 48 + itiles - 1) / itiles;
   const int maxS = (n + 127) / 128;
   if (S > 64) S = 64;
   if (S > maxS) S = maxS;
