@@ -424,7 +424,9 @@ __host__ __device__ __forceinline__ double sep2_int(double dx, double dy, double
 // there: at 1e6 (id + 1) AU, beyond 2^38 AU from id ~ 275 000).
 // The difference of two of them is exact, so the kick forms dx, dy, dz on the
 // integer pipe: fix_diff rounds X_j - X_i to a double (to nearest, ties
-// upward) and returns the top 64 bits of its square for sep2_fix.
+// upward; a negative difference is taken one unit of 2^-88 AU small, which
+// matters only below ~2^-35 AU) and returns the top 64 bits of its square for
+// sep2_fix.
 typedef unsigned __int128 nb_u128;
 __host__ __device__ __forceinline__ nb_u128 fix_of(double x) {
   const unsigned long long b = nb_dbits(x);
@@ -443,9 +445,11 @@ struct FixDiff {
 };
 __host__ __device__ __forceinline__ FixDiff fix_diff(nb_u128 xj, nb_u128 xi) {
   const nb_u128 dv = xj - xi;
-  const bool neg = (dv >> 127) != 0;
-  const nb_u128 mag = neg ? (nb_u128)0 - dv : dv;
-  const unsigned long long h = (unsigned long long)(mag >> 64), l = (unsigned long long)mag;
+  const unsigned long long hw = (unsigned long long)(dv >> 64);
+  const unsigned long long sgn = (unsigned long long)((long long)hw >> 63);  // ~0 if negative
+  // one's-complement magnitude: |dv| for dv >= 0, |dv| - 1 (one unit, 2^-88 AU)
+  // below it for dv < 0, which changes the result only for |dx| < ~2^-35 AU
+  const unsigned long long h = hw ^ sgn, l = (unsigned long long)dv ^ sgn;
   FixDiff r;
   if ((h | l) == 0ull) {
     r.d = 0.0;
@@ -453,11 +457,21 @@ __host__ __device__ __forceinline__ FixDiff fix_diff(nb_u128 xj, nb_u128 xi) {
     r.key = -4096;
     return r;
   }
-  const int L = h ? 127 - nb_clzll(h) : 63 - nb_clzll(l);
-  const unsigned long long N = (unsigned long long)((mag << (127 - L)) >> 64);  // bit 63 set
-  const unsigned long long Q = (N + (1ull << 10)) >> 11;  // 53 bits (2^53 on a carry)
-  const unsigned long long bits =
-      ((unsigned long long)neg << 63) + Q + ((unsigned long long)(L + 934) << 52);
+  int L;
+  unsigned long long N;  // the magnitude's top 64 bits, bit 63 set
+  if (h) {
+    const int s = nb_clzll(h);
+    N = s ? (h << s) | (l >> (64 - s)) : h;
+    L = 127 - s;
+  } else {  // |dx| < 2^-24 AU
+    const int s = nb_clzll(l);
+    N = l << s;
+    L = 63 - s;
+  }
+  // round at bit 10 (without forming N + 2^10, which can overflow 64 bits):
+  // 53 bits, 2^53 on a carry (which the exponent add absorbs)
+  const unsigned long long Q = (N >> 11) + ((N >> 10) & 1ull);
+  const unsigned long long bits = (sgn << 63) + Q + ((unsigned long long)(L + 934) << 52);
 #ifdef __CUDA_ARCH__
   r.d = __longlong_as_double((long long)bits);
 #else

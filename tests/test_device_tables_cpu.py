@@ -143,8 +143,9 @@ def test_fixed_point_differences(tmp_path):
     """The kick's integer dx (128-bit fixed-point positions, exact difference,
     rounded to a double): for coordinates in the exact range (2^-36..1e8 AU,
     both signs, coincident and nearly coincident pairs) it equals the FP64
-    subtraction except on exact ties (rounded upward, so within half an ulp);
-    for smaller coordinates its error stays below 2^-87 AU plus half an ulp;
+    subtraction except on exact ties (rounded upward, so within half an ulp)
+    and, for a negative difference, one unit of 2^-88 AU;
+    for smaller coordinates its error stays below 2^-86 AU plus half an ulp;
     r^2 is within half an ulp plus 2^-57 of the long-double sum of the exact
     differences."""
     nvcc = "/usr/local/cuda/bin/nvcc"
@@ -160,6 +161,21 @@ int main() {
   auto rnd = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return st; };
   auto uni = [&]() { return (double)((rnd() >> 11) | 1ull) * 0x1p-53; };
   long bad = 0, ties = 0, n = 0;
+  // magnitudes whose top 54 bits are all ones (rounding carries out of 64
+  // bits) and exact powers of two, both signs: X = 2^k units - 1 unit
+  for (int k = 40; k <= 120; ++k) {
+    const double a = ldexp(1.0, k - 88), b = ldexp(1.0, -88);
+    const double cases[4][2] = {{a, b}, {b, a}, {a, 0.0}, {0.0, a}};
+    for (auto& c : cases) {
+      const nb::FixDiff f = nb::fix_diff(nb::fix_of(c[0]), nb::fix_of(c[1]));
+      const long double dl = (long double)c[0] - (long double)c[1];
+      const double u = fabs(nextafter((double)dl, INFINITY) - (double)dl);
+      if (fabsl((long double)f.d - dl) > 0.5L * u + ldexpl(1.0L, -88)) {
+        if (bad < 5) printf("edge k=%d %.17g %.17g: %.17g\n", k, c[0], c[1], f.d);
+        ++bad;
+      }
+    }
+  }
   for (long it = 0; it < 2000000; ++it) {
     const bool tiny = (it % 10) == 0;
     double a[3], b[3];
@@ -182,14 +198,15 @@ int main() {
       ex += dl * dl;
       if (tiny) {  // truncation of each coordinate (< 2^-88) plus the rounding of dx
         const long double u = (long double)fabs(nextafter(want, INFINITY) - want);
-        if (fabsl((long double)f[k].d - dl) > ldexpl(1.0L, -87) + 0.5L * u) ++bad;
+        if (fabsl((long double)f[k].d - dl) > ldexpl(1.0L, -86) + 0.5L * u) ++bad;
         continue;
       }
       ++n;
       if (f[k].d != want) {
+        // ties round upward; a negative difference is taken one unit (2^-88 AU) small
         const double u = fabs(nextafter(want, INFINITY) - want);
         const long double err = fabsl((long double)f[k].d - dl);
-        if (err > 0.5L * u) { if (bad < 5) printf("dx %.17g %.17g: %.17g vs %.17g\n", a[k], b[k], f[k].d, want); ++bad; }
+        if (err > 0.5L * u + ldexpl(1.0L, -88)) { if (bad < 5) printf("dx %.17g %.17g: %.17g vs %.17g\n", a[k], b[k], f[k].d, want); ++bad; }
         else ++ties;
       }
     }
@@ -198,8 +215,9 @@ int main() {
     const long double ulp = (long double)(nextafter((double)ex, INFINITY) - (double)ex);
     // tiny: each difference is off by e < 2^-87 (plus its rounding), so r^2 by
     // at most 3 (2 |d| e + e^2)
-    const long double tol = tiny ? ldexpl(ex, -50) + 3.0L * (ldexpl(sqrtl(ex), -86) + ldexpl(1.0L, -174))
-                                 : 0.5L * ulp + ldexpl(ex, -57);
+    // (a negative difference is taken one unit, 2^-88 AU, small: 2 |d| 2^-88 per component)
+    const long double tol = tiny ? ldexpl(ex, -50) + 3.0L * (ldexpl(sqrtl(ex), -83) + ldexpl(1.0L, -170))
+                                 : 0.5L * ulp + ldexpl(ex, -57) + 3.0L * ldexpl(sqrtl(ex), -87);
     if (fabsl((long double)r2 - ex) > tol) { if (bad < 10) printf("r2 %.20Lg %.20g\n", ex, r2); ++bad; }
   }
   printf("ties %ld of %ld\n%ld\n", ties, n, bad);
