@@ -200,3 +200,27 @@ def test_batch_speculative_half_steps_are_bit_identical():
     for k in ("groups", "bs_derivs", "bs_substeps", "bs_halvings", "merges"):
         assert t0[k] == t1[k], (k, t0[k], t1[k])
     assert t0["bs_halvings"] > 0 and t0["merges"] > 0
+
+
+def test_batch_kick_awkward_coordinates():
+    """The batched kick's fixed-point differences on coordinates they do not
+    hold exactly (|x| < 2^-36 AU), exact zeros (a flat disk) and close pairs
+    straddling an axis, against the oracle over 20 steps."""
+    d = ics.make_disk(40, 2.0, 0.8, 1.2, 0.02, 0.01, 6.0, seed=4242)
+    x = d.x.copy()
+    x[:12, 2] = 0.0
+    x[12:20, 2] = np.linspace(-3e-13, 3e-13, 8)
+    v = d.v.copy()
+    x[20] = [1e-12, 1.0, 0.0]                      # on a circular orbit across the y axis
+    v[20] = [-np.sqrt(ics.G_GAUSS), 0.0, 0.0]
+    x[21] = x[20] + np.array([-3e-12, 2e-4, 1e-14])
+    v[21] = v[20]                                  # a co-moving close pair
+    d2 = ics.Disk(x=x, v=v, m=d.m, R=d.R, dt=d.dt)
+    dt, steps = 6.0, 20
+    ref, rc = oracle_run(d2, steps, dt)
+    b = batch_of([d2], dt, [rc])
+    b.step(steps, dt)
+    sg, sr = b.system_state(0), ref.state()
+    assert np.array_equal(sg["ids"], sr["ids"])
+    rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
+    assert rel.max() <= 1e-12, rel.max()
