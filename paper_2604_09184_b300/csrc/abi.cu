@@ -285,6 +285,12 @@ int nb_init_system(nb_system** out, const nb_params* p, int n, const double* x, 
   s->events = new std::vector<cudaEvent_t>();
   s->prm = *p;
   s->st = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    nb_destroy(s);
+    return NB_E_CUDA;
+  }
   s->P = make_phys(*p);
   layout(*p, n, (char*)workspace, &s->d);
   const size_t tail = align256(need - 512);
@@ -409,13 +415,21 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k + 1], s->st));
     }
     {
-      NvtxRange r("encounter set, groups, direct solver");
+      NvtxRange r("encounter set, groups, direct solver (trial half of the force beside it)");
       launch_encounter(d, s->P, s->st);
+      // the trial half of the incremental force update needs only the groups
+      // and the trial state, so it runs on the side stream while the direct
+      // solver (a few latency-bound CTAs) runs on the launching stream
+      NB_CU(cudaEventRecord(s->ev_fork, s->st));
+      NB_CU(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+      launch_finish_part(d, s->P, 1, s->side);
+      NB_CU(cudaEventRecord(s->ev_join, s->side));
       launch_bs(d, s->P, dt, s->st);
+      NB_CU(cudaStreamWaitEvent(s->st, s->ev_join, 0));
     }
     {
       NvtxRange r("final force (incremental) and scatter");
-      launch_finish(d, s->P, 1, s->st);
+      launch_finish_part(d, s->P, 2, s->st);
       launch_scatter(d, s->P, s->st);
       launch_member_kick(d, s->P, s->st);
     }
@@ -431,9 +445,9 @@ int nb_step(nb_system* s, int nsteps, double dt) {
   rc = read_ctrl(s, &c);
   if (rc) return rc;
   // kernels per step: open (split) or once per call, drift, kick, encounter,
-  // the direct solver (1 or 2), finish, scatter, member re-kick, close; and
-  // eject 1, r_crit 1, the force anew 3, gas 2 + 2
-  const long long per_step = 7 + bs_launches(d, s->P) + (split ? 1 : 0) + (eject ? 1 : 0) +
+  // the direct solver (1 or 2), finish (2 halves), scatter, member re-kick,
+  // close; and eject 1, r_crit 1, the force anew 3, gas 2 + 2
+  const long long per_step = 8 + bs_launches(d, s->P) + (split ? 1 : 0) + (eject ? 1 : 0) +
                              (refresh ? 1 : 0) + ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0);
   s->launches += (split ? 0 : 1) + per_step * nsteps;
   if (s->timing) {
@@ -566,6 +580,12 @@ void nb_destroy(nb_system* s) {
     for (cudaEvent_t e : *s->events) cudaEventDestroy(e);
     delete s->events;
   }
+  if (s->side) {
+    cudaStreamSynchronize(s->side);
+    cudaStreamDestroy(s->side);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   free(s);
 }
 

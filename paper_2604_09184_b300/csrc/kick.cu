@@ -466,8 +466,13 @@ __device__ __forceinline__ double finish_scale(double dx, double dy, double dz, 
   return scale_fast<NB_PREC_FP64>(r2, mj, sj[6 * FNT + k], sj[7 * FNT + k]);
 }
 
-__global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
-                                               const int* cond) {
+// PH = 0: the whole update in one pass. The step splits it so that the trial
+// half can run beside the direct solver: PH = 1 writes the unscaled sum of
+// the partials minus the group bodies' trial terms into a; PH = 2 (after the
+// direct solver) adds their final terms and applies G and the live mask.
+template <int PH>
+__global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delta,
+                                                 const int* cond) {
   __shared__ int s_stop, s_M;
   // members' trial (so) and final (snw) states: x, y, z, m, rc, rc^2, 1.5 m, 1.875 m
   __shared__ double so[8][FNT], snw[8][FNT];
@@ -481,11 +486,15 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
   const int i = blockIdx.x * FNT + threadIdx.x;
   double ax = 0.0, ay = 0.0, az = 0.0;
   if (i < n) {
-    for (int s = 0; s < d.S; ++s) {
-      const double* p = d.kpart + (size_t)(3 * s) * n;
-      ax += p[i];
-      ay += p[n + i];
-      az += p[2 * n + i];
+    if (PH == 2) {  // the trial half's result
+      ax = d.ax[i]; ay = d.ay[i]; az = d.az[i];
+    } else {
+      for (int s = 0; s < d.S; ++s) {
+        const double* p = d.kpart + (size_t)(3 * s) * n;
+        ax += p[i];
+        ay += p[n + i];
+        az += p[2 * n + i];
+      }
     }
   }
   const int M = s_M;
@@ -498,7 +507,7 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
   for (int q0 = 0; q0 < M; q0 += FNT) {
     __syncthreads();
     const int q = q0 + threadIdx.x;
-    if (q < M) {
+    if (q < M && PH != 2) {
       int b = d.grp_mem[q];
       if (!NB_GUARD(d.ctrl, b >= 0 && b < d.n, 58)) b = 0;
       so[0][threadIdx.x] = d.x[b];
@@ -510,6 +519,8 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
       so[5][threadIdx.x] = d.rc2[b];
       so[6][threadIdx.x] = 1.5 * mo;
       so[7][threadIdx.x] = 1.875 * mo;
+    }
+    if (q < M && PH != 1) {
       const double* g = d.gnew + (size_t)q * 10;
       snw[0][threadIdx.x] = g[0];
       snw[1][threadIdx.x] = g[1];
@@ -528,26 +539,44 @@ __global__ void __launch_bounds__(FNT) k_finish(Dev d, double G, int with_delta,
         // the trial kick's term of member k (same arithmetic as the kick:
         // seeded reciprocal root beyond rc, the exact weight inside), then
         // the term at the member's new state
-        double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
-        double s = finish_scale(dx, dy, dz, &so[0][0], k, rci, rc2i);
-        cx -= s * dx; cy -= s * dy; cz -= s * dz;
-        dx = snw[0][k] - xi; dy = snw[1][k] - yi; dz = snw[2][k] - zi;
-        s = finish_scale(dx, dy, dz, &snw[0][0], k, rci, rc2i);
-        cx += s * dx; cy += s * dy; cz += s * dz;
+        if (PH != 2) {
+          const double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
+          const double s = finish_scale(dx, dy, dz, &so[0][0], k, rci, rc2i);
+          cx -= s * dx; cy -= s * dy; cz -= s * dz;
+        }
+        if (PH != 1) {
+          const double dx = snw[0][k] - xi, dy = snw[1][k] - yi, dz = snw[2][k] - zi;
+          const double s = finish_scale(dx, dy, dz, &snw[0][0], k, rci, rc2i);
+          cx += s * dx; cy += s * dy; cz += s * dz;
+        }
       }
     }
   }
   if (i < n) {
-    const bool live = d.alive[i] != 0;
-    d.ax[i] = live ? G * (ax + cx) : 0.0;
-    d.ay[i] = live ? G * (ay + cy) : 0.0;
-    d.az[i] = live ? G * (az + cz) : 0.0;
+    if (PH == 1) {
+      d.ax[i] = ax + cx;
+      d.ay[i] = ay + cy;
+      d.az[i] = az + cz;
+    } else {
+      const bool live = d.alive[i] != 0;
+      d.ax[i] = live ? G * (ax + cx) : 0.0;
+      d.ay[i] = live ? G * (ay + cy) : 0.0;
+      d.az[i] = live ? G * (az + cz) : 0.0;
+    }
   }
 }
 
 void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st) {
   const int grid = (d.n + FNT - 1) / FNT;
-  k_finish<<<grid, FNT, 0, st>>>(d, P.G, with_delta, nullptr);
+  k_finish_t<0><<<grid, FNT, 0, st>>>(d, P.G, with_delta, nullptr);
+}
+
+void launch_finish_part(const Dev& d, const Phys& P, int part, cudaStream_t st) {
+  const int grid = (d.n + FNT - 1) / FNT;
+  if (part == 1)
+    k_finish_t<1><<<grid, FNT, 0, st>>>(d, P.G, 1, nullptr);
+  else
+    k_finish_t<2><<<grid, FNT, 0, st>>>(d, P.G, 1, nullptr);
 }
 
 void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStream_t st) {
@@ -566,7 +595,7 @@ void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStr
   A.counter = &d.ctrl->n_ftrial;
   A.ctrl = d.ctrl;
   launch_kick_args(A, P.precision, st);
-  k_finish<<<(d.n + FNT - 1) / FNT, FNT, 0, st>>>(d, P.G, 0, cond);
+  k_finish_t<0><<<(d.n + FNT - 1) / FNT, FNT, 0, st>>>(d, P.G, 0, cond);
   launch_fsal_init(d, st, cond);
 }
 

@@ -596,6 +596,9 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
                      const double* m, const double* rc, const double* rc2, int S, int precision,
                      double* kpart, int2* pairs, int cap, Ctrl* ctrl, cudaStream_t st);
 void launch_finish(const Dev& d, const Phys& P, int with_delta, cudaStream_t st);
+// part 1: partial sums minus the group bodies' trial terms (unscaled); part 2:
+// plus their final terms, times G (the step runs part 1 beside the direct solver)
+void launch_finish_part(const Dev& d, const Phys& P, int part, cudaStream_t st);
 void launch_member_kick(const Dev& d, const Phys& P, cudaStream_t st);
 void launch_open_h(const Dev& d, double h, cudaStream_t st);
 void launch_drift_h(const Dev& d, const Phys& P, double h, cudaStream_t st);
@@ -648,6 +651,10 @@ struct nb_system {
   double* out8;  // device: energy results
   int* cnt;      // device: gather count
   char err[256];
+  // a second stream for the trial half of the force update, which runs beside
+  // the direct solver, and the fork/join events
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   // kick timing (CUDA events on the launching stream) and launch counting
   int timing;
   std::vector<cudaEvent_t>* events;
