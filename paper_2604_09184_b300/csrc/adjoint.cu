@@ -879,6 +879,20 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
     }                                                                                   \
   } while (0)
 
+// Bit comparison of the replayed state (x, v, m) with a checkpoint: a replay
+// that does not reproduce the forward would give the gradient of another
+// trajectory, so the backward pass reports it instead.
+__global__ void k_replay_check(Dev d, const double* cd, int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = d.n;
+  if (i >= n) return;
+  const double* arr[7] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m};
+  bool same = true;
+  for (int q = 0; q < 7; ++q)
+    same = same && __double_as_longlong(arr[q][i]) == __double_as_longlong(cd[(size_t)q * n + i]);
+  if (!same) atomicExch(bad, 1);
+}
+
 // Copy the system's full state to (dir 0) or from (dir 1) checkpoint k.
 int checkpoint(nb_adjoint* a, int k, int dir) {
   const Dev& d = a->sys->d;
@@ -913,8 +927,11 @@ void replay_step(nb_adjoint* a, double dt, const StepRec& r) {
   k_rec_saved<<<g, 256, 0, a->st>>>(d, r);
   launch_kick(d, s->P, 0, a->st);
   launch_encounter(d, s->P, a->st);
+  // the force update in the two halves nb_step uses (same arithmetic, so the
+  // replay reproduces the forward bit for bit; here on one stream)
+  launch_finish_part(d, s->P, 1, a->st);
   launch_bs(d, s->P, dt, a->st);
-  launch_finish(d, s->P, 1, a->st);
+  launch_finish_part(d, s->P, 2, a->st);
   launch_scatter(d, s->P, a->st);
   launch_member_kick(d, s->P, a->st);
   k_rec_after<<<g + 1, 256, 0, a->st>>>(d, r);
@@ -1101,6 +1118,8 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
     {
       NvtxRange r("adjoint: replay segment");
       for (int t = 0; t < len; ++t) replay_step(a, a->dt, a->recs[t]);
+      // the replay must end on the next checkpoint bit for bit
+      k_replay_check<<<g, 256, 0, a->st>>>(d, a->ck_d + (size_t)(seg + 1) * 13 * n, a->status + 2);
     }
     {
       NvtxRange r("adjoint: reverse segment");
@@ -1115,6 +1134,13 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
     if (c.status || st[0]) {
       snprintf(a->err, sizeof(a->err), "backward: %s", nb_status_string(c.status ? c.status : st[0]));
       return c.status ? c.status : st[0];
+    }
+    int mismatch = 0;
+    NB_ACU(cudaMemcpy(&mismatch, a->status + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (mismatch) {
+      snprintf(a->err, sizeof(a->err),
+               "backward: the replay of segment %d did not reproduce the forward state", seg);
+      return NB_E_INVALID;
     }
   }
   // leave the system at its final state again

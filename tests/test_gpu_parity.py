@@ -752,3 +752,23 @@ def test_speculative_half_steps_are_bit_identical(workload):
     for k in ("groups", "bs_derivs", "bs_substeps", "bs_halvings", "merges"):
         assert sa[k] == sb[k], (k, sa[k], sb[k])
     assert sa["bs_halvings"] > 0
+
+
+def test_one_call_equals_step_by_step_with_mergers():
+    """nb_step(40) and forty nb_step(1) calls give the same bits on a merging
+    disk: the fused closing/opening kick of consecutive steps rounds as the
+    separate closing and opening kicks do (the adjoint's replay relies on it,
+    and checks it)."""
+    nb = nbmod()
+    d = ics.make_disk(24, 2.0, 0.97, 1.03, 0.01, 0.005, 6.0, seed=12, f_radius=300.0)
+    rp = nbref.params(dt_rcrit=d.dt)
+    rc = oracle_rc(d, rp)
+    a = nb.NBodySystem(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc=rc)
+    a.step(40, d.dt)
+    b = nb.NBodySystem(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc=rc)
+    for _ in range(40):
+        b.step(1, d.dt)
+    sa, sb = a.state(), b.state()
+    assert a.stats()["merges"] > 0
+    for k in ("ids", "x", "v", "m"):
+        assert np.array_equal(sa[k], sb[k]), k
