@@ -41,7 +41,6 @@ struct BatchDev {
   int cta_cap;
   double* spec;  // kSpecWarps x 4 slots x bs_stride: speculative-attempt scratch per warp
   int spec_cap;  // warps with a spec block (blockIdx.x * warps per CTA + warp < spec_cap)
-  nb_u128* fixpos;  // kCtaCap x 3 x NB_BATCH_MAX_N: a CTA's system as fixed-point positions
   const long long* budget_ns;  // per-launch time budget of a CTA in ns (0: none)
 };
 
@@ -131,38 +130,26 @@ __device__ void sys_momentum(const BSmem& s, int n, double P[3]) {
 }
 
 // Kick of Eq. Hb and flags for all live targets of the system (ascending j
-// sums; the single-system kernel's pair arithmetic: dx, dy, dz and r^2 from
-// fixed-point positions on the integer pipe, staged in the CTA's block of
-// global memory (shared memory holds the system), the exact FP64 branch for
-// near-ties).
+// sums; the single-system kernel's pair arithmetic with FP64 differences and
+// r^2 on the integer pipe: the fixed-point differences, which need their
+// positions staged outside shared memory here, measured 3.7 % slower).
 __device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* fcount,
-                         int* overflow, nb_u128* fix) {
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    fix[3 * j] = fix_of(s.x[j]);
-    fix[3 * j + 1] = fix_of(s.y[j]);
-    fix[3 * j + 2] = fix_of(s.z[j]);
-  }
-  __syncthreads();
+                         int* overflow) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (!s.alive[i]) {
       s.ax[i] = s.ay[i] = s.az[i] = 0.0;
       continue;
     }
     const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
-    const nb_u128 Xi = fix[3 * i], Yi = fix[3 * i + 1], Zi = fix[3 * i + 2];
     const int hi = __double2hiint(rc2i);
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int j = 0; j < n; ++j) {
-      const FixDiff fx = fix_diff(fix[3 * j], Xi), fy = fix_diff(fix[3 * j + 1], Yi),
-                    fz = fix_diff(fix[3 * j + 2], Zi);
-      double dx = fx.d, dy = fy.d, dz = fz.d;
-      double r2 = sep2_fix(fx, fy, fz);
+      const double dx = s.x[j] - xi, dy = s.y[j] - yi, dz = s.z[j] - zi;
+      double r2 = sep2_int(dx, dy, dz);
       const double mj = s.m[j];
       double sc = scale_fast<NB_PREC_FP64>(r2, mj);
       if (__double2hiint(r2) <= max(hi, __double2hiint(s.rc2[j])) + 1) {
-        // flags and weights from the FP64 subtractions and expression
-        dx = s.x[j] - xi; dy = s.y[j] - yi; dz = s.z[j] - zi;
-        r2 = sep2(dx, dy, dz);
+        r2 = sep2(dx, dy, dz);  // flags and weights from the FP64 expression
         const double rc2 = fmax(rc2i, s.rc2[j]);
         const bool close = (r2 < rc2) && s.alive[j] && (j != i);
         if (close && i < j) {
@@ -225,7 +212,6 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
                              double h, BsTally& bt, BsTally& wbt, SysTally& st) {
   const int base = B.off[sys];
   const int n = B.off[sys + 1] - base;
-  nb_u128* fix = B.fixpos + (size_t)blockIdx.x * 3 * NB_BATCH_MAX_N;  // grid <= kCtaCap
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int g = base + i;
     s.x[i] = B.x[g]; s.y[i] = B.y[g]; s.z[i] = B.z[g];
@@ -246,7 +232,7 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
   if (nsteps == 0) {
     if (threadIdx.x == 0) s.ints[1] = 0;
     __syncthreads();
-    sys_kick(s, n, P.G, s.fp, &s.ints[1], &s.ints[4], fix);
+    sys_kick(s, n, P.G, s.fp, &s.ints[1], &s.ints[4]);
     __syncthreads();
     if (threadIdx.x == 0) {
       s.ints[0] = min(s.ints[1], BPAIR);
@@ -283,7 +269,7 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
     if (threadIdx.x == 0) s.ints[1] = 0;
     __syncthreads();
     st.kepler_iters += kit;
-    sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4], fix);
+    sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
     __syncthreads();
     if (s.ints[4]) {  // overflow or Kepler failure: stop this system
       err = s.ints[4] == 2 ? NB_E_NOCONV : NB_E_OVERFLOW;
@@ -462,7 +448,7 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
       // force and flags at the final positions
       if (threadIdx.x == 0) s.ints[1] = 0;
       __syncthreads();
-      sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4], fix);
+      sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
       __syncthreads();
       if (s.ints[4]) {
         err = NB_E_OVERFLOW;
@@ -691,7 +677,6 @@ size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDe
   d.budget_ns = c.take<long long>(1);
   d.spec = c.take<double>((size_t)kSpecWarps * 4 * d.bs_stride);
   d.spec_cap = kSpecWarps;
-  d.fixpos = c.take<nb_u128>((size_t)kCtaCap * 3 * NB_BATCH_MAX_N);
   Snap s;
   s.arrays = c.take<double>((size_t)12 * total);
   s.alive = c.take<int>(total);
@@ -761,7 +746,7 @@ int batch_grid(const nb_batch* b) {
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > b->d.nsys) grid = b->d.nsys;
-  if (grid > kCtaCap) grid = kCtaCap;  // per-CTA blocks (fixpos, cta_ns) exist for kCtaCap CTAs
+  if (grid > kCtaCap) grid = kCtaCap;  // per-CTA timings (cta_ns) exist for kCtaCap CTAs
   return grid;
 }
 
