@@ -671,10 +671,13 @@ def test_long_run_energy_bounded_like_oracle():
     apart meet different encounters, and the energy error, made mostly at
     the encounters, ends anywhere between ~1e-7 and ~5e-7 after 10^4 steps);
     angular momentum stays conserved. The no-drift property itself is pinned
-    on the oracle for an encounter-free system."""
+    on the oracle for an encounter-free system. With mergers off two bodies
+    can pass almost through each other; both sides allow 30 substep halvings
+    (default 20) so that such a passage, which any change of rounding order
+    may or may not meet, does not stop the run."""
     nb = nbmod()
     d = ics.workload("toy_disk_256")
-    rp = nbref.params(dt_rcrit=d.dt, merge=0)
+    rp = nbref.params(dt_rcrit=d.dt, merge=0, bs_max_halvings=30)
     rc = oracle_rc(d, rp)
     worst_ref = 0.0
     for k in range(3):
@@ -684,7 +687,8 @@ def test_long_run_energy_bounded_like_oracle():
         for _ in range(50):
             assert ref.step(200, d.dt) == 0
             worst_ref = max(worst_ref, abs(ref.energy_momentum()["E"] / e0r - 1))
-    gpu = nb.NBodySystem(nb.params(dt_rcrit=d.dt, merge=0), d.x, d.v, d.m, d.R, rc=rc)
+    gpu = nb.NBodySystem(nb.params(dt_rcrit=d.dt, merge=0, bs_max_halvings=30), d.x, d.v, d.m, d.R,
+                          rc=rc)
     e0g = gpu.energy_momentum()
     eg = []
     for _ in range(50):
