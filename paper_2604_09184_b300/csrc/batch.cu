@@ -3,8 +3,8 @@
 // work counter), loads it into shared memory and runs every step of the chunk
 // there: B(h/2) C(h/2) A(h) C(h/2) B(h/2) with the same kick, flags, Kepler
 // drift, encounter set, groups, Bulirsch-Stoer and mergers as the
-// single-system path (the force after an encounter is re-evaluated in full:
-// N <= 512 makes that cheaper than bookkeeping). Systems never interact, so
+// single-system path (after an encounter only the group members' terms are
+// evaluated again). Systems never interact, so
 // no CTA waits on another. Chunks of steps are replayed from a captured CUDA
 // graph; the launch shape (threads per CTA) comes from the autotuner.
 #include <algorithm>
@@ -129,10 +129,48 @@ __device__ void sys_momentum(const BSmem& s, int n, double P[3]) {
   __syncthreads();
 }
 
-// Kick of Eq. Hb and flags for all live targets of the system (ascending j
-// sums; the single-system kernel's pair arithmetic with FP64 differences and
-// r^2 on the integer pipe: the fixed-point differences, which need their
-// positions staged outside shared memory here, measured 3.7 % slower).
+// One pair term of Eq. Hb for target i (xi, its rc^2 and rc, hi = high word of
+// its rc^2) and source j: a_i gains G sc (dx, dy, dz). The single-system
+// kernel's pair arithmetic with FP64 differences and r^2 on the integer pipe
+// (the fixed-point differences, which need their positions staged outside
+// shared memory here, measured 3.7 % slower); near ties of r^2 and rc^2 take
+// the FP64 expression, which decides close (r^2 < rc_ij^2) and the weight.
+struct KTerm {
+  double sc, dx, dy, dz;
+  bool close;
+};
+__device__ __forceinline__ KTerm kick_term(double xi, double yi, double zi, double rc2i, double rci,
+                                           int hi, double xj, double yj, double zj, double mj,
+                                           double rc2j, double rcj) {
+  KTerm t;
+  t.dx = xj - xi;
+  t.dy = yj - yi;
+  t.dz = zj - zi;
+  double r2 = sep2_int(t.dx, t.dy, t.dz);
+  t.sc = scale_fast<NB_PREC_FP64>(r2, mj);
+  t.close = false;
+  if (__double2hiint(r2) <= max(hi, __double2hiint(rc2j)) + 1) {
+    r2 = sep2(t.dx, t.dy, t.dz);
+    t.close = r2 < fmax(rc2i, rc2j);
+    if (r2 == 0.0) {
+      t.sc = 0.0;
+    } else if (t.close) {  // a dead source has m = 0: no force either way
+      const double r = sqrt(r2);
+      t.sc = mj * kick_weight(r, fmax(rci, rcj)) / (r2 * r);
+    }
+  }
+  return t;
+}
+
+__device__ __forceinline__ void push_flag(unsigned* flist, int* fcount, int* overflow, int i, int j) {
+  const int pos = atomicAdd(fcount, 1);
+  if (pos < BPAIR)
+    flist[pos] = ((unsigned)i << 16) | (unsigned)j;
+  else
+    *overflow = 1;
+}
+
+// Kick of Eq. Hb and flags for all live targets of the system (ascending j sums).
 __device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* fcount,
                          int* overflow) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -144,35 +182,91 @@ __device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* 
     const int hi = __double2hiint(rc2i);
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int j = 0; j < n; ++j) {
-      const double dx = s.x[j] - xi, dy = s.y[j] - yi, dz = s.z[j] - zi;
-      double r2 = sep2_int(dx, dy, dz);
-      const double mj = s.m[j];
-      double sc = scale_fast<NB_PREC_FP64>(r2, mj);
-      if (__double2hiint(r2) <= max(hi, __double2hiint(s.rc2[j])) + 1) {
-        r2 = sep2(dx, dy, dz);  // flags and weights from the FP64 expression
-        const double rc2 = fmax(rc2i, s.rc2[j]);
-        const bool close = (r2 < rc2) && s.alive[j] && (j != i);
-        if (close && i < j) {
-          const int pos = atomicAdd(fcount, 1);
-          if (pos < BPAIR)
-            flist[pos] = ((unsigned)i << 16) | (unsigned)j;
-          else
-            *overflow = 1;
-        }
-        if (r2 == 0.0) {
-          sc = 0.0;
-        } else if (close) {
-          const double r = sqrt(r2);
-          sc = mj * kick_weight(r, fmax(rci, s.rc[j])) / (r2 * r);
-        }
-      }
-      ax = __fma_rn(sc, dx, ax);
-      ay = __fma_rn(sc, dy, ay);
-      az = __fma_rn(sc, dz, az);
+      const KTerm t =
+          kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j], s.rc2[j], s.rc[j]);
+      if (t.close && i < j && s.alive[j]) push_flag(flist, fcount, overflow, i, j);
+      ax = __fma_rn(t.sc, t.dx, ax);
+      ay = __fma_rn(t.sc, t.dy, ay);
+      az = __fma_rn(t.sc, t.dz, az);
     }
     s.ax[i] = G * ax;
     s.ay[i] = G * ay;
     s.az[i] = G * az;
+  }
+}
+
+// Force and flags at the final positions after the direct solver, from the
+// trial ones (the incremental update of the single-system path). Only the
+// group members moved (or merged); each stashed its trial position, mass,
+// rc and rc^2 in xs, ys, zs, vxs, vys, vzs when its group wrote back.
+//   * Non-members: a_i += G sum_members (new term - trial term), members in
+//     list order; the trial term is recomputed bit for bit (same inputs, same
+//     arithmetic), so only the pairs with members change.
+//   * Members: the whole row again, one warp per member (lanes split j, a
+//     butterfly sum), with the flags of every pair it is in (a member pair
+//     once, from its lower index).
+//   * Flags between two non-members are those of the trial evaluation.
+// nmem members of n bodies cost about 3 nmem n pair terms instead of n^2.
+__device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* overflow) {
+  if (threadIdx.x == 0) {  // keep the trial flags of non-member pairs
+    const int nft = min(s.ints[1], BPAIR);
+    int kept = 0;
+    for (int k = 0; k < nft; ++k) {
+      const unsigned key = s.ft[k];
+      if (s.gidx[key >> 16] < 0 && s.gidx[key & 0xffffu] < 0) s.ft[kept++] = key;
+    }
+    s.ints[1] = kept;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (!s.alive[i] || s.gidx[i] >= 0) continue;
+    const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
+    const int hi = __double2hiint(rc2i);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int k = 0; k < nmem; ++k) {
+      const int j = s.gmem[k];
+      const KTerm tn =
+          kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j], s.rc2[j], s.rc[j]);
+      const KTerm tt = kick_term(xi, yi, zi, rc2i, rci, hi, s.xs[j], s.ys[j], s.zs[j], s.vxs[j],
+                                 s.vzs[j], s.vys[j]);
+      ax = __fma_rn(tn.sc, tn.dx, ax);
+      ay = __fma_rn(tn.sc, tn.dy, ay);
+      az = __fma_rn(tn.sc, tn.dz, az);
+      ax = __fma_rn(-tt.sc, tt.dx, ax);
+      ay = __fma_rn(-tt.sc, tt.dy, ay);
+      az = __fma_rn(-tt.sc, tt.dz, az);
+    }
+    s.ax[i] = __fma_rn(G, ax, s.ax[i]);
+    s.ay[i] = __fma_rn(G, ay, s.ay[i]);
+    s.az[i] = __fma_rn(G, az, s.az[i]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < nmem; k += nw) {
+    const int i = s.gmem[k];
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    if (s.alive[i]) {  // warp-uniform
+      const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
+      const int hi = __double2hiint(rc2i);
+      for (int j = lane; j < n; j += 32) {
+        const KTerm t = kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j],
+                                  s.rc2[j], s.rc[j]);
+        if (t.close && j != i && s.alive[j] && (s.gidx[j] < 0 || i < j))
+          push_flag(s.ft, &s.ints[1], overflow, min(i, j), max(i, j));
+        ax = __fma_rn(t.sc, t.dx, ax);
+        ay = __fma_rn(t.sc, t.dy, ay);
+        az = __fma_rn(t.sc, t.dz, az);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+      }
+    }
+    if (lane == 0) {
+      s.ax[i] = G * ax;
+      s.ay[i] = G * ay;
+      s.az[i] = G * az;
+    }
   }
 }
 
@@ -378,6 +472,8 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
             const int b = s.gmem[g0 + k];
             const double* yk = c.base + (size_t)k * c.stride + OY;
             const double* gk = c.g + 10 * k;
+            s.xs[b] = s.x[b]; s.ys[b] = s.y[b]; s.zs[b] = s.z[b];  // trial state, for the update
+            s.vxs[b] = s.m[b]; s.vys[b] = s.rc[b]; s.vzs[b] = s.rc2[b];
             if (gk[9] != 0.0) {
               s.x[b] = yk[0]; s.y[b] = yk[1]; s.z[b] = yk[2];
               s.vx[b] = yk[3]; s.vy[b] = yk[4]; s.vz[b] = yk[5];
@@ -427,6 +523,8 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
           const int b = s.gmem[g0 + k];
           const double* yk = c.base + (size_t)k * c.stride + OY;
           const double* gk = c.g + 10 * k;
+          s.xs[b] = s.x[b]; s.ys[b] = s.y[b]; s.zs[b] = s.z[b];  // trial state, for the update
+          s.vxs[b] = s.m[b]; s.vys[b] = s.rc[b]; s.vzs[b] = s.rc2[b];
           if (gk[9] != 0.0) {
             s.x[b] = yk[0]; s.y[b] = yk[1]; s.z[b] = yk[2];
             s.vx[b] = yk[3]; s.vy[b] = yk[4]; s.vz[b] = yk[5];
@@ -445,10 +543,16 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
         }
       }
       if (err) break;
-      // force and flags at the final positions
-      if (threadIdx.x == 0) s.ints[1] = 0;
-      __syncthreads();
-      sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
+      // force and flags at the final positions: the members' terms again, or
+      // the whole kick when the members are more than a third of the system
+      const int nmem = s.goff[ng];
+      if (3 * nmem <= n) {
+        sys_kick_update(s, n, nmem, P.G, &s.ints[4]);
+      } else {
+        if (threadIdx.x == 0) s.ints[1] = 0;
+        __syncthreads();
+        sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
+      }
       __syncthreads();
       if (s.ints[4]) {
         err = NB_E_OVERFLOW;
