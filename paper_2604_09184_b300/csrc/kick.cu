@@ -27,17 +27,18 @@
 //     (ballot + popc).
 // j-tiles of 128 bodies (fixed-point positions, m, 1.5 m, 1.875 m) are staged
 // through shared memory; each thread owns one target (the integer arithmetic
-// takes registers: 80 per thread, 6 CTAs per SM); a CTA covers 128 targets x
-// one j-chunk, and the j-chunks' partial sums are added in a fixed order by
-// k_finish (deterministic results). The double-single kernel has the same
-// shape (one target per thread: 27.7 ms against 30.7 ms with two at N = 65538).
+// takes registers: bounded at 64 for 8 CTAs per SM, 3 % faster than 80 and 6);
+// a CTA covers 128 targets x one j-chunk, and the j-chunks' partial sums are
+// added in a fixed order by k_finish (deterministic results). The double-single
+// kernel has the same shape (one target per thread: 27.7 ms against 30.7 ms
+// with two at N = 65538).
 #include "nb_internal.cuh"
 
 namespace nb {
 
 constexpr int KNT = 128;  // threads per kick CTA (= j-tile size)
 constexpr int KIPT = 1;   // targets per thread (the integer pair arithmetic needs registers:
-                          // one target, 80 registers, 6 CTAs per SM)
+                          // one target, 64 registers, 8 CTAs per SM)
 #ifndef NB_KICK_UNROLL
 #define NB_KICK_UNROLL 4
 #endif
@@ -94,7 +95,7 @@ __device__ __forceinline__ double rare_pair(double r2, double sc, double mj, int
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(KNT, 6) k_kick(KickArgs A) {
+__global__ void __launch_bounds__(KNT, 8) k_kick(KickArgs A) {
   __shared__ nb_u128 sX[KNT], sY[KNT], sZ[KNT];  // fixed-point positions of the j-tile
   __shared__ double sm[KNT], sm15[KNT], sm1875[KNT];
   __shared__ int sh[KNT];
