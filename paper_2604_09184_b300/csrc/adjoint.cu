@@ -802,11 +802,14 @@ int kmax_of(const nb_params& p) {
   return p.bs_kmax < 3 ? 3 : (p.bs_kmax > kMaxBsK ? kMaxBsK : p.bs_kmax);
 }
 
-// j-chunks of the kick VJP: about four CTAs per SM on 148 SMs, whole tiles.
+// Source chunks of the kick VJP: about 8 CTAs per SM over the launch (at
+// N = 2049 whole 128-body chunks gave 289 CTAs, two per SM, and the dependent
+// FP64 chain of each pair went unhidden), chunks of at least 16 sources.
 int vjp_split(int n) {
   const int tiles = (n + VNT - 1) / VNT;
-  int S = (148 * 4 + tiles - 1) / tiles;
-  if (S > tiles) S = tiles;
+  int S = (148 * 8 + tiles - 1) / tiles;
+  const int maxS = (n + 15) / 16;
+  if (S > maxS) S = maxS;
   return S < 1 ? 1 : S;
 }
 
@@ -950,7 +953,7 @@ void kick_vjp(nb_adjoint* a, const double* x6, const double* m, const double* rc
   V.mux = a->mux; V.muy = a->muy; V.muz = a->muz;
   V.part = a->vpart;
   V.n = n;
-  V.chunk = ((tiles + S - 1) / S) * VNT;
+  V.chunk = (n + S - 1) / S;  // the last chunks may be short or empty (zero partials)
   k_kick_vjp<<<dim3(tiles, S), VNT, 0, a->st>>>(V);
   k_kick_vjp_sum<<<g, ANT, 0, a->st>>>(n, S, a->vpart, a->sys->P.G, alive, a->lx, a->ly, a->lz,
                                        a->lm);
