@@ -86,6 +86,41 @@ def test_batch_with_encounters_and_mergers():
         assert abs(El[k] - em["E_lost"]) <= 1e-9 * abs(em["E_lost"]) + 1e-24
 
 
+def test_batch_force_update_after_encounters_both_branches():
+    """After the direct solver the batch updates the force from the trial one
+    (the members' new minus trial terms) unless the group members are more
+    than a third of the system, where it evaluates the force in full. Five-body
+    systems whose one encounter ends in a merger take the full branch; a
+    12-body system with three merging pairs and a 64-body one take the
+    incremental branch. All against the oracle over 40 steps."""
+    w = 0.05
+    disks = [ics.make_disk(5, 2.0, 1.0 - w / 2, 1.0 + w / 2, 0.02, 0.01, 6.0, seed=3000 + k,
+                           f_radius=300.0) for k in (0, 9, 19, 28)]
+    disks.append(ics.make_disk(12, 2.0, 1.0 - w / 2, 1.0 + w / 2, 0.02, 0.01, 6.0, seed=3103,
+                               f_radius=300.0))
+    disks.append(ics.make_disk(64, 2.0, 0.7, 1.3, 0.01, 0.005, 6.0, seed=964, f_radius=400.0))
+    dt, steps = 6.0, 40
+    refs, rcs = [], []
+    for d in disks:
+        s, rc = oracle_run(d, steps, dt)
+        refs.append(s)
+        rcs.append(rc)
+    for r in refs[:5]:
+        assert r.stats()["groups"] >= 1 and r.stats()["merges"] >= 1
+    b = batch_of(disks, dt, rcs)
+    b.step(steps, dt)
+    st = b.state()
+    assert b.stats()["merges"] == sum(r.stats()["merges"] for r in refs)
+    assert b.stats()["groups"] == sum(r.stats()["groups"] for r in refs)
+    for k, ref in enumerate(refs):
+        sg, sr = b.system_state(k, st), ref.state()
+        assert np.array_equal(sg["ids"], sr["ids"])
+        rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
+        assert rel.max() <= 1e-11, (k, rel.max())
+        relv = np.linalg.norm(sg["v"] - sr["v"], axis=1) / np.linalg.norm(sr["v"], axis=1)
+        assert relv.max() <= 1e-11, (k, relv.max())
+
+
 def test_batch_chunking_and_autotune_are_transparent():
     """Graph replay of chunks, a direct remainder launch and one-step calls give
     the same bits; autotuning leaves the state unchanged."""
