@@ -31,10 +31,11 @@ int auto_split(int n) {
   // 58.6 ms with S = 8, 14, 20, 28 and 64. Beyond S ~ 28 the partial sums
   // (S x 3 x N doubles) outgrow L2: at S = 56 the kick wrote 36.5 MB to DRAM
   // per launch (1.1 MB at S = 28) for a 0.4 ms gain, so S stays near 28.
-  // Whole 128-body j-tiles per chunk, at most 64 chunks.
+  // At most 64 chunks of at least 32 sources (chunks of any length: at
+  // N = 2049 whole 128-body chunks left 289 CTAs, two per SM).
   const int itiles = (n + 255) / 256;
   int S = (148 * 48 + itiles - 1) / itiles;
-  const int maxS = (n + 127) / 128;
+  const int maxS = (n + 31) / 32;
   if (S > 64) S = 64;
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;

@@ -405,9 +405,13 @@ static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) 
     k_kick<NB_PREC_FP64><<<grid, KNT, 0, st>>>(A);
 }
 
+// Sources per j-chunk. Chunks above 4 tiles take whole tiles (a partial tile
+// at every chunk's end cost 0.4 % at N = 65538); shorter ones any length (the
+// tile loop stages partial tiles), so that small systems still spread over
+// many CTAs (N = 2049: 1088 CTAs instead of 289, 6 % off the step).
 static int jchunk_for(int n, int S) {
   int c = (n + S - 1) / S;
-  c = ((c + KNT - 1) / KNT) * KNT;  // whole tiles
+  if (c > 4 * KNT) c = ((c + KNT - 1) / KNT) * KNT;
   return c > 0 ? c : KNT;
 }
 
