@@ -680,3 +680,122 @@ def test_multilevel_system_energy():
     # symplectic substeps: a larger but bounded energy error (measured 1.5e-8
     # against 3.0e-9 for the direct solver)
     assert out[0][0] < 1e-8 and out[2][0] < 1e-7, (out[0][0], out[2][0])
+
+
+# ---------------------------------------------------------------- Eq. rcrit
+def test_rcrit_hill_term_hand_values():
+    """Eq. rcrit's Hill term, R_Hill = |x| (m / 3 m0)^(1/3), on values worked
+    out by hand: a body on an exact circular orbit (no velocity term under
+    the relative-speed reading) with m = 3e-6 at 1 AU has R_Hill = 0.01 AU,
+    so r_crit = 0.03 AU; at 8 AU with m = 3 * 8e-9 * m0 and m0 = 2 it is
+    8 * 0.002 = 0.016 AU, so r_crit = 0.048 AU."""
+    vk = math.sqrt(G)
+    p = nbref.params(dt_rcrit=6.0)
+    assert nbref.rcrit(p, [1.0, 0.0, 0.0], [0.0, vk, 0.0], 3e-6) == pytest.approx(0.03, rel=1e-15)
+    # the same orbit rotated into the y axis (the prograde tangent turns with it)
+    assert nbref.rcrit(p, [0.0, 1.0, 0.0], [-vk, 0.0, 0.0], 3e-6) == pytest.approx(0.03, rel=1e-15)
+    p2 = nbref.params(dt_rcrit=6.0, m0=2.0)
+    vk8 = math.sqrt(G * 2.0 / 8.0)
+    assert nbref.rcrit(p2, [0.0, -8.0, 0.0], [vk8, 0.0, 0.0], 3 * 8e-9 * 2.0) == pytest.approx(
+        0.048, rel=1e-15)
+    # hill_factor scales the term
+    p3 = nbref.params(dt_rcrit=6.0, hill_factor=5.0)
+    assert nbref.rcrit(p3, [1.0, 0.0, 0.0], [0.0, vk, 0.0], 3e-6) == pytest.approx(0.05, rel=1e-15)
+
+
+def test_rcrit_velocity_term_hand_values():
+    """Eq. rcrit's velocity term 0.4 |dt| v. Under the relative-speed reading
+    (vel_mode 0) v is the speed relative to the circular prograde orbit at
+    the body's distance: sqrt(G m0 / |x|) along z-hat x (x, y, 0) / |(x, y)|.
+    At x = (3, 4, 0) AU (|x| = 5) the tangent is (-0.8, 0.6, 0). Checked:
+    a random offset from that orbit (v = |dv|), the retrograde orbit
+    (v = 2 v_circ), an inclined position (speed from the full distance,
+    direction from the projection), the literal reading (vel_mode 1: v = |v|)
+    and a negative dt (|dt|)."""
+    m = 1e-15  # Hill term 5 * (1e-15 / 3)^(1/3) * 3 ~ 1e-4 AU, below every velocity term here
+    x = [3.0, 4.0, 0.0]
+    vk = math.sqrt(G / 5.0)
+    vc = np.array([-0.8 * vk, 0.6 * vk, 0.0])
+    dv = np.array([2e-3, -1e-3, 5e-4])  # |dv| = sqrt(5.25e-6)
+    p = nbref.params(dt_rcrit=6.0)
+    assert nbref.rcrit(p, x, vc + dv, m) == pytest.approx(0.4 * 6.0 * math.sqrt(5.25e-6),
+                                                           rel=1e-12)
+    assert nbref.rcrit(p, x, -vc, m) == pytest.approx(0.4 * 6.0 * 2.0 * vk, rel=1e-14)
+    pneg = nbref.params(dt_rcrit=-6.0)
+    assert nbref.rcrit(pneg, x, vc + dv, m) == nbref.rcrit(p, x, vc + dv, m)
+    # inclined: x = (3, 4, 12), |x| = 13, horizontal tangent (-0.8, 0.6, 0)
+    vk13 = math.sqrt(G / 13.0)
+    xi = [3.0, 4.0, 12.0]
+    assert nbref.rcrit(p, xi, [-0.8 * vk13, 0.6 * vk13, 1e-3], m) == pytest.approx(
+        0.4 * 6.0 * 1e-3, rel=1e-9)
+    # the literal reading: the body's full speed
+    p1 = nbref.params(dt_rcrit=6.0, vel_mode=1)
+    assert nbref.rcrit(p1, x, vc, m) == pytest.approx(0.4 * 6.0 * vk, rel=1e-14)
+    assert nbref.rcrit(p1, x, [3e-3, 4e-3, 0.0], m) == pytest.approx(0.4 * 6.0 * 5e-3,
+                                                                      rel=1e-15)
+    # vel_factor scales the term; the larger of the two terms wins
+    p4 = nbref.params(dt_rcrit=6.0, vel_factor=0.8)
+    assert nbref.rcrit(p4, x, -vc, m) == pytest.approx(0.8 * 6.0 * 2.0 * vk, rel=1e-14)
+    big = 3e-6 * 125.0  # R_Hill = 5 * 0.05 = 0.25 AU: the Hill term wins over 0.037 AU
+    assert nbref.rcrit(p, x, -vc, big) == pytest.approx(0.75, rel=1e-14)
+
+
+# ---------------------------------------------------------------- Eqs. Ha-Hc
+def _inertial_energy_mp(x, v, m, m0=1.0, digits=50):
+    """Newtonian energy of the star + bodies in the barycentric inertial frame,
+    in mpmath: the star sits at X0 = -sum m x / M and moves at V0 = -P / m0,
+    body i at X0 + x_i with velocity v_i (heliocentric positions, barycentric
+    velocities). No term of the split appears here."""
+    with mp.workdps(digits):
+        n = len(m)
+        mm = [mp.mpf(float(q)) for q in m]
+        M = mp.mpf(m0) + sum(mm)
+        xs = [[mp.mpf(float(c)) for c in row] for row in x]
+        vs = [[mp.mpf(float(c)) for c in row] for row in v]
+        X0 = [-sum(mm[i] * xs[i][k] for i in range(n)) / M for k in range(3)]
+        P = [sum(mm[i] * vs[i][k] for i in range(n)) for k in range(3)]
+        V0 = [-P[k] / m0 for k in range(3)]
+        pos = [X0] + [[X0[k] + xs[i][k] for k in range(3)] for i in range(n)]
+        vel = [V0] + vs
+        mass = [mp.mpf(m0)] + mm
+        Gm = mp.mpf(G)
+        T = sum(mass[a] * sum(c * c for c in vel[a]) for a in range(n + 1)) / 2
+        U = mp.mpf(0)
+        for a in range(n + 1):
+            for b in range(a + 1, n + 1):
+                d = mp.sqrt(sum((pos[a][k] - pos[b][k]) ** 2 for k in range(3)))
+                U -= Gm * mass[a] * mass[b] / d
+        Lz = [sum(mass[a] * (pos[a][(k + 1) % 3] * vel[a][(k + 2) % 3]
+                             - pos[a][(k + 2) % 3] * vel[a][(k + 1) % 3]) for a in range(n + 1))
+              for k in range(3)]
+        return T + U, Lz, P, abs(T) + abs(U)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_energy_equals_inertial_newtonian_energy(seed):
+    """E = H_A + H_B + H_C (K cancels) must equal the total Newtonian energy of
+    the star and bodies in the inertial barycentric frame, and L = sum m x
+    cross v its angular momentum, for a system with a sizeable net momentum P
+    of the bodies (so |P|^2 / (2 m0), the star's kinetic energy, matters:
+    ~1e-3 of E here). A missing or mis-scaled Eq. Hc term, a wrong sign of the
+    star's potential or a pair-sum slip fails this."""
+    rng = np.random.default_rng(seed)
+    n = 3 + seed
+    m = np.array([1e-3, 3e-4, 5e-5, 2e-6, 7e-7, 4e-8][:n])
+    r = rng.uniform(0.7, 6.0, n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    x = np.stack([r * np.cos(ph), r * np.sin(ph), rng.normal(0, 0.05, n)], 1)
+    vk = np.sqrt(G / r)
+    v = np.stack([-vk * np.sin(ph), vk * np.cos(ph), np.zeros(n)], 1) * rng.uniform(0.8, 1.2, n)[:, None]
+    v += rng.normal(0, 2e-3, (n, 3))
+    p = nbref.params(dt_rcrit=6.0, merge=0)
+    s = nbref.RefSystem(p, x, v, m, np.full(n, 1e-6))
+    em = s.energy_momentum()
+    E_mp, L_mp, P_mp, scale = _inertial_energy_mp(x, v, m)
+    Pn = np.array([float(q) for q in P_mp])
+    hc = float(Pn @ Pn / 2.0)
+    assert hc > 1e-4 * abs(float(E_mp))  # the Eq. Hc term is not negligible here
+    assert abs(em["E"] - float(E_mp)) <= 1e-14 * float(scale)
+    assert np.allclose(em["P"], Pn, rtol=1e-14, atol=0)
+    Ln = np.array([float(q) for q in L_mp])
+    assert np.all(np.abs(em["L"] - Ln) <= 1e-14 * np.abs(Ln).max())
