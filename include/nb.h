@@ -300,13 +300,34 @@ int nb_kick_rows(int n, int row0, int row1, const double* x, const double* m, co
  * has no counterpart; this is a deployment convenience. Arguments as in
  * nb_kick() minus the scratch: the library keeps a static device array of
  * about 8.4 MB on every GPU that loads it, so n must not exceed
- * NB_NOALLOC_MAX_N (NB_E_INVALID otherwise). The first call on a device looks
- * up that array's device address (make it before any stream capture). Calls
- * share the array: calls that overlap on the GPU race, so serialise them.
+ * NB_NOALLOC_MAX_N (NB_E_INVALID otherwise). The first call in each CUDA
+ * context (a device's primary context, again after cudaDeviceReset, or a
+ * caller's own driver-API context) looks up that array's device address:
+ * make it before any stream capture. Calls share the array: calls that
+ * overlap on the GPU race, so serialise them. The pair set equals nb_kick()'s;
+ * the accelerations agree with it to rounding (at most 4 source chunks here,
+ * so the partial sums are added in another order), not bit for bit.
  * Allocates nothing; synchronises the stream before returning. */
 #define NB_NOALLOC_MAX_N 65600
 int nb_kick_noalloc(int n, const double* x, const double* m, const double* rc, double G,
                     int precision, double* a, int* pairs_ij, int cap, int* npairs, void* stream);
+
+/* Gradient of the total energy E = H_A + H_B + H_C (Eqs. Ha-Hc; the
+ * changeover K cancels, leaving the Newtonian pair sum) with respect to the
+ * state of the live bodies, for losses that contain the energy (the adjoint's
+ * cotangent of a final-energy term):
+ *   dE/dx_i = G m_i (m0 x_i / |x_i|^3 + sum_j m_j (x_i - x_j) / r_ij^3)
+ *   dE/dv_i = m_i (v_i + P / m0),  P = sum_j m_j v_j
+ *   dE/dm_i = |v_i|^2 / 2 - G m0 / |x_i| - G sum_j m_j / r_ij + P . v_i / m0
+ * Device arrays: x, v [n][3], m [n], alive [n] int32 (0 = absorbed; NULL =
+ * every body live); outputs gx, gv [n][3], gm [n] (zero for absorbed
+ * bodies). scratch: nb_energy_grad_scratch_bytes(n) bytes of device memory,
+ * 8-byte aligned. Asynchronous on the stream. NB_E_INVALID for n < 1, null
+ * arrays or m0 <= 0; NB_E_WORKSPACE for a short or misaligned scratch. */
+size_t nb_energy_grad_scratch_bytes(int n);
+int nb_energy_grad(int n, const double* x, const double* v, const double* m, const int* alive,
+                   double G, double m0, double* gx, double* gv, double* gm, void* scratch,
+                   size_t scratch_bytes, void* stream);
 
 /* Universal-variable Kepler drift (first sum of Eq. Ha) of n bodies about
  * mu = G m0 by dt, in place on device x, v [n][3]. Returns NB_E_NOCONV if a

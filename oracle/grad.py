@@ -67,6 +67,24 @@ def kick_accel(x, m, rc, G=G_GAUSS):
     return a, float(ratio.detach().min())
 
 
+def energy(x, v, m, m0=1.0, G=G_GAUSS):
+    """Total energy E = H_A + H_B + H_C of Eqs. Ha-Hc: the changeover K
+    cancels between the close part of H_A and H_B, so
+    E = sum m v^2 / 2 - sum G m0 m / |x| - sum_{i<j} G m_i m_j / r_ij
+        + |sum m v|^2 / (2 m0).
+    x, v (n, 3) heliocentric positions and barycentric velocities, m (n,)
+    (absorbed bodies are left out by the caller). Differentiable by autograd."""
+    n = x.shape[0]
+    kin = 0.5 * (m * (v * v).sum(1)).sum()
+    star = -(G * m0 * m / torch.sqrt((x * x).sum(1))).sum()
+    d = x.unsqueeze(0) - x.unsqueeze(1)
+    iu = torch.triu_indices(n, n, 1)
+    r = torch.sqrt((d[iu[0], iu[1]] ** 2).sum(-1))
+    pair = -(G * m[iu[0]] * m[iu[1]] / r).sum()
+    P = (m.unsqueeze(1) * v).sum(0)
+    return kin + star + pair + (P * P).sum() / (2.0 * m0)
+
+
 def stumpff(z):
     """Stumpff functions c0..c3 of z (elementwise): the power series of c2 and
     c3 at |z| / 4^q <= 0.1, c0 = 1 - z c2, c1 = 1 - z c3 there, and q

@@ -5,6 +5,8 @@
 // The O(N^2) pair potential uses 1/r from the same float seed as the kick,
 // refined to FP64 (second order in the residual). Per-thread and per-block
 // sums are Neumaier-compensated; the final reduction runs in a fixed order.
+#include <cmath>
+
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -115,6 +117,113 @@ __global__ void k_energy_final(Dev d, Phys P, int nblocks, double* out8) {
 
 int energy_blocks(int n) { return (n + ENT2 - 1) / ENT2; }
 
+// ---------------------------------------------------------------------------
+// Gradient of E = H_A + H_B + H_C with respect to the state (x, v, m) of the
+// live bodies, for losses that contain the total energy:
+//   dE/dx_i = G m_i (m0 x_i / |x_i|^3 + sum_j m_j (x_i - x_j) / r_ij^3)
+//   dE/dv_i = m_i (v_i + P / m0)                      (P = sum_j m_j v_j)
+//   dE/dm_i = |v_i|^2 / 2 - G m0 / |x_i| - G sum_j m_j / r_ij + P . v_i / m0
+// Arrays interleaved [n][3] as at the boundary. P is reduced in a fixed order
+// (per-block Neumaier sums, then the blocks in order), so results do not
+// depend on the launch.
+constexpr int EGT = 256;
+
+__global__ void __launch_bounds__(EGT) k_egrad_momentum(int n, const double* __restrict__ v,
+                                                        const double* __restrict__ m,
+                                                        const int* __restrict__ alive,
+                                                        double* __restrict__ parts) {
+  __shared__ double red[3 * EGT];
+  const int i = blockIdx.x * EGT + threadIdx.x;
+  const bool live = i < n && (!alive || alive[i]);
+  for (int k = 0; k < 3; ++k) red[k * EGT + threadIdx.x] = live ? m[i] * v[3 * i + k] : 0.0;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    Neu a{0.0, 0.0};
+    for (int t = 0; t < EGT; ++t) a.add(red[threadIdx.x * EGT + t]);
+    parts[2 * (3 * blockIdx.x + threadIdx.x)] = a.s;
+    parts[2 * (3 * blockIdx.x + threadIdx.x) + 1] = a.c;
+  }
+}
+
+__global__ void __launch_bounds__(EGT) k_egrad(int n, const double* __restrict__ x,
+                                               const double* __restrict__ v,
+                                               const double* __restrict__ m,
+                                               const int* __restrict__ alive, double G, double m0,
+                                               int nparts, const double* __restrict__ parts,
+                                               double* __restrict__ gx, double* __restrict__ gv,
+                                               double* __restrict__ gm) {
+  __shared__ double sx[EGT], sy[EGT], sz[EGT], sm[EGT];
+  __shared__ double Psh[3];
+  if (threadIdx.x < 3) {
+    Neu a{0.0, 0.0};
+    for (int b = 0; b < nparts; ++b) {
+      a.add(parts[2 * (3 * b + threadIdx.x)]);
+      a.add(parts[2 * (3 * b + threadIdx.x) + 1]);
+    }
+    Psh[threadIdx.x] = a.s + a.c;
+  }
+  const int i = blockIdx.x * EGT + threadIdx.x;
+  const bool live = i < n && (!alive || alive[i]);
+  const double xi = live ? x[3 * i] : 0.0, yi = live ? x[3 * i + 1] : 0.0,
+               zi = live ? x[3 * i + 2] : 0.0;
+  double fx = 0.0, fy = 0.0, fz = 0.0, pot = 0.0;
+  for (int jt = 0; jt < n; jt += EGT) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < n) {
+      const bool lj = !alive || alive[j];
+      sx[threadIdx.x] = x[3 * j];
+      sy[threadIdx.x] = x[3 * j + 1];
+      sz[threadIdx.x] = x[3 * j + 2];
+      sm[threadIdx.x] = lj ? m[j] : 0.0;
+    }
+    __syncthreads();
+    const int cnt = min(EGT, n - jt);
+    if (live) {
+      double tx = 0.0, ty = 0.0, tz = 0.0, tp = 0.0;
+      for (int q = 0; q < cnt; ++q) {
+        const double dx = xi - sx[q], dy = yi - sy[q], dz = zi - sz[q];
+        const double r2 = sep2(dx, dy, dz);
+        if (r2 == 0.0) continue;  // the body itself (absorbed bodies have no mass)
+        const double ir = inv_r(r2);
+        const double mir = sm[q] * ir;
+        const double mir3 = mir * ir * ir;
+        tx = __fma_rn(mir3, dx, tx);
+        ty = __fma_rn(mir3, dy, ty);
+        tz = __fma_rn(mir3, dz, tz);
+        tp += mir;
+      }
+      fx += tx;
+      fy += ty;
+      fz += tz;
+      pot += tp;
+    }
+  }
+  __syncthreads();
+  if (i >= n) return;
+  if (!live) {
+    for (int k = 0; k < 3; ++k) {
+      gx[3 * i + k] = 0.0;
+      gv[3 * i + k] = 0.0;
+    }
+    gm[i] = 0.0;
+    return;
+  }
+  const double mi = m[i];
+  const double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+  const double r = sqrt(xi * xi + yi * yi + zi * zi);
+  const double c0 = m0 / (r * r * r);
+  gx[3 * i] = G * mi * __fma_rn(c0, xi, fx);
+  gx[3 * i + 1] = G * mi * __fma_rn(c0, yi, fy);
+  gx[3 * i + 2] = G * mi * __fma_rn(c0, zi, fz);
+  const double Px = Psh[0], Py = Psh[1], Pz = Psh[2];
+  gv[3 * i] = mi * (vx + Px / m0);
+  gv[3 * i + 1] = mi * (vy + Py / m0);
+  gv[3 * i + 2] = mi * (vz + Pz / m0);
+  gm[i] = 0.5 * (vx * vx + vy * vy + vz * vz) - G * m0 / r - G * pot +
+          (Px * vx + Py * vy + Pz * vz) / m0;
+}
+
 void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st) {
   const int nb = energy_blocks(d.n);
   k_energy_parts<<<nb, ENT2, 0, st>>>(d, P);
@@ -122,3 +231,24 @@ void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st) {
 }
 
 }  // namespace nb
+
+extern "C" size_t nb_energy_grad_scratch_bytes(int n) {
+  if (n < 1) return 0;
+  return sizeof(double) * 6 * (size_t)((n + nb::EGT - 1) / nb::EGT);
+}
+
+extern "C" int nb_energy_grad(int n, const double* x, const double* v, const double* m,
+                              const int* alive, double G, double m0, double* gx, double* gv,
+                              double* gm, void* scratch, size_t scratch_bytes, void* stream) {
+  if (n < 1 || !x || !v || !m || !gx || !gv || !gm) return NB_E_INVALID;
+  if (!std::isfinite(G) || !std::isfinite(m0) || !(m0 > 0.0)) return NB_E_INVALID;
+  if (!scratch || scratch_bytes < nb_energy_grad_scratch_bytes(n) || ((uintptr_t)scratch & 7))
+    return NB_E_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = (n + nb::EGT - 1) / nb::EGT;
+  double* parts = (double*)scratch;
+  nb::k_egrad_momentum<<<nb, nb::EGT, 0, st>>>(n, v, m, alive, parts);
+  nb::k_egrad<<<nb, nb::EGT, 0, st>>>(n, x, v, m, alive, G, m0, nb, parts, gx, gv, gm);
+  if (cudaGetLastError() != cudaSuccess) return NB_E_CUDA;
+  return NB_OK;
+}

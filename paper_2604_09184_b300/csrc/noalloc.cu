@@ -11,11 +11,24 @@
 //
 // Host code must not hand the array's name to a kernel (on the host it only
 // stands in for the symbol); the device address is looked up with
-// cudaGetSymbolAddress once per device, by the first call made on that
-// device, with that device current. Make that first call before any stream
-// capture. All calls share the one array: calls that overlap on the GPU
-// (other streams, other host threads) race and corrupt each other's results,
-// so serialise them. Each call clears the counters it needs before use.
+// cudaGetSymbolAddress once per device context, by the first call made in
+// that context (the device's primary context, or a caller's own context made
+// current through the driver API), with that device current. After
+// cudaDeviceReset the primary context is a new one and the module is loaded
+// again, so the address is looked up again: the cache is keyed on the
+// driver's unique context id, never on the device ordinal alone. Make the
+// first call in a context before any stream capture. All calls share the one
+// array: calls that overlap on the GPU (other streams, other host threads)
+// race and corrupt each other's results, so serialise them. Each call clears
+// the counters it needs before use.
+//
+// The accelerations agree with nb_kick() to rounding (the parity suite's
+// 1e-13 relative bound), not bit for bit: this variant splits the sources
+// into at most kNoallocSplit chunks where nb_kick picks its own split, so
+// the partial sums are added in another order. The flagged pair set is the
+// same.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "nb_internal.cuh"
@@ -30,21 +43,71 @@ constexpr size_t kNoallocBytes = kNoallocDoubles * sizeof(double) + 256 + sizeof
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 namespace {
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 std::mutex g_mu;
-void* g_ptr[kMaxDevices] = {nullptr};
+struct CtxAddr {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+CtxAddr g_cache[kMaxContexts];
+int g_ncache = 0;
 
-// Device address of the scratch array on the current device (set-up on first use).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+
+// Unique id of the context current on this thread (0 if none can be had).
+// The two driver functions are resolved through the runtime, so the library
+// does not link the driver library itself.
+unsigned long long current_context_id() {
+  if (!g_get_current || !g_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return 0;
+    g_get_current = (CtxGetCurrentFn)f1;
+    g_get_id = (CtxGetIdFn)f2;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (g_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context: looked up by
+// the first call made in each context and cached under the context's id.
 int scratch_address(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NB_E_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NB_E_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NB_E_CUDA;
-    g_ptr[dev] = p;
+  unsigned long long id = current_context_id();
+  if (id != 0) {
+    for (int k = 0; k < g_ncache; ++k)
+      if (g_cache[k].ctx_id == id) {
+        *out = g_cache[k].ptr;
+        return NB_OK;
+      }
   }
-  *out = g_ptr[dev];
+  // First call in this context (or no context yet: the lookup creates the
+  // device's primary context, whose id is read afterwards).
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NB_E_CUDA;
+  if (id == 0) id = current_context_id();
+  if (id != 0) {
+    if (g_ncache < kMaxContexts) {
+      g_cache[g_ncache++] = {id, p};
+    } else {
+      g_cache[id % kMaxContexts] = {id, p};  // evict one: a later call looks it up again
+    }
+  }
+  *out = p;
   return NB_OK;
 }
 }  // namespace

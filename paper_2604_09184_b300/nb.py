@@ -109,6 +109,10 @@ def lib():
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p]
         L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int, C.c_void_p, C.c_void_p]
+        L.nb_energy_grad_scratch_bytes.argtypes = [C.c_int]
+        L.nb_energy_grad_scratch_bytes.restype = C.c_size_t
+        L.nb_energy_grad.argtypes = [C.c_int] + [C.c_void_p] * 4 + [C.c_double, C.c_double] + [
+            C.c_void_p] * 4 + [C.c_size_t, C.c_void_p]
         L.nb_batch_workspace_bytes.argtypes = [C.POINTER(NbParams), C.c_int, C.c_void_p]
         L.nb_batch_workspace_bytes.restype = C.c_size_t
         L.nb_batch_init.argtypes = [C.POINTER(C.c_void_p), C.POINTER(NbParams), C.c_int,
@@ -444,12 +448,53 @@ class NBodyBatch:
 
 def kick_noalloc(x, m, rc, a, pairs, G=2.959122082855911e-4, precision=NB_PREC_FP64):
     """nb_kick_noalloc on caller-provided CUDA tensors a (n, 3) and pairs
-    (cap, 2): nothing is allocated by this call. Returns (npairs, status)."""
+    (cap, 2): nothing is allocated by this call. Returns (npairs, status).
+
+    The kernel writes n x 3 doubles through a and up to cap int32 pairs
+    through pairs, so every tensor must be a contiguous CUDA tensor on the
+    current device with the stated dtype and shape (ValueError otherwise;
+    the checks allocate nothing)."""
     torch = _torch()
+    n = int(x.shape[0]) if x.dim() >= 1 else -1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    want = [("x", x, torch.float64, (n, 3)), ("m", m, torch.float64, (n,)),
+            ("rc", rc, torch.float64, (n,)), ("a", a, torch.float64, (n, 3)),
+            ("pairs", pairs, torch.int32, None)]
+    for name, t, dt, shape in want:
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise ValueError("%s must be a CUDA tensor on %s" % (name, dev))
+        if t.dtype != dt or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor" % (name, dt))
+        if shape is not None and tuple(t.shape) != shape:
+            raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
     cnt = C.c_int()
     code = lib().nb_kick_noalloc(x.shape[0], _ptr(x), _ptr(m), _ptr(rc), G, precision, _ptr(a),
                                  _ptr(pairs), pairs.shape[0], C.byref(cnt), _stream(torch))
     return cnt.value, code
+
+
+def energy_grad(x, v, m, alive=None, G=2.959122082855911e-4, m0=1.0):
+    """Gradient of the total energy (Eqs. Ha-Hc) with respect to the state on
+    CUDA tensors x, v (n, 3), m (n,), alive (n,) int32 or None (nb_energy_grad).
+    Returns (dE/dx, dE/dv, dE/dm) as new tensors; zero for absorbed bodies."""
+    torch = _torch()
+    n = int(m.shape[0])
+    x, v, m = (t.contiguous().to(torch.float64) for t in (x, v, m))
+    al = None if alive is None else alive.contiguous().to(torch.int32)
+    gx = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    gv = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    gm = torch.empty(n, dtype=torch.float64, device="cuda")
+    L = lib()
+    nbytes = L.nb_energy_grad_scratch_bytes(n)
+    scratch = torch.empty(max(nbytes, 8), dtype=torch.uint8, device="cuda")
+    code = L.nb_energy_grad(n, _ptr(x), _ptr(v), _ptr(m), None if al is None else _ptr(al), G,
+                            m0, _ptr(gx), _ptr(gv), _ptr(gm), _ptr(scratch), nbytes,
+                            _stream(torch))
+    if code != NB_OK:
+        raise NbError(code, "nb_energy_grad")
+    return gx, gv, gm
 
 
 def kepler_drift(x, v, mu, dt, max_iter=30):

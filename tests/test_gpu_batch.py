@@ -259,3 +259,29 @@ def test_batch_kick_awkward_coordinates():
     assert np.array_equal(sg["ids"], sr["ids"])
     rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
     assert rel.max() <= 1e-12, rel.max()
+
+
+def test_batch_size_extremes_match_oracle():
+    """Systems at the batch's limits in one launch: N = NB_BATCH_MAX_N (512,
+    the most a CTA holds in shared memory), 511, 16, 2 and a lone body, each
+    against its own oracle run over 30 steps."""
+    nb = nbm()
+    sizes = [nb.NB_BATCH_MAX_N, 16, 2, 1, nb.NB_BATCH_MAX_N - 1]
+    disks = [ics.make_disk(n, 2.0, 0.5, 2.0, 0.02, 0.01, 3.0, seed=4100 + n) for n in sizes]
+    dt, steps = 3.0, 30
+    refs, rcs = [], []
+    for d in disks:
+        s, rc = oracle_run(d, steps, dt)
+        refs.append(s)
+        rcs.append(rc)
+    b = batch_of(disks, dt, rcs)
+    b.step(steps, dt)
+    st = b.state()
+    assert b.stats()["groups"] == sum(r.stats()["groups"] for r in refs)
+    for k, (d, ref) in enumerate(zip(disks, refs)):
+        sg, sr = b.system_state(k, st), ref.state()
+        assert np.array_equal(sg["ids"], sr["ids"]), k
+        rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
+        assert rel.max() <= 1e-12, (k, d.n, rel.max())
+        relv = np.linalg.norm(sg["v"] - sr["v"], axis=1) / np.linalg.norm(sr["v"], axis=1)
+        assert relv.max() <= 1e-11, (k, d.n, relv.max())

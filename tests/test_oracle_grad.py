@@ -113,3 +113,47 @@ def test_step_jacobian_is_symplectic(steps):
     assert np.max(np.abs(resid) / scale) <= 1e-12
     # the check is not vacuous: M is far from the identity (x depends on p / m)
     assert np.abs(M - np.eye(18)).max() > 1e3
+
+
+def _energy_system(seed, n=6):
+    """Bodies with a sizeable net momentum (so the Eq. Hc term matters)."""
+    rng = np.random.default_rng(seed)
+    m = np.array([1e-3, 3e-4, 5e-5, 2e-6, 7e-7, 4e-8, 1e-9, 2e-9][:n])
+    r = rng.uniform(0.7, 6.0, n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    x = np.stack([r * np.cos(ph), r * np.sin(ph), rng.normal(0, 0.05, n)], 1)
+    vk = np.sqrt(G / r)
+    v = np.stack([-vk * np.sin(ph), vk * np.cos(ph), np.zeros(n)], 1) + rng.normal(0, 2e-3, (n, 3))
+    return x, v, m
+
+
+def _c_energy(x, v, m):
+    s = nbref.RefSystem(nbref.params(merge=0), x, v, m, np.full(len(m), 1e-6))
+    return s.energy_momentum()["E"]
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_energy_matches_c_oracle_and_its_gradient_central_differences(seed):
+    """og.energy equals the C oracle's E (pinned to the inertial-frame
+    Newtonian energy) and its autograd gradient equals central differences of
+    the C oracle's E in every coordinate, velocity and mass."""
+    x, v, m = _energy_system(seed)
+    xt, vt, mt = (torch.tensor(a, dtype=torch.float64, requires_grad=True) for a in (x, v, m))
+    E = og.energy(xt, vt, mt)
+    Ec = _c_energy(x, v, m)
+    assert abs(E.item() - Ec) <= 1e-14 * abs(Ec)
+    gx, gv, gm = torch.autograd.grad(E, (xt, vt, mt))
+    for arr, g, rel in ((x, gx, 1e-6), (v, gv, 1e-6), (m, gm, 1e-6)):
+        flat = arr.reshape(-1)
+        for k in range(flat.size):
+            h = rel * max(abs(flat[k]), 1e-3 if arr is not m else 1e-12)
+            up = [a.copy() for a in (x, v, m)]
+            dn = [a.copy() for a in (x, v, m)]
+            which = 0 if arr is x else (1 if arr is v else 2)
+            up[which].reshape(-1)[k] += h
+            dn[which].reshape(-1)[k] -= h
+            fd = (_c_energy(*up) - _c_energy(*dn)) / (2 * h)
+            ad = g.reshape(-1)[k].item()
+            # truncation O(h^2) plus the rounding noise of E itself over 2h
+            noise = 64 * np.spacing(abs(Ec)) / (2 * h)
+            assert abs(fd - ad) <= 2e-6 * abs(ad) + noise, (which, k, fd, ad, noise)
