@@ -14,9 +14,20 @@ kick's throughput, the roofline of the dominant kernel (the kick), the end-to-
 end number through the C ABI with host buffers, the oracle on the host cores,
 and the SM clocks sampled during the timed region.
 
-Under torchrun (N > 1) every rank integrates its own replica of the workload
-on its own GPU (the single-system step does not shard across ranks); the
-reported value is the sum over ranks divided by the slowest rank's time.
+Accuracy of the reduced-precision kicks on the same workload (its 1000-step
+form): the literal mixed form and double-single run 100 and 1000 steps next to
+an FP64 run from the same state and radii, and their state errors against it
+are reported, with the error of each against the oracle after 100 steps. The
+oracle's 100 steps are the run the CPU-baseline leg times (warm-up and timed
+steps, the reference arm's sample), continued in a background thread on the
+host cores while the GPU runs the other legs.
+
+Under torchrun (N > 1) the ranks integrate one system together: every rank
+holds the whole state and evaluates the O(N^2) kick for its own block of
+target rows, and two NCCL all-gathers per step join the blocks (the row-
+sharded step, nb_set_shard). The work is fixed as N grows (strong scaling);
+the value is the job's pair interactions per second of the slowest rank's
+time. Only the headline step is timed at N > 1.
 """
 from __future__ import annotations
 
@@ -39,6 +50,7 @@ UNIT = "pair interactions/s"
 WORKLOAD = "mmsn_64k_js"
 FLOP_PER_PAIR = 20        # direct-summation convention (Nyland, Harris & Prins 2007)
 FP64_INSTR_PER_PAIR = 7  # FP64 instructions in the kick's pair loop (FP64 mode)
+ACC_SHORT, ACC_LONG = 100, 1000  # steps of the accuracy leg (oracle comparison, long run)
 
 
 def parse():
@@ -55,6 +67,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-options", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the 100/1000-step accuracy leg of the reduced-precision kicks")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="steps of the adjoint leg (2000 is the workload; fewer for profiling)")
     ap.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval")
@@ -86,10 +100,10 @@ def max_over_ranks(value: float, world: int, device) -> float:
     return float(t.item())
 
 
-def whole_job_rate(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
-    """Units processed by all ranks (replicas: each rank its own copy) per
-    second of the slowest rank."""
-    return world * units_per_rank_step * steps / (max_ms * 1e-3)
+def job_rate(units_per_step: float, steps: int, max_ms: float) -> float:
+    """Units the whole job processes (all ranks together: one sharded system)
+    per second of the slowest rank."""
+    return units_per_step * steps / (max_ms * 1e-3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -236,14 +250,11 @@ def run_ours(args):
     n = disk.n
     pps = pairs_per_step(n)
 
-    # CPU baseline first (before any GPU work), rank 0 only, bounded sample
-    cpu = None
+    # CPU baseline first (before any GPU work), rank 0 only: the reference arm's
+    # sample (warm-up, then the timed steps) of the same workload
+    cpu, oracle_run = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        threads = os.cpu_count() or 1
-        t_step = oracle_step_time(disk, 1, threads)
-        cpu = {"value": pps / t_step, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "1 full oracle step of %s (N=%d), %d OpenMP threads, %.1f s" % (
-                   args.workload, n, threads, t_step)}
+        cpu, oracle_run = cpu_baseline_leg(disk, args)
 
     stream = torch.cuda.current_stream()
     f64_peak, f32_peak = nb.measure_peaks()
@@ -251,6 +262,14 @@ def run_ours(args):
     prec = {"fp64": nb.NB_PREC_FP64, "mixed": nb.NB_PREC_MIXED, "ds": nb.NB_PREC_DS}[args.precision]
     p = nb.params(dt_rcrit=disk.dt, precision=prec)
     sysm = nb.NBodySystem(p, disk.x, disk.v, disk.m, disk.R)
+    sharding = None
+    if world > 1:
+        # one system on all ranks: the kick's target rows split across them
+        from paper_2604_09184_b300 import shard
+        sharding = shard.Shard(sysm, rank, world)
+        for k in ("no_e2e", "no_cpu", "no_mixed", "no_batch", "no_adjoint", "no_options",
+                  "no_accuracy"):
+            setattr(args, k, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 0)):
         sysm.step(1, disk.dt)
@@ -278,7 +297,7 @@ def run_ours(args):
     gpu_launches = tm["launches"] - launches0
     total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_per_step = total_ms / max(args.steps, 1)
-    value = whole_job_rate(pps, args.steps, world, total_ms)
+    value = job_rate(pps, args.steps, total_ms)
     kick_ms = tm["kick_ms"] / max(tm["kick_launches"], 1)
     st = sysm.stats()
 
@@ -289,19 +308,40 @@ def run_ours(args):
         "kernel": "k_kick<FP64>", "kick_ms": kick_ms,
         "flop_per_pair": FLOP_PER_PAIR,
         "peak_source": "FP64 DFMA loop measured in this run (nb_measure_peaks)",
-        "fp64_pipe_frac": FP64_INSTR_PER_PAIR * pps / (kick_ms * 1e-3) / (f64_peak / 2),
-        "fp64_instr_per_pair": FP64_INSTR_PER_PAIR,
+        "fp64_pipe_frac_by_count": FP64_INSTR_PER_PAIR * pps / (kick_ms * 1e-3) / (f64_peak / 2),
+        "fp64_instr_per_pair_design": FP64_INSTR_PER_PAIR,
         "fp32_peak_tflops": f32_peak / 1e12,
         "note": "achieved counts 20 flop per pair (the direct-summation convention); the kick "
                 "forms dx, dy, dz and r^2 on the integer pipe (exact fixed-point differences), "
-                "so its FP64 pipe executes %d FP64 instructions per pair and the conventional "
+                "so its FP64 pipe executes ~%d FP64 instructions per pair and the conventional "
                 "rate can exceed the DFMA peak; fp64_pipe_frac is the FP64 pipe's busy share "
-                "by instruction count" % FP64_INSTR_PER_PAIR,
+                "measured by ncu on one launch of this kernel at this N" % FP64_INSTR_PER_PAIR,
     }
     tr = read_traffic(os.path.join(ROOT, "profiles", "kick_fp64_mmsn_64k_dram.txt"))
     if tr.get("n") == str(n):
         roofline["traffic"] = float(tr["bytes_per_launch"])
         roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 1 launch"
+    # pipe shares measured by ncu (one launch of each kick at this N), not asserted
+    pf = read_traffic(os.path.join(ROOT, "profiles", "kick_fp64_mmsn_64k_pipes.txt"))
+    if pf.get("n") == str(n):
+        roofline["fp64_pipe_frac"] = float(pf["fp64_pipe_pct"]) / 100
+        roofline["alu_pipe_frac"] = float(pf["alu_pipe_pct"]) / 100
+        roofline["issue_active_frac"] = float(pf["issue_active_pct"]) / 100
+        roofline["fp64_instr_per_pair"] = float(pf["fp64_inst_per_pair"])
+        roofline["pipes_source"] = ("ncu sm__pipe_fp64_cycles_active, sm__pipe_alu_cycles_active, "
+                                    "sm__issue_active (% of peak sustained active) and "
+                                    "sm__inst_executed_pipe_fp64.sum, profiles/"
+                                    "kick_fp64_mmsn_64k_pipes.txt")
+    pd = read_traffic(os.path.join(ROOT, "profiles", "kick_ds_mmsn_64k_pipes.txt"))
+    if pd.get("n") == str(n):
+        roofline["double_single"] = {
+            "kernel": "k_kick_ds", "bound": "alu",
+            "fp32_pipe_frac": float(pd["fma_pipe_pct"]) / 100,
+            "fp64_pipe_frac": float(pd["fp64_pipe_pct"]) / 100,
+            "issue_active_frac": float(pd["issue_active_pct"]) / 100,
+            "source": "ncu sm__pipe_fma_cycles_active (the FP32 FMA pipes), "
+                      "sm__pipe_fp64_cycles_active, sm__issue_active, one launch, profiles/"
+                      "kick_ds_mmsn_64k_pipes.txt"}
 
     # reduced-precision kicks on the same workload: the literal mixed mode
     # (float seed + one FP64 Newton step) and double-single on the FP32 pipe
@@ -311,6 +351,14 @@ def run_ours(args):
                                       kick_ms, pps, flush, stream),
                  "double_single": run_variant(nb, torch, disk, args, nb.NB_PREC_DS, ms_per_step,
                                               kick_ms, pps, flush, stream)}
+        mixed["note"] = (
+            "the literal mixed form (FP32 rsqrt seed + one FP64 Newton step) gives only %.2fx "
+            "per kick on B300: the FP64 kick already takes r^-3 from an FP32 seed and forms "
+            "dx, dy, dz and r^2 on the integer pipe, so the mixed form removes one of its 7 FP64 "
+            "instructions per pair. Double-single (float-pair arithmetic on the FP32 pipe) is "
+            "the form that gives the speed-up: %.2fx per kick, %.2fx per step" % (
+                mixed["mixed"]["speedup_kick"], mixed["double_single"]["speedup_kick"],
+                mixed["double_single"]["speedup_step"]))
 
     batched = None
     if not args.no_batch:
@@ -332,15 +380,30 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(nb, torch, sysm, disk, args.steps, pps)
 
+    # accuracy of the reduced-precision kicks (untimed; last, so that the oracle
+    # thread it starts overlaps no timed leg)
+    accuracy = None
+    if not args.no_accuracy and world == 1:
+        del sysm
+        accuracy = run_accuracy(nb, disk, oracle_run)
+        if mixed is not None:
+            for key in ("mixed", "double_single"):
+                mixed[key].update(accuracy.pop(key))
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "steps_per_s": 1e3 / ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_bodies": n, "dt_days": disk.dt,
-                   "precision": args.precision, "parallelism": "replica per GPU" if world > 1 else "1 GPU",
+                   "precision": args.precision,
+                   "parallelism": ("row-sharded kick over %d GPUs (rows %d..%d on rank 0), two "
+                                   "NCCL all-gathers per step" % (world, sharding.row0,
+                                                                  sharding.row1)
+                                   if sharding else "1 GPU"),
                    "l2": "flushed before each timed step (256 MiB write, outside the step events)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+        "accuracy": accuracy,
         "batched": batched, "adjoint": adjoint, "options": options,
         "clocks": clk, "gpu_launches": gpu_launches,
         "encounters": {"pairs": st["encounter_pairs"], "groups": st["groups"],
@@ -352,6 +415,111 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def cpu_baseline_leg(disk, args):
+    """The oracle on all host cores over the sample the reference arm times
+    (args.warmup untimed steps, then args.steps timed full steps of the
+    workload, from the same initial state). Returns the cpu_baseline entry and
+    the oracle run, whose state and encounter log the accuracy leg continues
+    to ACC_SHORT steps."""
+    import threading  # noqa: F401  (the continuation runs in a thread)
+    from oracle import nbref
+    threads = os.cpu_count() or 1
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    nbref.set_threads(threads)
+    p = nbref.params(dt_rcrit=disk.dt)
+    s = nbref.RefSystem(p, disk.x, disk.v, disk.m, disk.R)
+    rc0 = s.state()["rc"]
+    logs = []
+    if args.warmup > 0:
+        if s.step(args.warmup, disk.dt) != 0:
+            raise RuntimeError("oracle step failed")
+        logs.append(s.encounter_list())
+    t0 = time.perf_counter()
+    if s.step(args.steps, disk.dt) != 0:
+        raise RuntimeError("oracle step failed")
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    logs.append(s.encounter_list())
+    cpu = {"value": pairs_per_step(disk.n) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "%d full oracle steps of %s (N=%d) after %d untimed, %d OpenMP threads, "
+                     "%.2f s per step (the reference arm's sample)" % (
+                         args.steps, args.workload, disk.n, args.warmup, threads, dt)}
+    return cpu, {"sys": s, "logs": logs, "rc": rc0, "threads": threads, "nbref": nbref}
+
+
+def _state_err(a, b):
+    """Relative position error of state a against state b over their common
+    ids: max, median, bodies above 1e-12, and whether the id sets agree."""
+    common, ia, ib = np.intersect1d(a["ids"], b["ids"], return_indices=True)
+    rel = np.linalg.norm(a["x"][ia] - b["x"][ib], axis=1) / np.linalg.norm(b["x"][ib], axis=1)
+    return {"max": float(rel.max()), "median": float(np.median(rel)),
+            "bodies_above_1e-12": int((rel > 1e-12).sum()), "bodies": int(len(rel)),
+            "ids_identical": bool(len(a["ids"]) == len(b["ids"]) == len(common))}
+
+
+def run_accuracy(nb, disk, oracle_run):
+    """The workload in FP64, in the literal mixed form and in double-single
+    from the same state and critical radii: ACC_SHORT and ACC_LONG steps each.
+    Errors of the reduced-precision runs against the FP64 run at both counts,
+    and of all three against the oracle at ACC_SHORT (the oracle run of the
+    CPU-baseline leg, continued meanwhile in a background thread)."""
+    import threading
+    from paper_2604_09184_b300 import nb as nbm
+    rc = None
+    th = None
+    orc = None
+    if oracle_run is not None:
+        rc = oracle_run["rc"]
+        s, nbref = oracle_run["sys"], oracle_run["nbref"]
+        done = s.step_index
+        if done <= ACC_SHORT:
+            def rest():
+                # leave cores to the GPU launches meanwhile (results do not
+                # depend on the thread count)
+                nbref.set_threads(max(oracle_run["threads"] - 2, 1))
+                if done < ACC_SHORT:
+                    s.step(ACC_SHORT - done, disk.dt)
+                    oracle_run["logs"].append(s.encounter_list())
+            th = threading.Thread(target=rest)
+            th.start()
+    runs = {}
+    for name, prec in (("fp64", nbm.NB_PREC_FP64), ("mixed", nbm.NB_PREC_MIXED),
+                       ("double_single", nbm.NB_PREC_DS)):
+        g = nb.NBodySystem(nb.params(dt_rcrit=disk.dt, precision=prec), disk.x, disk.v, disk.m,
+                           disk.R, rc=rc)
+        g.step(ACC_SHORT, disk.dt)
+        s100, e100 = g.state(), g.encounter_list()
+        g.step(ACC_LONG - ACC_SHORT, disk.dt)
+        runs[name] = (s100, e100, g.state(), g.stats())
+        del g
+    if th is not None:
+        th.join()
+        sref = oracle_run["sys"].state()
+        eref = np.concatenate([q for q in oracle_run["logs"] if len(q)]) if any(
+            len(q) for q in oracle_run["logs"]) else np.zeros((0, 3), np.int32)
+        orc = (sref, eref)
+    out = {"workload": "%s, %d and %d steps from the initial state" % (disk.name, ACC_SHORT,
+                                                                       ACC_LONG)}
+    f100, fe100, f1000, fst = runs["fp64"]
+    if orc is not None:
+        out["fp64"] = {"err_oracle_%d" % ACC_SHORT: _state_err(f100, orc[0]),
+                       "encounters_identical_oracle_%d" % ACC_SHORT: bool(
+                           np.array_equal(fe100, orc[1]))}
+    for name in ("mixed", "double_single"):
+        s100, e100, s1000, st = runs[name]
+        r = {"err_state_%d" % ACC_SHORT: _state_err(s100, f100),
+             "err_state_%d" % ACC_LONG: _state_err(s1000, f1000),
+             "encounters_identical_fp64_%d" % ACC_SHORT: bool(np.array_equal(e100, fe100)),
+             "merges_%d" % ACC_LONG: st["merges"], "merges_fp64_%d" % ACC_LONG: fst["merges"]}
+        if orc is not None:
+            r["err_oracle_%d" % ACC_SHORT] = _state_err(s100, orc[0])
+            r["encounters_identical_oracle_%d" % ACC_SHORT] = bool(np.array_equal(e100, orc[1]))
+        r["bound"] = ("per-body kick error <= 1e-10 |a_i| against the FP64 kick and the oracle "
+                      "(tests); the state errors are set by the encounters' amplification of "
+                      "that difference, to be read against the FP64 run's own oracle error")
+        out[name] = r
+    return out
 
 
 def run_variant(nb, torch, disk, args, precision, ms64, kick64, pps, flush, stream):
@@ -389,15 +557,18 @@ def run_variant(nb, torch, disk, args, precision, ms64, kick64, pps, flush, stre
 
 
 def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=32):
-    """The 4096-system ensemble (N log-uniform in [16, 512]) in one persistent
-    launch per step; speedup against integrating the same systems one at a time
-    through the single-system path, estimated on a random sample of systems."""
+    """The 4096-system ensemble (N log-uniform in [16, 512]): per step an
+    opening, a tiled kick and a closing launch over all systems, replayed from
+    a captured graph in the autotuned shape; speedup against integrating the
+    same systems one at a time through the single-system path, estimated on a
+    random sample of systems."""
     from paper_2604_09184_b300 import ics
     disks = ics.ensemble(n_systems=n_systems)
     pairs = float(sum(d.n * (d.n - 1) for d in disks))
     b = nb.NBodyBatch(nb.params(dt_rcrit=dt), disks)
-    threads, _ = b.autotune(dt)
-    b.set_shape(threads, 25)
+    b.autotune(dt)
+    shape = b.shape()  # threads, steps per graph chunk, kick tile rows, buckets
+    threads, chunk = shape["threads"], shape["chunk"]
     for _ in range(max(args.warmup, 0)):
         b.step(1, dt)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -414,12 +585,15 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
     flush_l2(flush)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(chunk, dt)  # capture the chunk's graph outside the timed call
+    torch.cuda.synchronize()
+    flush_l2(flush)
     e0.record(stream)
-    b.step(2 * 25, dt)
+    b.step(2 * chunk, dt)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 50
-    bal = b.balance()  # the last 25-step launch
+    ms = e0.elapsed_time(e1) / (2 * chunk)
+    bal = b.balance()  # the last close launch
     st = b.stats()
     del b
     # single-system path on a random sample of the same systems
@@ -442,15 +616,23 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
     single_ms = float(np.mean(t_single)) * n_systems
     return {"workload": "ensemble_4096 (N log-uniform 16..512, dt 3 d)", "systems": n_systems,
             "pairs_per_step": pairs, "value": pairs / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms, "steps_per_s": 1e3 / ms, "threads_per_cta": threads,
-            "timing": "one call of 50 steps (2 graph replays of 25-step chunks), L2 flushed before",
+            "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "autotuned_shape": {"threads_per_cta": threads, "steps_per_graph": chunk,
+                                "kick_tile_rows": shape["tile_rows"],
+                                "buckets": shape["buckets"],
+                                "schedule": "per step and bucket (every k-th system of the "
+                                            "largest-first order, its own stream): open (per "
+                                            "system), kick (tiles of %d rows of one system), "
+                                            "close (per system)" % shape["tile_rows"]},
+            "timing": "one call of 2 graph replays of the autotuned chunk, L2 flushed before",
             "ms_per_step_one_call_per_step": ms_call,
             "single_system_path_ms_per_step_est": single_ms, "speedup_vs_single": single_ms / ms,
             "speedup_vs_single_one_call_per_step": single_ms / ms_call,
             "single_sample": int(len(pick)), "bs_substeps": st["bs_substeps"],
             "load_balance": {"efficiency": bal["efficiency"], "ctas": bal["ctas"],
                              "max_cta_ms": bal["max_cta_ms"],
-                             "definition": "sum of CTA busy times / (CTAs x longest), last launch"},
+                             "definition": "sum of CTA busy times / (CTAs x longest), the last "
+                                           "close launch"},
             "groups": st["groups"], "merges": st["merges"]}
 
 
@@ -502,48 +684,116 @@ def run_options(nb, torch, disk, args, ms_plain, flush, stream, steps=3):
     return out
 
 
-def run_adjoint(nb, torch, stream, nsteps=2000, every=100):
-    """Gradient of a loss on the final state of the 2048-planetesimal disk
-    with Jupiter (2000 steps of 6 d) with respect to the initial x, v, m:
+def run_adjoint(nb, torch, stream, nsteps=2000, every=100, fd_steps=100, fd_coords=32):
+    """Gradient of the adjoint workload's loss (the sum of |x|^2 over 16 tagged
+    bodies plus the final total energy, Eqs. Ha-Hc) on the 2048-planetesimal
+    disk with Jupiter (2000 steps of 6 d) with respect to the initial x, v, m:
     checkpointed forward, then the backward pass (segment replays plus the
-    adjoint kernels). Loss: |x|^2 of 16 tagged bodies plus the kinetic energy."""
+    adjoint kernels), both timed with CUDA events on the library's stream,
+    state and cotangents on the device. The energy's cotangent comes from
+    nb_energy_grad. Its error: the same gradient over fd_steps steps against
+    central differences of the forward map (nb_step, bit-identical to the
+    adjoint's forward) on fd_coords sampled entries, two step sizes each."""
     from paper_2604_09184_b300 import ics
     disk = ics.workload("adjoint_2k_j")
     rc = nb_rc_initial(nb, disk)
-    a = nb.NBodyAdjoint(nb.params(dt_rcrit=disk.dt), disk.x, disk.v, disk.m, disk.R, rc,
-                        nsteps, every)
     n = disk.n
+    tagged = 16
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")  # noqa: E731
+    dev = [cu(q) for q in (disk.x, disk.v, disk.m, disk.R, rc)]
 
-    def cotangent():
-        st = a.state()
-        gx = np.zeros((n, 3))
-        gx[:16] = 2.0 * st["x"][:16]
-        return gx, st["m"][:, None] * st["v"], 0.5 * (st["v"] ** 2).sum(1)
+    def cotangent(adj):
+        st = adj.state()
+        gx, gv, gm = nb.energy_grad(st["x"], st["v"], st["m"], st["alive"])
+        gx[:tagged] += 2.0 * st["x"][:tagged]
+        return gx, gv, gm
 
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=disk.dt), *dev, nsteps, every)
     # warm-up on a short run
     a.forward(disk.dt, nsteps=every)
-    a.backward(*cotangent())
+    a.backward(*cotangent(a))
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     e[0].record(stream)
     a.forward(disk.dt)
     e[1].record(stream)
-    torch.cuda.synchronize()
-    g = cotangent()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    g = cotangent(a)
+    e[2].record(stream)
     dx, dv, dm = a.backward(*g)
-    t_bwd = time.perf_counter() - t0
-    fwd_ms = e[0].elapsed_time(e[1])
-    ok = bool(np.isfinite(dx).all() and np.isfinite(dv).all() and np.isfinite(dm).all())
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    ok = bool(torch.isfinite(dx).all() and torch.isfinite(dv).all() and torch.isfinite(dm).all())
     ckpt = (nsteps // every + 2) * (13 * n * 8 + n * 4)
     del a
+    fd = adjoint_fd_error(nb, torch, disk, rc, dev, cotangent, fd_steps, fd_coords, tagged)
     return {"workload": "adjoint_2k_j (2048 planetesimals + Jupiter, dt 6 d)", "n_bodies": n,
-            "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd_ms,
-            "backward_ms": t_bwd * 1e3, "backward_over_forward": t_bwd * 1e3 / fwd_ms,
-            "gradient_steps_per_s": nsteps / t_bwd, "checkpoint_bytes": ckpt,
-            "finite": ok, "timing": "forward: CUDA events; backward: host clock around the "
-            "synchronous nb_adjoint_backward call (includes its host copies of 7n doubles)"}
+            "steps": nsteps, "checkpoint_every": every,
+            "loss": "sum of |x_T|^2 over the first %d bodies + total energy E_T (Eqs. Ha-Hc); "
+                    "gradients w.r.t. all initial x, v, m" % tagged,
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "backward_over_forward": bwd_ms / fwd_ms,
+            "forward_ms_per_step": fwd_ms / nsteps, "backward_ms_per_step": bwd_ms / nsteps,
+            "gradient_steps_per_s": nsteps / (bwd_ms * 1e-3), "checkpoint_bytes": ckpt,
+            "finite": ok, "err_vs_fd": fd,
+            "timing": "CUDA events on the library's stream around nb_adjoint_forward and around "
+                      "nb_adjoint_backward (device cotangents and gradients, no host copies)"}
+
+
+def adjoint_fd_error(nb, torch, disk, rc, dev, cotangent, steps, ncoord, tagged):
+    """Adjoint gradient of the same loss over `steps` steps against central
+    differences of the forward map: per sampled entry the differences at two
+    step sizes (1e-6 and 1e-7 relative; 1e-2 and 1e-3 for masses), the error of
+    the smaller against the adjoint, over their spread plus 1e-7 of the
+    gradient's scale (as in the tests)."""
+    a = nb.NBodyAdjoint(nb.params(dt_rcrit=disk.dt), *dev, steps, 25)
+    a.forward(disk.dt)
+    grads = [t.cpu().numpy() for t in a.backward(*cotangent(a))]
+    del a
+
+    def loss(x, v, m):
+        s = nb.NBodySystem(nb.params(dt_rcrit=disk.dt), x, v, m, disk.R, rc=rc)
+        s.step(steps, disk.dt)
+        st = s.state()
+        tag = st["ids"] < tagged
+        q = s.stats()
+        ev = (q["groups"], q["bs_substeps"], q["merges"], q["encounter_pairs"])
+        return float((st["x"][tag] ** 2).sum() + s.energy_momentum()["E"]), ev
+
+    arrays = (disk.x, disk.v, disk.m)
+    _, ev0 = loss(*arrays)
+    rng = np.random.default_rng(17)
+    worst, ratios, changed = 0.0, [], []
+    for _ in range(ncoord):
+        k = int(rng.integers(0, 3))
+        idx = tuple(int(rng.integers(0, q)) for q in arrays[k].shape)
+        f, same = [], True
+        for rel in ((1e-2, 1e-3) if k == 2 else (1e-6, 1e-7)):
+            h = rel * abs(arrays[k][idx]) or 1e-9
+            plus = [q.copy() for q in arrays]
+            minus = [q.copy() for q in arrays]
+            plus[k][idx] += h
+            minus[k][idx] -= h
+            (lp, ep), (lm, em) = loss(*plus), loss(*minus)
+            f.append((lp - lm) / (2 * h))
+            same = same and ep == ev0 and em == ev0
+        scale = float(np.abs(grads[k]).max())
+        err = abs(f[1] - grads[k][idx])
+        if same:
+            worst = max(worst, err / (abs(f[0] - f[1]) + 1e-7 * scale))
+            ratios.append(err / scale)
+        else:
+            changed.append(err / scale)
+    return {"steps": steps, "entries": ncoord, "entries_same_events": len(ratios),
+            "worst_err_over_bound": worst,
+            "median_err_of_scale": float(np.median(ratios)) if ratios else None,
+            "max_err_of_scale": float(np.max(ratios)) if ratios else None,
+            "entries_other_events": len(changed),
+            "max_err_of_scale_other_events": float(np.max(changed)) if changed else None,
+            "reference": "central differences of nb_step (the adjoint's forward map, bit for bit); "
+                         "bound = spread of the two step sizes + 1e-7 of the gradient's scale; "
+                         "entries whose +-h runs took another direct-solver decision (group, "
+                         "accepted substeps, merger) are reported apart"}
 
 
 def nb_rc_initial(nb, disk):

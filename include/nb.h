@@ -211,12 +211,63 @@ const char* nb_last_error(const nb_system* s);
 const char* nb_status_string(int status);
 
 /* ---------------------------------------------------------------------
+ * Row sharding across ranks (section "Increasing N": large N is the point of
+ * the GPU method, and the O(N^2) kick is split by target rows). Every rank
+ * holds the whole system (the same inputs, so the same state bit for bit)
+ * and calls nb_step with the same arguments. Each rank evaluates the kick,
+ * and the row-wise part of the force update after the direct solver, for
+ * its own block of target rows only; everything else (the O(N) drifts, the
+ * encounter set, the groups, the direct solver, the members' rows) runs on
+ * every rank on identical data. Two exchanges per step join the blocks:
+ *   1. after the trial kick, every rank's flagged pairs (a header of 4 ints,
+ *      count, status, unclipped count, 0, then pair_capacity (i, j) int
+ *      pairs, count of them valid), so that every rank forms the same
+ *      encounter set; a rank's kick error (overflow, a bad coordinate)
+ *      reaches every rank through the status and the step rolls back on all;
+ *   2. after the force update, every rank's rows of the acceleration (three
+ *      blocks of `chunk` doubles, ax, ay, az, zero beyond its last row), so
+ *      that every rank closes the step with the whole force.
+ * The blocks are contiguous: rank r owns rows [r c, min(n, (r + 1) c)),
+ * c = ceil(n / world) (nb_shard_rows). With the same n and kick split the
+ * rows are bit-identical to those of the unsharded kick, so a sharded run
+ * equals nb_step bit for bit for any world size.
+ * --------------------------------------------------------------------- */
+
+/* The exchange: gather `bytes` bytes from every rank's send buffer into recv
+ * (world x bytes, rank r's block at offset r x bytes), both device memory of
+ * this rank, ordered after the work already enqueued on `stream` and before
+ * the work enqueued on it afterwards (an NCCL all-gather on that stream, for
+ * example). Returns 0 on success; anything else fails the step. */
+typedef int (*nb_allgather_fn)(void* user, const void* send, void* recv, size_t bytes,
+                               void* stream);
+
+/* Rows [row0, row1) of rank `rank` out of `world` for n bodies (host
+ * function; an empty block when n < world). NB_E_INVALID for bad arguments. */
+int nb_shard_rows(int n, int rank, int world, int* row0, int* row1);
+
+/* Bytes of exchange buffer (device memory, 256-byte aligned) that
+ * nb_set_shard needs for this system and world size; 0 if invalid. */
+size_t nb_shard_buffer_bytes(const nb_system* s, int world);
+
+/* Shard the system's kick across `world` ranks as rank `rank`, with the
+ * caller's all-gather `fn` (called from inside nb_step with `user`) and an
+ * exchange buffer of nb_shard_buffer_bytes() bytes that stays allocated while
+ * the system is sharded. world = 1 (fn and buf may be NULL) returns to the
+ * unsharded step. Not combinable with rcrit_refresh, gas drag or ejection
+ * (their extra force evaluations are not sharded): NB_E_INVALID. */
+int nb_set_shard(nb_system* s, int rank, int world, nb_allgather_fn fn, void* user, void* buf,
+                 size_t buf_bytes);
+
+/* ---------------------------------------------------------------------
  * Batched ensembles: many independent systems (each its own star and
- * bodies, the same method and parameters) integrated by one persistent
- * launch in which a CTA takes whole systems, largest first, and runs all
- * steps of a chunk with the system in shared memory. Chunks are replayed
- * from a captured CUDA graph. System s owns body slots offsets[s] ..
- * offsets[s+1]-1 of the concatenated arrays; 1 <= N_s <= NB_BATCH_MAX_N.
+ * bodies, the same method and parameters) integrated together. Each step of
+ * every system is three launches: the O(N) opening phase (a CTA takes whole
+ * systems, largest first), the O(N^2) kick over tiles of 128 target rows of
+ * one system, and the closing phase (encounters, groups, Bulirsch-Stoer,
+ * the incremental force update, closing kicks) with a system in shared
+ * memory. Chunks of steps are replayed from a captured CUDA graph. System s
+ * owns body slots offsets[s] .. offsets[s+1]-1 of the concatenated arrays;
+ * 1 <= N_s <= NB_BATCH_MAX_N.
  * --------------------------------------------------------------------- */
 #define NB_BATCH_MAX_N 512
 typedef struct nb_batch nb_batch;
@@ -237,16 +288,32 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
  * nb_step (any error restores the state at entry). */
 int nb_batch_step(nb_batch* b, int nsteps, double dt);
 
-/* Launch shape: threads per CTA (64, 128 or 256) and steps per launch
- * (1..1000). nb_batch_autotune() times each shape on a copy of the state
- * (the state is restored afterwards) and keeps the fastest. */
+/* Launch shape: threads per CTA of the per-system launches (64, 128 or 256)
+ * and steps per captured graph (1..1000). Schedule: target rows per kick
+ * tile (32, 64 or 128) and the number of buckets (1..16), independent chains
+ * of launches on their own streams, each holding every k-th system of the
+ * largest-first order (one bucket's latency-bound direct solver then overlaps
+ * the others' kicks). nb_batch_autotune() times threads, then tile rows x
+ * buckets {1, 4, 8, 16}, then chunks of 10, 25 and 50 steps, on graph replays
+ * of a copy of the state (restored afterwards), and keeps the fastest;
+ * nb_batch_get_shape() reports what is in use. None of these changes a
+ * result: every system's arithmetic is the same in any shape. */
 int nb_batch_set_shape(nb_batch* b, int threads, int chunk);
+int nb_batch_set_schedule(nb_batch* b, int tile_rows, int buckets);
 int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step);
+int nb_batch_get_shape(nb_batch* b, int* threads, int* chunk, int* tile_rows, int* buckets);
 
 /* All slots (offsets layout): x, v [total][3], m, R [total], alive [total]
  * (0 for bodies absorbed by mergers). Any pointer may be NULL. */
 int nb_batch_get_state(nb_batch* b, double* x, double* v, double* m, double* R, int* alive,
                        int out_on_device);
+
+/* Encounter pairs of system `sys` during the last nb_batch_step() call as
+ * (step, i, j) triples, i < j the body's index within the system, sorted by
+ * step then indices (the same list nb_encounter_list gives for that system on
+ * its own). *count receives the total; the library keeps the first 256 per
+ * system and call. NB_E_OVERFLOW when the total exceeds 256 or cap. */
+int nb_batch_encounter_list(nb_batch* b, int sys, int* step_ij, int cap, int* count);
 
 /* Per-system energy (Eqs. Ha + Hb + Hc) and energy removed by mergers, host
  * arrays of nsys. */

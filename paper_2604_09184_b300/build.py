@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnb.so")
 LIB_DEBUG = os.path.join(HERE, "libnb_debug.so")
 SOURCES = ["abi.cu", "kick.cu", "drift.cu", "encounter.cu", "energy.cu", "peaks.cu",
-           "noalloc.cu", "batch.cu", "adjoint.cu", "mathcheck.cu"]
+           "noalloc.cu", "batch.cu", "adjoint.cu", "mathcheck.cu", "shard.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("nb_internal.cuh", "bs.cuh", "kepler.cuh")] + [
     os.path.join(ROOT, "include", "nb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

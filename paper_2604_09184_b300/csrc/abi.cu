@@ -59,6 +59,8 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
   Dev d;
   memset(&d, 0, sizeof(d));
   d.n = n;
+  d.row0 = 0;
+  d.row1 = n;
   d.S = p.kick_split > 0 ? p.kick_split : auto_split(n);
   const int cap = p.pair_capacity > 0 ? p.pair_capacity : (4 * n > 4096 ? 4 * n : 4096);
   d.pair_cap = round_pow2(cap);
@@ -213,8 +215,19 @@ const char* where_name(int w) {
     case 21: return "initial flag set";
     case 22: return "coordinate range of the standalone kick";
     case 30: return "Bulirsch-Stoer";
+    case 70: return "another rank's kick (sharded step)";
+    case 71: return "flagged-pair buffer (sharded step, all ranks together)";
     default: return "device";
   }
+}
+
+// A failed exchange of a sharded step: wait for the enqueued work, restore
+// the state of the call's start and report.
+int shard_fail(nb_system* s, int rc) {
+  cudaStreamSynchronize(s->st);
+  snprintf(s->err, sizeof(s->err), "the all-gather of a sharded step failed (state rolled back)");
+  const int r2 = snapshot(s, 1);
+  return r2 ? r2 : rc;
 }
 
 }  // namespace
@@ -414,6 +427,9 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k], s->st));
       launch_kick(d, s->P, 0, s->st);
       if (s->timing) NB_CU(cudaEventRecord((*s->events)[2 * k + 1], s->st));
+      // sharded: every rank's flagged pairs (nothing when not sharded)
+      rc = shard_exchange(s, 1);
+      if (rc) return shard_fail(s, rc);
     }
     {
       NvtxRange r("encounter set, groups, direct solver (trial half of the force beside it)");
@@ -433,6 +449,9 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       launch_finish_part(d, s->P, 2, s->st);
       launch_scatter(d, s->P, s->st);
       launch_member_kick(d, s->P, s->st);
+      // sharded: every rank's rows of the force (nothing when not sharded)
+      rc = shard_exchange(s, 2);
+      if (rc) return shard_fail(s, rc);
     }
     {
       NvtxRange r("C(h/2) + B(h/2)");
@@ -449,7 +468,8 @@ int nb_step(nb_system* s, int nsteps, double dt) {
   // the direct solver (1 or 2), finish (2 halves), scatter, member re-kick,
   // close; and eject 1, r_crit 1, the force anew 3, gas 2 + 2
   const long long per_step = 8 + bs_launches(d, s->P) + (split ? 1 : 0) + (eject ? 1 : 0) +
-                             (refresh ? 1 : 0) + ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0);
+                             (refresh ? 1 : 0) + ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0) +
+                             (s->shard_world > 1 ? 4 : 0);
   s->launches += (split ? 0 : 1) + per_step * nsteps;
   if (s->timing) {
     for (int k = 0; k < nsteps; ++k) {

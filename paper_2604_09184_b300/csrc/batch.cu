@@ -1,12 +1,23 @@
 // Batched ensembles: thousands of independent systems of uneven N integrated
-// by one persistent launch. A CTA takes a whole system (largest first, from a
-// work counter), loads it into shared memory and runs every step of the chunk
-// there: B(h/2) C(h/2) A(h) C(h/2) B(h/2) with the same kick, flags, Kepler
-// drift, encounter set, groups, Bulirsch-Stoer and mergers as the
-// single-system path (after an encounter only the group members' terms are
-// evaluated again). Systems never interact, so
-// no CTA waits on another. Chunks of steps are replayed from a captured CUDA
-// graph; the launch shape (threads per CTA) comes from the autotuner.
+// together. One step of every system is three launches:
+//   k_batch_open   per system (a CTA takes whole systems, largest first, from
+//                  a work counter): the opening kick B(h/2), C(h/2), the saved
+//                  state and the Kepler drift A(h), O(N) in global memory;
+//   k_batch_kick   the O(N^2) kick and flags at the trial positions, one CTA
+//                  per tile of 128 target rows of one system, the single-system
+//                  kick's pair arithmetic (fixed-point differences, 7 FP64
+//                  instructions per pair) in a lean kernel (64 registers,
+//                  8 CTAs per SM), so the pair loop has the warps to hide its
+//                  integer chain;
+//   k_batch_close  per system: the encounter set, groups, Bulirsch-Stoer with
+//                  mergers and the incremental force update (only the group
+//                  members' terms again) in shared memory, then C(h/2) and the
+//                  closing kick; a system without flagged pairs takes an O(N)
+//                  path in global memory.
+// Systems never interact, so no CTA waits on another. The ensemble's state
+// (~100 B per body) stays in L2 between the launches. Chunks of steps are
+// replayed from a captured CUDA graph; the launch shape (threads of the
+// per-system kernels, steps per chunk) comes from the autotuner.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -27,9 +38,16 @@ struct BatchDev {
   const int* off;    // nsys + 1 body offsets
   const int* order;  // systems, largest first
   double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *ax, *ay, *az;
+  double *xs, *ys, *zs, *vxs, *vys, *vzs;  // saved state of a step (per body slot)
   int* alive;
   unsigned* fprev;  // nsys * BPAIR keys (i << 16 | j), local indices, i < j
   int* nfprev;      // nsys
+  unsigned* ftrial; // nsys * BPAIR keys of the trial kick
+  int* nftrial;     // nsys (unclipped counts)
+  const int2* tiles;  // (system, first row) of each kick tile, largest systems first
+  int ntiles;
+  int* blog;        // nsys * kBatchLogCap * 3: each system's encounter log of the current call
+  int* nblog;       // nsys (unclipped counts)
   double* El;       // nsys: energy removed by mergers
   double* gscr;     // total * bs_stride: BS scratch per body slot
   double* gnew;     // total * 10
@@ -45,6 +63,8 @@ struct BatchDev {
 };
 
 constexpr int kCtaCap = 4096;
+constexpr int kMaxBuckets = 16;  // independent chains of launches (streams) at most
+constexpr int kBatchLogCap = 256;  // encounter-log entries per system per nb_batch_step call
 constexpr int kSpecWarps = 148 * 64;  // resident warps of a full B300 (64 per SM)
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -53,10 +73,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Shared-memory layout for nmax bodies and NT threads.
+// Per-system working set. In shared memory: what the O(N^2) kick loops read
+// (positions as doubles and as 128-bit fixed-point numbers, masses, critical
+// radii), flags, pair lists and group bookkeeping. In global memory (this
+// system's slice of the batch arrays, owned by the CTA for the launch): the
+// arrays of the O(N) phases (velocities, radii, accelerations, the saved
+// state of the step), set per system by batch_system.
 struct BSmem {
-  double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *rc2, *ax, *ay, *az, *xs, *ys, *zs, *vxs, *vys,
-      *vzs;
+  nb_u128 *fX, *fY, *fZ;  // fix_of(x), fix_of(y), fix_of(z), staged before each kick
+  double *x, *y, *z, *m, *rc, *rc2;
+  double *vx, *vy, *vz, *R, *ax, *ay, *az, *xs, *ys, *zs, *vxs, *vys, *vzs;  // global
   double* red;   // 99 doubles (block reductions)
   double* bred;  // NT doubles (BS error reduction)
   int* alive;
@@ -67,19 +93,25 @@ struct BSmem {
 };
 
 __host__ __device__ inline size_t batch_smem_bytes(int nmax, int NT) {
-  return (size_t)19 * nmax * 8 + (size_t)(99 + NT) * 8 + (size_t)nmax * 4 +
-         (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 + (16 + 4 * 32) * 4;
+  return (size_t)3 * nmax * 16 + (size_t)6 * nmax * 8 + (size_t)(99 + NT) * 8 +
+         (size_t)nmax * 4 + (size_t)4 * BPAIR * 4 + (size_t)(4 * nmax + 1) * 4 +
+         (16 + 4 * 32) * 4;
 }
 
 __device__ inline BSmem carve_smem(char* base, int nmax, int NT) {
   BSmem s;
-  double* d = (double*)base;
-  double** arr[] = {&s.x,  &s.y,  &s.z,  &s.vx, &s.vy, &s.vz, &s.m,   &s.R,   &s.rc,  &s.rc2,
-                    &s.ax, &s.ay, &s.az, &s.xs, &s.ys, &s.zs, &s.vxs, &s.vys, &s.vzs};
+  nb_u128* f = (nb_u128*)base;  // 16-byte aligned
+  s.fX = f;
+  s.fY = f + nmax;
+  s.fZ = f + 2 * nmax;
+  double* d = (double*)(f + 3 * nmax);
+  double** arr[] = {&s.x, &s.y, &s.z, &s.m, &s.rc, &s.rc2};
   for (double** a : arr) {
     *a = d;
     d += nmax;
   }
+  s.vx = s.vy = s.vz = s.R = s.ax = s.ay = s.az = nullptr;
+  s.xs = s.ys = s.zs = s.vxs = s.vys = s.vzs = nullptr;
   s.red = d;
   d += 99;
   s.bred = d;
@@ -129,37 +161,91 @@ __device__ void sys_momentum(const BSmem& s, int n, double P[3]) {
   __syncthreads();
 }
 
-// One pair term of Eq. Hb for target i (xi, its rc^2 and rc, hi = high word of
-// its rc^2) and source j: a_i gains G sc (dx, dy, dz). The single-system
-// kernel's pair arithmetic with FP64 differences and r^2 on the integer pipe
-// (the fixed-point differences, which need their positions staged outside
-// shared memory here, measured 3.7 % slower); near ties of r^2 and rc^2 take
-// the FP64 expression, which decides close (r^2 < rc_ij^2) and the weight.
+// One pair term of Eq. Hb for target i and source j: a_i gains G sc (dx, dy,
+// dz). The single-system kick's pair arithmetic: dx, dy, dz and r^2 from the
+// exact differences of the fixed-point positions (integer pipe), m r^-3 from
+// the seeded reciprocal root (4 FP64 instructions); a pair whose r^2 high word
+// is within one unit of the threshold's (hi, the high word of rc_i^2, or
+// rc_j^2's), or coincident, takes the exact branch, which decides close
+// (r^2 < rc_ij^2) and the changeover weight from the FP64 subtractions of
+// the double positions and sep2. The same function serves the tiled kick
+// (global arrays) and the close phase (shared memory), so a term recomputed
+// from the same inputs is the same bits.
 struct KTerm {
   double sc, dx, dy, dz;
   bool close;
 };
-__device__ __forceinline__ KTerm kick_term(double xi, double yi, double zi, double rc2i, double rci,
-                                           int hi, double xj, double yj, double zj, double mj,
-                                           double rc2j, double rcj) {
-  KTerm t;
-  t.dx = xj - xi;
-  t.dy = yj - yi;
-  t.dz = zj - zi;
-  double r2 = sep2_int(t.dx, t.dy, t.dz);
+struct KTarget {
+  nb_u128 X, Y, Z;
+  double rc2;
+  int hi, i;
+};
+// The double positions and rc read only by the exact branch: the target's at
+// (tx, ty, tz, trc)[ti.i], the source's at (xa, ya, za, rca)[j].
+struct KArrays {
+  const double *x, *y, *z, *rc;
+};
+// The integer-pipe part and the far-pair weight; returns whether the pair
+// needs the exact branch.
+__device__ __forceinline__ bool kick_fast(KTerm& t, const KTarget& ti, const nb_u128& Xj,
+                                          const nb_u128& Yj, const nb_u128& Zj, double mj,
+                                          double rc2j) {
+  const FixDiff fx = fix_diff(Xj, ti.X), fy = fix_diff(Yj, ti.Y), fz = fix_diff(Zj, ti.Z);
+  t.dx = fx.d;
+  t.dy = fy.d;
+  t.dz = fz.d;
+  const double r2 = sep2_fix(fx, fy, fz);
   t.sc = scale_fast<NB_PREC_FP64>(r2, mj);
   t.close = false;
-  if (__double2hiint(r2) <= max(hi, __double2hiint(rc2j)) + 1) {
-    r2 = sep2(t.dx, t.dy, t.dz);
-    t.close = r2 < fmax(rc2i, rc2j);
-    if (r2 == 0.0) {
-      t.sc = 0.0;
-    } else if (t.close) {  // a dead source has m = 0: no force either way
-      const double r = sqrt(r2);
-      t.sc = mj * kick_weight(r, fmax(rci, rcj)) / (r2 * r);
-    }
+  return __double2hiint(r2) <= max(ti.hi, __double2hiint(rc2j)) + 1;
+}
+// The exact branch: flag and changeover weight from the FP64 expression.
+__device__ __forceinline__ void kick_rare(KTerm& t, const KTarget& ti, const KArrays& ta,
+                                          double mj, double rc2j, const KArrays& sa, int j) {
+  const int i = ti.i;
+  const double r2e = sep2(sa.x[j] - ta.x[i], sa.y[j] - ta.y[i], sa.z[j] - ta.z[i]);
+  t.close = r2e < fmax(ti.rc2, rc2j);
+  if (r2e == 0.0) {
+    t.sc = 0.0;
+  } else if (t.close) {  // a dead source has m = 0: no force either way
+    const double r = sqrt(r2e);
+    t.sc = mj * kick_weight(r, fmax(ta.rc[i], sa.rc[j])) / (r2e * r);
   }
+}
+__device__ __forceinline__ KTerm kick_term(const KTarget& ti, const KArrays& ta,
+                                           const nb_u128& Xj, const nb_u128& Yj,
+                                           const nb_u128& Zj, double mj, double rc2j,
+                                           const KArrays& sa, int j) {
+  KTerm t;
+  if (kick_fast(t, ti, Xj, Yj, Zj, mj, rc2j)) kick_rare(t, ti, ta, mj, rc2j, sa, j);
   return t;
+}
+
+__device__ __forceinline__ KTarget target_of(const BSmem& s, int i) {
+  KTarget t;
+  t.X = s.fX[i];
+  t.Y = s.fY[i];
+  t.Z = s.fZ[i];
+  t.rc2 = s.rc2[i];
+  t.hi = __double2hiint(t.rc2);
+  t.i = i;
+  return t;
+}
+
+// Source term of body j at its current position (staged fixed point).
+__device__ __forceinline__ KTerm kick_term_j(const KTarget& ti, const BSmem& s, int j) {
+  const KArrays a{s.x, s.y, s.z, s.rc};
+  return kick_term(ti, a, s.fX[j], s.fY[j], s.fZ[j], s.m[j], s.rc2[j], a, j);
+}
+
+// Fixed-point positions of all bodies, from the double positions.
+__device__ void stage_fixed(const BSmem& s, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s.fX[i] = fix_of(s.x[i]);
+    s.fY[i] = fix_of(s.y[i]);
+    s.fZ[i] = fix_of(s.z[i]);
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ void push_flag(unsigned* flist, int* fcount, int* overflow, int i, int j) {
@@ -173,17 +259,16 @@ __device__ __forceinline__ void push_flag(unsigned* flist, int* fcount, int* ove
 // Kick of Eq. Hb and flags for all live targets of the system (ascending j sums).
 __device__ void sys_kick(const BSmem& s, int n, double G, unsigned* flist, int* fcount,
                          int* overflow) {
+  stage_fixed(s, n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (!s.alive[i]) {
       s.ax[i] = s.ay[i] = s.az[i] = 0.0;
       continue;
     }
-    const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
-    const int hi = __double2hiint(rc2i);
+    const KTarget ti = target_of(s, i);
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int j = 0; j < n; ++j) {
-      const KTerm t =
-          kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j], s.rc2[j], s.rc[j]);
+      const KTerm t = kick_term_j(ti, s, j);
       if (t.close && i < j && s.alive[j]) push_flag(flist, fcount, overflow, i, j);
       ax = __fma_rn(t.sc, t.dx, ax);
       ay = __fma_rn(t.sc, t.dy, ay);
@@ -217,18 +302,18 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
     }
     s.ints[1] = kept;
   }
-  __syncthreads();
+  stage_fixed(s, n);  // the members' new positions (the others did not move)
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (!s.alive[i] || s.gidx[i] >= 0) continue;
-    const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
-    const int hi = __double2hiint(rc2i);
+    const KTarget ti = target_of(s, i);
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int k = 0; k < nmem; ++k) {
       const int j = s.gmem[k];
-      const KTerm tn =
-          kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j], s.rc2[j], s.rc[j]);
-      const KTerm tt = kick_term(xi, yi, zi, rc2i, rci, hi, s.xs[j], s.ys[j], s.zs[j], s.vxs[j],
-                                 s.vzs[j], s.vys[j]);
+      const KTerm tn = kick_term_j(ti, s, j);
+      // the trial term: position, mass, rc^2 and rc stashed in xs, ys, zs, vxs, vzs, vys
+      const KArrays ta{s.x, s.y, s.z, s.rc}, tr{s.xs, s.ys, s.zs, s.vys};
+      const KTerm tt = kick_term(ti, ta, fix_of(s.xs[j]), fix_of(s.ys[j]), fix_of(s.zs[j]),
+                                 s.vxs[j], s.vzs[j], tr, j);
       ax = __fma_rn(tn.sc, tn.dx, ax);
       ay = __fma_rn(tn.sc, tn.dy, ay);
       az = __fma_rn(tn.sc, tn.dz, az);
@@ -245,11 +330,9 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
     const int i = s.gmem[k];
     double ax = 0.0, ay = 0.0, az = 0.0;
     if (s.alive[i]) {  // warp-uniform
-      const double xi = s.x[i], yi = s.y[i], zi = s.z[i], rc2i = s.rc2[i], rci = s.rc[i];
-      const int hi = __double2hiint(rc2i);
+      const KTarget ti = target_of(s, i);
       for (int j = lane; j < n; j += 32) {
-        const KTerm t = kick_term(xi, yi, zi, rc2i, rci, hi, s.x[j], s.y[j], s.z[j], s.m[j],
-                                  s.rc2[j], s.rc[j]);
+        const KTerm t = kick_term_j(ti, s, j);
         if (t.close && j != i && s.alive[j] && (s.gidx[j] < 0 || i < j))
           push_flag(s.ft, &s.ints[1], overflow, min(i, j), max(i, j));
         ax = __fma_rn(t.sc, t.dx, ax);
@@ -267,6 +350,96 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
       s.ay[i] = G * ay;
       s.az[i] = G * az;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_batch_kick: the kick of Eq. Hb and the flags at the trial positions for
+// one tile of KBT target rows of one system, against all of the system's
+// bodies (j-tiles of KBT staged in shared memory as fixed-point positions,
+// masses and rc^2): a_i = G sum_j (ascending) sc_ij (dx, dy, dz). Flags (i < j,
+// both live) go to the system's trial list with one atomic each (rare).
+// Registers bounded at 64 for 32 warps per SM whatever the tile: KBT = 32
+// (one warp per CTA; a system of n bodies wastes at most 31 rows), 64 or 128
+// (fewer stagings of the sources per system), chosen by the autotuner.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows[3] = {32, 64, 128};
+constexpr int kMinTileRows = 32;
+
+template <int KBT>
+__global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys P) {
+  __shared__ nb_u128 sX[KBT], sY[KBT], sZ[KBT];
+  __shared__ double sm[KBT], src2[KBT];
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = B.status[0];
+  __syncthreads();
+  if (s_stop) return;
+  const int2 tile = B.tiles[blockIdx.x];
+  const int sys = tile.x;
+  const int base = B.off[sys], n = B.off[sys + 1] - base;
+  const int i = tile.y + threadIdx.x;
+  const bool act = i < n && B.alive[base + i] != 0;
+  KTarget ti;
+  if (act) {
+    ti.X = fix_of(B.x[base + i]);
+    ti.Y = fix_of(B.y[base + i]);
+    ti.Z = fix_of(B.z[base + i]);
+    ti.rc2 = B.rc[base + i] * B.rc[base + i];
+  } else {  // padding row far from everything, never flagged
+    ti.X = ti.Y = ti.Z = fix_of(1e10);
+    ti.rc2 = 0.0;
+  }
+  ti.hi = __double2hiint(ti.rc2);
+  ti.i = act ? i : 0;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int jt = 0; jt < n; jt += KBT) {
+    __syncthreads();
+    const int j = base + jt + threadIdx.x;
+    if (jt + threadIdx.x < n) {
+      sX[threadIdx.x] = fix_of(B.x[j]);
+      sY[threadIdx.x] = fix_of(B.y[j]);
+      sZ[threadIdx.x] = fix_of(B.z[j]);
+      sm[threadIdx.x] = B.m[j];
+      src2[threadIdx.x] = B.rc[j] * B.rc[j];
+    }
+    __syncthreads();
+    const int cnt = min(KBT, n - jt);
+    for (int q = 0; q < cnt; ++q) {
+      KTerm t;
+      const double mj = sm[q], rc2j = src2[q];
+      if (kick_fast(t, ti, sX[q], sY[q], sZ[q], mj, rc2j)) {
+        const KArrays g{B.x + base, B.y + base, B.z + base, B.rc + base};
+        const int jj = jt + q;
+        kick_rare(t, ti, g, mj, rc2j, g, jj);
+        if (t.close && act && i < jj && B.alive[base + jj]) {
+          const int pos = atomicAdd(&B.nftrial[sys], 1);
+          if (pos < BPAIR) B.ftrial[(size_t)sys * BPAIR + pos] = ((unsigned)i << 16) | (unsigned)jj;
+        }
+      }
+      ax = __fma_rn(t.sc, t.dx, ax);
+      ay = __fma_rn(t.sc, t.dy, ay);
+      az = __fma_rn(t.sc, t.dz, az);
+    }
+  }
+  if (i < n) {
+    B.ax[base + i] = act ? P.G * ax : 0.0;
+    B.ay[base + i] = act ? P.G * ay : 0.0;
+    B.az[base + i] = act ? P.G * az : 0.0;
+  }
+}
+
+// After the initial kick: the trial flags become the cached flag set F_prev.
+__global__ void k_batch_fsal(BatchDev B) {
+  const int sys = blockIdx.x;
+  const int raw = B.nftrial[sys];
+  if (raw > BPAIR && threadIdx.x == 0 && atomicCAS(&B.status[0], 0, NB_E_OVERFLOW) == 0)
+    B.status[1] = sys;
+  const int nf = min(raw, BPAIR);
+  for (int k = threadIdx.x; k < nf; k += blockDim.x)
+    B.fprev[(size_t)sys * BPAIR + k] = B.ftrial[(size_t)sys * BPAIR + k];
+  if (threadIdx.x == 0) {
+    B.nfprev[sys] = nf;
+    B.nftrial[sys] = 0;
   }
 }
 
@@ -301,74 +474,128 @@ struct SysTally {
   unsigned long long force_evals, enc_pairs, groups, kepler_iters;
 };
 
-// One system for nsteps steps (nsteps == 0: initial force and flags only).
-__device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, int sys, int nsteps,
-                             double h, BsTally& bt, BsTally& wbt, SysTally& st) {
+// Momentum sum m v over the live bodies of a system in global memory (fixed
+// order: per-thread partial sums, then the block reduction); in all threads.
+__device__ void momentum_g(const BatchDev& B, int base, int n, double* red, double Pt[3]) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    if (!B.alive[g]) continue;
+    a += B.m[g] * B.vx[g];
+    b += B.m[g] * B.vy[g];
+    c += B.m[g] * B.vz[g];
+  }
+  block_sum3(a, b, c, red);
+  if (threadIdx.x == 0) {
+    red[96] = a;
+    red[97] = b;
+    red[98] = c;
+  }
+  __syncthreads();
+  Pt[0] = red[96];
+  Pt[1] = red[97];
+  Pt[2] = red[98];
+  __syncthreads();
+}
+
+// Open phase of one system's step: B(h/2) with the cached force, C(h/2), the
+// saved state (for the direct solver's restart) and the Kepler drift A(h) of
+// every live body to its trial position; the trial flag list is emptied for
+// the kick. Returns NB_E_NOCONV (in every thread) if a Kepler solve failed.
+__device__ int open_system(const BatchDev& B, const Phys& P, double* red, int* flag, int sys,
+                           double h, SysTally& st) {
   const int base = B.off[sys];
   const int n = B.off[sys + 1] - base;
+  const double hh = 0.5 * h;
+  if (threadIdx.x == 0) *flag = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    if (!B.alive[g]) continue;
+    B.vx[g] += hh * B.ax[g];
+    B.vy[g] += hh * B.ay[g];
+    B.vz[g] += hh * B.az[g];
+  }
+  __syncthreads();
+  double Pt[3];
+  momentum_g(B, base, n, red, Pt);
+  unsigned long long kit = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int g = base + i;
+    if (!B.alive[g]) continue;
+    double x = B.x[g] + hh * Pt[0] / P.m0, y = B.y[g] + hh * Pt[1] / P.m0,
+           z = B.z[g] + hh * Pt[2] / P.m0;
+    double vx = B.vx[g], vy = B.vy[g], vz = B.vz[g];
+    B.xs[g] = x; B.ys[g] = y; B.zs[g] = z;
+    B.vxs[g] = vx; B.vys[g] = vy; B.vzs[g] = vz;
+    int it = 0;
+    if (kepler_drift(P.mu, x, y, z, vx, vy, vz, h, P.kepler_max_iter, &it)) *flag = 1;
+    kit += it;
+    B.x[g] = x; B.y[g] = y; B.z[g] = z;
+    B.vx[g] = vx; B.vy[g] = vy; B.vz[g] = vz;
+  }
+  st.kepler_iters += kit;
+  if (threadIdx.x == 0) B.nftrial[sys] = 0;
+  __syncthreads();
+  const int bad = *flag;
+  __syncthreads();
+  return bad ? NB_E_NOCONV : 0;
+}
+
+// Close phase of one system's step, after its trial kick: E = F_prev U F_trial,
+// groups, the direct solver with mergers from the saved state, the force and
+// flags at the final positions (the members' terms again), then C(h/2) and
+// the closing B(h/2). A system with no flagged pair before or after the drift
+// has no encounter: its trial force is the force, and C(h/2) B(h/2) run in
+// global memory.
+__device__ void close_system(const BatchDev& B, const Phys& P, const BSmem& s0, int sys, double h,
+                             BsTally& bt, BsTally& wbt, SysTally& st) {
+  const int base = B.off[sys];
+  const int n = B.off[sys + 1] - base;
+  const double hh = 0.5 * h;
+  const int nfp0 = min(B.nfprev[sys], BPAIR);
+  const int nft_raw = B.nftrial[sys];
+  int err = nft_raw > BPAIR ? NB_E_OVERFLOW : 0;
+  if (!err && nfp0 == 0 && nft_raw == 0) {
+    if (threadIdx.x == 0) st.force_evals += 1;
+    double Pt[3];
+    momentum_g(B, base, n, s0.red, Pt);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int g = base + i;
+      if (!B.alive[g]) continue;
+      B.x[g] += hh * Pt[0] / P.m0;
+      B.y[g] += hh * Pt[1] / P.m0;
+      B.z[g] += hh * Pt[2] / P.m0;
+      B.vx[g] += hh * B.ax[g];
+      B.vy[g] += hh * B.ay[g];
+      B.vz[g] += hh * B.az[g];
+    }
+    __syncthreads();
+    return;
+  }
+  BSmem s = s0;  // the O(N) arrays stay in this system's slice of global memory
+  s.vx = B.vx + base; s.vy = B.vy + base; s.vz = B.vz + base;
+  s.R = B.R + base;
+  s.ax = B.ax + base; s.ay = B.ay + base; s.az = B.az + base;
+  s.xs = B.xs + base; s.ys = B.ys + base; s.zs = B.zs + base;
+  s.vxs = B.vxs + base; s.vys = B.vys + base; s.vzs = B.vzs + base;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int g = base + i;
     s.x[i] = B.x[g]; s.y[i] = B.y[g]; s.z[i] = B.z[g];
-    s.vx[i] = B.vx[g]; s.vy[i] = B.vy[g]; s.vz[i] = B.vz[g];
-    s.m[i] = B.m[g]; s.R[i] = B.R[g]; s.rc[i] = B.rc[g]; s.rc2[i] = B.rc[g] * B.rc[g];
-    s.ax[i] = B.ax[g]; s.ay[i] = B.ay[g]; s.az[i] = B.az[g];
+    s.m[i] = B.m[g]; s.rc[i] = B.rc[g]; s.rc2[i] = B.rc[g] * B.rc[g];
     s.alive[i] = B.alive[g];
   }
-  const int nfp0 = min(B.nfprev[sys], BPAIR);
+  const int nft0 = min(nft_raw, BPAIR);
   for (int k = threadIdx.x; k < nfp0; k += blockDim.x) s.fp[k] = B.fprev[(size_t)sys * BPAIR + k];
+  for (int k = threadIdx.x; k < nft0; k += blockDim.x) s.ft[k] = B.ftrial[(size_t)sys * BPAIR + k];
   if (threadIdx.x == 0) {
     s.ints[0] = nfp0;
+    s.ints[1] = nft0;
     s.ints[4] = 0;
   }
   double El_sys = 0.0;
-  int err = 0;
   __syncthreads();
-  if (nsteps == 0) {
-    if (threadIdx.x == 0) s.ints[1] = 0;
-    __syncthreads();
-    sys_kick(s, n, P.G, s.fp, &s.ints[1], &s.ints[4]);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s.ints[0] = min(s.ints[1], BPAIR);
-      st.force_evals += 1;
-      if (s.ints[4]) err = NB_E_OVERFLOW;
-    }
-    __syncthreads();
-  }
-  const double hh = 0.5 * h;
-  for (int step = 0; step < nsteps; ++step) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      if (!s.alive[i]) continue;
-      s.vx[i] += hh * s.ax[i];
-      s.vy[i] += hh * s.ay[i];
-      s.vz[i] += hh * s.az[i];
-    }
-    __syncthreads();
-    double Pt[3];
-    sys_momentum(s, n, Pt);
-    unsigned long long kit = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      if (!s.alive[i]) continue;
-      double x = s.x[i] + hh * Pt[0] / P.m0, y = s.y[i] + hh * Pt[1] / P.m0,
-             z = s.z[i] + hh * Pt[2] / P.m0;
-      double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
-      s.xs[i] = x; s.ys[i] = y; s.zs[i] = z;
-      s.vxs[i] = vx; s.vys[i] = vy; s.vzs[i] = vz;
-      int it = 0;
-      if (kepler_drift(P.mu, x, y, z, vx, vy, vz, h, P.kepler_max_iter, &it)) s.ints[4] = 2;
-      kit += it;
-      s.x[i] = x; s.y[i] = y; s.z[i] = z;
-      s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
-    }
-    if (threadIdx.x == 0) s.ints[1] = 0;
-    __syncthreads();
-    st.kepler_iters += kit;
-    sys_kick(s, n, P.G, s.ft, &s.ints[1], &s.ints[4]);
-    __syncthreads();
-    if (s.ints[4]) {  // overflow or Kepler failure: stop this system
-      err = s.ints[4] == 2 ? NB_E_NOCONV : NB_E_OVERFLOW;
-      break;
-    }
+  do {
+    if (err) break;
     // E = F_prev U F_trial
     const int nfp = s.ints[0], nft = min(s.ints[1], BPAIR), nk = nfp + nft;
     int P2 = 1;
@@ -384,6 +611,18 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
       s.ints[2] = ne;
       st.force_evals += 1;
       st.enc_pairs += ne;
+      {  // the system's encounter log: (step of this call, i, j) for the pairs of E
+        const int lb = B.nblog[sys];
+        const int step = B.queue[2] - 1;
+        for (int k = 0; k < ne; ++k) {
+          if (lb + k >= kBatchLogCap) break;
+          int* e = B.blog + ((size_t)sys * kBatchLogCap + lb + k) * 3;
+          e[0] = step;
+          e[1] = (int)(s.e[k] >> 16);
+          e[2] = (int)(s.e[k] & 0xffffu);
+        }
+        B.nblog[sys] = lb + ne;
+      }
       // groups: union by the smaller index; groups in ascending order of their
       // smallest member, members ascending
       int ng = 0;
@@ -560,6 +799,9 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
       }
       if (threadIdx.x == 0) st.force_evals += 1;
     }
+  } while (0);
+  if (!err) {
+    double Pt[3];
     const int nf = min(s.ints[1], BPAIR);
     for (int k = threadIdx.x; k < nf; k += blockDim.x) s.fp[k] = s.ft[k];
     if (threadIdx.x == 0) s.ints[0] = nf;
@@ -582,9 +824,7 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int g = base + i;
     B.x[g] = s.x[i]; B.y[g] = s.y[i]; B.z[g] = s.z[i];
-    B.vx[g] = s.vx[i]; B.vy[g] = s.vy[i]; B.vz[g] = s.vz[i];
-    B.m[g] = s.m[i]; B.R[g] = s.R[i]; B.rc[g] = s.rc[i];
-    B.ax[g] = s.ax[i]; B.ay[g] = s.ay[i]; B.az[g] = s.az[i];
+    B.m[g] = s.m[i]; B.rc[g] = s.rc[i];
     B.alive[g] = s.alive[i];
   }
   const int nfp = s.ints[0];
@@ -596,35 +836,64 @@ __device__ void batch_system(const BatchDev& B, const Phys& P, const BSmem& s, i
   __syncthreads();
 }
 
-__global__ void k_batch(BatchDev B, Phys P, int nsteps, double h) {
+// Take the next system from work counter q (largest first); B.nsys when
+// there is none, an error is set, or this CTA ran past its time budget.
+__device__ __forceinline__ int next_system(const BatchDev& B, int* q, unsigned long long t0,
+                                           long long budget, int* s_next) {
+  if (threadIdx.x == 0) {
+    int stop = B.status[0];
+    if (!stop && budget > 0 && (long long)(global_ns() - t0) > budget) {
+      if (atomicCAS(&B.status[0], 0, NB_E_TIMEOUT) == 0) B.status[1] = -1;
+      stop = 1;
+    }
+    *s_next = stop ? B.nsys : atomicAdd(q, 1);
+  }
+  __syncthreads();
+  const int k = *s_next;
+  __syncthreads();
+  return k;
+}
+
+constexpr int kOpenThreads = 128;
+
+__global__ void __launch_bounds__(kOpenThreads) k_batch_open(BatchDev B, Phys P, double h) {
+  __shared__ double red[99];
+  __shared__ int s_next, s_flag;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    B.queue[1] = 0;  // the close launch's counter
+    B.queue[2] += 1;  // steps of this call so far (the encounter log's step)
+  }
+  SysTally st{0, 0, 0, 0};
+  const unsigned long long t0 = global_ns();
+  const long long budget = *B.budget_ns;
+  for (;;) {
+    const int k = next_system(B, &B.queue[0], t0, budget, &s_next);
+    if (k >= B.nsys) break;
+    const int sys = B.order[k];
+    const int err = open_system(B, P, red, &s_flag, sys, h, st);
+    if (err && threadIdx.x == 0 && atomicCAS(&B.status[0], 0, err) == 0) B.status[1] = sys;
+  }
+  unsigned long long kit = st.kepler_iters;
+  for (int o = 16; o > 0; o >>= 1) kit += __shfl_down_sync(0xffffffffu, kit, o);
+  if ((threadIdx.x & 31) == 0 && kit) atomicAdd(&B.stats[ST_KEPLER_ITERS], kit);
+}
+
+__global__ void __launch_bounds__(256, 2) k_batch_close(BatchDev B, Phys P, double h) {
   extern __shared__ __align__(16) char smem_raw[];
   const BSmem s = carve_smem(smem_raw, B.nmax, blockDim.x);
-  __shared__ int s_next, s_stop;
+  __shared__ int s_next;
+  if (blockIdx.x == 0 && threadIdx.x == 0) B.queue[0] = 0;  // the next open launch's counter
   BsTally bt{0, 0, 0, 0};
   BsTally wbt{0, 0, 0, 0};  // warp-team groups (each warp's lane 0 counts its own)
   SysTally st{0, 0, 0, 0};
   const unsigned long long t0 = global_ns();
   const long long budget = *B.budget_ns;
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_stop = B.status[0];
-      // time budget: no new system once this CTA has run longer than allowed
-      if (!s_stop && budget > 0 && (long long)(global_ns() - t0) > budget) {
-        if (atomicCAS(&B.status[0], 0, NB_E_TIMEOUT) == 0) B.status[1] = -1;
-        s_stop = 1;
-      }
-      s_next = s_stop ? B.nsys : atomicAdd(B.queue, 1);
-    }
-    __syncthreads();
-    const int k = s_next;
+    const int k = next_system(B, &B.queue[1], t0, budget, &s_next);
     if (k >= B.nsys) break;
-    batch_system(B, P, s, B.order[k], nsteps, h, bt, wbt, st);
+    close_system(B, P, s, B.order[k], h, bt, wbt, st);
   }
   if (threadIdx.x == 0 && blockIdx.x < B.cta_cap) B.cta_ns[blockIdx.x] = global_ns() - t0;
-  // counters: kepler iterations are per thread; the rest are kept by thread 0
-  unsigned long long kit = st.kepler_iters;
-  for (int o = 16; o > 0; o >>= 1) kit += __shfl_down_sync(0xffffffffu, kit, o);
-  if ((threadIdx.x & 31) == 0 && kit) atomicAdd(&B.stats[ST_KEPLER_ITERS], kit);
   if ((threadIdx.x & 31) == 0 && (wbt.substeps || wbt.derivs || wbt.halvings || wbt.merges)) {
     atomicAdd(&B.stats[ST_BS_SUBSTEPS], (unsigned long long)wbt.substeps);
     atomicAdd(&B.stats[ST_BS_HALVINGS], (unsigned long long)wbt.halvings);
@@ -755,8 +1024,16 @@ struct Snap {
   unsigned long long* stats;
 };
 
-size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDev* out,
-                    Snap* snap, double** eout, double** stage) {
+// Kick tiles of `rows` target rows for systems of the given sizes (the
+// layout holds the count for the smallest tile).
+int count_tiles(int nsys, const int* offsets, int rows = kMinTileRows) {
+  long long t = 0;
+  for (int s = 0; s < nsys; ++s) t += (offsets[s + 1] - offsets[s] + rows - 1) / rows;
+  return (int)t;
+}
+
+size_t batch_layout(const nb_params& p, int nsys, int total, int ntiles, char* base,
+                    BatchDev* out, Snap* snap, double** eout, double** stage) {
   BatchDev d;
   memset(&d, 0, sizeof(d));
   d.nsys = nsys;
@@ -767,13 +1044,21 @@ size_t batch_layout(const nb_params& p, int nsys, int total, char* base, BatchDe
   d.order = c.take<int>(nsys);
   double** arr[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.m, &d.R, &d.rc, &d.ax, &d.ay, &d.az};
   for (double** a : arr) *a = c.take<double>(total);
+  double** sav[] = {&d.xs, &d.ys, &d.zs, &d.vxs, &d.vys, &d.vzs};
+  for (double** a : sav) *a = c.take<double>(total);
   d.alive = c.take<int>(total);
   d.fprev = c.take<unsigned>((size_t)nsys * BPAIR);
   d.nfprev = c.take<int>(nsys);
+  d.ftrial = c.take<unsigned>((size_t)nsys * BPAIR);
+  d.nftrial = c.take<int>(nsys);
+  d.tiles = c.take<int2>(ntiles);
+  d.ntiles = ntiles;
+  d.blog = c.take<int>((size_t)nsys * kBatchLogCap * 3);
+  d.nblog = c.take<int>(nsys);
   d.El = c.take<double>(nsys);
   d.gscr = c.take<double>((size_t)total * d.bs_stride);
   d.gnew = c.take<double>((size_t)total * 10);
-  d.queue = c.take<int>(4);
+  d.queue = c.take<int>(4 * kMaxBuckets);  // per chain: open, close counters, step count
   d.status = c.take<int>(4);
   d.stats = c.take<unsigned long long>(kStatN);
   d.cta_ns = c.take<unsigned long long>(kCtaCap);
@@ -813,6 +1098,18 @@ struct nb_batch {
   double g_dt;
   int last_grid;  // CTAs of the last launch (for nb_batch_balance)
   long long steps_done;
+  long long call_base;  // steps done when the last nb_batch_step call started
+  // schedule: kick tile rows and the number of buckets, independent chains of
+  // open/kick/close launches on their own streams (systems never interact, so
+  // one bucket's slow direct solver overlaps the others' kicks)
+  int tile_rows, buckets;
+  int g_tile_rows, g_buckets;           // of the captured graph
+  int arr_tile_rows, arr_buckets;       // of the order and tile arrays on the device
+  int bk_sys0[kMaxBuckets + 1], bk_tile0[kMaxBuckets + 1];
+  int* h_off;    // host copies: offsets (nsys + 1) and the largest-first order (nsys)
+  int* h_order;
+  cudaStream_t bst[kMaxBuckets];
+  cudaEvent_t ev_fork, ev_join[kMaxBuckets];
   char err[256];
 };
 
@@ -839,7 +1136,7 @@ Phys phys_of(const nb_params& p) {
   return P;
 }
 
-int batch_grid(const nb_batch* b) {
+int batch_grid(const nb_batch* b, int nsys) {
   int dev = 0, sms = 148, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -849,21 +1146,121 @@ int batch_grid(const nb_batch* b) {
   if (per_sm > by_threads) per_sm = by_threads;
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
-  if (grid > b->d.nsys) grid = b->d.nsys;
+  if (grid > nsys) grid = nsys;
   if (grid > kCtaCap) grid = kCtaCap;  // per-CTA timings (cta_ns) exist for kCtaCap CTAs
   return grid;
 }
 
-int launch_batch(nb_batch* b, int nsteps, double dt) {
+int open_grid(const nb_batch* b, int nsys) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms * (2048 / kOpenThreads);
+  return grid > nsys ? nsys : grid;
+}
+
+// Order and kick-tile arrays for a schedule: the system at position k of the
+// largest-first order goes to bucket k % buckets, so every bucket holds the
+// same spread of sizes; within a bucket systems (and their tiles of `rows`
+// target rows) stay largest first.
+int arrange(nb_batch* b, int rows, int buckets) {
+  if (b->arr_tile_rows == rows && b->arr_buckets == buckets) return NB_OK;
+  const int nsys = b->d.nsys;
+  std::vector<int> order;
+  std::vector<int2> tiles;
+  order.reserve(nsys);
+  for (int q = 0; q < buckets; ++q) {
+    b->bk_sys0[q] = (int)order.size();
+    b->bk_tile0[q] = (int)tiles.size();
+    for (int k = q; k < nsys; k += buckets) {
+      const int sys = b->h_order[k], n = b->h_off[sys + 1] - b->h_off[sys];
+      order.push_back(sys);
+      for (int i0 = 0; i0 < n; i0 += rows) tiles.push_back(make_int2(sys, i0));
+    }
+  }
+  b->bk_sys0[buckets] = (int)order.size();
+  b->bk_tile0[buckets] = (int)tiles.size();
+  NB_BCU(cudaMemcpyAsync((void*)b->d.order, order.data(), sizeof(int) * order.size(),
+                         cudaMemcpyHostToDevice, b->st));
+  NB_BCU(cudaMemcpyAsync((void*)b->d.tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                         cudaMemcpyHostToDevice, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  b->arr_tile_rows = rows;
+  b->arr_buckets = buckets;
+  return NB_OK;
+}
+
+template <int KT>
+void launch_kick_t(const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st) {
+  if (ntiles > 0) k_batch_kick<KT><<<ntiles, KT, 0, st>>>(d, P);
+}
+void launch_kick_rows(int rows, const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st) {
+  if (rows == 32)
+    launch_kick_t<32>(d, P, ntiles, st);
+  else if (rows == 64)
+    launch_kick_t<64>(d, P, ntiles, st);
+  else
+    launch_kick_t<128>(d, P, ntiles, st);
+}
+
+// nsteps steps of every system on stream st: per step and bucket the open,
+// kick and close launches, the buckets forked onto their own streams and
+// joined back into st. nsteps == 0: the initial force and flags (the tiled
+// kick over all systems, then its flags become F_prev).
+int enqueue_steps(nb_batch* b, int nsteps, double dt, cudaStream_t st) {
+  int rc = arrange(b, b->tile_rows, b->buckets);
+  if (rc) return rc;
+  if (nsteps == 0) {
+    NB_BCU(cudaMemsetAsync(b->d.nftrial, 0, sizeof(int) * b->d.nsys, st));
+    launch_kick_rows(b->tile_rows, b->d, b->P, b->bk_tile0[b->buckets], st);
+    k_batch_fsal<<<b->d.nsys, 128, 0, st>>>(b->d);
+    NB_BCU(cudaGetLastError());
+    return NB_OK;
+  }
   b->smem = batch_smem_bytes(b->d.nmax, b->threads);
-  NB_BCU(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NB_BCU(cudaFuncSetAttribute(k_batch_close, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)b->smem));
-  NB_BCU(cudaMemsetAsync(b->d.queue, 0, sizeof(int), b->st));
-  b->last_grid = batch_grid(b);
-  k_batch<<<b->last_grid, b->threads, b->smem, b->st>>>(b->d, b->P, nsteps, dt);
+  const int nb = b->buckets;
+  if (nb > 1) {
+    NB_BCU(cudaEventRecord(b->ev_fork, st));
+    for (int q = 0; q < nb; ++q) NB_BCU(cudaStreamWaitEvent(b->bst[q], b->ev_fork, 0));
+  }
+  for (int q = 0; q < nb; ++q) {
+    cudaStream_t sq = nb > 1 ? b->bst[q] : st;
+    BatchDev dq = b->d;
+    dq.order = b->d.order + b->bk_sys0[q];
+    dq.nsys = b->bk_sys0[q + 1] - b->bk_sys0[q];
+    dq.tiles = b->d.tiles + b->bk_tile0[q];
+    dq.ntiles = b->bk_tile0[q + 1] - b->bk_tile0[q];
+    dq.queue = b->d.queue + 4 * q;
+    dq.cta_ns = b->d.cta_ns + (size_t)q * (kCtaCap / kMaxBuckets);
+    dq.cta_cap = kCtaCap / kMaxBuckets;
+    // concurrent close launches must not share a warp's speculation scratch
+    // (indexed by CTA and warp): each bucket takes its own slice; warps beyond
+    // it attempt one substep size at a time (the same results)
+    dq.spec_cap = kSpecWarps / nb;
+    dq.spec = b->d.spec + (size_t)q * dq.spec_cap * 4 * b->d.bs_stride;
+    if (dq.nsys == 0) continue;
+    const int ga = open_grid(b, dq.nsys), gc = batch_grid(b, dq.nsys);
+    NB_BCU(cudaMemsetAsync(dq.queue, 0, 2 * sizeof(int), sq));
+    for (int k = 0; k < nsteps; ++k) {
+      k_batch_open<<<ga, kOpenThreads, 0, sq>>>(dq, b->P, dt);
+      launch_kick_rows(b->tile_rows, dq, b->P, dq.ntiles, sq);
+      k_batch_close<<<gc, b->threads, b->smem, sq>>>(dq, b->P, dt);
+    }
+    if (q == 0) b->last_grid = gc < dq.cta_cap ? gc : dq.cta_cap;
+  }
+  if (nb > 1) {
+    for (int q = 0; q < nb; ++q) {
+      NB_BCU(cudaEventRecord(b->ev_join[q], b->bst[q]));
+      NB_BCU(cudaStreamWaitEvent(st, b->ev_join[q], 0));
+    }
+  }
   NB_BCU(cudaGetLastError());
   return NB_OK;
 }
+
+int launch_batch(nb_batch* b, int nsteps, double dt) { return enqueue_steps(b, nsteps, dt, b->st); }
 
 int batch_snapshot(nb_batch* b, int dir) {
   const BatchDev& d = b->d;
@@ -896,28 +1293,29 @@ int run_steps(nb_batch* b, int nsteps, double dt) {
   const int chunk = b->chunk;
   const int full = nsteps / chunk, rem = nsteps - full * chunk;
   if (full > 0) {
-    if (!b->gexec || b->g_threads != b->threads || b->g_chunk != chunk || b->g_dt != dt) {
+    if (!b->gexec || b->g_threads != b->threads || b->g_chunk != chunk || b->g_dt != dt ||
+        b->g_tile_rows != b->tile_rows || b->g_buckets != b->buckets) {
+      int rca = arrange(b, b->tile_rows, b->buckets);  // before the capture (host copies)
+      if (rca) return rca;
       if (b->gexec) cudaGraphExecDestroy(b->gexec);
       b->gexec = nullptr;
-      // capture one chunk: reset the work counter, run `chunk` steps
-      b->smem = batch_smem_bytes(b->d.nmax, b->threads);
-      NB_BCU(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)b->smem));
-      const int grid = batch_grid(b);
+      // capture one chunk: reset the work counters, `chunk` steps of three launches
       if (!b->cap) NB_BCU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
       cudaGraph_t g;
       NB_BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-      cudaMemsetAsync(b->d.queue, 0, sizeof(int), b->cap);
-      k_batch<<<grid, b->threads, b->smem, b->cap>>>(b->d, b->P, chunk, dt);
-      NB_BCU(cudaStreamEndCapture(b->cap, &g));
+      const int rcq = enqueue_steps(b, chunk, dt, b->cap);
+      const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+      if (rcq) return rcq;
+      NB_BCU(ec);
       NB_BCU(cudaGraphInstantiate(&b->gexec, g, 0));
       cudaGraphDestroy(g);
       b->g_threads = b->threads;
       b->g_chunk = chunk;
       b->g_dt = dt;
+      b->g_tile_rows = b->tile_rows;
+      b->g_buckets = b->buckets;
     }
     for (int k = 0; k < full; ++k) NB_BCU(cudaGraphLaunch(b->gexec, b->st));
-    b->last_grid = batch_grid(b);
   }
   if (rem > 0) {
     const int rc = launch_batch(b, rem, dt);
@@ -938,7 +1336,8 @@ size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets
     const int n = offsets[s + 1] - offsets[s];
     if (n < 1 || n > NB_BATCH_MAX_N) return 0;
   }
-  return batch_layout(*p, nsys, offsets[nsys], nullptr, nullptr, nullptr, nullptr, nullptr);
+  return batch_layout(*p, nsys, offsets[nsys], count_tiles(nsys, offsets), nullptr, nullptr,
+                      nullptr, nullptr, nullptr);
 }
 
 int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offsets,
@@ -957,7 +1356,8 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
   b->st = (cudaStream_t)stream;
   const int total = offsets[nsys];
   double* stage = nullptr;
-  batch_layout(*p, nsys, total, (char*)workspace, &b->d, &b->snap, &b->E, &stage);
+  batch_layout(*p, nsys, total, count_tiles(nsys, offsets), (char*)workspace, &b->d, &b->snap,
+               &b->E, &stage);
   // host bookkeeping: max N and the largest-first order
   std::vector<int> order(nsys);
   int nmax = 1;
@@ -971,16 +1371,33 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
   b->d.nmax = nmax;
   b->threads = 128;
   b->chunk = 25;
+  b->tile_rows = 32;
+  b->buckets = 4;
+  b->h_off = (int*)malloc(sizeof(int) * (nsys + 1));
+  b->h_order = (int*)malloc(sizeof(int) * nsys);
+  if (!b->h_off || !b->h_order) {
+    nb_batch_destroy(b);
+    return NB_E_INVALID;
+  }
+  memcpy(b->h_off, offsets, sizeof(int) * (nsys + 1));
+  memcpy(b->h_order, order.data(), sizeof(int) * nsys);
   int rc = NB_OK;
   do {
     if (cudaMemcpyAsync((void*)b->d.off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice,
                         b->st) != cudaSuccess ||
-        cudaMemcpyAsync((void*)b->d.order, order.data(), sizeof(int) * nsys,
-                        cudaMemcpyHostToDevice, b->st) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
       rc = NB_E_CUDA;
       break;
     }
+    for (int q = 0; q < kMaxBuckets && rc == NB_OK; ++q)
+      if (cudaStreamCreateWithFlags(&b->bst[q], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[q], cudaEventDisableTiming) != cudaSuccess)
+        rc = NB_E_CUDA;
+    if (rc) break;
     cudaMemsetAsync(b->d.nfprev, 0, sizeof(int) * nsys, b->st);
+    cudaMemsetAsync(b->d.nftrial, 0, sizeof(int) * nsys, b->st);
+    cudaMemsetAsync(b->d.nblog, 0, sizeof(int) * nsys, b->st);
+    cudaMemsetAsync(b->d.queue, 0, 4 * kMaxBuckets * sizeof(int), b->st);
     cudaMemsetAsync(b->d.El, 0, sizeof(double) * nsys, b->st);
     cudaMemsetAsync(b->d.status, 0, 4 * sizeof(int), b->st);
     cudaMemsetAsync(b->d.stats, 0, sizeof(unsigned long long) * kStatN, b->st);
@@ -1031,6 +1448,10 @@ int nb_batch_step(nb_batch* b, int nsteps, double dt) {
   NvtxRange range("nb_batch_step");
   int rc = batch_snapshot(b, 0);
   if (rc) return rc;
+  // the encounter logs cover this call
+  b->call_base = b->steps_done;
+  NB_BCU(cudaMemsetAsync(b->d.nblog, 0, sizeof(int) * b->d.nsys, b->st));
+  NB_BCU(cudaMemsetAsync(b->d.queue, 0, 4 * kMaxBuckets * sizeof(int), b->st));
   rc = run_steps(b, nsteps, dt);
   if (rc) return rc;
   int st2[2];
@@ -1075,46 +1496,108 @@ int nb_batch_balance(nb_batch* b, double* efficiency, double* max_cta_ms, int* c
   return NB_OK;
 }
 
+namespace {
+// ms per step of `steps` steps on graph replays in the current shape (the
+// first chunk captures and warms up, untimed); the state is restored after.
+int time_graph(nb_batch* b, int steps, double dt, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+  int rc = run_steps(b, b->chunk, dt);
+  if (rc) return rc;
+  NB_BCU(cudaEventRecord(e0, b->st));
+  rc = run_steps(b, steps, dt);
+  if (rc) return rc;
+  NB_BCU(cudaEventRecord(e1, b->st));
+  NB_BCU(cudaEventSynchronize(e1));
+  float t = 0.f;
+  NB_BCU(cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / steps;
+  return batch_snapshot(b, 1);
+}
+}  // namespace
+
 int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step) {
   if (!b || !std::isfinite(dt)) return NB_E_INVALID;
-  const int shapes[3] = {64, 128, 256};
-  const int probe = 2;
-  const int keep_t = b->threads, keep_c = b->chunk;
-  double best = 1e30;
-  int best_t = keep_t;
+  // Each trial runs on a copy of the state (restored after it), timed on
+  // graph replays: (1) threads of the per-system launches; (2) the schedule,
+  // kick tile rows x independent buckets of systems; (3) steps per graph.
+  const int keep_t = b->threads, keep_c = b->chunk, keep_r = b->tile_rows, keep_k = b->buckets;
   int rc = batch_snapshot(b, 0);
   if (rc) return rc;
   cudaEvent_t e0, e1;
   NB_BCU(cudaEventCreate(&e0));
   NB_BCU(cudaEventCreate(&e1));
-  for (int t : shapes) {
+  double best = 1e30, ms = 0.0;
+  int bt_ = keep_t, br = keep_r, bk = keep_k, bc = keep_c;
+  b->chunk = 10;
+  for (int t : {64, 128, 256}) {
     b->threads = t;
-    b->chunk = probe;
-    rc = launch_batch(b, 1, dt);  // warm-up
-    if (rc) break;
-    NB_BCU(cudaEventRecord(e0, b->st));
-    rc = launch_batch(b, probe, dt);
-    if (rc) break;
-    NB_BCU(cudaEventRecord(e1, b->st));
-    NB_BCU(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    NB_BCU(cudaEventElapsedTime(&ms, e0, e1));
-    const double per = ms / probe;
-    if (per < best) {
-      best = per;
-      best_t = t;
+    if ((rc = time_graph(b, 10, dt, e0, e1, &ms))) break;
+    if (ms < best) { best = ms; bt_ = t; }
+  }
+  b->threads = bt_;
+  for (int r = 0; r < 3 && !rc; ++r) {
+    for (int k : {1, 4, 8, 16}) {
+      b->tile_rows = kTileRows[r];
+      b->buckets = k;
+      if ((rc = time_graph(b, 10, dt, e0, e1, &ms))) break;
+      if (ms < best) { best = ms; br = kTileRows[r]; bk = k; }
     }
-    rc = batch_snapshot(b, 1);  // restore the state after every trial
+  }
+  b->tile_rows = br;
+  b->buckets = bk;
+  for (int c : {10, 25, 50}) {
     if (rc) break;
+    b->chunk = c;
+    if ((rc = time_graph(b, c, dt, e0, e1, &ms))) break;
+    if (ms < best) { best = ms; bc = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   NB_BCU(cudaStreamSynchronize(b->st));
-  b->threads = rc ? keep_t : best_t;
-  b->chunk = keep_c;
+  if (rc) {
+    b->threads = keep_t; b->chunk = keep_c; b->tile_rows = keep_r; b->buckets = keep_k;
+    batch_snapshot(b, 1);
+    return rc;
+  }
+  b->chunk = bc;
   if (threads) *threads = b->threads;
   if (ms_per_step) *ms_per_step = best;
-  return rc;
+  return NB_OK;
+}
+
+int nb_batch_set_schedule(nb_batch* b, int tile_rows, int buckets) {
+  if (!b || (tile_rows != 32 && tile_rows != 64 && tile_rows != 128) || buckets < 1 ||
+      buckets > kMaxBuckets)
+    return NB_E_INVALID;
+  b->tile_rows = tile_rows;
+  b->buckets = buckets;
+  return NB_OK;
+}
+
+int nb_batch_encounter_list(nb_batch* b, int sys, int* step_ij, int cap, int* count) {
+  if (!b || sys < 0 || sys >= b->d.nsys || cap < 0 || (cap > 0 && !step_ij)) return NB_E_INVALID;
+  int total = 0;
+  NB_BCU(cudaMemcpyAsync(&total, b->d.nblog + sys, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  NB_BCU(cudaStreamSynchronize(b->st));
+  if (count) *count = total;
+  const int stored = total < kBatchLogCap ? total : kBatchLogCap;
+  const int k = stored < cap ? stored : cap;
+  if (k > 0) {
+    NB_BCU(cudaMemcpyAsync(step_ij, b->d.blog + (size_t)sys * kBatchLogCap * 3,
+                           sizeof(int) * 3 * k, cudaMemcpyDeviceToHost, b->st));
+    NB_BCU(cudaStreamSynchronize(b->st));
+    for (int q = 0; q < k; ++q) step_ij[3 * q] += (int)b->call_base;
+  }
+  if (total > kBatchLogCap) return NB_E_OVERFLOW;
+  return total > cap ? NB_E_OVERFLOW : NB_OK;
+}
+
+int nb_batch_get_shape(nb_batch* b, int* threads, int* chunk, int* tile_rows, int* buckets) {
+  if (!b) return NB_E_INVALID;
+  if (threads) *threads = b->threads;
+  if (chunk) *chunk = b->chunk;
+  if (tile_rows) *tile_rows = b->tile_rows;
+  if (buckets) *buckets = b->buckets;
+  return NB_OK;
 }
 
 int nb_batch_get_state(nb_batch* b, double* x, double* v, double* m, double* R, int* alive,
@@ -1174,6 +1657,13 @@ void nb_batch_destroy(nb_batch* b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int q = 0; q < kMaxBuckets; ++q) {
+    if (b->bst[q]) cudaStreamDestroy(b->bst[q]);
+    if (b->ev_join[q]) cudaEventDestroy(b->ev_join[q]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  free(b->h_off);
+  free(b->h_order);
   free(b);
 }
 

@@ -420,8 +420,8 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   A.n = d.n;
   A.S = d.S;
   A.jchunk = jchunk_for(d.n, d.S);
-  A.ib = 0;
-  A.ie = d.n;
+  A.ib = d.row0;  // this rank's rows when sharded, else all
+  A.ie = d.row1;
   A.cond = nullptr;
   A.x = d.x; A.y = d.y; A.z = d.z; A.m = d.m; A.rc = d.rc; A.rc2 = d.rc2;
   A.kpart = d.kpart;
@@ -489,8 +489,9 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
   if (s_stop) return;
   const int n = d.n;
   const int i = blockIdx.x * FNT + threadIdx.x;
+  const bool row = i >= d.row0 && i < d.row1;  // this rank's rows (all unless sharded)
   double ax = 0.0, ay = 0.0, az = 0.0;
-  if (i < n) {
+  if (row) {
     if (PH == 2) {  // the trial half's result
       ax = d.ax[i]; ay = d.ay[i]; az = d.az[i];
     } else {
@@ -503,7 +504,7 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
     }
   }
   const int M = s_M;
-  const bool delta = (i < n) && M > 0 && d.member_slot[i] < 0 && d.alive[i];
+  const bool delta = row && M > 0 && d.member_slot[i] < 0 && d.alive[i];
   double xi = 0.0, yi = 0.0, zi = 0.0, rci = 0.0, rc2i = 0.0;
   if (delta) {
     xi = d.x[i]; yi = d.y[i]; zi = d.z[i]; rci = d.rc[i]; rc2i = d.rc2[i];
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
       }
     }
   }
-  if (i < n) {
+  if (row) {
     if (PH == 1) {
       d.ax[i] = ax + cx;
       d.ay[i] = ay + cy;

@@ -75,6 +75,8 @@ struct Dev {
   int member_cap; // group-member capacity (= n)
   int bs_kmax;
   int ppart_n;    // blocks of the O(N) kernels (P partial sums)
+  int row0, row1; // target rows of the kick and of the row-wise force finish: [0, n)
+                  // unless the system is sharded across ranks (nb_set_shard)
   double *x, *y, *z, *vx, *vy, *vz, *m, *R, *rc, *rc2, *ax, *ay, *az;
   double *xs, *ys, *zs, *vxs, *vys, *vzs;  // saved state after C(h/2)
   int *id, *alive, *member_slot, *uf;
@@ -661,4 +663,16 @@ struct nb_system {
   double kick_ms;
   long long kick_launches;
   long long launches;
+  // row sharding across ranks (nb_set_shard): this rank's block of target
+  // rows, the caller's all-gather and the exchange buffers (caller memory)
+  int shard_rank, shard_world, shard_chunk;
+  nb_allgather_fn shard_fn;
+  void* shard_user;
+  char* shard_buf;
 };
+
+namespace nb {
+// The all-gather of a sharded step: 1 = the trial kick's flagged pairs of
+// every rank, 2 = every rank's rows of the force (nothing when unsharded).
+int shard_exchange(nb_system* s, int which);
+}  // namespace nb

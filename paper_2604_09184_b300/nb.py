@@ -55,6 +55,10 @@ class NbStats(C.Structure):
         ("m_ejected", C.c_double), ("ml_substeps", C.c_longlong), ("ml_groups", C.c_longlong)]
 
 
+# nb_allgather_fn: int (*)(void* user, const void* send, void* recv, size_t bytes, void* stream)
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
 class NbError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("%s (%d): %s" % (status_string(code), code, msg))
@@ -109,6 +113,14 @@ def lib():
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_int, _I, C.c_void_p]
         L.nb_kepler_drift.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int, C.c_void_p, C.c_void_p]
+        L.nb_shard_rows.argtypes = [C.c_int, C.c_int, C.c_int, _I, _I]
+        L.nb_shard_buffer_bytes.argtypes = [C.c_void_p, C.c_int]
+        L.nb_shard_buffer_bytes.restype = C.c_size_t
+        L.nb_set_shard.argtypes = [C.c_void_p, C.c_int, C.c_int, ALLGATHER_FN, C.c_void_p,
+                                   C.c_void_p, C.c_size_t]
+        L.nb_batch_get_shape.argtypes = [C.c_void_p, _I, _I, _I, _I]
+        L.nb_batch_set_schedule.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.nb_batch_encounter_list.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, _I]
         L.nb_energy_grad_scratch_bytes.argtypes = [C.c_int]
         L.nb_energy_grad_scratch_bytes.restype = C.c_size_t
         L.nb_energy_grad.argtypes = [C.c_int] + [C.c_void_p] * 4 + [C.c_double, C.c_double] + [
@@ -407,6 +419,31 @@ class NBodyBatch:
         t, ms = C.c_int(), C.c_double()
         self._check(lib().nb_batch_autotune(self._h, dt, C.byref(t), C.byref(ms)))
         return t.value, ms.value
+
+    def encounter_list(self, s: int) -> np.ndarray:
+        """(step, i, j) encounter pairs of system s during the last step() call
+        (i < j, indices within the system)."""
+        cnt = C.c_int()
+        code = lib().nb_batch_encounter_list(self._h, int(s), None, 0, C.byref(cnt))
+        if code not in (NB_OK, NB_E_OVERFLOW):
+            self._check(code)
+        out = np.zeros((cnt.value, 3), dtype=np.int32)
+        if cnt.value:
+            self._check(lib().nb_batch_encounter_list(self._h, int(s),
+                                                      C.c_void_p(out.ctypes.data), cnt.value,
+                                                      C.byref(cnt)))
+        return out
+
+    def shape(self) -> dict:
+        """The launch shape and schedule in use: threads per CTA, steps per
+        graph chunk, kick tile rows and buckets of independent launch chains."""
+        t, c, r, k = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().nb_batch_get_shape(self._h, C.byref(t), C.byref(c), C.byref(r),
+                                             C.byref(k)))
+        return {"threads": t.value, "chunk": c.value, "tile_rows": r.value, "buckets": k.value}
+
+    def set_schedule(self, tile_rows: int, buckets: int):
+        self._check(lib().nb_batch_set_schedule(self._h, int(tile_rows), int(buckets)))
 
     def state(self) -> dict:
         n = self.total

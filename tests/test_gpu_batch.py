@@ -55,6 +55,7 @@ def test_batch_matches_oracle_per_system():
     for k, (d, ref) in enumerate(zip(disks, refs)):
         sg, sr = b.system_state(k, st), ref.state()
         assert np.array_equal(sg["ids"], sr["ids"])
+        assert np.array_equal(b.encounter_list(k), ref.encounter_list()), k
         rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
         assert rel.max() <= 1e-12, (k, d.n, rel.max())
         assert np.allclose(sg["m"], sr["m"], rtol=1e-15, atol=0)
@@ -79,6 +80,7 @@ def test_batch_with_encounters_and_mergers():
     for k, ref in enumerate(refs):
         sg, sr = b.system_state(k, st), ref.state()
         assert np.array_equal(sg["ids"], sr["ids"])
+        assert np.array_equal(b.encounter_list(k), ref.encounter_list()), k
         rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
         assert rel.max() <= 1e-11, (k, rel.max())
         em = ref.energy_momentum()
@@ -115,6 +117,7 @@ def test_batch_force_update_after_encounters_both_branches():
     for k, ref in enumerate(refs):
         sg, sr = b.system_state(k, st), ref.state()
         assert np.array_equal(sg["ids"], sr["ids"])
+        assert np.array_equal(b.encounter_list(k), ref.encounter_list()), k
         rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
         assert rel.max() <= 1e-11, (k, rel.max())
         relv = np.linalg.norm(sg["v"] - sr["v"], axis=1) / np.linalg.norm(sr["v"], axis=1)
@@ -285,3 +288,28 @@ def test_batch_size_extremes_match_oracle():
         assert rel.max() <= 1e-12, (k, d.n, rel.max())
         relv = np.linalg.norm(sg["v"] - sr["v"], axis=1) / np.linalg.norm(sr["v"], axis=1)
         assert relv.max() <= 1e-11, (k, d.n, relv.max())
+
+
+def test_batch_schedules_are_bit_identical():
+    """Kick tile rows (32, 64, 128), buckets of independent launch chains
+    (1, 3, 8) and threads per CTA change where and when each system's work
+    runs, never its arithmetic: identical states, encounter lists and
+    counters after 30 steps with encounters and mergers."""
+    disks = [ics.make_disk(n, 2.0, 0.7, 1.3, 0.01, 0.005, 6.0, seed=900 + n, f_radius=400.0)
+             for n in (64, 128, 200)] + ics.ensemble(n_systems=40, seed=ics.SEED_BASE + 36)
+    dt, steps = 6.0, 30
+    runs = []
+    for rows, buckets, threads in ((128, 1, 128), (32, 3, 256), (64, 8, 64)):
+        b = batch_of(disks, dt)
+        b.set_shape(threads, 7)
+        b.set_schedule(rows, buckets)
+        b.step(steps, dt)
+        runs.append((b.state(), [b.encounter_list(k) for k in range(len(disks))], b.stats()))
+    s0, e0, t0 = runs[0]
+    assert t0["merges"] > 0 and t0["groups"] > 0
+    for s1, e1, t1 in runs[1:]:
+        for k in s0:
+            assert np.array_equal(np.asarray(s0[k]), np.asarray(s1[k])), k
+        assert all(np.array_equal(a, c) for a, c in zip(e0, e1))
+        for k in ("groups", "bs_derivs", "bs_substeps", "bs_halvings", "merges"):
+            assert t0[k] == t1[k], k

@@ -63,14 +63,14 @@ def oracle_rc(d, p):
 _SPREAD = {}
 
 
-def oracle_spread(d, rc, steps, xb, trials):
+def oracle_spread(d, rc, steps, xb, trials, **kw):
     """Largest relative position spread of the oracle against its own run xb
     when every input coordinate moves by one ulp (the run's conditioning),
     and the oracle's direct-solver counts in those runs."""
-    key = (d.name, d.n, steps, trials)
+    key = (d.name, d.n, steps, trials, tuple(sorted(kw.items())))
     if key in _SPREAD:
         return _SPREAD[key]
-    rp = nbref.params(dt_rcrit=d.dt)
+    rp = nbref.params(dt_rcrit=d.dt, **kw)
     rng = np.random.default_rng(1)
     worst = np.zeros(len(xb))
     counts = []
@@ -89,7 +89,7 @@ def oracle_spread(d, rc, steps, xb, trials):
     return _SPREAD[key]
 
 
-def check_run(d, steps, sr_sys, sg, enc_list_g, stats_g, trials, label):
+def check_run(d, steps, sr_sys, sg, enc_list_g, stats_g, trials, label, **kw):
     """Compare one GPU result (state sg, encounter list, stats) with the oracle
     system sr_sys after `steps` steps."""
     sr = sr_sys.state()
@@ -107,7 +107,7 @@ def check_run(d, steps, sr_sys, sg, enc_list_g, stats_g, trials, label):
         counts_note = "; BS substeps %d vs oracle %d, halvings %d vs %d" % (
             stats_g["bs_substeps"], rs["bs_substeps"], stats_g["bs_halvings"], rs["bs_halvings"])
         if dsub or dhalv:
-            _, counts = oracle_spread(d, sr_sys._rc_init, steps, sr["x"], trials)
+            _, counts = oracle_spread(d, sr_sys._rc_init, steps, sr["x"], trials, **kw)
             counts_note += " (oracle under 1-ulp input perturbations: %s)" % counts
         assert abs(dsub) <= max(2, 1e-3 * rs["bs_substeps"]), (label, counts_note)
         assert abs(dhalv) <= max(2, 1e-3 * rs["bs_substeps"]), (label, counts_note)
@@ -121,7 +121,7 @@ def check_run(d, steps, sr_sys, sg, enc_list_g, stats_g, trials, label):
     spread_max = 0.0
     if over.any():
         rc = sr_sys._rc_init
-        spread, _ = oracle_spread(d, rc, steps, sr["x"], trials)
+        spread, _ = oracle_spread(d, rc, steps, sr["x"], trials, **kw)
         spread_max = float(np.max(spread))
         bound = max(1e-12, 3.0 * spread_max)
         assert rel.max() <= bound, (label, rel.max(), spread_max)
@@ -132,14 +132,15 @@ def check_run(d, steps, sr_sys, sg, enc_list_g, stats_g, trials, label):
     return rel
 
 
-def run_pair(d, steps):
+def run_pair(d, steps, gpu_kw=None, **kw):
     nb = nbmod()
-    rp = nbref.params(dt_rcrit=d.dt)
+    rp = nbref.params(dt_rcrit=d.dt, **kw)
     rc = oracle_rc(d, rp)
     ref = nbref.RefSystem(rp, d.x, d.v, d.m, d.R, rc=rc)
     ref._rc_init = rc
     assert ref.step(steps, d.dt) == 0
-    gpu = nb.NBodySystem(nb.params(dt_rcrit=d.dt), d.x, d.v, d.m, d.R, rc=rc)
+    gpu = nb.NBodySystem(nb.params(dt_rcrit=d.dt, **kw, **(gpu_kw or {})), d.x, d.v, d.m, d.R,
+                         rc=rc)
     gpu.step(steps, d.dt)
     return ref, gpu, rc
 
@@ -183,3 +184,33 @@ def test_fullsize_mmsn_64k_10_steps():
     st = gpu.stats()
     assert st["steps"] == 10 and st["groups"] > 0
     check_run(d, 10, ref, gpu.state(), gpu.encounter_list(), st, 1, "mmsn_64k_js x 10")
+
+
+def test_large_groups_on_the_cluster_solver_5_steps():
+    """The 16k disk family at N = 4098 under the literal velocity reading of
+    Eq. rcrit (vel_mode 1): every step forms one group of ~280 bodies and
+    hundreds of small ones. Groups of 64 or more bodies run on a thread-block
+    cluster (k_bs_cluster); the run is checked against the oracle over 5 steps
+    like the other full-size runs, and the GPU step time is printed."""
+    import networkx as nx
+    nb = nbmod()
+    d = ics.workload("mmsn_16k_js", n=4096)
+    ref, gpu, rc = run_pair(d, 5, gpu_kw={"bs_cluster_min": 64}, vel_mode=1)
+    el = ref.encounter_list()
+    g = nx.Graph()
+    g.add_edges_from((int(i), int(j)) for s, i, j in el if s == 0)
+    largest = max(len(c) for c in nx.connected_components(g))
+    assert largest >= 100, largest
+    check_run(d, 5, ref, gpu.state(), gpu.encounter_list(), gpu.stats(), 2,
+              "mmsn_16k_js n=4096 vel_mode=1 x 5 (largest group %d)" % largest, vel_mode=1)
+    # the step time with the cluster solver (events on the library's stream)
+    g2 = nb.NBodySystem(nb.params(dt_rcrit=d.dt, vel_mode=1, bs_cluster_min=64), d.x, d.v, d.m,
+                        d.R, rc=rc)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    g2.step(3, d.dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    print("large-group step: %.1f ms per step (3 steps from the initial state)" % (
+        e0.elapsed_time(e1) / 3))
