@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--no-options", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the 100/1000-step accuracy leg of the reduced-precision kicks")
+    ap.add_argument("--batch-shape", default=None,
+                    help="threads:chunk:tile_rows:buckets of the batched leg instead of the "
+                         "autotuner's (profiling)")
+    ap.add_argument("--batch-systems", type=int, default=4096,
+                    help="systems of the batched leg (4096 is the workload; fewer for profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="steps of the adjoint leg (2000 is the workload; fewer for profiling)")
     ap.add_argument("--adjoint-every", type=int, default=100, help="checkpoint interval")
@@ -362,7 +367,7 @@ def run_ours(args):
 
     batched = None
     if not args.no_batch:
-        batched = run_batched(nb, torch, args, flush, stream)
+        batched = run_batched(nb, torch, args, flush, stream, n_systems=args.batch_systems)
 
     # the step with the start-of-step options of the non-Newtonian row on:
     # gas drag at both ends of the step and the ejection scan
@@ -566,7 +571,12 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
     disks = ics.ensemble(n_systems=n_systems)
     pairs = float(sum(d.n * (d.n - 1) for d in disks))
     b = nb.NBodyBatch(nb.params(dt_rcrit=dt), disks)
-    b.autotune(dt)
+    if args.batch_shape:
+        t_, c_, r_, k_ = (int(q) for q in args.batch_shape.split(":"))
+        b.set_shape(t_, c_)
+        b.set_schedule(r_, k_)
+    else:
+        b.autotune(dt)
     shape = b.shape()  # threads, steps per graph chunk, kick tile rows, buckets
     threads, chunk = shape["threads"], shape["chunk"]
     for _ in range(max(args.warmup, 0)):

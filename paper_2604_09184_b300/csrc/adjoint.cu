@@ -766,9 +766,12 @@ struct nb_adjoint {
   int* ck_i;
   Ctrl* ck_c;
   int n_ckpt;
-  // step records of one segment
-  StepRec* recs;  // host array of device pointers
+  // step records of two segments: the backward pass reverses one segment
+  // while the replay of the one before it fills the other buffer
+  StepRec* recs[2];  // host arrays of device pointers
   int rec_cap;
+  cudaStream_t st2;  // the replays' stream
+  cudaEvent_t ev_rep;
   // adjoint vectors and scratch
   double *lx, *ly, *lz, *lvx, *lvy, *lvz, *lm, *mux, *muy, *muz, *parts;
   int* alive0;
@@ -828,8 +831,8 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
   Ctrl* ck_c = c.take<Ctrl>(nck);
   const int kmax = kmax_of(p);
   const int stride = adj_slot_stride(kmax);
-  std::vector<StepRec> recs(every);
-  for (int t = 0; t < every; ++t) {
+  std::vector<StepRec> recs(2 * (size_t)every);
+  for (int t = 0; t < 2 * every; ++t) {
     recs[t].xs6 = c.take<double>(6 * (size_t)n);
     recs[t].st0 = c.take<double>(4 * (size_t)n);
     recs[t].x26 = c.take<double>(6 * (size_t)n);
@@ -860,8 +863,10 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
     a->ck_d = ck_d; a->ck_i = ck_i; a->ck_c = ck_c;
     a->max_ckpt = nck;
     a->rec_cap = every;
-    a->recs = (StepRec*)malloc(sizeof(StepRec) * every);
-    for (int t = 0; t < every; ++t) a->recs[t] = recs[t];
+    for (int b = 0; b < 2; ++b) {
+      a->recs[b] = (StepRec*)malloc(sizeof(StepRec) * every);
+      for (int t = 0; t < every; ++t) a->recs[b][t] = recs[(size_t)b * every + t];
+    }
     a->lx = vec; a->ly = vec + n; a->lz = vec + 2 * n;
     a->lvx = vec + 3 * n; a->lvy = vec + 4 * n; a->lvz = vec + 5 * n;
     a->lm = vec + 6 * n; a->mux = vec + 7 * n; a->muy = vec + 8 * n; a->muz = vec + 9 * n;
@@ -896,8 +901,10 @@ __global__ void k_replay_check(Dev d, const double* cd, int* bad) {
   if (!same) atomicExch(bad, 1);
 }
 
-// Copy the system's full state to (dir 0) or from (dir 1) checkpoint k.
-int checkpoint(nb_adjoint* a, int k, int dir) {
+// Copy the system's full state to (dir 0) or from (dir 1) checkpoint k, on
+// stream st (the adjoint's own stream unless given).
+int checkpoint(nb_adjoint* a, int k, int dir, cudaStream_t st = nullptr) {
+  if (!st) st = a->st;
   const Dev& d = a->sys->d;
   const int n = d.n;
   double* arr[] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.R, d.rc, d.rc2, d.ax, d.ay, d.az};
@@ -906,39 +913,54 @@ int checkpoint(nb_adjoint* a, int k, int dir) {
   const cudaMemcpyKind K = cudaMemcpyDeviceToDevice;
   for (int q = 0; q < 13; ++q)
     NB_ACU(cudaMemcpyAsync(dir ? arr[q] : cd + (size_t)q * n, dir ? cd + (size_t)q * n : arr[q],
-                           sizeof(double) * n, K, a->st));
-  NB_ACU(cudaMemcpyAsync(dir ? d.alive : ci, dir ? ci : d.alive, sizeof(int) * n, K, a->st));
+                           sizeof(double) * n, K, st));
+  NB_ACU(cudaMemcpyAsync(dir ? d.alive : ci, dir ? ci : d.alive, sizeof(int) * n, K, st));
   NB_ACU(cudaMemcpyAsync(dir ? (void*)d.fprev : (void*)(ci + n), dir ? (void*)(ci + n) : (void*)d.fprev,
-                         sizeof(int2) * d.pair_cap, K, a->st));
-  NB_ACU(cudaMemcpyAsync(dir ? d.ctrl : a->ck_c + k, dir ? a->ck_c + k : d.ctrl, sizeof(Ctrl), K, a->st));
+                         sizeof(int2) * d.pair_cap, K, st));
+  NB_ACU(cudaMemcpyAsync(dir ? d.ctrl : a->ck_c + k, dir ? a->ck_c + k : d.ctrl, sizeof(Ctrl), K, st));
   if (dir) {
-    NB_ACU(cudaMemsetAsync(d.member_slot, 0xff, sizeof(int) * n, a->st));
+    NB_ACU(cudaMemsetAsync(d.member_slot, 0xff, sizeof(int) * n, st));
     // forget the previous step's members (their slots were just cleared)
-    NB_ACU(cudaMemsetAsync(&d.ctrl->n_prev_members, 0, sizeof(int), a->st));
+    NB_ACU(cudaMemsetAsync(&d.ctrl->n_prev_members, 0, sizeof(int), st));
   }
   return NB_OK;
 }
 
 // One step of the replay with the recording kernels around the BS phase
 // (the same kernels as nb_step(1)).
-void replay_step(nb_adjoint* a, double dt, const StepRec& r) {
+void replay_step(nb_adjoint* a, double dt, const StepRec& r, cudaStream_t st) {
   nb_system* s = a->sys;
   const Dev& d = s->d;
   const int g = (d.n + 255) / 256;
-  launch_open_h(d, dt, a->st);
-  launch_drift_h(d, s->P, dt, a->st);
-  k_rec_saved<<<g, 256, 0, a->st>>>(d, r);
-  launch_kick(d, s->P, 0, a->st);
-  launch_encounter(d, s->P, a->st);
+  launch_open_h(d, dt, st);
+  launch_drift_h(d, s->P, dt, st);
+  k_rec_saved<<<g, 256, 0, st>>>(d, r);
+  launch_kick(d, s->P, 0, st);
+  launch_encounter(d, s->P, st);
   // the force update in the two halves nb_step uses (same arithmetic, so the
   // replay reproduces the forward bit for bit; here on one stream)
-  launch_finish_part(d, s->P, 1, a->st);
-  launch_bs(d, s->P, dt, a->st);
-  launch_finish_part(d, s->P, 2, a->st);
-  launch_scatter(d, s->P, a->st);
-  launch_member_kick(d, s->P, a->st);
-  k_rec_after<<<g + 1, 256, 0, a->st>>>(d, r);
-  launch_close_h(d, s->P, dt, 1, a->st);
+  launch_finish_part(d, s->P, 1, st);
+  launch_bs(d, s->P, dt, st);
+  launch_finish_part(d, s->P, 2, st);
+  launch_scatter(d, s->P, st);
+  launch_member_kick(d, s->P, st);
+  k_rec_after<<<g + 1, 256, 0, st>>>(d, r);
+  launch_close_h(d, s->P, dt, 1, st);
+}
+
+// Replay of segment seg from its checkpoint into the records `recs` on
+// stream st, and the bit comparison of its end with the next checkpoint
+// (flag status[2 + slot]).
+int replay_segment(nb_adjoint* a, int seg, StepRec* recs, cudaStream_t st, int slot) {
+  const int start = seg * a->every;
+  const int len = a->nsteps_done - start < a->every ? a->nsteps_done - start : a->every;
+  int rc = checkpoint(a, seg, 1, st);
+  if (rc) return rc;
+  for (int t = 0; t < len; ++t) replay_step(a, a->dt, recs[t], st);
+  const int n = a->n;
+  k_replay_check<<<(n + 255) / 256, 256, 0, st>>>(a->sys->d, a->ck_d + (size_t)(seg + 1) * 13 * n,
+                                                  a->status + 2 + slot);
+  return NB_OK;
 }
 
 void kick_vjp(nb_adjoint* a, const double* x6, const double* m, const double* rc,
@@ -1034,10 +1056,15 @@ int nb_adjoint_init(nb_adjoint** out, const nb_params* p, int n, const double* x
   nb_system* s = nullptr;
   const int rc0 = nb_init_system(&s, p, n, x, v, m, R, rc, nullptr, workspace,
                                  nb_workspace_bytes(p, n), stream, inputs_on_device);
-  if (rc0 != NB_OK) {
-    free(a->recs);
+  if (rc0 != NB_OK ||
+      cudaStreamCreateWithFlags(&a->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&a->ev_rep, cudaEventDisableTiming) != cudaSuccess) {
+    if (s) nb_destroy(s);
+    if (a->st2) cudaStreamDestroy(a->st2);
+    free(a->recs[0]);
+    free(a->recs[1]);
     free(a);
-    return rc0;
+    return rc0 != NB_OK ? rc0 : NB_E_CUDA;
   }
   a->sys = s;
   *out = a;
@@ -1113,22 +1140,38 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
   k_mask<<<g, 256, 0, a->st>>>(n, d.alive, a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->lm);
   NB_ACU(cudaMemsetAsync(a->status, 0, 4 * sizeof(int), a->st));
   const int total = a->nsteps_done;
+  // Segments from the last to the first. A segment's replay (forward with
+  // recording, the system's arrays) and the reverse of the segment after it
+  // (its records and the adjoint's own arrays) touch disjoint memory, so the
+  // replay of segment seg - 1 runs on the second stream beside the reverse of
+  // segment seg; both are latency-bound (the direct solver's groups) and
+  // leave most of the GPU idle. Buffers alternate; the streams join after
+  // every segment, when the host checks the status words.
+  NB_ACU(cudaEventRecord(a->ev_rep, a->st));
+  NB_ACU(cudaStreamWaitEvent(a->st2, a->ev_rep, 0));
+  int cur = 0;
+  {
+    NvtxRange r("adjoint: replay the last segment");
+    int rc = replay_segment(a, a->n_ckpt - 1, a->recs[cur], a->st2, cur);
+    if (rc) return rc;
+  }
   for (int seg = a->n_ckpt - 1; seg >= 0; --seg) {
     const int start = seg * a->every;
     const int len = total - start < a->every ? total - start : a->every;
-    int rc = checkpoint(a, seg, 1);
-    if (rc) return rc;
-    {
-      NvtxRange r("adjoint: replay segment");
-      for (int t = 0; t < len; ++t) replay_step(a, a->dt, a->recs[t]);
-      // the replay must end on the next checkpoint bit for bit
-      k_replay_check<<<g, 256, 0, a->st>>>(d, a->ck_d + (size_t)(seg + 1) * 13 * n, a->status + 2);
+    NB_ACU(cudaEventRecord(a->ev_rep, a->st2));  // segment seg's records are complete
+    NB_ACU(cudaStreamWaitEvent(a->st, a->ev_rep, 0));
+    if (seg > 0) {
+      NvtxRange r("adjoint: replay the segment before, beside the reverse");
+      int rc = replay_segment(a, seg - 1, a->recs[1 - cur], a->st2, 1 - cur);
+      if (rc) return rc;
     }
     {
       NvtxRange r("adjoint: reverse segment");
-      for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[t]);
+      for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[cur][t]);
     }
-    int st[2] = {0, 0};
+    NB_ACU(cudaEventRecord(a->ev_rep, a->st2));
+    NB_ACU(cudaStreamWaitEvent(a->st, a->ev_rep, 0));
+    int st[4] = {0, 0, 0, 0};
     NB_ACU(cudaMemcpyAsync(st, a->status, sizeof(st), cudaMemcpyDeviceToHost, a->st));
     Ctrl c;
     NB_ACU(cudaMemcpyAsync(&c, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a->st));
@@ -1138,13 +1181,13 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
       snprintf(a->err, sizeof(a->err), "backward: %s", nb_status_string(c.status ? c.status : st[0]));
       return c.status ? c.status : st[0];
     }
-    int mismatch = 0;
-    NB_ACU(cudaMemcpy(&mismatch, a->status + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    if (mismatch) {
+    if (st[2 + cur] || (seg > 0 && st[2 + (1 - cur)])) {
       snprintf(a->err, sizeof(a->err),
-               "backward: the replay of segment %d did not reproduce the forward state", seg);
+               "backward: the replay of segment %d did not reproduce the forward state",
+               st[2 + cur] ? seg : seg - 1);
       return NB_E_INVALID;
     }
+    cur = 1 - cur;
   }
   // leave the system at its final state again
   int rc = checkpoint(a, a->n_ckpt, 1);
@@ -1164,7 +1207,10 @@ const char* nb_adjoint_last_error(const nb_adjoint* a) { return a ? a->err : "no
 void nb_adjoint_destroy(nb_adjoint* a) {
   if (!a) return;
   nb_destroy(a->sys);
-  free(a->recs);
+  if (a->st2) cudaStreamDestroy(a->st2);
+  if (a->ev_rep) cudaEventDestroy(a->ev_rep);
+  free(a->recs[0]);
+  free(a->recs[1]);
   free(a);
 }
 

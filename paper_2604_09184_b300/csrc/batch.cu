@@ -366,10 +366,21 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
 constexpr int kTileRows[3] = {32, 64, 128};
 constexpr int kMinTileRows = 32;
 
+#ifndef NB_KICK_SC
+#define NB_KICK_SC 32
+#endif
+// Sources staged per j-tile: at least the tile's rows (each thread stages
+// SC / KBT of them). Staging 64 or 128 sources per one-warp tile measured no
+// gain over 32 (3.48 and 3.50 against 3.40 ms per ensemble step).
 template <int KBT>
+constexpr int kick_sc() {
+  return KBT > NB_KICK_SC ? KBT : NB_KICK_SC;
+}
+
+template <int KBT, int SC>
 __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys P) {
-  __shared__ nb_u128 sX[KBT], sY[KBT], sZ[KBT];
-  __shared__ double sm[KBT], src2[KBT];
+  __shared__ nb_u128 sX[SC], sY[SC], sZ[SC];
+  __shared__ double sm[SC], src2[SC];
   __shared__ int s_stop;
   if (threadIdx.x == 0) s_stop = B.status[0];
   __syncthreads();
@@ -392,18 +403,20 @@ __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys
   ti.hi = __double2hiint(ti.rc2);
   ti.i = act ? i : 0;
   double ax = 0.0, ay = 0.0, az = 0.0;
-  for (int jt = 0; jt < n; jt += KBT) {
+  for (int jt = 0; jt < n; jt += SC) {
     __syncthreads();
-    const int j = base + jt + threadIdx.x;
-    if (jt + threadIdx.x < n) {
-      sX[threadIdx.x] = fix_of(B.x[j]);
-      sY[threadIdx.x] = fix_of(B.y[j]);
-      sZ[threadIdx.x] = fix_of(B.z[j]);
-      sm[threadIdx.x] = B.m[j];
-      src2[threadIdx.x] = B.rc[j] * B.rc[j];
+    for (int q = threadIdx.x; q < SC; q += KBT) {
+      if (jt + q < n) {
+        const int j = base + jt + q;
+        sX[q] = fix_of(B.x[j]);
+        sY[q] = fix_of(B.y[j]);
+        sZ[q] = fix_of(B.z[j]);
+        sm[q] = B.m[j];
+        src2[q] = B.rc[j] * B.rc[j];
+      }
     }
     __syncthreads();
-    const int cnt = min(KBT, n - jt);
+    const int cnt = min(SC, n - jt);
     for (int q = 0; q < cnt; ++q) {
       KTerm t;
       const double mj = sm[q], rc2j = src2[q];
@@ -1192,7 +1205,7 @@ int arrange(nb_batch* b, int rows, int buckets) {
 
 template <int KT>
 void launch_kick_t(const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st) {
-  if (ntiles > 0) k_batch_kick<KT><<<ntiles, KT, 0, st>>>(d, P);
+  if (ntiles > 0) k_batch_kick<KT, kick_sc<KT>()><<<ntiles, KT, 0, st>>>(d, P);
 }
 void launch_kick_rows(int rows, const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st) {
   if (rows == 32)
