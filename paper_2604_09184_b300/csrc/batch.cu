@@ -189,13 +189,13 @@ struct KArrays {
 // needs the exact branch.
 __device__ __forceinline__ bool kick_fast(KTerm& t, const KTarget& ti, const nb_u128& Xj,
                                           const nb_u128& Yj, const nb_u128& Zj, double mj,
-                                          double rc2j) {
+                                          double m15j, double m1875j, double rc2j) {
   const FixDiff fx = fix_diff(Xj, ti.X), fy = fix_diff(Yj, ti.Y), fz = fix_diff(Zj, ti.Z);
   t.dx = fx.d;
   t.dy = fy.d;
   t.dz = fz.d;
   const double r2 = sep2_fix(fx, fy, fz);
-  t.sc = scale_fast<NB_PREC_FP64>(r2, mj);
+  t.sc = scale_fast<NB_PREC_FP64>(r2, mj, m15j, m1875j);
   t.close = false;
   return __double2hiint(r2) <= max(ti.hi, __double2hiint(rc2j)) + 1;
 }
@@ -217,7 +217,9 @@ __device__ __forceinline__ KTerm kick_term(const KTarget& ti, const KArrays& ta,
                                            const nb_u128& Zj, double mj, double rc2j,
                                            const KArrays& sa, int j) {
   KTerm t;
-  if (kick_fast(t, ti, Xj, Yj, Zj, mj, rc2j)) kick_rare(t, ti, ta, mj, rc2j, sa, j);
+  // 1.5 m and 1.875 m as the tiled kick stages them (FP64 products, the same bits)
+  if (kick_fast(t, ti, Xj, Yj, Zj, mj, 1.5 * mj, 1.875 * mj, rc2j))
+    kick_rare(t, ti, ta, mj, rc2j, sa, j);
   return t;
 }
 
@@ -359,6 +361,8 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
 // bodies (j-tiles of KBT staged in shared memory as fixed-point positions,
 // masses and rc^2): a_i = G sum_j (ascending) sc_ij (dx, dy, dz). Flags (i < j,
 // both live) go to the system's trial list with one atomic each (rare).
+// 1.5 m and 1.875 m are staged with the sources as FP64 products (1.2 % off
+// the ensemble step against forming them per pair by integer ops).
 // Registers bounded at 64 for 32 warps per SM whatever the tile: KBT = 32
 // (one warp per CTA; a system of n bodies wastes at most 31 rows), 64 or 128
 // (fewer stagings of the sources per system), chosen by the autotuner.
@@ -380,7 +384,7 @@ constexpr int kick_sc() {
 template <int KBT, int SC>
 __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys P) {
   __shared__ nb_u128 sX[SC], sY[SC], sZ[SC];
-  __shared__ double sm[SC], src2[SC];
+  __shared__ double sm[SC], sm15[SC], sm1875[SC], src2[SC];
   __shared__ int s_stop;
   if (threadIdx.x == 0) s_stop = B.status[0];
   __syncthreads();
@@ -411,7 +415,10 @@ __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys
         sX[q] = fix_of(B.x[j]);
         sY[q] = fix_of(B.y[j]);
         sZ[q] = fix_of(B.z[j]);
-        sm[q] = B.m[j];
+        const double mj = B.m[j];
+        sm[q] = mj;
+        sm15[q] = 1.5 * mj;
+        sm1875[q] = 1.875 * mj;
         src2[q] = B.rc[j] * B.rc[j];
       }
     }
@@ -420,15 +427,20 @@ __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys
     for (int q = 0; q < cnt; ++q) {
       KTerm t;
       const double mj = sm[q], rc2j = src2[q];
-      if (kick_fast(t, ti, sX[q], sY[q], sZ[q], mj, rc2j)) {
+      const int jj = jt + q;
+      // a row's own source (r^2 = 0) would take the exact branch, and a warp
+      // runs a branch once for every lane that takes it: 32 times per tile,
+      // a third more FP64 work for a system of ~150 bodies. Its term is zero
+      // (no force on itself, no flag), set without the branch.
+      if (kick_fast(t, ti, sX[q], sY[q], sZ[q], mj, sm15[q], sm1875[q], rc2j) && jj != i) {
         const KArrays g{B.x + base, B.y + base, B.z + base, B.rc + base};
-        const int jj = jt + q;
         kick_rare(t, ti, g, mj, rc2j, g, jj);
         if (t.close && act && i < jj && B.alive[base + jj]) {
           const int pos = atomicAdd(&B.nftrial[sys], 1);
           if (pos < BPAIR) B.ftrial[(size_t)sys * BPAIR + pos] = ((unsigned)i << 16) | (unsigned)jj;
         }
       }
+      if (jj == i) t.sc = 0.0;
       ax = __fma_rn(t.sc, t.dx, ax);
       ay = __fma_rn(t.sc, t.dy, ay);
       az = __fma_rn(t.sc, t.dz, az);
@@ -1254,7 +1266,15 @@ int enqueue_steps(nb_batch* b, int nsteps, double dt, cudaStream_t st) {
     dq.spec_cap = kSpecWarps / nb;
     dq.spec = b->d.spec + (size_t)q * dq.spec_cap * 4 * b->d.bs_stride;
     if (dq.nsys == 0) continue;
-    const int ga = open_grid(b, dq.nsys), gc = batch_grid(b, dq.nsys);
+    // the buckets' close launches run side by side: each takes about twice
+    // its share of the GPU's CTA slots (16 buckets: 37 CTAs instead of 296,
+    // 3.40 -> 3.34 ms per ensemble step), leaving the SMs' registers to the
+    // other buckets' kicks while a slow system's direct solver runs
+    const int ga = open_grid(b, dq.nsys);
+    const int gfull = batch_grid(b, dq.nsys);
+    int gc = (2 * gfull + nb - 1) / nb;
+    if (gc > gfull) gc = gfull;
+    if (gc < 1) gc = 1;
     NB_BCU(cudaMemsetAsync(dq.queue, 0, 2 * sizeof(int), sq));
     for (int k = 0; k < nsteps; ++k) {
       k_batch_open<<<ga, kOpenThreads, 0, sq>>>(dq, b->P, dt);
