@@ -422,6 +422,12 @@ int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void
  *                          paragraph after Eq. Hc) for rc = 1, x = r
  *   NB_MATH_MASS15         1.5 m as the kernels build it from a mass x
  *   NB_MATH_MASS1875       1.875 m likewise (x = 0 or 2^-126 <= x <= 2^127)
+ *   NB_MATH_NEVILLE        the direct solver's Neville weight (j - q)^2 /
+ *                          (q (2j - q)) for x = 16 j + q, 1 <= q < j <= 12
+ *                          (0 otherwise), as the solver reads it
+ *   NB_MATH_RATIO_LE       the solver's acceptance test fl(a / b) <= tol as
+ *                          1 or 0, reading in[3i .. 3i+2] = (a, b, tol), b > 0,
+ *                          tol >= 0 (in then holds 3n doubles)
  * NB_E_INVALID for an unknown fn, n < 0 or null arrays (n > 0); asynchronous
  * on the stream. */
 enum {
@@ -433,7 +439,9 @@ enum {
   NB_MATH_RPOW32_M = 5,
   NB_MATH_CLOSE_WEIGHT = 6,
   NB_MATH_MASS15 = 7,
-  NB_MATH_MASS1875 = 8
+  NB_MATH_MASS1875 = 8,
+  NB_MATH_NEVILLE = 9,
+  NB_MATH_RATIO_LE = 10
 };
 int nb_math_eval(int fn, int n, const double* in, double* out, void* stream);
 

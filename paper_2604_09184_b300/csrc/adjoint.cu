@@ -242,33 +242,45 @@ __global__ void __launch_bounds__(ANT) k_cdrift_vjp(int n, int nparts, const dou
   lm[i] += hh * (vx[i] * S[0] + vy[i] * S[1] + vz[i] * S[2]) / m0;
 }
 
-// Transposed Jacobian of the Kepler drift for bodies outside the step's groups.
+// Transposed Jacobian of the Kepler drift for bodies outside the step's
+// groups. Six threads per body: thread c carries the derivative along input
+// c (one column of the 6x6 Jacobian, forward mode, one partial), so that
+// lambda_in[c] = sum_o lambda_out[o] dout_o / din_c is its own dot product;
+// the six take the same iteration path (it depends on the values only). Five
+// bodies per warp: each thread's FP64 work is about twice the drift's instead
+// of seven times with all six partials in one thread.
+constexpr int kKvBodies = 5;
 __global__ void __launch_bounds__(ANT) k_kepler_vjp(int n, const double* xs6, const int* alive,
                                                    const int* ingrp, double mu, double h,
                                                    int max_iter, double* lx, double* ly,
                                                    double* lz, double* lvx, double* lvy,
                                                    double* lvz, int* status) {
-  const int i = blockIdx.x * ANT + threadIdx.x;
-  if (i >= n || !alive[i] || ingrp[i]) return;
-  Dual6 q[6];
-  for (int a = 0; a < 6; ++a) {
-    q[a] = mkd(xs6[(size_t)a * n + i]);
-    q[a].d[a] = 1.0;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane / 6, c = lane - 6 * slot;
+  const int i = ((blockIdx.x * ANT + threadIdx.x) >> 5) * kKvBodies + slot;
+  const bool act = slot < kKvBodies && i < n && alive[i] && !ingrp[i];
+  bool ok = false;
+  double li = 0.0;
+  if (act) {
+    Dual<1> q[6];
+    for (int a = 0; a < 6; ++a) {
+      q[a] = mkd<1>(xs6[(size_t)a * n + i]);
+      q[a].d[0] = a == c ? 1.0 : 0.0;
+    }
+    int it;
+    ok = kepler_drift(mu, q[0], q[1], q[2], q[3], q[4], q[5], h, max_iter, &it) == 0;
+    if (ok) {
+      const double lo[6] = {lx[i], ly[i], lz[i], lvx[i], lvy[i], lvz[i]};
+      for (int a = 0; a < 6; ++a) li += lo[a] * q[a].d[0];
+    } else if (c == 0) {
+      atomicCAS(status, 0, NB_E_NOCONV);
+    }
   }
-  int it;
-  if (kepler_drift(mu, q[0], q[1], q[2], q[3], q[4], q[5], h, max_iter, &it)) {
-    atomicCAS(status, 0, NB_E_NOCONV);
-    return;
+  __syncwarp();  // the body's six threads have read lambda before any of them writes
+  if (act && ok) {
+    double* o = c == 0 ? lx : c == 1 ? ly : c == 2 ? lz : c == 3 ? lvx : c == 4 ? lvy : lvz;
+    o[i] = li;
   }
-  const double lo[6] = {lx[i], ly[i], lz[i], lvx[i], lvy[i], lvz[i]};
-  double li[6];
-  for (int b = 0; b < 6; ++b) {
-    double s = 0.0;
-    for (int a = 0; a < 6; ++a) s += lo[a] * q[a].d[b];
-    li[b] = s;
-  }
-  lx[i] = li[0]; ly[i] = li[1]; lz[i] = li[2];
-  lvx[i] = li[3]; lvy[i] = li[4]; lvz[i] = li[5];
 }
 
 // ---------------------------------------------------------------------------
@@ -285,6 +297,43 @@ __host__ __device__ constexpr int adj_sidx(int j, int t) { return j * j - 1 + t;
 // (6 state + 1 mass), an accumulator (6) and a mass accumulator per column.
 __host__ __device__ inline int adj_slot_stride(int kmax) {
   return kSubCap * 10 + 12 * adj_nstates(kmax) + 7 * kmax + 25;
+}
+
+// Weights of the extrapolated value: T_kk = sum_j c_kj T_j1, the Neville
+// recursion being linear in the column results. [k][j] for 1 <= j <= k <=
+// kMaxBsK, the recursion applied to unit vectors, evaluated by the compiler.
+struct ExtrapTab {
+  double c[kMaxBsK + 1][kMaxBsK + 1];
+};
+__host__ __device__ constexpr ExtrapTab extrap_tab() {
+  ExtrapTab t{};
+  for (int k = 1; k <= kMaxBsK; ++k)
+    for (int j0 = 1; j0 <= k; ++j0) {
+      double Tn[kMaxBsK + 1][kMaxBsK + 1] = {};
+      for (int j = 1; j <= k; ++j) {
+        Tn[j][1] = (j == j0) ? 1.0 : 0.0;
+        for (int q = 1; q < j; ++q) {
+          const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+          Tn[j][q + 1] = Tn[j][q] + (Tn[j][q] - Tn[j - 1][q]) * inv;
+        }
+      }
+      t.c[k][j0] = Tn[k][k];
+    }
+  return t;
+}
+static __constant__ ExtrapTab kExtrap = extrap_tab();
+// the Lagrange weights at h = 0 of n = 2, 4, 6 in h^2: 1/24, -16/15, 81/40
+static_assert(extrap_tab().c[3][1] - 1.0 / 24.0 < 1e-15 && 1.0 / 24.0 - extrap_tab().c[3][1] < 1e-15 &&
+                  extrap_tab().c[3][2] + 16.0 / 15.0 < 1e-15 && -16.0 / 15.0 - extrap_tab().c[3][2] < 1e-15 &&
+                  extrap_tab().c[3][3] - 81.0 / 40.0 < 1e-15 && 81.0 / 40.0 - extrap_tab().c[3][3] < 1e-15,
+              "extrapolation weights");
+
+// H / h for a substep H = h 2^-level (both normal): the power of two from
+// the exponent fields.
+__device__ __forceinline__ double pow2_ratio(double H, double h) {
+  const long long eH = (__double_as_longlong(H) >> 52) & 0x7ff;
+  const long long eh = (__double_as_longlong(h) >> 52) & 0x7ff;
+  return __longlong_as_double((1023ll + eH - eh) << 52);
 }
 
 struct AdjGroupArgs {
@@ -390,12 +439,12 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
 // columns; the Neville extrapolation is linear in the column results, with
 // weights c_j from the same recursion applied to unit vectors.
 // The adjoint of one group's integration by a team (one warp or one CTA):
-// cw and Tn are the team's shared scratch for the extrapolation weights.
+// cw is the team's shared scratch for the extrapolation weights.
 // scr: the team's direct-solver scratch (M slots of bs_stride doubles;
 // nslots >= 2 M lets the replay speculate on half-size attempts).
 template <class Team>
 __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
-                                 Team& team, double* cw, double (*Tn)[kMaxBsK + 2], double* scr,
+                                 Team& team, double* cw, double* scr,
                                  int nslots) {
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
@@ -403,6 +452,8 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
   const int n = A.n;
   const int tid = team.tid(), NT = team.nthreads();
   const int NS = adj_nstates(A.kmax);
+  double hj[kMaxBsK + 1];  // h / n_j
+  for (int j = 1; j <= A.kmax; ++j) hj[j] = h / (2 * j);
   {
     const int off = goff[grp];
     BsCtx c;
@@ -517,19 +568,10 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
         for (int j = 1; j <= kacc; ++j) lmc[(j - 1) * M + b] = 0.0;
       }
       for (int e = tid; e < adj_nstates(kacc) * 6 * M; e += NT) lzst[e] = 0.0;
-      if (tid == 0) {
-        // extrapolation weights: T_kk = sum_j cw[j] T_j1 (Neville is linear)
-        for (int j0 = 1; j0 <= kacc; ++j0) {
-          for (int j = 1; j <= kacc; ++j) {
-            Tn[j][1] = (j == j0) ? 1.0 : 0.0;
-            for (int q = 1; q < j; ++q) {
-              const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
-              Tn[j][q + 1] = Tn[j][q] + (Tn[j][q] - Tn[j - 1][q]) * inv;
-            }
-          }
-          cw[j0] = Tn[kacc][kacc];
-        }
-      }
+      // extrapolation weights: T_kk = sum_j cw[j] T_j1; the column sizes
+      // H / n_j = hj[j] (H / h), the power of two exact
+      for (int j = 1 + tid; j <= kacc; j += NT) cw[j] = kExtrap.c[kacc][j];
+      const double sc = pow2_ratio(H, h);
       team.sync();
       const double* y = zst;  // M states
       for (int b = tid; b < M; b += NT) grp_f(c, y, b, f0 + 6 * b);
@@ -537,7 +579,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
       // replay: z_0 = y, z_1 = y + hs f0, z_{t+1} = z_{t-1} + 2 hs f(z_t)
       for (int it = tid; it < kacc * M; it += NT) {
         const int j = 1 + it / M, b = it % M;
-        const double hs = H / (2 * j);
+        const double hs = hj[j] * sc;
         double* z0 = zst + (size_t)adj_sidx(j, 0) * 6 * M + 6 * b;
         double* z1 = zst + (size_t)adj_sidx(j, 1) * 6 * M + 6 * b;
         for (int k = 0; k < 6; ++k) {
@@ -556,7 +598,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
         team.sync();
         for (int it = tid; it < ncol * M; it += NT) {
           const int j = j0 + it / M, b = it % M;
-          const double hs = H / (2 * j);
+          const double hs = hj[j] * sc;
           const double* zm = zst + (size_t)adj_sidx(j, t - 1) * 6 * M + 6 * b;
           double* zn = zst + (size_t)adj_sidx(j, t + 1) * 6 * M + 6 * b;
           const double* f = fcol + (size_t)(j - 1) * 6 * M + 6 * b;
@@ -585,7 +627,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
       team.sync();
       for (int it = tid; it < kacc * M; it += NT) {
         const int j = 1 + it / M, b = it % M;
-        const double hs = H / (2 * j);
+        const double hs = hj[j] * sc;
         grp_vjp(c, zst + (size_t)adj_sidx(j, 2 * j) * 6 * M, fcol + (size_t)(j - 1) * 6 * M, b,
                 lzst + (size_t)adj_sidx(j, 2 * j) * 6 * M + 6 * b, lmc + (j - 1) * M + b,
                 0.5 * hs);
@@ -598,7 +640,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
         for (int it = tid; it < ncol * M; it += NT) {
           const int j = j0 + it / M, b = it % M;
           const int m = 2 * j - tau;
-          const double hs = H / (2 * j);
+          const double hs = hj[j] * sc;
           const double* lnext = lzst + (size_t)adj_sidx(j, m + 1) * 6 * M;
           double* lprev = lzst + (size_t)adj_sidx(j, m - 1) * 6 * M + 6 * b;
           for (int k = 0; k < 6; ++k) lprev[k] += lnext[6 * b + k];
@@ -614,7 +656,7 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
         double acc[6] = {0, 0, 0, 0, 0, 0}, af[6] = {0, 0, 0, 0, 0, 0};
         double am = 0.0;
         for (int j = 1; j <= kacc; ++j) {
-          const double hs = H / (2 * j);
+          const double hs = hj[j] * sc;
           const double* l0 = lzst + (size_t)adj_sidx(j, 0) * 6 * M + 6 * b;
           const double* l1 = lzst + (size_t)adj_sidx(j, 1) * 6 * M + 6 * b;
           for (int k = 0; k < 6; ++k) {
@@ -654,7 +696,6 @@ __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) 
   __shared__ double s_red[ABNT];
   __shared__ int s_flags[4];
   __shared__ double cw[ABNT / 32][kMaxBsK + 2];
-  __shared__ double Tn[ABNT / 32][kMaxBsK + 2][kMaxBsK + 2];
   __shared__ int s_wflags[ABNT / 32][4];
   extern __shared__ double s_bscr[];  // the warp teams' scratch, 8 slots each
   const int ng = A.grp[0];
@@ -664,14 +705,14 @@ __global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) 
   WarpTeam wt{s_wflags[warp]};
   for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
     if (goff[grp + 1] - goff[grp] > 8) continue;
-    bs_adjoint_group(A, P, h, grp, wt, cw[warp], Tn[warp],
+    bs_adjoint_group(A, P, h, grp, wt, cw[warp],
                      s_bscr + (size_t)warp * 8 * A.bs_stride, 8);
   }
   __syncthreads();
   BlockTeam bt{s_red, s_flags};
   for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
     if (goff[grp + 1] - goff[grp] <= 8) continue;
-    bs_adjoint_group(A, P, h, grp, bt, cw[0], Tn[0], A.gscr + (size_t)goff[grp] * A.bs_stride,
+    bs_adjoint_group(A, P, h, grp, bt, cw[0], A.gscr + (size_t)goff[grp] * A.bs_stride,
                      0);
   }
 }
@@ -990,19 +1031,27 @@ void cdrift_vjp(nb_adjoint* a, const int* alive, const double* m, const double* 
                                      a->lm);
 }
 
-void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
+// The reverse of one step. The closing B(h/2) of a step and the opening
+// B(h/2) of the next act at the same positions, masses and critical radii,
+// with nothing in between, and the kick's transpose is linear in lambda_v:
+// the two are one kick_vjp of weight h, taken with the earlier step's closing
+// kick (close_w = h), and the later step skips its opening one (open = false).
+// The last step closes with h/2 and the first step opens with h/2.
+void backward_step(nb_adjoint* a, double dt, const StepRec& r, double close_w, bool open) {
   const int n = a->n;
   const int g = (n + ANT - 1) / ANT;
   const double hh = 0.5 * dt;
   k_alive_from<<<g, ANT, 0, a->st>>>(n, r.st1 + 2 * n, a->alive1);
   k_alive_from<<<g, ANT, 0, a->st>>>(n, r.st0 + 3 * n, a->alive0);
-  // closing B(h/2) at the final positions, then the closing C(h/2)
-  kick_vjp(a, r.x26, r.st1, r.st1 + n, a->alive1, hh);
+  // closing B(h/2) at the final positions (with the next step's opening
+  // B(h/2)), then the closing C(h/2)
+  kick_vjp(a, r.x26, r.st1, r.st1 + n, a->alive1, close_w);
   cdrift_vjp(a, a->alive1, r.st1, r.x26, hh);
   // A(h): Kepler outside the groups, Bulirsch-Stoer inside
   const Phys& P = a->sys->P;
-  k_kepler_vjp<<<g, ANT, 0, a->st>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
-                                     a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
+  const int gk = (((n + kKvBodies - 1) / kKvBodies) * 32 + ANT - 1) / ANT;
+  k_kepler_vjp<<<gk, ANT, 0, a->st>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
+                                      a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
   AdjGroupArgs A;
   A.n = n;
   A.kmax = P.bs_kmax;
@@ -1022,8 +1071,9 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r) {
     cudaFuncSetAttribute(k_bs_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
   k_bs_adjoint<<<grid, ABNT, wsm, a->st>>>(A, P, dt);
   // opening C(h/2), then the opening B(h/2) at the step's start positions
+  // (for the first step; the others' went with the step before)
   cdrift_vjp(a, a->alive0, r.st0, r.xs6, hh);
-  kick_vjp(a, r.xs6, r.st0, r.st0 + 2 * n, a->alive0, hh);
+  if (open) kick_vjp(a, r.xs6, r.st0, r.st0 + 2 * n, a->alive0, hh);
 }
 
 }  // namespace
@@ -1167,7 +1217,9 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
     }
     {
       NvtxRange r("adjoint: reverse segment");
-      for (int t = len - 1; t >= 0; --t) backward_step(a, a->dt, a->recs[cur][t]);
+      for (int t = len - 1; t >= 0; --t)
+        backward_step(a, a->dt, a->recs[cur][t], start + t == total - 1 ? 0.5 * a->dt : a->dt,
+                      start + t == 0);
     }
     NB_ACU(cudaEventRecord(a->ev_rep, a->st2));
     NB_ACU(cudaStreamWaitEvent(a->st, a->ev_rep, 0));

@@ -78,6 +78,63 @@ __device__ __forceinline__ double close_weight(double qq, double rc01, double in
   return 1.0 - (K - qq * dKdy * inv09);
 }
 
+// Neville weights 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for
+// the substep counts n_k = 2k, [j][q] for 1 <= q < j <= kMaxBsK: each the
+// correctly rounded quotient, as the division gives it at run time, folded
+// by the compiler.
+struct NevilleTab {
+  double w[kMaxBsK + 1][kMaxBsK + 1];
+};
+__host__ __device__ constexpr NevilleTab neville_tab() {
+  NevilleTab t{};
+  for (int j = 2; j <= kMaxBsK; ++j)
+    for (int q = 1; q < j; ++q)
+      t.w[j][q] = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+  return t;
+}
+static __constant__ NevilleTab kNeville = neville_tab();
+
+// fmax(m, |v|) for m >= 0 (a NaN v leaves m), on bit patterns: the integer
+// pipe instead of the FP64 one.
+__device__ __forceinline__ double nn_max_abs(double m, double v) {
+  const long long b = __double_as_longlong(v) & 0x7fffffffffffffffll;
+  return (b > 0x7ff0000000000000ll || b <= __double_as_longlong(m)) ? m : __longlong_as_double(b);
+}
+
+// fl(a / b) <= tol for b > 0, with tol_up the next double above tol, almost
+// always without the division: the FMA residual a - t b is rounded once, so
+// its sign is that of the exact value; a < tol b accepts (a / b < tol) and
+// a > tol_up b rejects (a / b > tol_up). Only a quotient strictly between
+// tol and tol_up, or a non-finite one, goes through the division, which
+// rejects a NaN.
+__device__ __forceinline__ bool ratio_le(double a, double b, double tol, double tol_up) {
+  if (__fma_rn(-tol, b, a) < 0.0) return true;
+  if (__fma_rn(-tol_up, b, a) > 0.0) return false;
+  return a / b <= tol;
+}
+
+// The next double above tol (tol >= 0).
+__device__ __forceinline__ double next_up(double tol) {
+  return __longlong_as_double(__double_as_longlong(tol) + 1ll);
+}
+
+// The acceptance test of column j >= 3 for one member: the position and the
+// velocity parts of the change between the two highest extrapolations A and
+// B, each in the max-norm relative to the part's own max-norm, within tol.
+__device__ __forceinline__ bool bs_member_ok(const double* A, const double* B, double tol,
+                                             double tol_up) {
+  bool ok = true;
+  for (int part = 0; part < 2; ++part) {
+    double dm = 0.0, ym = 0.0;
+    for (int k = 3 * part; k < 3 * part + 3; ++k) {
+      dm = nn_max_abs(dm, A[k] - B[k]);
+      ym = nn_max_abs(ym, A[k]);
+    }
+    ok = ok && ratio_le(dm, ym + 1e-300, tol, tol_up);
+  }
+  return ok;
+}
+
 // Field fout of member b = d/dt of field fo (Eq. Ha restricted to the group).
 static __device__ void bs_deriv(const BsCtx& c, int fo, int fout, int b) {
   const double* yb = c.base + (size_t)b * c.stride + fo;
@@ -208,19 +265,21 @@ struct BsTally {
 // (its f0 included), up to its acceptance or its last column.
 template <class Sy>
 static __device__ long long bs_attempt_pair(const BsCtx& c, const BsCtx& cs, const Phys& P,
-                                            double H, Sy& sy, BsTally& tally) {
+                                            const double* hj, double sc, Sy& sy,
+                                            BsTally& tally) {
   const int kmax = c.kmax, M = c.M;
   const int NT = sy.nthreads(), tid = sy.tid();
   int* s_flags = sy.flags();
   const int offT = bs_off_T(kmax);
   const int KM = kmax * M;
+  const double tol_up = next_up(P.bs_tol);
   // start both column sets: z0 = y, z1 = y + hs f0
   for (int it = tid; it < 2 * KM; it += NT) {
     const int half = it >= KM, r = it - half * KM;
     const int j = 1 + r / M, b = r % M;
     const double* s = c.base + (size_t)b * c.stride;
     double* col = (half ? cs.base : c.base) + (size_t)b * c.stride + bs_off_col(j);
-    const double hs = (half ? 0.5 * H : H) / (2 * j);
+    const double hs = hj[j] * (half ? 0.5 * sc : sc);
     for (int k = 0; k < 6; ++k) {
       col[CZM + k] = s[OY + k];
       col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
@@ -245,7 +304,7 @@ static __device__ long long bs_attempt_pair(const BsCtx& c, const BsCtx& cs, con
       const int j = j0 + r / M, b = r % M;
       double* sl = (half ? cs.base : c.base) + (size_t)b * c.stride;
       double* col = sl + bs_off_col(j);
-      const double hs = (half ? 0.5 * H : H) / (2 * j);
+      const double hs = hj[j] * (half ? 0.5 * sc : sc);
       if (t < 2 * j) {
         for (int k = 0; k < 6; ++k) {
           const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
@@ -260,7 +319,7 @@ static __device__ long long bs_attempt_pair(const BsCtx& c, const BsCtx& cs, con
     sy.sync();
     if (t & 1) continue;
     const int j = t / 2;  // column j of both attempts is complete: Neville rows and tests
-    double em = 0.0, es = 0.0;
+    bool fm = false, fs = false;  // a member of the H (H/2) attempt fails the test
     for (int it = tid; it < 2 * M; it += NT) {
       const int half = it >= M, b = it - half * M;
       if (half && sdone) continue;
@@ -268,36 +327,30 @@ static __device__ long long bs_attempt_pair(const BsCtx& c, const BsCtx& cs, con
       double* Tc = sl + offT + (j & 1) * kmax * 6;
       double* Tp = sl + offT + ((j - 1) & 1) * kmax * 6;
       for (int q = 1; q < j; ++q) {
-        const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+        const double inv = kNeville.w[j][q];
         for (int k = 0; k < 6; ++k) {
           const double tq = Tc[6 * (q - 1) + k];
           Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
         }
       }
-      if (j >= 3 && bs_alive(c, b)) {
-        const double* A = Tc + 6 * (j - 1);
-        const double* B = Tc + 6 * (j - 2);
-        double e = 0.0;
-        for (int part = 0; part < 2; ++part) {
-          double dm = 0.0, ym = 0.0;
-          for (int k = 3 * part; k < 3 * part + 3; ++k) {
-            dm = fmax(dm, fabs(A[k] - B[k]));
-            ym = fmax(ym, fabs(A[k]));
-          }
-          e = fmax(e, dm / (ym + 1e-300));
-        }
-        if (half) es = fmax(es, e); else em = fmax(em, e);
+      if (j >= 3 && bs_alive(c, b) &&
+          !bs_member_ok(Tc + 6 * (j - 1), Tc + 6 * (j - 2), P.bs_tol, tol_up)) {
+        if (half) fs = true; else fm = true;
       }
     }
-    const double Em = sy.max_to_first(em);
+    if (j < 3) {
+      sy.sync();
+      continue;
+    }
+    const bool Fm = sy.any_to_first(fm);
     sy.sync();  // the team's reduction scratch is reused
-    const double Es = sy.max_to_first(es);
-    if (tid == 0 && j >= 3) {
-      if (Em <= P.bs_tol) {
+    const bool Fs = sy.any_to_first(fs);
+    if (tid == 0) {
+      if (!Fm) {
         s_flags[0] = 1;
         s_flags[1] = j;
       }
-      if (!sdone && Es <= P.bs_tol) {
+      if (!sdone && !Fs) {
         s_flags[2] = 1;
         s_flags[3] = j;
       }
@@ -357,6 +410,12 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
   int W = (2 * NT) / (M > 0 ? M : 1);
   W = W < 1 ? 1 : (W > kmax ? kmax : W);
   const bool can_spec = spec != nullptr && 2 * kmax * M <= NT;
+  // h / n_j for the columns; an attempt of size H = h 2^-level takes
+  // hj[j] 2^-level, the same double as H / n_j (scaling by a power of two is
+  // exact), so no attempt divides
+  double hj[kMaxBsK + 1];
+  for (int j = 1; j <= kmax; ++j) hj[j] = h / (2 * j);
+  const double tol_up = next_up(P.bs_tol);
   BsCtx cs = c;
   if (can_spec) cs.base = spec;
   int level = 0;
@@ -366,6 +425,7 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
   int merges = 0;
   while (done < (1ll << level)) {
     const double H = ldexp(h, -level);
+    const double sc = ldexp(1.0, -level);
     const bool sp = can_spec && level + 1 <= P.bs_max_halvings;
     if (rec && rec_n < rec->cap) {  // stage the substep's start (kept if it is accepted)
       for (int b = tid; b < M; b += NT) {
@@ -400,7 +460,7 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
     tally.derivs += 1;
     long long sderivs = 0;
     if (sp) {
-      sderivs = bs_attempt_pair(c, cs, P, H, sy, tally);
+      sderivs = bs_attempt_pair(c, cs, P, hj, sc, sy, tally);
     } else {
       for (int ja = 1; ja <= kmax && !s_flags[0]; ja += W) {
         const int jb = ja + W - 1 < kmax ? ja + W - 1 : kmax;
@@ -410,7 +470,7 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
           const int j = ja + it / M, b = it % M;
           double* s = c.base + (size_t)b * c.stride;
           double* col = s + bs_off_col(j);
-          const double hs = H / (2 * j);
+          const double hs = hj[j] * sc;
           for (int k = 0; k < 6; ++k) {
             col[CZM + k] = s[OY + k];
             col[CZC + k] = s[OY + k] + hs * s[OF0 + k];
@@ -431,7 +491,7 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
             const int j = j0 + it / M, b = it % M;
             double* s = c.base + (size_t)b * c.stride;
             double* col = s + bs_off_col(j);
-            const double hs = H / (2 * j);
+            const double hs = hj[j] * sc;
             if (t < 2 * j) {
               for (int k = 0; k < 6; ++k) {
                 const double zn = col[CZM + k] + 2.0 * hs * col[CF + k];
@@ -446,38 +506,30 @@ static __device__ int bs_integrate(const BsCtx& c, const Phys& P, double h, Sy& 
           sy.sync();
           if ((t & 1) || t / 2 < ja) continue;
           const int j = t / 2;  // column j is complete: Neville row j and the test
-          double emax = 0.0;
+          bool fail = false;
           for (int b = tid; b < M; b += NT) {
             double* s = c.base + (size_t)b * c.stride;
             double* Tc = s + offT + (j & 1) * kmax * 6;
             double* Tp = s + offT + ((j - 1) & 1) * kmax * 6;
             for (int q = 1; q < j; ++q) {
-              // 1 / ((n_j / n_{j-q})^2 - 1) = (j - q)^2 / (q (2j - q)) for n_k = 2k
-              const double inv = (double)((j - q) * (j - q)) / (double)(q * (2 * j - q));
+              const double inv = kNeville.w[j][q];
               for (int k = 0; k < 6; ++k) {
                 const double tq = Tc[6 * (q - 1) + k];
                 Tc[6 * q + k] = __fma_rn(tq - Tp[6 * (q - 1) + k], inv, tq);
               }
             }
-            if (j >= 3 && bs_alive(c, b)) {
-              const double* A = Tc + 6 * (j - 1);
-              const double* B = Tc + 6 * (j - 2);
-              for (int part = 0; part < 2; ++part) {
-                double dm = 0.0, ym = 0.0;
-                for (int k = 3 * part; k < 3 * part + 3; ++k) {
-                  dm = fmax(dm, fabs(A[k] - B[k]));
-                  ym = fmax(ym, fabs(A[k]));
-                }
-                emax = fmax(emax, dm / (ym + 1e-300));
-              }
-            }
+            if (j >= 3 && bs_alive(c, b) &&
+                !bs_member_ok(Tc + 6 * (j - 1), Tc + 6 * (j - 2), P.bs_tol, tol_up))
+              fail = true;
           }
-          const double e = sy.max_to_first(emax);  // valid in tid 0
-          if (tid == 0) {
-            if (j >= 3 && e <= P.bs_tol) {
-              s_flags[0] = 1;
-              s_flags[1] = j;
-            }
+          if (j < 3) {
+            sy.sync();
+            continue;
+          }
+          const bool F = sy.any_to_first(fail);  // valid in tid 0
+          if (tid == 0 && !F) {
+            s_flags[0] = 1;
+            s_flags[1] = j;
           }
           sy.sync();
           if (s_flags[0]) {
@@ -583,7 +635,8 @@ struct BlockTeam {
     if (threadIdx.x == 0)
       for (int q = 0; q < (int)blockDim.x; ++q) e = fmax(e, s_red[q]);
     return e;
-  }
+  }  // whether v holds in any thread (here: in all of them)
+  __device__ bool any_to_first(bool v) const { return __syncthreads_or(v) != 0; }
 };
 
 // One warp as the team (small groups: a CTA integrates one group per warp
@@ -597,7 +650,7 @@ struct WarpTeam {
   __device__ double max_to_first(double v) const {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
-  }
+  }  __device__ bool any_to_first(bool v) const { return __any_sync(0xffffffffu, v) != 0; }
 };
 
 static __device__ int bs_integrate_group(const BsCtx& c, const Phys& P, double h, double* s_red,

@@ -642,7 +642,8 @@ struct ClusterTeam {
     if (tid() == 0)
       for (int q = 0; q < ncta; ++q) e = fmax(e, s_slot[q]);
     return e;
-  }
+  }  // whether v holds in any thread (valid in the first thread)
+  __device__ bool any_to_first(bool v) const { return max_to_first(v ? 1.0 : 0.0) > 0.0; }
 };
 
 __global__ void __launch_bounds__(CNT) k_bs_cluster(Dev d, Phys P, double h, int min_m) {

@@ -1,8 +1,8 @@
 // Universal-variable Kepler drift (the first sum of Eq. Ha: Kepler motion
 // about mu = G m0, "solved analytically"), shared by the single-system drift
 // kernel, the batched kernel and the adjoint. The solver is written once,
-// templated on its scalar type: double for the integrator, Dual6 (value and
-// six partial derivatives) for the adjoint's Jacobian of the drift map.
+// templated on its scalar type: double for the integrator, Dual<1> (value
+// and one partial derivative) for the adjoint's Jacobian of the drift map.
 #pragma once
 
 #include "nb_internal.cuh"
@@ -10,97 +10,127 @@
 namespace nb {
 
 // ---------------------------------------------------------------------------
-// Forward-mode dual numbers with six partials (the Jacobian of (x, v) -> (x', v')).
-// They live in their own namespace so that their sqrt/log/fabs/copysign are
-// found only by argument-dependent lookup and never hide the double versions.
+// Forward-mode dual numbers with ND partials: ND = 6 carries the whole
+// Jacobian of (x, v) -> (x', v'), ND = 1 one of its columns (one input
+// direction per thread). They live in their own namespace so that their
+// sqrt/log/fabs/copysign are found only by argument-dependent lookup and
+// never hide the double versions.
 // ---------------------------------------------------------------------------
 namespace ad {
-struct Dual6 {
+template <int ND>
+struct Dual {
   double v;
-  double d[6];
+  double d[ND];
 };
 
-__device__ __forceinline__ double val(const Dual6& a) { return a.v; }
+template <int ND>
+__device__ __forceinline__ double val(const Dual<ND>& a) { return a.v; }
 
-__device__ __forceinline__ Dual6 mkd(double v) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> mkd(double v) {
+  Dual<ND> r;
   r.v = v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = 0.0;
+  for (int k = 0; k < ND; ++k) r.d[k] = 0.0;
   return r;
 }
-__device__ __forceinline__ Dual6 operator+(const Dual6& a, const Dual6& b) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator+(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r;
   r.v = a.v + b.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] + b.d[k];
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] + b.d[k];
   return r;
 }
-__device__ __forceinline__ Dual6 operator-(const Dual6& a, const Dual6& b) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator-(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r;
   r.v = a.v - b.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] - b.d[k];
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] - b.d[k];
   return r;
 }
-__device__ __forceinline__ Dual6 operator-(const Dual6& a) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator-(const Dual<ND>& a) {
+  Dual<ND> r;
   r.v = -a.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = -a.d[k];
+  for (int k = 0; k < ND; ++k) r.d[k] = -a.d[k];
   return r;
 }
-__device__ __forceinline__ Dual6 operator*(const Dual6& a, const Dual6& b) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator*(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r;
   r.v = a.v * b.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
   return r;
 }
-__device__ __forceinline__ Dual6 operator/(const Dual6& a, const Dual6& b) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator/(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r;
   r.v = a.v / b.v;
   const double ib = 1.0 / b.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
   return r;
 }
-__device__ __forceinline__ Dual6 operator+(const Dual6& a, double b) { Dual6 r = a; r.v += b; return r; }
-__device__ __forceinline__ Dual6 operator+(double b, const Dual6& a) { return a + b; }
-__device__ __forceinline__ Dual6 operator-(const Dual6& a, double b) { Dual6 r = a; r.v -= b; return r; }
-__device__ __forceinline__ Dual6 operator-(double b, const Dual6& a) { return -(a - b); }
-__device__ __forceinline__ Dual6 operator*(const Dual6& a, double b) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator+(const Dual<ND>& a, double b) {
+  Dual<ND> r = a;
+  r.v += b;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator+(double b, const Dual<ND>& a) { return a + b; }
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator-(const Dual<ND>& a, double b) {
+  Dual<ND> r = a;
+  r.v -= b;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator-(double b, const Dual<ND>& a) { return -(a - b); }
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator*(const Dual<ND>& a, double b) {
+  Dual<ND> r;
   r.v = a.v * b;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * b;
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b;
   return r;
 }
-__device__ __forceinline__ Dual6 operator*(double b, const Dual6& a) { return a * b; }
-__device__ __forceinline__ Dual6 operator/(const Dual6& a, double b) { return a * (1.0 / b); }
-__device__ __forceinline__ Dual6 operator/(double a, const Dual6& b) { return mkd(a) / b; }
-__device__ __forceinline__ Dual6 sqrt(const Dual6& a) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator*(double b, const Dual<ND>& a) { return a * b; }
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator/(const Dual<ND>& a, double b) { return a * (1.0 / b); }
+template <int ND>
+__device__ __forceinline__ Dual<ND> operator/(double a, const Dual<ND>& b) { return mkd<ND>(a) / b; }
+template <int ND>
+__device__ __forceinline__ Dual<ND> sqrt(const Dual<ND>& a) {
+  Dual<ND> r;
   r.v = ::sqrt(a.v);
   const double h = 0.5 / r.v;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * h;
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * h;
   return r;
 }
-__device__ __forceinline__ Dual6 log(const Dual6& a) {
-  Dual6 r;
+template <int ND>
+__device__ __forceinline__ Dual<ND> log(const Dual<ND>& a) {
+  Dual<ND> r;
   r.v = ::log(a.v);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] / a.v;
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] / a.v;
   return r;
 }
-__device__ __forceinline__ Dual6 fabs(const Dual6& a) { return a.v < 0.0 ? -a : a; }
-__device__ __forceinline__ Dual6 copysign(const Dual6& a, const Dual6& s) {
+template <int ND>
+__device__ __forceinline__ Dual<ND> fabs(const Dual<ND>& a) { return a.v < 0.0 ? -a : a; }
+template <int ND>
+__device__ __forceinline__ Dual<ND> copysign(const Dual<ND>& a, const Dual<ND>& s) {
   return (a.v < 0.0) != (s.v < 0.0) ? -a : a;
 }
 }  // namespace ad
 
-using ad::Dual6;
+using ad::Dual;
 using ad::mkd;
 __device__ __forceinline__ double val(double a) { return a; }
 using ad::val;

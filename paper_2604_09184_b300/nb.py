@@ -29,7 +29,7 @@ NB_PREC_MIXED = 1
 NB_PREC_DS = 2
 NB_MATH_EXP, NB_MATH_RCP, NB_MATH_RSQRT, NB_MATH_RPOW32 = 0, 1, 2, 3
 NB_MATH_RPOW32_MIXED, NB_MATH_RPOW32_M, NB_MATH_CLOSE_WEIGHT = 4, 5, 6
-NB_MATH_MASS15, NB_MATH_MASS1875 = 7, 8
+NB_MATH_MASS15, NB_MATH_MASS1875, NB_MATH_NEVILLE, NB_MATH_RATIO_LE = 7, 8, 9, 10
 
 
 class NbParams(C.Structure):
@@ -549,6 +549,20 @@ def math_eval(fn: int, x):
     x = x.contiguous()
     out = torch.empty_like(x)
     code = lib().nb_math_eval(fn, x.numel(), _ptr(x), _ptr(out), _stream(torch))
+    if code != NB_OK:
+        raise NbError(code, "nb_math_eval")
+    return out
+
+
+def ratio_le(a, b, tol):
+    """The direct solver's acceptance test fl(a / b) <= tol, element-wise on
+    float64 CUDA tensors a, b, tol of one length (NB_MATH_RATIO_LE); returns
+    a float64 tensor of 1.0 / 0.0."""
+    torch = _torch()
+    tri = torch.stack([a, b, tol], dim=1).contiguous()
+    out = torch.empty(tri.shape[0], dtype=torch.float64, device=tri.device)
+    code = lib().nb_math_eval(NB_MATH_RATIO_LE, tri.shape[0], _ptr(tri), _ptr(out),
+                              _stream(torch))
     if code != NB_OK:
         raise NbError(code, "nb_math_eval")
     return out

@@ -119,6 +119,49 @@ def test_mass_coefficients(nb):
     assert m15[~nz].tolist() == [0.0] and m1875[~nz].tolist() == [0.0]
 
 
+def test_neville_weights_are_the_correctly_rounded_quotients(nb):
+    """The direct solver's Neville weights 1 / ((n_j / n_{j-q})^2 - 1) for
+    n_k = 2k, read from its table, equal the IEEE quotients (j - q)^2 /
+    (q (2j - q)) bit for bit (the values the division gave at run time)."""
+    x = np.array([16 * j + q for j in range(13) for q in range(16)], dtype=np.float64)
+    got = evaluate(nb, nb.NB_MATH_NEVILLE, x)
+    want = np.array([((j - q) ** 2 / (q * (2 * j - q))) if 1 <= q < j else 0.0
+                     for j in range(13) for q in range(16)])
+    assert np.array_equal(got, want)
+    assert got[16 * 2 + 1] == 1.0 / 3.0  # (n_2 / n_1)^2 - 1 = 3
+
+
+def test_acceptance_test_equals_the_division(nb):
+    """The solver's division-free acceptance test decides fl(a / b) <= tol
+    exactly as the IEEE division does: random quotients, quotients within a
+    few ulps of tol on either side, exact ones (b a power of two) at tol and
+    its neighbours, and non-finite values (a NaN or inf / inf rejects)."""
+    rng = np.random.default_rng(11)
+    n = 20000
+    tol = 10.0 ** rng.uniform(-16, -6, n)
+    b = 10.0 ** rng.uniform(-3, 3, n)
+    a_rand = b * tol * 10.0 ** rng.uniform(-1, 1, n)
+    near = [b * tol]
+    for k in (1, 2, 3):
+        near.append(np.nextafter(near[-1], np.inf))
+    lo = [b * tol]
+    for k in (1, 2, 3):
+        lo.append(np.nextafter(lo[-1], -np.inf))
+    b2 = 2.0 ** rng.integers(-20, 20, n).astype(np.float64)
+    exact_q = [tol * b2, np.nextafter(tol, np.inf) * b2, np.nextafter(tol, 0.0) * b2]
+    A = np.concatenate([a_rand] + near + lo + exact_q + [np.zeros(4)])
+    B = np.concatenate([b] * 9 + [b2] * 3 + [np.ones(4)])
+    T = np.concatenate([tol] * 12 + [np.full(4, 1e-14)])
+    A = np.concatenate([A, [np.inf, 1.0, np.nan, np.inf, 0.0]])
+    B = np.concatenate([B, [1.0, np.inf, 1.0, np.inf, 1e-300]])
+    T = np.concatenate([T, [1e-14, 1e-14, 1e-14, 1e-14, 0.0]])
+    with np.errstate(invalid="ignore"):
+        want = (A / B <= T).astype(np.float64)
+    got = nb.ratio_le(*(torch.as_tensor(v, device="cuda") for v in (A, B, T))).cpu().numpy()
+    assert np.array_equal(got, want)
+    assert 0 < want.sum() < len(want)
+
+
 def test_invalid_function_rejected(nb):
     L = nb.lib()
     assert L.nb_math_eval(99, 0, None, None, None) == nb.NB_E_INVALID
