@@ -389,7 +389,8 @@ int nb_kick_noalloc(int n, const double* x, const double* m, const double* rc, d
  * Device arrays: x, v [n][3], m [n], alive [n] int32 (0 = absorbed; NULL =
  * every body live); outputs gx, gv [n][3], gm [n] (zero for absorbed
  * bodies). scratch: nb_energy_grad_scratch_bytes(n) bytes of device memory,
- * 8-byte aligned. Asynchronous on the stream. NB_E_INVALID for n < 1, null
+ * 8-byte aligned (the pair sums' per-chunk partials, at most 256 n doubles,
+ * and the momentum's per-block sums). Asynchronous on the stream. NB_E_INVALID for n < 1, null
  * arrays or m0 <= 0; NB_E_WORKSPACE for a short or misaligned scratch. */
 size_t nb_energy_grad_scratch_bytes(int n);
 int nb_energy_grad(int n, const double* x, const double* v, const double* m, const int* alive,

@@ -440,8 +440,8 @@ int nb_step(nb_system* s, int nsteps, double dt) {
       NB_CU(cudaEventRecord(s->ev_fork, s->st));
       NB_CU(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
       launch_finish_part(d, s->P, 1, s->side);
+      launch_bs(d, s->P, dt, s->st, s->side);  // the cluster solver's launch on the side stream
       NB_CU(cudaEventRecord(s->ev_join, s->side));
-      launch_bs(d, s->P, dt, s->st);
       NB_CU(cudaStreamWaitEvent(s->st, s->ev_join, 0));
     }
     {

@@ -775,7 +775,7 @@ int bs_launches(const Dev& d, const Phys& P) {
   return (P.ml_levels == 0 && P.bs_cluster_min > 0 && d.n >= P.bs_cluster_min) ? 2 : 1;
 }
 
-void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
+void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st, cudaStream_t side) {
   int grid = d.n < 2 * 148 ? d.n : 2 * 148;
   if (grid < 1) grid = 1;
   if (P.ml_levels > 0) {
@@ -785,7 +785,9 @@ void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st) {
   // <= 48 KB for bs_kmax <= 12 (2 warps x 8 slots x 376 doubles)
   const size_t wsm = (size_t)(BNT / 32) * kWarpGroupMax * d.bs_stride * sizeof(double);
   k_bs_t<false><<<grid, BNT, wsm, st>>>(d, P, h);
-  if (bs_launches(d, P) == 2) launch_bs_cluster(d, P, h, st);
+  // the cluster solver takes the other groups (disjoint rows of gnew): on the
+  // side stream, when there is one, it runs beside the warp and CTA solver
+  if (bs_launches(d, P) == 2) launch_bs_cluster(d, P, h, side ? side : st);
 }
 
 // ---------------------------------------------------------------------------

@@ -145,14 +145,76 @@ __global__ void __launch_bounds__(EGT) k_egrad_momentum(int n, const double* __r
   }
 }
 
-__global__ void __launch_bounds__(EGT) k_egrad(int n, const double* __restrict__ x,
+// Source chunks of the pair sums: about 8 CTAs per SM over target tiles x
+// chunks, chunks of at least 64 sources, at most 64 chunks. Depends on n only.
+constexpr int EPT = 128;  // targets (threads) per CTA of the pair sums
+inline int egrad_split(int n) {
+  const int tiles = (n + EPT - 1) / EPT;
+  int S = (8 * 148 + tiles - 1) / tiles;
+  if (S > n / 64) S = n / 64;
+  if (S > 64) S = 64;
+  return S < 1 ? 1 : S;
+}
+
+// Partial pair sums of the j-chunk blockIdx.y for the targets of the tile
+// blockIdx.x: sum_j m_j (x_i - x_j) / r^3 and sum_j m_j / r into part
+// [S][4][n]. r^2 on the integer pipe and 1/r from the seeded reciprocal root.
+__global__ void __launch_bounds__(EPT) k_egrad_pairs(int n, int chunk, const double* __restrict__ x,
+                                                    const double* __restrict__ m,
+                                                    const int* __restrict__ alive,
+                                                    double* __restrict__ part) {
+  __shared__ double sx[EPT], sy[EPT], sz[EPT], sm[EPT];
+  const int i = blockIdx.x * EPT + threadIdx.x;
+  const bool live = i < n && (!alive || alive[i]);
+  const double xi = live ? x[3 * i] : 0.0, yi = live ? x[3 * i + 1] : 0.0,
+               zi = live ? x[3 * i + 2] : 0.0;
+  const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+  double fx = 0.0, fy = 0.0, fz = 0.0, pot = 0.0;
+  for (int jt = j0; jt < j1; jt += EPT) {
+    __syncthreads();
+    const int j = jt + threadIdx.x;
+    if (j < j1) {
+      sx[threadIdx.x] = x[3 * j];
+      sy[threadIdx.x] = x[3 * j + 1];
+      sz[threadIdx.x] = x[3 * j + 2];
+      sm[threadIdx.x] = (!alive || alive[j]) ? m[j] : 0.0;
+    }
+    __syncthreads();
+    const int cnt = min(EPT, j1 - jt);
+    if (live) {
+      for (int q = 0; q < cnt; ++q) {
+        const double dx = xi - sx[q], dy = yi - sy[q], dz = zi - sz[q];
+        const double r2 = sep2_int(dx, dy, dz);
+        if (__double_as_longlong(r2) == 0ll) continue;  // the body itself
+        const double ir = rinv_fast(r2);
+        const double mir = sm[q] * ir;
+        const double mir3 = mir * (ir * ir);
+        fx = __fma_rn(mir3, dx, fx);
+        fy = __fma_rn(mir3, dy, fy);
+        fz = __fma_rn(mir3, dz, fz);
+        pot += mir;
+      }
+    }
+  }
+  if (i < n) {
+    double* o = part + (size_t)blockIdx.y * 4 * n;
+    o[i] = fx;
+    o[n + i] = fy;
+    o[2 * n + i] = fz;
+    o[3 * n + i] = pot;
+  }
+}
+
+// The chunks' partial sums in chunk order, the momentum from the per-block
+// sums in block order, and the gradient of every body.
+__global__ void __launch_bounds__(EGT) k_egrad(int n, int S, const double* __restrict__ part,
+                                               const double* __restrict__ x,
                                                const double* __restrict__ v,
                                                const double* __restrict__ m,
                                                const int* __restrict__ alive, double G, double m0,
                                                int nparts, const double* __restrict__ parts,
                                                double* __restrict__ gx, double* __restrict__ gv,
                                                double* __restrict__ gm) {
-  __shared__ double sx[EGT], sy[EGT], sz[EGT], sm[EGT];
   __shared__ double Psh[3];
   if (threadIdx.x < 3) {
     Neu a{0.0, 0.0};
@@ -162,45 +224,10 @@ __global__ void __launch_bounds__(EGT) k_egrad(int n, const double* __restrict__
     }
     Psh[threadIdx.x] = a.s + a.c;
   }
-  const int i = blockIdx.x * EGT + threadIdx.x;
-  const bool live = i < n && (!alive || alive[i]);
-  const double xi = live ? x[3 * i] : 0.0, yi = live ? x[3 * i + 1] : 0.0,
-               zi = live ? x[3 * i + 2] : 0.0;
-  double fx = 0.0, fy = 0.0, fz = 0.0, pot = 0.0;
-  for (int jt = 0; jt < n; jt += EGT) {
-    __syncthreads();
-    const int j = jt + threadIdx.x;
-    if (j < n) {
-      const bool lj = !alive || alive[j];
-      sx[threadIdx.x] = x[3 * j];
-      sy[threadIdx.x] = x[3 * j + 1];
-      sz[threadIdx.x] = x[3 * j + 2];
-      sm[threadIdx.x] = lj ? m[j] : 0.0;
-    }
-    __syncthreads();
-    const int cnt = min(EGT, n - jt);
-    if (live) {
-      double tx = 0.0, ty = 0.0, tz = 0.0, tp = 0.0;
-      for (int q = 0; q < cnt; ++q) {
-        const double dx = xi - sx[q], dy = yi - sy[q], dz = zi - sz[q];
-        const double r2 = sep2(dx, dy, dz);
-        if (r2 == 0.0) continue;  // the body itself (absorbed bodies have no mass)
-        const double ir = inv_r(r2);
-        const double mir = sm[q] * ir;
-        const double mir3 = mir * ir * ir;
-        tx = __fma_rn(mir3, dx, tx);
-        ty = __fma_rn(mir3, dy, ty);
-        tz = __fma_rn(mir3, dz, tz);
-        tp += mir;
-      }
-      fx += tx;
-      fy += ty;
-      fz += tz;
-      pot += tp;
-    }
-  }
   __syncthreads();
+  const int i = blockIdx.x * EGT + threadIdx.x;
   if (i >= n) return;
+  const bool live = !alive || alive[i];
   if (!live) {
     for (int k = 0; k < 3; ++k) {
       gx[3 * i + k] = 0.0;
@@ -209,6 +236,15 @@ __global__ void __launch_bounds__(EGT) k_egrad(int n, const double* __restrict__
     gm[i] = 0.0;
     return;
   }
+  double fx = 0.0, fy = 0.0, fz = 0.0, pot = 0.0;
+  for (int c = 0; c < S; ++c) {
+    const double* o = part + (size_t)c * 4 * n;
+    fx += o[i];
+    fy += o[n + i];
+    fz += o[2 * n + i];
+    pot += o[3 * n + i];
+  }
+  const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
   const double mi = m[i];
   const double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
   const double r = sqrt(xi * xi + yi * yi + zi * zi);
@@ -234,7 +270,9 @@ void launch_energy(const Dev& d, const Phys& P, double* out8, cudaStream_t st) {
 
 extern "C" size_t nb_energy_grad_scratch_bytes(int n) {
   if (n < 1) return 0;
-  return sizeof(double) * 6 * (size_t)((n + nb::EGT - 1) / nb::EGT);
+  // the momentum's per-block sums, then the pair sums' partials (256-byte aligned)
+  const size_t mom = (sizeof(double) * 6 * (size_t)((n + nb::EGT - 1) / nb::EGT) + 255) & ~(size_t)255;
+  return mom + sizeof(double) * 4 * (size_t)n * (size_t)nb::egrad_split(n);
 }
 
 extern "C" int nb_energy_grad(int n, const double* x, const double* v, const double* m,
@@ -246,9 +284,14 @@ extern "C" int nb_energy_grad(int n, const double* x, const double* v, const dou
     return NB_E_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   const int nb = (n + nb::EGT - 1) / nb::EGT;
+  const int S = nb::egrad_split(n);
   double* parts = (double*)scratch;
+  double* part = (double*)((char*)scratch +
+                           ((sizeof(double) * 6 * (size_t)nb + 255) & ~(size_t)255));
   nb::k_egrad_momentum<<<nb, nb::EGT, 0, st>>>(n, v, m, alive, parts);
-  nb::k_egrad<<<nb, nb::EGT, 0, st>>>(n, x, v, m, alive, G, m0, nb, parts, gx, gv, gm);
+  nb::k_egrad_pairs<<<dim3((n + nb::EPT - 1) / nb::EPT, S), nb::EPT, 0, st>>>(
+      n, (n + S - 1) / S, x, m, alive, part);
+  nb::k_egrad<<<nb, nb::EGT, 0, st>>>(n, S, part, x, v, m, alive, G, m0, nb, parts, gx, gv, gm);
   if (cudaGetLastError() != cudaSuccess) return NB_E_CUDA;
   return NB_OK;
 }

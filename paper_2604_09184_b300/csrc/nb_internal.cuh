@@ -606,7 +606,8 @@ void launch_open_h(const Dev& d, double h, cudaStream_t st);
 void launch_drift_h(const Dev& d, const Phys& P, double h, cudaStream_t st);
 void launch_close_h(const Dev& d, const Phys& P, double h, int last, cudaStream_t st);
 void launch_encounter(const Dev& d, const Phys& P, cudaStream_t st);
-void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st);
+void launch_bs(const Dev& d, const Phys& P, double h, cudaStream_t st,
+               cudaStream_t side = nullptr);
 int bs_launches(const Dev& d, const Phys& P);  // kernels launch_bs launches
 void launch_scatter(const Dev& d, const Phys& P, cudaStream_t st);
 void launch_init_in(const Dev& d, const Phys& P, const double* x3, const double* v3,
