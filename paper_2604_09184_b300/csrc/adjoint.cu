@@ -291,12 +291,15 @@ __global__ void __launch_bounds__(ANT) k_kepler_vjp(int n, const double* xs6, co
 __host__ __device__ constexpr int adj_nstates(int kmax) { return kmax * kmax + 2 * kmax; }
 __host__ __device__ constexpr int adj_sidx(int j, int t) { return j * j - 1 + t; }
 
-// Per-member-slot scratch (doubles): recorded substep starts (kSubCap x
-// (6 + 4)), the midpoint states of one substep and their adjoints, a
-// derivative buffer per column, f0 and its adjoint, the running adjoint
-// (6 state + 1 mass), an accumulator (6) and a mass accumulator per column.
-__host__ __device__ inline int adj_slot_stride(int kmax) {
-  return kSubCap * 10 + 12 * adj_nstates(kmax) + 7 * kmax + 25;
+// Per-member record of a step's direct-solver replay (doubles): the starts
+// of the accepted substeps (kSubCap x (6 + 4)).
+__host__ __device__ constexpr int adj_rec_stride() { return kSubCap * 10; }
+// Per-member scratch of the reverse (doubles): the midpoint states of one
+// substep and their adjoints, a derivative buffer per column, f0 and its
+// adjoint, the running adjoint (6 state + 1 mass), an accumulator (6) and a
+// mass accumulator per column.
+__host__ __device__ inline int adj_work_stride(int kmax) {
+  return 12 * adj_nstates(kmax) + 7 * kmax + 25;
 }
 
 // Weights of the extrapolated value: T_kk = sum_j c_kj T_j1, the Neville
@@ -337,21 +340,25 @@ __device__ __forceinline__ double pow2_ratio(double H, double h) {
 }
 
 struct AdjGroupArgs {
-  int n, kmax, bs_stride, slot_stride;
+  int n, kmax, bs_stride, work_stride;
   const int* grp;  // [0] ngroups [1] nmembers [2..] off[ng+1] then members
   const double* xs6;
   const double *m0, *R0, *rc0;
   double* lx[3];
   double* lv[3];
   double* lm;
-  double* gscr;
-  double* gnew;
-  double* slot;    // n * slot_stride
+  double* gscr;    // the record pass's scratch for groups of more than 8 bodies
+  // the step's record buffer: written by the record pass, read by the reverse
+  double* rslot;   // n * adj_rec_stride()
+  double* gend;    // n * 10: the record pass's working copies, left at the end state
   double* H;       // n * kSubCap
   int* kk;         // n * kSubCap
-  int* counts;     // n * 4
+  int* counts;     // n * 4: substeps, mergers, overflow, the record's status
   int* mrg;        // n * kMrgCap * 3
   double* mst;     // n * kMrgCap * 14
+  // the reverse's own scratch
+  double* work;    // n * work_stride
+  double* gwork;   // n * 10
   int* status;
 };
 
@@ -442,38 +449,112 @@ __device__ void grp_vjp(const BsCtx& c, const double* z, const double* w, int b,
 // cw is the team's shared scratch for the extrapolation weights.
 // scr: the team's direct-solver scratch (M slots of bs_stride doubles;
 // nslots >= 2 M lets the replay speculate on half-size attempts).
+// The record pass of one group's adjoint by a team (one warp or one CTA):
+// replay the group's integration from the step's saved state with the
+// direct solver, recording every accepted substep's start, size and column
+// and every merger into the step's record buffer (counts[3] = the status).
+// scr: the team's direct-solver scratch (M slots of bs_stride doubles;
+// nslots >= 2 M lets the replay speculate on half-size attempts).
 template <class Team>
-__device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
-                                 Team& team, double* cw, double* scr,
-                                 int nslots) {
+__device__ void bs_record_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
+                                Team& team, double* scr, int nslots) {
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int* gmem = A.grp + 2 + ng + 1;
   const int n = A.n;
+  const int tid = team.tid(), NT = team.nthreads();
+  const int off = goff[grp];
+  BsCtx c;
+  c.M = goff[grp + 1] - off;
+  c.stride = A.bs_stride;
+  c.base = scr;
+  c.g = A.gend + (size_t)off * 10;
+  c.kmax = A.kmax;
+  c.G = P.G;
+  c.mu = P.mu;
+  c.mu15 = 1.5 * P.mu;
+  c.mu1875 = 1.875 * P.mu;
+  const int M = c.M;
+  // the group's contiguous record block, arrays of M members each
+  double* r_ys = A.rslot + (size_t)off * adj_rec_stride();
+  BsRec rec;
+  rec.cap = kSubCap;
+  rec.mcap = kMrgCap;
+  rec.counts = A.counts + 4 * (size_t)grp;
+  rec.H = A.H + (size_t)grp * kSubCap;
+  rec.k = A.kk + (size_t)grp * kSubCap;
+  rec.ys = r_ys;
+  rec.ms = r_ys + (size_t)kSubCap * M * 6;
+  rec.Rs = rec.ms + (size_t)kSubCap * M;
+  rec.rcs = rec.Rs + (size_t)kSubCap * M;
+  rec.alv = rec.rcs + (size_t)kSubCap * M;
+  rec.mrg = A.mrg + (size_t)grp * kMrgCap * 3;
+  rec.mst = A.mst + (size_t)grp * kMrgCap * 14;
+  for (int b = tid; b < M; b += NT) {
+    const int body = gmem[off + b];
+    double* y = c.base + (size_t)b * c.stride + OY;
+    for (int k = 0; k < 6; ++k) y[k] = A.xs6[(size_t)k * n + body];
+    double* g = c.g + 10 * b;
+    g[6] = A.m0[body]; g[7] = A.R0[body]; g[8] = A.rc0[body]; g[9] = 1.0;
+    bs_set_aux(c, b, P.G, g[6], g[8]);
+  }
+  if (tid == 0) {
+    rec.counts[0] = 0; rec.counts[1] = 0; rec.counts[2] = 0; rec.counts[3] = 0;
+  }
+  team.sync();
+  BsTally tally{0, 0, 0, 0};
+  double El = 0.0;
+  int st = bs_integrate(c, P, h, team, tally, &El, &rec,
+                        P.bs_speculate && 2 * M <= nslots ? scr + (size_t)M * c.stride : nullptr);
+  team.sync();
+  if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
+  if (st && tid == 0) {
+    rec.counts[3] = st;
+    atomicCAS(A.status, 0, st);
+  }
+  team.sync();
+}
+
+// The reverse of one group's integration by a team, from the record pass's
+// buffer: pull the adjoint back through the recorded substeps, last first.
+// Per substep: undo the mergers that followed it (merge map x' = (m_a x_a +
+// m_b x_b) / M, M = m_a + m_b), replay the midpoint sequences of columns
+// 1..k (k the accepted column) keeping every state, and reverse them as a
+// wave over the columns; the Neville extrapolation is linear in the column
+// results, with weights c_j from the same recursion applied to unit vectors.
+// cw is the team's shared scratch for the extrapolation weights. A group
+// whose record pass failed is left alone (its status fails the pass).
+template <class Team>
+__device__ void bs_reverse_group(const AdjGroupArgs& A, const Phys& P, double h, int grp,
+                                 Team& team, double* cw) {
+  const int ng = A.grp[0];
+  const int* goff = A.grp + 2;
+  const int* gmem = A.grp + 2 + ng + 1;
   const int tid = team.tid(), NT = team.nthreads();
   const int NS = adj_nstates(A.kmax);
   double hj[kMaxBsK + 1];  // h / n_j
   for (int j = 1; j <= A.kmax; ++j) hj[j] = h / (2 * j);
   {
     const int off = goff[grp];
+    if (A.counts[4 * (size_t)grp + 3]) return;
     BsCtx c;
     c.M = goff[grp + 1] - off;
     c.stride = A.bs_stride;
-    c.base = scr;
-    c.g = A.gnew + (size_t)off * 10;
+    c.base = nullptr;
+    c.g = A.gwork + (size_t)off * 10;
     c.kmax = A.kmax;
     c.G = P.G;
     c.mu = P.mu;
     c.mu15 = 1.5 * P.mu;
     c.mu1875 = 1.875 * P.mu;
     const int M = c.M;
-    // the group's contiguous slot block, arrays of M members each
-    double* r_ys = A.slot + (size_t)off * A.slot_stride;
-    double* r_ms = r_ys + (size_t)kSubCap * M * 6;
-    double* r_Rs = r_ms + (size_t)kSubCap * M;
-    double* r_rcs = r_Rs + (size_t)kSubCap * M;
-    double* r_alv = r_rcs + (size_t)kSubCap * M;
-    double* zst = r_alv + (size_t)kSubCap * M;      // NS states x 6M
+    const double* r_ys = A.rslot + (size_t)off * adj_rec_stride();
+    const double* r_ms = r_ys + (size_t)kSubCap * M * 6;
+    const double* r_Rs = r_ms + (size_t)kSubCap * M;
+    const double* r_rcs = r_Rs + (size_t)kSubCap * M;
+    const double* r_alv = r_rcs + (size_t)kSubCap * M;
+    // the group's contiguous work block, arrays of M members each
+    double* zst = A.work + (size_t)off * A.work_stride;  // NS states x 6M
     double* lzst = zst + (size_t)NS * 6 * M;        // NS states x 6M
     double* fcol = lzst + (size_t)NS * 6 * M;       // kmax x 6M
     double* f0 = fcol + (size_t)A.kmax * 6 * M;     // 6M
@@ -483,44 +564,17 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
     double* lmv = lin + 6 * M;                      // M
     double* lmc = lmv + M;                          // kmax x M
     BsRec rec;
-    rec.cap = kSubCap;
-    rec.mcap = kMrgCap;
     rec.counts = A.counts + 4 * (size_t)grp;
     rec.H = A.H + (size_t)grp * kSubCap;
     rec.k = A.kk + (size_t)grp * kSubCap;
-    rec.ys = r_ys; rec.ms = r_ms; rec.Rs = r_Rs; rec.rcs = r_rcs; rec.alv = r_alv;
     rec.mrg = A.mrg + (size_t)grp * kMrgCap * 3;
     rec.mst = A.mst + (size_t)grp * kMrgCap * 14;
-    // forward replay from the saved state, recording the accepted substeps
-    for (int b = tid; b < M; b += NT) {
-      const int body = gmem[off + b];
-      double* y = c.base + (size_t)b * c.stride + OY;
-      for (int k = 0; k < 6; ++k) y[k] = A.xs6[(size_t)k * n + body];
-      double* g = c.g + 10 * b;
-      g[6] = A.m0[body]; g[7] = A.R0[body]; g[8] = A.rc0[body]; g[9] = 1.0;
-      bs_set_aux(c, b, P.G, g[6], g[8]);
-    }
-    if (tid == 0) {
-      rec.counts[0] = 0; rec.counts[1] = 0; rec.counts[2] = 0;
-    }
-    team.sync();
-    BsTally tally{0, 0, 0, 0};
-    double El = 0.0;
-    int st = bs_integrate(c, P, h, team, tally, &El, &rec,
-                          P.bs_speculate && 2 * M <= nslots ? scr + (size_t)M * c.stride
-                                                            : nullptr);
-    team.sync();
-    if (!st && rec.counts[2]) st = NB_E_OVERFLOW;
-    if (st) {
-      if (tid == 0) atomicCAS(A.status, 0, st);
-      return;
-    }
     const int nsub = rec.counts[0], nmrg = rec.counts[1];
     // adjoint at the end of the BS: members alive at the end take the step's
     // lambda; absorbed members start from zero
     for (int b = tid; b < M; b += NT) {
       const int body = gmem[off + b];
-      const bool live = c.g[10 * b + 9] != 0.0;
+      const bool live = A.gend[(size_t)(off + b) * 10 + 9] != 0.0;
       for (int k = 0; k < 3; ++k) {
         ly[6 * b + k] = live ? A.lx[k][body] : 0.0;
         ly[6 * b + 3 + k] = live ? A.lv[k][body] : 0.0;
@@ -692,28 +746,50 @@ __device__ void bs_adjoint_group(const AdjGroupArgs& A, const Phys& P, double h,
 }
 
 
-__global__ void __maxnreg__(168) k_bs_adjoint(AdjGroupArgs A, Phys P, double h) {
+// Record pass of a step's groups: groups of up to 8 bodies one per warp (the
+// warp's direct-solver scratch in dynamic shared memory), larger ones one per
+// CTA (scratch in gscr).
+__global__ void __maxnreg__(128) k_bs_record(AdjGroupArgs A, Phys P, double h) {
   __shared__ double s_red[ABNT];
   __shared__ int s_flags[4];
-  __shared__ double cw[ABNT / 32][kMaxBsK + 2];
   __shared__ int s_wflags[ABNT / 32][4];
   extern __shared__ double s_bscr[];  // the warp teams' scratch, 8 slots each
   const int ng = A.grp[0];
   const int* goff = A.grp + 2;
   const int warp = threadIdx.x >> 5;
-  // groups of up to 8 bodies: one per warp, warp barriers only
   WarpTeam wt{s_wflags[warp]};
   for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
     if (goff[grp + 1] - goff[grp] > 8) continue;
-    bs_adjoint_group(A, P, h, grp, wt, cw[warp],
-                     s_bscr + (size_t)warp * 8 * A.bs_stride, 8);
+    bs_record_group(A, P, h, grp, wt, s_bscr + (size_t)warp * 8 * A.bs_stride, 8);
   }
   __syncthreads();
   BlockTeam bt{s_red, s_flags};
   for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
     if (goff[grp + 1] - goff[grp] <= 8) continue;
-    bs_adjoint_group(A, P, h, grp, bt, cw[0], A.gscr + (size_t)goff[grp] * A.bs_stride,
-                     0);
+    bs_record_group(A, P, h, grp, bt, A.gscr + (size_t)goff[grp] * A.bs_stride, 0);
+  }
+}
+
+// Reverse of a step's groups from the record buffer: groups of up to 8
+// bodies one per warp, larger ones one per CTA.
+__global__ void __maxnreg__(168) k_bs_reverse(AdjGroupArgs A, Phys P, double h) {
+  __shared__ double s_red[ABNT];
+  __shared__ int s_flags[4];
+  __shared__ double cw[ABNT / 32][kMaxBsK + 2];
+  __shared__ int s_wflags[ABNT / 32][4];
+  const int ng = A.grp[0];
+  const int* goff = A.grp + 2;
+  const int warp = threadIdx.x >> 5;
+  WarpTeam wt{s_wflags[warp]};
+  for (int grp = blockIdx.x * (ABNT / 32) + warp; grp < ng; grp += gridDim.x * (ABNT / 32)) {
+    if (goff[grp + 1] - goff[grp] > 8) continue;
+    bs_reverse_group(A, P, h, grp, wt, cw[warp]);
+  }
+  __syncthreads();
+  BlockTeam bt{s_red, s_flags};
+  for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+    if (goff[grp + 1] - goff[grp] <= 8) continue;
+    bs_reverse_group(A, P, h, grp, bt, cw[0]);
   }
 }
 
@@ -818,9 +894,17 @@ struct nb_adjoint {
   int* alive0;
   int* alive1;
   int* status;
-  double *gscr, *gnew, *slot, *H, *mst;
-  int *kk, *counts, *mrg;
-  int slot_stride;
+  double* gscr;  // the record pass's direct-solver scratch (groups of more than 8 bodies)
+  // the records of two steps' direct-solver replays: the record pass of step
+  // t - 1 fills one on its own stream while the reverse of step t reads the other
+  struct RecBuf {
+    double *rslot, *gend, *H, *mst;
+    int *kk, *counts, *mrg;
+  } rb[2];
+  double *work, *gwork;  // the reverse's scratch
+  int work_stride;
+  cudaStream_t st3;  // the record passes' stream
+  cudaEvent_t ev_rec[2], ev_free[2], ev_seg;
   double* vpart;  // kick VJP partial sums, vjp_S x 4 x n
   int vjp_S;
   char err[256];
@@ -871,7 +955,7 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
   int* ck_i = c.take<int>((size_t)nck * (n + 2 * (size_t)pair_cap));
   Ctrl* ck_c = c.take<Ctrl>(nck);
   const int kmax = kmax_of(p);
-  const int stride = adj_slot_stride(kmax);
+  const int stride = adj_work_stride(kmax);
   std::vector<StepRec> recs(2 * (size_t)every);
   for (int t = 0; t < 2 * every; ++t) {
     recs[t].xs6 = c.take<double>(6 * (size_t)n);
@@ -888,13 +972,18 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
   int* alive1 = c.take<int>(n);
   int* status = c.take<int>(4);
   double* gscr = c.take<double>((size_t)n * bs_stride_for_kmax(kmax));
-  double* gnew = c.take<double>((size_t)n * 10);
-  double* slot = c.take<double>((size_t)n * stride);
-  double* H = c.take<double>((size_t)n * kSubCap);
-  int* kk = c.take<int>((size_t)n * kSubCap);
-  int* counts = c.take<int>((size_t)n * 4);
-  int* mrg = c.take<int>((size_t)n * kMrgCap * 3);
-  double* mst = c.take<double>((size_t)n * kMrgCap * 14);
+  nb_adjoint::RecBuf rb[2];
+  for (int q = 0; q < 2; ++q) {
+    rb[q].rslot = c.take<double>((size_t)n * adj_rec_stride());
+    rb[q].gend = c.take<double>((size_t)n * 10);
+    rb[q].H = c.take<double>((size_t)n * kSubCap);
+    rb[q].kk = c.take<int>((size_t)n * kSubCap);
+    rb[q].counts = c.take<int>((size_t)n * 4);
+    rb[q].mrg = c.take<int>((size_t)n * kMrgCap * 3);
+    rb[q].mst = c.take<double>((size_t)n * kMrgCap * 14);
+  }
+  double* work = c.take<double>((size_t)n * stride);
+  double* gwork = c.take<double>((size_t)n * 10);
   const int vS = vjp_split(n);
   double* vpart = c.take<double>((size_t)vS * 4 * n);
   if (a && base) {
@@ -912,8 +1001,10 @@ size_t adj_layout(const nb_params& p, int n, int nsteps, int every, char* base, 
     a->lvx = vec + 3 * n; a->lvy = vec + 4 * n; a->lvz = vec + 5 * n;
     a->lm = vec + 6 * n; a->mux = vec + 7 * n; a->muy = vec + 8 * n; a->muz = vec + 9 * n;
     a->parts = parts; a->alive0 = alive0; a->alive1 = alive1; a->status = status;
-    a->gscr = gscr; a->gnew = gnew; a->slot = slot; a->H = H; a->kk = kk;
-    a->counts = counts; a->mrg = mrg; a->mst = mst; a->slot_stride = stride;
+    a->gscr = gscr;
+    a->rb[0] = rb[0];
+    a->rb[1] = rb[1];
+    a->work = work; a->gwork = gwork; a->work_stride = stride;
   }
   (void)sysws;
   return al256(c.off);
@@ -1037,7 +1128,52 @@ void cdrift_vjp(nb_adjoint* a, const int* alive, const double* m, const double* 
 // the two are one kick_vjp of weight h, taken with the earlier step's closing
 // kick (close_w = h), and the later step skips its opening one (open = false).
 // The last step closes with h/2 and the first step opens with h/2.
-void backward_step(nb_adjoint* a, double dt, const StepRec& r, double close_w, bool open) {
+// The direct solver's arguments of a step: its groups and saved state, the
+// record buffer buf, the adjoint vectors and the reverse's scratch.
+AdjGroupArgs group_args(nb_adjoint* a, const StepRec& r, int buf) {
+  const int n = a->n;
+  const Phys& P = a->sys->P;
+  AdjGroupArgs A;
+  A.n = n;
+  A.kmax = P.bs_kmax;
+  A.bs_stride = bs_stride_for_kmax(P.bs_kmax);
+  A.work_stride = a->work_stride;
+  A.grp = r.grp;
+  A.xs6 = r.xs6;
+  A.m0 = r.st0; A.R0 = r.st0 + n; A.rc0 = r.st0 + 2 * n;
+  A.lx[0] = a->lx; A.lx[1] = a->ly; A.lx[2] = a->lz;
+  A.lv[0] = a->lvx; A.lv[1] = a->lvy; A.lv[2] = a->lvz;
+  A.lm = a->lm;
+  A.gscr = a->gscr;
+  const nb_adjoint::RecBuf& b = a->rb[buf];
+  A.rslot = b.rslot; A.gend = b.gend; A.H = b.H; A.kk = b.kk; A.counts = b.counts;
+  A.mrg = b.mrg; A.mst = b.mst;
+  A.work = a->work; A.gwork = a->gwork;
+  A.status = a->status;
+  return A;
+}
+
+int group_grid(int n) { return n < 2 * 148 ? n : 2 * 148; }
+
+// The record pass of a step (the direct solver's replay of its groups with
+// recording) into buffer buf, on stream st.
+void record_step(nb_adjoint* a, double dt, const StepRec& r, int buf, cudaStream_t st) {
+  const AdjGroupArgs A = group_args(a, r, buf);
+  const size_t wsm = (size_t)(ABNT / 32) * 8 * A.bs_stride * sizeof(double);  // <= 48.1 KB
+  if (wsm > 40 * 1024)  // with the static shared memory beyond the 48 KB default
+    cudaFuncSetAttribute(k_bs_record, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+  k_bs_record<<<group_grid(a->n), ABNT, wsm, st>>>(A, a->sys->P, dt);
+}
+
+// The reverse of one step, its direct-solver records in buffer buf. The
+// closing B(h/2) of a step and the opening B(h/2) of the next act at the same
+// positions, masses and critical radii, with nothing in between, and the
+// kick's transpose is linear in lambda_v: the two are one kick_vjp of weight
+// h, taken with the earlier step's closing kick (close_w = h), and the later
+// step skips its opening one (open = false). The last step closes with h/2
+// and the first step opens with h/2.
+void backward_step(nb_adjoint* a, double dt, const StepRec& r, double close_w, bool open,
+                   int buf) {
   const int n = a->n;
   const int g = (n + ANT - 1) / ANT;
   const double hh = 0.5 * dt;
@@ -1052,24 +1188,9 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r, double close_w, b
   const int gk = (((n + kKvBodies - 1) / kKvBodies) * 32 + ANT - 1) / ANT;
   k_kepler_vjp<<<gk, ANT, 0, a->st>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
                                       a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
-  AdjGroupArgs A;
-  A.n = n;
-  A.kmax = P.bs_kmax;
-  A.bs_stride = bs_stride_for_kmax(P.bs_kmax);
-  A.slot_stride = a->slot_stride;
-  A.grp = r.grp;
-  A.xs6 = r.xs6;
-  A.m0 = r.st0; A.R0 = r.st0 + n; A.rc0 = r.st0 + 2 * n;
-  A.lx[0] = a->lx; A.lx[1] = a->ly; A.lx[2] = a->lz;
-  A.lv[0] = a->lvx; A.lv[1] = a->lvy; A.lv[2] = a->lvz;
-  A.lm = a->lm;
-  A.gscr = a->gscr; A.gnew = a->gnew; A.slot = a->slot; A.H = a->H; A.kk = a->kk;
-  A.counts = a->counts; A.mrg = a->mrg; A.mst = a->mst; A.status = a->status;
-  int grid = n < 2 * 148 ? n : 2 * 148;
-  const size_t wsm = (size_t)(ABNT / 32) * 8 * A.bs_stride * sizeof(double);  // <= 48.1 KB
-  if (wsm > 40 * 1024)  // with the static shared memory beyond the 48 KB default
-    cudaFuncSetAttribute(k_bs_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
-  k_bs_adjoint<<<grid, ABNT, wsm, a->st>>>(A, P, dt);
+  k_bs_reverse<<<group_grid(n), ABNT, 0, a->st>>>(group_args(a, r, buf), P, dt);
+  // the record buffer is free for the record pass two steps back
+  cudaEventRecord(a->ev_free[buf], a->st);
   // opening C(h/2), then the opening B(h/2) at the step's start positions
   // (for the first step; the others' went with the step before)
   cdrift_vjp(a, a->alive0, r.st0, r.xs6, hh);
@@ -1106,14 +1227,17 @@ int nb_adjoint_init(nb_adjoint** out, const nb_params* p, int n, const double* x
   nb_system* s = nullptr;
   const int rc0 = nb_init_system(&s, p, n, x, v, m, R, rc, nullptr, workspace,
                                  nb_workspace_bytes(p, n), stream, inputs_on_device);
-  if (rc0 != NB_OK ||
-      cudaStreamCreateWithFlags(&a->st2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&a->ev_rep, cudaEventDisableTiming) != cudaSuccess) {
-    if (s) nb_destroy(s);
-    if (a->st2) cudaStreamDestroy(a->st2);
-    free(a->recs[0]);
-    free(a->recs[1]);
-    free(a);
+  bool ok = rc0 == NB_OK &&
+            cudaStreamCreateWithFlags(&a->st2, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&a->st3, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a->ev_rep, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a->ev_seg, cudaEventDisableTiming) == cudaSuccess;
+  for (int q = 0; q < 2 && ok; ++q)
+    ok = cudaEventCreateWithFlags(&a->ev_rec[q], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&a->ev_free[q], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    a->sys = s;
+    nb_adjoint_destroy(a);
     return rc0 != NB_OK ? rc0 : NB_E_CUDA;
   }
   a->sys = s;
@@ -1216,10 +1340,24 @@ int nb_adjoint_backward(nb_adjoint* a, const double* gx, const double* gv, const
       if (rc) return rc;
     }
     {
+      // the reverse of the segment's steps, last first; the record pass of
+      // step t - 1 (its own stream, its own buffer) runs beside the reverse
+      // of step t, and waits for the reverse that last read its buffer
       NvtxRange r("adjoint: reverse segment");
-      for (int t = len - 1; t >= 0; --t)
+      NB_ACU(cudaEventRecord(a->ev_seg, a->st));
+      NB_ACU(cudaStreamWaitEvent(a->st3, a->ev_seg, 0));
+      record_step(a, a->dt, a->recs[cur][len - 1], (len - 1) & 1, a->st3);
+      NB_ACU(cudaEventRecord(a->ev_rec[(len - 1) & 1], a->st3));
+      for (int t = len - 1; t >= 0; --t) {
+        NB_ACU(cudaStreamWaitEvent(a->st, a->ev_rec[t & 1], 0));
+        if (t > 0) {
+          if (t + 1 <= len - 1) NB_ACU(cudaStreamWaitEvent(a->st3, a->ev_free[(t - 1) & 1], 0));
+          record_step(a, a->dt, a->recs[cur][t - 1], (t - 1) & 1, a->st3);
+          NB_ACU(cudaEventRecord(a->ev_rec[(t - 1) & 1], a->st3));
+        }
         backward_step(a, a->dt, a->recs[cur][t], start + t == total - 1 ? 0.5 * a->dt : a->dt,
-                      start + t == 0);
+                      start + t == 0, t & 1);
+      }
     }
     NB_ACU(cudaEventRecord(a->ev_rep, a->st2));
     NB_ACU(cudaStreamWaitEvent(a->st, a->ev_rep, 0));
@@ -1258,9 +1396,15 @@ const char* nb_adjoint_last_error(const nb_adjoint* a) { return a ? a->err : "no
 
 void nb_adjoint_destroy(nb_adjoint* a) {
   if (!a) return;
-  nb_destroy(a->sys);
+  if (a->sys) nb_destroy(a->sys);
   if (a->st2) cudaStreamDestroy(a->st2);
+  if (a->st3) cudaStreamDestroy(a->st3);
   if (a->ev_rep) cudaEventDestroy(a->ev_rep);
+  if (a->ev_seg) cudaEventDestroy(a->ev_seg);
+  for (int q = 0; q < 2; ++q) {
+    if (a->ev_rec[q]) cudaEventDestroy(a->ev_rec[q]);
+    if (a->ev_free[q]) cudaEventDestroy(a->ev_free[q]);
+  }
   free(a->recs[0]);
   free(a->recs[1]);
   free(a);
