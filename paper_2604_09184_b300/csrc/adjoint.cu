@@ -905,6 +905,8 @@ struct nb_adjoint {
   int work_stride;
   cudaStream_t st3;  // the record passes' stream
   cudaEvent_t ev_rec[2], ev_free[2], ev_seg;
+  cudaStream_t st4;  // the Kepler transpose, beside the direct solver's reverse
+  cudaEvent_t ev_kf, ev_kj;
   double* vpart;  // kick VJP partial sums, vjp_S x 4 x n
   int vjp_S;
   char err[256];
@@ -1183,12 +1185,18 @@ void backward_step(nb_adjoint* a, double dt, const StepRec& r, double close_w, b
   // B(h/2)), then the closing C(h/2)
   kick_vjp(a, r.x26, r.st1, r.st1 + n, a->alive1, close_w);
   cdrift_vjp(a, a->alive1, r.st1, r.x26, hh);
-  // A(h): Kepler outside the groups, Bulirsch-Stoer inside
+  // A(h): Kepler outside the groups, Bulirsch-Stoer inside; the two touch
+  // disjoint bodies' lambda, so the Kepler transpose runs on its own stream
+  // beside the direct solver's reverse
   const Phys& P = a->sys->P;
   const int gk = (((n + kKvBodies - 1) / kKvBodies) * 32 + ANT - 1) / ANT;
-  k_kepler_vjp<<<gk, ANT, 0, a->st>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
-                                      a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
+  cudaEventRecord(a->ev_kf, a->st);
+  cudaStreamWaitEvent(a->st4, a->ev_kf, 0);
+  k_kepler_vjp<<<gk, ANT, 0, a->st4>>>(n, r.xs6, a->alive0, r.ingrp, P.mu, dt, P.kepler_max_iter,
+                                       a->lx, a->ly, a->lz, a->lvx, a->lvy, a->lvz, a->status);
+  cudaEventRecord(a->ev_kj, a->st4);
   k_bs_reverse<<<group_grid(n), ABNT, 0, a->st>>>(group_args(a, r, buf), P, dt);
+  cudaStreamWaitEvent(a->st, a->ev_kj, 0);
   // the record buffer is free for the record pass two steps back
   cudaEventRecord(a->ev_free[buf], a->st);
   // opening C(h/2), then the opening B(h/2) at the step's start positions
@@ -1230,6 +1238,9 @@ int nb_adjoint_init(nb_adjoint** out, const nb_params* p, int n, const double* x
   bool ok = rc0 == NB_OK &&
             cudaStreamCreateWithFlags(&a->st2, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&a->st3, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&a->st4, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a->ev_kf, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a->ev_kj, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&a->ev_rep, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&a->ev_seg, cudaEventDisableTiming) == cudaSuccess;
   for (int q = 0; q < 2 && ok; ++q)
@@ -1399,6 +1410,9 @@ void nb_adjoint_destroy(nb_adjoint* a) {
   if (a->sys) nb_destroy(a->sys);
   if (a->st2) cudaStreamDestroy(a->st2);
   if (a->st3) cudaStreamDestroy(a->st3);
+  if (a->st4) cudaStreamDestroy(a->st4);
+  if (a->ev_kf) cudaEventDestroy(a->ev_kf);
+  if (a->ev_kj) cudaEventDestroy(a->ev_kj);
   if (a->ev_rep) cudaEventDestroy(a->ev_rep);
   if (a->ev_seg) cudaEventDestroy(a->ev_seg);
   for (int q = 0; q < 2; ++q) {
