@@ -469,7 +469,9 @@ int nb_step(nb_system* s, int nsteps, double dt) {
   // close; and eject 1, r_crit 1, the force anew 3, gas 2 + 2
   const long long per_step = 8 + bs_launches(d, s->P) + (split ? 1 : 0) + (eject ? 1 : 0) +
                              (refresh ? 1 : 0) + ((refresh || eject) ? 3 : 0) + (gas ? 4 : 0) +
-                             (s->shard_world > 1 ? 4 : 0);
+                             (s->shard_world > 1 ? 4 : 0) +
+                             // the double-single kick's grid, before each kick
+                             (s->P.precision == NB_PREC_DS ? 1 + ((refresh || eject) ? 1 : 0) : 0);
   s->launches += (split ? 0 : 1) + per_step * nsteps;
   if (s->timing) {
     for (int k = 0; k < nsteps; ++k) {

@@ -210,17 +210,26 @@ __global__ void __launch_bounds__(KNT, 8) k_kick(KickArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Double-single kick (NB_PREC_DS). Only the relative coordinates are formed in
-// FP64 (3 DADD per pair, exact to half an ulp); they are split into float
-// pairs by integer ops, and r^2, r^-3, m r^-3 and the products run as
-// double-single arithmetic (unevaluated float pairs, error-free FMA
-// transforms, Dekker/Knuth style) on the FP32 pipe. Each term is accurate to
-// a few 2^-48; per-tile sums are float pairs folded into FP64 accumulators.
-// The encounter test compares the float r^2 with a float threshold that
-// over-estimates max(rc_i^2, rc_j^2) by 2^-20; any pair that passes it takes
-// the exact FP64 branch of the FP64 kernel, so flags are identical.
+// Double-single kick (NB_PREC_DS). The pair arithmetic runs as double-single
+// (unevaluated float pairs, error-free FMA transforms, Dekker/Knuth style) on
+// the FP32 pipe, with no FP64 instruction per pair: a lone FP64 instruction
+// per pair costs as much pipe time as ~64 FP32 ones on the B300.
+//  - Relative coordinates: every coordinate is split on a common grid G = 2^g
+//    (k_ds_grid: |c| < 2^23 G for every body not parked beyond 2^19 AU) into
+//    a multiple of G and a multiple of G2 = 2^-24 G, each exact as a float,
+//    and the float nearest the rest. The multiples subtract exactly in float,
+//    so dx carries 2^-48 relative plus 2^-47 G absolute error (2^-66 AU for
+//    bodies within 16 AU), in 7 FP32 instructions.
+//  - r^2, r^-3, m r^-3 and the products in double-single; each term accurate
+//    to a few 2^-48; per-tile sums are float pairs folded into FP64
+//    accumulators.
+//  - The encounter test compares the float r^2 with a float threshold that
+//    over-estimates max(rc_i^2, rc_j^2) by 2^-20; any pair that passes takes
+//    the exact FP64 branch of the FP64 kernel (from the FP64 positions), so
+//    flags are identical.
 // All float arithmetic uses the _rn intrinsics so that no operation is
-// contracted or reassociated.
+// contracted or reassociated. The grid depends on all positions only, so a
+// row block's kick equals the whole kick's rows bit for bit.
 // ---------------------------------------------------------------------------
 struct F2 {
   float h, l;
@@ -266,21 +275,91 @@ __device__ __forceinline__ float rc2_threshold(double rc2) {
   return __uint_as_float(__float_as_uint(f) + 16u);
 }
 
-constexpr int DNT2 = 128;  // threads per DS kick CTA (= j-tile size)
-constexpr int DIPT = 1;    // targets per thread (one: 80 registers, 6 CTAs per SM)
+constexpr unsigned kDsParkedExp = 1023 + 19;  // |c| >= 2^19 AU: parked bodies, off the grid
+constexpr unsigned kDsMinExp = 943;            // G2 = 2^-24 G >= 2^-126 (a normal float)
 
-__global__ void __launch_bounds__(DNT2, 6) k_kick_ds(KickArgs A) {
-  __shared__ double sx[DNT2], sy[DNT2], sz[DNT2];
+// The largest biased exponent among a body's coordinates (0 when parked).
+__device__ __forceinline__ unsigned ds_exp_of(double x, double y, double z) {
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  const unsigned ey = ((unsigned)__double2hiint(y) >> 20) & 0x7ffu;
+  const unsigned ez = ((unsigned)__double2hiint(z) >> 20) & 0x7ffu;
+  const unsigned e = max(ex, max(ey, ez));
+  return e >= kDsParkedExp ? 0u : e;
+}
+
+// The grid exponent of a launch: the largest coordinate exponent of all
+// bodies (one CTA; ctrl->ds_exp).
+constexpr int DGT = 1024;
+__global__ void __launch_bounds__(DGT) k_ds_grid(int n, const double* __restrict__ x,
+                                                 const double* __restrict__ y,
+                                                 const double* __restrict__ z, Ctrl* ctrl) {
+  __shared__ unsigned red[DGT / 32];
+  unsigned e = kDsMinExp;
+  for (int j = threadIdx.x; j < n; j += DGT) e = max(e, ds_exp_of(x[j], y[j], z[j]));
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    e = red[threadIdx.x];
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (threadIdx.x == 0) ctrl->ds_exp = (int)e;
+  }
+}
+
+// A coordinate on two nested grids: c = h + m + l with h = k G and m = k2 G2
+// (G2 = 2^-24 G) exact as floats (|k|, |k2| <= 2^23), and l the float
+// nearest to the rest c - k G - k2 G2 (both subtractions exact in FP64,
+// |.| <= G2 / 2): absolute error <= 2^-25 G2 = 2^-49 G.
+struct DsCoord {
+  float h, m, l;
+};
+__device__ __forceinline__ DsCoord ds_coord(double c, double G, double iG, float Gf) {
+  const double k = rint(c * iG);
+  const double r = __fma_rn(-k, G, c);
+  const double k2 = rint(r * (iG * 16777216.0));
+  const double r2 = __fma_rn(-k2, G * 0x1p-24, r);
+  return {__fmul_rn(__double2float_rn(k), Gf), __fmul_rn(__double2float_rn(k2), Gf * 0x1p-24f),
+          __double2float_rn(r2)};
+}
+
+// c_j - c_i as a float pair: the multiples of G and of G2 subtract exactly
+// (integers below 2^24 times a power of two); a nonzero difference of the
+// first (>= G) dominates the second's (<= G), so fast_two_sum joins them
+// exactly, and the rests' difference enters the low part: error below
+// 2^-48 |dx| + 2^-47 G (2^-66 AU for bodies within 16 AU).
+__device__ __forceinline__ F2 ds_diff(const DsCoord& j, const DsCoord& i) {
+  const F2 s = fast_two_sum(__fsub_rn(j.h, i.h), __fsub_rn(j.m, i.m));
+  return F2{s.h, __fadd_rn(s.l, __fsub_rn(j.l, i.l))};
+}
+
+constexpr int DNT2 = 128;  // threads per DS kick CTA (= j-tile size)
+constexpr int DIPT = 1;    // targets per thread
+#ifndef NB_DS_MINB
+#define NB_DS_MINB 5
+#endif
+constexpr int kDsMinBlocks = NB_DS_MINB;  // CTAs per SM the registers are bounded for (tuning)
+
+__global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
+  __shared__ float sxh[DNT2], sxm[DNT2], sxl[DNT2], syh[DNT2], sym[DNT2], syl[DNT2];
+  __shared__ float szh[DNT2], szm[DNT2], szl[DNT2];
   __shared__ float smh[DNT2], sml[DNT2], sthr[DNT2];
-  __shared__ int s_stop;
-  if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
+  __shared__ int s_stop, s_exp;
+  if (threadIdx.x == 0) {
+    s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
+    s_exp = A.ctrl->ds_exp;
+  }
   __syncthreads();
   if (s_stop) return;
+  const unsigned ge = (unsigned)s_exp - 22u;  // biased exponent of G
+  const double G = __longlong_as_double((long long)ge << 52);
+  const double iG = __longlong_as_double((long long)(2046u - ge) << 52);
+  const float Gf = __uint_as_float((ge - 896u) << 23);
   const int n = A.n;
   const int it = blockIdx.x / A.S;
   const int sidx = blockIdx.x - it * A.S;
   const int i0 = A.ib + it * (DNT2 * DIPT) + threadIdx.x;
-  double xi[DIPT], yi[DIPT], zi[DIPT], rc2i[DIPT], rci[DIPT];
+  DsCoord cx[DIPT], cy[DIPT], cz[DIPT];
+  double rc2i[DIPT], rci[DIPT];
   double ax[DIPT], ay[DIPT], az[DIPT];
   float thi[DIPT];
   int ii[DIPT];
@@ -288,13 +367,16 @@ __global__ void __launch_bounds__(DNT2, 6) k_kick_ds(KickArgs A) {
   for (int k = 0; k < DIPT; ++k) {
     const int i = i0 + k * DNT2;
     ii[k] = i;
+    double xi = 1e10, yi = 1e10, zi = 1e10;
     if (i < A.ie) {
-      xi[k] = A.x[i]; yi[k] = A.y[i]; zi[k] = A.z[i];
+      xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
       rc2i[k] = A.rc2[i]; rci[k] = A.rc[i];
     } else {
-      xi[k] = yi[k] = zi[k] = 1e10;
       rc2i[k] = 0.0; rci[k] = 0.0;
     }
+    cx[k] = ds_coord(xi, G, iG, Gf);
+    cy[k] = ds_coord(yi, G, iG, Gf);
+    cz[k] = ds_coord(zi, G, iG, Gf);
     thi[k] = rc2_threshold(rc2i[k]);
     ax[k] = ay[k] = az[k] = 0.0;
   }
@@ -304,9 +386,11 @@ __global__ void __launch_bounds__(DNT2, 6) k_kick_ds(KickArgs A) {
     __syncthreads();
     const int j = jt + threadIdx.x;
     if (j < j1) {
-      sx[threadIdx.x] = A.x[j];
-      sy[threadIdx.x] = A.y[j];
-      sz[threadIdx.x] = A.z[j];
+      const DsCoord qx = ds_coord(A.x[j], G, iG, Gf), qy = ds_coord(A.y[j], G, iG, Gf),
+                    qz = ds_coord(A.z[j], G, iG, Gf);
+      sxh[threadIdx.x] = qx.h; sxm[threadIdx.x] = qx.m; sxl[threadIdx.x] = qx.l;
+      syh[threadIdx.x] = qy.h; sym[threadIdx.x] = qy.m; syl[threadIdx.x] = qy.l;
+      szh[threadIdx.x] = qz.h; szm[threadIdx.x] = qz.m; szl[threadIdx.x] = qz.l;
       const F2 mm = split_d(A.m[j]);
       smh[threadIdx.x] = mm.h;
       sml[threadIdx.x] = mm.l;
@@ -319,13 +403,13 @@ __global__ void __launch_bounds__(DNT2, 6) k_kick_ds(KickArgs A) {
     for (int k = 0; k < DIPT; ++k) tx[k] = ty[k] = tz[k] = F2{0.0f, 0.0f};
 #pragma unroll 2
     for (int q = 0; q < cnt; ++q) {
-      const double xj = sx[q], yj = sy[q], zj = sz[q];
+      const DsCoord qx{sxh[q], sxm[q], sxl[q]}, qy{syh[q], sym[q], syl[q]},
+          qz{szh[q], szm[q], szl[q]};
       const F2 mj{smh[q], sml[q]};
       const float thj = sthr[q];
 #pragma unroll
       for (int k = 0; k < DIPT; ++k) {
-        const double dx = xj - xi[k], dy = yj - yi[k], dz = zj - zi[k];
-        const F2 fx = split_d(dx), fy = split_d(dy), fz = split_d(dz);
+        F2 fx = ds_diff(qx, cx[k]), fy = ds_diff(qy, cy[k]), fz = ds_diff(qz, cz[k]);
         // r^2 as a float pair (the 2^-48-relative squares of the low parts dropped)
         F2 px = two_prod(fx.h, fx.h), py = two_prod(fy.h, fy.h), pz = two_prod(fz.h, fz.h);
         px.l = __fmaf_rn(__fmul_rn(2.0f, fx.h), fx.l, px.l);
@@ -353,19 +437,26 @@ __global__ void __launch_bounds__(DNT2, 6) k_kick_ds(KickArgs A) {
         const F2 y12 = ds_mul(y1, y1);
         F2 sc = ds_mul(mj, ds_mul(y12, y1));
         if (r2.h <= fmaxf(thi[k], thj)) {
-          // possible encounter (or coincident bodies): exact FP64 branch
-          const double r2d = sep2(dx, dy, dz);
-          const double s64 = rare_pair<true>(r2d, scale_fast<NB_PREC_FP64>(r2d, A.m[jt + q]),
-                                             A.m[jt + q], ii[k], jt + q, rc2i[k], rci[k], A);
+          // possible encounter (or coincident bodies): the exact FP64 branch,
+          // from the FP64 positions
+          const int i = ii[k] < A.ie ? ii[k] : A.ie - 1, jj = jt + q;
+          const double dx = __ldg(A.x + jj) - __ldg(A.x + i), dy = __ldg(A.y + jj) - __ldg(A.y + i),
+                       dz = __ldg(A.z + jj) - __ldg(A.z + i);
+          const double r2d = ii[k] < A.ie ? sep2(dx, dy, dz) : 1e20;
+          const double s64 = rare_pair<true>(r2d, scale_fast<NB_PREC_FP64>(r2d, A.m[jj]),
+                                             A.m[jj], ii[k], jj, rc2i[k], rci[k], A);
           sc = split_d(s64);
+          fx = split_d(dx);
+          fy = split_d(dy);
+          fz = split_d(dz);
         }
-        const F2 cx = ds_mul(sc, fx), cy = ds_mul(sc, fy), cz = ds_mul(sc, fz);
-        F2 w = two_sum(tx[k].h, cx.h);
-        tx[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tx[k].l, cx.l))};
-        w = two_sum(ty[k].h, cy.h);
-        ty[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(ty[k].l, cy.l))};
-        w = two_sum(tz[k].h, cz.h);
-        tz[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tz[k].l, cz.l))};
+        const F2 gx = ds_mul(sc, fx), gy = ds_mul(sc, fy), gz = ds_mul(sc, fz);
+        F2 w = two_sum(tx[k].h, gx.h);
+        tx[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tx[k].l, gx.l))};
+        w = two_sum(ty[k].h, gy.h);
+        ty[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(ty[k].l, gy.l))};
+        w = two_sum(tz[k].h, gz.h);
+        tz[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tz[k].l, gz.l))};
       }
     }
 #pragma unroll
@@ -399,8 +490,10 @@ static void launch_kick_args(const KickArgs& A, int precision, cudaStream_t st) 
   if (grid <= 0) return;
   if (precision == NB_PREC_MIXED)
     k_kick<NB_PREC_MIXED><<<grid, KNT, 0, st>>>(A);
-  else if (precision == NB_PREC_DS)
+  else if (precision == NB_PREC_DS) {
+    k_ds_grid<<<1, DGT, 0, st>>>(A.n, A.x, A.y, A.z, A.ctrl);
     k_kick_ds<<<grid, DNT2, 0, st>>>(A);
+  }
   else
     k_kick<NB_PREC_FP64><<<grid, KNT, 0, st>>>(A);
 }

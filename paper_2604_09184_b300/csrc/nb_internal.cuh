@@ -63,7 +63,7 @@ struct Ctrl {
   unsigned long long stats[kStatN];
   double m_ejected;  // mass removed beyond eject_r
   int n_eject_step;  // bodies removed at the start of the current step
-  int pad3;
+  int ds_exp;        // the double-single kick's grid: the largest coordinate exponent
 };
 
 // Device arrays carved from the caller's workspace (SoA, FP64).
