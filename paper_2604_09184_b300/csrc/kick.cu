@@ -340,9 +340,9 @@ constexpr int DIPT = 1;    // targets per thread
 constexpr int kDsMinBlocks = NB_DS_MINB;  // CTAs per SM the registers are bounded for (tuning)
 
 __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
-  __shared__ float sxh[DNT2], sxm[DNT2], sxl[DNT2], syh[DNT2], sym[DNT2], syl[DNT2];
-  __shared__ float szh[DNT2], szm[DNT2], szl[DNT2];
-  __shared__ float smh[DNT2], sml[DNT2], sthr[DNT2];
+  // a source's 12 floats as three float4 (three shared loads per pair, broadcast):
+  // (x.h, x.m, x.l, y.h), (y.m, y.l, z.h, z.m), (z.l, m.h, m.l, threshold)
+  __shared__ float4 sA[DNT2], sB[DNT2], sC[DNT2];
   __shared__ int s_stop, s_exp;
   if (threadIdx.x == 0) {
     s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
@@ -388,13 +388,10 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
     if (j < j1) {
       const DsCoord qx = ds_coord(A.x[j], G, iG, Gf), qy = ds_coord(A.y[j], G, iG, Gf),
                     qz = ds_coord(A.z[j], G, iG, Gf);
-      sxh[threadIdx.x] = qx.h; sxm[threadIdx.x] = qx.m; sxl[threadIdx.x] = qx.l;
-      syh[threadIdx.x] = qy.h; sym[threadIdx.x] = qy.m; syl[threadIdx.x] = qy.l;
-      szh[threadIdx.x] = qz.h; szm[threadIdx.x] = qz.m; szl[threadIdx.x] = qz.l;
       const F2 mm = split_d(A.m[j]);
-      smh[threadIdx.x] = mm.h;
-      sml[threadIdx.x] = mm.l;
-      sthr[threadIdx.x] = rc2_threshold(A.rc2[j]);
+      sA[threadIdx.x] = make_float4(qx.h, qx.m, qx.l, qy.h);
+      sB[threadIdx.x] = make_float4(qy.m, qy.l, qz.h, qz.m);
+      sC[threadIdx.x] = make_float4(qz.l, mm.h, mm.l, rc2_threshold(A.rc2[j]));
     }
     __syncthreads();
     const int cnt = min(DNT2, j1 - jt);
@@ -403,10 +400,10 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
     for (int k = 0; k < DIPT; ++k) tx[k] = ty[k] = tz[k] = F2{0.0f, 0.0f};
 #pragma unroll 2
     for (int q = 0; q < cnt; ++q) {
-      const DsCoord qx{sxh[q], sxm[q], sxl[q]}, qy{syh[q], sym[q], syl[q]},
-          qz{szh[q], szm[q], szl[q]};
-      const F2 mj{smh[q], sml[q]};
-      const float thj = sthr[q];
+      const float4 va = sA[q], vb = sB[q], vc = sC[q];
+      const DsCoord qx{va.x, va.y, va.z}, qy{va.w, vb.x, vb.y}, qz{vb.z, vb.w, vc.x};
+      const F2 mj{vc.y, vc.z};
+      const float thj = vc.w;
 #pragma unroll
       for (int k = 0; k < DIPT; ++k) {
         F2 fx = ds_diff(qx, cx[k]), fy = ds_diff(qy, cy[k]), fz = ds_diff(qz, cz[k]);
