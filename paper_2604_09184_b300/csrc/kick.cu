@@ -256,6 +256,14 @@ __device__ __forceinline__ F2 ds_mul(F2 a, F2 b) {
   return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
 }
 
+// The same without the final renormalisation (the low part up to ~3 ulps of
+// the high one): for a product that only feeds another product or a sum
+// whose two_sum takes the high parts exactly.
+__device__ __forceinline__ F2 ds_mul_u(F2 a, F2 b) {
+  const F2 p = two_prod(a.h, b.h);
+  return F2{p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l))};
+}
+
 // d (FP64) -> h + l: h is d truncated to 24 significant bits, l the next 23
 // bits; |d| < 2^-74 (irrelevant here) maps to 0.
 __device__ __forceinline__ F2 split_d(double d) {
@@ -421,7 +429,7 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
         // y1 = y0 (1 + e/2 + 3 e^2 / 8)
         const float y0 = rsqrtf(r2.h);
         const F2 q2 = two_prod(y0, y0);
-        const F2 s = ds_mul(r2, q2);
+        const F2 s = ds_mul_u(r2, q2);
         const float eh = __fsub_rn(1.0f, s.h);  // exact (Sterbenz)
         // y0 e / 2 = (c.h + c.l - y0 s.l) / 2 with y0 eh = c.h + c.l exactly;
         // the 3 y0 e^2 / 8 term enters the low part as 0.75 y0 eh^2 / 2
@@ -431,8 +439,8 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
         const F2 yy = fast_two_sum(y0, __fmul_rn(0.5f, c.h));
         const F2 y1{yy.h, __fmaf_rn(0.5f, cl, yy.l)};
         // m_j r^-3 = m_j y1^3
-        const F2 y12 = ds_mul(y1, y1);
-        F2 sc = ds_mul(mj, ds_mul(y12, y1));
+        const F2 y12 = ds_mul_u(y1, y1);
+        F2 sc = ds_mul(mj, ds_mul_u(y12, y1));
         if (r2.h <= fmaxf(thi[k], thj)) {
           // possible encounter (or coincident bodies): the exact FP64 branch,
           // from the FP64 positions
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
           fy = split_d(dy);
           fz = split_d(dz);
         }
-        const F2 gx = ds_mul(sc, fx), gy = ds_mul(sc, fy), gz = ds_mul(sc, fz);
+        const F2 gx = ds_mul_u(sc, fx), gy = ds_mul_u(sc, fy), gz = ds_mul_u(sc, fz);
         F2 w = two_sum(tx[k].h, gx.h);
         tx[k] = F2{w.h, __fadd_rn(w.l, __fadd_rn(tx[k].l, gx.l))};
         w = two_sum(ty[k].h, gy.h);
