@@ -340,13 +340,30 @@ def run_ours(args):
     pd = read_traffic(os.path.join(ROOT, "profiles", "kick_ds_mmsn_64k_pipes.txt"))
     if pd.get("n") == str(n):
         roofline["double_single"] = {
-            "kernel": "k_kick_ds", "bound": "alu",
+            "kernel": "k_kick_ds", "bound": "issue",
             "fp32_pipe_frac": float(pd["fma_pipe_pct"]) / 100,
             "fp64_pipe_frac": float(pd["fp64_pipe_pct"]) / 100,
             "issue_active_frac": float(pd["issue_active_pct"]) / 100,
+            "inst_per_pair": float(pd["inst_per_pair"]),
             "source": "ncu sm__pipe_fma_cycles_active (the FP32 FMA pipes), "
-                      "sm__pipe_fp64_cycles_active, sm__issue_active, one launch, profiles/"
-                      "kick_ds_mmsn_64k_pipes.txt"}
+                      "sm__pipe_fp64_cycles_active, sm__issue_active, smsp__inst_executed.sum, "
+                      "one launch, profiles/kick_ds_mmsn_64k_pipes.txt"}
+    if args.precision != "fp64":
+        # the line's kick is the reduced-precision one: the FP64 kernel's pipe
+        # shares and traffic do not describe it
+        for k in ("fp64_pipe_frac", "alu_pipe_frac", "issue_active_frac", "fp64_instr_per_pair",
+                  "pipes_source", "traffic_source", "fp64_pipe_frac_by_count",
+                  "fp64_instr_per_pair_design"):
+            roofline.pop(k, None)
+        roofline["traffic"] = None
+        roofline["kernel"] = "k_kick_ds" if args.precision == "ds" else "k_kick<MIXED>"
+        roofline["note"] = ("achieved counts 20 flop per pair (the direct-summation convention) "
+                            "against the FP64 DFMA peak, for comparison with the FP64 line")
+        if args.precision == "ds" and "double_single" in roofline:
+            ds = roofline.pop("double_single")
+            roofline.update({k: ds[k] for k in ("fp32_pipe_frac", "fp64_pipe_frac",
+                                                "issue_active_frac", "inst_per_pair")})
+            roofline["pipes_source"] = ds["source"]
 
     # reduced-precision kicks on the same workload: the literal mixed mode
     # (float seed + one FP64 Newton step) and double-single on the FP32 pipe

@@ -293,9 +293,10 @@ int nb_batch_step(nb_batch* b, int nsteps, double dt);
  * tile (32, 64 or 128) and the number of buckets (1..16), independent chains
  * of launches on their own streams, each holding every k-th system of the
  * largest-first order (one bucket's latency-bound direct solver then overlaps
- * the others' kicks). nb_batch_autotune() times threads, then tile rows x
- * buckets {1, 4, 8, 16}, then chunks of 10, 25 and 50 steps, on graph replays
- * of a copy of the state (restored afterwards), and keeps the fastest;
+ * the others' kicks). nb_batch_autotune() times threads {64, 128, 256} x
+ * buckets {4, 8, 16} at 32-row tiles and 25-step graphs, then tile rows 64
+ * and 128, then chunks of 10 and 50 steps, on graph replays of a copy of the
+ * state (restored afterwards), and keeps the fastest;
  * nb_batch_get_shape() reports what is in use. None of these changes a
  * result: every system's arithmetic is the same in any shape. */
 int nb_batch_set_shape(nb_batch* b, int threads, int chunk);

@@ -367,7 +367,6 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
 // (one warp per CTA; a system of n bodies wastes at most 31 rows), 64 or 128
 // (fewer stagings of the sources per system), chosen by the autotuner.
 // ---------------------------------------------------------------------------
-constexpr int kTileRows[3] = {32, 64, 128};
 constexpr int kMinTileRows = 32;
 
 #ifndef NB_KICK_SC
@@ -1550,8 +1549,10 @@ int time_graph(nb_batch* b, int steps, double dt, cudaEvent_t e0, cudaEvent_t e1
 int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step) {
   if (!b || !std::isfinite(dt)) return NB_E_INVALID;
   // Each trial runs on a copy of the state (restored after it), timed on
-  // graph replays: (1) threads of the per-system launches; (2) the schedule,
-  // kick tile rows x independent buckets of systems; (3) steps per graph.
+  // graph replays of 25 steps (short graphs favour few buckets: every graph
+  // ends on its slowest bucket): (1) threads of the per-system launches x
+  // independent buckets of systems, at 32-row kick tiles; (2) tile rows 64
+  // and 128; (3) 10 and 50 steps per graph.
   const int keep_t = b->threads, keep_c = b->chunk, keep_r = b->tile_rows, keep_k = b->buckets;
   int rc = batch_snapshot(b, 0);
   if (rc) return rc;
@@ -1559,25 +1560,28 @@ int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step)
   NB_BCU(cudaEventCreate(&e0));
   NB_BCU(cudaEventCreate(&e1));
   double best = 1e30, ms = 0.0;
-  int bt_ = keep_t, br = keep_r, bk = keep_k, bc = keep_c;
-  b->chunk = 10;
+  int bt_ = keep_t, br = 32, bk = keep_k, bc = 25;
+  b->chunk = 25;
+  b->tile_rows = 32;
   for (int t : {64, 128, 256}) {
-    b->threads = t;
-    if ((rc = time_graph(b, 10, dt, e0, e1, &ms))) break;
-    if (ms < best) { best = ms; bt_ = t; }
-  }
-  b->threads = bt_;
-  for (int r = 0; r < 3 && !rc; ++r) {
-    for (int k : {1, 4, 8, 16}) {
-      b->tile_rows = kTileRows[r];
+    for (int k : {4, 8, 16}) {
+      if (rc) break;
+      b->threads = t;
       b->buckets = k;
-      if ((rc = time_graph(b, 10, dt, e0, e1, &ms))) break;
-      if (ms < best) { best = ms; br = kTileRows[r]; bk = k; }
+      if ((rc = time_graph(b, 25, dt, e0, e1, &ms))) break;
+      if (ms < best) { best = ms; bt_ = t; bk = k; }
     }
   }
-  b->tile_rows = br;
+  b->threads = bt_;
   b->buckets = bk;
-  for (int c : {10, 25, 50}) {
+  for (int r : {64, 128}) {
+    if (rc) break;
+    b->tile_rows = r;
+    if ((rc = time_graph(b, 25, dt, e0, e1, &ms))) break;
+    if (ms < best) { best = ms; br = r; }
+  }
+  b->tile_rows = br;
+  for (int c : {10, 50}) {
     if (rc) break;
     b->chunk = c;
     if ((rc = time_graph(b, c, dt, e0, e1, &ms))) break;

@@ -143,6 +143,40 @@ def test_kick_ds_small_and_ragged(n):
     assert pairset(pairs.cpu().numpy()) == pairset(pr)
 
 
+@pytest.mark.parametrize("far", [False, True])
+def test_kick_ds_with_parked_bodies_and_a_distant_body(far):
+    """The double-single kick's coordinate grid is set by the largest live
+    coordinate (bodies parked beyond 2^19 AU, as absorbed bodies are, stay
+    off it). With parked massless bodies among the disk, and optionally a
+    live body at 3000 AU that makes the grid 2^9 times coarser, the live
+    bodies' accelerations stay within the double-single bound of the FP64
+    kick's and the oracle's, every value is finite and the flags are
+    identical."""
+    nb = nbmod()
+    d = ics.workload("mmsn_16k_js", n=3000)
+    x, m = d.x.copy(), d.m.copy()
+    rc = oracle_rc(d, scale=3.0)
+    parked = np.arange(5, d.n, 97)
+    x[parked] = np.outer(1e6 * (parked + 1.0), [1.0, 0.0, 0.0])
+    m[parked] = 0.0
+    rc[parked] = 0.0
+    if far:
+        x[7] = [3000.0, -20.0, 1.0]
+    live = np.ones(d.n, bool)
+    live[parked] = False
+    a64, p64, c1 = nb.kick(cuda(x), cuda(m), cuda(rc), G, nb.NB_PREC_FP64)
+    ads, pds, c2 = nb.kick(cuda(x), cuda(m), cuda(rc), G, nb.NB_PREC_DS)
+    assert c1 == 0 and c2 == 0
+    a64, ads = a64.cpu().numpy(), ads.cpu().numpy()
+    assert np.all(np.isfinite(ads))
+    rel = np.linalg.norm(ads - a64, axis=1)[live] / np.linalg.norm(a64, axis=1)[live]
+    assert rel.max() < 1e-10 and np.median(rel) < 1e-12
+    assert pairset(pds.cpu().numpy()) == pairset(p64.cpu().numpy())
+    ar, pr = nbref.forces(x, m, rc, G)
+    rel_o = np.linalg.norm(ads - ar, axis=1)[live] / np.linalg.norm(ar, axis=1)[live]
+    assert rel_o.max() < 1e-10
+
+
 @pytest.mark.parametrize("prec_name", ["NB_PREC_FP64", "NB_PREC_DS"])
 def test_kick_row_blocks_reproduce_full_kick(prec_name):
     """Row sharding emulated on one GPU: the kick of row blocks that partition
