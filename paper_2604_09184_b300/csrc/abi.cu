@@ -232,6 +232,17 @@ int shard_fail(nb_system* s, int rc) {
 
 }  // namespace
 
+namespace nb {
+// Drop the plain step's graphs (their kernels hold the Dev and Phys of the
+// capture by value: recaptured at the next step).
+void drop_step_graphs(nb_system* s) {
+  if (s->gx_mid) cudaGraphExecDestroy(s->gx_mid);
+  if (s->gx_last) cudaGraphExecDestroy(s->gx_last);
+  s->gx_mid = nullptr;
+  s->gx_last = nullptr;
+}
+}  // namespace nb
+
 extern "C" {
 
 void nb_default_params(nb_params* p) {
@@ -387,6 +398,73 @@ int nb_set_fsal(nb_system* s, const double* a, const int* pairs_ij, int npairs, 
   return NB_OK;
 }
 
+// One plain step (no split phases, unsharded, untimed) on stream st, with
+// the closing kick fused with the next opening one unless last: the same
+// launches, in the same order, as the general loop of nb_step.
+static int enqueue_plain_step(nb_system* s, cudaStream_t st, double dt, bool last) {
+  const Dev& d = s->d;
+  launch_drift_h(d, s->P, dt, st);
+  launch_kick(d, s->P, 0, st);
+  launch_encounter(d, s->P, st);
+  NB_CU(cudaEventRecord(s->ev_fork, st));
+  NB_CU(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+  launch_finish_part(d, s->P, 1, s->side);
+  launch_bs(d, s->P, dt, st, s->side);
+  NB_CU(cudaEventRecord(s->ev_join, s->side));
+  NB_CU(cudaStreamWaitEvent(st, s->ev_join, 0));
+  launch_finish_part(d, s->P, 2, st);
+  launch_scatter(d, s->P, st);
+  launch_member_kick(d, s->P, st);
+  launch_close_h(d, s->P, dt, last, st);
+  return NB_OK;
+}
+
+static int capture_plain_step(nb_system* s, double dt, bool last, cudaGraphExec_t* out) {
+  *out = nullptr;
+  if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return NB_E_CUDA;
+  }
+  const int rc = enqueue_plain_step(s, s->cap, dt, last);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+  if (rc != NB_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return NB_E_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return NB_E_CUDA;
+  }
+  return NB_OK;
+}
+
+// The plain step's graphs for dt, captured at the first call with that dt.
+// NB_E_CUDA when capture is unavailable (nb_step then launches directly).
+static int step_graphs(nb_system* s, double dt) {
+  if (s->g_fail) return NB_E_CUDA;
+  if (s->gx_mid && s->gx_last && s->g_dt == dt) return NB_OK;
+  drop_step_graphs(s);
+  if (!s->cap && cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s->cap = nullptr;
+    s->g_fail = 1;
+    return NB_E_CUDA;
+  }
+  if (capture_plain_step(s, dt, false, &s->gx_mid) != NB_OK ||
+      capture_plain_step(s, dt, true, &s->gx_last) != NB_OK) {
+    drop_step_graphs(s);
+    s->g_fail = 1;
+    return NB_E_CUDA;
+  }
+  s->g_dt = dt;
+  return NB_OK;
+}
+
 int nb_step(nb_system* s, int nsteps, double dt) {
   if (!s || nsteps < 0 || !std::isfinite(dt)) return NB_E_INVALID;
   if (nsteps == 0) return NB_OK;
@@ -407,7 +485,14 @@ int nb_step(nb_system* s, int nsteps, double dt) {
   const int gas = s->P.gas;
   const int split = refresh || eject || gas;  // no fusion of closing and opening kicks
   if (!split) launch_open_h(d, dt, s->st);
-  for (int k = 0; k < nsteps; ++k) {
+  // the plain step as CUDA graphs: the same launches without the gaps
+  // between dependent launches (which matter where the step is short)
+  const bool graphs = !split && !s->timing && s->shard_world <= 1 && step_graphs(s, dt) == NB_OK;
+  if (graphs) {
+    for (int k = 0; k + 1 < nsteps; ++k) NB_CU(cudaGraphLaunch(s->gx_mid, s->st));
+    NB_CU(cudaGraphLaunch(s->gx_last, s->st));
+  }
+  for (int k = 0; k < (graphs ? 0 : nsteps); ++k) {
     if (split) {
       // step start: ejection, Eq. rcrit anew, the cached force and flags
       // anew where either changed, then G(h/2) and the opening B(h/2)
@@ -599,6 +684,8 @@ int nb_stats(nb_system* s, nb_stats_t* out) {
 
 void nb_destroy(nb_system* s) {
   if (!s) return;
+  drop_step_graphs(s);
+  if (s->cap) cudaStreamDestroy(s->cap);
   if (s->events) {
     for (cudaEvent_t e : *s->events) cudaEventDestroy(e);
     delete s->events;

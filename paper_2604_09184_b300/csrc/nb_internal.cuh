@@ -670,10 +670,19 @@ struct nb_system {
   nb_allgather_fn shard_fn;
   void* shard_user;
   char* shard_buf;
+  // CUDA graphs of the plain step (no split phases, unsharded, untimed) for
+  // one dt: a middle step (its closing kick fused with the next opening one)
+  // and a last step, captured on a private stream and launched on st
+  cudaStream_t cap;
+  cudaGraphExec_t gx_mid, gx_last;
+  double g_dt;
+  int g_fail;  // capture unavailable: direct launches
 };
 
 namespace nb {
 // The all-gather of a sharded step: 1 = the trial kick's flagged pairs of
 // every rank, 2 = every rank's rows of the force (nothing when unsharded).
 int shard_exchange(nb_system* s, int which);
+// Drop the plain step's CUDA graphs (after a change of the Dev or Phys they captured).
+void drop_step_graphs(nb_system* s);
 }  // namespace nb

@@ -165,6 +165,7 @@ extern "C" size_t nb_shard_buffer_bytes(const nb_system* s, int world) {
 extern "C" int nb_set_shard(nb_system* s, int rank, int world, nb_allgather_fn fn, void* user,
                             void* buf, size_t buf_bytes) {
   if (!s || world < 1 || rank < 0 || rank >= world) return NB_E_INVALID;
+  drop_step_graphs(s);  // the kick's rows change
   if (world == 1) {
     s->shard_rank = 0;
     s->shard_world = 1;
