@@ -284,7 +284,10 @@ __device__ __forceinline__ float rc2_threshold(double rc2) {
 }
 
 constexpr unsigned kDsParkedExp = 1023 + 19;  // |c| >= 2^19 AU: parked bodies, off the grid
-constexpr unsigned kDsMinExp = 943;            // G2 = 2^-24 G >= 2^-126 (a normal float)
+// The finest grid: G >= 2^-64 (G2 >= 2^-88, a normal float), so that a parked
+// body (up to 2^38 AU) still has a finite float multiple of G (k <= 2^102)
+// however small the live coordinates are.
+constexpr unsigned kDsMinExp = 981;
 
 // The largest biased exponent among a body's coordinates (0 when parked).
 __device__ __forceinline__ unsigned ds_exp_of(double x, double y, double z) {
