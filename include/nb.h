@@ -181,7 +181,11 @@ int nb_set_timing(nb_system* s, int enable);
 int nb_timing(nb_system* s, double* kick_ms, long long* kick_launches, long long* launches);
 
 /* Advance nsteps steps of size dt (dt may be negative). Synchronises the
- * stream before returning. The encounter log is cleared at entry. */
+ * stream before returning. The encounter log is cleared at entry. Without
+ * split phases (rcrit_refresh, gas, ejection), row sharding or timing, the
+ * steps replay two CUDA graphs captured at the first call with this dt (the
+ * same kernels; results are identical to direct launches, which are used when
+ * capture is unavailable). */
 int nb_step(nb_system* s, int nsteps, double dt);
 
 /* Total energy E = H_A + H_B + H_C (K cancels, Eqs. Ha-Hc), angular
