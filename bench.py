@@ -384,7 +384,8 @@ def run_ours(args):
 
     batched = None
     if not args.no_batch:
-        batched = run_batched(nb, torch, args, flush, stream, n_systems=args.batch_systems)
+        batched = run_batched(nb, torch, args, flush, stream, n_systems=args.batch_systems,
+                              f64_peak=f64_peak)
 
     # the step with the start-of-step options of the non-Newtonian row on:
     # gas drag at both ends of the step and the ejection scan
@@ -578,7 +579,7 @@ def run_variant(nb, torch, disk, args, precision, ms64, kick64, pps, flush, stre
             "median_rel_err_accel_vs_fp64": rel.median().item(), "flags_identical": same_flags}
 
 
-def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=32):
+def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=32, f64_peak=None):
     """The 4096-system ensemble (N log-uniform in [16, 512]): per step an
     opening, a tiled kick and a closing launch over all systems, replayed from
     a captured graph in the autotuned shape; speedup against integrating the
@@ -660,7 +661,30 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
                              "max_cta_ms": bal["max_cta_ms"],
                              "definition": "sum of CTA busy times / (CTAs x longest), the last "
                                            "close launch"},
-            "groups": st["groups"], "merges": st["merges"]}
+            "groups": st["groups"], "merges": st["merges"],
+            "roofline": batched_roofline(pairs, ms, f64_peak)}
+
+
+def batched_roofline(pairs, ms, f64_peak):
+    """The ensemble step against the FP64 pipe: the kick's 7 FP64 instructions
+    per pair (dx, dy, dz and r^2 on the integer pipe, as in the single-system
+    kick) at the step's rate, over the DFMA peak measured in the same run; and
+    the kick's own FP64 pipe share in one launch (ncu, profiles/)."""
+    out = {"bound": "alu", "kernel": "k_batch_kick<32, 32>",
+           "fp64_instr_per_pair_design": FP64_INSTR_PER_PAIR}
+    if f64_peak:
+        out["fp64_pipe_frac_by_count_step"] = (FP64_INSTR_PER_PAIR * pairs / (ms * 1e-3)
+                                               / (f64_peak / 2))
+        out["peak_source"] = "FP64 DFMA loop measured in this run (nb_measure_peaks)"
+    pb = read_traffic(os.path.join(ROOT, "profiles", "batch_kick_ensemble_4096_pipes.txt"))
+    if pb.get("systems") == "4096":
+        out["kick_fp64_pipe_frac"] = float(pb["fp64_pipe_pct"]) / 100
+        out["kick_fp64_instr_per_lane_pair"] = float(pb["fp64_inst_per_lane_pair"])
+        out["kick_ms_one_launch"] = float(pb["gpu_time_ms"])
+        out["pipes_source"] = ("ncu sm__pipe_fp64_cycles_active and sm__inst_executed_pipe_fp64.sum, "
+                               "one launch of the whole ensemble's kick, profiles/"
+                               "batch_kick_ensemble_4096_pipes.txt")
+    return out
 
 
 def run_options(nb, torch, disk, args, ms_plain, flush, stream, steps=3):
