@@ -412,9 +412,15 @@ static int enqueue_plain_step(nb_system* s, cudaStream_t st, double dt, bool las
   launch_bs(d, s->P, dt, st, s->side);
   NB_CU(cudaEventRecord(s->ev_join, s->side));
   NB_CU(cudaStreamWaitEvent(st, s->ev_join, 0));
-  launch_finish_part(d, s->P, 2, st);
+  // the closing half of the force update (rows outside the groups) beside
+  // the scatter and the members' re-kick (the members' rows)
+  NB_CU(cudaEventRecord(s->ev_fork, st));
+  NB_CU(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+  launch_finish_part(d, s->P, 2, s->side);
+  NB_CU(cudaEventRecord(s->ev_join, s->side));
   launch_scatter(d, s->P, st);
   launch_member_kick(d, s->P, st);
+  NB_CU(cudaStreamWaitEvent(st, s->ev_join, 0));
   launch_close_h(d, s->P, dt, last, st);
   return NB_OK;
 }
@@ -531,9 +537,15 @@ int nb_step(nb_system* s, int nsteps, double dt) {
     }
     {
       NvtxRange r("final force (incremental) and scatter");
-      launch_finish_part(d, s->P, 2, s->st);
+      // the closing half of the force update (rows outside the groups) on
+      // the side stream beside the scatter and the members' re-kick
+      NB_CU(cudaEventRecord(s->ev_fork, s->st));
+      NB_CU(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+      launch_finish_part(d, s->P, 2, s->side);
+      NB_CU(cudaEventRecord(s->ev_join, s->side));
       launch_scatter(d, s->P, s->st);
       launch_member_kick(d, s->P, s->st);
+      NB_CU(cudaStreamWaitEvent(s->st, s->ev_join, 0));
       // sharded: every rank's rows of the force (nothing when not sharded)
       rc = shard_exchange(s, 2);
       if (rc) return shard_fail(s, rc);

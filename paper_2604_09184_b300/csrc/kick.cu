@@ -590,7 +590,11 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
   if (s_stop) return;
   const int n = d.n;
   const int i = blockIdx.x * FNT + threadIdx.x;
-  const bool row = i >= d.row0 && i < d.row1;  // this rank's rows (all unless sharded)
+  const int M = s_M;
+  // this rank's rows (all unless sharded); the closing half leaves the group
+  // members' rows to the member re-kick, which recomputes their force in full
+  // (and runs beside this kernel)
+  const bool row = i >= d.row0 && i < d.row1 && !(PH == 2 && M > 0 && d.member_slot[i] >= 0);
   double ax = 0.0, ay = 0.0, az = 0.0;
   if (row) {
     if (PH == 2) {  // the trial half's result
@@ -604,7 +608,6 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
       }
     }
   }
-  const int M = s_M;
   const bool delta = row && M > 0 && d.member_slot[i] < 0 && d.alive[i];
   double xi = 0.0, yi = 0.0, zi = 0.0, rci = 0.0, rc2i = 0.0;
   if (delta) {
