@@ -131,6 +131,25 @@ def test_sharded_step_equals_nb_step_bit_for_bit(world):
         assert ex.calls == [2 * 20] * world  # two exchanges per step
 
 
+def test_sharded_double_single_step_equals_nb_step_bit_for_bit():
+    """The double-single kick sets its coordinate grid from all positions, so
+    a rank's block of rows is bit-identical to those rows of the whole kick:
+    the sharded double-single step equals the unsharded one bit for bit
+    (2049 bodies with Jupiter, 3 ranks, 10 steps with encounter groups)."""
+    nb, _ = mods()
+    d = ics.workload("adjoint_2k_j")
+    rc = oracle_rc(d)
+    kw = dict(precision=nb.NB_PREC_DS)
+    sr, er, str_ = reference(d, rc, 10, **kw)
+    assert str_["groups"] > 0
+    out, _ = run_sharded(d, rc, 3, 10, **kw)
+    for sg, eg, stg, code, r0, r1 in out:
+        assert code == 0
+        for k in ("ids", "x", "v", "m"):
+            assert np.array_equal(sg[k], sr[k]), k
+        assert np.array_equal(eg, er)
+
+
 def test_sharded_step_with_mergers_and_uneven_blocks():
     """A merging disk (radii inflated 400x) on 3 ranks over 60 steps: mergers
     change masses and positions inside the direct solver, identically on
