@@ -49,7 +49,10 @@ METRIC = "pair interactions/s & steps/s at N=65536 (FP64, % peak); mixed vs FP64
 UNIT = "pair interactions/s"
 WORKLOAD = "mmsn_64k_js"
 FLOP_PER_PAIR = 20        # direct-summation convention (Nyland, Harris & Prins 2007)
-FP64_INSTR_PER_PAIR = 7  # FP64 instructions in the kick's pair loop (FP64 mode)
+FP64_INSTR_PER_PAIR = 7  # FP64 instructions per pair in the row kick's loop (FP64 mode)
+# the unordered-pair kick: 9 FP64 instructions per pair {i, j} (r^-3 = y0^3 p with p
+# on the integer pipe, the two mass scales, six FMAs), 4.5 per ordered pair
+FP64_INSTR_PER_PAIR_SYM = 4.5
 ACC_SHORT, ACC_LONG = 100, 1000  # steps of the accuracy leg (oracle comparison, long run)
 
 
@@ -307,27 +310,33 @@ def run_ours(args):
     st = sysm.stats()
 
     achieved = FLOP_PER_PAIR * pps / (kick_ms * 1e-3)
+    sym = bool(st.get("kick_symmetric", 0))
+    ipp = FP64_INSTR_PER_PAIR_SYM if sym else FP64_INSTR_PER_PAIR
     roofline = {
         "bound": "alu", "achieved": achieved / 1e12, "peak": f64_peak / 1e12, "unit": "TFLOP/s",
         "frac": achieved / f64_peak, "traffic": None,
-        "kernel": "k_kick<FP64>", "kick_ms": kick_ms,
+        "kernel": "k_kick_sym" if sym else "k_kick<FP64>", "kick_ms": kick_ms,
         "flop_per_pair": FLOP_PER_PAIR,
         "peak_source": "FP64 DFMA loop measured in this run (nb_measure_peaks)",
-        "fp64_pipe_frac_by_count": FP64_INSTR_PER_PAIR * pps / (kick_ms * 1e-3) / (f64_peak / 2),
-        "fp64_instr_per_pair_design": FP64_INSTR_PER_PAIR,
+        "fp64_pipe_frac_by_count": ipp * pps / (kick_ms * 1e-3) / (f64_peak / 2),
+        "fp64_instr_per_pair_design": ipp,
         "fp32_peak_tflops": f32_peak / 1e12,
-        "note": "achieved counts 20 flop per pair (the direct-summation convention); the kick "
-                "forms dx, dy, dz and r^2 on the integer pipe (exact fixed-point differences), "
-                "so its FP64 pipe executes ~%d FP64 instructions per pair and the conventional "
-                "rate can exceed the DFMA peak; fp64_pipe_frac is the FP64 pipe's busy share "
-                "measured by ncu on one launch of this kernel at this N" % FP64_INSTR_PER_PAIR,
+        "note": "achieved counts 20 flop per ordered pair (the direct-summation convention); "
+                "the kick forms dx, dy, dz and r^2 on the integer pipe (exact fixed-point "
+                "differences)%s, so its FP64 pipe executes ~%g FP64 instructions per ordered "
+                "pair and the conventional rate can exceed the DFMA peak; fp64_pipe_frac is the "
+                "FP64 pipe's busy share measured by ncu on one launch of this kernel at this N"
+                % (", evaluates each unordered pair once for both bodies and forms r^-3's "
+                   "residual and series on the integer pipe too" if sym else "", ipp),
     }
-    tr = read_traffic(os.path.join(ROOT, "profiles", "kick_fp64_mmsn_64k_dram.txt"))
+    prof = "kick_sym_mmsn_64k" if sym else "kick_fp64_mmsn_64k"
+    tr = read_traffic(os.path.join(ROOT, "profiles", prof + "_dram.txt"))
     if tr.get("n") == str(n):
         roofline["traffic"] = float(tr["bytes_per_launch"])
-        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 1 launch"
+        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 1 "
+                                      "launch, profiles/%s_dram.txt" % prof)
     # pipe shares measured by ncu (one launch of each kick at this N), not asserted
-    pf = read_traffic(os.path.join(ROOT, "profiles", "kick_fp64_mmsn_64k_pipes.txt"))
+    pf = read_traffic(os.path.join(ROOT, "profiles", prof + "_pipes.txt"))
     if pf.get("n") == str(n):
         roofline["fp64_pipe_frac"] = float(pf["fp64_pipe_pct"]) / 100
         roofline["alu_pipe_frac"] = float(pf["alu_pipe_pct"]) / 100
@@ -336,7 +345,7 @@ def run_ours(args):
         roofline["pipes_source"] = ("ncu sm__pipe_fp64_cycles_active, sm__pipe_alu_cycles_active, "
                                     "sm__issue_active (% of peak sustained active) and "
                                     "sm__inst_executed_pipe_fp64.sum, profiles/"
-                                    "kick_fp64_mmsn_64k_pipes.txt")
+                                    "%s_pipes.txt" % prof)
     pd = read_traffic(os.path.join(ROOT, "profiles", "kick_ds_mmsn_64k_pipes.txt"))
     if pd.get("n") == str(n):
         roofline["double_single"] = {

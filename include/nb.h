@@ -117,6 +117,17 @@ typedef struct {
    * to, and takes it on a failure; 0 = attempts one after the other. The
    * results, counters and adjoint records are the same bit for bit. */
   int bs_speculate;
+  /* Unordered-pair kick (FP64 precision, unsharded systems): each pair {i, j}
+   * is evaluated once and its term applied to both bodies (Newton's third
+   * law), 6 FP64 instructions per ordered pair against 7 in the row kick.
+   * 0 (default) = automatic: on for 4096 <= n <= 262144; 1 = on for any
+   * n <= 262144 (nb_init_system returns NB_E_INVALID above); -1 = off (the
+   * row kick). The other precisions always run the row kick. Results agree
+   * with the row kick to rounding (the products and the order of the sums
+   * differ), deterministic for a given n. A sharded system (nb_set_shard,
+   * world > 1) runs the row kick whatever the setting; the shards equal the
+   * one-GPU step with -1 bit for bit. */
+  int kick_symmetric;
 } nb_params;
 
 typedef struct {
@@ -137,6 +148,8 @@ typedef struct {
   double m_ejected;          /* their mass */
   long long ml_substeps;     /* substeps on the intermediate changeover levels */
   long long ml_groups;       /* groups formed on the intermediate levels */
+  int kick_symmetric;        /* 1 when the step's kicks evaluate each pair once (the
+                                unordered-pair kick), 0 for the row kick */
 } nb_stats_t;
 
 typedef struct nb_system nb_system; /* opaque host handle (small, malloc'd by the library) */
@@ -434,6 +447,9 @@ int nb_measure_peaks(double* fp64_flops, double* fp32_flops, void* scratch, void
  *   NB_MATH_RATIO_LE       the solver's acceptance test fl(a / b) <= tol as
  *                          1 or 0, reading in[3i .. 3i+2] = (a, b, tol), b > 0,
  *                          tol >= 0 (in then holds 3n doubles)
+ *   NB_MATH_RINV3          x^(-3/2) as the unordered-pair kick forms r^-3 from
+ *                          x = r^2 (residual and series on the integer pipe,
+ *                          one FP64 product; 2^-126 <= x < 2^128)
  * NB_E_INVALID for an unknown fn, n < 0 or null arrays (n > 0); asynchronous
  * on the stream. */
 enum {
@@ -447,7 +463,8 @@ enum {
   NB_MATH_MASS15 = 7,
   NB_MATH_MASS1875 = 8,
   NB_MATH_NEVILLE = 9,
-  NB_MATH_RATIO_LE = 10
+  NB_MATH_RATIO_LE = 10,
+  NB_MATH_RINV3 = 11
 };
 int nb_math_eval(int fn, int n, const double* in, double* out, void* stream);
 

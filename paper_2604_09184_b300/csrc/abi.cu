@@ -78,7 +78,25 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
   d.alive = c.take<int>(n);
   d.member_slot = c.take<int>(n);
   d.uf = c.take<int>(n > 64 ? n : 64);
-  d.kpart = c.take<double>((size_t)3 * d.S * n);
+  // the unordered-pair kick's partials share the kpart allocation
+  const bool sym = p.precision == NB_PREC_FP64 &&
+                   (p.kick_symmetric == 1 ? n <= kSymMaxN
+                                          : p.kick_symmetric == 0 && n >= kSymMinN && n <= kSymMaxN);
+  size_t kpart_n = (size_t)3 * d.S * n;
+  if (sym) {
+    const SymLayout L = sym_layout(n);
+    d.sym = d.sym_ok = 1;
+    d.sym_nb = L.nb;
+    d.sym_hrow = L.hrow;
+    d.sym_per = L.per;
+    d.sym_grid = L.grid;
+    if (L.doubles > kpart_n) kpart_n = L.doubles;
+  }
+  d.kpart = c.take<double>(kpart_n);
+  if (sym) {
+    d.sym_xpart = d.kpart;
+    d.sym_ypart = d.kpart + (size_t)d.sym_grid * 2 * 3 * kSymBlock;
+  }
   d.ppartA = c.take<double>((size_t)3 * d.ppart_n);
   d.ppartB = c.take<double>((size_t)3 * d.ppart_n);
   d.ftrial = c.take<int2>(d.pair_cap);
@@ -153,6 +171,7 @@ bool params_ok(const nb_params* p) {
   if (p->ml_levels < 0 || p->ml_levels > kMlMax || p->ml_factor < 2 || p->ml_factor > 64)
     return false;
   if (p->bs_speculate != 0 && p->bs_speculate != 1) return false;
+  if (p->kick_symmetric < -1 || p->kick_symmetric > 1) return false;
   return true;
 }
 
@@ -275,6 +294,7 @@ void nb_default_params(nb_params* p) {
   p->ml_levels = 0;
   p->ml_factor = 3;
   p->bs_speculate = 1;
+  p->kick_symmetric = 0;
 }
 
 size_t nb_workspace_bytes(const nb_params* p, int n) {
@@ -303,6 +323,7 @@ int nb_init_system(nb_system** out, const nb_params* p, int n, const double* x, 
   if (!out) return NB_E_INVALID;
   *out = nullptr;
   if (!params_ok(p) || n < 1 || !x || !v || !m || !R) return NB_E_INVALID;
+  if (p->kick_symmetric == 1 && p->precision == NB_PREC_FP64 && n > kSymMaxN) return NB_E_INVALID;
   const size_t need = layout(*p, n, nullptr, nullptr);
   if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return NB_E_WORKSPACE;
   nb_system* s = (nb_system*)calloc(1, sizeof(nb_system));
@@ -691,6 +712,7 @@ int nb_stats(nb_system* s, nb_stats_t* out) {
   out->m_ejected = c.m_ejected;
   out->ml_substeps = (long long)c.stats[ST_ML_SUBSTEPS];
   out->ml_groups = (long long)c.stats[ST_ML_GROUPS];
+  out->kick_symmetric = s->d.sym;
   return NB_OK;
 }
 

@@ -210,6 +210,210 @@ __global__ void __launch_bounds__(KNT, 8) k_kick(KickArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Unordered-pair kick (FP64, whole system). Each pair {i, j} is evaluated
+// once and its term goes to both bodies (Newton's third law): the seeded
+// r^-3 (4 FP64 operations), the scales m_j r^-3 and m_i r^-3 and six FMAs,
+// 12 FP64 instructions per unordered pair (6 per ordered pair against 7 in
+// k_kick), and the integer work (fixed-point differences, r^2, the seed) once
+// per pair instead of twice.
+// Bodies form NB blocks of kSymBlock. The block pairs (X, Y = X + d mod NB),
+// d = 1..NB/2, cover every pair of distinct blocks once (for even NB the
+// pairs at d = NB/2 come from the lower block X < NB/2 only); d = 0 is the
+// block with itself, one-sided, with the flag taken for i < j. The row-major
+// list of NB (NB/2 + 1) tiles is cut into equal ranges, one per CTA; a CTA
+// keeps its row's sums in registers (a range spans at most two rows; one
+// partial per row and CTA) and writes one partial per tile for block Y.
+// In a tile, warp w pairs its 32 bodies of X with the 128 of Y in four
+// 32 x 32 sub-tiles: at step s lane l takes body (l + s) mod 32 of the
+// sub-tile, and the Y-side sums move one lane down after every step
+// (shuffles), so that after 32 steps lane l holds body l's sum; the four
+// warps' sums are added in warp order. k_finish adds a body's partials in a
+// fixed order (its row's in CTA order, then its column's by d), so the
+// results are deterministic. The exact branch (near or inside the changeover
+// radius) is that of k_kick with both scales, (m w) / (r^2 r) each.
+// ---------------------------------------------------------------------------
+struct SymArgs {
+  int nb, hrow, tiles, per;
+  double* xpart;  // grid x 2 x 3 x kSymBlock
+  double* ypart;  // nb x hrow x 3 x kSymBlock
+};
+
+static_assert(KNT == kSymBlock, "one thread per body of a block");
+#ifndef NB_SYM_UNROLL
+#define NB_SYM_UNROLL 4
+#endif
+constexpr int kSymUnroll = NB_SYM_UNROLL;  // unroll of the 32-step rotation loop (tuning)
+
+template <bool DIAG>
+__device__ __forceinline__ void sym_rare(int i, int j, double mi, double mj, const KickArgs& A,
+                                         double& sj, double& si) {
+  const bool ok = i < A.n && j < A.n;
+  double r2 = 1e20, rc2 = 0.0, rc = 0.0;
+  if (ok) {
+    r2 = sep2(__ldg(A.x + j) - __ldg(A.x + i), __ldg(A.y + j) - __ldg(A.y + i),
+              __ldg(A.z + j) - __ldg(A.z + i));
+    rc2 = fmax(__ldg(A.rc2 + i), __ldg(A.rc2 + j));
+    rc = fmax(__ldg(A.rc + i), __ldg(A.rc + j));
+  }
+  // coincident distinct bodies are flagged too
+  const bool flag = ok && (r2 < rc2) && (!DIAG || i < j);
+  if (ok && r2 == 0.0) {
+    sj = 0.0;
+    si = 0.0;
+  } else if (ok && r2 < rc2) {
+    const double r = sqrt(r2);
+    const double w = kick_weight(r, rc);
+    sj = mj * w / (r2 * r);
+    if (!DIAG) si = mi * w / (r2 * r);
+  }
+  emit_pair(flag, min(i, j), max(i, j), A.pairs, A.cap, A.counter, A.ctrl);
+}
+
+__global__ void __launch_bounds__(KNT, kSymCtasPerSm) k_kick_sym(KickArgs A, SymArgs L) {
+  __shared__ nb_u128 sX[KNT], sY[KNT], sZ[KNT];  // block Y: fixed-point positions
+  __shared__ double sm[KNT];
+  __shared__ int sh[KNT];
+  __shared__ double sacc[3][4][KNT];  // the warps' Y-side sums of a tile
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
+  __syncthreads();
+  if (s_stop) return;
+  const int n = A.n;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int H1 = L.hrow + 1;
+  const int f0 = blockIdx.x * L.per;
+  const int f1 = min(L.tiles, f0 + L.per);
+  int X = -1, seg = 0, i = 0, hi = 0;
+  nb_u128 Xi = 0, Yi = 0, Zi = 0;
+  double mi = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+  for (int f = f0; f < f1; ++f) {
+    const int Xf = f / H1, dd = f - Xf * H1;
+    if (Xf != X) {
+      if (X >= 0) {
+        double* p = L.xpart + (size_t)((blockIdx.x * 2 + seg) * 3) * KNT + threadIdx.x;
+        p[0] = ax;
+        p[KNT] = ay;
+        p[2 * KNT] = az;
+        seg = 1;
+      }
+      X = Xf;
+      i = X * KNT + threadIdx.x;
+      if (i < n) {
+        Xi = fix_of(A.x[i]);
+        Yi = fix_of(A.y[i]);
+        Zi = fix_of(A.z[i]);
+        mi = A.m[i];
+        hi = __double2hiint(A.rc2[i]);
+      } else {  // padding far from everything, massless, never flagged
+        Xi = Yi = Zi = fix_of(1e10);
+        mi = 0.0;
+        hi = 0;
+      }
+      ax = ay = az = 0.0;
+    }
+    if (2 * dd == L.nb && X >= L.nb / 2) continue;  // the lower block covers this pair
+    int Yb = X + dd;
+    if (Yb >= L.nb) Yb -= L.nb;
+    const int jb = Yb * KNT;
+    __syncthreads();
+    {
+      const int j = jb + threadIdx.x;
+      if (j < n) {
+        sX[threadIdx.x] = fix_of(A.x[j]);
+        sY[threadIdx.x] = fix_of(A.y[j]);
+        sZ[threadIdx.x] = fix_of(A.z[j]);
+        sm[threadIdx.x] = A.m[j];
+        sh[threadIdx.x] = __double2hiint(A.rc2[j]);
+      } else {
+        sX[threadIdx.x] = sY[threadIdx.x] = sZ[threadIdx.x] = fix_of(1e10);
+        sm[threadIdx.x] = 0.0;
+        sh[threadIdx.x] = 0;
+      }
+    }
+    __syncthreads();
+    if (dd == 0) {
+      // the block with itself: every ordered pair, this body's side only
+#pragma unroll 4
+      for (int q = 0; q < KNT; ++q) {
+        const FixDiff fx = fix_diff(sX[q], Xi), fy = fix_diff(sY[q], Yi), fz = fix_diff(sZ[q], Zi);
+        const double r2 = sep2_fix(fx, fy, fz);
+        const double mj = sm[q];
+        double sj = mj * rinv3_fast(r2), si = 0.0;
+        if (__double2hiint(r2) <= max(hi, sh[q]) + 1) sym_rare<true>(i, jb + q, mi, mj, A, sj, si);
+        ax = __fma_rn(sj, fx.d, ax);
+        ay = __fma_rn(sj, fy.d, ay);
+        az = __fma_rn(sj, fz.d, az);
+      }
+      continue;
+    }
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+      double bx = 0.0, by = 0.0, bz = 0.0;  // Y-side sums, one lane down per step
+#pragma unroll kSymUnroll
+      for (int s = 0; s < 32; ++s) {
+        const int q = 32 * u + ((lane + s) & 31);
+        const FixDiff fx = fix_diff(sX[q], Xi), fy = fix_diff(sY[q], Yi), fz = fix_diff(sZ[q], Zi);
+        const double r2 = sep2_fix(fx, fy, fz);
+        const double mj = sm[q];
+        const double r3 = rinv3_fast(r2);
+        double sj = mj * r3, si = mi * r3;
+        if (__double2hiint(r2) <= max(hi, sh[q]) + 1) sym_rare<false>(i, jb + q, mi, mj, A, sj, si);
+        ax = __fma_rn(sj, fx.d, ax);
+        ay = __fma_rn(sj, fy.d, ay);
+        az = __fma_rn(sj, fz.d, az);
+        bx = __fma_rn(-si, fx.d, bx);
+        by = __fma_rn(-si, fy.d, by);
+        bz = __fma_rn(-si, fz.d, bz);
+        const int src = (lane + 1) & 31;
+        bx = __shfl_sync(0xffffffffu, bx, src);
+        by = __shfl_sync(0xffffffffu, by, src);
+        bz = __shfl_sync(0xffffffffu, bz, src);
+      }
+      sacc[0][wp][32 * u + lane] = bx;
+      sacc[1][wp][32 * u + lane] = by;
+      sacc[2][wp][32 * u + lane] = bz;
+    }
+    __syncthreads();
+    double* p = L.ypart + ((size_t)Yb * L.hrow + (dd - 1)) * 3 * KNT + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      p[c * KNT] = ((sacc[c][0][threadIdx.x] + sacc[c][1][threadIdx.x]) + sacc[c][2][threadIdx.x]) +
+                   sacc[c][3][threadIdx.x];
+  }
+  if (X >= 0) {
+    double* p = L.xpart + (size_t)((blockIdx.x * 2 + seg) * 3) * KNT + threadIdx.x;
+    p[0] = ax;
+    p[KNT] = ay;
+    p[2 * KNT] = az;
+  }
+}
+
+// A body's sum of the unordered-pair kick's partials, in a fixed order: its
+// row's partials in CTA order, then its column's by d.
+__device__ __forceinline__ void sym_partials(const Dev& d, int i, double& ax, double& ay,
+                                             double& az) {
+  const int X = i / kSymBlock, t = i - X * kSymBlock;
+  const int H1 = d.sym_hrow + 1;
+  const int fa = X * H1, fb = fa + H1 - 1;
+  for (int b = fa / d.sym_per; b <= fb / d.sym_per; ++b) {
+    const int seg = (b * d.sym_per) / H1 == X ? 0 : 1;
+    const double* p = d.sym_xpart + (size_t)((b * 2 + seg) * 3) * kSymBlock + t;
+    ax += p[0];
+    ay += p[kSymBlock];
+    az += p[2 * kSymBlock];
+  }
+  const double* p = d.sym_ypart + (size_t)X * d.sym_hrow * 3 * kSymBlock + t;
+#pragma unroll 4
+  for (int dd = 1; dd <= d.sym_hrow; ++dd, p += 3 * kSymBlock) {
+    const int Xs = X - dd < 0 ? X - dd + d.sym_nb : X - dd;
+    if (2 * dd == d.sym_nb && Xs >= d.sym_nb / 2) continue;
+    ax += p[0];
+    ay += p[kSymBlock];
+    az += p[2 * kSymBlock];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Double-single kick (NB_PREC_DS). The pair arithmetic runs as double-single
 // (unevaluated float pairs, error-free FMA transforms, Dekker/Knuth style) on
 // the FP32 pipe, with no FP64 instruction per pair: a lone FP64 instruction
@@ -516,6 +720,17 @@ static int jchunk_for(int n, int S) {
   return c > 0 ? c : KNT;
 }
 
+static void launch_kick_sym(const KickArgs& A, const Dev& d, cudaStream_t st) {
+  SymArgs L;
+  L.nb = d.sym_nb;
+  L.hrow = d.sym_hrow;
+  L.tiles = d.sym_nb * (d.sym_hrow + 1);
+  L.per = d.sym_per;
+  L.xpart = d.sym_xpart;
+  L.ypart = d.sym_ypart;
+  k_kick_sym<<<d.sym_grid, KNT, 0, st>>>(A, L);
+}
+
 void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t st) {
   KickArgs A;
   A.n = d.n;
@@ -530,7 +745,10 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   A.cap = d.pair_cap;
   A.counter = &d.ctrl->n_ftrial;
   A.ctrl = d.ctrl;
-  launch_kick_args(A, P.precision, st);
+  if (d.sym)
+    launch_kick_sym(A, d, st);
+  else
+    launch_kick_args(A, P.precision, st);
 }
 
 void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, const double* z,
@@ -556,10 +774,11 @@ void launch_kick_raw(int n, int ib, int ie, const double* x, const double* y, co
 constexpr int FNT = 256;
 
 // m_j w / r^3 as the kick computes it: the seeded reciprocal root beyond
-// rc_ij (m_j with 1.5 m_j and 1.875 m_j), the exact changeover weight inside,
-// 0 for coincident bodies; the range test compares bit patterns.
+// rc_ij (m_j with 1.5 m_j and 1.875 m_j in the row kick, m_j times the seeded
+// r^-3 in the unordered-pair kick), the exact changeover weight inside, 0 for
+// coincident bodies; the range test compares bit patterns.
 __device__ __forceinline__ double finish_scale(double dx, double dy, double dz, const double* sj,
-                                               int k, double rci, double rc2i) {
+                                               int k, double rci, double rc2i, bool sym) {
   const double mj = sj[3 * FNT + k];
   const double r2 = sep2_int(dx, dy, dz);
   // near or inside rc (one high-word unit of slack for the integer r^2), or
@@ -569,6 +788,7 @@ __device__ __forceinline__ double finish_scale(double dx, double dy, double dz, 
     if (nn_less(r2x, rc2i) || nn_less(r2x, sj[5 * FNT + k]) || __double_as_longlong(r2x) == 0ll)
       return pair_scale(r2x, mj, rci, sj[4 * FNT + k]);
   }
+  if (sym) return mj * rinv3_fast(r2);
   return scale_fast<NB_PREC_FP64>(r2, mj, sj[6 * FNT + k], sj[7 * FNT + k]);
 }
 
@@ -599,6 +819,8 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
   if (row) {
     if (PH == 2) {  // the trial half's result
       ax = d.ax[i]; ay = d.ay[i]; az = d.az[i];
+    } else if (d.sym) {
+      sym_partials(d, i, ax, ay, az);
     } else {
       for (int s = 0; s < d.S; ++s) {
         const double* p = d.kpart + (size_t)(3 * s) * n;
@@ -651,12 +873,12 @@ __global__ void __launch_bounds__(FNT) k_finish_t(Dev d, double G, int with_delt
         // the term at the member's new state
         if (PH != 2) {
           const double dx = so[0][k] - xi, dy = so[1][k] - yi, dz = so[2][k] - zi;
-          const double s = finish_scale(dx, dy, dz, &so[0][0], k, rci, rc2i);
+          const double s = finish_scale(dx, dy, dz, &so[0][0], k, rci, rc2i, d.sym);
           cx -= s * dx; cy -= s * dy; cz -= s * dz;
         }
         if (PH != 1) {
           const double dx = snw[0][k] - xi, dy = snw[1][k] - yi, dz = snw[2][k] - zi;
-          const double s = finish_scale(dx, dy, dz, &snw[0][0], k, rci, rc2i);
+          const double s = finish_scale(dx, dy, dz, &snw[0][0], k, rci, rc2i, d.sym);
           cx += s * dx; cy += s * dy; cz += s * dz;
         }
       }
@@ -704,7 +926,10 @@ void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStr
   A.cap = d.pair_cap;
   A.counter = &d.ctrl->n_ftrial;
   A.ctrl = d.ctrl;
-  launch_kick_args(A, P.precision, st);
+  if (d.sym)
+    launch_kick_sym(A, d, st);
+  else
+    launch_kick_args(A, P.precision, st);
   k_finish_t<0><<<(d.n + FNT - 1) / FNT, FNT, 0, st>>>(d, P.G, 0, cond);
   launch_fsal_init(d, st, cond);
 }

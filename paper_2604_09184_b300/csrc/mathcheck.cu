@@ -42,6 +42,7 @@ __global__ void k_math_eval(int fn, int n, const double* in, double* out) {
       r = ratio_le(in[3 * i], in[3 * i + 1], tol, next_up(tol)) ? 1.0 : 0.0;
       break;
     }
+    case NB_MATH_RINV3: r = rinv3_fast(x); break;
     default: r = 0.0;
   }
   out[i] = r;
@@ -50,7 +51,7 @@ __global__ void k_math_eval(int fn, int n, const double* in, double* out) {
 }  // namespace nb
 
 extern "C" int nb_math_eval(int fn, int n, const double* in, double* out, void* stream) {
-  if (n < 0 || fn < 0 || fn > NB_MATH_RATIO_LE) return NB_E_INVALID;
+  if (n < 0 || fn < 0 || fn > NB_MATH_RINV3) return NB_E_INVALID;
   if (n == 0) return NB_OK;
   if (!in || !out) return NB_E_INVALID;
   nb::k_math_eval<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(fn, n, in, out);

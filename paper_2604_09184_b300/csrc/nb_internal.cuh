@@ -20,6 +20,43 @@ constexpr double kDeadOffset = 1e6;  // absorbed bodies sit at (1e6 (id + 1), 0,
 // positions are exact below 2^38 AU).
 constexpr double kPosMax = 0x1p37;
 
+// Unordered-pair kick: blocks of kSymBlock bodies, the tile list cut into
+// equal ranges, one per CTA, for about NB_SYM_WAVES waves of 8 CTAs per SM on
+// 148 SMs (the block scheduler then evens out the SMs: at N = 65538 one wave
+// of 112-tile ranges took 40.9 ms, 4, 8 and 16 waves 39.2, 38.4 and 38.0 ms),
+// and at least one CTA per block, so that a range spans at most two block
+// rows. The grid is fixed by n alone, so the partial sums (and the results)
+// do not depend on the device. Automatic selection covers
+// kSymMinN <= n <= kSymMaxN (the column partials take 3 x 8 bytes per body
+// per block of the other half: 6.4 GB at kSymMaxN).
+#ifndef NB_SYM_MINB
+#define NB_SYM_MINB 8
+#endif
+#ifndef NB_SYM_WAVES
+#define NB_SYM_WAVES 16
+#endif
+constexpr int kSymBlock = 128;
+constexpr int kSymCtasPerSm = NB_SYM_MINB;  // CTAs per SM the registers are bounded for
+constexpr int kSymWave = 148 * kSymCtasPerSm * NB_SYM_WAVES;
+constexpr int kSymMinN = 4096;  // kick 0.237 against 0.270 ms at 4096, 0.163 against 0.092 at 2050
+constexpr int kSymMaxN = 262144;
+struct SymLayout {
+  int nb, hrow, tiles, per, grid;
+  size_t doubles;  // xpart + ypart
+};
+inline SymLayout sym_layout(int n) {
+  SymLayout L;
+  L.nb = (n + kSymBlock - 1) / kSymBlock;
+  L.hrow = L.nb / 2;
+  L.tiles = L.nb * (L.hrow + 1);
+  int g = ((L.nb + kSymWave - 1) / kSymWave) * kSymWave;
+  if (g > L.tiles) g = L.tiles;
+  L.per = (L.tiles + g - 1) / g;
+  L.grid = (L.tiles + L.per - 1) / L.per;
+  L.doubles = (size_t)L.grid * 2 * 3 * kSymBlock + (size_t)L.nb * L.hrow * 3 * kSymBlock;
+  return L;
+}
+
 // Bulirsch-Stoer scratch per group member (doubles): y[6] | f0[6] | per
 // extrapolation column j = 1..kmax: zm[6] zc[6] f[6] | T[2][kmax][6] | aux[4].
 __host__ __device__ constexpr int bs_off_col(int j) { return 12 + 18 * (j - 1); }
@@ -81,6 +118,15 @@ struct Dev {
   double *xs, *ys, *zs, *vxs, *vys, *vzs;  // saved state after C(h/2)
   int *id, *alive, *member_slot, *uf;
   double* kpart;      // S x 3 x n partial kick sums
+  // Unordered-pair kick (each pair evaluated once, FP64, whole system): sym
+  // selects it for the step's kicks; sym_nb blocks of kSymBlock bodies,
+  // sym_hrow off-diagonal tiles per block row, sym_per tiles per CTA;
+  // sym_xpart holds the CTAs' row sums (grid x 2 x 3 x kSymBlock), sym_ypart
+  // one partial per tile for its column block (sym_nb x sym_hrow x 3 x
+  // kSymBlock). Both live in the kpart allocation.
+  int sym, sym_ok, sym_nb, sym_hrow, sym_per, sym_grid;
+  double* sym_xpart;
+  double* sym_ypart;
   double* ppartA;     // 3 x ppart_n partial momenta (after the opening kick)
   double* ppartB;     // 3 x ppart_n partial momenta (after the drift)
   int2* ftrial;       // pairs of the trial kick
@@ -239,6 +285,7 @@ __device__ __forceinline__ double scale_fast(double r2, double m, double m15, do
   if (PREC == NB_PREC_FP64) return sp.y3 * __fma_rn(__fma_rn(m1875, e, m15), e, m);
   return sp.y3 * __fma_rn(m15, e, m);
 }
+
 // 1.5 m and 1.875 m for m >= 0 (zero or normal) by integer ops on m's bits:
 // 1.5 m = m + m/2 as a significand sum (truncated, relative error < 2^-52)
 // and 1.875 m through the float built from m's high word (relative error
@@ -502,6 +549,50 @@ __host__ __device__ __forceinline__ double sep2_fix(const FixDiff& a, const FixD
   __builtin_memcpy(&r, &bits, 8);
   return r;
 #endif
+}
+
+// r^-3 alone for the unordered-pair kick (which scales it by each body's
+// mass), with one FP64 instruction: r^-3 = y0^3 p, p = (1 - e)^(-3/2) =
+// 1 + 3e/2 + 15e^2/8 + O(e^3), e = 1 - r^2 y0^2, and p formed on the integer
+// pipe. r^2 = R 2^(er - 1075) (R its 53-bit significand) and y0^2 = s^2
+// 2^(2 ey - 300) (s the seed's 24-bit significand), so r^2 y0^2 = R s^2 2^-K
+// with K = 1375 - er - 2 ey: the 101-bit product R s^2 is exact, and
+// D = (2^K - R s^2) 2^(63 - K), rounded toward minus infinity, is e in units
+// of 2^-63 (|D| < 2^45 for |e| < 2^-18). p - 1 = 1.5 e + 1.875 e^2 is then an
+// integer in the same units (e^2 from the square of D / 2^14, error below
+// 2^-60 in all), and p's bits follow by rounding that integer to p's ulp
+// (2^-52 above 1, 2^-53 below). With y3 = y0^3 rounded (seed_powers) and the
+// one rounded product, r^-3 is within ~1.6 ulp (the e^3 term, < 2^-55.7 for
+// |e| < 2e-6, as in scale_fast). Valid for seeds with |e| < 2^-18 and
+// 2^-126 <= r^2 < 2^128 (the seed's range). Host-callable with the seed's
+// bits as an input, so that it can be checked on the CPU.
+__host__ __device__ __forceinline__ double rinv3_from_seed(double r2, unsigned yb) {
+  const unsigned long long B = nb_dbits(r2);
+  const int er = (int)(B >> 52);
+  const unsigned long long R = (B & 0xfffffffffffffull) | 0x10000000000000ull;
+  const unsigned s = (yb & 0x7fffffu) | 0x800000u;
+  const int ey = (int)(yb >> 23);
+  const unsigned long long S2 = (unsigned long long)s * s;  // < 2^48
+  const nb_u128 P = (nb_u128)R * S2;                        // < 2^101
+  const int K = 1375 - er - 2 * ey;                         // r^2 y0^2 = P 2^-K, K in 98..101
+  const long long D = (long long)((__int128)(((nb_u128)1 << K) - P) >> (K - 63));
+  const unsigned long long a = (unsigned long long)(D < 0 ? -D : D) >> 14;
+  const long long q = (long long)((a * a) >> 35);        // e^2 in units of 2^-63
+  const long long dp = D + (D >> 1) + ((q << 1) - (q >> 3));  // p - 1 = 1.5 e + 1.875 e^2
+  const unsigned long long pb =
+      dp >= 0 ? 0x3ff0000000000000ull + (((unsigned long long)dp + 1024ull) >> 11)
+              : 0x3ff0000000000000ull - (((unsigned long long)(-dp) + 512ull) >> 10);
+  double p;
+#ifdef __CUDA_ARCH__
+  p = __longlong_as_double((long long)pb);
+  return __dmul_rn(seed_powers(yb).y3, p);
+#else
+  __builtin_memcpy(&p, &pb, 8);
+  return seed_powers(yb).y3 * p;
+#endif
+}
+__device__ __forceinline__ double rinv3_fast(double r2) {
+  return rinv3_from_seed(r2, rsqrt_seed_bits(r2));
 }
 
 // m_j w / r^3 for one pair with full-precision r (used off the hot loop).

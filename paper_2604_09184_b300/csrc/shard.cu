@@ -175,6 +175,7 @@ extern "C" int nb_set_shard(nb_system* s, int rank, int world, nb_allgather_fn f
     s->shard_buf = nullptr;
     s->d.row0 = 0;
     s->d.row1 = s->d.n;
+    s->d.sym = s->d.sym_ok;  // the unordered-pair kick again where it was chosen
     return NB_OK;
   }
   if (!fn) return NB_E_INVALID;
@@ -195,5 +196,6 @@ extern "C" int nb_set_shard(nb_system* s, int rank, int world, nb_allgather_fn f
   s->shard_buf = (char*)buf;
   s->d.row0 = r0;
   s->d.row1 = r1;
+  s->d.sym = 0;  // row blocks: the row kick
   return NB_OK;
 }

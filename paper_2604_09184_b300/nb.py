@@ -30,6 +30,7 @@ NB_PREC_DS = 2
 NB_MATH_EXP, NB_MATH_RCP, NB_MATH_RSQRT, NB_MATH_RPOW32 = 0, 1, 2, 3
 NB_MATH_RPOW32_MIXED, NB_MATH_RPOW32_M, NB_MATH_CLOSE_WEIGHT = 4, 5, 6
 NB_MATH_MASS15, NB_MATH_MASS1875, NB_MATH_NEVILLE, NB_MATH_RATIO_LE = 7, 8, 9, 10
+NB_MATH_RINV3 = 11
 
 
 class NbParams(C.Structure):
@@ -43,7 +44,7 @@ class NbParams(C.Structure):
         ("gas", C.c_int), ("gas_rho0", C.c_double), ("gas_p", C.c_double),
         ("gas_eta", C.c_double), ("gas_cd", C.c_double), ("gas_iter", C.c_int),
         ("eject_r", C.c_double), ("bs_cluster_min", C.c_int), ("ml_levels", C.c_int),
-        ("ml_factor", C.c_int), ("bs_speculate", C.c_int),
+        ("ml_factor", C.c_int), ("bs_speculate", C.c_int), ("kick_symmetric", C.c_int),
     ]
 
 
@@ -52,7 +53,8 @@ class NbStats(C.Structure):
         "steps", "force_evals", "encounter_pairs", "groups", "bs_substeps", "bs_halvings",
         "bs_derivs", "merges", "kepler_iters", "moved_bodies", "log_dropped")] + [
         ("n_active", C.c_int), ("last_pairs", C.c_int), ("ejections", C.c_longlong),
-        ("m_ejected", C.c_double), ("ml_substeps", C.c_longlong), ("ml_groups", C.c_longlong)]
+        ("m_ejected", C.c_double), ("ml_substeps", C.c_longlong), ("ml_groups", C.c_longlong),
+        ("kick_symmetric", C.c_int)]
 
 
 # nb_allgather_fn: int (*)(void* user, const void* send, void* recv, size_t bytes, void* stream)

@@ -231,3 +231,68 @@ int main() {
     assert r.returncode == 0, r.stderr[-2000:]
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
+
+
+def test_integer_pipe_rinv3_against_long_double(tmp_path):
+    """r^-3 from a float seed with the residual and the (1 - e)^(-3/2) series
+    on the integer pipe and one FP64 product (host-callable, the same code the
+    unordered-pair kick runs): within 1.7 ulp of 1 / (r^2 sqrt(r^2)) in long
+    double, for r^2 over 2^-100..2^100 with extreme significands and seeds
+    off by up to 1e-6 relative either way (|e| up to ~2e-6; the kick's seed,
+    rsqrtf of r^2 truncated to a float, is off by at most ~2^-20)."""
+    nvcc = "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "r3.cu"
+    src.write_text(r"""
+#include "nb_internal.cuh"
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+int main() {
+  unsigned long long st = 0x2545F4914F6CDD1Dull;
+  auto rnd = [&]() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return st; };
+  long bad = 0;
+  long double worst = 0.0L;
+  for (long it = 0; it < 3000000; ++it) {
+    const int E = (int)(rnd() % 201) - 100;
+    unsigned long long mant = rnd() >> 12;
+    const int mode = (int)(it % 16);
+    if (mode == 0) mant = 0ull;
+    if (mode == 1) mant = 0xfffffffffffffull;
+    if (mode == 2) mant = 1ull;
+    const double r2 = ldexp(1.0 + (double)mant * 0x1p-52, E);
+    const long double y = 1.0L / sqrtl((long double)r2);
+    // seed: the exact root moved by up to 1e-6 relative (or the kick's own
+    // construction: rsqrt of r^2 truncated to a float), rounded to a float
+    float yf;
+    if (mode == 3) {
+      unsigned hr = (unsigned)(nb::nb_dbits(r2) >> 32);
+      unsigned fb = (hr << 3) + 0x40000000u;
+      float r2f; memcpy(&r2f, &fb, 4);
+      yf = 1.0f / sqrtf(r2f);
+    } else {
+      const long double u = ((long double)(rnd() >> 11) * 0x1p-53L * 2.0L - 1.0L) * 1e-6L;
+      yf = (float)(y * (1.0L + u));
+    }
+    unsigned yb; memcpy(&yb, &yf, 4);
+    const double got = nb::rinv3_from_seed(r2, yb);
+    const long double ex = y * y * y;
+    const long double rel = fabsl((long double)got - ex) / ex;
+    if (rel > worst) worst = rel;
+    if (rel > 1.7L * 0x1p-52L) {
+      if (bad < 5) printf("bad r2=%a yb=%08x got=%a ex=%La\n", r2, yb, got, ex);
+      ++bad;
+    }
+  }
+  printf("worst %.3Lg ulp\n%ld\n", worst / 0x1p-52L, bad);
+  return bad != 0;
+}
+""")
+    exe = tmp_path / "r3"
+    r = subprocess.run([nvcc, "-O2", "-std=c++17", "-I" + os.path.dirname(HDR),
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip().endswith("\n0"), out.stdout + out.stderr

@@ -71,10 +71,13 @@ def test_reciprocal_and_reciprocal_root(nb):
 
 
 @pytest.mark.parametrize("fn_name,bound", [("NB_MATH_RPOW32", 2.0), ("NB_MATH_RPOW32_M", 2.0),
+                                           ("NB_MATH_RINV3", 2.0),
                                            ("NB_MATH_RPOW32_MIXED", 1e-11 / U)])
 def test_r_minus_three(nb, fn_name, bound):
     """x^(-3/2) from x = r^2 as the kicks form m / r^3 (m = 1): the FP64
-    forms within 2 ulp, the single-Newton-step (mixed) form within 1e-11."""
+    forms within 2 ulp (the unordered-pair kick's r^-3 with its residual and
+    series on the integer pipe too), the single-Newton-step (mixed) form
+    within 1e-11."""
     rng = np.random.default_rng(3)
     x = np.concatenate([10.0 ** rng.uniform(-30, 30, 20000), [1.0, 4.0, 2.0, 1e-20]])
     got = evaluate(nb, getattr(nb, fn_name), x)

@@ -224,6 +224,117 @@ def test_kick_full_size_sampled():
     assert mine == pairset(pr)
 
 
+# ------------------------------------------------------------------ unordered-pair kick
+def sym_force(x, m, rc, sym=1):
+    """The cached force and flags after nb_init_system (one kick of the
+    whole system) with kick_symmetric = sym."""
+    nb = nbmod()
+    n = len(m)
+    p = nb.params(dt_rcrit=6.0)
+    p.kick_symmetric = sym
+    s = nb.NBodySystem(p, x, np.zeros((n, 3)), m, np.zeros(n), rc=rc)
+    return s.fsal()
+
+
+def check_sym(x, m, rc, tol=1e-13):
+    a, pairs = sym_force(x, m, rc)
+    ar, pr = nbref.forces(x, m, rc, G)
+    scale = np.abs(ar).max()
+    err = np.linalg.norm(a - ar, axis=1)
+    bound = tol * np.linalg.norm(ar, axis=1) + 1e-15 * scale
+    assert np.all(err <= bound), (err / np.maximum(np.linalg.norm(ar, axis=1), 1e-300)).max()
+    assert pairset(pairs) == pairset(pr)
+    return a, ar
+
+
+@pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 256, 257, 300, 385, 1000, 2049])
+def test_unordered_pair_kick_matches_oracle(n):
+    """Each pair once, applied to both bodies: one block, two (even: the
+    pairs at half the blocks' distance come from the lower block), three and
+    four blocks with a ragged last one, and 17 blocks; changeover radii x8 so
+    that many pairs take the exact branch (flags from both sides of a tile)."""
+    d = ics.workload("toy_disk_256", n=n, seed_offset=n)
+    check_sym(d.x, d.m, oracle_rc(d, scale=8.0))
+
+
+def test_unordered_pair_kick_edge_cases():
+    """Coincident distinct bodies (in one block and across blocks), a far
+    body, coordinates below the fixed-point resolution and near 2^36 AU, a
+    body of 1e-30 solar masses (the system takes no massless input; absorbed
+    bodies, massless, come with the merger tests)."""
+    d = ics.workload("toy_disk_256", n=300)
+    x = d.x.copy()
+    m = d.m.copy()
+    x[7] = x[3]                                   # same block
+    x[200] = x[5]                                 # across blocks
+    x[11] = [1e4, 0.0, 0.0]
+    x[20:30, 2] = np.linspace(-3e-13, 3e-13, 10)
+    x[130, :] = [2.0 ** 36, 0.0, 0.0]
+    x[131, :] = x[132, :] * (1 + 1e-9)            # nearly coincident
+    m[140] = 1e-30
+    check_sym(x, m, oracle_rc(d, scale=3.0))
+
+
+def test_unordered_pair_kick_agrees_with_row_kick_and_is_deterministic():
+    """16384 bodies (the automatic choice takes the unordered-pair kick):
+    the same flags as the row kick, forces within the kick bar of each other,
+    and the same bits on a second evaluation."""
+    d = ics.workload("mmsn_16k_js", n=16384)
+    rc = oracle_rc(d)
+    a0, p0 = sym_force(d.x, d.m, rc, sym=0)
+    a1, p1 = sym_force(d.x, d.m, rc, sym=1)
+    ar, pr = sym_force(d.x, d.m, rc, sym=-1)
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)  # automatic = on at this n
+    assert pairset(p1) == pairset(pr)
+    err = np.linalg.norm(a1 - ar, axis=1) / np.linalg.norm(ar, axis=1)
+    assert err.max() < 2e-13, err.max()
+    a2, _ = sym_force(d.x, d.m, rc, sym=1)
+    assert np.array_equal(a1, a2)
+
+
+def test_unordered_pair_kick_full_size_sampled():
+    """N = 65538 (the benchmark workload; 513 blocks, the launch the step
+    runs): 48 sampled bodies against the oracle row by row and their flags."""
+    d = ics.workload("mmsn_64k_js")
+    rc = oracle_rc(d)
+    a, pairs = sym_force(d.x, d.m, rc, sym=0)
+    rng = np.random.default_rng(0)
+    targets = np.concatenate([[0, 1, 2, 127, 128, d.n - 1], rng.choice(d.n, 42, replace=False)])
+    ar, pr = nbref.forces_targets(d.x, d.m, rc, targets, G)
+    err = np.linalg.norm(a[targets] - ar, axis=1) / np.linalg.norm(ar, axis=1)
+    assert err.max() < 1e-13
+    ts = set(int(t) for t in targets)
+    assert [q for q in pairset(pairs) if q[0] in ts or q[1] in ts] == pairset(pr)
+
+
+def test_kick_choice_is_reported_in_stats():
+    """The automatic choice: the unordered-pair kick for FP64 at 4096 <= n,
+    the row kick below, for the other precisions and when switched off."""
+    nb = nbmod()
+    for n, kw, want in ((4096, {}, 1), (4095, {}, 0), (2049, {"kick_symmetric": 1}, 1),
+                        (8192, {"kick_symmetric": -1}, 0),
+                        (8192, {"precision": nb.NB_PREC_MIXED}, 0),
+                        (8192, {"precision": nb.NB_PREC_DS, "kick_symmetric": 1}, 0)):
+        d = ics.workload("mmsn_16k_js", n=n - 2)
+        s = nb.NBodySystem(nb.params(dt_rcrit=d.dt, **kw), d.x, d.v, d.m, d.R)
+        assert s.n == n and s.stats()["kick_symmetric"] == want, (n, kw)
+
+
+def test_unordered_pair_kick_rejects_oversize_and_bad_values():
+    nb = nbmod()
+    d = ics.workload("toy_disk_256", n=8)
+    p = nb.params(dt_rcrit=d.dt)
+    p.kick_symmetric = 2
+    with pytest.raises(nb.NbError):
+        nb.NBodySystem(p, d.x, d.v, d.m, d.R)
+    n = 262145
+    p = nb.params(dt_rcrit=d.dt)
+    p.kick_symmetric = 1
+    x = np.tile(d.x, (n // 8 + 1, 1))[:n] * (1 + np.arange(n)[:, None] * 1e-7)
+    with pytest.raises(nb.NbError):
+        nb.NBodySystem(p, x, np.zeros((n, 3)), np.full(n, 1e-12), np.zeros(n))
+
+
 def _orbits(n, seed):
     rng = np.random.default_rng(seed)
     a = rng.uniform(0.3, 6.0, n)
@@ -257,12 +368,13 @@ def test_kepler_iteration_cap():
 
 
 # ------------------------------------------------------------------ full steps
-def run_both(d, steps, rc_scale=1.0, precision=0, **kw):
+def run_both(d, steps, rc_scale=1.0, precision=0, sym=0, **kw):
     nb = nbmod()
     rp = nbref.params(dt_rcrit=d.dt, **kw)
     rc = oracle_rc(d, rp, rc_scale)
     ref = nbref.RefSystem(rp, d.x, d.v, d.m, d.R, rc=rc)
     gp = nb.params(dt_rcrit=d.dt, precision=precision, **kw)
+    gp.kick_symmetric = sym
     gpu = nb.NBodySystem(gp, d.x, d.v, d.m, d.R, rc=rc)
     assert ref.step(steps, d.dt) == 0
     gpu.step(steps, d.dt)
@@ -340,6 +452,27 @@ def test_step_parity_with_mergers():
     er, eg = ref.energy_momentum(), gpu.energy_momentum()
     assert abs(eg["E_lost"] - er["E_lost"]) <= 1e-10 * abs(er["E_lost"]) + 1e-22
     assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+
+
+def test_step_parity_unordered_pair_kick():
+    """The step with the unordered-pair kick forced on at small N: the
+    merging disk over 100 steps (the incremental force update subtracts the
+    group members' terms in that kick's arithmetic) and the disk with the
+    giants."""
+    d = ics.workload("toy_disk_256", f_radius=400.0)
+    ref, gpu = run_both(d, 100, sym=1)
+    assert gpu.stats()["merges"] == ref.stats()["merges"] > 0
+    compare_states(ref, gpu)
+    assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+    d = ics.workload("mmsn_16k_js", n=2000)
+    ref, gpu = run_both(d, 30, sym=1)
+    er = ref.encounter_list()
+    assert len(er) > 0 and np.array_equal(er, gpu.encounter_list())
+    sr, sg = ref.state(), gpu.state()
+    rel = np.linalg.norm(sg["x"] - sr["x"], axis=1) / np.linalg.norm(sr["x"], axis=1)
+    enc = np.isin(sr["ids"], er[:, 1:].reshape(-1))
+    assert rel[~enc].max() <= 1e-12
+    assert rel.max() <= max(1e-12, 3.0 * oracle_self_sensitivity(d, 30))
 
 
 @pytest.mark.parametrize("prec_name", ["NB_PREC_MIXED", "NB_PREC_DS"])

@@ -171,8 +171,8 @@ def test_sharded_step_full_size_two_ranks():
     """The 64k disk with Jupiter and Saturn on 2 emulated ranks, 2 steps."""
     d = ics.workload("mmsn_64k_js")
     rc = oracle_rc(d)
-    sr, er, _ = reference(d, rc, 2)
-    out, _ = run_sharded(d, rc, 2, 2)
+    sr, er, _ = reference(d, rc, 2, kick_symmetric=-1)  # ranks run the row kick
+    out, _ = run_sharded(d, rc, 2, 2, kick_symmetric=-1)
     for sg, eg, stg, code, r0, r1 in out:
         assert code == 0
         assert np.array_equal(sg["x"], sr["x"]) and np.array_equal(sg["v"], sr["v"])
