@@ -563,7 +563,10 @@ __host__ __device__ __forceinline__ double sep2_fix(const FixDiff& a, const FixD
 // 2^-60 in all), and p's bits follow by rounding that integer to p's ulp
 // (2^-52 above 1, 2^-53 below). With y3 = y0^3 rounded (seed_powers) and the
 // one rounded product, r^-3 is within ~1.6 ulp (the e^3 term, < 2^-55.7 for
-// |e| < 2e-6, as in scale_fast). Valid for seeds with |e| < 2^-18 and
+// |e| < 2e-6, as in scale_fast). The product y3 p stays on the FP64 pipe:
+// forming it from the 117-bit integer product too (1.0 ulp) made the kick
+// 9 % slower at N = 65538 (40.1 against 36.7 ms), the integer pipe being the
+// busier one by then. Valid for seeds with |e| < 2^-18 and
 // 2^-126 <= r^2 < 2^128 (the seed's range). Host-callable with the seed's
 // bits as an input, so that it can be checked on the CPU.
 __host__ __device__ __forceinline__ double rinv3_from_seed(double r2, unsigned yb) {
