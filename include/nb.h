@@ -117,12 +117,13 @@ typedef struct {
    * to, and takes it on a failure; 0 = attempts one after the other. The
    * results, counters and adjoint records are the same bit for bit. */
   int bs_speculate;
-  /* Unordered-pair kick (FP64 precision, unsharded systems): each pair {i, j}
-   * is evaluated once and its term applied to both bodies (Newton's third
-   * law), 6 FP64 instructions per ordered pair against 7 in the row kick.
+  /* Unordered-pair kick (FP64 and double-single precision, unsharded
+   * systems): each pair {i, j} is evaluated once and its term applied to both
+   * bodies (Newton's third law); in FP64, 4.5 FP64 instructions per ordered
+   * pair against 7 in the row kick.
    * 0 (default) = automatic: on for 4096 <= n <= 262144; 1 = on for any
    * n <= 262144 (nb_init_system returns NB_E_INVALID above); -1 = off (the
-   * row kick). The other precisions always run the row kick. Results agree
+   * row kick). The mixed precision always runs the row kick. Results agree
    * with the row kick to rounding (the products and the order of the sums
    * differ), deterministic for a given n. A sharded system (nb_set_shard,
    * world > 1) runs the row kick whatever the setting; the shards equal the

@@ -79,7 +79,7 @@ size_t layout(const nb_params& p, int n, char* base, Dev* out) {
   d.member_slot = c.take<int>(n);
   d.uf = c.take<int>(n > 64 ? n : 64);
   // the unordered-pair kick's partials share the kpart allocation
-  const bool sym = p.precision == NB_PREC_FP64 &&
+  const bool sym = (p.precision == NB_PREC_FP64 || p.precision == NB_PREC_DS) &&
                    (p.kick_symmetric == 1 ? n <= kSymMaxN
                                           : p.kick_symmetric == 0 && n >= kSymMinN && n <= kSymMaxN);
   size_t kpart_n = (size_t)3 * d.S * n;
@@ -323,7 +323,7 @@ int nb_init_system(nb_system** out, const nb_params* p, int n, const double* x, 
   if (!out) return NB_E_INVALID;
   *out = nullptr;
   if (!params_ok(p) || n < 1 || !x || !v || !m || !R) return NB_E_INVALID;
-  if (p->kick_symmetric == 1 && p->precision == NB_PREC_FP64 && n > kSymMaxN) return NB_E_INVALID;
+  if (p->kick_symmetric == 1 && p->precision != NB_PREC_MIXED && n > kSymMaxN) return NB_E_INVALID;
   const size_t need = layout(*p, n, nullptr, nullptr);
   if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)) return NB_E_WORKSPACE;
   nb_system* s = (nb_system*)calloc(1, sizeof(nb_system));

@@ -693,6 +693,212 @@ __global__ void __launch_bounds__(DNT2, kDsMinBlocks) k_kick_ds(KickArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-single unordered-pair kick (NB_PREC_DS, whole system): the tile
+// schedule, rotation and partial sums of k_kick_sym with the pair arithmetic
+// of k_kick_ds. Per pair {i, j} the float-pair differences, r^2 and r^-3 = y1^3
+// once (y1 the refined float-pair r^-1), then m_j r^-3 and m_i r^-3, the
+// products with dx, dy, dz and the float-pair sums of both sides. The row
+// side's sums are float pairs over a tile (128 pairs) folded into FP64, the
+// column side's float pairs over a 32-pair sub-tile, folded into FP64 and
+// added over the four warps in warp order. A pair whose float r^2 passes the
+// encounter pre-test takes the exact FP64 branch of k_kick_sym (from the FP64
+// positions), so flags are identical to the FP64 kicks'.
+// ---------------------------------------------------------------------------
+#ifndef NB_DS_SYM_MINB
+#define NB_DS_SYM_MINB 5
+#endif
+constexpr int kDsSymMinBlocks = NB_DS_SYM_MINB;  // CTAs per SM the registers are bounded for
+
+// dx, dy, dz, r^2 (high part) and r^-3 of a source staged as three float4
+// (x.h, x.m, x.l, y.h), (y.m, y.l, z.h, z.m), (z.l, m.h, m.l, threshold)
+// against a target's grid coordinates: the arithmetic of k_kick_ds.
+struct DsPairTerm {
+  F2 fx, fy, fz, r3;
+  float r2h;
+};
+__device__ __forceinline__ DsPairTerm ds_pair_term(const float4& va, const float4& vb,
+                                                   const float4& vc, const DsCoord& cx,
+                                                   const DsCoord& cy, const DsCoord& cz) {
+  DsPairTerm o;
+  const DsCoord qx{va.x, va.y, va.z}, qy{va.w, vb.x, vb.y}, qz{vb.z, vb.w, vc.x};
+  o.fx = ds_diff(qx, cx);
+  o.fy = ds_diff(qy, cy);
+  o.fz = ds_diff(qz, cz);
+  F2 px = two_prod(o.fx.h, o.fx.h), py = two_prod(o.fy.h, o.fy.h), pz = two_prod(o.fz.h, o.fz.h);
+  px.l = __fmaf_rn(__fmul_rn(2.0f, o.fx.h), o.fx.l, px.l);
+  py.l = __fmaf_rn(__fmul_rn(2.0f, o.fy.h), o.fy.l, py.l);
+  pz.l = __fmaf_rn(__fmul_rn(2.0f, o.fz.h), o.fz.l, pz.l);
+  F2 t = two_sum(px.h, py.h);
+  t.l = __fadd_rn(t.l, __fadd_rn(px.l, py.l));
+  F2 u = two_sum(t.h, pz.h);
+  u.l = __fadd_rn(u.l, __fadd_rn(t.l, pz.l));
+  const F2 r2 = fast_two_sum(u.h, u.l);
+  const float y0 = rsqrtf(r2.h);
+  const F2 q2 = two_prod(y0, y0);
+  const F2 s = ds_mul_u(r2, q2);
+  const float eh = __fsub_rn(1.0f, s.h);
+  const F2 c = two_prod(y0, eh);
+  const float cl = __fmaf_rn(__fmul_rn(0.75f, y0), __fmul_rn(eh, eh), __fmaf_rn(y0, -s.l, c.l));
+  const F2 yy = fast_two_sum(y0, __fmul_rn(0.5f, c.h));
+  const F2 y1{yy.h, __fmaf_rn(0.5f, cl, yy.l)};
+  o.r3 = ds_mul(ds_mul_u(y1, y1), y1);
+  o.r2h = r2.h;
+  return o;
+}
+
+// The exact FP64 branch for a pair that passed the float pre-test: r^2 from
+// the FP64 positions, the scales of k_kick_sym (seeded r^-3 beyond rc, the
+// changeover weight inside, 0 for coincident bodies) and the flag; the
+// differences and scales are returned as float pairs.
+template <bool DIAG>
+__device__ __forceinline__ void ds_sym_rare(int i, int j, const KickArgs& A, DsPairTerm& p,
+                                            F2& sj, F2& si) {
+  if (i >= A.n || j >= A.n) return;  // padding: massless, far, never flagged
+  const double dx = __ldg(A.x + j) - __ldg(A.x + i), dy = __ldg(A.y + j) - __ldg(A.y + i),
+               dz = __ldg(A.z + j) - __ldg(A.z + i);
+  const double mj = __ldg(A.m + j), mi = __ldg(A.m + i);
+  const double r2 = sep2(dx, dy, dz);
+  const double r3 = r2 > 0.0 ? rinv3_fast(r2) : 0.0;
+  double sj64 = mj * r3, si64 = mi * r3;
+  sym_rare<DIAG>(i, j, mi, mj, A, sj64, si64);
+  sj = split_d(sj64);
+  si = split_d(si64);
+  p.fx = split_d(dx);
+  p.fy = split_d(dy);
+  p.fz = split_d(dz);
+}
+
+// s += g as a float pair (the sums' two_sum on the high parts, the low parts added)
+__device__ __forceinline__ void ds_acc(F2& s, const F2& g) {
+  const F2 w = two_sum(s.h, g.h);
+  s = F2{w.h, __fadd_rn(w.l, __fadd_rn(s.l, g.l))};
+}
+
+__global__ void __launch_bounds__(KNT, kDsSymMinBlocks) k_kick_ds_sym(KickArgs A, SymArgs L) {
+  __shared__ float4 sA[KNT], sB[KNT], sC[KNT];  // block Y, as staged by k_kick_ds
+  __shared__ double sacc[3][4][KNT];            // the warps' column sums of a tile
+  __shared__ int s_stop, s_exp;
+  if (threadIdx.x == 0) {
+    s_stop = A.ctrl->status || (A.cond && *A.cond == 0);
+    s_exp = A.ctrl->ds_exp;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const unsigned ge = (unsigned)s_exp - 22u;  // biased exponent of G
+  const double G = __longlong_as_double((long long)ge << 52);
+  const double iG = __longlong_as_double((long long)(2046u - ge) << 52);
+  const float Gf = __uint_as_float((ge - 896u) << 23);
+  const int n = A.n;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int H1 = L.hrow + 1;
+  const int f0 = blockIdx.x * L.per;
+  const int f1 = min(L.tiles, f0 + L.per);
+  int X = -1, seg = 0, i = 0;
+  DsCoord cx{0.0f, 0.0f, 0.0f}, cy = cx, cz = cx;
+  F2 mi{0.0f, 0.0f};
+  float thi = 0.0f;
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int f = f0; f < f1; ++f) {
+    const int Xf = f / H1, dd = f - Xf * H1;
+    if (Xf != X) {
+      if (X >= 0) {
+        double* p = L.xpart + (size_t)((blockIdx.x * 2 + seg) * 3) * KNT + threadIdx.x;
+        p[0] = ax;
+        p[KNT] = ay;
+        p[2 * KNT] = az;
+        seg = 1;
+      }
+      X = Xf;
+      i = X * KNT + threadIdx.x;
+      const bool live = i < n;
+      cx = ds_coord(live ? A.x[i] : 1e10, G, iG, Gf);
+      cy = ds_coord(live ? A.y[i] : 1e10, G, iG, Gf);
+      cz = ds_coord(live ? A.z[i] : 1e10, G, iG, Gf);
+      mi = live ? split_d(A.m[i]) : F2{0.0f, 0.0f};
+      thi = rc2_threshold(live ? A.rc2[i] : 0.0);
+      ax = ay = az = 0.0;
+    }
+    if (2 * dd == L.nb && X >= L.nb / 2) continue;  // the lower block covers this pair
+    int Yb = X + dd;
+    if (Yb >= L.nb) Yb -= L.nb;
+    const int jb = Yb * KNT;
+    __syncthreads();
+    {
+      const int j = jb + threadIdx.x;
+      const bool live = j < n;
+      const DsCoord qx = ds_coord(live ? A.x[j] : 1e10, G, iG, Gf),
+                    qy = ds_coord(live ? A.y[j] : 1e10, G, iG, Gf),
+                    qz = ds_coord(live ? A.z[j] : 1e10, G, iG, Gf);
+      const F2 mm = live ? split_d(A.m[j]) : F2{0.0f, 0.0f};
+      sA[threadIdx.x] = make_float4(qx.h, qx.m, qx.l, qy.h);
+      sB[threadIdx.x] = make_float4(qy.m, qy.l, qz.h, qz.m);
+      sC[threadIdx.x] = make_float4(qz.l, mm.h, mm.l, rc2_threshold(live ? A.rc2[j] : 0.0));
+    }
+    __syncthreads();
+    F2 tx{0.0f, 0.0f}, ty = tx, tz = tx;  // this body's sums over the tile
+    if (dd == 0) {
+      // the block with itself: every ordered pair, this body's side only
+#pragma unroll 1
+      for (int q = 0; q < KNT; ++q) {
+        const float4 va = sA[q], vb = sB[q], vc = sC[q];
+        DsPairTerm p = ds_pair_term(va, vb, vc, cx, cy, cz);
+        F2 sj = ds_mul(F2{vc.y, vc.z}, p.r3), si{0.0f, 0.0f};
+        if (p.r2h <= fmaxf(thi, vc.w)) ds_sym_rare<true>(i, jb + q, A, p, sj, si);
+        ds_acc(tx, ds_mul_u(sj, p.fx));
+        ds_acc(ty, ds_mul_u(sj, p.fy));
+        ds_acc(tz, ds_mul_u(sj, p.fz));
+      }
+    } else {
+#pragma unroll 1
+      for (int u = 0; u < 4; ++u) {
+        F2 bx{0.0f, 0.0f}, by = bx, bz = bx;  // column sums, one lane down per step
+#pragma unroll 1
+        for (int s = 0; s < 32; ++s) {
+          const int q = 32 * u + ((lane + s) & 31);
+          const float4 va = sA[q], vb = sB[q], vc = sC[q];
+          DsPairTerm p = ds_pair_term(va, vb, vc, cx, cy, cz);
+          F2 sj = ds_mul(F2{vc.y, vc.z}, p.r3), si = ds_mul(mi, p.r3);
+          if (p.r2h <= fmaxf(thi, vc.w)) ds_sym_rare<false>(i, jb + q, A, p, sj, si);
+          ds_acc(tx, ds_mul_u(sj, p.fx));
+          ds_acc(ty, ds_mul_u(sj, p.fy));
+          ds_acc(tz, ds_mul_u(sj, p.fz));
+          const F2 gx = ds_mul_u(si, p.fx), gy = ds_mul_u(si, p.fy), gz = ds_mul_u(si, p.fz);
+          ds_acc(bx, F2{-gx.h, -gx.l});
+          ds_acc(by, F2{-gy.h, -gy.l});
+          ds_acc(bz, F2{-gz.h, -gz.l});
+          const int src = (lane + 1) & 31;
+          bx.h = __shfl_sync(0xffffffffu, bx.h, src);
+          bx.l = __shfl_sync(0xffffffffu, bx.l, src);
+          by.h = __shfl_sync(0xffffffffu, by.h, src);
+          by.l = __shfl_sync(0xffffffffu, by.l, src);
+          bz.h = __shfl_sync(0xffffffffu, bz.h, src);
+          bz.l = __shfl_sync(0xffffffffu, bz.l, src);
+        }
+        sacc[0][wp][32 * u + lane] = (double)bx.h + (double)bx.l;
+        sacc[1][wp][32 * u + lane] = (double)by.h + (double)by.l;
+        sacc[2][wp][32 * u + lane] = (double)bz.h + (double)bz.l;
+      }
+    }
+    ax += (double)tx.h + (double)tx.l;
+    ay += (double)ty.h + (double)ty.l;
+    az += (double)tz.h + (double)tz.l;
+    if (dd == 0) continue;
+    __syncthreads();
+    double* p = L.ypart + ((size_t)Yb * L.hrow + (dd - 1)) * 3 * KNT + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      p[c * KNT] = ((sacc[c][0][threadIdx.x] + sacc[c][1][threadIdx.x]) + sacc[c][2][threadIdx.x]) +
+                   sacc[c][3][threadIdx.x];
+  }
+  if (X >= 0) {
+    double* p = L.xpart + (size_t)((blockIdx.x * 2 + seg) * 3) * KNT + threadIdx.x;
+    p[0] = ax;
+    p[KNT] = ay;
+    p[2 * KNT] = az;
+  }
+}
+
 // CTAs of a kick launch: target tiles (KNT KIPT targets, DNT2 DIPT for the
 // double-single kernel) x S j-chunks
 int kick_blocks(int n, int S, int precision) {
@@ -723,7 +929,7 @@ static int jchunk_for(int n, int S) {
   return c > 0 ? c : KNT;
 }
 
-static void launch_kick_sym(const KickArgs& A, const Dev& d, cudaStream_t st) {
+static void launch_kick_sym(const KickArgs& A, const Dev& d, const Phys& P, cudaStream_t st) {
   SymArgs L;
   L.nb = d.sym_nb;
   L.hrow = d.sym_hrow;
@@ -731,7 +937,12 @@ static void launch_kick_sym(const KickArgs& A, const Dev& d, cudaStream_t st) {
   L.per = d.sym_per;
   L.xpart = d.sym_xpart;
   L.ypart = d.sym_ypart;
-  k_kick_sym<<<d.sym_grid, KNT, 0, st>>>(A, L);
+  if (P.precision == NB_PREC_DS) {
+    k_ds_grid<<<1, DGT, 0, st>>>(A.n, A.x, A.y, A.z, A.ctrl);
+    k_kick_ds_sym<<<d.sym_grid, KNT, 0, st>>>(A, L);
+  } else {
+    k_kick_sym<<<d.sym_grid, KNT, 0, st>>>(A, L);
+  }
 }
 
 void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t st) {
@@ -749,7 +960,7 @@ void launch_kick(const Dev& d, const Phys& P, int /*target_sel*/, cudaStream_t s
   A.counter = &d.ctrl->n_ftrial;
   A.ctrl = d.ctrl;
   if (d.sym)
-    launch_kick_sym(A, d, st);
+    launch_kick_sym(A, d, P, st);
   else
     launch_kick_args(A, P.precision, st);
 }
@@ -930,7 +1141,7 @@ void launch_force_anew(const Dev& d, const Phys& P, int only_if_ejected, cudaStr
   A.counter = &d.ctrl->n_ftrial;
   A.ctrl = d.ctrl;
   if (d.sym)
-    launch_kick_sym(A, d, st);
+    launch_kick_sym(A, d, P, st);
   else
     launch_kick_args(A, P.precision, st);
   k_finish_t<0><<<(d.n + FNT - 1) / FNT, FNT, 0, st>>>(d, P.G, 0, cond);

@@ -225,12 +225,12 @@ def test_kick_full_size_sampled():
 
 
 # ------------------------------------------------------------------ unordered-pair kick
-def sym_force(x, m, rc, sym=1):
+def sym_force(x, m, rc, sym=1, precision=0):
     """The cached force and flags after nb_init_system (one kick of the
     whole system) with kick_symmetric = sym."""
     nb = nbmod()
     n = len(m)
-    p = nb.params(dt_rcrit=6.0)
+    p = nb.params(dt_rcrit=6.0, precision=precision)
     p.kick_symmetric = sym
     s = nb.NBodySystem(p, x, np.zeros((n, 3)), m, np.zeros(n), rc=rc)
     return s.fsal()
@@ -307,14 +307,68 @@ def test_unordered_pair_kick_full_size_sampled():
     assert [q for q in pairset(pairs) if q[0] in ts or q[1] in ts] == pairset(pr)
 
 
+@pytest.mark.parametrize("n", [1, 2, 129, 257, 385, 1000, 2049])
+def test_unordered_pair_ds_kick_matches_oracle(n):
+    """The double-single unordered-pair kick against the oracle at the
+    double-single bar (1e-10 |a_i| + 1e-13 max|a|), flags identical: one to
+    seventeen blocks, ragged last blocks, many pairs in the exact branch."""
+    nb = nbmod()
+    d = ics.workload("toy_disk_256", n=n, seed_offset=7 * n)
+    rc = oracle_rc(d, scale=8.0)
+    a, pairs = sym_force(d.x, d.m, rc, precision=nb.NB_PREC_DS)
+    ar, pr = nbref.forces(d.x, d.m, rc, G)
+    err = np.linalg.norm(a - ar, axis=1)
+    assert np.all(err <= 1e-10 * np.linalg.norm(ar, axis=1) + 1e-13 * np.abs(ar).max())
+    assert pairset(pairs) == pairset(pr)
+
+
+@pytest.mark.parametrize("far", [False, True])
+def test_unordered_pair_ds_kick_against_fp64_and_oracle(far):
+    """3002 bodies with the giants (and optionally a live body at 3000 AU that
+    makes the coordinate grid 2^9 times coarser): the double-single
+    unordered-pair kick within 1e-10 (median 1e-12) of the FP64
+    unordered-pair kick and of the oracle, finite, flags identical."""
+    nb = nbmod()
+    d = ics.workload("mmsn_16k_js", n=3000)
+    x = d.x.copy()
+    if far:
+        x[7] = [3000.0, -20.0, 1.0]
+    rc = oracle_rc(d, scale=3.0)
+    a64, p64 = sym_force(x, d.m, rc)
+    ads, pds = sym_force(x, d.m, rc, precision=nb.NB_PREC_DS)
+    assert np.all(np.isfinite(ads))
+    rel = np.linalg.norm(ads - a64, axis=1) / np.linalg.norm(a64, axis=1)
+    assert rel.max() < 1e-10 and np.median(rel) < 1e-12
+    assert pairset(pds) == pairset(p64)
+    ar, _ = nbref.forces(x, d.m, rc, G)
+    assert (np.linalg.norm(ads - ar, axis=1) / np.linalg.norm(ar, axis=1)).max() < 1e-10
+
+
+def test_step_parity_unordered_pair_ds_kick_with_mergers():
+    """The double-single unordered-pair kick in the step, forced on at small
+    N: the merging disk over 100 steps (absorbed bodies parked massless far
+    out among the live ones) at the FP64 step bar, with identical encounter
+    lists and merger counts."""
+    nb = nbmod()
+    d = ics.workload("toy_disk_256", f_radius=400.0)
+    ref, gpu = run_both(d, 100, precision=nb.NB_PREC_DS, sym=1)
+    assert gpu.stats()["kick_symmetric"] == 1
+    assert gpu.stats()["merges"] == ref.stats()["merges"] > 0
+    compare_states(ref, gpu)
+    assert np.array_equal(ref.encounter_list(), gpu.encounter_list())
+
+
 def test_kick_choice_is_reported_in_stats():
-    """The automatic choice: the unordered-pair kick for FP64 at 4096 <= n,
-    the row kick below, for the other precisions and when switched off."""
+    """The automatic choice: the unordered-pair kick for FP64 and
+    double-single at 4096 <= n, the row kick below, for the mixed precision
+    and when switched off."""
     nb = nbmod()
     for n, kw, want in ((4096, {}, 1), (4095, {}, 0), (2049, {"kick_symmetric": 1}, 1),
                         (8192, {"kick_symmetric": -1}, 0),
                         (8192, {"precision": nb.NB_PREC_MIXED}, 0),
-                        (8192, {"precision": nb.NB_PREC_DS, "kick_symmetric": 1}, 0)):
+                        (8192, {"precision": nb.NB_PREC_MIXED, "kick_symmetric": 1}, 0),
+                        (8192, {"precision": nb.NB_PREC_DS}, 1),
+                        (4095, {"precision": nb.NB_PREC_DS}, 0)):
         d = ics.workload("mmsn_16k_js", n=n - 2)
         s = nb.NBodySystem(nb.params(dt_rcrit=d.dt, **kw), d.x, d.v, d.m, d.R)
         assert s.n == n and s.stats()["kick_symmetric"] == want, (n, kw)
