@@ -654,6 +654,7 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
     ms = e0.elapsed_time(e1) / (2 * chunk)
     bal = b.balance()  # the last close launch
     st = b.stats()
+    sym = bool(st.get("kick_symmetric", 0))
     del b
     # single-system path on a random sample of the same systems
     rng = np.random.default_rng(7)
@@ -677,12 +678,15 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
             "pairs_per_step": pairs, "value": pairs / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms, "steps_per_s": 1e3 / ms,
             "autotuned_shape": {"threads_per_cta": threads, "steps_per_graph": chunk,
-                                "kick_tile_rows": shape["tile_rows"],
+                                "kick_tile_rows": None if sym else shape["tile_rows"],
                                 "buckets": shape["buckets"],
                                 "schedule": "per step and bucket (every k-th system of the "
                                             "largest-first order, its own stream): open (per "
-                                            "system), kick (tiles of %d rows of one system), "
-                                            "close (per system)" % shape["tile_rows"]},
+                                            "system), kick (%s), close (per system)" % (
+                                                "one warp per 32-body block pair of one "
+                                                "system, each pair once for both bodies" if sym
+                                                else "tiles of %d rows of one system"
+                                                % shape["tile_rows"])},
             "timing": "one call of 2 graph replays of the autotuned chunk, L2 flushed before",
             "ms_per_step_one_call_per_step": ms_call,
             "single_system_path_ms_per_step_est": single_ms, "speedup_vs_single": single_ms / ms,
@@ -693,28 +697,30 @@ def run_batched(nb, torch, args, flush, stream, n_systems=4096, dt=3.0, sample=3
                              "definition": "sum of CTA busy times / (CTAs x longest), the last "
                                            "close launch"},
             "groups": st["groups"], "merges": st["merges"],
-            "roofline": batched_roofline(pairs, ms, f64_peak)}
+            "roofline": batched_roofline(pairs, ms, f64_peak, sym)}
 
 
-def batched_roofline(pairs, ms, f64_peak):
-    """The ensemble step against the FP64 pipe: the kick's 7 FP64 instructions
-    per pair (dx, dy, dz and r^2 on the integer pipe, as in the single-system
-    kick) at the step's rate, over the DFMA peak measured in the same run; and
-    the kick's own FP64 pipe share in one launch (ncu, profiles/)."""
-    out = {"bound": "alu", "kernel": "k_batch_kick<32, 32>",
-           "fp64_instr_per_pair_design": FP64_INSTR_PER_PAIR}
+def batched_roofline(pairs, ms, f64_peak, sym):
+    """The ensemble step against the FP64 pipe: the kick's FP64 instructions
+    per ordered pair (4.5 for the unordered-pair kick, 7 for the row kick; dx,
+    dy, dz and r^2 on the integer pipe, as in the single-system kicks) at the
+    step's rate, over the DFMA peak measured in the same run; and the kick's
+    own FP64 pipe share in one launch (ncu, profiles/)."""
+    ipp = FP64_INSTR_PER_PAIR_SYM if sym else FP64_INSTR_PER_PAIR
+    kernel = "k_batch_kick_sym" if sym else "k_batch_kick<32, 32>"
+    out = {"bound": "alu", "kernel": kernel, "fp64_instr_per_pair_design": ipp}
     if f64_peak:
-        out["fp64_pipe_frac_by_count_step"] = (FP64_INSTR_PER_PAIR * pairs / (ms * 1e-3)
-                                               / (f64_peak / 2))
+        out["fp64_pipe_frac_by_count_step"] = ipp * pairs / (ms * 1e-3) / (f64_peak / 2)
         out["peak_source"] = "FP64 DFMA loop measured in this run (nb_measure_peaks)"
-    pb = read_traffic(os.path.join(ROOT, "profiles", "batch_kick_ensemble_4096_pipes.txt"))
-    if pb.get("systems") == "4096":
+    name = "batch_kick_sym_ensemble_4096_pipes.txt" if sym else \
+        "batch_kick_ensemble_4096_pipes.txt"
+    pb = read_traffic(os.path.join(ROOT, "profiles", name))
+    if pb.get("systems") == "4096" and pb.get("kernel") == kernel:
         out["kick_fp64_pipe_frac"] = float(pb["fp64_pipe_pct"]) / 100
         out["kick_fp64_instr_per_lane_pair"] = float(pb["fp64_inst_per_lane_pair"])
         out["kick_ms_one_launch"] = float(pb["gpu_time_ms"])
         out["pipes_source"] = ("ncu sm__pipe_fp64_cycles_active and sm__inst_executed_pipe_fp64.sum, "
-                               "one launch of the whole ensemble's kick, profiles/"
-                               "batch_kick_ensemble_4096_pipes.txt")
+                               "one launch of the whole ensemble's kick, profiles/" + name)
     return out
 
 

@@ -127,7 +127,9 @@ typedef struct {
    * with the row kick to rounding (the products and the order of the sums
    * differ), deterministic for a given n. A sharded system (nb_set_shard,
    * world > 1) runs the row kick whatever the setting; the shards equal the
-   * one-GPU step with -1 bit for bit. */
+   * one-GPU step with -1 bit for bit. Batches (nb_batch_*): 0 or 1 (default)
+   * = the unordered-pair kick on 32-body block pairs of each system, -1 = the
+   * row kick in tiles of the schedule's tile rows. */
   int kick_symmetric;
 } nb_params;
 
@@ -313,7 +315,8 @@ int nb_batch_step(nb_batch* b, int nsteps, double dt);
  * largest-first order (one bucket's latency-bound direct solver then overlaps
  * the others' kicks). nb_batch_autotune() times threads {64, 128, 256} x
  * buckets {4, 8, 16} at 32-row tiles and 25-step graphs, then tile rows 64
- * and 128, then chunks of 10 and 50 steps, on graph replays of a copy of the
+ * and 128 (the row kick only: the unordered-pair kick's tiles are 32-body
+ * block pairs), then chunks of 10 and 50 steps, on graph replays of a copy of the
  * state (restored afterwards), and keeps the fastest;
  * nb_batch_get_shape() reports what is in use. None of these changes a
  * result: every system's arithmetic is the same in any shape. */

@@ -44,8 +44,12 @@ struct BatchDev {
   int* nfprev;      // nsys
   unsigned* ftrial; // nsys * BPAIR keys of the trial kick
   int* nftrial;     // nsys (unclipped counts)
-  const int2* tiles;  // (system, first row) of each kick tile, largest systems first
+  const int2* tiles;  // kick tiles, largest systems first: (system, first row) for the row
+                      // kick, (system, X << 16 | Y) for the unordered-pair kick
   int ntiles;
+  int sym;            // 1: the unordered-pair kick (32-body block pairs, partial sums)
+  double* kp;         // its partials: per system and tile (X <= Y) 2 x 3 x 32 doubles
+  const int* kpo;     // nsys: offset of a system's partials in kp (doubles)
   int* blog;        // nsys * kBatchLogCap * 3: each system's encounter log of the current call
   int* nblog;       // nsys (unclipped counts)
   double* El;       // nsys: energy removed by mergers
@@ -88,6 +92,7 @@ struct BSmem {
   int* alive;
   unsigned *fp, *ft, *e;  // F_prev, F_trial (BPAIR each), E keys (2 BPAIR)
   int *uf, *goff, *gmem, *gidx;
+  int sym;    // the kick's terms in the unordered-pair kick's arithmetic
   int* ints;  // [0] nFp [1] nFt [2] nE [3] ngroups [4] overflow [6..7] bs flags;
               // [16 + 4w ..] flags of warp w (warp-team groups), [8] error of a warp team
 };
@@ -136,6 +141,7 @@ __device__ inline BSmem carve_smem(char* base, int nmax, int NT) {
   s.gidx = ip;
   ip += nmax;
   s.ints = ip;
+  s.sym = 0;
   return s;
 }
 
@@ -187,15 +193,18 @@ struct KArrays {
 };
 // The integer-pipe part and the far-pair weight; returns whether the pair
 // needs the exact branch.
+// With sym the far-pair scale is m_j times the seeded r^-3 of the unordered-pair
+// kick (rinv3_fast), so that the close phase recomputes that kick's terms.
 __device__ __forceinline__ bool kick_fast(KTerm& t, const KTarget& ti, const nb_u128& Xj,
                                           const nb_u128& Yj, const nb_u128& Zj, double mj,
-                                          double m15j, double m1875j, double rc2j) {
+                                          double m15j, double m1875j, double rc2j,
+                                          bool sym = false) {
   const FixDiff fx = fix_diff(Xj, ti.X), fy = fix_diff(Yj, ti.Y), fz = fix_diff(Zj, ti.Z);
   t.dx = fx.d;
   t.dy = fy.d;
   t.dz = fz.d;
   const double r2 = sep2_fix(fx, fy, fz);
-  t.sc = scale_fast<NB_PREC_FP64>(r2, mj, m15j, m1875j);
+  t.sc = sym ? mj * rinv3_fast(r2) : scale_fast<NB_PREC_FP64>(r2, mj, m15j, m1875j);
   t.close = false;
   return __double2hiint(r2) <= max(ti.hi, __double2hiint(rc2j)) + 1;
 }
@@ -215,10 +224,10 @@ __device__ __forceinline__ void kick_rare(KTerm& t, const KTarget& ti, const KAr
 __device__ __forceinline__ KTerm kick_term(const KTarget& ti, const KArrays& ta,
                                            const nb_u128& Xj, const nb_u128& Yj,
                                            const nb_u128& Zj, double mj, double rc2j,
-                                           const KArrays& sa, int j) {
+                                           const KArrays& sa, int j, bool sym) {
   KTerm t;
   // 1.5 m and 1.875 m as the tiled kick stages them (FP64 products, the same bits)
-  if (kick_fast(t, ti, Xj, Yj, Zj, mj, 1.5 * mj, 1.875 * mj, rc2j))
+  if (kick_fast(t, ti, Xj, Yj, Zj, mj, 1.5 * mj, 1.875 * mj, rc2j, sym))
     kick_rare(t, ti, ta, mj, rc2j, sa, j);
   return t;
 }
@@ -237,7 +246,7 @@ __device__ __forceinline__ KTarget target_of(const BSmem& s, int i) {
 // Source term of body j at its current position (staged fixed point).
 __device__ __forceinline__ KTerm kick_term_j(const KTarget& ti, const BSmem& s, int j) {
   const KArrays a{s.x, s.y, s.z, s.rc};
-  return kick_term(ti, a, s.fX[j], s.fY[j], s.fZ[j], s.m[j], s.rc2[j], a, j);
+  return kick_term(ti, a, s.fX[j], s.fY[j], s.fZ[j], s.m[j], s.rc2[j], a, j, s.sym);
 }
 
 // Fixed-point positions of all bodies, from the double positions.
@@ -315,7 +324,7 @@ __device__ void sys_kick_update(const BSmem& s, int n, int nmem, double G, int* 
       // the trial term: position, mass, rc^2 and rc stashed in xs, ys, zs, vxs, vzs, vys
       const KArrays ta{s.x, s.y, s.z, s.rc}, tr{s.xs, s.ys, s.zs, s.vys};
       const KTerm tt = kick_term(ti, ta, fix_of(s.xs[j]), fix_of(s.ys[j]), fix_of(s.zs[j]),
-                                 s.vxs[j], s.vzs[j], tr, j);
+                                 s.vxs[j], s.vzs[j], tr, j, s.sym);
       ax = __fma_rn(tn.sc, tn.dx, ax);
       ay = __fma_rn(tn.sc, tn.dy, ay);
       az = __fma_rn(tn.sc, tn.dz, az);
@@ -452,9 +461,172 @@ __global__ void __launch_bounds__(KBT, 1024 / KBT) k_batch_kick(BatchDev B, Phys
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_batch_kick_sym: the unordered-pair kick of the batch. A system's bodies
+// form blocks of 32; one warp (one CTA) takes one block pair (X, Y), X <= Y,
+// and evaluates each pair once for both bodies with the arithmetic of the
+// single-system unordered-pair kick (fixed-point differences, r^-3 = y0^3 p
+// with p on the integer pipe, m_j r^-3 and m_i r^-3, six FMAs). Off the
+// diagonal lane l pairs with body (l + s) mod 32 of block Y at step s, and the
+// Y side's sums move one lane down after every step, home after 32 steps; on
+// the diagonal (X == Y) the steps s = 1 .. 16 (the last one for lanes 0..15
+// only) meet every pair of the block once, and a last shuffle brings each
+// body's second sum home. Each tile writes its X side's and Y side's sums
+// (3 x 32 doubles each) as partials; the close phase adds a body's partials
+// in a fixed order (sum_sym_partials). A pair near or inside the changeover
+// radius takes the single-system kernel's exact branch, with the flag (both
+// bodies live) appended once.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int sym_tile_of(int nb, int X, int Y) {
+  return X * nb - (X * (X - 1)) / 2 + (Y - X);  // row-major over X <= Y
+}
+
+__device__ __forceinline__ void batch_sym_rare(const BatchDev& B, int sys, int base, int n, int i,
+                                               int j, double mi, double mj, double& sj,
+                                               double& si) {
+  if (i >= n || j >= n) return;  // padding: massless, far, never flagged
+  const int gi = base + i, gj = base + j;
+  const double r2 = sep2(B.x[gj] - B.x[gi], B.y[gj] - B.y[gi], B.z[gj] - B.z[gi]);
+  const double rci = B.rc[gi], rcj = B.rc[gj];
+  const bool close = r2 < fmax(rci * rci, rcj * rcj);
+  if (r2 == 0.0) {
+    sj = 0.0;
+    si = 0.0;
+  } else if (close) {  // a dead body has m = 0: no force either way
+    const double r = sqrt(r2);
+    const double w = kick_weight(r, fmax(rci, rcj));
+    sj = mj * w / (r2 * r);
+    si = mi * w / (r2 * r);
+  }
+  if (close && B.alive[gi] && B.alive[gj]) {
+    const int pos = atomicAdd(&B.nftrial[sys], 1);
+    if (pos < BPAIR)
+      B.ftrial[(size_t)sys * BPAIR + pos] = ((unsigned)min(i, j) << 16) | (unsigned)max(i, j);
+  }
+}
+
+__global__ void __launch_bounds__(32, 32) k_batch_kick_sym(BatchDev B) {
+  __shared__ nb_u128 sX[32], sY[32], sZ[32];  // block Y
+  __shared__ double sm[32];
+  __shared__ int sh[32];
+  if (B.status[0]) return;  // every lane reads the same word
+  const int2 tile = B.tiles[blockIdx.x];
+  const int sys = tile.x, X = tile.y >> 16, Y = tile.y & 0xffff;
+  const int base = B.off[sys], n = B.off[sys + 1] - base;
+  const int lane = threadIdx.x;
+  const int i = X * 32 + lane;
+  nb_u128 Xi, Yi, Zi;
+  double mi = 0.0;
+  int hi = 0;
+  if (i < n) {
+    Xi = fix_of(B.x[base + i]);
+    Yi = fix_of(B.y[base + i]);
+    Zi = fix_of(B.z[base + i]);
+    mi = B.m[base + i];
+    const double rci = B.rc[base + i];
+    hi = __double2hiint(rci * rci);
+  } else {  // padding far from everything
+    Xi = Yi = Zi = fix_of(1e10);
+  }
+  {
+    const int j = Y * 32 + lane;
+    if (j < n) {
+      sX[lane] = fix_of(B.x[base + j]);
+      sY[lane] = fix_of(B.y[base + j]);
+      sZ[lane] = fix_of(B.z[base + j]);
+      sm[lane] = B.m[base + j];
+      const double rcj = B.rc[base + j];
+      sh[lane] = __double2hiint(rcj * rcj);
+    } else {
+      sX[lane] = sY[lane] = sZ[lane] = fix_of(1e10);
+      sm[lane] = 0.0;
+      sh[lane] = 0;
+    }
+  }
+  __syncwarp();
+  const bool diag = X == Y;
+  const int s0 = diag ? 1 : 0, s1 = diag ? 17 : 32;
+  double ax = 0.0, ay = 0.0, az = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll 1
+  for (int s = s0; s < s1; ++s) {
+    const int q = (lane + s) & 31;
+    const FixDiff fx = fix_diff(sX[q], Xi), fy = fix_diff(sY[q], Yi), fz = fix_diff(sZ[q], Zi);
+    const double r2 = sep2_fix(fx, fy, fz);
+    const double r3 = rinv3_fast(r2);
+    const double mj = sm[q];
+    double sj = mj * r3, si = mi * r3;
+    // on the diagonal, the pair (l, l + 16) is lane l's for l < 16 only
+    const bool valid = !(diag && s == 16 && lane >= 16);
+    if (valid && __double2hiint(r2) <= max(hi, sh[q]) + 1)
+      batch_sym_rare(B, sys, base, n, i, Y * 32 + q, mi, mj, sj, si);
+    if (!valid) sj = si = 0.0;
+    ax = __fma_rn(sj, fx.d, ax);
+    ay = __fma_rn(sj, fy.d, ay);
+    az = __fma_rn(sj, fz.d, az);
+    bx = __fma_rn(-si, fx.d, bx);
+    by = __fma_rn(-si, fy.d, by);
+    bz = __fma_rn(-si, fz.d, bz);
+    if (s != 16 || !diag) {
+      const int src = (lane + 1) & 31;
+      bx = __shfl_sync(0xffffffffu, bx, src);
+      by = __shfl_sync(0xffffffffu, by, src);
+      bz = __shfl_sync(0xffffffffu, bz, src);
+    }
+  }
+  const int nb = (n + 31) >> 5;
+  double* p = B.kp + B.kpo[sys] + (size_t)sym_tile_of(nb, X, Y) * 192 + lane;
+  if (diag) {  // body l's second sum sits in lane l + 16: one tile sum
+    const int src = (lane + 16) & 31;
+    bx = __shfl_sync(0xffffffffu, bx, src);
+    by = __shfl_sync(0xffffffffu, by, src);
+    bz = __shfl_sync(0xffffffffu, bz, src);
+    p[0] = ax + bx;
+    p[32] = ay + by;
+    p[64] = az + bz;
+  } else {
+    p[0] = ax;
+    p[32] = ay;
+    p[64] = az;
+    p[96] = bx;
+    p[128] = by;
+    p[160] = bz;
+  }
+}
+
+// A system's force from the unordered-pair kick's partials, in a fixed order
+// (body i in block X: the X sides of tiles (X, Y) by ascending Y, then the Y
+// sides of tiles (Y', X) by ascending Y'): G times the sum, 0 for dead bodies.
+__device__ void sum_sym_partials(const BatchDev& B, const Phys& P, int sys) {
+  const int base = B.off[sys], n = B.off[sys + 1] - base;
+  const int nb = (n + 31) >> 5;
+  const double* kp = B.kp + B.kpo[sys];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int X = i >> 5, l = i & 31;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int Y = X; Y < nb; ++Y) {
+      const double* p = kp + (size_t)sym_tile_of(nb, X, Y) * 192 + l;
+      ax += p[0];
+      ay += p[32];
+      az += p[64];
+    }
+    for (int Y = 0; Y < X; ++Y) {
+      const double* p = kp + (size_t)sym_tile_of(nb, Y, X) * 192 + 96 + l;
+      ax += p[0];
+      ay += p[32];
+      az += p[64];
+    }
+    const bool live = B.alive[base + i] != 0;
+    B.ax[base + i] = live ? P.G * ax : 0.0;
+    B.ay[base + i] = live ? P.G * ay : 0.0;
+    B.az[base + i] = live ? P.G * az : 0.0;
+  }
+  __syncthreads();
+}
+
 // After the initial kick: the trial flags become the cached flag set F_prev.
-__global__ void k_batch_fsal(BatchDev B) {
+__global__ void k_batch_fsal(BatchDev B, Phys P) {
   const int sys = blockIdx.x;
+  if (B.sym) sum_sym_partials(B, P, sys);
   const int raw = B.nftrial[sys];
   if (raw > BPAIR && threadIdx.x == 0 && atomicCAS(&B.status[0], 0, NB_E_OVERFLOW) == 0)
     B.status[1] = sys;
@@ -573,6 +745,7 @@ __device__ int open_system(const BatchDev& B, const Phys& P, double* red, int* f
 // global memory.
 __device__ void close_system(const BatchDev& B, const Phys& P, const BSmem& s0, int sys, double h,
                              BsTally& bt, BsTally& wbt, SysTally& st) {
+  if (B.sym) sum_sym_partials(B, P, sys);  // the trial force from the kick's partials
   const int base = B.off[sys];
   const int n = B.off[sys + 1] - base;
   const double hh = 0.5 * h;
@@ -904,7 +1077,8 @@ __global__ void __launch_bounds__(kOpenThreads) k_batch_open(BatchDev B, Phys P,
 
 __global__ void __launch_bounds__(256, 2) k_batch_close(BatchDev B, Phys P, double h) {
   extern __shared__ __align__(16) char smem_raw[];
-  const BSmem s = carve_smem(smem_raw, B.nmax, blockDim.x);
+  BSmem s = carve_smem(smem_raw, B.nmax, blockDim.x);
+  s.sym = B.sym;
   __shared__ int s_next;
   if (blockIdx.x == 0 && threadIdx.x == 0) B.queue[0] = 0;  // the next open launch's counter
   BsTally bt{0, 0, 0, 0};
@@ -1056,8 +1230,28 @@ int count_tiles(int nsys, const int* offsets, int rows = kMinTileRows) {
   return (int)t;
 }
 
-size_t batch_layout(const nb_params& p, int nsys, int total, int ntiles, char* base,
-                    BatchDev* out, Snap* snap, double** eout, double** stage) {
+// The unordered-pair kick's tiles (block pairs X <= Y of 32-body blocks) and
+// partials (2 x 3 x 32 doubles per tile) for systems of the given sizes.
+bool batch_sym(const nb_params& p) { return p.kick_symmetric != -1; }
+long long count_sym_tiles(int nsys, const int* offsets) {
+  long long t = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const long long nb = (offsets[s + 1] - offsets[s] + 31) / 32;
+    t += nb * (nb + 1) / 2;
+  }
+  return t;
+}
+int layout_tiles(const nb_params& p, int nsys, const int* offsets) {
+  const long long a = count_tiles(nsys, offsets);
+  const long long b = batch_sym(p) ? count_sym_tiles(nsys, offsets) : 0;
+  return (int)(a > b ? a : b);
+}
+size_t sym_partial_doubles(const nb_params& p, int nsys, const int* offsets) {
+  return batch_sym(p) ? (size_t)count_sym_tiles(nsys, offsets) * 192 : 0;
+}
+
+size_t batch_layout(const nb_params& p, int nsys, int total, int ntiles, size_t kp_doubles,
+                    char* base, BatchDev* out, Snap* snap, double** eout, double** stage) {
   BatchDev d;
   memset(&d, 0, sizeof(d));
   d.nsys = nsys;
@@ -1077,6 +1271,9 @@ size_t batch_layout(const nb_params& p, int nsys, int total, int ntiles, char* b
   d.nftrial = c.take<int>(nsys);
   d.tiles = c.take<int2>(ntiles);
   d.ntiles = ntiles;
+  d.sym = batch_sym(p) ? 1 : 0;
+  d.kp = c.take<double>(kp_doubles);
+  d.kpo = c.take<int>(nsys);
   d.blog = c.take<int>((size_t)nsys * kBatchLogCap * 3);
   d.nblog = c.take<int>(nsys);
   d.El = c.take<double>(nsys);
@@ -1199,7 +1396,13 @@ int arrange(nb_batch* b, int rows, int buckets) {
     for (int k = q; k < nsys; k += buckets) {
       const int sys = b->h_order[k], n = b->h_off[sys + 1] - b->h_off[sys];
       order.push_back(sys);
-      for (int i0 = 0; i0 < n; i0 += rows) tiles.push_back(make_int2(sys, i0));
+      if (b->d.sym) {
+        const int nbk = (n + 31) / 32;
+        for (int X = 0; X < nbk; ++X)
+          for (int Y = X; Y < nbk; ++Y) tiles.push_back(make_int2(sys, (X << 16) | Y));
+      } else {
+        for (int i0 = 0; i0 < n; i0 += rows) tiles.push_back(make_int2(sys, i0));
+      }
     }
   }
   b->bk_sys0[buckets] = (int)order.size();
@@ -1219,7 +1422,9 @@ void launch_kick_t(const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st
   if (ntiles > 0) k_batch_kick<KT, kick_sc<KT>()><<<ntiles, KT, 0, st>>>(d, P);
 }
 void launch_kick_rows(int rows, const BatchDev& d, const Phys& P, int ntiles, cudaStream_t st) {
-  if (rows == 32)
+  if (d.sym) {
+    if (ntiles > 0) k_batch_kick_sym<<<ntiles, 32, 0, st>>>(d);
+  } else if (rows == 32)
     launch_kick_t<32>(d, P, ntiles, st);
   else if (rows == 64)
     launch_kick_t<64>(d, P, ntiles, st);
@@ -1237,7 +1442,7 @@ int enqueue_steps(nb_batch* b, int nsteps, double dt, cudaStream_t st) {
   if (nsteps == 0) {
     NB_BCU(cudaMemsetAsync(b->d.nftrial, 0, sizeof(int) * b->d.nsys, st));
     launch_kick_rows(b->tile_rows, b->d, b->P, b->bk_tile0[b->buckets], st);
-    k_batch_fsal<<<b->d.nsys, 128, 0, st>>>(b->d);
+    k_batch_fsal<<<b->d.nsys, 128, 0, st>>>(b->d, b->P);
     NB_BCU(cudaGetLastError());
     return NB_OK;
   }
@@ -1368,8 +1573,10 @@ size_t nb_batch_workspace_bytes(const nb_params* p, int nsys, const int* offsets
     const int n = offsets[s + 1] - offsets[s];
     if (n < 1 || n > NB_BATCH_MAX_N) return 0;
   }
-  return batch_layout(*p, nsys, offsets[nsys], count_tiles(nsys, offsets), nullptr, nullptr,
-                      nullptr, nullptr, nullptr);
+  if (sym_partial_doubles(*p, nsys, offsets) > (size_t)0x7fffffff) return 0;  // int offsets
+  return batch_layout(*p, nsys, offsets[nsys], layout_tiles(*p, nsys, offsets),
+                      sym_partial_doubles(*p, nsys, offsets), nullptr, nullptr, nullptr, nullptr,
+                      nullptr);
 }
 
 int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offsets,
@@ -1388,8 +1595,9 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
   b->st = (cudaStream_t)stream;
   const int total = offsets[nsys];
   double* stage = nullptr;
-  batch_layout(*p, nsys, total, count_tiles(nsys, offsets), (char*)workspace, &b->d, &b->snap,
-               &b->E, &stage);
+  batch_layout(*p, nsys, total, layout_tiles(*p, nsys, offsets),
+               sym_partial_doubles(*p, nsys, offsets), (char*)workspace, &b->d, &b->snap, &b->E,
+               &stage);
   // host bookkeeping: max N and the largest-first order
   std::vector<int> order(nsys);
   int nmax = 1;
@@ -1415,7 +1623,16 @@ int nb_batch_init(nb_batch** out, const nb_params* p, int nsys, const int* offse
   memcpy(b->h_order, order.data(), sizeof(int) * nsys);
   int rc = NB_OK;
   do {
-    if (cudaMemcpyAsync((void*)b->d.off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice,
+    std::vector<int> kpo(nsys);
+    long long acc = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const long long nbk = (offsets[s + 1] - offsets[s] + 31) / 32;
+      kpo[s] = (int)acc;
+      acc += nbk * (nbk + 1) / 2 * 192;
+    }
+    if ((b->d.sym && cudaMemcpyAsync((void*)b->d.kpo, kpo.data(), sizeof(int) * nsys,
+                                     cudaMemcpyHostToDevice, b->st) != cudaSuccess) ||
+        cudaMemcpyAsync((void*)b->d.off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice,
                         b->st) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
       rc = NB_E_CUDA;
@@ -1575,7 +1792,7 @@ int nb_batch_autotune(nb_batch* b, double dt, int* threads, double* ms_per_step)
   b->threads = bt_;
   b->buckets = bk;
   for (int r : {64, 128}) {
-    if (rc) break;
+    if (rc || b->d.sym) break;  // the unordered-pair kick's tiles are block pairs
     b->tile_rows = r;
     if ((rc = time_graph(b, 25, dt, e0, e1, &ms))) break;
     if (ms < best) { best = ms; br = r; }
@@ -1687,6 +1904,7 @@ int nb_batch_stats(nb_batch* b, nb_stats_t* out) {
   out->bs_derivs = (long long)h[ST_BS_DERIVS];
   out->merges = (long long)h[ST_MERGES];
   out->kepler_iters = (long long)h[ST_KEPLER_ITERS];
+  out->kick_symmetric = b->d.sym;
   return NB_OK;
 }
 

@@ -41,7 +41,10 @@ def batch_of(disks, dt, rcs=None, **kw):
     return nb.NBodyBatch(nb.params(dt_rcrit=dt, **kw), disks, rc=rc)
 
 
-def test_batch_matches_oracle_per_system():
+@pytest.mark.parametrize("sym", [0, -1])
+def test_batch_matches_oracle_per_system(sym):
+    """The unordered-pair kick (32-body block pairs, default) and the row kick
+    (kick_symmetric = -1), each system against its own oracle run."""
     disks = ics.ensemble(n_systems=24, seed=ics.SEED_BASE + 33)
     dt, steps = 3.0, 40
     refs, rcs = [], []
@@ -49,7 +52,7 @@ def test_batch_matches_oracle_per_system():
         s, rc = oracle_run(d, steps, dt)
         refs.append(s)
         rcs.append(rc)
-    b = batch_of(disks, dt, rcs)
+    b = batch_of(disks, dt, rcs, kick_symmetric=sym)
     b.step(steps, dt)
     st = b.state()
     for k, (d, ref) in enumerate(zip(disks, refs)):
@@ -61,7 +64,8 @@ def test_batch_matches_oracle_per_system():
         assert np.allclose(sg["m"], sr["m"], rtol=1e-15, atol=0)
 
 
-def test_batch_with_encounters_and_mergers():
+@pytest.mark.parametrize("sym", [0, -1])
+def test_batch_with_encounters_and_mergers(sym):
     disks = [ics.make_disk(n, 2.0, 0.7, 1.3, 0.01, 0.005, 6.0, seed=900 + n, f_radius=400.0)
              for n in (64, 128, 200)]
     dt, steps = 6.0, 60
@@ -71,7 +75,7 @@ def test_batch_with_encounters_and_mergers():
         refs.append(s)
         rcs.append(rc)
     assert sum(r.stats()["merges"] for r in refs) > 0
-    b = batch_of(disks, dt, rcs)
+    b = batch_of(disks, dt, rcs, kick_symmetric=sym)
     b.step(steps, dt)
     st = b.state()
     assert b.stats()["merges"] == sum(r.stats()["merges"] for r in refs)
@@ -290,17 +294,19 @@ def test_batch_size_extremes_match_oracle():
         assert relv.max() <= 1e-11, (k, d.n, relv.max())
 
 
-def test_batch_schedules_are_bit_identical():
-    """Kick tile rows (32, 64, 128), buckets of independent launch chains
-    (1, 3, 8) and threads per CTA change where and when each system's work
-    runs, never its arithmetic: identical states, encounter lists and
-    counters after 30 steps with encounters and mergers."""
+@pytest.mark.parametrize("sym", [0, -1])
+def test_batch_schedules_are_bit_identical(sym):
+    """Kick tile rows (32, 64, 128; the row kick's), buckets of independent
+    launch chains (1, 3, 8) and threads per CTA change where and when each
+    system's work runs, never its arithmetic: identical states, encounter
+    lists and counters after 30 steps with encounters and mergers, for the
+    unordered-pair kick and the row kick."""
     disks = [ics.make_disk(n, 2.0, 0.7, 1.3, 0.01, 0.005, 6.0, seed=900 + n, f_radius=400.0)
              for n in (64, 128, 200)] + ics.ensemble(n_systems=40, seed=ics.SEED_BASE + 36)
     dt, steps = 6.0, 30
     runs = []
     for rows, buckets, threads in ((128, 1, 128), (32, 3, 256), (64, 8, 64)):
-        b = batch_of(disks, dt)
+        b = batch_of(disks, dt, kick_symmetric=sym)
         b.set_shape(threads, 7)
         b.set_schedule(rows, buckets)
         b.step(steps, dt)
