@@ -188,6 +188,52 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _shape_ok(got, want, min_rows):
+    if len(got) != len(want):
+        return False
+    if any(w >= 0 and g != w for g, w in zip(got[1:], want[1:])):
+        return False
+    if want[0] < 0:
+        return True
+    return got[0] >= want[0] if min_rows else got[0] == want[0]
+
+
+def _dev_buf(torch, name, t, dtype, shape, convert=False, min_rows=False):
+    """t as a buffer the library may read or write through a raw device
+    pointer. It must be a CUDA tensor on the current device: a host pointer,
+    or another device's memory, handed to a kernel faults it. With convert a
+    tensor of another dtype or layout is copied to a contiguous one of dtype;
+    without, it must already be one (outputs are written in place). Its shape
+    must equal shape (-1 matches any extent; min_rows: at least shape[0]
+    rows), else the kernel would run past it. ValueError otherwise."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if not isinstance(t, torch.Tensor) or t.device != dev:
+        raise ValueError("%s must be a CUDA tensor on %s" % (name, dev))
+    if convert:
+        t = t.contiguous().to(dtype)
+    elif t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor" % (name, dtype))
+    if not _shape_ok(tuple(t.shape), tuple(shape), min_rows):
+        raise ValueError("%s must have shape %s%s, got %s" % (
+            name, tuple(shape), " (or more rows)" if min_rows else "", tuple(t.shape)))
+    return t
+
+
+def _host_buf(name, a, dtype, shape):
+    """a as a contiguous host array of dtype and exactly shape (the library
+    reads that many elements through its pointer); ValueError otherwise."""
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if not _shape_ok(a.shape, tuple(shape), False):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), a.shape))
+    return a
+
+
+def _len0(t):
+    """Leading extent of an array or tensor (-1 for a scalar)."""
+    s = tuple(t.shape) if hasattr(t, "shape") else np.shape(t)
+    return int(s[0]) if len(s) else -1
+
+
 class NBodySystem:
     """A planetary system integrated on the GPU by libnb.
 
@@ -201,20 +247,22 @@ class NBodySystem:
         L = lib()
         self.p = p
         on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        n = _len0(m)
+        shapes = {"x": (n, 3), "v": (n, 3), "m": (n,), "R": (n,)}
+        names = ("x", "v", "m", "R")
         if on_dev:
-            args = [t.contiguous().to(torch.float64) for t in (x, v, m, R)]
-            rcv = None if rc is None else rc.contiguous().to(torch.float64)
-            idv = None if ids is None else ids.contiguous().to(torch.int32)
+            args = [_dev_buf(torch, k, t, torch.float64, shapes[k], convert=True)
+                    for k, t in zip(names, (x, v, m, R))]
+            rcv = None if rc is None else _dev_buf(torch, "rc", rc, torch.float64, (n,), True)
+            idv = None if ids is None else _dev_buf(torch, "ids", ids, torch.int32, (n,), True)
             self._keep = (args, rcv, idv)
             ptrs = [_ptr(t) for t in args]
             rcp = None if rcv is None else _ptr(rcv)
             idp = None if idv is None else _ptr(idv)
-            n = args[0].shape[0]
         else:
-            args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, m, R)]
-            n = args[2].shape[0]
-            rcv = None if rc is None else np.ascontiguousarray(rc, dtype=np.float64)
-            idv = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+            args = [_host_buf(k, a, np.float64, shapes[k]) for k, a in zip(names, (x, v, m, R))]
+            rcv = None if rc is None else _host_buf("rc", rc, np.float64, (n,))
+            idv = None if ids is None else _host_buf("ids", ids, np.int32, (n,))
             self._keep = (args, rcv, idv)
             ptrs = [C.c_void_p(a.ctypes.data) for a in args]
             rcp = None if rcv is None else C.c_void_p(rcv.ctypes.data)
@@ -272,7 +320,15 @@ class NBodySystem:
         return dict(x=x[:k], v=v[:k], m=m[:k], R=R[:k], rc=rc[:k], ids=ids[:k])
 
     def state_device(self, out: dict) -> int:
-        """Gather the active bodies into caller CUDA tensors; returns their count."""
+        """Gather the active bodies into caller CUDA tensors; returns their count.
+        Each tensor needs room for all n slots: x, v (n, 3), m, R, rc (n,)
+        float64 and ids (n,) int32, contiguous (more rows are fine)."""
+        torch = _torch()
+        n = self.n
+        for k, dt, sh in (("x", torch.float64, (n, 3)), ("v", torch.float64, (n, 3)),
+                          ("m", torch.float64, (n,)), ("R", torch.float64, (n,)),
+                          ("rc", torch.float64, (n,)), ("ids", torch.int32, (n,))):
+            _dev_buf(torch, k, out[k], dt, sh, min_rows=True)
         k = C.c_int()
         self._check(lib().nb_get_state(self._h, _ptr(out["x"]), _ptr(out["v"]), _ptr(out["m"]),
                                        _ptr(out["R"]), _ptr(out["rc"]), _ptr(out["ids"]),
@@ -291,7 +347,7 @@ class NBodySystem:
         return a, pairs[:cnt.value]
 
     def set_fsal(self, a, pairs):
-        a = np.ascontiguousarray(a, dtype=np.float64)
+        a = _host_buf("a", a, np.float64, (self.n, 3))
         pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
         self._check(lib().nb_set_fsal(self._h, C.c_void_p(a.ctypes.data),
                                       C.c_void_p(pairs.ctypes.data), pairs.shape[0], 0))
@@ -301,13 +357,25 @@ class NBodySystem:
         evaluation; a is the cached force [n][3], pairs the cached flags."""
         import torch
         on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        n = self.n
+        f64 = ((n, 3), (n, 3), (n,), (n,), (n,), (n, 3))
+        names = ("x", "v", "m", "R", "rc", "a")
         if on_dev:
-            ptr = _ptr
+            x, v, m, R, rc, a = (_dev_buf(torch, k, t, torch.float64, sh, convert=True)
+                                 for k, t, sh in zip(names, (x, v, m, R, rc, a), f64))
+            ids = None if ids is None else _dev_buf(torch, "ids", ids, torch.int32, (n,), True)
+            pairs = _dev_buf(torch, "pairs", pairs, torch.int32, (-1, 2), True)
             npairs = int(pairs.shape[0])
+            ptr = _ptr
         else:
+            x, v, m, R, rc, a = (_host_buf(k, t, np.float64, sh)
+                                 for k, t, sh in zip(names, (x, v, m, R, rc, a), f64))
+            ids = None if ids is None else _host_buf("ids", ids, np.int32, (n,))
+            pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+            npairs = int(pairs.shape[0])
+
             def ptr(t):
                 return C.c_void_p(t.ctypes.data)
-            npairs = int(np.asarray(pairs).reshape(-1, 2).shape[0])
         idp = None if ids is None else ptr(ids)
         self._check(lib().nb_set_state(self._h, ptr(x), ptr(v), ptr(m), ptr(R), ptr(rc), idp,
                                        ptr(a), ptr(pairs) if npairs else None, npairs,
@@ -342,8 +410,10 @@ def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=
     status); with rows = (row0, row1) only those target rows (nb_kick_rows)."""
     torch = _torch()
     L = lib()
-    n = x.shape[0]
-    x = x.contiguous()
+    n = _len0(x)
+    x = _dev_buf(torch, "x", x, torch.float64, (n, 3), convert=True)
+    m = _dev_buf(torch, "m", m, torch.float64, (n,), convert=True)
+    rc = _dev_buf(torch, "rc", rc, torch.float64, (n,), convert=True)
     r0, r1 = (0, n) if rows is None else rows
     a = torch.empty((max(r1 - r0, 1), 3), dtype=torch.float64, device="cuda")
     cap = 16 * n + 64 if cap is None else cap
@@ -352,7 +422,7 @@ def kick(x, m, rc, G=2.959122082855911e-4, precision=NB_PREC_FP64, split=0, cap=
     scratch = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
     sp = scratch.data_ptr() + ((-scratch.data_ptr()) % 256)
     cnt = C.c_int()
-    code = L.nb_kick_rows(n, r0, r1, _ptr(x), _ptr(m.contiguous()), _ptr(rc.contiguous()), G,
+    code = L.nb_kick_rows(n, r0, r1, _ptr(x), _ptr(m), _ptr(rc), G,
                           precision, split, _ptr(a), _ptr(pairs), cap, C.byref(cnt),
                           C.c_void_p(sp), nb, _stream(torch))
     return a[:max(r1 - r0, 0)], pairs[:min(cnt.value, cap)], code
@@ -378,7 +448,10 @@ class NBodyBatch:
         cat = lambda k: np.ascontiguousarray(np.concatenate([np.asarray(getattr(d, k), dtype=np.float64)  # noqa: E731
                                                              for d in systems]))
         self._x, self._v, self._m, self._R = cat("x"), cat("v"), cat("m"), cat("R")
-        self._rc = None if rc is None else np.ascontiguousarray(rc, dtype=np.float64)
+        tot = int(self.offsets[-1])
+        for k, sh in (("x", (tot, 3)), ("v", (tot, 3)), ("m", (tot,)), ("R", (tot,))):
+            _host_buf(k, getattr(self, "_" + k), np.float64, sh)
+        self._rc = None if rc is None else _host_buf("rc", rc, np.float64, (tot,))
         nbytes = L.nb_batch_workspace_bytes(C.byref(p), self.nsys,
                                             C.c_void_p(self.offsets.ctypes.data))
         if nbytes == 0:
@@ -519,9 +592,11 @@ def energy_grad(x, v, m, alive=None, G=2.959122082855911e-4, m0=1.0):
     CUDA tensors x, v (n, 3), m (n,), alive (n,) int32 or None (nb_energy_grad).
     Returns (dE/dx, dE/dv, dE/dm) as new tensors; zero for absorbed bodies."""
     torch = _torch()
-    n = int(m.shape[0])
-    x, v, m = (t.contiguous().to(torch.float64) for t in (x, v, m))
-    al = None if alive is None else alive.contiguous().to(torch.int32)
+    n = _len0(m)
+    x = _dev_buf(torch, "x", x, torch.float64, (n, 3), convert=True)
+    v = _dev_buf(torch, "v", v, torch.float64, (n, 3), convert=True)
+    m = _dev_buf(torch, "m", m, torch.float64, (n,), convert=True)
+    al = None if alive is None else _dev_buf(torch, "alive", alive, torch.int32, (n,), True)
     gx = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     gv = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     gm = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -537,8 +612,12 @@ def energy_grad(x, v, m, alive=None, G=2.959122082855911e-4, m0=1.0):
 
 
 def kepler_drift(x, v, mu, dt, max_iter=30):
-    """Kepler-drift CUDA tensors x, v (n, 3) in place; returns the status code."""
+    """Kepler-drift CUDA tensors x, v (n, 3) in place (contiguous float64);
+    returns the status code."""
     torch = _torch()
+    n = _len0(x)
+    _dev_buf(torch, "x", x, torch.float64, (n, 3))
+    _dev_buf(torch, "v", v, torch.float64, (n, 3))
     scratch = torch.zeros(64, dtype=torch.uint8, device="cuda")
     return lib().nb_kepler_drift(x.shape[0], mu, _ptr(x), _ptr(v), dt, max_iter,
                                  _ptr(scratch), _stream(torch))
@@ -548,7 +627,7 @@ def math_eval(fn: int, x):
     """Evaluate device arithmetic helper fn (NB_MATH_*) element-wise on a
     float64 CUDA tensor (nb_math_eval); returns a new tensor."""
     torch = _torch()
-    x = x.contiguous()
+    x = _dev_buf(torch, "x", x, torch.float64, tuple(-1 for _ in x.shape))
     out = torch.empty_like(x)
     code = lib().nb_math_eval(fn, x.numel(), _ptr(x), _ptr(out), _stream(torch))
     if code != NB_OK:
@@ -561,6 +640,9 @@ def ratio_le(a, b, tol):
     float64 CUDA tensors a, b, tol of one length (NB_MATH_RATIO_LE); returns
     a float64 tensor of 1.0 / 0.0."""
     torch = _torch()
+    k = _len0(a)
+    a, b, tol = (_dev_buf(torch, nm, t, torch.float64, (k,), convert=True)
+                 for nm, t in (("a", a), ("b", b), ("tol", tol)))
     tri = torch.stack([a, b, tol], dim=1).contiguous()
     out = torch.empty(tri.shape[0], dtype=torch.float64, device=tri.device)
     code = lib().nb_math_eval(NB_MATH_RATIO_LE, tri.shape[0], _ptr(tri), _ptr(out),
@@ -597,14 +679,17 @@ class NBodyAdjoint:
         L = lib()
         self.p = p
         self.on_dev = isinstance(x, torch.Tensor) and x.is_cuda
+        n = _len0(m)
+        names = ("x", "v", "m", "R", "rc")
+        shapes = ((n, 3), (n, 3), (n,), (n,), (n,))
         if self.on_dev:
-            args = [t.contiguous().to(torch.float64) for t in (x, v, m, R, rc)]
+            args = [_dev_buf(torch, k, t, torch.float64, sh, convert=True)
+                    for k, t, sh in zip(names, (x, v, m, R, rc), shapes)]
             ptrs = [_ptr(t) for t in args]
-            n = args[0].shape[0]
         else:
-            args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, m, R, rc)]
+            args = [_host_buf(k, a, np.float64, sh)
+                    for k, a, sh in zip(names, (x, v, m, R, rc), shapes)]
             ptrs = [C.c_void_p(a.ctypes.data) for a in args]
-            n = args[2].shape[0]
         self._keep = args
         self.n = int(n)
         self.nsteps = int(nsteps)
@@ -657,14 +742,16 @@ class NBodyAdjoint:
         n = self.n
         if self.on_dev:
             import torch
-            g = [t.contiguous().to(torch.float64) for t in (gx, gv, gm)]
+            g = [_dev_buf(torch, k, t, torch.float64, sh, convert=True)
+                 for k, t, sh in (("gx", gx, (n, 3)), ("gv", gv, (n, 3)), ("gm", gm, (n,)))]
             out = (torch.empty((n, 3), dtype=torch.float64, device="cuda"),
                    torch.empty((n, 3), dtype=torch.float64, device="cuda"),
                    torch.empty(n, dtype=torch.float64, device="cuda"))
             gp = [_ptr(t) for t in g]
             op = [_ptr(t) for t in out]
         else:
-            g = [np.ascontiguousarray(a, dtype=np.float64) for a in (gx, gv, gm)]
+            g = [_host_buf(k, a, np.float64, sh)
+                 for k, a, sh in (("gx", gx, (n, 3)), ("gv", gv, (n, 3)), ("gm", gm, (n,)))]
             out = (np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n))
             gp = [C.c_void_p(a.ctypes.data) for a in g]
             op = [C.c_void_p(a.ctypes.data) for a in out]

@@ -59,3 +59,25 @@ def test_host_side_rejections_need_no_device(lib):
                               0, None, 0) == nb.NB_E_WORKSPACE
     assert lib.nb_step(None, 1, 6.0) == nb.NB_E_INVALID
     assert nb.status_string(nb.NB_E_OVERFLOW) == "buffer overflow"
+
+
+def test_binding_shape_checks_on_host_arrays():
+    """The binding's buffer checks: exact shapes, -1 as any extent, a row
+    minimum for outputs, and host arrays converted or refused (ValueError)."""
+    import numpy as np
+    from paper_2604_09184_b300 import nb
+    assert nb._shape_ok((5, 3), (5, 3), False)
+    assert not nb._shape_ok((4, 3), (5, 3), False)
+    assert not nb._shape_ok((5,), (5, 3), False)
+    assert not nb._shape_ok((15,), (5,), False)
+    assert not nb._shape_ok((5, 2), (5, 3), False)
+    assert nb._shape_ok((7, 3), (5, 3), True) and not nb._shape_ok((4, 3), (5, 3), True)
+    assert nb._shape_ok((0, 2), (-1, 2), False) and nb._shape_ok((9, 2), (-1, 2), False)
+    assert not nb._shape_ok((9, 3), (-1, 2), False)
+    a = nb._host_buf("x", [[1, 2, 3], [4, 5, 6]], np.float64, (2, 3))
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    with pytest.raises(ValueError):
+        nb._host_buf("x", np.ones(6), np.float64, (2, 3))
+    with pytest.raises(ValueError):
+        nb._host_buf("m", np.ones(3), np.float64, (4,))
+    assert nb._len0(np.ones((4, 3))) == 4 and nb._len0(np.float64(1.0)) == -1
