@@ -346,6 +346,20 @@ def run_ours(args):
                                     "sm__issue_active (% of peak sustained active) and "
                                     "sm__inst_executed_pipe_fp64.sum, profiles/"
                                     + prof + "_pipes.txt")
+    # the drift's HBM figures (ncu at this N): algorithmic bytes over its time
+    dr = read_traffic(os.path.join(ROOT, "profiles", "drift_mmsn_64k.txt"))
+    if dr.get("n") == str(n):
+        t_us = float(dr["gpu_time_us"])
+        hbm = load_peaks().get("hbm_gbs")
+        roofline["drift"] = {
+            "kernel": dr["kernel"], "bound": "fp64", "gpu_time_us": t_us,
+            "algorithmic_bytes": int(dr["algorithmic_bytes"]),
+            "achieved_gbs": int(dr["algorithmic_bytes"]) / (t_us * 1e3),
+            "hbm_frac": int(dr["algorithmic_bytes"]) / (t_us * 1e3) / hbm if hbm else None,
+            "dram_bytes": int(dr["dram_bytes_read"]) + int(dr["dram_bytes_write"]),
+            "fp64_pipe_frac": float(dr["fp64_pipe_pct"]) / 100,
+            "source": "ncu, 3 launches, profiles/drift_mmsn_64k.txt (HBM peak: "
+                      "MEASURED_PEAKS.json hbm_gbs)"}
     if args.precision == "ds":
         ds = ds_pipes(n, "k_kick_ds_sym" if sym else "k_kick_ds")
         if ds:
