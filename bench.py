@@ -27,7 +27,7 @@ holds the whole state and evaluates the O(N^2) kick for its own block of
 target rows, and two NCCL all-gathers per step join the blocks (the row-
 sharded step, nb_set_shard). The work is fixed as N grows (strong scaling);
 the value is the job's pair interactions per second of the slowest rank's
-time. Only the headline step is timed at N > 1.
+time. At N > 1 the headline step and its end-to-end form are timed.
 """
 from __future__ import annotations
 
@@ -275,8 +275,7 @@ def run_ours(args):
         # one system on all ranks: the kick's target rows split across them
         from paper_2604_09184_b300 import shard
         sharding = shard.Shard(sysm, rank, world)
-        for k in ("no_e2e", "no_cpu", "no_mixed", "no_batch", "no_adjoint", "no_options",
-                  "no_accuracy"):
+        for k in ("no_cpu", "no_mixed", "no_batch", "no_adjoint", "no_options", "no_accuracy"):
             setattr(args, k, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 0)):
@@ -309,7 +308,10 @@ def run_ours(args):
     kick_ms = tm["kick_ms"] / max(tm["kick_launches"], 1)
     st = sysm.stats()
 
-    achieved = FLOP_PER_PAIR * pps / (kick_ms * 1e-3)
+    # ordered pairs one launch of this rank's kick evaluates: its target rows
+    # against all bodies (every row on one GPU)
+    kick_pairs = pps if sharding is None else float(sharding.row1 - sharding.row0) * (n - 1)
+    achieved = FLOP_PER_PAIR * kick_pairs / (kick_ms * 1e-3)
     sym = bool(st.get("kick_symmetric", 0))
     ipp = FP64_INSTR_PER_PAIR_SYM if sym else FP64_INSTR_PER_PAIR
     roofline = {
@@ -318,7 +320,7 @@ def run_ours(args):
         "kernel": "k_kick_sym" if sym else "k_kick<FP64>", "kick_ms": kick_ms,
         "flop_per_pair": FLOP_PER_PAIR,
         "peak_source": "FP64 DFMA loop measured in this run (nb_measure_peaks)",
-        "fp64_pipe_frac_by_count": ipp * pps / (kick_ms * 1e-3) / (f64_peak / 2),
+        "fp64_pipe_frac_by_count": ipp * kick_pairs / (kick_ms * 1e-3) / (f64_peak / 2),
         "fp64_instr_per_pair_design": ipp,
         "fp32_peak_tflops": f32_peak / 1e12,
         "note": "achieved counts 20 flop per ordered pair (the direct-summation convention); "
@@ -331,13 +333,14 @@ def run_ours(args):
     }
     prof = "kick_sym_mmsn_64k" if sym else "kick_fp64_mmsn_64k"
     tr = read_traffic(os.path.join(ROOT, "profiles", prof + "_dram.txt"))
-    if tr.get("n") == str(n):
+    # the profiles describe a whole-system launch; a rank's row block is not one
+    if tr.get("n") == str(n) and sharding is None:
         roofline["traffic"] = float(tr["bytes_per_launch"])
         roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 1 "
                                       "launch, profiles/%s_dram.txt" % prof)
     # pipe shares measured by ncu (one launch of each kick at this N), not asserted
     pf = read_traffic(os.path.join(ROOT, "profiles", prof + "_pipes.txt"))
-    if pf.get("n") == str(n):
+    if pf.get("n") == str(n) and sharding is None:
         roofline["fp64_pipe_frac"] = float(pf["fp64_pipe_pct"]) / 100
         roofline["alu_pipe_frac"] = float(pf["alu_pipe_pct"]) / 100
         roofline["issue_active_frac"] = float(pf["issue_active_pct"]) / 100
@@ -423,7 +426,7 @@ def run_ours(args):
     # from pinned host memory, step, read the state back to pinned host memory
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(nb, torch, sysm, disk, args.steps, pps)
+        e2e = run_e2e(nb, torch, sysm, disk, args.steps, pps, world)
 
     # accuracy of the reduced-precision kicks (untimed; last, so that the oracle
     # thread it starts overlaps no timed leg)
@@ -905,7 +908,10 @@ def nb_rc_initial(nb, disk):
     return rc
 
 
-def run_e2e(nb, torch, sysm, disk, steps, pps):
+def run_e2e(nb, torch, sysm, disk, steps, pps, world=1):
+    """The headline step end to end through the C ABI with host buffers. On
+    a row-sharded system every rank loads the same state and steps it (the
+    step's all-gathers join the ranks); the slowest rank's time counts."""
     n = disk.n
     st = sysm.state()
     a, pairs = sysm.fsal()
@@ -924,26 +930,30 @@ def run_e2e(nb, torch, sysm, disk, steps, pps):
     if sysm.n != n:
         return None
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
+    err = None
     for _ in range(steps):
         rcode = L.nb_set_state(sysm._h, C.c_void_p(hx.data_ptr()), C.c_void_p(hv.data_ptr()),
                                C.c_void_p(hm.data_ptr()), C.c_void_p(hR.data_ptr()),
                                C.c_void_p(hrc.data_ptr()), C.c_void_p(hid.data_ptr()),
                                C.c_void_p(ha.data_ptr()), C.c_void_p(hp.data_ptr()),
                                int(hp.shape[0]), 0)
+        if not rcode:
+            rcode = L.nb_step(sysm._h, 1, disk.dt)
+        if not rcode:
+            rcode = L.nb_get_state(sysm._h, C.c_void_p(ox.data_ptr()), C.c_void_p(ov.data_ptr()),
+                                   C.c_void_p(om.data_ptr()), C.c_void_p(oR.data_ptr()),
+                                   C.c_void_p(orc.data_ptr()), C.c_void_p(oid.data_ptr()),
+                                   C.byref(k), 0)
         if rcode:
-            return {"error": nb.status_string(rcode)}
-        rcode = L.nb_step(sysm._h, 1, disk.dt)
-        if rcode:
-            return {"error": nb.status_string(rcode)}
-        rcode = L.nb_get_state(sysm._h, C.c_void_p(ox.data_ptr()), C.c_void_p(ov.data_ptr()),
-                               C.c_void_p(om.data_ptr()), C.c_void_p(oR.data_ptr()),
-                               C.c_void_p(orc.data_ptr()), C.c_void_p(oid.data_ptr()),
-                               C.byref(k), 0)
-        if rcode:
-            return {"error": nb.status_string(rcode)}
+            err = nb.status_string(rcode)
+            break
     torch.cuda.synchronize()
-    t = (time.perf_counter() - t0) / max(steps, 1)
+    t = max_over_ranks((time.perf_counter() - t0) / max(steps, 1), world, "cuda")
+    if err:
+        return {"error": err}
     return {"value": pps / t, "unit": UNIT, "ms_per_step": t * 1e3,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "api": "nb_set_state (pinned host) + nb_step(1) + nb_get_state (pinned host)"}
