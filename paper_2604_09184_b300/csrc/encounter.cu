@@ -4,8 +4,10 @@
 // "Detailing the outcomes of collisions").
 //
 // k_encounter (one CTA): E = F_prev U F_trial as sorted unique (i, j) keys,
-//   appended to the encounter log; connected components of E by union-find;
-//   member slots ordered by (smallest member, body).
+//   appended to the encounter log; connected components of E (each body
+//   labelled with its component's smallest body); member slots ordered by
+//   (smallest member, body). Sorts, compactions and labels run over the
+//   whole CTA, in shared memory when E is small.
 // k_bs (one CTA per group, grid-stride): Gragg modified midpoint with
 //   n_k = 2k substeps and Neville extrapolation in the substep squared,
 //   restarting from the state saved after C(h/2). Substep halving on
@@ -72,12 +74,98 @@ __device__ __forceinline__ int next_pow2(int v) {
   return p;
 }
 
-__device__ __forceinline__ int uf_find(int* uf, int k) {
-  while (uf[k] != k) {
-    uf[k] = uf[uf[k]];
-    k = uf[k];
+// Exclusive prefix sum of one count per thread over the CTA (ENT threads);
+// *total receives the sum. ws: ENT/32 ints of shared scratch. Every thread
+// must call it (it holds barriers).
+static_assert(ENT == 1024, "the scan below takes 32 warps");
+__device__ __forceinline__ int block_excl_scan(int v, int* ws, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  return k;
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  const int excl = x - v + (w > 0 ? ws[w - 1] : 0);
+  *total = ws[31];
+  __syncthreads();  // ws free for the next call
+  return excl;
+}
+
+// In-place unique of the sorted a[0, n) by the whole CTA, in chunks of ENT:
+// returns the count. A chunk reads its elements and predecessors before its
+// scan's barriers and writes after them, to positions below its own start
+// or within it; the last original value of a chunk is carried in *carry.
+__device__ int block_unique_sorted(unsigned long long* a, int n, int* ws,
+                                   unsigned long long* carry) {
+  int out = 0;
+  for (int base = 0; base < n; base += ENT) {
+    const int k = base + threadIdx.x;
+    unsigned long long v = 0ull, prev = 0ull;
+    if (k < n) {
+      v = a[k];
+      prev = threadIdx.x > 0 ? a[k - 1] : (base > 0 ? *carry : 0ull);
+    }
+    const int f = (k < n && (k == 0 || v != prev)) ? 1 : 0;
+    int tot;
+    const int pos = block_excl_scan(f, ws, &tot);
+    if (threadIdx.x == ENT - 1) *carry = v;
+    if (f) a[out + pos] = v;
+    out += tot;
+    __syncthreads();
+  }
+  return out;
+}
+
+// Connected components of the nb bodies joined by the nE edges (local
+// indices packed as a << 32 | b): label[k] becomes the smallest index of
+// k's component, the root the serial union-find by smaller index reaches.
+// Labels only decrease and stay indices of the same component, so passes of
+// min-propagation over the edges and pointer jumping reach that fixed point
+// whatever order the atomics take; a pass with a change lowers the sum of
+// the labels, which bounds the passes. s_flag: one shared int.
+__device__ void block_components(int* label, int nb, const unsigned long long* edges, int nE,
+                                 int* s_flag, Ctrl* C) {
+  for (int k = threadIdx.x; k < nb; k += ENT) label[k] = k;
+  const long long cap = (long long)nb * nb / 2 + 2;
+  for (long long pass = 0;; ++pass) {
+    __syncthreads();  // the previous pass's reads of *s_flag are done
+    if (threadIdx.x == 0) *s_flag = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nE; e += ENT) {
+      const int a = (int)(edges[e] >> 32), b = (int)(edges[e] & 0xffffffffu);
+      const int la = label[a], lb = label[b];
+      if (la != lb) {
+        const int m = min(la, lb);
+        atomicMin(&label[a], m);
+        atomicMin(&label[b], m);
+        *s_flag = 1;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += ENT) {
+      const int l = label[k], ll = label[l];
+      if (ll < l) atomicMin(&label[k], ll);
+    }
+    __syncthreads();
+    if (*s_flag == 0) break;
+    if (pass > cap) {  // cannot happen (see above); reported rather than looped on
+      if (threadIdx.x == 0) set_status(C, NB_E_INVALID, 60);
+      break;
+    }
+  }
 }
 
 __device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int n,
@@ -93,8 +181,18 @@ __device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int 
   return lo;
 }
 
+// Encounter sets of at most kEncSmall keys (F_prev plus F_trial, the common
+// case) keep every array in shared memory: pair keys and group keys
+// (next_pow2(nb) <= 2 kEncSmall), body keys (next_pow2(2 nE) <= 2 kEncSmall),
+// labels and edges; larger sets use the workspace's key regions.
+constexpr int kEncSmall = 512;
+
 __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
-  __shared__ int s_stop, s_nT, s_nP, s_nE, s_nb, s_step;
+  __shared__ int s_stop, s_nT, s_nP, s_step, s_flag;
+  __shared__ int ws[ENT / 32];
+  __shared__ unsigned long long s_carry;
+  __shared__ unsigned long long sKA[2 * kEncSmall], sKB[2 * kEncSmall], sEdge[kEncSmall];
+  __shared__ int sLab[2 * kEncSmall];
   Ctrl* C = d.ctrl;
   if (threadIdx.x == 0) {
     s_stop = C->status;
@@ -111,36 +209,33 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
     if (NB_GUARD(C, q < d.member_cap && b >= 0 && b < d.n, 50)) d.member_slot[b] = -1;
   }
   const int nT = s_nT, nP = s_nP, nK = nT + nP;
-  // region A holds <= next_pow2(2 pair_cap) pair keys and later <= 4 pair_cap
-  // group keys; region B holds <= 4 pair_cap body keys (pair_cap is a power of 2)
-  unsigned long long* kA = d.keys;
-  unsigned long long* kB = d.keys + 4 * (size_t)d.pair_cap;
+  const bool small = nK <= kEncSmall;
+  // global regions: A holds <= next_pow2(2 pair_cap) pair keys, then the
+  // edges at 2 pair_cap, later <= 4 pair_cap group keys; B holds <= 4
+  // pair_cap body keys (pair_cap is a power of 2)
+  unsigned long long* kA = small ? sKA : d.keys;
+  unsigned long long* kB = small ? sKB : d.keys + 4 * (size_t)d.pair_cap;
+  unsigned long long* edges = small ? sEdge : d.keys + 2 * (size_t)d.pair_cap;
+  int* label = small ? sLab : d.uf;
   const int P2 = next_pow2(nK > 0 ? nK : 1);
   for (int k = threadIdx.x; k < P2; k += ENT) {
     unsigned long long key = ~0ull;
     if (k < nP) {
       const int2 p = d.fprev[k];
-      if (!NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 51)) continue;
-      key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
+      if (NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 51))
+        key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
     } else if (k < nK) {
       const int2 p = d.ftrial[k - nP];
-      if (!NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 52)) continue;
-      key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
+      if (NB_GUARD(C, p.x >= 0 && p.x < p.y && p.y < d.n, 52))
+        key = ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.y;
     }
     kA[k] = key;
   }
   __syncthreads();
   bitonic_sort(kA, P2);
-  if (threadIdx.x == 0) {
-    int ne = 0;
-    for (int k = 0; k < nK; ++k) {
-      if (ne > 0 && kA[k] == kA[ne - 1]) continue;
-      kA[ne++] = kA[k];
-    }
-    s_nE = ne;
-  }
-  __syncthreads();
-  const int nE = s_nE;
+  // unique pairs; a pair refused by a guard sorts last as ~0 and is cut
+  int nE = block_unique_sorted(kA, nK, ws, &s_carry);
+  if (nE > 0 && kA[nE - 1] == ~0ull) --nE;
   // encounter log: (step, id_i, id_j)
   const int base = C->n_log;
   for (int k = threadIdx.x; k < nE; k += ENT) {
@@ -181,33 +276,19 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
   }
   __syncthreads();
   bitonic_sort(kB, P2b);
-  if (threadIdx.x == 0) {
-    int nb = 0;
-    for (int k = 0; k < 2 * nE; ++k) {
-      if (nb > 0 && kB[k] == kB[nb - 1]) continue;
-      kB[nb++] = kB[k];
-    }
-    s_nb = nb;
-    for (int k = 0; k < nb; ++k) d.uf[k] = k;
-    // union by the smaller local index (= smaller body index)
-    for (int k = 0; k < nE; ++k) {
-      const int a = lower_bound_u64(kB, nb, kA[k] >> 32);
-      const int b = lower_bound_u64(kB, nb, kA[k] & 0xffffffffu);
-      const int ra = uf_find(d.uf, a), rb = uf_find(d.uf, b);
-      if (ra < rb)
-        d.uf[rb] = ra;
-      else if (rb < ra)
-        d.uf[ra] = rb;
-    }
-    for (int k = 0; k < nb; ++k) d.uf[k] = uf_find(d.uf, k);  // flatten
+  const int nb = block_unique_sorted(kB, 2 * nE, ws, &s_carry);
+  // the pairs as edges between local body indices, then the components
+  for (int k = threadIdx.x; k < nE; k += ENT) {
+    const int a = lower_bound_u64(kB, nb, kA[k] >> 32);
+    const int b = lower_bound_u64(kB, nb, kA[k] & 0xffffffffu);
+    edges[k] = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
   }
-  __syncthreads();
-  const int nb = s_nb;
+  block_components(label, nb, edges, nE, &s_flag, C);
   // group keys (root body, body) reuse region A
   const int P2g = next_pow2(nb);
   for (int k = threadIdx.x; k < P2g; k += ENT) {
     unsigned long long v = ~0ull;
-    if (k < nb) v = (kB[d.uf[k]] << 32) | kB[k];
+    if (k < nb) v = (kB[label[k]] << 32) | kB[k];
     kA[k] = v;
   }
   __syncthreads();
@@ -218,10 +299,17 @@ __global__ void __launch_bounds__(ENT) k_encounter(Dev d) {
     d.grp_mem[k] = body;
     d.member_slot[body] = k;
   }
+  // group offsets: where the root changes
+  int g = 0;
+  for (int b0 = 0; b0 < nb; b0 += ENT) {
+    const int k = b0 + threadIdx.x;
+    const int f = (k < nb && (k == 0 || (kA[k] >> 32) != (kA[k - 1] >> 32))) ? 1 : 0;
+    int tot;
+    const int pos = block_excl_scan(f, ws, &tot);
+    if (f) d.grp_off[g + pos] = k;
+    g += tot;
+  }
   if (threadIdx.x == 0) {
-    int g = 0;
-    for (int k = 0; k < nb; ++k)
-      if (k == 0 || (kA[k] >> 32) != (kA[k - 1] >> 32)) d.grp_off[g++] = k;
     d.grp_off[g] = nb;
     C->n_groups = g;
     C->n_members = nb;
