@@ -316,8 +316,9 @@ int nb_batch_step(nb_batch* b, int nsteps, double dt);
  * the others' kicks). nb_batch_autotune() times threads {64, 128, 256} x
  * buckets {4, 8, 16} at 32-row tiles and 25-step graphs, then tile rows 64
  * and 128 (the row kick only: the unordered-pair kick's tiles are 32-body
- * block pairs), then chunks of 10 and 50 steps, on graph replays of a copy of the
- * state (restored afterwards), and keeps the fastest;
+ * block pairs), then chunks of 10, 25 and 50 steps (each timed afresh over
+ * the same 50 steps, best of three interleaved rounds), on graph replays of a copy of the state (restored
+ * afterwards), and keeps the fastest; *ms_per_step is the chosen chunk's time;
  * nb_batch_get_shape() reports what is in use. None of these changes a
  * result: every system's arithmetic is the same in any shape. */
 int nb_batch_set_shape(nb_batch* b, int threads, int chunk);
