@@ -278,13 +278,15 @@ def test_unordered_pair_kick_edge_cases():
 def test_unordered_pair_kick_agrees_with_row_kick_and_is_deterministic():
     """16384 bodies (the automatic choice takes the unordered-pair kick):
     the same flags as the row kick, forces within the kick bar of each other,
-    and the same bits on a second evaluation."""
+    and the same bits on a second evaluation. The flagged pairs are appended
+    by warp-aggregated atomics, so their order in the buffer is not unique
+    (the step sorts them); the pair sets are compared."""
     d = ics.workload("mmsn_16k_js", n=16384)
     rc = oracle_rc(d)
     a0, p0 = sym_force(d.x, d.m, rc, sym=0)
     a1, p1 = sym_force(d.x, d.m, rc, sym=1)
     ar, pr = sym_force(d.x, d.m, rc, sym=-1)
-    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)  # automatic = on at this n
+    assert np.array_equal(a0, a1) and pairset(p0) == pairset(p1)  # automatic = on at this n
     assert pairset(p1) == pairset(pr)
     err = np.linalg.norm(a1 - ar, axis=1) / np.linalg.norm(ar, axis=1)
     assert err.max() < 2e-13, err.max()
