@@ -232,7 +232,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "n_bodies": disk.n,
-                                        "dt_days": disk.dt, "l2": "host run"},
+                                        "dt_days": disk.dt, "precision": "fp64",
+                                        "parallelism": "%d host threads (OpenMP)" % threads,
+                                        "l2": "host run"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d full oracle steps of %s (N=%d)" % (args.steps,
                                                                            args.workload, disk.n)},
