@@ -430,45 +430,64 @@ struct GatherOut {
   int* count;
 };
 
-__global__ void __launch_bounds__(1024) k_gather(Dev d, GatherOut o) {
-  __shared__ int warp_tot[32];
-  __shared__ int s_base;
-  if (threadIdx.x == 0) s_base = 0;
+// The live bodies in slot order (ascending id), compacted: blocks of GNT
+// slots count their live bodies (k_gather_count), then each block writes its
+// own at the sum of the counts before it (k_gather), so the order is that of
+// a sequential scan whatever the grid.
+constexpr int GNT = 1024;
+__global__ void __launch_bounds__(GNT) k_gather_count(Dev d, int* bcnt) {
+  __shared__ int warp_tot[GNT / 32];
+  const int i = blockIdx.x * GNT + threadIdx.x;
+  const int f = (i < d.n && d.alive[i]) ? 1 : 0;
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(bal);
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < d.n; c0 += 1024) {
-    const int i = c0 + threadIdx.x;
-    const int f = (i < d.n && d.alive[i]) ? 1 : 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    const int wpre = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) warp_tot[wid] = __popc(bal);
-    __syncthreads();
-    int off = 0;
-    for (int w = 0; w < wid; ++w) off += warp_tot[w];
-    const int pos = s_base + off + wpre;
-    if (f) {
-      if (o.x3) { o.x3[3 * pos] = d.x[i]; o.x3[3 * pos + 1] = d.y[i]; o.x3[3 * pos + 2] = d.z[i]; }
-      if (o.v3) { o.v3[3 * pos] = d.vx[i]; o.v3[3 * pos + 1] = d.vy[i]; o.v3[3 * pos + 2] = d.vz[i]; }
-      if (o.m) o.m[pos] = d.m[i];
-      if (o.R) o.R[pos] = d.R[i];
-      if (o.rc) o.rc[pos] = d.rc[i];
-      if (o.ids) o.ids[pos] = d.id[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int w = 0; w < 32; ++w) tot += warp_tot[w];
-      s_base += tot;
-    }
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = __reduce_add_sync(0xffffffffu, warp_tot[threadIdx.x]);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0 && o.count) *o.count = s_base;
 }
 
+__global__ void __launch_bounds__(GNT) k_gather(Dev d, GatherOut o, const int* bcnt) {
+  __shared__ int warp_tot[GNT / 32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+    int b = 0;
+    for (int k = lane; k < (int)blockIdx.x; k += 32) b += bcnt[k];
+    b = __reduce_add_sync(0xffffffffu, b);
+    if (lane == 0) {
+      s_base = b;
+      if (blockIdx.x == gridDim.x - 1 && o.count) *o.count = b + bcnt[blockIdx.x];
+    }
+  }
+  const int i = blockIdx.x * GNT + threadIdx.x;
+  const int f = (i < d.n && d.alive[i]) ? 1 : 0;
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  const int wpre = __popc(bal & ((1u << lane) - 1u));
+  if (lane == 0) warp_tot[wid] = __popc(bal);
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < wid; ++w) off += warp_tot[w];
+  const int pos = s_base + off + wpre;
+  if (f) {
+    if (o.x3) { o.x3[3 * pos] = d.x[i]; o.x3[3 * pos + 1] = d.y[i]; o.x3[3 * pos + 2] = d.z[i]; }
+    if (o.v3) { o.v3[3 * pos] = d.vx[i]; o.v3[3 * pos + 1] = d.vy[i]; o.v3[3 * pos + 2] = d.vz[i]; }
+    if (o.m) o.m[pos] = d.m[i];
+    if (o.R) o.R[pos] = d.R[i];
+    if (o.rc) o.rc[pos] = d.rc[i];
+    if (o.ids) o.ids[pos] = d.id[i];
+  }
+}
+
+// bcnt: one int per block of GNT slots (the workspace's union-find labels,
+// free outside the encounter kernel)
 void launch_gather(const Dev& d, double* x3, double* v3, double* m, double* R, double* rc,
                    int* ids, int* count, cudaStream_t st) {
   GatherOut o{x3, v3, m, R, rc, ids, count};
-  k_gather<<<1, 1024, 0, st>>>(d, o);
+  const int nb = (d.n + GNT - 1) / GNT;
+  k_gather_count<<<nb, GNT, 0, st>>>(d, d.uf);
+  k_gather<<<nb, GNT, 0, st>>>(d, o, d.uf);
 }
 
 // Interleaved <-> SoA helpers for the cached force.
