@@ -142,3 +142,24 @@ def test_shard_partition_covers_every_row():
             assert b[0][0] == 0 and b[-1][1] == n
             assert all(b[k][1] == b[k + 1][0] for k in range(world - 1))
             assert all(r1 - r0 <= -(-n // world) for r0, r1 in b)
+
+
+def test_state_error_splits_encounter_and_quiet_bodies():
+    """The accuracy report's error of a state against the oracle's: common ids
+    only, and with the oracle's encounter log the bodies that entered an
+    encounter apart from the quiet rest (the 1e-12 bar applies to those)."""
+    import numpy as np
+    import bench
+    b = {"ids": np.array([0, 1, 2, 3, 4]), "x": np.ones((5, 3))}
+    a = {"ids": np.array([0, 1, 2, 4]), "x": np.ones((4, 3))}  # body 3 absorbed on one side
+    a["x"][2] *= 1 + 1e-10   # id 2: an encounter body
+    a["x"][3] *= 1 + 5e-13   # id 4: quiet
+    log = np.array([[0, 2, 3], [7, 1, 2]], np.int32)  # (step, id_i, id_j)
+    e = bench._state_err(a, b, log)
+    assert e["bodies"] == 4 and not e["ids_identical"]
+    assert e["bodies_above_1e-12"] == 1 and e["encounter_bodies"] == 2
+    assert e["encounter_bodies_above_1e-12"] == 1
+    assert abs(e["max"] - 1e-10) < 1e-16 and 4e-13 < e["quiet_max"] < 6e-13
+    q = bench._state_err(a, b, np.zeros((0, 3), np.int32))
+    assert q["encounter_bodies"] == 0 and q["quiet_max"] == q["max"]
+    assert "quiet_max" not in bench._state_err(a, b)
